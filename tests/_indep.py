@@ -1,0 +1,85 @@
+"""Independent numpy restatements used by the oracle pins.
+
+Nothing here imports the oracle.  These helpers restate the problem
+definition (speed fields, node kinds, h = k / c) and the Q1 transition
+weights so that the pins can check the oracle with a *different* algorithm
+(Dijkstra, policy iteration with exact linear solves, absorption
+probabilities) rather than by re-running its own code.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+
+def speed_np(p, x: np.ndarray) -> np.ndarray:
+    """c(x) for x of shape (M, dim)."""
+    q = p.speed_params
+    if p.speed == "one":
+        return np.ones(x.shape[0])
+    if p.speed == "sincos2d":
+        return 1.0 + q[0] * np.sin(2 * math.pi * x[:, 0]) * np.cos(2 * math.pi * x[:, 1])
+    if p.speed == "sin3d":
+        return 1.0 + q[0] * np.sin(math.pi * x[:, 0]) * np.sin(math.pi * x[:, 1]) * np.sin(math.pi * x[:, 2])
+    if p.speed == "fourier2d":
+        a = q[:16].reshape(4, 4)
+        th = q[16:32].reshape(4, 4)
+        ps = q[32:48].reshape(4, 4)
+        g = np.zeros(x.shape[0])
+        for i in range(4):
+            for j in range(4):
+                g += a[i, j] * np.cos(math.pi * i * x[:, 0] / 2 + th[i, j]) * np.cos(math.pi * j * x[:, 1] / 2 + ps[i, j])
+        return 1.0 + 0.5 * g / np.abs(a).sum()
+    raise ValueError(p.speed)
+
+
+def node_grid(p):
+    """Integer node indices (N, dim) with i1 fastest, and coordinates."""
+    rng = [range(p.n[d]) for d in range(p.dim)]
+    idx = np.array([t[::-1] for t in itertools.product(*reversed(rng))], dtype=np.int64)
+    x = np.array(p.lo[: p.dim]) + idx * p.spacing
+    return idx, x
+
+
+def linear(p, idx):
+    idx = np.atleast_2d(idx)
+    out = idx[:, 0].copy()
+    mul = p.n[0]
+    for d in range(1, p.dim):
+        out += idx[:, d] * mul
+        mul *= p.n[d]
+    return out
+
+
+def kinds(p):
+    """0 free, 1 target (part >= 0), 2 ghost; h = k / c(x)."""
+    idx, x = node_grid(p)
+    N = idx.shape[0]
+    part = np.full(N, -1)
+    for j in range(p.n_targets - 1, -1, -1):
+        c, r = p.targets[j, : p.dim], p.targets[j, p.dim]
+        part[np.linalg.norm(x - c, axis=1) <= r] = j
+    ring = np.zeros(N, bool)
+    for d in range(p.dim):
+        ring |= (idx[:, d] == 0) | (idx[:, d] == p.n[d] - 1)
+    kind = np.where(part >= 0, 1, np.where(ring, 2, 0))
+    h = p.spacing / speed_np(p, x)
+    return kind, part, h
+
+
+def q1_corners(p, node_idx, a):
+    """Corners and bilinear/trilinear weights of the foot node_idx + a (grid
+    coordinates); zero weights dropped."""
+    xi = np.asarray(node_idx, float) + np.asarray(a, float)
+    base = np.clip(np.floor(xi).astype(int), 0, np.array(p.n[: p.dim]) - 2)
+    t = xi - base
+    out = []
+    for bits in itertools.product((0, 1), repeat=p.dim):
+        w = 1.0
+        for d, b in enumerate(bits):
+            w *= t[d] if b else 1.0 - t[d]
+        if w > 0:
+            out.append((int(linear(p, base + np.array(bits))[0]), w))
+    return out
