@@ -1,0 +1,177 @@
+/*
+ * hjbp.h -- C ABI of the GB300 patchy semi-Lagrangian solver for the
+ * minimum-time Hamilton-Jacobi-Bellman equation
+ *
+ *     max_a { -f(x,a) . grad u(x) - 1 } = 0  on R^d \ Omega_0,   u = 0 on Omega_0
+ *
+ * (Cacace, Cristiani, Falcone, Picarelli, "A patchy dynamic programming scheme
+ * for a class of HJB equations", Sec. 1, Eq. (HJB)), solved on a box Omega with
+ * state constraints on its boundary.
+ *
+ * Conventions used by every entry point:
+ *  - Every call returns an hjbp_status; nothing is thrown across the ABI.  On
+ *    failure hjbp_last_error() returns a thread-local message.
+ *  - Host arrays passed in are owned by the caller and copied before the call
+ *    returns (create) or read during the call (set_initial).
+ *  - Device memory belongs to the plan.  It comes from the allocator given at
+ *    create (for example the PyTorch caching allocator) or, if none is given,
+ *    from cudaMallocAsync on the plan's stream.  It is released by destroy.
+ *  - Grids are node-centred: n[d] nodes per axis (n[d]-1 cells), equal
+ *    spacing k on every axis, node index i = i1 + n1*(i2 + n2*i3) (x1 fastest).
+ *  - All work of a plan runs on the CUDA stream given at create; calls that
+ *    return data to the host synchronise that stream.
+ */
+#ifndef HJBP_H
+#define HJBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HJBP_OK = 0,
+    HJBP_EINVAL = 1,    /* invalid descriptor or argument */
+    HJBP_ENOMEM = 2,    /* device or host allocation failed */
+    HJBP_ENOCONV = 3,   /* sweep cap reached before the sup-norm test passed; results stay readable */
+    HJBP_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    HJBP_ECUDA = 5,     /* a CUDA runtime call failed */
+    HJBP_EBUSY = 6,     /* not admissible now (server), or the plan is still running */
+    HJBP_ESTATE = 7     /* call not valid in the plan's current state */
+} hjbp_status;
+
+/* Speed fields c(x) of the dynamics f(x, a) = c(x) a, |a| = 1 (a fixed menu).
+ *  HJBP_C_ONE        c = 1                                   (eikonal)
+ *  HJBP_C_SINCOS2D   c = 1 + p0 sin(2 pi x1) cos(2 pi x2)
+ *  HJBP_C_SIN3D      c = 1 + p0 sin(pi x1) sin(pi x2) sin(pi x3)
+ *  HJBP_C_FOURIER2D  c = 1 + 0.5 g(x),  g = sum_{p,q=0..3} a_pq cos(pi p x1/2 + th_pq)
+ *                                       cos(pi q x2/2 + ps_pq) / sum |a_pq|,
+ *                    params = [a (16, row-major in p,q), th (16), ps (16)]          */
+typedef enum { HJBP_C_ONE = 0, HJBP_C_SINCOS2D = 1, HJBP_C_SIN3D = 2, HJBP_C_FOURIER2D = 3 } hjbp_speed_kind;
+
+/* Arithmetic of the fine-grid sweeps.  HJBP_FP64: every sweep in FP64.
+ * HJBP_FP32_POLISH64: bulk sweeps in FP32, then FP64 polishing sweeps.      */
+typedef enum { HJBP_FP64 = 0, HJBP_FP32_POLISH64 = 1 } hjbp_precision;
+
+/* Problem descriptor (Sec. 2.1 and Sec. 3 of the paper):
+ *   dim            2 or 3
+ *   n[3]           nodes per side of the fine grid G (n[2] ignored in 2D)
+ *   n_coarse[3]    nodes per side of the coarse grid G~; n_coarse[0] == 0 asks
+ *                  for the plain global solve (no patches)
+ *   lo[3], hi[3]   the box Omega; (hi-lo)/(n-1) must be equal on all axes
+ *   speed, speed_params[64]   c(x), see hjbp_speed_kind
+ *   n_controls, controls      discrete control set A: n_controls x dim unit
+ *                  vectors (row-major), 1 <= n_controls <= HJBP_MAX_CONTROLS
+ *   n_targets, targets        Omega_0 = union of balls: n_targets x (dim+1)
+ *                  rows (centre, radius); ball j is target part Omega_0^j and
+ *                  seeds patch j (1 <= n_targets <= HJBP_MAX_TARGETS)
+ *   tol            sup-norm stopping tolerance of the fine-grid iteration
+ *                  (Sec. 2.2, Step 4)
+ *   tol_coarse     same on the coarse grid (Step 1); <= 0 selects 1e-12
+ *   tol_phi        same for the colour transport (Step 3.1); <= 0 selects 1e-10
+ *   precision      hjbp_precision
+ *   max_sweeps     cap on tile sweeps per phase (<= 0 selects 1e6)            */
+#define HJBP_MAX_CONTROLS 256
+#define HJBP_MAX_TARGETS 64
+typedef struct {
+    int dim;
+    int n[3];
+    int n_coarse[3];
+    double lo[3];
+    double hi[3];
+    int speed;
+    double speed_params[64];
+    int n_controls;
+    const double *controls;
+    int n_targets;
+    const double *targets;
+    double tol;
+    double tol_coarse;
+    double tol_phi;
+    int precision;
+    int max_sweeps;
+} hjbp_problem_desc;
+
+/* Device allocator hooks (optional).  alloc returns device memory of at least
+ * `bytes` usable on `stream`, or NULL; release returns it.  ctx is passed back
+ * unchanged.                                                                  */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*release)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} hjbp_allocator;
+
+typedef struct hjbp_plan hjbp_plan;
+
+/* Per-solve statistics.  Sweep counts are tile-sweep launches (each launch
+ * runs every active tile through its in-tile Gauss-Seidel passes).           */
+typedef struct {
+    int n_patches;
+    int sweeps_coarse;
+    int sweeps_phi;
+    int sweeps_reach;
+    int sweeps_fine;
+    int sweeps_polish;
+    int sweeps_patch[HJBP_MAX_TARGETS];   /* launches in which patch j had an active tile */
+    int64_t patch_nodes[HJBP_MAX_TARGETS];
+    int64_t patch_tiles[HJBP_MAX_TARGETS];
+    double residual_fine;                 /* last sup-norm change of the FP32/FP64 bulk */
+    double residual_polish;               /* last FP64 polishing change */
+    int64_t unreachable;                  /* free nodes with value +inf */
+    int64_t uncovered_filled;             /* Remark 3.1 neighbour fills */
+    int64_t node_updates;                 /* node updates executed on the fine grid */
+    int64_t node_control_updates;         /* node_updates x controls */
+    double ms_setup, ms_coarse, ms_feedback, ms_labels, ms_compact, ms_fine, ms_polish, ms_total;
+} hjbp_stats;
+
+/* Validate the descriptor, copy its arrays, allocate device memory.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * allocator: optional, see hjbp_allocator.  Errors: EINVAL, ENOMEM, ECUDA.  */
+hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const hjbp_allocator *allocator,
+                        hjbp_plan **out);
+
+/* Run the whole solve (global SL of Eq. (iterativeSLscheme), or the patchy
+ * algorithm of Sec. 3, Steps 1-4) on the plan's stream.  Returns after the
+ * work is complete.  Errors: ENOCONV (results readable), ECUDA, ETIMEOUT.   */
+hjbp_status hjbp_solve(hjbp_plan *plan);
+
+/* Copy the N = prod n[d] fine-grid values (FP64, +INFINITY where the target
+ * cannot be reached) into host_out.                                          */
+hjbp_status hjbp_get_values(hjbp_plan *plan, double *host_out);
+
+/* Copy the N patch labels: j on patch j and on target part j, -1 on the ghost
+ * ring and on unreachable nodes (global solve: 0 / part index / -1).         */
+hjbp_status hjbp_get_labels(hjbp_plan *plan, int8_t *host_out);
+
+/* Intermediate arrays of the patchy algorithm (for verification):
+ *  HJBP_OUT_UCOARSE  coarse values U~_P (FP64, N~)          Step 1
+ *  HJBP_OUT_U0       U_P^(0) on G (FP64, N)                 Step 2
+ *  HJBP_OUT_ASTAR    coarse feedback index a*_k~ (int32, N; -1 undefined)  Step 2
+ *  HJBP_OUT_PHI      colour fields phi^j (FP64, R x N)      Step 3.1
+ *  HJBP_OUT_U32      FP32 bulk values before polishing (float, N)
+ * Errors: EINVAL (unknown id or not produced by this plan), ESTATE.          */
+enum { HJBP_OUT_UCOARSE = 0, HJBP_OUT_U0 = 1, HJBP_OUT_ASTAR = 2, HJBP_OUT_PHI = 3, HJBP_OUT_U32 = 4 };
+hjbp_status hjbp_get_intermediate(hjbp_plan *plan, int which, void *host_out, size_t bytes);
+
+/* Borrowed device pointers (valid until destroy): FP64 values and int8 labels. */
+hjbp_status hjbp_get_device_views(hjbp_plan *plan, const double **u, const int8_t **labels);
+
+hjbp_status hjbp_get_stats(hjbp_plan *plan, hjbp_stats *out);
+
+/* Node count N and coarse count N~ of the plan.                              */
+hjbp_status hjbp_get_sizes(hjbp_plan *plan, int64_t *n_nodes, int64_t *n_coarse_nodes);
+
+void hjbp_destroy(hjbp_plan *plan);
+
+const char *hjbp_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch.                        */
+int hjbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJBP_H */

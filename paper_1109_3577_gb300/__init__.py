@@ -1,0 +1,34 @@
+"""GB300-native patchy semi-Lagrangian solver for minimum-time HJB equations.
+
+A thin ctypes binding over ``libhjbp.so`` (C ABI in ``include/hjbp.h``).  Every
+step of a solve runs in the library's CUDA kernels; this module only marshals
+arguments.  There is no CPU fallback: if the library is missing the first call
+raises.
+"""
+from ._binding import (  # noqa: F401
+    HJBP_FP32_POLISH64,
+    HJBP_FP64,
+    HJBP_OUT_ASTAR,
+    HJBP_OUT_PHI,
+    HJBP_OUT_U0,
+    HJBP_OUT_U32,
+    HJBP_OUT_UCOARSE,
+    HjbpError,
+    Plan,
+    Stats,
+    desc_from_problem,
+    hjbp_create,
+    hjbp_destroy,
+    hjbp_get_device_views,
+    hjbp_get_intermediate,
+    hjbp_get_labels,
+    hjbp_get_sizes,
+    hjbp_get_stats,
+    hjbp_get_values,
+    hjbp_last_error,
+    hjbp_solve,
+    hjbp_version,
+    library,
+    library_path,
+    torch_allocator,
+)

@@ -1,0 +1,328 @@
+"""ctypes marshalling for libhjbp (names follow include/hjbp.h)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libhjbp.so")
+_lock = threading.Lock()
+_lib = None
+
+HJBP_OK, HJBP_EINVAL, HJBP_ENOMEM, HJBP_ENOCONV, HJBP_ETIMEOUT, HJBP_ECUDA, HJBP_EBUSY, HJBP_ESTATE = range(8)
+HJBP_FP64, HJBP_FP32_POLISH64 = 0, 1
+HJBP_OUT_UCOARSE, HJBP_OUT_U0, HJBP_OUT_ASTAR, HJBP_OUT_PHI, HJBP_OUT_U32 = range(5)
+MAX_CONTROLS, MAX_TARGETS = 256, 64
+SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3}
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ETIMEOUT", 5: "ECUDA", 6: "EBUSY", 7: "ESTATE"}
+
+
+class HjbpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hjbp {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("n", C.c_int * 3),
+        ("n_coarse", C.c_int * 3),
+        ("lo", C.c_double * 3),
+        ("hi", C.c_double * 3),
+        ("speed", C.c_int),
+        ("speed_params", C.c_double * 64),
+        ("n_controls", C.c_int),
+        ("controls", C.POINTER(C.c_double)),
+        ("n_targets", C.c_int),
+        ("targets", C.POINTER(C.c_double)),
+        ("tol", C.c_double),
+        ("tol_coarse", C.c_double),
+        ("tol_phi", C.c_double),
+        ("precision", C.c_int),
+        ("max_sweeps", C.c_int),
+    ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n_patches", C.c_int),
+        ("sweeps_coarse", C.c_int),
+        ("sweeps_phi", C.c_int),
+        ("sweeps_reach", C.c_int),
+        ("sweeps_fine", C.c_int),
+        ("sweeps_polish", C.c_int),
+        ("sweeps_patch", C.c_int * MAX_TARGETS),
+        ("patch_nodes", C.c_int64 * MAX_TARGETS),
+        ("patch_tiles", C.c_int64 * MAX_TARGETS),
+        ("residual_fine", C.c_double),
+        ("residual_polish", C.c_double),
+        ("unreachable", C.c_int64),
+        ("uncovered_filled", C.c_int64),
+        ("node_updates", C.c_int64),
+        ("node_control_updates", C.c_int64),
+        ("ms_setup", C.c_double),
+        ("ms_coarse", C.c_double),
+        ("ms_feedback", C.c_double),
+        ("ms_labels", C.c_double),
+        ("ms_compact", C.c_double),
+        ("ms_fine", C.c_double),
+        ("ms_polish", C.c_double),
+        ("ms_total", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {}
+        R = max(1, self.n_patches)
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v[:R]) if hasattr(v, "__len__") else v
+        return out
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def library():
+    """Load libhjbp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with paper_1109_3577_gb300/build.py "
+                              "(there is no CPU fallback)")
+        lib = C.CDLL(_LIB_PATH)
+        P = C.POINTER
+        vp = C.c_void_p
+        lib.hjbp_create.argtypes = [P(Desc), vp, P(Allocator), P(vp)]
+        lib.hjbp_create.restype = C.c_int
+        lib.hjbp_solve.argtypes = [vp]
+        lib.hjbp_solve.restype = C.c_int
+        lib.hjbp_get_values.argtypes = [vp, vp]
+        lib.hjbp_get_values.restype = C.c_int
+        lib.hjbp_get_labels.argtypes = [vp, vp]
+        lib.hjbp_get_labels.restype = C.c_int
+        lib.hjbp_get_intermediate.argtypes = [vp, C.c_int, vp, C.c_size_t]
+        lib.hjbp_get_intermediate.restype = C.c_int
+        lib.hjbp_get_device_views.argtypes = [vp, P(vp), P(vp)]
+        lib.hjbp_get_device_views.restype = C.c_int
+        lib.hjbp_get_stats.argtypes = [vp, P(Stats)]
+        lib.hjbp_get_stats.restype = C.c_int
+        lib.hjbp_get_sizes.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
+        lib.hjbp_get_sizes.restype = C.c_int
+        lib.hjbp_destroy.argtypes = [vp]
+        lib.hjbp_destroy.restype = None
+        lib.hjbp_last_error.argtypes = []
+        lib.hjbp_last_error.restype = C.c_char_p
+        lib.hjbp_version.argtypes = []
+        lib.hjbp_version.restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != HJBP_OK:
+        raise HjbpError(status, hjbp_last_error())
+
+
+# ----------------------------------------------------------- C-ABI names ---
+
+def hjbp_version() -> int:
+    return library().hjbp_version()
+
+
+def hjbp_last_error() -> str:
+    m = library().hjbp_last_error()
+    return m.decode() if m else ""
+
+
+def hjbp_create(desc: Desc, stream: int = 0, allocator: Optional[Allocator] = None) -> int:
+    plan = C.c_void_p()
+    st = library().hjbp_create(C.byref(desc), C.c_void_p(stream), C.byref(allocator) if allocator else None,
+                               C.byref(plan))
+    _check(st)
+    return plan.value
+
+
+def hjbp_solve(plan: int) -> int:
+    """Returns the status (OK or ENOCONV); raises on every other error."""
+    st = library().hjbp_solve(C.c_void_p(plan))
+    if st not in (HJBP_OK, HJBP_ENOCONV):
+        _check(st)
+    return st
+
+
+def hjbp_get_values(plan: int, out: np.ndarray) -> None:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(library().hjbp_get_values(C.c_void_p(plan), out.ctypes.data_as(C.c_void_p)))
+
+
+def hjbp_get_labels(plan: int, out: np.ndarray) -> None:
+    assert out.dtype == np.int8 and out.flags.c_contiguous
+    _check(library().hjbp_get_labels(C.c_void_p(plan), out.ctypes.data_as(C.c_void_p)))
+
+
+def hjbp_get_intermediate(plan: int, which: int, out: np.ndarray) -> None:
+    assert out.flags.c_contiguous
+    _check(library().hjbp_get_intermediate(C.c_void_p(plan), which, out.ctypes.data_as(C.c_void_p), out.nbytes))
+
+
+def hjbp_get_device_views(plan: int):
+    u, lab = C.c_void_p(), C.c_void_p()
+    _check(library().hjbp_get_device_views(C.c_void_p(plan), C.byref(u), C.byref(lab)))
+    return u.value, lab.value
+
+
+def hjbp_get_stats(plan: int) -> Stats:
+    s = Stats()
+    _check(library().hjbp_get_stats(C.c_void_p(plan), C.byref(s)))
+    return s
+
+
+def hjbp_get_sizes(plan: int):
+    n, nc = C.c_int64(), C.c_int64()
+    _check(library().hjbp_get_sizes(C.c_void_p(plan), C.byref(n), C.byref(nc)))
+    return n.value, nc.value
+
+
+def hjbp_destroy(plan: int) -> None:
+    library().hjbp_destroy(C.c_void_p(plan))
+
+
+# ------------------------------------------------------------ conveniences ---
+
+def torch_allocator() -> Allocator:
+    """Allocator hooks that draw device memory from PyTorch's caching allocator."""
+    import torch
+
+    live = {}
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+        live[ptr] = nbytes
+        return ptr
+
+    def _release(ptr, nbytes, stream, ctx):
+        live.pop(ptr, None)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator(ALLOC_FN(_alloc), RELEASE_FN(_release), None)
+    a._keep = (_alloc, _release, live)  # keep the callbacks alive
+    return a
+
+
+def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0):
+    """Build an hjbp_problem_desc from a workloads.Problem.  Returns the
+    struct plus the arrays it points into (keep both alive)."""
+    controls = np.ascontiguousarray(p.controls, dtype=np.float64)
+    targets = np.ascontiguousarray(p.targets, dtype=np.float64)
+    d = Desc()
+    d.dim = p.dim
+    for a in range(3):
+        d.n[a] = int(p.n[a]) if a < p.dim else 1
+        d.n_coarse[a] = (int(p.n_coarse[a]) if a < p.dim else 1) if p.n_coarse else 0
+        d.lo[a] = float(p.lo[a])
+        d.hi[a] = float(p.hi[a])
+    d.speed = SPEED_KINDS[p.speed]
+    for i in range(64):
+        d.speed_params[i] = float(p.speed_params[i])
+    d.n_controls = controls.shape[0]
+    d.controls = controls.ctypes.data_as(C.POINTER(C.c_double))
+    d.n_targets = targets.shape[0]
+    d.targets = targets.ctypes.data_as(C.POINTER(C.c_double))
+    d.tol = float(p.tol)
+    d.tol_coarse = float(p.tol_coarse)
+    d.tol_phi = float(p.tol_phi)
+    d.precision = int(precision)
+    d.max_sweeps = int(max_sweeps or 0)
+    return d, (controls, targets)
+
+
+class Plan:
+    """Owns one hjbp_plan.  ``Plan(problem).solve()`` then ``values()`` /
+    ``labels()`` / ``stats()``."""
+
+    def __init__(self, problem, precision: int = HJBP_FP32_POLISH64, stream: Optional[int] = None,
+                 use_torch_allocator: bool = False, max_sweeps: int = 0):
+        self.problem = problem
+        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps)
+        if stream is None:
+            stream = 0
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                pass
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.handle = hjbp_create(self._desc, stream, self._alloc)
+        self.N, self.Nc = hjbp_get_sizes(self.handle)
+        self.status = None
+
+    def solve(self) -> int:
+        self.status = hjbp_solve(self.handle)
+        return self.status
+
+    def values(self) -> np.ndarray:
+        out = np.empty(self.N, np.float64)
+        hjbp_get_values(self.handle, out)
+        return out
+
+    def labels(self) -> np.ndarray:
+        out = np.empty(self.N, np.int8)
+        hjbp_get_labels(self.handle, out)
+        return out
+
+    def intermediate(self, which: int) -> np.ndarray:
+        R = self.problem.n_targets
+        if which == HJBP_OUT_UCOARSE:
+            out = np.empty(self.Nc, np.float64)
+        elif which == HJBP_OUT_U0:
+            out = np.empty(self.N, np.float64)
+        elif which == HJBP_OUT_ASTAR:
+            out = np.empty(self.N, np.int32)
+        elif which == HJBP_OUT_PHI:
+            out = np.empty((R, self.N), np.float64)
+        elif which == HJBP_OUT_U32:
+            out = np.empty(self.N, np.float32)
+        else:
+            raise ValueError(which)
+        hjbp_get_intermediate(self.handle, which, out)
+        return out
+
+    def stats(self) -> dict:
+        return hjbp_get_stats(self.handle).as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hjbp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

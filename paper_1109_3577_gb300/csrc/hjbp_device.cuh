@@ -1,0 +1,109 @@
+// hjbp_device.cuh -- types and helpers shared by the CUDA kernels of libhjbp.
+//
+// Node codes (int8, one per node) drive every kernel:
+//   -1          hard +inf node: ghost ring dG (state constraints, Sec. 2.1),
+//               a node outside the set S* that reaches the target, or (in a
+//               per-patch solve) nothing else needs it;
+//   0 .. 63     free node belonging to patch j (the plain global solve uses 0);
+//   64 + j      target node of part Omega_0^j (value fixed by the caller).
+// A free node of patch j reads a neighbour as usable iff its code is j or
+// 64 + j; every other neighbour is +inf for it (state constraints on the
+// patch boundary, Sec. 3 "Details on boundary conditions").
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hjbp.h"
+
+namespace hjbp {
+
+constexpr int kTile = 32;                 // 2D tile side (one warp per tile)
+constexpr int kMaxControls = HJBP_MAX_CONTROLS;
+constexpr int kMaxTargets = HJBP_MAX_TARGETS;
+constexpr int8_t kHard = -1;
+constexpr int8_t kTargetBase = 64;
+constexpr uint8_t kNoControl = 255;
+
+// +inf is carried as a finite sentinel so that a zero weight times "+inf"
+// stays 0 (R3: corners of weight 0 are skipped); anything at or above the
+// threshold is +inf.  The start value M of the fixed-point iteration on S*
+// lies far below the threshold (R14).
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static __host__ __device__ constexpr float big() { return 1.0e30f; }
+    static __host__ __device__ constexpr float thresh() { return 1.0e25f; }
+};
+template <> struct Num<double> {
+    static __host__ __device__ constexpr double big() { return 1.0e300; }
+    static __host__ __device__ constexpr double thresh() { return 1.0e290; }
+};
+constexpr double kStartValue = 1.0e6;     // M, above every solution value (R14)
+constexpr double kU0Bound = 1.0e6;        // bound replacing +inf inside U_P^(0) (R7)
+
+// Control table in the self-solved form (R13) grouped by quadrant.  For a
+// control a with foot x_i + k a the cell corners other than x_i are
+// (i+sx, j), (i, j+sy), (i+sx, j+sy), sx = sign(a_x), sy = sign(a_y) (a >= 0
+// counts as +), with Q1 weights w10 = |a_x|(1-|a_y|), w01 = (1-|a_x|)|a_y|,
+// w11 = |a_x||a_y| and self weight w00 = (1-|a_x|)(1-|a_y|).  kap = 1/(1-w00)
+// and kw* = kap * w*; the update of node i under control a is
+//   kap * (w10 u10 + w01 u01 + w11 u11 + h_i).
+// Quadrant q = (sx > 0) + 2 (sy > 0); controls of quadrant q occupy
+// [qbeg[q], qbeg[q+1]).
+template <typename T> struct CtlTable2 {
+    int nc;
+    int qbeg[5];
+    T kw10[kMaxControls];
+    T kw01[kMaxControls];
+    T kw11[kMaxControls];
+    T kap[kMaxControls];
+};
+
+// Literal Q1 weights in the caller's control order, for Eq. (feedbackcontrol).
+struct CtlLiteral2 {
+    int nc;
+    int8_t sx[kMaxControls];
+    int8_t sy[kMaxControls];
+    double w00[kMaxControls];
+    double w10[kMaxControls];
+    double w01[kMaxControls];
+    double w11[kMaxControls];
+};
+
+// Support masks for the almost-sure reachability sweep: bit 0 corner 10,
+// bit 1 corner 01, bit 2 corner 11 (positive weight).  present[q] has bit m
+// set when some control of quadrant q needs exactly mask m.
+struct ReachTable2 {
+    uint8_t present[4];
+};
+
+// Geometry of a 2D grid and its tiling of the interior nodes 1..n-2.
+struct Grid2 {
+    int n0, n1;        // nodes per side
+    int ntx, nty;      // tiles per side
+    double lo0, lo1, k;
+};
+
+// Device-side state of one tile-sweep phase (active list, parities, ...).
+struct TileSched {
+    int *list[2];         // active tile lists (double-buffered by launch parity)
+    int *count;           // count[2]
+    float *chg[2];        // per-tile max change of the last launch (double-buffered)
+    uint8_t *latest;      // which value buffer holds each tile's current values
+    uint8_t *processed;   // tile ran in the current launch
+    uint64_t *tile_patch; // patch bitmask of each tile (for per-patch sweep counts)
+    uint64_t *patch_hist; // per-launch mask of patches with an active tile
+    float *res_hist;      // per-launch max change
+};
+
+__device__ __forceinline__ int tile_of(const Grid2 &g, int x, int y) {
+    if (x < 1 || y < 1 || x > g.n0 - 2 || y > g.n1 - 2) return -1;
+    return ((y - 1) / kTile) * g.ntx + (x - 1) / kTile;
+}
+
+__device__ __forceinline__ float atomic_max_pos(float *addr, float v) {
+    // non-negative floats order like their bit patterns
+    return __int_as_float(atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v)));
+}
+
+}  // namespace hjbp

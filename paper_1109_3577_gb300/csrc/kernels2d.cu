@@ -1,0 +1,1214 @@
+// kernels2d.cu -- CUDA kernels of the 2D path (sm_103a).
+//
+// Every hot step runs here: set-up of the node codes and time steps,
+// the almost-sure reachability sweep (S*), the semi-Lagrangian value sweep of
+// Eq. (SLscheme) (FP32 bulk / FP64), the colour transport of Eq.
+// (HJBridotta_discreta) (FP64), the coarse feedback of Eq. (feedbackcontrol)
+// (FP64), labels, patch compaction and the FP64 polishing pass.
+//
+// Tiled sweeps: the interior nodes 1..n-2 are cut into 32x32 tiles, one warp
+// per tile.  A tile loads itself plus a one-node halo into shared memory
+// (the foot x_i + k a of every control lies in the 3x3 neighbourhood, Sec.
+// 2.1: |h f| = k), runs line Gauss-Seidel passes in the four axis directions
+// (in each step the 32 lanes update one column or one row), and writes the
+// tile back.  Across tiles the iteration is block-Jacobi: each launch reads the
+// values of the previous launch (two value buffers, a per-tile parity bit says
+// which one is current), so results do not depend on the order in which tiles
+// run.  Only tiles whose 3x3 tile neighbourhood changed by more than the
+// tolerance in the previous launch run again; the solve stops when none is
+// left, which is the sup-norm test of Sec. 2.2 (Step 4) on launches.
+#include <cmath>
+#include <cstdint>
+
+#include "hjbp_device.cuh"
+#include "plan.h"
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+namespace hjbp {
+
+struct SpeedParams {
+    int kind;
+    double p[64];
+};
+
+struct TargetSet {
+    int n;
+    double c0[kMaxTargets], c1[kMaxTargets], c2[kMaxTargets], r[kMaxTargets];
+};
+
+// c(x) of f(x, a) = c(x) a (fixed menu, see hjbp_speed_kind).
+__device__ double speed_at(const SpeedParams &sp, double x0, double x1, double x2) {
+    const double pi = 3.14159265358979323846;
+    switch (sp.kind) {
+    case HJBP_C_ONE:
+        return 1.0;
+    case HJBP_C_SINCOS2D:
+        return 1.0 + sp.p[0] * sin(2.0 * pi * x0) * cos(2.0 * pi * x1);
+    case HJBP_C_SIN3D:
+        return 1.0 + sp.p[0] * sin(pi * x0) * sin(pi * x1) * sin(pi * x2);
+    case HJBP_C_FOURIER2D: {
+        double g = 0.0, norm = 0.0;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                const int m = 4 * a + b;
+                g += sp.p[m] * cos(pi * a * x0 / 2.0 + sp.p[16 + m]) * cos(pi * b * x1 / 2.0 + sp.p[32 + m]);
+                norm += fabs(sp.p[m]);
+            }
+        return 1.0 + 0.5 * g / norm;
+    }
+    default:
+        return nan("");
+    }
+}
+
+// ------------------------------------------------------------------ set-up --
+
+// Node codes, h_i = k / c(x_i) (|h f| = k, Sec. 2.1) and the fixed values of
+// target nodes.  Target part j: |x - c_j| <= r_j + extra (lowest j).  With
+// boundary_values, a target node outside its ball gets the time
+// (|x - c_j| - r_j) / c(x) to reach it (the coarse grid, Step 1); otherwise 0.
+// Coordinates and distances use explicitly rounded operations so that target
+// membership is decided exactly as x = lo + i k, r^2 = sum (x - c)^2 dictate.
+__global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
+                          int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
+                          double *__restrict__ fixed) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+        const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
+        const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
+        int part = -1;
+        double dist = 0.0;
+        for (int j = 0; j < ts.n && part < 0; ++j) {
+            const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]);
+            const double r2 = __dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1));
+            const double d = __dsqrt_rn(r2);
+            if (d <= __dadd_rn(ts.r[j], extra)) {
+                part = j;
+                dist = __dsub_rn(d, ts.r[j]);
+            }
+        }
+        const bool ring = ix == 0 || iy == 0 || ix == g.n0 - 1 || iy == g.n1 - 1;
+        const double c = speed_at(sp, x0, x1, 0.0);
+        const double hh = __ddiv_rn(g.k, c);
+        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : (ring ? kHard : (int8_t)0);
+        if (h32) h32[i] = (float)hh;
+        if (h64) h64[i] = hh;
+        if (fixed) fixed[i] = (part >= 0 && boundary_values && dist > 0.0) ? __ddiv_rn(dist, c) : 0.0;
+    }
+}
+
+// Start values of a value solve (R14): M on free nodes, the fixed value on
+// targets, +inf on hard nodes; written to both buffers.
+template <typename T>
+__global__ void k_init_values2d(int64_t N, const int8_t *__restrict__ code, const double *__restrict__ fixed,
+                                T start, T *__restrict__ b0, T *__restrict__ b1) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        T v;
+        if (c < 0) v = Num<T>::big();
+        else if (c >= kTargetBase) v = fixed ? (T)fixed[i] : (T)0;
+        else v = start;
+        b0[i] = v;
+        b1[i] = v;
+    }
+}
+
+// ------------------------------------------------------------ scheduling --
+
+// After each tile launch: flip the parity of the tiles that ran, activate every
+// tile whose 3x3 tile neighbourhood changed by more than tol, record the max
+// change and the patches that are still active, clear the other change buffer.
+__global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch) {
+    const int ntiles = g.ntx * g.nty;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    if (s.processed[t]) {
+        s.latest[t] ^= 1;
+        s.processed[t] = 0;
+    }
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    bool act = false;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int ux = tx + dx, uy = ty + dy;
+            if (ux < 0 || uy < 0 || ux >= g.ntx || uy >= g.nty) continue;
+            if (s.chg[par][uy * g.ntx + ux] > tol) act = true;
+        }
+    if (act) {
+        const int k = atomicAdd(&s.count[par ^ 1], 1);
+        s.list[par ^ 1][k] = t;
+    }
+    const float my = s.chg[par][t];
+    if (my > tol && s.tile_patch && s.patch_hist)
+        atomicOr(reinterpret_cast<unsigned long long *>(&s.patch_hist[launch]),
+                 (unsigned long long)s.tile_patch[t]);
+    if (my > 0.f && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
+    s.chg[par ^ 1][t] = 0.f;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Shared-memory image of one tile plus its halo.
+template <typename T> struct TileSmem {
+    T u[kTile + 2][kTile + 3];
+    int8_t c[kTile + 2][kTile + 4];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_tile(const Grid2 &g, const TileSched &s, const int8_t *__restrict__ code,
+                                          const T *__restrict__ b0, const T *__restrict__ b1, int x0, int y0,
+                                          TileSmem<T> &sm) {
+    const int lane = threadIdx.x;
+    for (int r = 0; r < kTile + 2; ++r) {
+        const int y = y0 - 1 + r;
+        for (int c = lane; c < kTile + 2; c += 32) {
+            const int x = x0 - 1 + c;
+            T v = Num<T>::big();
+            int8_t cd = kHard;
+            if (x < g.n0 && y < g.n1) {
+                const int64_t i = (int64_t)y * g.n0 + x;
+                cd = code[i];
+                const int tt = tile_of(g, x, y);
+                v = (tt >= 0 && s.latest[tt]) ? b1[i] : b0[i];
+            }
+            sm.u[r][c] = v;
+            sm.c[r][c] = cd;
+        }
+    }
+    __syncwarp();
+}
+
+// Write the tile's interior to the buffer that is not current, return the
+// warp's max |new - old| (0 where both are +inf).
+template <typename T>
+__device__ __forceinline__ float store_tile(const Grid2 &g, const TileSched &s, int t, T *__restrict__ b0,
+                                            T *__restrict__ b1, int x0, int y0, const TileSmem<T> &sm) {
+    const int lane = threadIdx.x;
+    const int cur = s.latest[t];
+    T *dst = cur ? b0 : b1;
+    const T *src = cur ? b1 : b0;
+    float mc = 0.f;
+    const int x = x0 + lane;
+    for (int r = 1; r <= kTile; ++r) {
+        const int y = y0 - 1 + r;
+        if (y > g.n1 - 2) break;
+        if (x > g.n0 - 2) continue;
+        const int64_t i = (int64_t)y * g.n0 + x;
+        const T v = sm.u[r][1 + lane];
+        const T o = src[i];
+        dst[i] = v;
+        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
+        float d;
+        if (vi && oi) d = 0.f;
+        else if (vi || oi) d = 3.0e38f;
+        else d = (float)fabs((double)v - (double)o);
+        mc = fmaxf(mc, d);
+    }
+    return warp_max(mc);
+}
+
+// --------------------------------------------------- value sweep (a6, a0) --
+
+// Self-solved SL update (R13) of node (c, r) of the tile for patch code cd:
+//   min over controls of kap (w10 u10 + w01 u01 + w11 u11 + h_i);
+// neighbours outside patch cd and its target part read +inf.  Returns +inf
+// sentinel when no control has all its positive-weight corners finite.
+template <typename T>
+__device__ __forceinline__ T sl_update(const TileSmem<T> &sm, int c, int r, int8_t cd, T hh,
+                                       const CtlTable2<T> &ct) {
+    const int8_t tg = (int8_t)(cd + kTargetBase);
+    T nb[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
+            nb[dy][dx] = (q == cd || q == tg) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+        }
+    T best = Num<T>::big();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+        const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
+        for (int m = ct.qbeg[q]; m < ct.qbeg[q + 1]; ++m) {
+            T v = ct.kap[m] * hh;
+            v = fma(ct.kw10[m], a10, v);
+            v = fma(ct.kw01[m], a01, v);
+            v = fma(ct.kw11[m], a11, v);
+            best = v < best ? v : best;
+        }
+    }
+    return best;
+}
+
+// One launch of the value iteration over the active tiles.  kClamp: monotone
+// update u <- min(u, F(u)) from the start value M (bulk); without it the
+// plain update u <- F(u) (polishing from a state near the fixed point).
+template <typename T, bool kClamp>
+__global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restrict__ code,
+                                                const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
+                                                TileSched s, int par, int rounds, unsigned long long *updates,
+                                                const CtlTable2<T> ct) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    __shared__ TileSmem<T> sm;
+    load_tile(g, s, code, b0, b1, x0, y0, sm);
+    const int lane = threadIdx.x;
+    int nfree = 0;
+    for (int r = 1; r <= kTile; ++r) {
+        const int8_t cd = sm.c[r][1 + lane];
+        nfree += (cd >= 0 && cd < kTargetBase);
+    }
+    for (int rd = 0; rd < rounds; ++rd) {
+        for (int dir = 0; dir < 4; ++dir) {
+            for (int st = 0; st < kTile; ++st) {
+                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+                const int c = (dir < 2) ? s1 : 1 + lane;
+                const int r = (dir < 2) ? 1 + lane : s1;
+                const int8_t cd = sm.c[r][c];
+                const bool active = cd >= 0 && cd < kTargetBase;
+                T nw = sm.u[r][c];
+                if (active) {
+                    const int64_t i = (int64_t)(y0 - 1 + r) * g.n0 + (x0 - 1 + c);
+                    const T best = sl_update(sm, c, r, cd, h[i], ct);
+                    if (best < Num<T>::thresh()) nw = kClamp ? (best < nw ? best : nw) : best;
+                }
+                __syncwarp();
+                if (active) sm.u[r][c] = nw;
+                __syncwarp();
+            }
+        }
+    }
+    const float mc = store_tile(g, s, t, b0, b1, x0, y0, sm);
+    const int nf = warp_sum(nfree);
+    if (lane == 0) {
+        s.chg[par][t] = mc;
+        s.processed[t] = 1;
+        if (updates) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+    }
+}
+
+// -------------------------------------------- almost-sure reachability (S*) --
+
+// Positive-probability reachability within the candidate set: a free node
+// becomes reached when some control whose positive-weight corners (other than
+// the node) are all usable puts positive weight on a reached node or on its
+// own target part (R14).  In place; monotone, so the order does not matter.
+__global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restrict__ code,
+                                                uint8_t *__restrict__ rch, TileSched s, int par,
+                                                ReachTable2 rt) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    __shared__ uint8_t sr[kTile + 2][kTile + 4];
+    __shared__ int8_t sc[kTile + 2][kTile + 4];
+    const int lane = threadIdx.x;
+    for (int r = 0; r < kTile + 2; ++r) {
+        const int y = y0 - 1 + r;
+        for (int c = lane; c < kTile + 2; c += 32) {
+            const int x = x0 - 1 + c;
+            uint8_t v = 0;
+            int8_t cd = kHard;
+            if (x < g.n0 && y < g.n1) {
+                const int64_t i = (int64_t)y * g.n0 + x;
+                cd = code[i];
+                v = rch[i];
+            }
+            sr[r][c] = v;
+            sc[r][c] = cd;
+        }
+    }
+    __syncwarp();
+    int flips = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int dir = 0; dir < 4; ++dir) {
+            for (int st = 0; st < kTile; ++st) {
+                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+                const int c = (dir < 2) ? s1 : 1 + lane;
+                const int r = (dir < 2) ? 1 + lane : s1;
+                const int8_t cd = sc[r][c];
+                bool hit = false;
+                if (cd >= 0 && cd < kTargetBase && !sr[r][c]) {
+                    const int8_t tg = (int8_t)(cd + kTargetBase);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
+                        const int8_t q10 = sc[r][c + sx], q01 = sc[r + sy][c], q11 = sc[r + sy][c + sx];
+                        const unsigned us = (unsigned)(q10 == cd || q10 == tg) | ((unsigned)(q01 == cd || q01 == tg) << 1) |
+                                            ((unsigned)(q11 == cd || q11 == tg) << 2);
+                        const unsigned rb = (unsigned)(q10 == tg || (q10 == cd && sr[r][c + sx])) |
+                                            ((unsigned)(q01 == tg || (q01 == cd && sr[r + sy][c])) << 1) |
+                                            ((unsigned)(q11 == tg || (q11 == cd && sr[r + sy][c + sx])) << 2);
+                        const unsigned pres = rt.present[q];
+                        for (unsigned m = 1; m < 8; ++m)
+                            if ((pres >> m) & 1u)
+                                if ((us & m) == m && (rb & m)) hit = true;
+                    }
+                }
+                __syncwarp();
+                if (hit) {
+                    sr[r][c] = 1;
+                    ++flips;
+                }
+                __syncwarp();
+            }
+        }
+    const int x = x0 + lane;
+    for (int r = 1; r <= kTile; ++r) {
+        const int y = y0 - 1 + r;
+        if (y > g.n1 - 2) break;
+        if (x > g.n0 - 2) continue;
+        rch[(int64_t)y * g.n0 + x] = sr[r][1 + lane];
+    }
+    const int nf = warp_sum(flips);
+    if (lane == 0) {
+        s.chg[par][t] = nf > 0 ? 1.f : 0.f;
+        s.processed[t] = 1;
+    }
+}
+
+// Free nodes not reached leave the candidate set (become hard); counts them.
+__global__ void k_reach_prune(int64_t N, int8_t *__restrict__ code, const uint8_t *__restrict__ rch,
+                              unsigned long long *removed) {
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c >= 0 && c < kTargetBase && !rch[i]) {
+            code[i] = kHard;
+            ++cnt;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(removed, cnt);
+}
+
+// ------------------------------------------------------------- gathering --
+
+template <typename T>
+__global__ void k_gather2d(Grid2 g, const uint8_t *__restrict__ latest, const T *__restrict__ b0,
+                           const T *__restrict__ b1, T *__restrict__ out_t, double *__restrict__ out64) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.n0), y = (int)(i / g.n0);
+        const int tt = tile_of(g, x, y);
+        const T v = (tt >= 0 && latest[tt]) ? b1[i] : b0[i];
+        if (out_t) out_t[i] = v;
+        if (out64) out64[i] = v >= Num<T>::thresh() ? (double)INFINITY : (double)v;
+    }
+}
+
+// ---------------------------------------------------- Step 2: U_P^(0), a* --
+
+// U_P^(0)(x_i) = Q1 of the coarse values at the fine node (R7: a coarse +inf
+// enters as the bound M; >= M means unreachable); 0 on fine targets, +inf on
+// the fine ghost ring.
+__global__ void k_u0_2d(Grid2 g, Grid2 gc, const int8_t *__restrict__ code, const double *__restrict__ uc,
+                        double *__restrict__ u0) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c >= kTargetBase) { u0[i] = 0.0; continue; }
+        if (c < 0) { u0[i] = Num<double>::big(); continue; }
+        const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+        const double xi0 = (double)ix * (double)(gc.n0 - 1) / (double)(g.n0 - 1);
+        const double xi1 = (double)iy * (double)(gc.n1 - 1) / (double)(g.n1 - 1);
+        int b0 = (int)floor(xi0), b1 = (int)floor(xi1);
+        b0 = min(max(b0, 0), gc.n0 - 2);
+        b1 = min(max(b1, 0), gc.n1 - 2);
+        const double t0 = xi0 - b0, t1 = xi1 - b1;
+        double sum = 0.0;
+        for (int cc = 0; cc < 4; ++cc) {
+            const double w = ((cc & 1) ? t0 : 1.0 - t0) * ((cc & 2) ? t1 : 1.0 - t1);
+            if (w > 0.0) {
+                const double v = uc[(int64_t)(b1 + ((cc >> 1) & 1)) * gc.n0 + b0 + (cc & 1)];
+                sum += w * (v >= Num<double>::thresh() ? kU0Bound : v);
+            }
+        }
+        u0[i] = sum >= kU0Bound ? Num<double>::big() : sum;
+    }
+}
+
+// a*_k~(x_i) = argmin_a { I[U_P^(0)](x_i + k a) + h_i } (Eq. feedbackcontrol),
+// literal Q1 with the node itself as a corner, controls in the caller's order,
+// lowest index on ties (R10); 255 where every control meets +inf.
+__global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const double *__restrict__ h,
+                             const double *__restrict__ u0, uint8_t *__restrict__ astar, const CtlLiteral2 cl) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c < 0 || c >= kTargetBase || u0[i] >= Num<double>::thresh()) {
+            astar[i] = kNoControl;
+            continue;
+        }
+        const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+        double nb[3][3];
+        for (int dy = 0; dy < 3; ++dy)
+            for (int dx = 0; dx < 3; ++dx) {
+                const int x = ix - 1 + dx, y = iy - 1 + dy;
+                nb[dy][dx] = (x >= 0 && y >= 0 && x < g.n0 && y < g.n1) ? u0[(int64_t)y * g.n0 + x]
+                                                                         : Num<double>::big();
+            }
+        const double hh = h[i];
+        double best = Num<double>::big();
+        int arg = kNoControl;
+        for (int m = 0; m < cl.nc; ++m) {
+            const int sx = cl.sx[m] > 0 ? 2 : 0, sy = cl.sy[m] > 0 ? 2 : 0;
+            double a10, a01, a11;
+            if (sx) { a10 = nb[1][2]; } else { a10 = nb[1][0]; }
+            if (sy) { a01 = nb[2][1]; a11 = sx ? nb[2][2] : nb[2][0]; } else { a01 = nb[0][1]; a11 = sx ? nb[0][2] : nb[0][0]; }
+            const double v = cl.w00[m] * nb[1][1] + cl.w10[m] * a10 + cl.w01[m] * a01 + cl.w11[m] * a11 + hh;
+            if (v < best) {
+                best = v;
+                arg = m;
+            }
+        }
+        astar[i] = best < Num<double>::thresh() ? (uint8_t)arg : kNoControl;
+    }
+}
+
+// --------------------------------------------------- Step 3.1: colours phi --
+
+struct PhiCtl {
+    int8_t sx[kMaxControls], sy[kMaxControls];
+    double kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls];
+};
+
+// phi values of a colour at set-up: 1 on target part j, 0 elsewhere.
+__global__ void k_phi_init2d(int64_t N, const int8_t *__restrict__ code, int j, double *__restrict__ b0,
+                             double *__restrict__ b1) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = code[i] == (int8_t)(kTargetBase + j) ? 1.0 : 0.0;
+        b0[i] = v;
+        b1[i] = v;
+    }
+}
+
+// One launch of Eq. (HJBridotta_discreta) over the active tiles, solved for
+// phi_i at each node (R13): phi_i = kap (w10 phi10 + w01 phi01 + w11 phi11)
+// with the node's fixed coarse feedback a*_i.  phi rises monotonically from 0.
+__global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
+                                              const uint8_t *__restrict__ astar, double *__restrict__ b0,
+                                              double *__restrict__ b1, TileSched s, int par, int rounds,
+                                              const PhiCtl *__restrict__ pc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    __shared__ TileSmem<double> sm;
+    load_tile(g, s, code, b0, b1, x0, y0, sm);
+    const int lane = threadIdx.x;
+    for (int rd = 0; rd < rounds; ++rd) {
+        for (int dir = 0; dir < 4; ++dir) {
+            for (int st = 0; st < kTile; ++st) {
+                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+                const int c = (dir < 2) ? s1 : 1 + lane;
+                const int r = (dir < 2) ? 1 + lane : s1;
+                const int8_t cd = sm.c[r][c];
+                double nw = sm.u[r][c];
+                bool active = false;
+                if (cd >= 0 && cd < kTargetBase) {
+                    const int64_t i = (int64_t)(y0 - 1 + r) * g.n0 + (x0 - 1 + c);
+                    const uint8_t a = astar[i];
+                    if (a != kNoControl) {
+                        active = true;
+                        const int sx = pc->sx[a], sy = pc->sy[a];
+                        const double v = pc->kw10[a] * sm.u[r][c + sx] + pc->kw01[a] * sm.u[r + sy][c] +
+                                         pc->kw11[a] * sm.u[r + sy][c + sx];
+                        nw = v > nw ? v : nw;
+                    }
+                }
+                __syncwarp();
+                if (active) sm.u[r][c] = nw;
+                __syncwarp();
+            }
+        }
+    }
+    const float mc = store_tile(g, s, t, b0, b1, x0, y0, sm);
+    if (lane == 0) {
+        s.chg[par][t] = mc;
+        s.processed[t] = 1;
+    }
+}
+
+// label = argmax_j phi^j if positive (lowest j on ties, R12); targets keep
+// their part; -1 on hard / unreachable nodes; -2 marks uncovered nodes.
+__global__ void k_label2d(int64_t N, const int8_t *__restrict__ code, const uint8_t *__restrict__ astar,
+                          const double *__restrict__ phi, int R, int8_t *__restrict__ label) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c >= kTargetBase) { label[i] = (int8_t)(c - kTargetBase); continue; }
+        if (c < 0 || astar[i] == kNoControl) { label[i] = -1; continue; }
+        double mx = 0.0;
+        int arg = -2;
+        for (int j = 0; j < R; ++j) {
+            const double v = phi[(int64_t)j * N + i];
+            if (v > mx) { mx = v; arg = j; }
+        }
+        label[i] = (int8_t)arg;
+    }
+}
+
+// One Jacobi round of the neighbour fill of Remark 3.1 (R12): an uncovered
+// node takes the label of its first labelled axis neighbour in increasing
+// node index (-y, -x, +x, +y).
+__global__ void k_fill2d(Grid2 g, const int8_t *__restrict__ lin, int8_t *__restrict__ lout,
+                         unsigned long long *changed) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        int8_t v = lin[i];
+        if (v == -2) {
+            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            int8_t nv = -2;
+            if (iy > 0 && lin[i - g.n0] >= 0) nv = lin[i - g.n0];
+            else if (ix > 0 && lin[i - 1] >= 0) nv = lin[i - 1];
+            else if (ix < g.n0 - 1 && lin[i + 1] >= 0) nv = lin[i + 1];
+            else if (iy < g.n1 - 1 && lin[i + g.n0] >= 0) nv = lin[i + g.n0];
+            if (nv >= 0) { v = nv; ++cnt; }
+        }
+        lout[i] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(changed, cnt);
+}
+
+// Codes of the per-patch solves: free node of patch j -> j, target part j ->
+// 64 + j, everything else hard.  Leftover uncovered nodes (-2) become -1.
+__global__ void k_patch_codes(int64_t N, const int8_t *__restrict__ code0, int8_t *__restrict__ label,
+                              int8_t *__restrict__ code) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c0 = code0[i];
+        int8_t l = label[i];
+        if (l == -2) { l = -1; label[i] = -1; }
+        if (c0 >= kTargetBase) code[i] = c0;
+        else if (c0 < 0 || l < 0) code[i] = kHard;
+        else code[i] = l;
+    }
+}
+
+// ------------------------------------------------------ patch compaction --
+
+// Per tile: bitmask of the patches with a free node in it and per-patch node
+// counts; per patch: its tile count.  (Step 3.1 assembles the patches; the
+// tile masks let every sweep launch report which patches are still active.)
+__global__ void __launch_bounds__(32) k_compact2d(Grid2 g, const int8_t *__restrict__ code,
+                                                  uint64_t *__restrict__ tile_patch,
+                                                  unsigned long long *__restrict__ patch_nodes,
+                                                  unsigned long long *__restrict__ patch_tiles) {
+    const int t = blockIdx.x;
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    const int lane = threadIdx.x;
+    uint64_t mask = 0;
+    const int x = x0 + lane;
+    for (int r = 0; r < kTile; ++r) {
+        const int y = y0 + r;
+        if (y > g.n1 - 2) break;
+        int8_t c = kHard;
+        if (x <= g.n0 - 2) c = code[(int64_t)y * g.n0 + x];
+        if (c >= 0 && c < kTargetBase) mask |= 1ull << c;
+    }
+    for (int o = 16; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+    // per-patch node counts: one ballot per patch present in the tile
+    uint64_t m = mask;
+    while (m) {
+        const int j = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        int cnt = 0;
+        for (int r = 0; r < kTile; ++r) {
+            const int y = y0 + r;
+            if (y > g.n1 - 2) break;
+            const bool is = x <= g.n0 - 2 && code[(int64_t)y * g.n0 + x] == (int8_t)j;
+            cnt += __popc(__ballot_sync(0xffffffffu, is));
+        }
+        if (lane == 0) {
+            atomicAdd(&patch_nodes[j], (unsigned long long)cnt);
+            atomicAdd(&patch_tiles[j], 1ull);
+        }
+    }
+    if (lane == 0) tile_patch[t] = mask;
+}
+
+// ------------------------------------------------- FP64 polishing pass (a8) --
+
+// u_out = F(u_in) in FP64 at every free node (self-solved form, no clamp),
+// one Jacobi application; max |change| into *maxchg.
+__global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const double *__restrict__ h,
+                           const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
+                           const CtlTable2<double> ct) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    float mc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t cd = code[i];
+        double v = uin[i];
+        if (cd >= 0 && cd < kTargetBase) {
+            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            const int8_t tg = (int8_t)(cd + kTargetBase);
+            double nb[3][3];
+            for (int dy = 0; dy < 3; ++dy)
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int64_t j = (int64_t)(iy - 1 + dy) * g.n0 + (ix - 1 + dx);
+                    const int8_t q = code[j];
+                    const double w = uin[j];
+                    nb[dy][dx] = (q == cd || q == tg) ? (w >= Num<double>::thresh() ? Num<double>::big() : w)
+                                                      : Num<double>::big();
+                }
+            double best = Num<double>::big();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+                const double a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
+                for (int m = ct.qbeg[q]; m < ct.qbeg[q + 1]; ++m) {
+                    double w = ct.kap[m] * h[i];
+                    w = fma(ct.kw10[m], a10, w);
+                    w = fma(ct.kw01[m], a01, w);
+                    w = fma(ct.kw11[m], a11, w);
+                    best = w < best ? w : best;
+                }
+            }
+            if (best < Num<double>::thresh() && v < Num<double>::thresh()) {
+                mc = fmaxf(mc, (float)fabs(best - v));
+                v = best;
+            }
+        }
+        uout[i] = v;
+    }
+    mc = warp_max(mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(maxchg, mc);
+}
+
+// A global solve has one target (the union of all parts): every target node
+// gets code 64 + 0 so that free nodes (code 0) read all of them.
+__global__ void k_merge_targets(int64_t N, int8_t *__restrict__ code) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        if (code[i] >= kTargetBase) code[i] = kTargetBase;
+}
+
+// Output labels: j on patch j (0 for the global solve) and on target part j,
+// -1 on the ghost ring and on free nodes outside S*; counts the latter.
+__global__ void k_final_labels(int64_t N, const int8_t *__restrict__ code0, const int8_t *__restrict__ code,
+                               int8_t *__restrict__ label, unsigned long long *unreachable) {
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        const int8_t c0 = code0[i];
+        label[i] = c0 >= kTargetBase ? (int8_t)(c0 - kTargetBase) : (c >= 0 && c < kTargetBase ? c : (int8_t)-1);
+        if (c0 >= 0 && c0 < kTargetBase && c < 0) ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(unreachable, cnt);
+}
+
+// FP32 bulk -> FP64 (and +inf sentinels)
+__global__ void k_widen(int64_t N, const float *__restrict__ in, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = in[i];
+        out[i] = v >= Num<float>::thresh() ? Num<double>::big() : (double)v;
+    }
+}
+
+__global__ void k_finalize(int64_t N, const double *__restrict__ in, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in[i];
+        out[i] = v >= Num<double>::thresh() ? (double)INFINITY : v;
+    }
+}
+
+// ---------------------------------------------------------- instantiation --
+
+template __global__ void k_init_values2d<float>(int64_t, const int8_t *, const double *, float, float *, float *);
+template __global__ void k_init_values2d<double>(int64_t, const int8_t *, const double *, double, double *, double *);
+template __global__ void k_value2d<float, true>(Grid2, const int8_t *, const float *, float *, float *, TileSched, int,
+                                                int, unsigned long long *, const CtlTable2<float>);
+template __global__ void k_value2d<double, true>(Grid2, const int8_t *, const double *, double *, double *, TileSched,
+                                                 int, int, unsigned long long *, const CtlTable2<double>);
+template __global__ void k_gather2d<float>(Grid2, const uint8_t *, const float *, const float *, float *, double *);
+template __global__ void k_gather2d<double>(Grid2, const uint8_t *, const double *, const double *, double *,
+                                            double *);
+
+}  // namespace hjbp
+
+// =====================================================================
+// Host driver of the 2D path
+// =====================================================================
+namespace hjbp {
+namespace {
+
+// The reachability sweep is monotone and settles after at most one launch per
+// node of the longest path; its cap is independent of max_sweeps.
+constexpr int kReachCap = 1 << 18;
+
+inline int grid_for(int64_t n, int bs = 256) {
+    int64_t b = (n + bs - 1) / bs;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+template <typename T> T *alloc_n(hjbp_plan &p, int64_t n) {
+    return static_cast<T *>(p.dev_alloc(sizeof(T) * (size_t)std::max<int64_t>(n, 1)));
+}
+
+struct Sched {
+    TileSched d{};
+    int ntiles = 0;
+    int hist = 0;
+    int *count_hist = nullptr;
+    int *iota = nullptr;
+};
+
+__global__ void k_iota(int n, int *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
+}
+
+__global__ void k_count_hist(TileSched s, int par, int launch, int *hist) { hist[launch] = s.count[par]; }
+
+Sched make_sched(hjbp_plan &p, const Grid2 &g, int hist) {
+    Sched s;
+    s.ntiles = g.ntx * g.nty;
+    s.hist = hist;
+    const int nt = std::max(1, s.ntiles);
+    s.d.list[0] = alloc_n<int>(p, nt);
+    s.d.list[1] = alloc_n<int>(p, nt);
+    s.d.count = alloc_n<int>(p, 2);
+    s.d.chg[0] = alloc_n<float>(p, nt);
+    s.d.chg[1] = alloc_n<float>(p, nt);
+    s.d.latest = alloc_n<uint8_t>(p, nt);
+    s.d.processed = alloc_n<uint8_t>(p, nt);
+    s.d.tile_patch = nullptr;
+    s.d.patch_hist = alloc_n<uint64_t>(p, hist);
+    s.d.res_hist = alloc_n<float>(p, hist);
+    s.count_hist = alloc_n<int>(p, hist);
+    s.iota = alloc_n<int>(p, nt);
+    k_iota<<<grid_for(nt), 256, 0, p.stream>>>(nt, s.iota);
+    return s;
+}
+
+void reset_sched(hjbp_plan &p, Sched &s) {
+    cudaStream_t st = p.stream;
+    const int nt = std::max(1, s.ntiles);
+    check_cuda(cudaMemcpyAsync(s.d.list[0], s.iota, sizeof(int) * nt, cudaMemcpyDeviceToDevice, st), "reset list");
+    const int counts[2] = {s.ntiles, 0};
+    check_cuda(cudaMemcpyAsync(s.d.count, counts, sizeof(counts), cudaMemcpyHostToDevice, st), "reset count");
+    check_cuda(cudaMemsetAsync(s.d.chg[0], 0, sizeof(float) * nt, st), "reset chg");
+    check_cuda(cudaMemsetAsync(s.d.chg[1], 0, sizeof(float) * nt, st), "reset chg");
+    check_cuda(cudaMemsetAsync(s.d.latest, 0, nt, st), "reset latest");
+    check_cuda(cudaMemsetAsync(s.d.processed, 0, nt, st), "reset processed");
+    check_cuda(cudaMemsetAsync(s.d.patch_hist, 0, sizeof(uint64_t) * s.hist, st), "reset hist");
+    check_cuda(cudaMemsetAsync(s.d.res_hist, 0, sizeof(float) * s.hist, st), "reset hist");
+    check_cuda(cudaMemsetAsync(s.count_hist, 0, sizeof(int) * s.hist, st), "reset hist");
+    // the counts copied from a host stack array must land before it goes away
+    check_cuda(cudaStreamSynchronize(st), "reset sync");
+}
+
+struct RunResult {
+    int launches = 0;        // launches that had work
+    bool converged = false;
+    float last_res = 0.f;
+};
+
+// Launch sweep+schedule pairs until no tile is active or the cap is hit.
+template <class Sweep>
+RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, Sweep sweep) {
+    RunResult rr;
+    if (s.ntiles == 0) {
+        rr.converged = true;
+        return rr;
+    }
+    reset_sched(p, s);
+    cap = std::min(cap, s.hist);
+    int par = 0, L = 0;
+    int *pinned = nullptr;
+    check_cuda(cudaMallocHost(&pinned, sizeof(int)), "pinned");
+    int check_every = 4;
+    while (L < cap) {
+        sweep(par, L);
+        check_cuda(cudaGetLastError(), "sweep launch");
+        k_count_hist<<<1, 1, 0, p.stream>>>(s.d, par, L, s.count_hist);
+        k_schedule2d<<<(s.ntiles + 255) / 256, 256, 0, p.stream>>>(g, s.d, par, tol, L);
+        check_cuda(cudaGetLastError(), "schedule launch");
+        par ^= 1;
+        ++L;
+        if (L % check_every == 0 || L == cap) {
+            check_cuda(cudaMemcpyAsync(pinned, s.d.count + par, sizeof(int), cudaMemcpyDeviceToHost, p.stream),
+                       "count readback");
+            check_cuda(cudaStreamSynchronize(p.stream), "sweep sync");
+            if (*pinned == 0) {
+                rr.converged = true;
+                break;
+            }
+            check_every = std::min(check_every * 2, 16);
+        }
+    }
+    cudaFreeHost(pinned);
+    std::vector<int> ch(L);
+    std::vector<float> rh(L);
+    if (L) {
+        check_cuda(cudaMemcpyAsync(ch.data(), s.count_hist, sizeof(int) * L, cudaMemcpyDeviceToHost, p.stream), "hist");
+        check_cuda(cudaMemcpyAsync(rh.data(), s.d.res_hist, sizeof(float) * L, cudaMemcpyDeviceToHost, p.stream),
+                   "hist");
+        check_cuda(cudaStreamSynchronize(p.stream), "hist sync");
+    }
+    for (int l = 0; l < L; ++l)
+        if (ch[l] > 0) {
+            rr.launches = l + 1;
+            rr.last_res = rh[l];
+        }
+    return rr;
+}
+
+template <typename T> CtlTable2<T> make_table(const hjbp_plan &p) {
+    CtlTable2<T> ct;
+    std::memset(&ct, 0, sizeof(ct));
+    const int nc = p.desc.n_controls;
+    ct.nc = nc;
+    std::vector<int> order[4];
+    for (int m = 0; m < nc; ++m) {
+        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        order[(ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0)].push_back(m);
+    }
+    int pos = 0;
+    for (int q = 0; q < 4; ++q) {
+        ct.qbeg[q] = pos;
+        for (int m : order[q]) {
+            const double ax = std::fabs(p.controls[2 * m]), ay = std::fabs(p.controls[2 * m + 1]);
+            const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
+            const double kap = 1.0 / (1.0 - w00);
+            ct.kw10[pos] = (T)(kap * w10);
+            ct.kw01[pos] = (T)(kap * w01);
+            ct.kw11[pos] = (T)(kap * w11);
+            ct.kap[pos] = (T)kap;
+            ++pos;
+        }
+    }
+    ct.qbeg[4] = pos;
+    return ct;
+}
+
+CtlLiteral2 make_literal(const hjbp_plan &p) {
+    CtlLiteral2 cl;
+    std::memset(&cl, 0, sizeof(cl));
+    cl.nc = p.desc.n_controls;
+    for (int m = 0; m < cl.nc; ++m) {
+        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double bx = std::fabs(ax), by = std::fabs(ay);
+        cl.sx[m] = ax >= 0.0 ? 1 : -1;
+        cl.sy[m] = ay >= 0.0 ? 1 : -1;
+        cl.w00[m] = (1.0 - bx) * (1.0 - by);
+        cl.w10[m] = bx * (1.0 - by);
+        cl.w01[m] = (1.0 - bx) * by;
+        cl.w11[m] = bx * by;
+    }
+    return cl;
+}
+
+ReachTable2 make_reach(const hjbp_plan &p) {
+    ReachTable2 rt;
+    std::memset(&rt, 0, sizeof(rt));
+    for (int m = 0; m < p.desc.n_controls; ++m) {
+        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double bx = std::fabs(ax), by = std::fabs(ay);
+        const unsigned need = (unsigned)(bx * (1.0 - by) > 0.0) | ((unsigned)((1.0 - bx) * by > 0.0) << 1) |
+                              ((unsigned)(bx * by > 0.0) << 2);
+        if (need) rt.present[(ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0)] |= (uint8_t)(1u << need);
+    }
+    return rt;
+}
+
+SpeedParams make_speed(const hjbp_plan &p) {
+    SpeedParams sp;
+    sp.kind = p.desc.speed;
+    for (int i = 0; i < 64; ++i) sp.p[i] = p.desc.speed_params[i];
+    return sp;
+}
+
+TargetSet make_targets(const hjbp_plan &p) {
+    TargetSet ts;
+    std::memset(&ts, 0, sizeof(ts));
+    const int d = p.desc.dim;
+    ts.n = p.desc.n_targets;
+    for (int j = 0; j < ts.n; ++j) {
+        ts.c0[j] = p.targets[(d + 1) * j + 0];
+        ts.c1[j] = p.targets[(d + 1) * j + 1];
+        ts.c2[j] = d == 3 ? p.targets[(d + 1) * j + 2] : 0.0;
+        ts.r[j] = p.targets[(d + 1) * j + d];
+    }
+    return ts;
+}
+
+Grid2 make_grid(int n0, int n1, double lo0, double lo1, double k) {
+    Grid2 g;
+    g.n0 = n0;
+    g.n1 = n1;
+    g.ntx = (n0 - 2 + kTile - 1) / kTile;
+    g.nty = (n1 - 2 + kTile - 1) / kTile;
+    g.lo0 = lo0;
+    g.lo1 = lo1;
+    g.k = k;
+    return g;
+}
+
+struct Ev {
+    cudaEvent_t e;
+    explicit Ev(cudaStream_t s) {
+        check_cuda(cudaEventCreate(&e), "event");
+        check_cuda(cudaEventRecord(e, s), "event record");
+    }
+    ~Ev() { cudaEventDestroy(e); }
+};
+
+float ms_between(const Ev &a, const Ev &b) {
+    float ms = 0.f;
+    cudaEventSynchronize(b.e);
+    cudaEventElapsedTime(&ms, a.e, b.e);
+    return ms;
+}
+
+// S* on the current codes (R14): reach from the targets, prune, repeat.
+int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, int cap, int64_t N) {
+    const ReachTable2 rt = make_reach(p);
+    unsigned long long *removed = alloc_n<unsigned long long>(p, 1);
+    int total = 0;
+    for (int round = 0; round < 64; ++round) {
+        check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
+        RunResult rr = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
+            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt);
+        });
+        total += rr.launches;
+        if (!rr.converged) throw HjbpError{HJBP_ECUDA, "reachability sweep did not settle"};
+        check_cuda(cudaMemsetAsync(removed, 0, sizeof(unsigned long long), p.stream), "memset");
+        k_reach_prune<<<grid_for(N), 256, 0, p.stream>>>(N, code, rch, removed);
+        unsigned long long h = 0;
+        check_cuda(cudaMemcpyAsync(&h, removed, sizeof(h), cudaMemcpyDeviceToHost, p.stream), "removed");
+        check_cuda(cudaStreamSynchronize(p.stream), "reach sync");
+        if (h == 0) break;
+    }
+    return total;
+}
+
+// Value iteration from M on S* (R14), monotone, to the sup-norm tolerance.
+template <typename T>
+RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, const double *fixed, T *b0, T *b1,
+                  Sched &s, double tol, int cap, int rounds, T *out_t, double *out64, unsigned long long *updates) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    k_init_values2d<T><<<grid_for(N), 256, 0, p.stream>>>(N, code, fixed, (T)kStartValue, b0, b1);
+    const CtlTable2<T> ct = make_table<T>(p);
+    RunResult rr = run_tiles(p, g, s, (float)tol, cap, [&](int par, int) {
+        k_value2d<T, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+    });
+    k_gather2d<T><<<grid_for(N), 256, 0, p.stream>>>(g, s.d.latest, b0, b1, out_t, out64);
+    check_cuda(cudaGetLastError(), "gather");
+    return rr;
+}
+
+}  // namespace
+
+hjbp_status solve2d(hjbp_plan &p) {
+    const hjbp_problem_desc &d = p.desc;
+    cudaStream_t st = p.stream;
+    const int64_t N = p.N;
+    const Grid2 g = make_grid(d.n[0], d.n[1], d.lo[0], d.lo[1], p.k);
+    const SpeedParams sp = make_speed(p);
+    const TargetSet ts = make_targets(p);
+    const int cap = d.max_sweeps > 0 ? d.max_sweeps : 1000000;
+    const int hist = std::max(std::min(cap, 1 << 20), kReachCap);
+    const bool fp32 = d.precision == HJBP_FP32_POLISH64;
+    const int R = d.n_targets;
+    hjbp_stats &S = p.stats;
+    std::memset(&S, 0, sizeof(S));
+    hjbp_status status = HJBP_OK;
+
+    Ev e0(st);
+    int8_t *code0 = alloc_n<int8_t>(p, N);
+    int8_t *code = alloc_n<int8_t>(p, N);
+    uint8_t *rch = alloc_n<uint8_t>(p, N);
+    double *h64 = alloc_n<double>(p, N);
+    float *h32 = fp32 ? alloc_n<float>(p, N) : nullptr;
+    unsigned long long *updates = alloc_n<unsigned long long>(p, 1);
+    check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
+    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr);
+    check_cuda(cudaGetLastError(), "setup");
+    Sched sched = make_sched(p, g, hist);
+    Ev e1(st);
+
+    if (p.patchy) {
+        // ---- Step 1: coarse solve (FP64)
+        const Grid2 gc = make_grid(d.n_coarse[0], d.n_coarse[1], d.lo[0], d.lo[1], p.kc);
+        const int64_t Nc = p.Nc;
+        int8_t *ccode = alloc_n<int8_t>(p, Nc);
+        uint8_t *crch = alloc_n<uint8_t>(p, Nc);
+        double *ch64 = alloc_n<double>(p, Nc);
+        double *cfix = alloc_n<double>(p, Nc);
+        double *cb0 = alloc_n<double>(p, Nc), *cb1 = alloc_n<double>(p, Nc);
+        k_setup2d<<<grid_for(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(2.0) / 2.0, 1, ccode, nullptr, ch64,
+                                                cfix);
+        k_merge_targets<<<grid_for(Nc), 256, 0, st>>>(Nc, ccode);
+        Sched csched = make_sched(p, gc, hist);
+        S.sweeps_reach += reach2d(p, gc, ccode, crch, csched, kReachCap, Nc);
+        const double tolc = d.tol_coarse > 0 ? d.tol_coarse : 1e-12;
+        RunResult rc = value2d<double>(p, gc, ccode, ch64, cfix, cb0, cb1, csched, tolc, cap, 2, nullptr, p.u_coarse,
+                                       nullptr);
+        S.sweeps_coarse = rc.launches;
+        if (!rc.converged) status = HJBP_ENOCONV;
+        Ev e2(st);
+        // ---- Step 2: U_P^(0) and the coarse feedback a*
+        k_u0_2d<<<grid_for(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0);
+        k_feedback2d<<<grid_for(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, make_literal(p));
+        check_cuda(cudaGetLastError(), "feedback");
+        Ev e3(st);
+        // ---- Step 3.1: colours phi^j, projection, Remark 3.1 fill
+        {
+            PhiCtl hpc;
+            std::memset(&hpc, 0, sizeof(hpc));
+            for (int m = 0; m < d.n_controls; ++m) {
+                const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+                const double bx = std::fabs(ax), by = std::fabs(ay);
+                const double kap = 1.0 / (1.0 - (1.0 - bx) * (1.0 - by));
+                hpc.sx[m] = ax >= 0 ? 1 : -1;
+                hpc.sy[m] = ay >= 0 ? 1 : -1;
+                hpc.kw10[m] = kap * bx * (1.0 - by);
+                hpc.kw01[m] = kap * (1.0 - bx) * by;
+                hpc.kw11[m] = kap * bx * by;
+            }
+            PhiCtl *dpc = static_cast<PhiCtl *>(p.dev_alloc(sizeof(PhiCtl)));
+            check_cuda(cudaMemcpyAsync(dpc, &hpc, sizeof(PhiCtl), cudaMemcpyHostToDevice, st), "phi ctl");
+            double *pb0 = alloc_n<double>(p, N), *pb1 = alloc_n<double>(p, N);
+            const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
+            for (int j = 0; j < R; ++j) {
+                k_phi_init2d<<<grid_for(N), 256, 0, st>>>(N, code0, j, pb0, pb1);
+                RunResult rp = run_tiles(p, g, sched, (float)tolp, cap, [&](int par, int) {
+                    k_phi2d<<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, pb0, pb1, sched.d, par, 2, dpc);
+                });
+                S.sweeps_phi += rp.launches;
+                if (!rp.converged) status = HJBP_ENOCONV;
+                k_gather2d<double><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, pb0, pb1, p.phi + (int64_t)j * N,
+                                                                nullptr);
+            }
+            k_label2d<<<grid_for(N), 256, 0, st>>>(N, code0, p.astar, p.phi, R, p.label_out);
+            int8_t *lab2 = reinterpret_cast<int8_t *>(rch);  // scratch (reach flags are reset before use)
+            unsigned long long *chg = alloc_n<unsigned long long>(p, 1);
+            for (int it = 0; it < 100000; ++it) {
+                check_cuda(cudaMemsetAsync(chg, 0, sizeof(unsigned long long), st), "memset");
+                k_fill2d<<<grid_for(N), 256, 0, st>>>(g, p.label_out, lab2, chg);
+                check_cuda(cudaMemcpyAsync(p.label_out, lab2, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
+                unsigned long long hc = 0;
+                check_cuda(cudaMemcpyAsync(&hc, chg, sizeof(hc), cudaMemcpyDeviceToHost, st), "fill count");
+                check_cuda(cudaStreamSynchronize(st), "fill sync");
+                S.uncovered_filled += (int64_t)hc;
+                if (!hc) break;
+            }
+            k_patch_codes<<<grid_for(N), 256, 0, st>>>(N, code0, p.label_out, code);
+        }
+        Ev e4(st);
+        // ---- patch compaction
+        {
+            uint64_t *tile_patch = alloc_n<uint64_t>(p, sched.ntiles);
+            unsigned long long *pn = alloc_n<unsigned long long>(p, kMaxTargets);
+            unsigned long long *pt = alloc_n<unsigned long long>(p, kMaxTargets);
+            check_cuda(cudaMemsetAsync(pn, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
+            check_cuda(cudaMemsetAsync(pt, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
+            if (sched.ntiles) k_compact2d<<<sched.ntiles, 32, 0, st>>>(g, code, tile_patch, pn, pt);
+            sched.d.tile_patch = tile_patch;
+            unsigned long long hn[kMaxTargets], ht[kMaxTargets];
+            check_cuda(cudaMemcpyAsync(hn, pn, sizeof(hn), cudaMemcpyDeviceToHost, st), "compact");
+            check_cuda(cudaMemcpyAsync(ht, pt, sizeof(ht), cudaMemcpyDeviceToHost, st), "compact");
+            check_cuda(cudaStreamSynchronize(st), "compact sync");
+            for (int j = 0; j < R; ++j) {
+                S.patch_nodes[j] = (int64_t)hn[j];
+                S.patch_tiles[j] = (int64_t)ht[j];
+            }
+        }
+        Ev e5(st);
+        S.ms_coarse = ms_between(e1, e2);
+        S.ms_feedback = ms_between(e2, e3);
+        S.ms_labels = ms_between(e3, e4);
+        S.ms_compact = ms_between(e4, e5);
+    } else {
+        check_cuda(cudaMemcpyAsync(code, code0, (size_t)N, cudaMemcpyDeviceToDevice, st), "code copy");
+        k_merge_targets<<<grid_for(N), 256, 0, st>>>(N, code);
+    }
+
+    // ---- Step 3.2 (or the global solve): S*, then the value iteration
+    Ev f0(st);
+    S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N);
+    RunResult rv;
+    if (fp32) {
+        float *b0 = alloc_n<float>(p, N), *b1 = alloc_n<float>(p, N);
+        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, 2, p.u32, nullptr, updates);
+    } else {
+        double *b0 = alloc_n<double>(p, N), *b1 = alloc_n<double>(p, N);
+        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, 2, nullptr, p.u_out, updates);
+    }
+    S.sweeps_fine = rv.launches;
+    S.residual_fine = rv.last_res;
+    if (!rv.converged) status = HJBP_ENOCONV;
+    // per-patch launch counts
+    if (rv.launches > 0) {
+        std::vector<uint64_t> ph(rv.launches);
+        check_cuda(cudaMemcpyAsync(ph.data(), sched.d.patch_hist, sizeof(uint64_t) * rv.launches,
+                                   cudaMemcpyDeviceToHost, st), "patch hist");
+        check_cuda(cudaStreamSynchronize(st), "patch hist sync");
+        for (int l = 0; l < rv.launches; ++l)
+            for (int j = 0; j < R && j < 64; ++j)
+                if ((ph[l] >> j) & 1ull) S.sweeps_patch[j]++;
+    }
+    Ev f1(st);
+    // ---- FP64 polishing
+    if (fp32) {
+        double *pa = alloc_n<double>(p, N), *pb = alloc_n<double>(p, N);
+        float *mc = alloc_n<float>(p, 1);
+        k_widen<<<grid_for(N), 256, 0, st>>>(N, p.u32, pa);
+        const CtlTable2<double> ct = make_table<double>(p);
+        double last = 0.0;
+        int it = 0;
+        for (; it < 8; ++it) {
+            check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
+            k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ct);
+            check_cuda(cudaGetLastError(), "polish");
+            std::swap(pa, pb);
+            float hm = 0.f;
+            check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(float), cudaMemcpyDeviceToHost, st), "polish res");
+            check_cuda(cudaStreamSynchronize(st), "polish sync");
+            last = hm;
+            if (hm < d.tol) {
+                ++it;
+                break;
+            }
+        }
+        S.sweeps_polish = it;
+        S.residual_polish = last;
+        k_finalize<<<grid_for(N), 256, 0, st>>>(N, pa, p.u_out);
+    }
+    unsigned long long *unreach = alloc_n<unsigned long long>(p, 1);
+    check_cuda(cudaMemsetAsync(unreach, 0, sizeof(unsigned long long), st), "memset");
+    k_final_labels<<<grid_for(N), 256, 0, st>>>(N, code0, code, p.label_out, unreach);
+    Ev f2(st);
+    unsigned long long hu = 0;
+    check_cuda(cudaMemcpyAsync(&hu, updates, sizeof(hu), cudaMemcpyDeviceToHost, st), "updates");
+    check_cuda(cudaStreamSynchronize(st), "final sync");
+    unsigned long long hun = 0;
+    check_cuda(cudaMemcpy(&hun, unreach, sizeof(hun), cudaMemcpyDeviceToHost), "unreachable");
+    S.unreachable = (int64_t)hun;
+    S.node_updates = (int64_t)hu;
+    S.node_control_updates = (int64_t)hu * d.n_controls;
+    S.n_patches = p.patchy ? R : 1;
+    S.ms_setup = ms_between(e0, e1);
+    S.ms_fine = ms_between(f0, f1);
+    S.ms_polish = ms_between(f1, f2);
+    S.ms_total = ms_between(e0, f2);
+    return status;
+}
+
+}  // namespace hjbp

@@ -1,0 +1,63 @@
+// plan.h -- host-side state of one solve (internal to libhjbp).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hjbp.h"
+
+struct hjbp_plan {
+    // --- descriptor (copied at create) ---
+    hjbp_problem_desc desc;
+    std::vector<double> controls;   // n_controls x dim
+    std::vector<double> targets;    // n_targets x (dim + 1)
+    bool patchy = false;
+    int64_t N = 0, Nc = 0;          // fine / coarse node counts
+    double k = 0.0, kc = 0.0;       // fine / coarse spacing
+
+    // --- execution ---
+    cudaStream_t stream = nullptr;
+    hjbp_allocator alloc{};
+    bool has_alloc = false;
+    bool solved = false;
+    hjbp_stats stats{};
+
+    // --- device arrays owned by the plan ---
+    struct Block {
+        void *ptr;
+        size_t bytes;
+    };
+    std::vector<Block> blocks;
+
+    double *u_out = nullptr;        // FP64 values (output)
+    int8_t *label_out = nullptr;    // labels (output)
+    double *u_coarse = nullptr;     // coarse values (Step 1)
+    double *u0 = nullptr;           // U_P^(0) (Step 2)
+    uint8_t *astar = nullptr;       // coarse feedback (Step 2)
+    double *phi = nullptr;          // R x N colour fields (Step 3.1)
+    float *u32 = nullptr;           // FP32 bulk values
+
+    void *dev_alloc(size_t bytes);  // throws std::bad_alloc on failure
+    void release_all();
+};
+
+namespace hjbp {
+
+struct HjbpError {
+    hjbp_status status;
+    std::string msg;
+};
+
+// Raise an HjbpError on a CUDA failure.
+void check_cuda(cudaError_t e, const char *what);
+
+void set_last_error(const std::string &msg);
+
+// 2D and 3D drivers: run the whole solve on the plan's stream.
+hjbp_status solve2d(hjbp_plan &p);
+hjbp_status solve3d(hjbp_plan &p);
+
+}  // namespace hjbp

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every entry point declared in
+include/hjbp.h (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "hjbp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hjbp_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    return ctypes.CDLL(b.LIB)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("hjbp_create", "hjbp_solve", "hjbp_get_values", "hjbp_get_labels", "hjbp_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_calls_need_no_gpu(lib):
+    import paper_1109_3577_gb300 as pkg
+
+    assert pkg.hjbp_version() >= 100
+    assert isinstance(pkg.hjbp_last_error(), str)
+
+
+def test_create_rejects_bad_descriptors(lib):
+    """Validation happens before any device work, so it runs on CPU."""
+    import numpy as np
+
+    import paper_1109_3577_gb300 as pkg
+    import workloads as W
+
+    p = W.sincos2d(0, n=65, n_coarse=17)
+    bad = [
+        p.with_(dim=4),
+        p.with_(n=(2, 65, 1)),
+        p.with_(controls=np.zeros((0, 2))),
+        p.with_(controls=p.controls * 2.0),
+        p.with_(targets=np.zeros((0, 3))),
+        p.with_(tol=0.0),
+        p.with_(hi=(2.0, 3.0, 0.0)),
+        p.with_(n_coarse=(129, 129, 1)),
+    ]
+    for q in bad:
+        d, keep = pkg.desc_from_problem(q)
+        with pytest.raises(pkg.HjbpError) as ei:
+            pkg.hjbp_create(d, 0, None)
+        assert ei.value.status == 1, q
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1109_3577_gb300 import _binding
+
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_binding, "_LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        _binding.library()
