@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the patchy semi-Lagrangian solver on one GB300.
+
+One step = one full patchy solve (setup, coarse solve, feedback, colour
+transport and labels, patch compaction, S*, FP32 value sweeps with the
+sup-norm reduction, FP64 polish, output) of the 2D workload: fine grid
+2049^2 on [-2,2]^2, coarse 65^2, c(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2),
+64 controls, four disks r = 0.05 at seeded centres (one patch each),
+tol 1e-6.  Inputs are resident on the device when a timed step starts; the
+L2 cache is flushed (512 MB write) between steps.
+
+value      executed fine-grid node-control updates per second (all ranks)
+e2e        the same metric through the public API with host buffers:
+           plan create (host -> device copy of the problem), solve, and the
+           device -> host copy of the values and labels, every step
+--impl reference   times the FP64 CPU oracle on the same metric (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "node-control updates/s and solves/s vs plain GPU SL at 1e-4 err; p50/p99 latency"
+UNIT = "node-control updates/s"
+WORKLOAD = "patchy2d_sincos_n2049_c65_nc64_R4"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+OPS_PER_UPDATE = 4          # canonical bilinear update: 3 FMA + 1 min per node-control pair
+
+
+def problem(seed: int):
+    return W.sincos2d(seed, n=2049, n_coarse=65, n_c=64, n_targets=4, radius=0.05, tol=1e-6)
+
+
+# ----------------------------------------------------------------- helpers --
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the sweep kernel from the committed ncu
+    summary (line 'traffic_bytes_per_launch: <int>'), or None."""
+    path = os.path.join(ROOT, "profiles", "k_value2d_f32_sincos2d.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, device: int = 0):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9 or f[0] != str(device):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(p, rows: int):
+    """Time one application of F (Eq. SLscheme) by the C oracle on a band of
+    ``rows`` grid rows of the workload; returns (node-control updates, s)."""
+    import oracle
+
+    kind, _, _ = oracle.setup(p)
+    x = oracle.grid_coords(p)
+    U = np.where(kind == oracle.GHOST, np.inf, np.linalg.norm(x, axis=1))
+    U[kind == oracle.TARGET] = 0.0
+    n = p.n[0]
+    r0 = n // 2 - rows // 2
+    band = np.zeros(kind.size, bool)
+    band[r0 * n:(r0 + rows) * n] = True
+    upd = band & (kind == oracle.FREE)
+    t = time.perf_counter()
+    oracle.sl_apply(p, U, upd=upd, mode=0)
+    dt = time.perf_counter() - t
+    return int(upd.sum()) * p.n_controls, dt
+
+
+# --------------------------------------------------------- reference arm --
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = problem(0)
+    rows = 48
+    for _ in range(args.warmup):
+        oracle_sample(p, rows)
+    tot_u, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        u, t = oracle_sample(p, rows)
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t
+    sample = (f"one application of F (Eq. SLscheme) by the single-threaded FP64 C oracle on a band of {rows} rows "
+              f"x 2049 nodes of the {WORKLOAD} workload, 64 controls, per step")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 2049, "n_coarse": 65, "n_controls": 64, "n_targets": 4,
+                   "tol": 1e-6, "seed": 0},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------- our arm --
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as P
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    p = problem(rank)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # CPU baseline first (rank 0 at N = 1 only), before the GPU work starts
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        tu, tt = 0, 0.0
+        while tt < 10.0:
+            u, t = oracle_sample(p, 48)
+            tu += u
+            tt += t
+        cpu = {"value": tu / tt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{tu // 64} node updates x 64 controls: applications of F (Eq. SLscheme) by the "
+                         f"single-threaded FP64 C oracle on 48-row bands of the same 2049^2 grid, {tt:.1f} s"}
+
+    plan = P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS)
+    for _ in range(args.warmup):
+        plan.solve()
+    torch.cuda.synchronize()
+
+    st = torch.cuda.current_stream()
+    ms_steps, stats = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks() as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            status = plan.solve()
+            e1.record(st)
+            e1.synchronize()
+            ms_steps.append(e0.elapsed_time(e1))
+            stats.append(plan.stats())
+            assert status == 0, f"solve status {status}"
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = float(sum(ms_steps))
+    ncu_local = sum(s["node_control_updates"] for s in stats)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        c = torch.tensor([float(ncu_local)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        ncu_all = float(c.item())
+    else:
+        ncu_all = float(ncu_local)
+    value = ncu_all / (total_ms / 1e3)
+    s0 = stats[-1]
+
+    # plain global GPU SL on the same input (comparison path)
+    g = p.with_(n_coarse=None)
+    gplan = P.Plan(g, precision=P.HJBP_FP32_POLISH64, stream=stream)
+    gplan.solve()
+    gms = []
+    for _ in range(2):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        gplan.solve()
+        e1.record(st)
+        e1.synchronize()
+        gms.append(e0.elapsed_time(e1))
+    gstats = gplan.stats()
+    gplan.close()
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    N = p.n_nodes
+    h2d = p.controls.nbytes + p.targets.nbytes + 512 + 64 * 8
+    d2h = N * 8 + N * 1
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream) as ep:
+            ep.solve()
+            u = ep.values()
+            lab = ep.labels()
+            ncu_e = ep.stats()["node_control_updates"]
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        assert np.isfinite(u).any() and lab.size == N
+    e2e_value = ncu_e / (statistics.mean(e2e_ms) / 1e3) * world
+
+    # roofline of the dominant kernel (fine-grid value sweep, FP32)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6            # lane-ops/s
+    launches = max(1, s0["sweep_kernel_launches"])
+    ops_per_launch = s0["node_control_updates"] * OPS_PER_UPDATE / launches
+    avg_launch_s = s0["ms_sweep_kernel"] / 1e3 / launches
+    achieved = ops_per_launch / avg_launch_s if avg_launch_s > 0 else None
+    traffic = profile_traffic()
+    roofline = {"bound": "alu", "kernel": "k_value2d<float>", "achieved": achieved / 1e12 if achieved else None,
+                "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
+                "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock); "
+                              f"{OPS_PER_UPDATE} lane-ops per node-control update"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": 2049, "n_coarse": 65, "n_controls": 64, "n_targets": 4,
+                       "tol": 1e-6, "seed": "rank", "precision": "FP32 sweeps, FP64 coarse/feedback/labels/polish",
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+            "solves_per_s": world * 1e3 * args.steps / total_ms,
+            "plain_sl_solves_per_s": 1e3 / statistics.mean(gms),
+            "plain_sl_ms": statistics.mean(gms),
+            "plain_sl_node_control_updates": gstats["node_control_updates"],
+            "node_control_updates_per_solve": s0["node_control_updates"],
+            "sweeps": {k: s0[k] for k in ("sweeps_coarse", "sweeps_phi", "sweeps_reach", "sweeps_fine",
+                                           "sweeps_polish", "sweeps_patch")},
+            "ms_phases": {k: round(s0[k], 3) for k in ("ms_setup", "ms_coarse", "ms_feedback", "ms_labels",
+                                                        "ms_compact", "ms_fine", "ms_polish", "ms_total")},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": statistics.mean(e2e_ms)},
+            "clocks": clk.summary(dev),
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        }
+        if cpu:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist_mod.init_process_group(backend=backend)
+        dist = dist_mod
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

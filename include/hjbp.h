@@ -92,7 +92,13 @@ typedef struct {
     double tol_phi;
     int precision;
     int max_sweeps;
+    int flags;          /* HJBP_FLAG_* bits */
 } hjbp_problem_desc;
+
+/* flags: HJBP_FLAG_TIME_SWEEPS records a CUDA event pair around every launch
+ * of the fine-grid value-sweep kernel (on the plan's stream) and reports their
+ * summed duration in hjbp_stats.ms_sweep_kernel.                              */
+#define HJBP_FLAG_TIME_SWEEPS 1
 
 /* Device allocator hooks (optional).  alloc returns device memory of at least
  * `bytes` usable on `stream`, or NULL; release returns it.  ctx is passed back
@@ -124,6 +130,10 @@ typedef struct {
     int64_t node_updates;                 /* node updates executed on the fine grid */
     int64_t node_control_updates;         /* node_updates x controls */
     double ms_setup, ms_coarse, ms_feedback, ms_labels, ms_compact, ms_fine, ms_polish, ms_total;
+    int64_t kernel_launches;              /* CUDA kernels launched by the solve */
+    int64_t sweep_kernel_launches;        /* launches of the fine-grid value-sweep kernel */
+    int64_t sweep_tile_visits;            /* active tiles summed over those launches */
+    double ms_sweep_kernel;               /* their summed duration (HJBP_FLAG_TIME_SWEEPS), else 0 */
 } hjbp_stats;
 
 /* Validate the descriptor, copy its arrays, allocate device memory.

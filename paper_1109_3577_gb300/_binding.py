@@ -45,6 +45,7 @@ class Desc(C.Structure):
         ("tol_phi", C.c_double),
         ("precision", C.c_int),
         ("max_sweeps", C.c_int),
+        ("flags", C.c_int),
     ]
 
 
@@ -81,6 +82,10 @@ class Stats(C.Structure):
         ("ms_fine", C.c_double),
         ("ms_polish", C.c_double),
         ("ms_total", C.c_double),
+        ("kernel_launches", C.c_int64),
+        ("sweep_kernel_launches", C.c_int64),
+        ("sweep_tile_visits", C.c_int64),
+        ("ms_sweep_kernel", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -228,7 +233,10 @@ def torch_allocator() -> Allocator:
     return a
 
 
-def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0):
+HJBP_FLAG_TIME_SWEEPS = 1
+
+
+def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0):
     """Build an hjbp_problem_desc from a workloads.Problem.  Returns the
     struct plus the arrays it points into (keep both alive)."""
     controls = np.ascontiguousarray(p.controls, dtype=np.float64)
@@ -252,6 +260,7 @@ def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 
     d.tol_phi = float(p.tol_phi)
     d.precision = int(precision)
     d.max_sweeps = int(max_sweeps or 0)
+    d.flags = int(flags)
     return d, (controls, targets)
 
 
@@ -260,9 +269,9 @@ class Plan:
     ``labels()`` / ``stats()``."""
 
     def __init__(self, problem, precision: int = HJBP_FP32_POLISH64, stream: Optional[int] = None,
-                 use_torch_allocator: bool = False, max_sweeps: int = 0):
+                 use_torch_allocator: bool = False, max_sweeps: int = 0, flags: int = 0):
         self.problem = problem
-        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps)
+        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps, flags)
         if stream is None:
             stream = 0
             try:

@@ -94,6 +94,7 @@ struct TileSched {
     uint64_t *tile_patch; // patch bitmask of each tile (for per-patch sweep counts)
     uint64_t *patch_hist; // per-launch mask of patches with an active tile
     float *res_hist;      // per-launch max change
+    int *count_hist;      // per-launch number of active tiles
 };
 
 __device__ __forceinline__ int tile_of(const Grid2 &g, int x, int y) {

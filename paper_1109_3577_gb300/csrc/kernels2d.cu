@@ -126,6 +126,7 @@ __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launc
     const int ntiles = g.ntx * g.nty;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
+    if (t == 0 && s.count_hist) s.count_hist[launch] = s.count[par];
     if (s.processed[t]) {
         s.latest[t] ^= 1;
         s.processed[t] = 0;
@@ -773,8 +774,6 @@ __global__ void k_iota(int n, int *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
 }
 
-__global__ void k_count_hist(TileSched s, int par, int launch, int *hist) { hist[launch] = s.count[par]; }
-
 Sched make_sched(hjbp_plan &p, const Grid2 &g, int hist) {
     Sched s;
     s.ntiles = g.ntx * g.nty;
@@ -791,8 +790,10 @@ Sched make_sched(hjbp_plan &p, const Grid2 &g, int hist) {
     s.d.patch_hist = alloc_n<uint64_t>(p, hist);
     s.d.res_hist = alloc_n<float>(p, hist);
     s.count_hist = alloc_n<int>(p, hist);
+    s.d.count_hist = s.count_hist;
     s.iota = alloc_n<int>(p, nt);
     k_iota<<<grid_for(nt), 256, 0, p.stream>>>(nt, s.iota);
+    ++p.stats.kernel_launches;
     return s;
 }
 
@@ -814,6 +815,7 @@ void reset_sched(hjbp_plan &p, Sched &s) {
 }
 
 struct RunResult {
+    int64_t tile_visits = 0; // active tiles summed over launches
     int launches = 0;        // launches that had work
     bool converged = false;
     float last_res = 0.f;
@@ -836,8 +838,8 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
     while (L < cap) {
         sweep(par, L);
         check_cuda(cudaGetLastError(), "sweep launch");
-        k_count_hist<<<1, 1, 0, p.stream>>>(s.d, par, L, s.count_hist);
         k_schedule2d<<<(s.ntiles + 255) / 256, 256, 0, p.stream>>>(g, s.d, par, tol, L);
+        ++p.stats.kernel_launches;
         check_cuda(cudaGetLastError(), "schedule launch");
         par ^= 1;
         ++L;
@@ -865,6 +867,7 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
         if (ch[l] > 0) {
             rr.launches = l + 1;
             rr.last_res = rh[l];
+            rr.tile_visits += ch[l];
         }
     return rr;
 }
@@ -985,11 +988,13 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         RunResult rr = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
             k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt);
+            ++p.stats.kernel_launches;
         });
         total += rr.launches;
         if (!rr.converged) throw HjbpError{HJBP_ECUDA, "reachability sweep did not settle"};
         check_cuda(cudaMemsetAsync(removed, 0, sizeof(unsigned long long), p.stream), "memset");
         k_reach_prune<<<grid_for(N), 256, 0, p.stream>>>(N, code, rch, removed);
+        ++p.stats.kernel_launches;
         unsigned long long h = 0;
         check_cuda(cudaMemcpyAsync(&h, removed, sizeof(h), cudaMemcpyDeviceToHost, p.stream), "removed");
         check_cuda(cudaStreamSynchronize(p.stream), "reach sync");
@@ -1001,14 +1006,47 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
 // Value iteration from M on S* (R14), monotone, to the sup-norm tolerance.
 template <typename T>
 RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, const double *fixed, T *b0, T *b1,
-                  Sched &s, double tol, int cap, int rounds, T *out_t, double *out64, unsigned long long *updates) {
+                  Sched &s, double tol, int cap, int rounds, T *out_t, double *out64, unsigned long long *updates,
+                  bool fine) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     k_init_values2d<T><<<grid_for(N), 256, 0, p.stream>>>(N, code, fixed, (T)kStartValue, b0, b1);
+    ++p.stats.kernel_launches;
     const CtlTable2<T> ct = make_table<T>(p);
+    const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
     RunResult rr = run_tiles(p, g, s, (float)tol, cap, [&](int par, int) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timed) {
+            check_cuda(cudaEventCreate(&a), "event");
+            check_cuda(cudaEventCreate(&b), "event");
+            check_cuda(cudaEventRecord(a, p.stream), "event");
+        }
         k_value2d<T, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        ++p.stats.kernel_launches;
+        if (fine) ++p.stats.sweep_kernel_launches;
+        if (timed) {
+            check_cuda(cudaEventRecord(b, p.stream), "event");
+            evs.emplace_back(a, b);
+        }
     });
+    if (fine) p.stats.sweep_tile_visits += rr.tile_visits;
+    if (timed) {
+        check_cuda(cudaStreamSynchronize(p.stream), "timing sync");
+        double ms = 0.0;
+        // launches after convergence found no active tile and did no work
+        for (size_t l = 0; l < evs.size(); ++l) {
+            float m = 0.f;
+            if ((int)l < rr.launches) {
+                cudaEventElapsedTime(&m, evs[l].first, evs[l].second);
+                ms += m;
+            }
+            cudaEventDestroy(evs[l].first);
+            cudaEventDestroy(evs[l].second);
+        }
+        p.stats.ms_sweep_kernel += ms;
+    }
     k_gather2d<T><<<grid_for(N), 256, 0, p.stream>>>(g, s.d.latest, b0, b1, out_t, out64);
+    ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "gather");
     return rr;
 }
@@ -1039,6 +1077,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     unsigned long long *updates = alloc_n<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
     k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr);
+    ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "setup");
     Sched sched = make_sched(p, g, hist);
     Ev e1(st);
@@ -1054,18 +1093,22 @@ hjbp_status solve2d(hjbp_plan &p) {
         double *cb0 = alloc_n<double>(p, Nc), *cb1 = alloc_n<double>(p, Nc);
         k_setup2d<<<grid_for(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(2.0) / 2.0, 1, ccode, nullptr, ch64,
                                                 cfix);
+                                                ++p.stats.kernel_launches;
         k_merge_targets<<<grid_for(Nc), 256, 0, st>>>(Nc, ccode);
+        ++p.stats.kernel_launches;
         Sched csched = make_sched(p, gc, hist);
         S.sweeps_reach += reach2d(p, gc, ccode, crch, csched, kReachCap, Nc);
         const double tolc = d.tol_coarse > 0 ? d.tol_coarse : 1e-12;
         RunResult rc = value2d<double>(p, gc, ccode, ch64, cfix, cb0, cb1, csched, tolc, cap, 2, nullptr, p.u_coarse,
-                                       nullptr);
+                                       nullptr, false);
         S.sweeps_coarse = rc.launches;
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev e2(st);
         // ---- Step 2: U_P^(0) and the coarse feedback a*
         k_u0_2d<<<grid_for(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0);
+        ++p.stats.kernel_launches;
         k_feedback2d<<<grid_for(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, make_literal(p));
+        ++p.stats.kernel_launches;
         check_cuda(cudaGetLastError(), "feedback");
         Ev e3(st);
         // ---- Step 3.1: colours phi^j, projection, Remark 3.1 fill
@@ -1088,20 +1131,25 @@ hjbp_status solve2d(hjbp_plan &p) {
             const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
             for (int j = 0; j < R; ++j) {
                 k_phi_init2d<<<grid_for(N), 256, 0, st>>>(N, code0, j, pb0, pb1);
+                ++p.stats.kernel_launches;
                 RunResult rp = run_tiles(p, g, sched, (float)tolp, cap, [&](int par, int) {
                     k_phi2d<<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, pb0, pb1, sched.d, par, 2, dpc);
+                    ++p.stats.kernel_launches;
                 });
                 S.sweeps_phi += rp.launches;
                 if (!rp.converged) status = HJBP_ENOCONV;
                 k_gather2d<double><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, pb0, pb1, p.phi + (int64_t)j * N,
                                                                 nullptr);
+                                                                ++p.stats.kernel_launches;
             }
             k_label2d<<<grid_for(N), 256, 0, st>>>(N, code0, p.astar, p.phi, R, p.label_out);
+            ++p.stats.kernel_launches;
             int8_t *lab2 = reinterpret_cast<int8_t *>(rch);  // scratch (reach flags are reset before use)
             unsigned long long *chg = alloc_n<unsigned long long>(p, 1);
             for (int it = 0; it < 100000; ++it) {
                 check_cuda(cudaMemsetAsync(chg, 0, sizeof(unsigned long long), st), "memset");
                 k_fill2d<<<grid_for(N), 256, 0, st>>>(g, p.label_out, lab2, chg);
+                ++p.stats.kernel_launches;
                 check_cuda(cudaMemcpyAsync(p.label_out, lab2, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
                 unsigned long long hc = 0;
                 check_cuda(cudaMemcpyAsync(&hc, chg, sizeof(hc), cudaMemcpyDeviceToHost, st), "fill count");
@@ -1110,6 +1158,7 @@ hjbp_status solve2d(hjbp_plan &p) {
                 if (!hc) break;
             }
             k_patch_codes<<<grid_for(N), 256, 0, st>>>(N, code0, p.label_out, code);
+            ++p.stats.kernel_launches;
         }
         Ev e4(st);
         // ---- patch compaction
@@ -1120,6 +1169,7 @@ hjbp_status solve2d(hjbp_plan &p) {
             check_cuda(cudaMemsetAsync(pn, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
             check_cuda(cudaMemsetAsync(pt, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
             if (sched.ntiles) k_compact2d<<<sched.ntiles, 32, 0, st>>>(g, code, tile_patch, pn, pt);
+            ++p.stats.kernel_launches;
             sched.d.tile_patch = tile_patch;
             unsigned long long hn[kMaxTargets], ht[kMaxTargets];
             check_cuda(cudaMemcpyAsync(hn, pn, sizeof(hn), cudaMemcpyDeviceToHost, st), "compact");
@@ -1138,6 +1188,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     } else {
         check_cuda(cudaMemcpyAsync(code, code0, (size_t)N, cudaMemcpyDeviceToDevice, st), "code copy");
         k_merge_targets<<<grid_for(N), 256, 0, st>>>(N, code);
+        ++p.stats.kernel_launches;
     }
 
     // ---- Step 3.2 (or the global solve): S*, then the value iteration
@@ -1146,10 +1197,10 @@ hjbp_status solve2d(hjbp_plan &p) {
     RunResult rv;
     if (fp32) {
         float *b0 = alloc_n<float>(p, N), *b1 = alloc_n<float>(p, N);
-        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, 2, p.u32, nullptr, updates);
+        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, 2, p.u32, nullptr, updates, true);
     } else {
         double *b0 = alloc_n<double>(p, N), *b1 = alloc_n<double>(p, N);
-        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, 2, nullptr, p.u_out, updates);
+        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, 2, nullptr, p.u_out, updates, true);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
@@ -1170,12 +1221,14 @@ hjbp_status solve2d(hjbp_plan &p) {
         double *pa = alloc_n<double>(p, N), *pb = alloc_n<double>(p, N);
         float *mc = alloc_n<float>(p, 1);
         k_widen<<<grid_for(N), 256, 0, st>>>(N, p.u32, pa);
+        ++p.stats.kernel_launches;
         const CtlTable2<double> ct = make_table<double>(p);
         double last = 0.0;
         int it = 0;
         for (; it < 8; ++it) {
             check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
             k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ct);
+            ++p.stats.kernel_launches;
             check_cuda(cudaGetLastError(), "polish");
             std::swap(pa, pb);
             float hm = 0.f;
@@ -1190,10 +1243,12 @@ hjbp_status solve2d(hjbp_plan &p) {
         S.sweeps_polish = it;
         S.residual_polish = last;
         k_finalize<<<grid_for(N), 256, 0, st>>>(N, pa, p.u_out);
+        ++p.stats.kernel_launches;
     }
     unsigned long long *unreach = alloc_n<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(unreach, 0, sizeof(unsigned long long), st), "memset");
     k_final_labels<<<grid_for(N), 256, 0, st>>>(N, code0, code, p.label_out, unreach);
+    ++p.stats.kernel_launches;
     Ev f2(st);
     unsigned long long hu = 0;
     check_cuda(cudaMemcpyAsync(&hu, updates, sizeof(hu), cudaMemcpyDeviceToHost, st), "updates");
