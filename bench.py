@@ -37,6 +37,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "node-control updates/s and solves/s vs plain GPU SL at 1e-4 err; p50/p99 latency"
 UNIT = "node-control updates/s"
+N_FINE, N_COARSE = 2049, 65
 WORKLOAD = "patchy2d_sincos_n2049_c65_nc64_R4"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -44,7 +45,7 @@ OPS_PER_UPDATE = 4          # canonical bilinear update: 3 FMA + 1 min per node-
 
 
 def problem(seed: int):
-    return W.sincos2d(seed, n=2049, n_coarse=65, n_c=64, n_targets=4, radius=0.05, tol=1e-6)
+    return W.sincos2d(seed, n=N_FINE, n_coarse=N_COARSE, n_c=64, n_targets=4, radius=0.05, tol=1e-6)
 
 
 # ----------------------------------------------------------------- helpers --
@@ -160,12 +161,12 @@ def run_reference(args, rank, world):
         tot_t += t
     v = tot_u / tot_t
     sample = (f"one application of F (Eq. SLscheme) by the single-threaded FP64 C oracle on a band of {rows} rows "
-              f"x 2049 nodes of the {WORKLOAD} workload, 64 controls, per step")
+              f"x {N_FINE} nodes of the {WORKLOAD} workload, 64 controls, per step")
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 2049, "n_coarse": 65, "n_controls": 64, "n_targets": 4,
+        "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": 64, "n_targets": 4,
                    "tol": 1e-6, "seed": 0},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -199,7 +200,7 @@ def run_ours(args, rank, world, dist):
             tt += t
         cpu = {"value": tu / tt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{tu // 64} node updates x 64 controls: applications of F (Eq. SLscheme) by the "
-                         f"single-threaded FP64 C oracle on 48-row bands of the same 2049^2 grid, {tt:.1f} s"}
+                         f"single-threaded FP64 C oracle on 48-row bands of the same {N_FINE}^2 grid, {tt:.1f} s"}
 
     plan = P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS)
     for _ in range(args.warmup):
@@ -296,7 +297,7 @@ def run_ours(args, rank, world, dist):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": 2049, "n_coarse": 65, "n_controls": 64, "n_targets": 4,
+            "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": 64, "n_targets": 4,
                        "tol": 1e-6, "seed": "rank", "precision": "FP32 sweeps, FP64 coarse/feedback/labels/polish",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solves_per_s": world * 1e3 * args.steps / total_ms,
@@ -326,7 +327,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--n", type=int, default=2049, help="fine nodes per side (smaller cases for profiling)")
+    ap.add_argument("--nc", type=int, default=65, help="coarse nodes per side")
     args = ap.parse_args()
+    global N_FINE, N_COARSE, WORKLOAD
+    N_FINE, N_COARSE = args.n, args.nc
+    WORKLOAD = f"patchy2d_sincos_n{N_FINE}_c{N_COARSE}_nc64_R4"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
