@@ -177,6 +177,27 @@ void hjbp_destroy(hjbp_plan *plan);
 
 const char *hjbp_last_error(void);
 
+/* Plain global 2D solve in FP64 that allocates nothing (the paper has no
+ * counterpart; it serves callers that cannot allocate at solve time, e.g.
+ * code running while a stream is captured into a CUDA graph, or real-time
+ * loops that forbid allocation after start-up).
+ *   desc        a 2D problem with n_coarse[0] == 0 (plain global solve) and at
+ *               most HJBP_NOALLOC_MAX_NODES nodes; precision is ignored (FP64)
+ *   cuda_stream the stream to run on (NULL = legacy default stream)
+ *   u_out       device array of N doubles: the values (+INFINITY unreachable)
+ *   labels_out  device array of N int8: 0 / target part / -1, as hjbp_get_labels
+ * Results equal hjbp_solve's for the same descriptor with HJBP_FP64.  Scratch
+ * comes from one fixed device array inside the library (32 MiB, held by every
+ * GPU that loads the library until the process exits); no cudaMalloc,
+ * cudaFree or other allocator is called.  The first call on each device looks
+ * up that array's device address, so make it before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Synchronises the stream before returning.
+ * Errors: EINVAL (descriptor, too large, NULL outputs), ECUDA, ENOCONV.      */
+#define HJBP_NOALLOC_MAX_NODES (1 << 20)
+hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc, void *cuda_stream, double *u_out,
+                                        int8_t *labels_out);
+
 /* Library version as major*10000 + minor*100 + patch.                        */
 int hjbp_version(void);
 

@@ -28,6 +28,8 @@ from ._binding import (  # noqa: F401
     hjbp_get_values,
     hjbp_last_error,
     hjbp_solve,
+    hjbp_solve_global2d_noalloc,
+    HJBP_NOALLOC_MAX_NODES,
     hjbp_version,
     library,
     library_path,

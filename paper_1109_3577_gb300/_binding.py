@@ -133,6 +133,8 @@ def library():
         lib.hjbp_destroy.restype = None
         lib.hjbp_last_error.argtypes = []
         lib.hjbp_last_error.restype = C.c_char_p
+        lib.hjbp_solve_global2d_noalloc.argtypes = [P(Desc), vp, vp, vp]
+        lib.hjbp_solve_global2d_noalloc.restype = C.c_int
         lib.hjbp_version.argtypes = []
         lib.hjbp_version.restype = C.c_int
         _lib = lib
@@ -202,6 +204,20 @@ def hjbp_get_sizes(plan: int):
     n, nc = C.c_int64(), C.c_int64()
     _check(library().hjbp_get_sizes(C.c_void_p(plan), C.byref(n), C.byref(nc)))
     return n.value, nc.value
+
+
+HJBP_NOALLOC_MAX_NODES = 1 << 20
+
+
+def hjbp_solve_global2d_noalloc(desc: Desc, stream: int, u_out_ptr: int, labels_out_ptr: int) -> int:
+    """Global 2D FP64 solve into caller-owned device arrays, allocating
+    nothing (scratch is a fixed array inside the library; calls must not
+    overlap on the GPU).  Returns OK or ENOCONV; raises on other errors."""
+    st = library().hjbp_solve_global2d_noalloc(C.byref(desc), C.c_void_p(stream), C.c_void_p(u_out_ptr),
+                                               C.c_void_p(labels_out_ptr))
+    if st not in (HJBP_OK, HJBP_ENOCONV):
+        _check(st)
+    return st
 
 
 def hjbp_destroy(plan: int) -> None:

@@ -14,8 +14,16 @@
 namespace hjbp {
 
 static thread_local std::string g_last_error;
+static thread_local const char *g_last_static = nullptr;
 
-void set_last_error(const std::string &msg) { g_last_error = msg; }
+void set_last_error(const std::string &msg) {
+    g_last_error = msg;
+    g_last_static = nullptr;
+}
+
+// Records a message with static storage without copying it (used by the
+// entry point that must not allocate).
+void set_last_error_static(const char *msg) { g_last_static = msg; }
 
 void check_cuda(cudaError_t e, const char *what) {
     if (e != cudaSuccess) {
@@ -112,7 +120,9 @@ extern "C" {
 
 int hjbp_version(void) { return 100; }
 
-const char *hjbp_last_error(void) { return hjbp::g_last_error.c_str(); }
+const char *hjbp_last_error(void) {
+    return hjbp::g_last_static ? hjbp::g_last_static : hjbp::g_last_error.c_str();
+}
 
 hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const hjbp_allocator *allocator,
                         hjbp_plan **out) {

@@ -77,6 +77,18 @@ struct ReachTable2 {
     uint8_t present[4];
 };
 
+// Speed field c(x) (hjbp_speed_kind) and its parameters, passed by value.
+struct SpeedParams {
+    int kind;
+    double p[64];
+};
+
+// Target balls: centres (c0, c1, c2) and radii, passed by value.
+struct TargetSet {
+    int n;
+    double c0[kMaxTargets], c1[kMaxTargets], c2[kMaxTargets], r[kMaxTargets];
+};
+
 // Geometry of a 2D grid and its tiling of the interior nodes 1..n-2.
 struct Grid2 {
     int n0, n1;        // nodes per side

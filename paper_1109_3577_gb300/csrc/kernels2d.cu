@@ -29,16 +29,6 @@
 
 namespace hjbp {
 
-struct SpeedParams {
-    int kind;
-    double p[64];
-};
-
-struct TargetSet {
-    int n;
-    double c0[kMaxTargets], c1[kMaxTargets], c2[kMaxTargets], r[kMaxTargets];
-};
-
 // c(x) of f(x, a) = c(x) a (fixed menu, see hjbp_speed_kind).
 __device__ double speed_at(const SpeedParams &sp, double x0, double x1, double x2) {
     const double pi = 3.14159265358979323846;
@@ -740,6 +730,23 @@ template __global__ void k_value2d<double, true>(Grid2, const int8_t *, const do
 template __global__ void k_gather2d<float>(Grid2, const uint8_t *, const float *, const float *, float *, double *);
 template __global__ void k_gather2d<double>(Grid2, const uint8_t *, const double *, const double *, double *,
                                             double *);
+
+// Host launchers of the FP64 template kernels for other translation units
+// (the no-allocation entry point launches the same kernels as hjbp_solve).
+void launch_init_values2d_f64(int blocks, cudaStream_t st, int64_t N, const int8_t *code, double start, double *b0,
+                              double *b1) {
+    k_init_values2d<double><<<blocks, 256, 0, st>>>(N, code, nullptr, start, b0, b1);
+}
+
+void launch_value2d_f64(int ntiles, cudaStream_t st, Grid2 g, const int8_t *code, const double *h, double *b0,
+                        double *b1, TileSched s, int par, int rounds, const CtlTable2<double> &ct) {
+    k_value2d<double, true><<<ntiles, 32, 0, st>>>(g, code, h, b0, b1, s, par, rounds, nullptr, ct);
+}
+
+void launch_gather2d_f64(int blocks, cudaStream_t st, Grid2 g, const uint8_t *latest, const double *b0,
+                         const double *b1, double *out64) {
+    k_gather2d<double><<<blocks, 256, 0, st>>>(g, latest, b0, b1, nullptr, out64);
+}
 
 }  // namespace hjbp
 
