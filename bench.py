@@ -62,7 +62,7 @@ def measured_peaks():
 def profile_traffic():
     """DRAM bytes per launch of the sweep kernel from the committed ncu
     summary (line 'traffic_bytes_per_launch: <int>'), or None."""
-    path = os.path.join(ROOT, "profiles", "k_value2d_f32_sincos2d.md")
+    path = os.path.join(ROOT, "profiles", "k_value2d_f32_traffic.md")
     try:
         txt = open(path).read()
     except OSError:
