@@ -306,7 +306,7 @@ def run_ours(args, rank, world, dist):
             "plain_sl_node_control_updates": gstats["node_control_updates"],
             "node_control_updates_per_solve": s0["node_control_updates"],
             "sweeps": {k: s0[k] for k in ("sweeps_coarse", "sweeps_phi", "sweeps_reach", "sweeps_fine",
-                                           "sweeps_polish", "sweeps_patch")},
+                                           "sweeps_polish", "sweeps_patch", "phi_refinements")},
             "ms_phases": {k: round(s0[k], 3) for k in ("ms_setup", "ms_coarse", "ms_feedback", "ms_labels",
                                                         "ms_compact", "ms_fine", "ms_polish", "ms_total")},
             "roofline": roofline,

@@ -134,6 +134,7 @@ typedef struct {
     int64_t sweep_kernel_launches;        /* launches of the fine-grid value-sweep kernel */
     int64_t sweep_tile_visits;            /* active tiles summed over those launches */
     double ms_sweep_kernel;               /* their summed duration (HJBP_FLAG_TIME_SWEEPS), else 0 */
+    int phi_refinements;                  /* FP64 residual evaluations of the colour transport */
 } hjbp_stats;
 
 /* Validate the descriptor, copy its arrays, allocate device memory.

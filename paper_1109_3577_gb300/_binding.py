@@ -86,6 +86,7 @@ class Stats(C.Structure):
         ("sweep_kernel_launches", C.c_int64),
         ("sweep_tile_visits", C.c_int64),
         ("ms_sweep_kernel", C.c_double),
+        ("phi_refinements", C.c_int),
     ]
 
     def as_dict(self) -> dict:

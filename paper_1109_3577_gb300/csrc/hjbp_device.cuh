@@ -57,6 +57,31 @@ template <typename T> struct CtlTable2 {
     T kw01[kMaxControls];
     T kw11[kMaxControls];
     T kap[kMaxControls];
+    // Symmetric form, used when the control set is invariant under the eight
+    // symmetries of the square (d4 = 1).  Controls a and a' = (|a_y|, |a_x|)
+    // in the same quadrant share kap and w11 and swap w10 <-> w01, so
+    //   min(v_a, v_a') = kap h + kw11 u11 + s (u10 + u01) - t |u10 - u01|
+    // with s = (kw10 + kw01)/2, t = |kw10 - kw01|/2 (t = 0 on the diagonal).
+    // Each class stands for one such pair in every quadrant; the four axis
+    // directions (kap = 1, one corner) are handled apart (axis = 1).
+    int d4;
+    int axis;
+    int ncls;
+    T cls_kap[kMaxControls / 4];
+    T cls_s[kMaxControls / 4];
+    T cls_t[kMaxControls / 4];
+    T cls_kw11[kMaxControls / 4];
+};
+
+// Per-control self-solved weights in any order (one control per lane).
+template <typename T> struct CtlSelf2 {
+    int nc;
+    int8_t sx[kMaxControls];
+    int8_t sy[kMaxControls];
+    T kw10[kMaxControls];
+    T kw01[kMaxControls];
+    T kw11[kMaxControls];
+    T kap[kMaxControls];
 };
 
 // Literal Q1 weights in the caller's control order, for Eq. (feedbackcontrol).

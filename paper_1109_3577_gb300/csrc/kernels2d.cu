@@ -24,6 +24,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -214,8 +215,10 @@ __device__ __forceinline__ float store_tile(const Grid2 &g, const TileSched &s, 
 
 // Self-solved SL update (R13) of node (c, r) of the tile for patch code cd:
 //   min over controls of kap (w10 u10 + w01 u01 + w11 u11 + h_i);
-// neighbours outside patch cd and its target part read +inf.  Returns +inf
-// sentinel when no control has all its positive-weight corners finite.
+// neighbours outside patch cd and its target part read +inf.  Returns the
+// +inf sentinel when no control has all its positive-weight corners finite.
+// Four independent minimum accumulators keep the FMA chains of different
+// controls in flight together.
 template <typename T>
 __device__ __forceinline__ T sl_update(const TileSmem<T> &sm, int c, int r, int8_t cd, T hh,
                                        const CtlTable2<T> &ct) {
@@ -228,20 +231,61 @@ __device__ __forceinline__ T sl_update(const TileSmem<T> &sm, int c, int r, int8
             const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
             nb[dy][dx] = (q == cd || q == tg) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
         }
-    T best = Num<T>::big();
+    T b0 = Num<T>::big(), b1 = Num<T>::big(), b2 = Num<T>::big(), b3 = Num<T>::big();
+    if (ct.d4) {
+        T E[4], G[4], A[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
-        const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
-        for (int m = ct.qbeg[q]; m < ct.qbeg[q + 1]; ++m) {
-            T v = ct.kap[m] * hh;
-            v = fma(ct.kw10[m], a10, v);
-            v = fma(ct.kw01[m], a01, v);
-            v = fma(ct.kw11[m], a11, v);
-            best = v < best ? v : best;
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const T a10 = nb[1][sx], a01 = nb[sy][1];
+            E[q] = a10 + a01;
+            G[q] = fabs(a10 - a01);
+            A[q] = nb[sy][sx];
+        }
+        for (int k = 0; k < ct.ncls; ++k) {
+            const T kh = ct.cls_kap[k] * hh;
+            const T s = ct.cls_s[k], t = -ct.cls_t[k], w = ct.cls_kw11[k];
+            T v0 = fma(t, G[0], fma(s, E[0], fma(w, A[0], kh)));
+            T v1 = fma(t, G[1], fma(s, E[1], fma(w, A[1], kh)));
+            T v2 = fma(t, G[2], fma(s, E[2], fma(w, A[2], kh)));
+            T v3 = fma(t, G[3], fma(s, E[3], fma(w, A[3], kh)));
+            b0 = v0 < b0 ? v0 : b0;
+            b1 = v1 < b1 ? v1 : b1;
+            b2 = v2 < b2 ? v2 : b2;
+            b3 = v3 < b3 ? v3 : b3;
+        }
+        if (ct.axis) {
+            const T ax = fmin(fmin(nb[1][0], nb[1][2]), fmin(nb[0][1], nb[2][1])) + hh;
+            b0 = ax < b0 ? ax : b0;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
+            int m = ct.qbeg[q];
+            const int me = ct.qbeg[q + 1];
+            for (; m + 3 < me; m += 4) {
+                const T v0 = fma(ct.kw11[m], a11, fma(ct.kw01[m], a01, fma(ct.kw10[m], a10, ct.kap[m] * hh)));
+                const T v1 =
+                    fma(ct.kw11[m + 1], a11, fma(ct.kw01[m + 1], a01, fma(ct.kw10[m + 1], a10, ct.kap[m + 1] * hh)));
+                const T v2 =
+                    fma(ct.kw11[m + 2], a11, fma(ct.kw01[m + 2], a01, fma(ct.kw10[m + 2], a10, ct.kap[m + 2] * hh)));
+                const T v3 =
+                    fma(ct.kw11[m + 3], a11, fma(ct.kw01[m + 3], a01, fma(ct.kw10[m + 3], a10, ct.kap[m + 3] * hh)));
+                b0 = v0 < b0 ? v0 : b0;
+                b1 = v1 < b1 ? v1 : b1;
+                b2 = v2 < b2 ? v2 : b2;
+                b3 = v3 < b3 ? v3 : b3;
+            }
+            for (; m < me; ++m) {
+                const T v = fma(ct.kw11[m], a11, fma(ct.kw01[m], a01, fma(ct.kw10[m], a10, ct.kap[m] * hh)));
+                b0 = v < b0 ? v : b0;
+            }
         }
     }
-    return best;
+    const T b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
+    return b01 < b23 ? b01 : b23;
 }
 
 // One launch of the value iteration over the active tiles.  kClamp: monotone
@@ -291,6 +335,65 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         s.processed[t] = 1;
         if (updates) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
     }
+}
+
+// ----------------------------------------- small grids: one warp per node --
+
+// One Jacobi launch of the value iteration for grids too small to fill the
+// GPU with 32x32 tiles (the coarse grid of Step 1): one warp per free node,
+// lanes take the controls m = lane, lane + 32, ..., and a warp-shuffle
+// minimum combines them.  Reads uin, writes uout (monotone clamp from M),
+// max |change| of the launch into res[launch].
+template <typename T>
+__global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T *__restrict__ h,
+                               const T *__restrict__ uin, T *__restrict__ uout, float *__restrict__ res, int launch,
+                               const CtlSelf2<T> ct) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    float mc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
+        const int8_t cd = code[i];
+        const T old = uin[i];
+        T nw = old;
+        if (cd >= 0 && cd < kTargetBase) {
+            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            const int8_t tg = (int8_t)(cd + kTargetBase);
+            T nb[3][3];
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int64_t j = (int64_t)(iy - 1 + dy) * g.n0 + (ix - 1 + dx);
+                    const int8_t q = code[j];
+                    nb[dy][dx] = (q == cd || q == tg) ? uin[j] : Num<T>::big();
+                }
+            const T hh = h[i];
+            T best = Num<T>::big();
+            for (int m = lane; m < ct.nc; m += 32) {
+                const int sx = ct.sx[m] > 0 ? 2 : 0, sy = ct.sy[m] > 0 ? 2 : 0;
+                const T a10 = sx ? nb[1][2] : nb[1][0];
+                const T a01 = sy ? nb[2][1] : nb[0][1];
+                const T a11 = sy ? (sx ? nb[2][2] : nb[2][0]) : (sx ? nb[0][2] : nb[0][0]);
+                const T v = fma(ct.kw11[m], a11, fma(ct.kw01[m], a01, fma(ct.kw10[m], a10, ct.kap[m] * hh)));
+                best = v < best ? v : best;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = other < best ? other : best;
+            }
+            if (best < Num<T>::thresh()) nw = best < old ? best : old;
+        }
+        if (lane == 0) {
+            uout[i] = nw;
+            const bool vi = nw >= Num<T>::thresh(), oi = old >= Num<T>::thresh();
+            const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)nw - (double)old));
+            mc = fmaxf(mc, d);
+        }
+    }
+    mc = warp_max(mc);
+    if (lane == 0 && mc > 0.f) atomic_max_pos(&res[launch], mc);
 }
 
 // -------------------------------------------- almost-sure reachability (S*) --
@@ -474,35 +577,91 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
 
 // --------------------------------------------------- Step 3.1: colours phi --
 
+// Controls in the caller's order for the colour transport: literal Q1
+// weights (FP64 residual) and the self-solved weights kw = kap w in FP32.
 struct PhiCtl {
     int8_t sx[kMaxControls], sy[kMaxControls];
-    double kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls];
+    double w00[kMaxControls], w10[kMaxControls], w01[kMaxControls], w11[kMaxControls];
+    float kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls], kap[kMaxControls];
 };
 
-// phi values of a colour at set-up: 1 on target part j, 0 elsewhere.
-__global__ void k_phi_init2d(int64_t N, const int8_t *__restrict__ code, int j, double *__restrict__ b0,
-                             double *__restrict__ b1) {
+// Colour transport of Step 3.1 in mixed precision.  Eq. (HJBridotta_discreta)
+// is linear, so FP64 accuracy comes from iterative refinement: an FP32 tile
+// solve gives phi, its residual is formed in FP64, the correction equation
+// (same transport operator, the residual as source) is solved in FP32, and the
+// correction is added in FP64; two or three rounds reach the FP64 tolerance
+// while the many sweeps all run in FP32.
+
+// phi planes at set-up for colours j0 .. j0+RG-1 (colour-major, N each):
+// 1 on target part j, 0 elsewhere (with zero_all: 0 everywhere).
+template <int RG>
+__global__ void k_phi_init2d(int64_t N, const int8_t *__restrict__ code, int j0, int zero_all,
+                             float *__restrict__ b0, float *__restrict__ b1) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = code[i] == (int8_t)(kTargetBase + j) ? 1.0 : 0.0;
-        b0[i] = v;
-        b1[i] = v;
+        const int8_t c = code[i];
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float v = (!zero_all && c == (int8_t)(kTargetBase + j0 + q)) ? 1.0f : 0.0f;
+            b0[(int64_t)q * N + i] = v;
+            b1[(int64_t)q * N + i] = v;
+        }
     }
 }
 
-// One launch of Eq. (HJBridotta_discreta) over the active tiles, solved for
-// phi_i at each node (R13): phi_i = kap (w10 phi10 + w01 phi01 + w11 phi11)
-// with the node's fixed coarse feedback a*_i.  phi rises monotonically from 0.
+template <int RG> struct PhiSmem {
+    float u[RG][kTile + 2][kTile + 3];
+    float src[RG][kTile][kTile + 1];
+    int8_t c[kTile + 2][kTile + 4];
+    uint8_t a[kTile][kTile + 4];
+};
+
+// One FP32 launch over the active tiles for RG colours, each node solved for
+// itself (R13) with its fixed coarse feedback a*_i:
+//   bulk (kSource = false):       phi_i <- max(phi_i, kap (w10 phi10 + w01 phi01 + w11 phi11))
+//   correction (kSource = true):  d_i   <- kap (w10 d10 + w01 d01 + w11 d11 + r_i)
+// The bulk rises monotonically from 0; the tile's change is the max over
+// its colours.
+template <int RG, bool kSource>
 __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
-                                              const uint8_t *__restrict__ astar, double *__restrict__ b0,
-                                              double *__restrict__ b1, TileSched s, int par, int rounds,
-                                              const PhiCtl *__restrict__ pc) {
+                                              const uint8_t *__restrict__ astar, float *__restrict__ b0,
+                                              float *__restrict__ b1, const float *__restrict__ src, TileSched s,
+                                              int par, int rounds, const PhiCtl *__restrict__ pc) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
-    __shared__ TileSmem<double> sm;
-    load_tile(g, s, code, b0, b1, x0, y0, sm);
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    __shared__ PhiSmem<RG> sm;
     const int lane = threadIdx.x;
+    for (int r = 0; r < kTile + 2; ++r) {
+        const int y = y0 - 1 + r;
+        for (int c = lane; c < kTile + 2; c += 32) {
+            const int x = x0 - 1 + c;
+            const bool in = x < g.n0 && y < g.n1;
+            const bool inner = r >= 1 && r <= kTile && c >= 1 && c <= kTile;
+            const int64_t i = (int64_t)y * g.n0 + x;
+            int8_t cd = kHard;
+            if (in) {
+                cd = code[i];
+                const int tt = tile_of(g, x, y);
+                const float *bsrc = (tt >= 0 && s.latest[tt]) ? b1 : b0;
+#pragma unroll
+                for (int q = 0; q < RG; ++q) sm.u[q][r][c] = bsrc[(int64_t)q * N + i];
+            } else {
+#pragma unroll
+                for (int q = 0; q < RG; ++q) sm.u[q][r][c] = 0.0f;
+            }
+            if (inner) {
+                sm.a[r - 1][c - 1] = in ? astar[i] : kNoControl;
+                if (kSource) {
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) sm.src[q][r - 1][c - 1] = in ? src[(int64_t)q * N + i] : 0.0f;
+                }
+            }
+            sm.c[r][c] = cd;
+        }
+    }
+    __syncwarp();
     for (int rd = 0; rd < rounds; ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
             for (int st = 0; st < kTile; ++st) {
@@ -510,30 +669,112 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
                 const int c = (dir < 2) ? s1 : 1 + lane;
                 const int r = (dir < 2) ? 1 + lane : s1;
                 const int8_t cd = sm.c[r][c];
-                double nw = sm.u[r][c];
-                bool active = false;
-                if (cd >= 0 && cd < kTargetBase) {
-                    const int64_t i = (int64_t)(y0 - 1 + r) * g.n0 + (x0 - 1 + c);
-                    const uint8_t a = astar[i];
-                    if (a != kNoControl) {
-                        active = true;
-                        const int sx = pc->sx[a], sy = pc->sy[a];
-                        const double v = pc->kw10[a] * sm.u[r][c + sx] + pc->kw01[a] * sm.u[r + sy][c] +
-                                         pc->kw11[a] * sm.u[r + sy][c + sx];
-                        nw = v > nw ? v : nw;
+                const uint8_t a = sm.a[r - 1][c - 1];
+                const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
+                float nw[RG];
+                if (active) {
+                    const int sx = pc->sx[a], sy = pc->sy[a];
+                    const float w10 = pc->kw10[a], w01 = pc->kw01[a], w11 = pc->kw11[a];
+                    const float kp = pc->kap[a];
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) {
+                        float v = w10 * sm.u[q][r][c + sx];
+                        v = fmaf(w01, sm.u[q][r + sy][c], v);
+                        v = fmaf(w11, sm.u[q][r + sy][c + sx], v);
+                        if (kSource) {
+                            nw[q] = fmaf(kp, sm.src[q][r - 1][c - 1], v);
+                        } else {
+                            const float o = sm.u[q][r][c];
+                            nw[q] = v > o ? v : o;
+                        }
                     }
                 }
                 __syncwarp();
-                if (active) sm.u[r][c] = nw;
+                if (active) {
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) sm.u[q][r][c] = nw[q];
+                }
                 __syncwarp();
             }
         }
     }
-    const float mc = store_tile(g, s, t, b0, b1, x0, y0, sm);
+    const int cur = s.latest[t];
+    float *dst = cur ? b0 : b1;
+    const float *old = cur ? b1 : b0;
+    float mc = 0.f;
+    const int x = x0 + lane;
+    for (int r = 1; r <= kTile; ++r) {
+        const int y = y0 - 1 + r;
+        if (y > g.n1 - 2) break;
+        if (x > g.n0 - 2) continue;
+        const int64_t i = (int64_t)y * g.n0 + x;
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float v = sm.u[q][r][1 + lane];
+            const float o = old[(int64_t)q * N + i];
+            dst[(int64_t)q * N + i] = v;
+            mc = fmaxf(mc, fabsf(v - o));
+        }
+    }
+    mc = warp_max(mc);
     if (lane == 0) {
         s.chg[par][t] = mc;
         s.processed[t] = 1;
     }
+}
+
+// Current FP32 planes (per-tile parity) -> FP64 planes: out = in (add = 0) or
+// out += in (add = 1).
+template <int RG>
+__global__ void k_phi_collect2d(Grid2 g, const uint8_t *__restrict__ latest, const float *__restrict__ b0,
+                                const float *__restrict__ b1, double *__restrict__ out, int add) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.n0), y = (int)(i / g.n0);
+        const int tt = tile_of(g, x, y);
+        const float *src = (tt >= 0 && latest[tt]) ? b1 : b0;
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const double v = (double)src[(int64_t)q * N + i];
+            if (add) out[(int64_t)q * N + i] += v;
+            else out[(int64_t)q * N + i] = v;
+        }
+    }
+}
+
+// FP64 residual of Eq. (HJBridotta_discreta) with the literal Q1 weights:
+//   r_i = w00 phi_i + w10 phi10 + w01 phi01 + w11 phi11 - phi_i
+// at free nodes with a defined feedback (0 elsewhere), stored in FP32 as the
+// source of the correction solve; max |r| into *rmax.
+template <int RG>
+__global__ void k_phi_residual2d(Grid2 g, const int8_t *__restrict__ code, const uint8_t *__restrict__ astar,
+                                 const double *__restrict__ phi, float *__restrict__ r32, float *rmax,
+                                 const PhiCtl *__restrict__ pc) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    float mc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        const uint8_t a = astar[i];
+        const bool active = c >= 0 && c < kTargetBase && a != kNoControl;
+        if (!active) {
+#pragma unroll
+            for (int q = 0; q < RG; ++q) r32[(int64_t)q * N + i] = 0.0f;
+            continue;
+        }
+        const int64_t dx = pc->sx[a], dy = (int64_t)pc->sy[a] * g.n0;
+        const double w00 = pc->w00[a], w10 = pc->w10[a], w01 = pc->w01[a], w11 = pc->w11[a];
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const double *f = phi + (int64_t)q * N;
+            const double p0 = f[i];
+            const double v = w00 * p0 + w10 * f[i + dx] + w01 * f[i + dy] + w11 * f[i + dx + dy];
+            const double r = v - p0;
+            r32[(int64_t)q * N + i] = (float)r;
+            mc = fmaxf(mc, (float)fabs(r));
+        }
+    }
+    mc = warp_max(mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(rmax, mc);
 }
 
 // label = argmax_j phi^j if positive (lowest j on ties, R12); targets keep
@@ -638,9 +879,17 @@ __global__ void __launch_bounds__(32) k_compact2d(Grid2 g, const int8_t *__restr
 
 // u_out = F(u_in) in FP64 at every free node (self-solved form, no clamp),
 // one Jacobi application; max |change| into *maxchg.
+//
+// FP32 filter: every control is first evaluated in FP32.  With inputs,
+// weights and four operations rounded to FP32, |v32 - v64| <= 8 u (kap h +
+// max |a|), u = 2^-24, and kap h + max|a| <= 2 (h + max|a|) here; so a
+// control whose FP32 value exceeds the FP32 minimum by more than
+// margin = 2^-18 (h + max|a|) cannot attain the FP64 minimum.  Only the
+// remaining candidates are evaluated in FP64: the result is the FP64 minimum
+// over all controls at close to FP32 cost.
 __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const double *__restrict__ h,
                            const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
-                           const CtlTable2<double> ct) {
+                           const CtlTable2<float> c32, const CtlTable2<double> c64) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     float mc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -650,28 +899,52 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
             const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
             const int8_t tg = (int8_t)(cd + kTargetBase);
             double nb[3][3];
+            float nf[3][3];
+            float amax = 0.f;
+#pragma unroll
             for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
                 for (int dx = 0; dx < 3; ++dx) {
                     const int64_t j = (int64_t)(iy - 1 + dy) * g.n0 + (ix - 1 + dx);
                     const int8_t q = code[j];
                     const double w = uin[j];
-                    nb[dy][dx] = (q == cd || q == tg) ? (w >= Num<double>::thresh() ? Num<double>::big() : w)
-                                                      : Num<double>::big();
+                    const bool fin = (q == cd || q == tg) && w < Num<double>::thresh();
+                    nb[dy][dx] = fin ? w : Num<double>::big();
+                    nf[dy][dx] = fin ? (float)w : Num<float>::big();
+                    if (fin) amax = fmaxf(amax, fabsf((float)w));
                 }
-            double best = Num<double>::big();
+            const double hh = h[i];
+            const float hf = (float)hh;
+            // pass 1: FP32 minimum
+            float b32 = Num<float>::big();
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
-                const double a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
-                for (int m = ct.qbeg[q]; m < ct.qbeg[q + 1]; ++m) {
-                    double w = ct.kap[m] * h[i];
-                    w = fma(ct.kw10[m], a10, w);
-                    w = fma(ct.kw01[m], a01, w);
-                    w = fma(ct.kw11[m], a11, w);
-                    best = w < best ? w : best;
+                const float a10 = nf[1][sx], a01 = nf[sy][1], a11 = nf[sy][sx];
+                for (int m = c32.qbeg[q]; m < c32.qbeg[q + 1]; ++m) {
+                    const float w = fmaf(c32.kw11[m], a11, fmaf(c32.kw01[m], a01, fmaf(c32.kw10[m], a10, c32.kap[m] * hf)));
+                    b32 = w < b32 ? w : b32;
                 }
             }
-            if (best < Num<double>::thresh() && v < Num<double>::thresh()) {
+            if (b32 < Num<float>::thresh() && v < Num<double>::thresh()) {
+                const float lim = b32 + ldexpf(hf + amax, -18);
+                // pass 2: FP64 over the candidates
+                double best = Num<double>::big();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+                    const float a10 = nf[1][sx], a01 = nf[sy][1], a11 = nf[sy][sx];
+                    const double d10 = nb[1][sx], d01 = nb[sy][1], d11 = nb[sy][sx];
+                    for (int m = c32.qbeg[q]; m < c32.qbeg[q + 1]; ++m) {
+                        const float w =
+                            fmaf(c32.kw11[m], a11, fmaf(c32.kw01[m], a01, fmaf(c32.kw10[m], a10, c32.kap[m] * hf)));
+                        if (w <= lim) {
+                            const double x =
+                                fma(c64.kw11[m], d11, fma(c64.kw01[m], d01, fma(c64.kw10[m], d10, c64.kap[m] * hh)));
+                            best = x < best ? x : best;
+                        }
+                    }
+                }
                 mc = fmaxf(mc, (float)fabs(best - v));
                 v = best;
             }
@@ -727,6 +1000,8 @@ template __global__ void k_value2d<float, true>(Grid2, const int8_t *, const flo
                                                 int, unsigned long long *, const CtlTable2<float>);
 template __global__ void k_value2d<double, true>(Grid2, const int8_t *, const double *, double *, double *, TileSched,
                                                  int, int, unsigned long long *, const CtlTable2<double>);
+template __global__ void k_value_wide2d<double>(Grid2, const int8_t *, const double *, const double *, double *,
+                                                float *, int, const CtlSelf2<double>);
 template __global__ void k_gather2d<float>(Grid2, const uint8_t *, const float *, const float *, float *, double *);
 template __global__ void k_gather2d<double>(Grid2, const uint8_t *, const double *, const double *, double *,
                                             double *);
@@ -879,6 +1154,48 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
     return rr;
 }
 
+// Fill the symmetric form of the table when the control set is invariant
+// under the eight symmetries of the square (see CtlTable2).
+template <typename T> void build_d4(const hjbp_plan &p, CtlTable2<T> &ct) {
+    ct.d4 = 0;
+    const int nc = p.desc.n_controls;
+    const double tol = 1e-12;
+    auto has = [&](double x, double y) {
+        for (int m = 0; m < nc; ++m)
+            if (std::fabs(p.controls[2 * m] - x) < tol && std::fabs(p.controls[2 * m + 1] - y) < tol) return true;
+        return false;
+    };
+    for (int m = 0; m < nc; ++m) {
+        const double x = p.controls[2 * m], y = p.controls[2 * m + 1];
+        const double img[8][2] = {{x, y}, {-x, y}, {x, -y}, {-x, -y}, {y, x}, {-y, x}, {y, -x}, {-y, -x}};
+        for (auto &v : img)
+            if (!has(v[0], v[1])) return;
+    }
+    int axis = 0, ncls = 0, count = 0;
+    for (int m = 0; m < nc; ++m) {
+        const double x = p.controls[2 * m], y = p.controls[2 * m + 1];
+        if (x > 0.0 && y == 0.0) {
+            axis = 1;
+            count += 4;
+        } else if (x > 0.0 && y > 0.0 && x >= y - tol) {
+            if (ncls >= kMaxControls / 4) return;
+            const double w00 = (1.0 - x) * (1.0 - y), w10 = x * (1.0 - y), w01 = (1.0 - x) * y, w11 = x * y;
+            const double kap = 1.0 / (1.0 - w00);
+            const bool diag = std::fabs(x - y) < tol;
+            ct.cls_kap[ncls] = (T)kap;
+            ct.cls_kw11[ncls] = (T)(kap * w11);
+            ct.cls_s[ncls] = (T)(kap * (w10 + w01) / 2.0);
+            ct.cls_t[ncls] = diag ? (T)0 : (T)(kap * std::fabs(w10 - w01) / 2.0);
+            ++ncls;
+            count += diag ? 4 : 8;
+        }
+    }
+    if (count != nc) return;
+    ct.d4 = 1;
+    ct.axis = axis;
+    ct.ncls = ncls;
+}
+
 template <typename T> CtlTable2<T> make_table(const hjbp_plan &p) {
     CtlTable2<T> ct;
     std::memset(&ct, 0, sizeof(ct));
@@ -904,7 +1221,26 @@ template <typename T> CtlTable2<T> make_table(const hjbp_plan &p) {
         }
     }
     ct.qbeg[4] = pos;
+    build_d4(p, ct);
     return ct;
+}
+
+template <typename T> CtlSelf2<T> make_self(const hjbp_plan &p) {
+    CtlSelf2<T> cs;
+    std::memset(&cs, 0, sizeof(cs));
+    cs.nc = p.desc.n_controls;
+    for (int m = 0; m < cs.nc; ++m) {
+        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double bx = std::fabs(ax), by = std::fabs(ay);
+        const double kap = 1.0 / (1.0 - (1.0 - bx) * (1.0 - by));
+        cs.sx[m] = ax >= 0.0 ? 1 : -1;
+        cs.sy[m] = ay >= 0.0 ? 1 : -1;
+        cs.kw10[m] = (T)(kap * bx * (1.0 - by));
+        cs.kw01[m] = (T)(kap * (1.0 - bx) * by);
+        cs.kw11[m] = (T)(kap * bx * by);
+        cs.kap[m] = (T)kap;
+    }
+    return cs;
 }
 
 CtlLiteral2 make_literal(const hjbp_plan &p) {
@@ -1058,6 +1394,51 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     return rr;
 }
 
+// Jacobi value iteration of a small grid with one warp per node (FP64).
+RunResult value_wide2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const double *h, const double *fixed,
+                       double *b0, double *b1, double tol, int cap, double *out64) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    cudaStream_t st = p.stream;
+    k_init_values2d<double><<<grid_for(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1);
+    ++p.stats.kernel_launches;
+    const CtlSelf2<double> cs = make_self<double>(p);
+    const int chunk = 16;
+    float *res = alloc_n<float>(p, chunk);
+    std::vector<float> hres(chunk);
+    RunResult rr;
+    const int blocks = (int)std::min<int64_t>((N + 7) / 8, 152 * 16);
+    int L = 0;
+    while (L < cap) {
+        check_cuda(cudaMemsetAsync(res, 0, sizeof(float) * chunk, st), "memset");
+        int n = std::min(chunk, cap - L);
+        for (int l = 0; l < n; ++l) {
+            const double *in = ((L + l) & 1) ? b1 : b0;
+            double *out = ((L + l) & 1) ? b0 : b1;
+            k_value_wide2d<double><<<blocks, 256, 0, st>>>(g, code, h, in, out, res, l, cs);
+            ++p.stats.kernel_launches;
+        }
+        check_cuda(cudaGetLastError(), "wide launch");
+        check_cuda(cudaMemcpyAsync(hres.data(), res, sizeof(float) * chunk, cudaMemcpyDeviceToHost, st), "res");
+        check_cuda(cudaStreamSynchronize(st), "wide sync");
+        for (int l = 0; l < n; ++l) {
+            rr.launches = L + l + 1;
+            rr.last_res = hres[l];
+            if (hres[l] <= tol) {
+                rr.converged = true;
+                break;
+            }
+        }
+        L += n;
+        if (rr.converged) break;
+    }
+    // the launch that met the test wrote into the buffer of its parity
+    const double *fin = (rr.launches & 1) ? b1 : b0;
+    k_finalize<<<grid_for(N), 256, 0, st>>>(N, fin, out64);
+    ++p.stats.kernel_launches;
+    check_cuda(cudaGetLastError(), "wide finalize");
+    return rr;
+}
+
 }  // namespace
 
 hjbp_status solve2d(hjbp_plan &p) {
@@ -1106,8 +1487,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         Sched csched = make_sched(p, gc, hist);
         S.sweeps_reach += reach2d(p, gc, ccode, crch, csched, kReachCap, Nc);
         const double tolc = d.tol_coarse > 0 ? d.tol_coarse : 1e-12;
-        RunResult rc = value2d<double>(p, gc, ccode, ch64, cfix, cb0, cb1, csched, tolc, cap, 2, nullptr, p.u_coarse,
-                                       nullptr, false);
+        RunResult rc = value_wide2d(p, gc, ccode, ch64, cfix, cb0, cb1, tolc, cap, p.u_coarse);
         S.sweeps_coarse = rc.launches;
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev e2(st);
@@ -1125,29 +1505,72 @@ hjbp_status solve2d(hjbp_plan &p) {
             for (int m = 0; m < d.n_controls; ++m) {
                 const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
                 const double bx = std::fabs(ax), by = std::fabs(ay);
-                const double kap = 1.0 / (1.0 - (1.0 - bx) * (1.0 - by));
+                const double w00 = (1.0 - bx) * (1.0 - by), w10 = bx * (1.0 - by), w01 = (1.0 - bx) * by;
+                const double w11 = bx * by, kap = 1.0 / (1.0 - w00);
                 hpc.sx[m] = ax >= 0 ? 1 : -1;
                 hpc.sy[m] = ay >= 0 ? 1 : -1;
-                hpc.kw10[m] = kap * bx * (1.0 - by);
-                hpc.kw01[m] = kap * (1.0 - bx) * by;
-                hpc.kw11[m] = kap * bx * by;
+                hpc.w00[m] = w00;
+                hpc.w10[m] = w10;
+                hpc.w01[m] = w01;
+                hpc.w11[m] = w11;
+                hpc.kw10[m] = (float)(kap * w10);
+                hpc.kw01[m] = (float)(kap * w01);
+                hpc.kw11[m] = (float)(kap * w11);
+                hpc.kap[m] = (float)kap;
             }
             PhiCtl *dpc = static_cast<PhiCtl *>(p.dev_alloc(sizeof(PhiCtl)));
             check_cuda(cudaMemcpyAsync(dpc, &hpc, sizeof(PhiCtl), cudaMemcpyHostToDevice, st), "phi ctl");
-            double *pb0 = alloc_n<double>(p, N), *pb1 = alloc_n<double>(p, N);
+            const int RG = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+            float *f0 = alloc_n<float>(p, N * RG), *f1 = alloc_n<float>(p, N * RG), *r32 = alloc_n<float>(p, N * RG);
+            double *phig = alloc_n<double>(p, N * RG);
+            float *rmax = alloc_n<float>(p, 1);
             const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
-            for (int j = 0; j < R; ++j) {
-                k_phi_init2d<<<grid_for(N), 256, 0, st>>>(N, code0, j, pb0, pb1);
-                ++p.stats.kernel_launches;
-                RunResult rp = run_tiles(p, g, sched, (float)tolp, cap, [&](int par, int) {
-                    k_phi2d<<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, pb0, pb1, sched.d, par, 2, dpc);
+            for (int j0 = 0; j0 < R; j0 += RG) {
+                const int rg = std::min(RG, R - j0);
+                // colours past R in the last group see no target and stay 0
+                const int rgl = rg >= 4 ? 4 : (rg == 3 ? 4 : rg);
+                auto launch_group = [&](auto tag) {
+                    constexpr int G = decltype(tag)::value;
+                    // FP32 bulk solve
+                    k_phi_init2d<G><<<grid_for(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++p.stats.kernel_launches;
-                });
-                S.sweeps_phi += rp.launches;
-                if (!rp.converged) status = HJBP_ENOCONV;
-                k_gather2d<double><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, pb0, pb1, p.phi + (int64_t)j * N,
-                                                                nullptr);
-                                                                ++p.stats.kernel_launches;
+                    RunResult rp = run_tiles(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par, int) {
+                        k_phi2d<G, false><<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d,
+                                                                       par, 2, dpc);
+                        ++p.stats.kernel_launches;
+                    });
+                    S.sweeps_phi += rp.launches;
+                    if (!rp.converged) status = HJBP_ENOCONV;
+                    k_phi_collect2d<G><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, f0, f1, phig, 0);
+                    ++p.stats.kernel_launches;
+                    // FP64 refinement: residual in FP64, correction solved in FP32
+                    for (int it = 0; it < 6; ++it) {
+                        check_cuda(cudaMemsetAsync(rmax, 0, sizeof(float), st), "memset");
+                        k_phi_residual2d<G><<<grid_for(N), 256, 0, st>>>(g, code0, p.astar, phig, r32, rmax, dpc);
+                        ++p.stats.kernel_launches;
+                        float hr = 0.f;
+                        check_cuda(cudaMemcpyAsync(&hr, rmax, sizeof(float), cudaMemcpyDeviceToHost, st), "rmax");
+                        check_cuda(cudaStreamSynchronize(st), "rmax sync");
+                        S.phi_refinements++;
+                        if (hr <= tolp) break;
+                        k_phi_init2d<G><<<grid_for(N), 256, 0, st>>>(N, code0, j0, 1, f0, f1);
+                        ++p.stats.kernel_launches;
+                        const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
+                        RunResult rc = run_tiles(p, g, sched, told, cap, [&](int par, int) {
+                            k_phi2d<G, true><<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, f0, f1, r32, sched.d,
+                                                                          par, 2, dpc);
+                            ++p.stats.kernel_launches;
+                        });
+                        S.sweeps_phi += rc.launches;
+                        k_phi_collect2d<G><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, f0, f1, phig, 1);
+                        ++p.stats.kernel_launches;
+                    }
+                    check_cuda(cudaMemcpyAsync(p.phi + (int64_t)j0 * N, phig, sizeof(double) * N * rg,
+                                               cudaMemcpyDeviceToDevice, st), "phi copy");
+                };
+                if (rgl == 4) launch_group(std::integral_constant<int, 4>());
+                else if (rgl == 2) launch_group(std::integral_constant<int, 2>());
+                else launch_group(std::integral_constant<int, 1>());
             }
             k_label2d<<<grid_for(N), 256, 0, st>>>(N, code0, p.astar, p.phi, R, p.label_out);
             ++p.stats.kernel_launches;
@@ -1230,11 +1653,13 @@ hjbp_status solve2d(hjbp_plan &p) {
         k_widen<<<grid_for(N), 256, 0, st>>>(N, p.u32, pa);
         ++p.stats.kernel_launches;
         const CtlTable2<double> ct = make_table<double>(p);
+        CtlTable2<float> ctf = make_table<float>(p);
+        ctf.d4 = 0;
         double last = 0.0;
         int it = 0;
         for (; it < 8; ++it) {
             check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
-            k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ct);
+            k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ctf, ct);
             ++p.stats.kernel_launches;
             check_cuda(cudaGetLastError(), "polish");
             std::swap(pa, pb);
