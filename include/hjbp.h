@@ -93,6 +93,9 @@ typedef struct {
     int precision;
     int max_sweeps;
     int flags;          /* HJBP_FLAG_* bits */
+    int tune[4];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
+                           launch of the value sweep (2), [1] of the colour transport (3),
+                           [2] passes per launch of the reachability sweep (1), [3] reserved */
 } hjbp_problem_desc;
 
 /* flags: HJBP_FLAG_TIME_SWEEPS records a CUDA event pair around every launch
@@ -135,6 +138,7 @@ typedef struct {
     int64_t sweep_tile_visits;            /* active tiles summed over those launches */
     double ms_sweep_kernel;               /* their summed duration (HJBP_FLAG_TIME_SWEEPS), else 0 */
     int phi_refinements;                  /* FP64 residual evaluations of the colour transport */
+    double ms_reach;                      /* S* computation on the fine grid (inside ms_fine) */
 } hjbp_stats;
 
 /* Validate the descriptor, copy its arrays, allocate device memory.

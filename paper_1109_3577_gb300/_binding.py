@@ -46,6 +46,7 @@ class Desc(C.Structure):
         ("precision", C.c_int),
         ("max_sweeps", C.c_int),
         ("flags", C.c_int),
+        ("tune", C.c_int * 4),
     ]
 
 
@@ -87,6 +88,7 @@ class Stats(C.Structure):
         ("sweep_tile_visits", C.c_int64),
         ("ms_sweep_kernel", C.c_double),
         ("phi_refinements", C.c_int),
+        ("ms_reach", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -253,7 +255,7 @@ def torch_allocator() -> Allocator:
 HJBP_FLAG_TIME_SWEEPS = 1
 
 
-def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0):
+def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0, tune=None):
     """Build an hjbp_problem_desc from a workloads.Problem.  Returns the
     struct plus the arrays it points into (keep both alive)."""
     controls = np.ascontiguousarray(p.controls, dtype=np.float64)
@@ -278,6 +280,8 @@ def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 
     d.precision = int(precision)
     d.max_sweeps = int(max_sweeps or 0)
     d.flags = int(flags)
+    for i, v in enumerate(tune or ()):
+        d.tune[i] = int(v)
     return d, (controls, targets)
 
 
@@ -286,9 +290,9 @@ class Plan:
     ``labels()`` / ``stats()``."""
 
     def __init__(self, problem, precision: int = HJBP_FP32_POLISH64, stream: Optional[int] = None,
-                 use_torch_allocator: bool = False, max_sweeps: int = 0, flags: int = 0):
+                 use_torch_allocator: bool = False, max_sweeps: int = 0, flags: int = 0, tune=None):
         self.problem = problem
-        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps, flags)
+        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps, flags, tune)
         if stream is None:
             stream = 0
             try:

@@ -404,7 +404,7 @@ __global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T
 // own target part (R14).  In place; monotone, so the order does not matter.
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restrict__ code,
                                                 uint8_t *__restrict__ rch, TileSched s, int par,
-                                                ReachTable2 rt) {
+                                                ReachTable2 rt, int passes) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     }
     __syncwarp();
     int flips = 0;
-    for (int pass = 0; pass < 2; ++pass)
+    for (int pass = 0; pass < passes; ++pass)
         for (int dir = 0; dir < 4; ++dir) {
             for (int st = 0; st < kTile; ++st) {
                 const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
@@ -1324,13 +1324,14 @@ float ms_between(const Ev &a, const Ev &b) {
 
 // S* on the current codes (R14): reach from the targets, prune, repeat.
 int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, int cap, int64_t N) {
+    const int passes = p.desc.tune[2] > 0 ? p.desc.tune[2] : 1;
     const ReachTable2 rt = make_reach(p);
     unsigned long long *removed = alloc_n<unsigned long long>(p, 1);
     int total = 0;
     for (int round = 0; round < 64; ++round) {
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         RunResult rr = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
-            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt);
+            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt, passes);
             ++p.stats.kernel_launches;
         });
         total += rr.launches;
@@ -1452,6 +1453,8 @@ hjbp_status solve2d(hjbp_plan &p) {
     const int hist = std::max(std::min(cap, 1 << 20), kReachCap);
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
     const int R = d.n_targets;
+    const int vrounds = d.tune[0] > 0 ? d.tune[0] : 2;
+    const int prounds = d.tune[1] > 0 ? d.tune[1] : 3;
     hjbp_stats &S = p.stats;
     std::memset(&S, 0, sizeof(S));
     hjbp_status status = HJBP_OK;
@@ -1536,7 +1539,7 @@ hjbp_status solve2d(hjbp_plan &p) {
                     ++p.stats.kernel_launches;
                     RunResult rp = run_tiles(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par, int) {
                         k_phi2d<G, false><<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d,
-                                                                       par, 2, dpc);
+                                                                       par, prounds, dpc);
                         ++p.stats.kernel_launches;
                     });
                     S.sweeps_phi += rp.launches;
@@ -1558,7 +1561,7 @@ hjbp_status solve2d(hjbp_plan &p) {
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         RunResult rc = run_tiles(p, g, sched, told, cap, [&](int par, int) {
                             k_phi2d<G, true><<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, f0, f1, r32, sched.d,
-                                                                          par, 2, dpc);
+                                                                          par, prounds, dpc);
                             ++p.stats.kernel_launches;
                         });
                         S.sweeps_phi += rc.launches;
@@ -1624,13 +1627,14 @@ hjbp_status solve2d(hjbp_plan &p) {
     // ---- Step 3.2 (or the global solve): S*, then the value iteration
     Ev f0(st);
     S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N);
+    Ev fr(st);
     RunResult rv;
     if (fp32) {
         float *b0 = alloc_n<float>(p, N), *b1 = alloc_n<float>(p, N);
-        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, 2, p.u32, nullptr, updates, true);
+        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, true);
     } else {
         double *b0 = alloc_n<double>(p, N), *b1 = alloc_n<double>(p, N);
-        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, 2, nullptr, p.u_out, updates, true);
+        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates, true);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
@@ -1693,6 +1697,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     S.n_patches = p.patchy ? R : 1;
     S.ms_setup = ms_between(e0, e1);
     S.ms_fine = ms_between(f0, f1);
+    S.ms_reach = ms_between(f0, fr);
     S.ms_polish = ms_between(f1, f2);
     S.ms_total = ms_between(e0, f2);
     return status;

@@ -33,7 +33,7 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
                           float *h32, double *h64, double *fixed);
 __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
-                                                ReachTable2 rt);
+                                                ReachTable2 rt, int passes);
 __global__ void k_reach_prune(int64_t N, int8_t *code, const uint8_t *rch, unsigned long long *removed);
 __global__ void k_merge_targets(int64_t N, int8_t *code);
 __global__ void k_final_labels(int64_t N, const int8_t *code0, const int8_t *code, int8_t *label,
@@ -296,7 +296,7 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     for (int round = 0; round < 64; ++round) {
         NA_CHECK(cudaMemsetAsync(rch, 0, (size_t)N, st));
         hjbp_status rs = run(st, g, s, ntiles, iota, 0.5f, 1 << 18, &conv, [&](int par) {
-            k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt);
+            k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt, 2);
         });
         if (rs != HJBP_OK) return rs;
         if (!conv) return fail_static(HJBP_ECUDA, "reachability sweep did not settle");
