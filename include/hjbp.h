@@ -156,8 +156,11 @@ hjbp_status hjbp_solve(hjbp_plan *plan);
  * cannot be reached) into host_out.                                          */
 hjbp_status hjbp_get_values(hjbp_plan *plan, double *host_out);
 
-/* Copy the N patch labels: j on patch j and on target part j, -1 on the ghost
- * ring and on unreachable nodes (global solve: 0 / part index / -1).         */
+/* Copy the N labels.  Patchy solve: j on patch j (Step 3.1; a node of patch j
+ * that cannot reach its target inside the patch keeps label j and has value
+ * +INFINITY) and on target part j, -1 on the ghost ring and where U_P^(0) is
+ * unreachable.  Global solve: 0 on nodes that reach the target, the part index
+ * on target nodes, -1 elsewhere.                                              */
 hjbp_status hjbp_get_labels(hjbp_plan *plan, int8_t *host_out);
 
 /* Intermediate arrays of the patchy algorithm (for verification):

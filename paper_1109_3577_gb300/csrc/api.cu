@@ -287,9 +287,3 @@ void hjbp_destroy(hjbp_plan *p) {
 }
 
 }  // extern "C"
-
-namespace hjbp {
-hjbp_status solve3d(hjbp_plan &) {
-    throw HjbpError{HJBP_EINVAL, "3D solves are not built yet"};
-}
-}  // namespace hjbp

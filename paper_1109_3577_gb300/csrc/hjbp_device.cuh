@@ -114,6 +114,31 @@ struct TargetSet {
     double c0[kMaxTargets], c1[kMaxTargets], c2[kMaxTargets], r[kMaxTargets];
 };
 
+// c(x) of f(x, a) = c(x) a (fixed menu, see hjbp_speed_kind).
+__device__ inline double speed_at(const SpeedParams &sp, double x0, double x1, double x2) {
+    const double pi = 3.14159265358979323846;
+    switch (sp.kind) {
+    case HJBP_C_ONE:
+        return 1.0;
+    case HJBP_C_SINCOS2D:
+        return 1.0 + sp.p[0] * sin(2.0 * pi * x0) * cos(2.0 * pi * x1);
+    case HJBP_C_SIN3D:
+        return 1.0 + sp.p[0] * sin(pi * x0) * sin(pi * x1) * sin(pi * x2);
+    case HJBP_C_FOURIER2D: {
+        double g = 0.0, norm = 0.0;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                const int m = 4 * a + b;
+                g += sp.p[m] * cos(pi * a * x0 / 2.0 + sp.p[16 + m]) * cos(pi * b * x1 / 2.0 + sp.p[32 + m]);
+                norm += fabs(sp.p[m]);
+            }
+        return 1.0 + 0.5 * g / norm;
+    }
+    default:
+        return nan("");
+    }
+}
+
 // Geometry of a 2D grid and its tiling of the interior nodes 1..n-2.
 struct Grid2 {
     int n0, n1;        // nodes per side

@@ -30,31 +30,6 @@
 
 namespace hjbp {
 
-// c(x) of f(x, a) = c(x) a (fixed menu, see hjbp_speed_kind).
-__device__ double speed_at(const SpeedParams &sp, double x0, double x1, double x2) {
-    const double pi = 3.14159265358979323846;
-    switch (sp.kind) {
-    case HJBP_C_ONE:
-        return 1.0;
-    case HJBP_C_SINCOS2D:
-        return 1.0 + sp.p[0] * sin(2.0 * pi * x0) * cos(2.0 * pi * x1);
-    case HJBP_C_SIN3D:
-        return 1.0 + sp.p[0] * sin(pi * x0) * sin(pi * x1) * sin(pi * x2);
-    case HJBP_C_FOURIER2D: {
-        double g = 0.0, norm = 0.0;
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 4; ++b) {
-                const int m = 4 * a + b;
-                g += sp.p[m] * cos(pi * a * x0 / 2.0 + sp.p[16 + m]) * cos(pi * b * x1 / 2.0 + sp.p[32 + m]);
-                norm += fabs(sp.p[m]);
-            }
-        return 1.0 + 0.5 * g / norm;
-    }
-    default:
-        return nan("");
-    }
-}
-
 // ------------------------------------------------------------------ set-up --
 
 // Node codes, h_i = k / c(x_i) (|h f| = k, Sec. 2.1) and the fixed values of
@@ -962,15 +937,16 @@ __global__ void k_merge_targets(int64_t N, int8_t *__restrict__ code) {
         if (code[i] >= kTargetBase) code[i] = kTargetBase;
 }
 
-// Output labels: j on patch j (0 for the global solve) and on target part j,
-// -1 on the ghost ring and on free nodes outside S*; counts the latter.
+// Output labels of the global solve: 0 on S*, the part on target nodes, -1
+// on the ghost ring and on free nodes outside S* (label may be null: the
+// patchy solve keeps its Step 3.1 labels); counts free nodes outside S*.
 __global__ void k_final_labels(int64_t N, const int8_t *__restrict__ code0, const int8_t *__restrict__ code,
                                int8_t *__restrict__ label, unsigned long long *unreachable) {
     unsigned long long cnt = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
         const int8_t c0 = code0[i];
-        label[i] = c0 >= kTargetBase ? (int8_t)(c0 - kTargetBase) : (c >= 0 && c < kTargetBase ? c : (int8_t)-1);
+        if (label) label[i] = c0 >= kTargetBase ? (int8_t)(c0 - kTargetBase) : (c >= 0 && c < kTargetBase ? c : (int8_t)-1);
         if (c0 >= 0 && c0 < kTargetBase && c < 0) ++cnt;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -1683,7 +1659,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     }
     unsigned long long *unreach = alloc_n<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(unreach, 0, sizeof(unsigned long long), st), "memset");
-    k_final_labels<<<grid_for(N), 256, 0, st>>>(N, code0, code, p.label_out, unreach);
+    k_final_labels<<<grid_for(N), 256, 0, st>>>(N, code0, code, p.patchy ? nullptr : p.label_out, unreach);
     ++p.stats.kernel_launches;
     Ev f2(st);
     unsigned long long hu = 0;

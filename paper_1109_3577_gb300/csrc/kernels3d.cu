@@ -1,0 +1,1416 @@
+// kernels3d.cu -- CUDA kernels and host driver of the 3D path (sm_103a).
+//
+// Same method and structure as the 2D path (kernels2d.cu) with trilinear
+// interpolation: the foot x_i + k a of every control lies in the 3x3x3
+// neighbourhood (|h f| = k, Sec. 2.1).  Interior nodes are cut into 8x8x8
+// tiles, one CTA of 64 threads per tile; a tile loads itself plus a one-node
+// halo into shared memory and runs line Gauss-Seidel passes in the six axis
+// directions (in each step the 64 threads update one 8x8 plane), then writes
+// back.  Across tiles the iteration is block-Jacobi (two value buffers and a
+// per-tile parity bit), and only tiles whose 3x3x3 tile neighbourhood changed
+// by more than the tolerance run again.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "hjbp_device.cuh"
+#include "plan.h"
+
+namespace hjbp {
+
+// Dimension-free kernels defined in kernels2d.cu.
+__global__ void k_reach_prune(int64_t N, int8_t *code, const uint8_t *rch, unsigned long long *removed);
+__global__ void k_label2d(int64_t N, const int8_t *code, const uint8_t *astar, const double *phi, int R,
+                          int8_t *label);
+__global__ void k_patch_codes(int64_t N, const int8_t *code0, int8_t *label, int8_t *code);
+__global__ void k_merge_targets(int64_t N, int8_t *code);
+__global__ void k_final_labels(int64_t N, const int8_t *code0, const int8_t *code, int8_t *label,
+                               unsigned long long *unreachable);
+__global__ void k_widen(int64_t N, const float *in, double *out);
+__global__ void k_finalize(int64_t N, const double *in, double *out);
+
+constexpr int kT3 = 8;          // tile side
+constexpr int kT3n = kT3 * kT3; // threads per tile CTA (one 8x8 plane per step)
+
+struct Grid3 {
+    int n0, n1, n2;
+    int ntx, nty, ntz;
+    double lo0, lo1, lo2, k;
+};
+
+__device__ __forceinline__ int tile_of3(const Grid3 &g, int x, int y, int z) {
+    if (x < 1 || y < 1 || z < 1 || x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) return -1;
+    return (((z - 1) / kT3) * g.nty + (y - 1) / kT3) * g.ntx + (x - 1) / kT3;
+}
+
+// Self-solved trilinear controls grouped by octant o = (a_x>=0) + 2(a_y>=0) +
+// 4(a_z>=0); controls of octant o occupy [obeg[o], obeg[o+1]).  Corner b =
+// (bx, by, bz) != 0 of the cell is offset (bx sx, by sy, bz sz) from the
+// node with weight prod_d (b_d ? |a_d| : 1-|a_d|); kw[b-1] = kap w_b,
+// kap = 1/(1 - w_000).
+template <typename T> struct CtlTable3 {
+    int nc;
+    int obeg[9];
+    T kw[7][kMaxControls];
+    T kap[kMaxControls];
+};
+
+// Per-control table in the caller's order: literal weights w[0..7] (corner
+// b = bit0 x, bit1 y, bit2 z, b = 0 the node) for the feedback and the FP64
+// residual of the colour transport, self-solved FP32 weights for the sweeps.
+struct Ctl3 {
+    int nc;
+    int8_t sx[kMaxControls], sy[kMaxControls], sz[kMaxControls];
+    double w[8][kMaxControls];
+    float kw[8][kMaxControls];   // kw[0] = kap, kw[b] = kap w_b
+};
+
+// Masks of positive-weight corners (bits 0..6 for b = 1..7) present in each octant.
+struct ReachTable3 {
+    uint32_t present[8][4];
+};
+
+__device__ __forceinline__ float warp_max3(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Max over the 64 threads of the CTA (two warps).
+__device__ __forceinline__ float block_max64(float v, float *scratch) {
+    v = warp_max3(v);
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    const float r = fmaxf(scratch[0], scratch[1]);
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ set-up --
+
+__global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
+                          int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
+                          double *__restrict__ fixed) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % g.n0);
+        const int64_t r = i / g.n0;
+        const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+        const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
+        const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
+        const double x2 = __dadd_rn(g.lo2, __dmul_rn((double)iz, g.k));
+        int part = -1;
+        double dist = 0.0;
+        for (int j = 0; j < ts.n && part < 0; ++j) {
+            const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]), d2 = __dsub_rn(x2, ts.c2[j]);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+            const double dd = __dsqrt_rn(r2);
+            if (dd <= __dadd_rn(ts.r[j], extra)) {
+                part = j;
+                dist = __dsub_rn(dd, ts.r[j]);
+            }
+        }
+        const bool ring = ix == 0 || iy == 0 || iz == 0 || ix == g.n0 - 1 || iy == g.n1 - 1 || iz == g.n2 - 1;
+        const double c = speed_at(sp, x0, x1, x2);
+        const double hh = __ddiv_rn(g.k, c);
+        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : (ring ? kHard : (int8_t)0);
+        if (h32) h32[i] = (float)hh;
+        if (h64) h64[i] = hh;
+        if (fixed) fixed[i] = (part >= 0 && boundary_values && dist > 0.0) ? __ddiv_rn(dist, c) : 0.0;
+    }
+}
+
+template <typename T>
+__global__ void k_init3d(int64_t N, const int8_t *__restrict__ code, const double *__restrict__ fixed, T start,
+                         T *__restrict__ b0, T *__restrict__ b1) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        T v;
+        if (c < 0) v = Num<T>::big();
+        else if (c >= kTargetBase) v = fixed ? (T)fixed[i] : (T)0;
+        else v = start;
+        b0[i] = v;
+        b1[i] = v;
+    }
+}
+
+// ------------------------------------------------------------ scheduling --
+
+__global__ void k_schedule3d(Grid3 g, TileSched s, int par, float tol, int launch) {
+    const int ntiles = g.ntx * g.nty * g.ntz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    if (t == 0 && s.count_hist) s.count_hist[launch] = s.count[par];
+    if (s.processed[t]) {
+        s.latest[t] ^= 1;
+        s.processed[t] = 0;
+    }
+    const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
+    bool act = false;
+    for (int dz = -1; dz <= 1 && !act; ++dz)
+        for (int dy = -1; dy <= 1 && !act; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int ux = tx + dx, uy = ty + dy, uz = tz + dz;
+                if (ux < 0 || uy < 0 || uz < 0 || ux >= g.ntx || uy >= g.nty || uz >= g.ntz) continue;
+                if (s.chg[par][(uz * g.nty + uy) * g.ntx + ux] > tol) {
+                    act = true;
+                    break;
+                }
+            }
+    if (act) {
+        const int k = atomicAdd(&s.count[par ^ 1], 1);
+        s.list[par ^ 1][k] = t;
+    }
+    const float my = s.chg[par][t];
+    if (my > tol && s.tile_patch && s.patch_hist)
+        atomicOr(reinterpret_cast<unsigned long long *>(&s.patch_hist[launch]),
+                 (unsigned long long)s.tile_patch[t]);
+    if (my > 0.f && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
+    s.chg[par ^ 1][t] = 0.f;
+}
+
+// Tile image in shared memory: u[z][y][x] with a one-node halo.
+template <typename T> struct Tile3 {
+    T u[kT3 + 2][kT3 + 2][kT3 + 3];
+    int8_t c[kT3 + 2][kT3 + 2][kT3 + 4];
+    float red[2];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_tile3(const Grid3 &g, const TileSched &s, const int8_t *__restrict__ code,
+                                           const T *__restrict__ b0, const T *__restrict__ b1, int x0, int y0, int z0,
+                                           Tile3<T> &sm) {
+    constexpr int E = kT3 + 2;
+    for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
+        const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        T v = Num<T>::big();
+        int8_t cd = kHard;
+        if (x < g.n0 && y < g.n1 && z < g.n2) {
+            const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+            cd = code[i];
+            const int tt = tile_of3(g, x, y, z);
+            v = (tt >= 0 && s.latest[tt]) ? b1[i] : b0[i];
+        }
+        sm.u[lz][ly][lx] = v;
+        sm.c[lz][ly][lx] = cd;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ float store_tile3(const Grid3 &g, const TileSched &s, int t, T *__restrict__ b0,
+                                             T *__restrict__ b1, int x0, int y0, int z0, Tile3<T> &sm) {
+    const int cur = s.latest[t];
+    T *dst = cur ? b0 : b1;
+    const T *src = cur ? b1 : b0;
+    float mc = 0.f;
+    for (int e = threadIdx.x; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+        const T v = sm.u[lz + 1][ly + 1][lx + 1];
+        const T o = src[i];
+        dst[i] = v;
+        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
+        const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        mc = fmaxf(mc, d);
+    }
+    return block_max64(mc, sm.red);
+}
+
+// Local coordinates (1..8) of the node thread `tid` updates at step `st` of
+// pass `dir` (0/1: +-x, 2/3: +-y, 4/5: +-z).
+__device__ __forceinline__ void plane_node(int dir, int st, int tid, int &lx, int &ly, int &lz) {
+    const int s1 = 1 + ((dir & 1) ? (kT3 - 1 - st) : st);
+    const int a = 1 + (tid % kT3), b = 1 + (tid / kT3);
+    if (dir < 2) { lx = s1; ly = a; lz = b; }
+    else if (dir < 4) { lx = a; ly = s1; lz = b; }
+    else { lx = a; ly = b; lz = s1; }
+}
+
+// --------------------------------------------------------- value sweep 3D --
+
+template <typename T>
+__device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int lz, int8_t cd, T hh,
+                                        const CtlTable3<T> &ct) {
+    const int8_t tg = (int8_t)(cd + kTargetBase);
+    T nb[3][3][3];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int8_t q = sm.c[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx];
+                nb[dz][dy][dx] = (q == cd || q == tg) ? sm.u[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx] : Num<T>::big();
+            }
+    T b0 = Num<T>::big(), b1 = Num<T>::big();
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int sx = (o & 1) ? 2 : 0, sy = (o & 2) ? 2 : 0, sz = (o & 4) ? 2 : 0;
+        T c[7];
+#pragma unroll
+        for (int b = 1; b < 8; ++b) c[b - 1] = nb[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
+        int m = ct.obeg[o];
+        const int me = ct.obeg[o + 1];
+        for (; m + 1 < me; m += 2) {
+            T v0 = ct.kap[m] * hh, v1 = ct.kap[m + 1] * hh;
+#pragma unroll
+            for (int b = 0; b < 7; ++b) {
+                v0 = fma(ct.kw[b][m], c[b], v0);
+                v1 = fma(ct.kw[b][m + 1], c[b], v1);
+            }
+            b0 = v0 < b0 ? v0 : b0;
+            b1 = v1 < b1 ? v1 : b1;
+        }
+        if (m < me) {
+            T v0 = ct.kap[m] * hh;
+#pragma unroll
+            for (int b = 0; b < 7; ++b) v0 = fma(ct.kw[b][m], c[b], v0);
+            b0 = v0 < b0 ? v0 : b0;
+        }
+    }
+    return b0 < b1 ? b0 : b1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restrict__ code,
+                                                  const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
+                                                  TileSched s, int par, int rounds, unsigned long long *updates,
+                                                  const CtlTable3<T> ct) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
+    __shared__ Tile3<T> sm;
+    load_tile3(g, s, code, b0, b1, x0, y0, z0, sm);
+    const int tid = threadIdx.x;
+    int nfree = 0;
+    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int8_t cd = sm.c[e / 64 + 1][(e / 8) % 8 + 1][e % 8 + 1];
+        nfree += (cd >= 0 && cd < kTargetBase);
+    }
+    for (int rd = 0; rd < rounds; ++rd)
+        for (int dir = 0; dir < 6; ++dir)
+            for (int st = 0; st < kT3; ++st) {
+                int lx, ly, lz;
+                plane_node(dir, st, tid, lx, ly, lz);
+                const int8_t cd = sm.c[lz][ly][lx];
+                const bool active = cd >= 0 && cd < kTargetBase;
+                T nw = sm.u[lz][ly][lx];
+                if (active) {
+                    const int64_t i = ((int64_t)(z0 - 1 + lz) * g.n1 + (y0 - 1 + ly)) * g.n0 + (x0 - 1 + lx);
+                    const T best = sl_update3(sm, lx, ly, lz, cd, h[i], ct);
+                    if (best < Num<T>::thresh()) nw = best < nw ? best : nw;
+                }
+                __syncthreads();
+                if (active) sm.u[lz][ly][lx] = nw;
+                __syncthreads();
+            }
+    const float mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm);
+    nfree = __reduce_add_sync(0xffffffffu, nfree);
+    if ((tid & 31) == 0 && updates && nfree)
+        atomicAdd(updates, (unsigned long long)nfree * 6ull * (unsigned long long)rounds);
+    if (tid == 0) {
+        s.chg[par][t] = mc;
+        s.processed[t] = 1;
+    }
+}
+
+// ---------------------------------------------------------- reach (S*) 3D --
+
+__global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restrict__ code,
+                                                  uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
+    constexpr int E = kT3 + 2;
+    __shared__ uint8_t sr[E][E][E + 2];
+    __shared__ int8_t sc[E][E][E + 2];
+    __shared__ int flips_s;
+    const int tid = threadIdx.x;
+    if (tid == 0) flips_s = 0;
+    for (int e = tid; e < E * E * E; e += blockDim.x) {
+        const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        uint8_t v = 0;
+        int8_t cd = kHard;
+        if (x < g.n0 && y < g.n1 && z < g.n2) {
+            const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+            cd = code[i];
+            v = rch[i];
+        }
+        sr[lz][ly][lx] = v;
+        sc[lz][ly][lx] = cd;
+    }
+    __syncthreads();
+    int flips = 0;
+    for (int dir = 0; dir < 6; ++dir)
+        for (int st = 0; st < kT3; ++st) {
+            int lx, ly, lz;
+            plane_node(dir, st, tid, lx, ly, lz);
+            const int8_t cd = sc[lz][ly][lx];
+            bool hit = false;
+            if (cd >= 0 && cd < kTargetBase && !sr[lz][ly][lx]) {
+                const int8_t tg = (int8_t)(cd + kTargetBase);
+                for (int o = 0; o < 8 && !hit; ++o) {
+                    const int sx = (o & 1) ? 1 : -1, sy = (o & 2) ? 1 : -1, sz = (o & 4) ? 1 : -1;
+                    unsigned us = 0, rb = 0;
+                    for (int b = 1; b < 8; ++b) {
+                        const int zz = lz + ((b & 4) ? sz : 0), yy = ly + ((b & 2) ? sy : 0), xx = lx + ((b & 1) ? sx : 0);
+                        const int8_t q = sc[zz][yy][xx];
+                        const bool usable = q == cd || q == tg;
+                        us |= (unsigned)usable << (b - 1);
+                        rb |= (unsigned)(q == tg || (q == cd && sr[zz][yy][xx])) << (b - 1);
+                    }
+                    for (int w = 0; w < 4 && !hit; ++w) {
+                        uint32_t pres = rt.present[o][w];
+                        while (pres) {
+                            const unsigned m = (unsigned)(w * 32 + __ffs(pres) - 1);
+                            pres &= pres - 1;
+                            if ((us & m) == m && (rb & m)) {
+                                hit = true;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (hit) {
+                sr[lz][ly][lx] = 1;
+                ++flips;
+            }
+            __syncthreads();
+        }
+    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        rch[((int64_t)z * g.n1 + y) * g.n0 + x] = sr[lz + 1][ly + 1][lx + 1];
+    }
+    if (flips) atomicAdd(&flips_s, flips);
+    __syncthreads();
+    if (tid == 0) {
+        s.chg[par][t] = flips_s > 0 ? 1.f : 0.f;
+        s.processed[t] = 1;
+    }
+}
+
+template <typename T>
+__global__ void k_gather3d(Grid3 g, const uint8_t *__restrict__ latest, const T *__restrict__ b0,
+                           const T *__restrict__ b1, T *__restrict__ out_t, double *__restrict__ out64) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.n0);
+        const int64_t r = i / g.n0;
+        const int y = (int)(r % g.n1), z = (int)(r / g.n1);
+        const int tt = tile_of3(g, x, y, z);
+        const T v = (tt >= 0 && latest[tt]) ? b1[i] : b0[i];
+        if (out_t) out_t[i] = v;
+        if (out64) out64[i] = v >= Num<T>::thresh() ? (double)INFINITY : (double)v;
+    }
+}
+
+// ------------------------------------------- small grids: one warp per node --
+
+template <typename T>
+__global__ void k_value_wide3d(Grid3 g, const int8_t *__restrict__ code, const T *__restrict__ h,
+                               const T *__restrict__ uin, T *__restrict__ uout, float *__restrict__ res, int launch,
+                               const Ctl3 *__restrict__ ct) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    float mc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
+        const int8_t cd = code[i];
+        const T old = uin[i];
+        T nw = old;
+        if (cd >= 0 && cd < kTargetBase) {
+            const int8_t tg = (int8_t)(cd + kTargetBase);
+            const T hh = h[i];
+            T best = Num<T>::big();
+            for (int m = lane; m < ct->nc; m += 32) {
+                const int64_t dx = ct->sx[m], dy = (int64_t)ct->sy[m] * g.n0, dz = (int64_t)ct->sz[m] * g.n0 * g.n1;
+                const double kap = 1.0 / (1.0 - ct->w[0][m]);
+                T v = (T)kap * hh;
+                for (int b = 1; b < 8; ++b) {
+                    const int64_t j = i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0);
+                    const int8_t q = code[j];
+                    const T a = (q == cd || q == tg) ? uin[j] : Num<T>::big();
+                    v = fma((T)(kap * ct->w[b][m]), a, v);
+                }
+                best = v < best ? v : best;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = other < best ? other : best;
+            }
+            if (best < Num<T>::thresh()) nw = best < old ? best : old;
+        }
+        if (lane == 0) {
+            uout[i] = nw;
+            const bool vi = nw >= Num<T>::thresh(), oi = old >= Num<T>::thresh();
+            const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)nw - (double)old));
+            mc = fmaxf(mc, d);
+        }
+    }
+    mc = warp_max3(mc);
+    if (lane == 0 && mc > 0.f) atomic_max_pos(&res[launch], mc);
+}
+
+// ---------------------------------------------------- Step 2: U_P^(0), a* --
+
+__global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, const double *__restrict__ uc,
+                        double *__restrict__ u0) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c >= kTargetBase) { u0[i] = 0.0; continue; }
+        if (c < 0) { u0[i] = Num<double>::big(); continue; }
+        const int ix = (int)(i % g.n0);
+        const int64_t r = i / g.n0;
+        const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+        const double xi[3] = {(double)ix * (double)(gc.n0 - 1) / (double)(g.n0 - 1),
+                              (double)iy * (double)(gc.n1 - 1) / (double)(g.n1 - 1),
+                              (double)iz * (double)(gc.n2 - 1) / (double)(g.n2 - 1)};
+        const int nn[3] = {gc.n0, gc.n1, gc.n2};
+        int bb[3];
+        double tt[3];
+        for (int d = 0; d < 3; ++d) {
+            int b = (int)floor(xi[d]);
+            b = min(max(b, 0), nn[d] - 2);
+            bb[d] = b;
+            tt[d] = xi[d] - b;
+        }
+        double sum = 0.0;
+        for (int cc = 0; cc < 8; ++cc) {
+            double w = 1.0;
+            for (int d = 0; d < 3; ++d) w *= (cc >> d & 1) ? tt[d] : 1.0 - tt[d];
+            if (w > 0.0) {
+                const int64_t j = ((int64_t)(bb[2] + (cc >> 2 & 1)) * gc.n1 + (bb[1] + (cc >> 1 & 1))) * gc.n0 + bb[0] +
+                                  (cc & 1);
+                const double v = uc[j];
+                sum += w * (v >= Num<double>::thresh() ? kU0Bound : v);
+            }
+        }
+        u0[i] = sum >= kU0Bound ? Num<double>::big() : sum;
+    }
+}
+
+// Eq. (feedbackcontrol) with literal trilinear weights, lowest index on ties.
+__global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
+                             const double *__restrict__ u0, uint8_t *__restrict__ astar, const Ctl3 *__restrict__ ct) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c < 0 || c >= kTargetBase || u0[i] >= Num<double>::thresh()) {
+            astar[i] = kNoControl;
+            continue;
+        }
+        const double hh = h[i];
+        double best = Num<double>::big();
+        int arg = kNoControl;
+        for (int m = 0; m < ct->nc; ++m) {
+            const int64_t dx = ct->sx[m], dy = (int64_t)ct->sy[m] * g.n0, dz = (int64_t)ct->sz[m] * g.n0 * g.n1;
+            double v = hh;
+            for (int b = 0; b < 8; ++b) {
+                const int64_t j = i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0);
+                v += ct->w[b][m] * u0[j];
+            }
+            if (v < best) {
+                best = v;
+                arg = m;
+            }
+        }
+        astar[i] = best < Num<double>::thresh() ? (uint8_t)arg : kNoControl;
+    }
+}
+
+// --------------------------------------------------- Step 3.1: colours phi --
+
+template <int RG>
+__global__ void k_phi_init3d(int64_t N, const int8_t *__restrict__ code, int j0, int zero_all,
+                             float *__restrict__ b0, float *__restrict__ b1) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float v = (!zero_all && c == (int8_t)(kTargetBase + j0 + q)) ? 1.0f : 0.0f;
+            b0[(int64_t)q * N + i] = v;
+            b1[(int64_t)q * N + i] = v;
+        }
+    }
+}
+
+template <int RG> struct Phi3Smem {
+    float u[RG][kT3 + 2][kT3 + 2][kT3 + 3];
+    float src[RG][kT3][kT3][kT3 + 1];
+    int8_t c[kT3 + 2][kT3 + 2][kT3 + 4];
+    uint8_t a[kT3][kT3][kT3 + 4];
+    float red[2];
+};
+
+// FP32 colour transport (bulk: monotone max from 0; correction: with source).
+template <int RG, bool kSource>
+__global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restrict__ code,
+                                                const uint8_t *__restrict__ astar, float *__restrict__ b0,
+                                                float *__restrict__ b1, const float *__restrict__ src, TileSched s,
+                                                int par, int rounds, const Ctl3 *__restrict__ pc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    __shared__ Phi3Smem<RG> sm;
+    constexpr int E = kT3 + 2;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < E * E * E; e += blockDim.x) {
+        const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        const bool in = x < g.n0 && y < g.n1 && z < g.n2;
+        const bool inner = lx >= 1 && lx <= kT3 && ly >= 1 && ly <= kT3 && lz >= 1 && lz <= kT3;
+        const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+        int8_t cd = kHard;
+        if (in) {
+            cd = code[i];
+            const int tt = tile_of3(g, x, y, z);
+            const float *bs = (tt >= 0 && s.latest[tt]) ? b1 : b0;
+#pragma unroll
+            for (int q = 0; q < RG; ++q) sm.u[q][lz][ly][lx] = bs[(int64_t)q * N + i];
+        } else {
+#pragma unroll
+            for (int q = 0; q < RG; ++q) sm.u[q][lz][ly][lx] = 0.0f;
+        }
+        if (inner) {
+            sm.a[lz - 1][ly - 1][lx - 1] = in ? astar[i] : kNoControl;
+            if (kSource) {
+#pragma unroll
+                for (int q = 0; q < RG; ++q) sm.src[q][lz - 1][ly - 1][lx - 1] = in ? src[(int64_t)q * N + i] : 0.0f;
+            }
+        }
+        sm.c[lz][ly][lx] = cd;
+    }
+    __syncthreads();
+    for (int rd = 0; rd < rounds; ++rd)
+        for (int dir = 0; dir < 6; ++dir)
+            for (int st = 0; st < kT3; ++st) {
+                int lx, ly, lz;
+                plane_node(dir, st, tid, lx, ly, lz);
+                const int8_t cd = sm.c[lz][ly][lx];
+                const uint8_t a = sm.a[lz - 1][ly - 1][lx - 1];
+                const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
+                float nw[RG];
+                if (active) {
+                    const int sx = pc->sx[a], sy = pc->sy[a], sz = pc->sz[a];
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) {
+                        float v = 0.0f;
+#pragma unroll
+                        for (int b = 1; b < 8; ++b)
+                            v = fmaf(pc->kw[b][a],
+                                     sm.u[q][lz + ((b & 4) ? sz : 0)][ly + ((b & 2) ? sy : 0)][lx + ((b & 1) ? sx : 0)], v);
+                        if (kSource) {
+                            nw[q] = fmaf(pc->kw[0][a], sm.src[q][lz - 1][ly - 1][lx - 1], v);
+                        } else {
+                            const float o = sm.u[q][lz][ly][lx];
+                            nw[q] = v > o ? v : o;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) sm.u[q][lz][ly][lx] = nw[q];
+                }
+                __syncthreads();
+            }
+    const int cur = s.latest[t];
+    float *dst = cur ? b0 : b1;
+    const float *old = cur ? b1 : b0;
+    float mc = 0.f;
+    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float v = sm.u[q][lz + 1][ly + 1][lx + 1];
+            const float o = old[(int64_t)q * N + i];
+            dst[(int64_t)q * N + i] = v;
+            mc = fmaxf(mc, fabsf(v - o));
+        }
+    }
+    mc = block_max64(mc, sm.red);
+    if (tid == 0) {
+        s.chg[par][t] = mc;
+        s.processed[t] = 1;
+    }
+}
+
+template <int RG>
+__global__ void k_phi_collect3d(Grid3 g, const uint8_t *__restrict__ latest, const float *__restrict__ b0,
+                                const float *__restrict__ b1, double *__restrict__ out, int add) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.n0);
+        const int64_t r = i / g.n0;
+        const int y = (int)(r % g.n1), z = (int)(r / g.n1);
+        const int tt = tile_of3(g, x, y, z);
+        const float *src = (tt >= 0 && latest[tt]) ? b1 : b0;
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const double v = (double)src[(int64_t)q * N + i];
+            if (add) out[(int64_t)q * N + i] += v;
+            else out[(int64_t)q * N + i] = v;
+        }
+    }
+}
+
+template <int RG>
+__global__ void k_phi_residual3d(Grid3 g, const int8_t *__restrict__ code, const uint8_t *__restrict__ astar,
+                                 const double *__restrict__ phi, float *__restrict__ r32, float *rmax,
+                                 const Ctl3 *__restrict__ pc) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    float mc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        const uint8_t a = astar[i];
+        if (!(c >= 0 && c < kTargetBase && a != kNoControl)) {
+#pragma unroll
+            for (int q = 0; q < RG; ++q) r32[(int64_t)q * N + i] = 0.0f;
+            continue;
+        }
+        const int64_t dx = pc->sx[a], dy = (int64_t)pc->sy[a] * g.n0, dz = (int64_t)pc->sz[a] * g.n0 * g.n1;
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const double *f = phi + (int64_t)q * N;
+            double v = 0.0;
+            for (int b = 0; b < 8; ++b)
+                v += pc->w[b][a] * f[i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0)];
+            const double r = v - f[i];
+            r32[(int64_t)q * N + i] = (float)r;
+            mc = fmaxf(mc, (float)fabs(r));
+        }
+    }
+    mc = warp_max3(mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(rmax, mc);
+}
+
+// Remark 3.1 fill round (R12), axis neighbours in increasing node index.
+__global__ void k_fill3d(Grid3 g, const int8_t *__restrict__ lin, int8_t *__restrict__ lout,
+                         unsigned long long *changed) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        int8_t v = lin[i];
+        if (v == -2) {
+            const int ix = (int)(i % g.n0);
+            const int64_t r = i / g.n0;
+            const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+            int8_t nv = -2;
+            if (iz > 0 && lin[i - sz] >= 0) nv = lin[i - sz];
+            else if (iy > 0 && lin[i - sy] >= 0) nv = lin[i - sy];
+            else if (ix > 0 && lin[i - 1] >= 0) nv = lin[i - 1];
+            else if (ix < g.n0 - 1 && lin[i + 1] >= 0) nv = lin[i + 1];
+            else if (iy < g.n1 - 1 && lin[i + sy] >= 0) nv = lin[i + sy];
+            else if (iz < g.n2 - 1 && lin[i + sz] >= 0) nv = lin[i + sz];
+            if (nv >= 0) { v = nv; ++cnt; }
+        }
+        lout[i] = v;
+    }
+    cnt = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(changed, cnt);
+}
+
+// Patch compaction: per-tile patch masks, per-patch node and tile counts.
+__global__ void __launch_bounds__(kT3n) k_compact3d(Grid3 g, const int8_t *__restrict__ code,
+                                                    uint64_t *__restrict__ tile_patch,
+                                                    unsigned long long *__restrict__ patch_nodes,
+                                                    unsigned long long *__restrict__ patch_tiles) {
+    const int t = blockIdx.x;
+    const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
+    __shared__ unsigned long long mask_s;
+    __shared__ int cnt_s[kMaxTargets];
+    if (threadIdx.x == 0) mask_s = 0;
+    for (int j = threadIdx.x; j < kMaxTargets; j += blockDim.x) cnt_s[j] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int x = x0 + e % kT3, y = y0 + (e / kT3) % kT3, z = z0 + e / (kT3 * kT3);
+        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        const int8_t c = code[((int64_t)z * g.n1 + y) * g.n0 + x];
+        if (c >= 0 && c < kTargetBase) {
+            atomicOr(&mask_s, 1ull << c);
+            atomicAdd(&cnt_s[c], 1);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kMaxTargets; j += blockDim.x)
+        if (cnt_s[j]) {
+            atomicAdd(&patch_nodes[j], (unsigned long long)cnt_s[j]);
+            atomicAdd(&patch_tiles[j], 1ull);
+        }
+    if (threadIdx.x == 0) tile_patch[t] = mask_s;
+}
+
+// FP64 polish with the FP32 filter (see k_polish2d): margin 2^-17 (h + max|a|)
+// covers the eight-term trilinear sum.
+__global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
+                           const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
+                           const CtlTable3<float> c32, const CtlTable3<double> c64) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    float mc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t cd = code[i];
+        double v = uin[i];
+        if (cd >= 0 && cd < kTargetBase) {
+            const int ix = (int)(i % g.n0);
+            const int64_t r = i / g.n0;
+            const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+            const int8_t tg = (int8_t)(cd + kTargetBase);
+            double nb[3][3][3];
+            float nf[3][3][3];
+            float amax = 0.f;
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int64_t j = ((int64_t)(iz - 1 + dz) * g.n1 + (iy - 1 + dy)) * g.n0 + (ix - 1 + dx);
+                        const int8_t q = code[j];
+                        const double w = uin[j];
+                        const bool fin = (q == cd || q == tg) && w < Num<double>::thresh();
+                        nb[dz][dy][dx] = fin ? w : Num<double>::big();
+                        nf[dz][dy][dx] = fin ? (float)w : Num<float>::big();
+                        if (fin) amax = fmaxf(amax, fabsf((float)w));
+                    }
+            const double hh = h[i];
+            const float hf = (float)hh;
+            float b32 = Num<float>::big();
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int sx = (o & 1) ? 2 : 0, sy = (o & 2) ? 2 : 0, sz = (o & 4) ? 2 : 0;
+                float c[7];
+#pragma unroll
+                for (int b = 1; b < 8; ++b) c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
+                for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
+                    float w = c32.kap[m] * hf;
+#pragma unroll
+                    for (int b = 0; b < 7; ++b) w = fmaf(c32.kw[b][m], c[b], w);
+                    b32 = w < b32 ? w : b32;
+                }
+            }
+            if (b32 < Num<float>::thresh() && v < Num<double>::thresh()) {
+                const float lim = b32 + ldexpf(hf + amax, -17);
+                double best = Num<double>::big();
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    const int sx = (o & 1) ? 2 : 0, sy = (o & 2) ? 2 : 0, sz = (o & 4) ? 2 : 0;
+                    float c[7];
+                    double cdd[7];
+#pragma unroll
+                    for (int b = 1; b < 8; ++b) {
+                        c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
+                        cdd[b - 1] = nb[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
+                    }
+                    for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
+                        float w = c32.kap[m] * hf;
+#pragma unroll
+                        for (int b = 0; b < 7; ++b) w = fmaf(c32.kw[b][m], c[b], w);
+                        if (w <= lim) {
+                            double x = c64.kap[m] * hh;
+#pragma unroll
+                            for (int b = 0; b < 7; ++b) x = fma(c64.kw[b][m], cdd[b], x);
+                            best = x < best ? x : best;
+                        }
+                    }
+                }
+                mc = fmaxf(mc, (float)fabs(best - v));
+                v = best;
+            }
+        }
+        uout[i] = v;
+    }
+    mc = warp_max3(mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(maxchg, mc);
+}
+
+// ======================================================================
+// Host driver of the 3D path
+// ======================================================================
+namespace {
+
+constexpr int kReachCap3 = 1 << 18;
+
+inline int grid_for3(int64_t n, int bs = 256) {
+    int64_t b = (n + bs - 1) / bs;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+template <typename T> T *alloc3(hjbp_plan &p, int64_t n) {
+    return static_cast<T *>(p.dev_alloc(sizeof(T) * (size_t)std::max<int64_t>(n, 1)));
+}
+
+__global__ void k_iota3(int n, int *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
+}
+
+struct Sched3 {
+    TileSched d{};
+    int ntiles = 0;
+    int hist = 0;
+    int *iota = nullptr;
+};
+
+Sched3 make_sched3(hjbp_plan &p, const Grid3 &g, int hist) {
+    Sched3 s;
+    s.ntiles = g.ntx * g.nty * g.ntz;
+    s.hist = hist;
+    const int nt = std::max(1, s.ntiles);
+    s.d.list[0] = alloc3<int>(p, nt);
+    s.d.list[1] = alloc3<int>(p, nt);
+    s.d.count = alloc3<int>(p, 2);
+    s.d.chg[0] = alloc3<float>(p, nt);
+    s.d.chg[1] = alloc3<float>(p, nt);
+    s.d.latest = alloc3<uint8_t>(p, nt);
+    s.d.processed = alloc3<uint8_t>(p, nt);
+    s.d.tile_patch = nullptr;
+    s.d.patch_hist = alloc3<uint64_t>(p, hist);
+    s.d.res_hist = alloc3<float>(p, hist);
+    s.d.count_hist = alloc3<int>(p, hist);
+    s.iota = alloc3<int>(p, nt);
+    k_iota3<<<grid_for3(nt), 256, 0, p.stream>>>(nt, s.iota);
+    ++p.stats.kernel_launches;
+    return s;
+}
+
+struct Run3 {
+    int64_t tile_visits = 0;
+    int launches = 0;
+    bool converged = false;
+    float last_res = 0.f;
+};
+
+template <class Sweep> Run3 run_tiles3(hjbp_plan &p, const Grid3 &g, Sched3 &s, float tol, int cap, Sweep sweep) {
+    Run3 rr;
+    if (s.ntiles == 0) {
+        rr.converged = true;
+        return rr;
+    }
+    cudaStream_t st = p.stream;
+    const int nt = s.ntiles;
+    check_cuda(cudaMemcpyAsync(s.d.list[0], s.iota, sizeof(int) * nt, cudaMemcpyDeviceToDevice, st), "reset");
+    const int counts[2] = {nt, 0};
+    check_cuda(cudaMemcpyAsync(s.d.count, counts, sizeof(counts), cudaMemcpyHostToDevice, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.chg[0], 0, sizeof(float) * nt, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.chg[1], 0, sizeof(float) * nt, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.latest, 0, nt, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.processed, 0, nt, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.patch_hist, 0, sizeof(uint64_t) * s.hist, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.res_hist, 0, sizeof(float) * s.hist, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.count_hist, 0, sizeof(int) * s.hist, st), "reset");
+    check_cuda(cudaStreamSynchronize(st), "reset sync");
+    cap = std::min(cap, s.hist);
+    int par = 0, L = 0, check_every = 4;
+    while (L < cap) {
+        sweep(par);
+        check_cuda(cudaGetLastError(), "sweep3 launch");
+        k_schedule3d<<<(nt + 255) / 256, 256, 0, st>>>(g, s.d, par, tol, L);
+        ++p.stats.kernel_launches;
+        par ^= 1;
+        ++L;
+        if (L % check_every == 0 || L == cap) {
+            int left = 0;
+            check_cuda(cudaMemcpyAsync(&left, s.d.count + par, sizeof(int), cudaMemcpyDeviceToHost, st), "count");
+            check_cuda(cudaStreamSynchronize(st), "sweep3 sync");
+            if (left == 0) {
+                rr.converged = true;
+                break;
+            }
+            check_every = std::min(check_every * 2, 16);
+        }
+    }
+    std::vector<int> ch(L);
+    std::vector<float> rh(L);
+    if (L) {
+        check_cuda(cudaMemcpyAsync(ch.data(), s.d.count_hist, sizeof(int) * L, cudaMemcpyDeviceToHost, st), "hist");
+        check_cuda(cudaMemcpyAsync(rh.data(), s.d.res_hist, sizeof(float) * L, cudaMemcpyDeviceToHost, st), "hist");
+        check_cuda(cudaStreamSynchronize(st), "hist sync");
+    }
+    for (int l = 0; l < L; ++l)
+        if (ch[l] > 0) {
+            rr.launches = l + 1;
+            rr.last_res = rh[l];
+            rr.tile_visits += ch[l];
+        }
+    return rr;
+}
+
+template <typename T> CtlTable3<T> make_table3(const hjbp_plan &p) {
+    CtlTable3<T> ct;
+    std::memset(&ct, 0, sizeof(ct));
+    const int nc = p.desc.n_controls;
+    ct.nc = nc;
+    int pos = 0;
+    for (int o = 0; o < 8; ++o) {
+        ct.obeg[o] = pos;
+        for (int m = 0; m < nc; ++m) {
+            const double *a = &p.controls[3 * m];
+            const int oo = (a[0] >= 0.0 ? 1 : 0) + (a[1] >= 0.0 ? 2 : 0) + (a[2] >= 0.0 ? 4 : 0);
+            if (oo != o) continue;
+            const double b[3] = {std::fabs(a[0]), std::fabs(a[1]), std::fabs(a[2])};
+            double w[8];
+            for (int c = 0; c < 8; ++c) {
+                w[c] = 1.0;
+                for (int d = 0; d < 3; ++d) w[c] *= (c >> d & 1) ? b[d] : 1.0 - b[d];
+            }
+            const double kap = 1.0 / (1.0 - w[0]);
+            for (int c = 1; c < 8; ++c) ct.kw[c - 1][pos] = (T)(kap * w[c]);
+            ct.kap[pos] = (T)kap;
+            ++pos;
+        }
+    }
+    ct.obeg[8] = pos;
+    return ct;
+}
+
+Ctl3 make_ctl3(const hjbp_plan &p) {
+    Ctl3 c;
+    std::memset(&c, 0, sizeof(c));
+    c.nc = p.desc.n_controls;
+    for (int m = 0; m < c.nc; ++m) {
+        const double *a = &p.controls[3 * m];
+        c.sx[m] = a[0] >= 0.0 ? 1 : -1;
+        c.sy[m] = a[1] >= 0.0 ? 1 : -1;
+        c.sz[m] = a[2] >= 0.0 ? 1 : -1;
+        const double b[3] = {std::fabs(a[0]), std::fabs(a[1]), std::fabs(a[2])};
+        double w[8];
+        for (int cc = 0; cc < 8; ++cc) {
+            w[cc] = 1.0;
+            for (int d = 0; d < 3; ++d) w[cc] *= (cc >> d & 1) ? b[d] : 1.0 - b[d];
+            c.w[cc][m] = w[cc];
+        }
+        const double kap = 1.0 / (1.0 - w[0]);
+        c.kw[0][m] = (float)kap;
+        for (int cc = 1; cc < 8; ++cc) c.kw[cc][m] = (float)(kap * w[cc]);
+    }
+    return c;
+}
+
+ReachTable3 make_reach3(const hjbp_plan &p) {
+    ReachTable3 rt;
+    std::memset(&rt, 0, sizeof(rt));
+    for (int m = 0; m < p.desc.n_controls; ++m) {
+        const double *a = &p.controls[3 * m];
+        const int o = (a[0] >= 0.0 ? 1 : 0) + (a[1] >= 0.0 ? 2 : 0) + (a[2] >= 0.0 ? 4 : 0);
+        const double b[3] = {std::fabs(a[0]), std::fabs(a[1]), std::fabs(a[2])};
+        unsigned need = 0;
+        for (int c = 1; c < 8; ++c) {
+            double w = 1.0;
+            for (int d = 0; d < 3; ++d) w *= (c >> d & 1) ? b[d] : 1.0 - b[d];
+            if (w > 0.0) need |= 1u << (c - 1);
+        }
+        if (need) rt.present[o][need >> 5] |= 1u << (need & 31);
+    }
+    return rt;
+}
+
+Grid3 make_grid3(const int n[3], const double lo[3], double k) {
+    Grid3 g;
+    g.n0 = n[0];
+    g.n1 = n[1];
+    g.n2 = n[2];
+    g.ntx = (n[0] - 2 + kT3 - 1) / kT3;
+    g.nty = (n[1] - 2 + kT3 - 1) / kT3;
+    g.ntz = (n[2] - 2 + kT3 - 1) / kT3;
+    g.lo0 = lo[0];
+    g.lo1 = lo[1];
+    g.lo2 = lo[2];
+    g.k = k;
+    return g;
+}
+
+struct Ev3 {
+    cudaEvent_t e;
+    explicit Ev3(cudaStream_t s) {
+        check_cuda(cudaEventCreate(&e), "event");
+        check_cuda(cudaEventRecord(e, s), "event");
+    }
+    ~Ev3() { cudaEventDestroy(e); }
+};
+
+float ms3(const Ev3 &a, const Ev3 &b) {
+    float ms = 0.f;
+    cudaEventSynchronize(b.e);
+    cudaEventElapsedTime(&ms, a.e, b.e);
+    return ms;
+}
+
+int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, int64_t N) {
+    const ReachTable3 rt = make_reach3(p);
+    unsigned long long *removed = alloc3<unsigned long long>(p, 1);
+    int total = 0;
+    for (int round = 0; round < 64; ++round) {
+        check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
+        Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
+            k_reach3d<<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt);
+            ++p.stats.kernel_launches;
+        });
+        total += rr.launches;
+        if (!rr.converged) throw HjbpError{HJBP_ECUDA, "reachability sweep did not settle"};
+        check_cuda(cudaMemsetAsync(removed, 0, sizeof(unsigned long long), p.stream), "memset");
+        k_reach_prune<<<grid_for3(N), 256, 0, p.stream>>>(N, code, rch, removed);
+        ++p.stats.kernel_launches;
+        unsigned long long h = 0;
+        check_cuda(cudaMemcpyAsync(&h, removed, sizeof(h), cudaMemcpyDeviceToHost, p.stream), "removed");
+        check_cuda(cudaStreamSynchronize(p.stream), "reach sync");
+        if (h == 0) break;
+    }
+    return total;
+}
+
+template <typename T>
+Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0, T *b1, Sched3 &s, double tol,
+            int cap, int rounds, T *out_t, double *out64, unsigned long long *updates) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    k_init3d<T><<<grid_for3(N), 256, 0, p.stream>>>(N, code, nullptr, (T)kStartValue, b0, b1);
+    ++p.stats.kernel_launches;
+    const CtlTable3<T> ct = make_table3<T>(p);
+    const bool timed = (p.desc.flags & HJBP_FLAG_TIME_SWEEPS) != 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+    Run3 rr = run_tiles3(p, g, s, (float)tol, cap, [&](int par) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timed) {
+            check_cuda(cudaEventCreate(&a), "event");
+            check_cuda(cudaEventCreate(&b), "event");
+            check_cuda(cudaEventRecord(a, p.stream), "event");
+        }
+        k_value3d<T><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        ++p.stats.kernel_launches;
+        ++p.stats.sweep_kernel_launches;
+        if (timed) {
+            check_cuda(cudaEventRecord(b, p.stream), "event");
+            evs.emplace_back(a, b);
+        }
+    });
+    p.stats.sweep_tile_visits += rr.tile_visits;
+    if (timed) {
+        check_cuda(cudaStreamSynchronize(p.stream), "timing sync");
+        double ms = 0.0;
+        for (size_t l = 0; l < evs.size(); ++l) {
+            float m = 0.f;
+            if ((int)l < rr.launches) {
+                cudaEventElapsedTime(&m, evs[l].first, evs[l].second);
+                ms += m;
+            }
+            cudaEventDestroy(evs[l].first);
+            cudaEventDestroy(evs[l].second);
+        }
+        p.stats.ms_sweep_kernel += ms;
+    }
+    k_gather3d<T><<<grid_for3(N), 256, 0, p.stream>>>(g, s.d.latest, b0, b1, out_t, out64);
+    ++p.stats.kernel_launches;
+    check_cuda(cudaGetLastError(), "gather3");
+    return rr;
+}
+
+Run3 wide3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const double *h, const double *fixed, double *b0,
+           double *b1, double tol, int cap, const Ctl3 *dct, double *out64) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    cudaStream_t st = p.stream;
+    k_init3d<double><<<grid_for3(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1);
+    ++p.stats.kernel_launches;
+    const int chunk = 16;
+    float *res = alloc3<float>(p, chunk);
+    std::vector<float> hres(chunk);
+    Run3 rr;
+    const int blocks = (int)std::min<int64_t>((N + 7) / 8, 152 * 16);
+    int L = 0;
+    while (L < cap) {
+        check_cuda(cudaMemsetAsync(res, 0, sizeof(float) * chunk, st), "memset");
+        const int n = std::min(chunk, cap - L);
+        for (int l = 0; l < n; ++l) {
+            const double *in = ((L + l) & 1) ? b1 : b0;
+            double *out = ((L + l) & 1) ? b0 : b1;
+            k_value_wide3d<double><<<blocks, 256, 0, st>>>(g, code, h, in, out, res, l, dct);
+            ++p.stats.kernel_launches;
+        }
+        check_cuda(cudaGetLastError(), "wide3");
+        check_cuda(cudaMemcpyAsync(hres.data(), res, sizeof(float) * chunk, cudaMemcpyDeviceToHost, st), "res");
+        check_cuda(cudaStreamSynchronize(st), "wide3 sync");
+        for (int l = 0; l < n; ++l) {
+            rr.launches = L + l + 1;
+            rr.last_res = hres[l];
+            if (hres[l] <= tol) {
+                rr.converged = true;
+                break;
+            }
+        }
+        L += n;
+        if (rr.converged) break;
+    }
+    const double *fin = (rr.launches & 1) ? b1 : b0;
+    k_finalize<<<grid_for3(N), 256, 0, st>>>(N, fin, out64);
+    ++p.stats.kernel_launches;
+    return rr;
+}
+
+}  // namespace
+
+hjbp_status solve3d(hjbp_plan &p) {
+    const hjbp_problem_desc &d = p.desc;
+    cudaStream_t st = p.stream;
+    const int64_t N = p.N;
+    const Grid3 g = make_grid3(d.n, d.lo, p.k);
+    SpeedParams sp;
+    sp.kind = d.speed;
+    for (int i = 0; i < 64; ++i) sp.p[i] = d.speed_params[i];
+    TargetSet ts;
+    std::memset(&ts, 0, sizeof(ts));
+    ts.n = d.n_targets;
+    for (int j = 0; j < ts.n; ++j) {
+        ts.c0[j] = p.targets[4 * j];
+        ts.c1[j] = p.targets[4 * j + 1];
+        ts.c2[j] = p.targets[4 * j + 2];
+        ts.r[j] = p.targets[4 * j + 3];
+    }
+    const int cap = d.max_sweeps > 0 ? d.max_sweeps : 1000000;
+    const int hist = std::max(std::min(cap, 1 << 20), kReachCap3);
+    const bool fp32 = d.precision == HJBP_FP32_POLISH64;
+    const int R = d.n_targets;
+    const int vrounds = d.tune[0] > 0 ? d.tune[0] : 1;
+    const int prounds = d.tune[1] > 0 ? d.tune[1] : 2;
+    hjbp_stats &S = p.stats;
+    std::memset(&S, 0, sizeof(S));
+    hjbp_status status = HJBP_OK;
+
+    Ctl3 hct = make_ctl3(p);
+    Ctl3 *dct = static_cast<Ctl3 *>(p.dev_alloc(sizeof(Ctl3)));
+    check_cuda(cudaMemcpyAsync(dct, &hct, sizeof(Ctl3), cudaMemcpyHostToDevice, st), "ctl3");
+
+    Ev3 e0(st);
+    int8_t *code0 = alloc3<int8_t>(p, N);
+    int8_t *code = alloc3<int8_t>(p, N);
+    uint8_t *rch = alloc3<uint8_t>(p, N);
+    double *h64 = alloc3<double>(p, N);
+    float *h32 = fp32 ? alloc3<float>(p, N) : nullptr;
+    unsigned long long *updates = alloc3<unsigned long long>(p, 1);
+    check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
+    k_setup3d<<<grid_for3(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr);
+    ++S.kernel_launches;
+    check_cuda(cudaGetLastError(), "setup3");
+    Sched3 sched = make_sched3(p, g, hist);
+    Ev3 e1(st);
+
+    if (p.patchy) {
+        const Grid3 gc = make_grid3(d.n_coarse, d.lo, p.kc);
+        const int64_t Nc = p.Nc;
+        int8_t *ccode = alloc3<int8_t>(p, Nc);
+        uint8_t *crch = alloc3<uint8_t>(p, Nc);
+        double *ch64 = alloc3<double>(p, Nc);
+        double *cfix = alloc3<double>(p, Nc);
+        double *cb0 = alloc3<double>(p, Nc), *cb1 = alloc3<double>(p, Nc);
+        k_setup3d<<<grid_for3(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(3.0) / 2.0, 1, ccode, nullptr, ch64,
+                                                 cfix);
+        k_merge_targets<<<grid_for3(Nc), 256, 0, st>>>(Nc, ccode);
+        S.kernel_launches += 2;
+        Sched3 csched = make_sched3(p, gc, hist);
+        S.sweeps_reach += reach3(p, gc, ccode, crch, csched, Nc);
+        const double tolc = d.tol_coarse > 0 ? d.tol_coarse : 1e-12;
+        Run3 rc = wide3(p, gc, ccode, ch64, cfix, cb0, cb1, tolc, cap, dct, p.u_coarse);
+        S.sweeps_coarse = rc.launches;
+        if (!rc.converged) status = HJBP_ENOCONV;
+        Ev3 e2(st);
+        k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0);
+        k_feedback3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, dct);
+        S.kernel_launches += 2;
+        check_cuda(cudaGetLastError(), "feedback3");
+        Ev3 e3(st);
+        {
+            const int RG = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+            float *f0 = alloc3<float>(p, N * RG), *f1 = alloc3<float>(p, N * RG), *r32 = alloc3<float>(p, N * RG);
+            double *phig = alloc3<double>(p, N * RG);
+            float *rmax = alloc3<float>(p, 1);
+            const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
+            for (int j0 = 0; j0 < R; j0 += RG) {
+                const int rg = std::min(RG, R - j0);
+                const int rgl = rg >= 4 ? 4 : (rg == 3 ? 4 : rg);
+                auto launch_group = [&](auto tag) {
+                    constexpr int G = decltype(tag)::value;
+                    k_phi_init3d<G><<<grid_for3(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
+                    ++S.kernel_launches;
+                    Run3 rp = run_tiles3(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par) {
+                        k_phi3d<G, false><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d,
+                                                                         par, prounds, dct);
+                        ++S.kernel_launches;
+                    });
+                    S.sweeps_phi += rp.launches;
+                    if (!rp.converged) status = HJBP_ENOCONV;
+                    k_phi_collect3d<G><<<grid_for3(N), 256, 0, st>>>(g, sched.d.latest, f0, f1, phig, 0);
+                    ++S.kernel_launches;
+                    for (int it = 0; it < 6; ++it) {
+                        check_cuda(cudaMemsetAsync(rmax, 0, sizeof(float), st), "memset");
+                        k_phi_residual3d<G><<<grid_for3(N), 256, 0, st>>>(g, code0, p.astar, phig, r32, rmax, dct);
+                        ++S.kernel_launches;
+                        float hr = 0.f;
+                        check_cuda(cudaMemcpyAsync(&hr, rmax, sizeof(float), cudaMemcpyDeviceToHost, st), "rmax");
+                        check_cuda(cudaStreamSynchronize(st), "rmax sync");
+                        S.phi_refinements++;
+                        if (hr <= tolp) break;
+                        k_phi_init3d<G><<<grid_for3(N), 256, 0, st>>>(N, code0, j0, 1, f0, f1);
+                        ++S.kernel_launches;
+                        const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
+                        Run3 rc2 = run_tiles3(p, g, sched, told, cap, [&](int par) {
+                            k_phi3d<G, true><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, r32, sched.d,
+                                                                            par, prounds, dct);
+                            ++S.kernel_launches;
+                        });
+                        S.sweeps_phi += rc2.launches;
+                        k_phi_collect3d<G><<<grid_for3(N), 256, 0, st>>>(g, sched.d.latest, f0, f1, phig, 1);
+                        ++S.kernel_launches;
+                    }
+                    check_cuda(cudaMemcpyAsync(p.phi + (int64_t)j0 * N, phig, sizeof(double) * N * rg,
+                                               cudaMemcpyDeviceToDevice, st), "phi copy");
+                };
+                if (rgl == 4) launch_group(std::integral_constant<int, 4>());
+                else if (rgl == 2) launch_group(std::integral_constant<int, 2>());
+                else launch_group(std::integral_constant<int, 1>());
+            }
+            k_label2d<<<grid_for3(N), 256, 0, st>>>(N, code0, p.astar, p.phi, R, p.label_out);
+            ++S.kernel_launches;
+            int8_t *lab2 = reinterpret_cast<int8_t *>(rch);
+            unsigned long long *chg = alloc3<unsigned long long>(p, 1);
+            for (int it = 0; it < 100000; ++it) {
+                check_cuda(cudaMemsetAsync(chg, 0, sizeof(unsigned long long), st), "memset");
+                k_fill3d<<<grid_for3(N), 256, 0, st>>>(g, p.label_out, lab2, chg);
+                ++S.kernel_launches;
+                check_cuda(cudaMemcpyAsync(p.label_out, lab2, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
+                unsigned long long hc = 0;
+                check_cuda(cudaMemcpyAsync(&hc, chg, sizeof(hc), cudaMemcpyDeviceToHost, st), "fill count");
+                check_cuda(cudaStreamSynchronize(st), "fill sync");
+                S.uncovered_filled += (int64_t)hc;
+                if (!hc) break;
+            }
+            k_patch_codes<<<grid_for3(N), 256, 0, st>>>(N, code0, p.label_out, code);
+            ++S.kernel_launches;
+        }
+        Ev3 e4(st);
+        {
+            uint64_t *tile_patch = alloc3<uint64_t>(p, sched.ntiles);
+            unsigned long long *pn = alloc3<unsigned long long>(p, kMaxTargets);
+            unsigned long long *pt = alloc3<unsigned long long>(p, kMaxTargets);
+            check_cuda(cudaMemsetAsync(pn, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
+            check_cuda(cudaMemsetAsync(pt, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
+            if (sched.ntiles) {
+                k_compact3d<<<sched.ntiles, kT3n, 0, st>>>(g, code, tile_patch, pn, pt);
+                ++S.kernel_launches;
+            }
+            sched.d.tile_patch = tile_patch;
+            unsigned long long hn[kMaxTargets], ht[kMaxTargets];
+            check_cuda(cudaMemcpyAsync(hn, pn, sizeof(hn), cudaMemcpyDeviceToHost, st), "compact");
+            check_cuda(cudaMemcpyAsync(ht, pt, sizeof(ht), cudaMemcpyDeviceToHost, st), "compact");
+            check_cuda(cudaStreamSynchronize(st), "compact sync");
+            for (int j = 0; j < R; ++j) {
+                S.patch_nodes[j] = (int64_t)hn[j];
+                S.patch_tiles[j] = (int64_t)ht[j];
+            }
+        }
+        Ev3 e5(st);
+        S.ms_coarse = ms3(e1, e2);
+        S.ms_feedback = ms3(e2, e3);
+        S.ms_labels = ms3(e3, e4);
+        S.ms_compact = ms3(e4, e5);
+    } else {
+        check_cuda(cudaMemcpyAsync(code, code0, (size_t)N, cudaMemcpyDeviceToDevice, st), "code copy");
+        k_merge_targets<<<grid_for3(N), 256, 0, st>>>(N, code);
+        ++S.kernel_launches;
+    }
+
+    Ev3 f0(st);
+    S.sweeps_reach += reach3(p, g, code, rch, sched, N);
+    Ev3 fr(st);
+    Run3 rv;
+    if (fp32) {
+        float *b0 = alloc3<float>(p, N), *b1 = alloc3<float>(p, N);
+        rv = value3<float>(p, g, code, h32, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates);
+    } else {
+        double *b0 = alloc3<double>(p, N), *b1 = alloc3<double>(p, N);
+        rv = value3<double>(p, g, code, h64, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates);
+    }
+    S.sweeps_fine = rv.launches;
+    S.residual_fine = rv.last_res;
+    if (!rv.converged) status = HJBP_ENOCONV;
+    if (rv.launches > 0) {
+        std::vector<uint64_t> ph(rv.launches);
+        check_cuda(cudaMemcpyAsync(ph.data(), sched.d.patch_hist, sizeof(uint64_t) * rv.launches,
+                                   cudaMemcpyDeviceToHost, st), "patch hist");
+        check_cuda(cudaStreamSynchronize(st), "patch hist sync");
+        for (int l = 0; l < rv.launches; ++l)
+            for (int j = 0; j < R && j < 64; ++j)
+                if ((ph[l] >> j) & 1ull) S.sweeps_patch[j]++;
+    }
+    Ev3 f1(st);
+    if (fp32) {
+        double *pa = alloc3<double>(p, N), *pb = alloc3<double>(p, N);
+        float *mc = alloc3<float>(p, 1);
+        k_widen<<<grid_for3(N), 256, 0, st>>>(N, p.u32, pa);
+        ++S.kernel_launches;
+        const CtlTable3<double> c64 = make_table3<double>(p);
+        const CtlTable3<float> c32 = make_table3<float>(p);
+        double last = 0.0;
+        int it = 0;
+        for (; it < 8; ++it) {
+            check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
+            k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64);
+            ++S.kernel_launches;
+            check_cuda(cudaGetLastError(), "polish3");
+            std::swap(pa, pb);
+            float hm = 0.f;
+            check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(float), cudaMemcpyDeviceToHost, st), "polish res");
+            check_cuda(cudaStreamSynchronize(st), "polish sync");
+            last = hm;
+            if (hm < d.tol) {
+                ++it;
+                break;
+            }
+        }
+        S.sweeps_polish = it;
+        S.residual_polish = last;
+        k_finalize<<<grid_for3(N), 256, 0, st>>>(N, pa, p.u_out);
+        ++S.kernel_launches;
+    }
+    unsigned long long *unreach = alloc3<unsigned long long>(p, 1);
+    check_cuda(cudaMemsetAsync(unreach, 0, sizeof(unsigned long long), st), "memset");
+    k_final_labels<<<grid_for3(N), 256, 0, st>>>(N, code0, code, p.patchy ? nullptr : p.label_out, unreach);
+    ++S.kernel_launches;
+    Ev3 f2(st);
+    unsigned long long hu = 0, hun = 0;
+    check_cuda(cudaMemcpyAsync(&hu, updates, sizeof(hu), cudaMemcpyDeviceToHost, st), "updates");
+    check_cuda(cudaMemcpyAsync(&hun, unreach, sizeof(hun), cudaMemcpyDeviceToHost, st), "unreachable");
+    check_cuda(cudaStreamSynchronize(st), "final sync");
+    S.unreachable = (int64_t)hun;
+    S.node_updates = (int64_t)hu;
+    S.node_control_updates = (int64_t)hu * d.n_controls;
+    S.n_patches = p.patchy ? R : 1;
+    S.ms_setup = ms3(e0, e1);
+    S.ms_fine = ms3(f0, f1);
+    S.ms_reach = ms3(f0, fr);
+    S.ms_polish = ms3(f1, f2);
+    S.ms_total = ms3(e0, f2);
+    return status;
+}
+
+// ---------------------------------------------------------- instantiation --
+template __global__ void k_init3d<float>(int64_t, const int8_t *, const double *, float, float *, float *);
+template __global__ void k_init3d<double>(int64_t, const int8_t *, const double *, double, double *, double *);
+
+}  // namespace hjbp
