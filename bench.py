@@ -42,9 +42,15 @@ WORKLOAD = "patchy2d_sincos_n2049_c65_nc64_R4"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 OPS_PER_UPDATE = 4          # canonical bilinear update: 3 FMA + 1 min per node-control pair
+OPS_PER_UPDATE_3D = 8       # canonical trilinear update: 7 FMA + 1 min
+
+
+FAMILY = "sincos2d"
 
 
 def problem(seed: int):
+    if FAMILY == "sin3d":
+        return W.sin3d(seed, n=N_FINE, n_coarse=N_COARSE, n_c=98, n_targets=8, radius=0.05, tol=1e-6)
     return W.sincos2d(seed, n=N_FINE, n_coarse=N_COARSE, n_c=64, n_targets=4, radius=0.05, tol=1e-6)
 
 
@@ -281,23 +287,24 @@ def run_ours(args, rank, world, dist):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6            # lane-ops/s
     launches = max(1, s0["sweep_kernel_launches"])
-    ops_per_launch = s0["node_control_updates"] * OPS_PER_UPDATE / launches
+    ops_per_launch = s0["node_control_updates"] * (OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D) / launches
     avg_launch_s = s0["ms_sweep_kernel"] / 1e3 / launches
     achieved = ops_per_launch / avg_launch_s if avg_launch_s > 0 else None
     traffic = profile_traffic()
-    roofline = {"bound": "alu", "kernel": "k_value2d<float>", "achieved": achieved / 1e12 if achieved else None,
+    roofline = {"bound": "alu", "kernel": "k_value2d<float>" if p.dim == 2 else "k_value3d<float>", "achieved": achieved / 1e12 if achieved else None,
                 "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
                 "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock); "
-                              f"{OPS_PER_UPDATE} lane-ops per node-control update"}
+                              f"{OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D} lane-ops per node-control update"}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": 64, "n_targets": 4,
+            "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": p.n_controls,
+                       "n_targets": p.n_targets,
                        "tol": 1e-6, "seed": "rank", "precision": "FP32 sweeps, FP64 coarse/feedback/labels/polish",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solves_per_s": world * 1e3 * args.steps / total_ms,
@@ -327,12 +334,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--n", type=int, default=2049, help="fine nodes per side (smaller cases for profiling)")
-    ap.add_argument("--nc", type=int, default=65, help="coarse nodes per side")
+    ap.add_argument("--workload", default="sincos2d", choices=["sincos2d", "sin3d"],
+                    help="sincos2d: 2D patchy workload (default); sin3d: 3D patchy workload")
+    ap.add_argument("--n", type=int, default=0, help="fine nodes per side (default 2049 / 257)")
+    ap.add_argument("--nc", type=int, default=0, help="coarse nodes per side (default 65 / 33)")
     args = ap.parse_args()
-    global N_FINE, N_COARSE, WORKLOAD
-    N_FINE, N_COARSE = args.n, args.nc
-    WORKLOAD = f"patchy2d_sincos_n{N_FINE}_c{N_COARSE}_nc64_R4"
+    global N_FINE, N_COARSE, WORKLOAD, FAMILY
+    FAMILY = args.workload
+    if FAMILY == "sin3d":
+        N_FINE, N_COARSE = args.n or 257, args.nc or 33
+        WORKLOAD = f"patchy3d_sin_n{N_FINE}_c{N_COARSE}_nc98_R8"
+    else:
+        N_FINE, N_COARSE = args.n or 2049, args.nc or 65
+        WORKLOAD = f"patchy2d_sincos_n{N_FINE}_c{N_COARSE}_nc64_R4"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
