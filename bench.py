@@ -327,6 +327,92 @@ def run_ours(args, rank, world, dist):
         print(json.dumps(out))
 
 
+def run_batched(args):
+    """Batched family (512 seeded 2D problems of uneven size): throughput of
+    hjbp_batch_solve against the same plans solved one at a time."""
+    import torch
+
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as P
+
+    torch.cuda.set_device(0)
+    probs = W.batched(seed=0, count=args.count)
+    plans = [P.Plan(p, stream=0) for p in probs]
+    nodes = sum(p.n_nodes for p in probs)
+    for pl in plans[: min(8, len(plans))]:
+        pl.solve()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for pl in plans:
+        pl.solve()
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t
+    ncu_seq = sum(pl.stats()["node_control_updates"] for pl in plans)
+    t = time.perf_counter()
+    st = P.hjbp_batch_solve([pl.handle for pl in plans], workers=args.workers)
+    torch.cuda.synchronize()
+    bat = time.perf_counter() - t
+    ncu_bat = sum(pl.stats()["node_control_updates"] for pl in plans)
+    assert all(s == 0 for s in st), st
+    out = {"metric": "solves/s, batched vs one at a time", "workload": f"batched2d_fourier_x{len(probs)}",
+           "value": len(probs) / bat, "unit": "solves/s", "one_at_a_time_solves_per_s": len(probs) / seq,
+           "speedup": seq / bat, "batched_s": bat, "one_at_a_time_s": seq, "workers": args.workers,
+           "total_nodes": nodes, "node_control_updates_per_s_batched": ncu_bat / bat,
+           "node_control_updates_per_s_one_at_a_time": ncu_seq / seq, "data": "synthetic", "dtype": "f32"}
+    for pl in plans:
+        pl.close()
+    print(json.dumps(out))
+
+
+def run_serving(args):
+    """Served family: Poisson arrivals (mean 200/s), 80 % 2D / 20 % 3D, replayed
+    in real time against one server; latency from submit to completion."""
+    import torch
+
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as P
+
+    torch.cuda.set_device(0)
+    stream = W.serving_stream(seed=0, count=args.count, rate=args.rate)
+    descs = [P.desc_from_problem(p) for _, p in stream]
+    # warm-up: one small 2D and one small 3D solve
+    for p in (W.fourier2d(np.random.default_rng(9), 129, 32, 2), W.sin3d(0, n=33, n_coarse=17, n_targets=2)):
+        with P.Plan(p, stream=0) as pl:
+            pl.solve()
+    srv = P.hjbp_server_create(budget_bytes=int(args.budget_gb * (1 << 30)), workers=args.workers)
+    lat, pending, done = [], {}, 0
+    t0 = time.perf_counter()
+    i = 0
+    with Clocks() as clk:
+        while done < len(stream):
+            now = time.perf_counter() - t0
+            while i < len(stream) and stream[i][0] <= now:
+                pending[P.hjbp_server_submit(srv, descs[i][0])] = i
+                i += 1
+            for tk in list(pending):
+                st, h, l = P.hjbp_server_poll(srv, tk)
+                if h:
+                    assert st == 0, st
+                    lat.append(l)
+                    P.hjbp_destroy(h)
+                    del pending[tk]
+                    done += 1
+            time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    P.hjbp_server_destroy(srv)
+    lat = np.array(lat)
+    out = {"metric": "p50/p99 latency and solves/s, served", "workload": f"serving_poisson{args.rate:g}_x{len(stream)}",
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "mean_ms": 1e3 * float(lat.mean()), "value": len(stream) / wall, "unit": "solves/s",
+           "offered_rate": args.rate, "arrival_span_s": stream[-1][0], "wall_s": wall, "workers": args.workers,
+           "budget_gb": args.budget_gb, "clocks": clk.summary(0), "data": "synthetic"}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,13 +420,24 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--workload", default="sincos2d", choices=["sincos2d", "sin3d"],
-                    help="sincos2d: 2D patchy workload (default); sin3d: 3D patchy workload")
+    ap.add_argument("--workload", default="sincos2d", choices=["sincos2d", "sin3d", "batched", "serving"],
+                    help="sincos2d: 2D patchy workload (default); sin3d: 3D patchy workload; batched: 512 "
+                         "problems, batch vs one at a time; serving: Poisson request stream, p50/p99")
+    ap.add_argument("--count", type=int, default=0, help="problems (batched: 512) / requests (serving: 2000)")
+    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--n", type=int, default=0, help="fine nodes per side (default 2049 / 257)")
     ap.add_argument("--nc", type=int, default=0, help="coarse nodes per side (default 65 / 33)")
     args = ap.parse_args()
     global N_FINE, N_COARSE, WORKLOAD, FAMILY
     FAMILY = args.workload
+    if FAMILY == "batched":
+        args.count = args.count or 512
+        return run_batched(args)
+    if FAMILY == "serving":
+        args.count = args.count or 2000
+        return run_serving(args)
     if FAMILY == "sin3d":
         N_FINE, N_COARSE = args.n or 257, args.nc or 33
         WORKLOAD = f"patchy3d_sin_n{N_FINE}_c{N_COARSE}_nc98_R8"

@@ -185,6 +185,34 @@ void hjbp_destroy(hjbp_plan *plan);
 
 const char *hjbp_last_error(void);
 
+/* ---- batched and served solves (not in the paper: throughput patterns) ----
+ *
+ * hjbp_batch_solve: solve `count` plans at once.  `workers` host threads (<= 0
+ * selects 8), each with its own non-blocking CUDA stream, take plans in order
+ * and run their solves concurrently so that small problems overlap on the GPU.
+ * Each plan's results are read as usual afterwards.  statuses (optional,
+ * count entries) receives each plan's status; the return value is the worst
+ * one (an error, else ENOCONV, else OK).                                     */
+hjbp_status hjbp_batch_solve(hjbp_plan *const *plans, int count, int workers, hjbp_status *statuses);
+
+/* Serving.  A server owns a pool of `workers` threads (<= 0 selects 8) with
+ * their own streams and a device-memory budget (0 selects half of the free
+ * memory).  submit validates and copies a problem, estimates the device bytes
+ * its solve needs, and queues it; EBUSY if it can never fit the budget.  A
+ * queued request starts as soon as a worker is idle and its bytes fit next to
+ * the requests in flight (continuous batching).  poll returns OK with
+ * *done = NULL while the request is queued or running; once finished it hands
+ * over the plan (values and labels resident on the device; the caller
+ * destroys it), returns that solve's status and the latency from submit to
+ * completion in seconds.  destroy waits for running requests, drops queued
+ * ones and destroys plans nobody collected.                                  */
+typedef struct hjbp_server hjbp_server;
+hjbp_status hjbp_server_create(size_t device_budget_bytes, int workers, hjbp_server **out);
+hjbp_status hjbp_server_submit(hjbp_server *server, const hjbp_problem_desc *desc, uint64_t *ticket);
+hjbp_status hjbp_server_poll(hjbp_server *server, uint64_t ticket, hjbp_plan **done, double *latency_s);
+hjbp_status hjbp_server_stats(hjbp_server *server, int *queued, int *running, size_t *bytes_in_use);
+void hjbp_server_destroy(hjbp_server *server);
+
 /* Plain global 2D solve in FP64 that allocates nothing (the paper has no
  * counterpart; it serves callers that cannot allocate at solve time, e.g.
  * code running while a stream is captured into a CUDA graph, or real-time

@@ -18,6 +18,7 @@ from ._binding import (  # noqa: F401
     Plan,
     Stats,
     desc_from_problem,
+    hjbp_batch_solve,
     hjbp_create,
     hjbp_destroy,
     hjbp_get_device_views,
@@ -30,6 +31,11 @@ from ._binding import (  # noqa: F401
     hjbp_solve,
     hjbp_solve_global2d_noalloc,
     HJBP_NOALLOC_MAX_NODES,
+    hjbp_server_create,
+    hjbp_server_destroy,
+    hjbp_server_poll,
+    hjbp_server_stats,
+    hjbp_server_submit,
     hjbp_version,
     library,
     library_path,

@@ -138,6 +138,18 @@ def library():
         lib.hjbp_last_error.restype = C.c_char_p
         lib.hjbp_solve_global2d_noalloc.argtypes = [P(Desc), vp, vp, vp]
         lib.hjbp_solve_global2d_noalloc.restype = C.c_int
+        lib.hjbp_batch_solve.argtypes = [P(vp), C.c_int, C.c_int, P(C.c_int)]
+        lib.hjbp_batch_solve.restype = C.c_int
+        lib.hjbp_server_create.argtypes = [C.c_size_t, C.c_int, P(vp)]
+        lib.hjbp_server_create.restype = C.c_int
+        lib.hjbp_server_submit.argtypes = [vp, P(Desc), P(C.c_uint64)]
+        lib.hjbp_server_submit.restype = C.c_int
+        lib.hjbp_server_poll.argtypes = [vp, C.c_uint64, P(vp), P(C.c_double)]
+        lib.hjbp_server_poll.restype = C.c_int
+        lib.hjbp_server_stats.argtypes = [vp, P(C.c_int), P(C.c_int), P(C.c_size_t)]
+        lib.hjbp_server_stats.restype = C.c_int
+        lib.hjbp_server_destroy.argtypes = [vp]
+        lib.hjbp_server_destroy.restype = None
         lib.hjbp_version.argtypes = []
         lib.hjbp_version.restype = C.c_int
         _lib = lib
@@ -207,6 +219,49 @@ def hjbp_get_sizes(plan: int):
     n, nc = C.c_int64(), C.c_int64()
     _check(library().hjbp_get_sizes(C.c_void_p(plan), C.byref(n), C.byref(nc)))
     return n.value, nc.value
+
+
+def hjbp_batch_solve(plans, workers: int = 0):
+    """Solve plan handles concurrently; returns the per-plan statuses."""
+    n = len(plans)
+    arr = (C.c_void_p * n)(*plans)
+    st = (C.c_int * n)()
+    rc = library().hjbp_batch_solve(arr, n, int(workers), st)
+    if rc not in (HJBP_OK, HJBP_ENOCONV):
+        _check(rc)
+    return list(st)
+
+
+def hjbp_server_create(budget_bytes: int = 0, workers: int = 0) -> int:
+    s = C.c_void_p()
+    _check(library().hjbp_server_create(C.c_size_t(budget_bytes), int(workers), C.byref(s)))
+    return s.value
+
+
+def hjbp_server_submit(server: int, desc: Desc) -> int:
+    t = C.c_uint64()
+    _check(library().hjbp_server_submit(C.c_void_p(server), C.byref(desc), C.byref(t)))
+    return t.value
+
+
+def hjbp_server_poll(server: int, ticket: int):
+    """(status, plan handle or None, latency seconds)."""
+    plan = C.c_void_p()
+    lat = C.c_double()
+    st = library().hjbp_server_poll(C.c_void_p(server), C.c_uint64(ticket), C.byref(plan), C.byref(lat))
+    if st not in (HJBP_OK, HJBP_ENOCONV):
+        _check(st)
+    return st, plan.value, lat.value
+
+
+def hjbp_server_stats(server: int):
+    q, r, b = C.c_int(), C.c_int(), C.c_size_t()
+    _check(library().hjbp_server_stats(C.c_void_p(server), C.byref(q), C.byref(r), C.byref(b)))
+    return q.value, r.value, b.value
+
+
+def hjbp_server_destroy(server: int) -> None:
+    library().hjbp_server_destroy(C.c_void_p(server))
 
 
 HJBP_NOALLOC_MAX_NODES = 1 << 20
@@ -305,6 +360,17 @@ class Plan:
         self.handle = hjbp_create(self._desc, stream, self._alloc)
         self.N, self.Nc = hjbp_get_sizes(self.handle)
         self.status = None
+
+    @classmethod
+    def adopt(cls, problem, handle: int):
+        """Wrap a plan handle produced by the library (e.g. a served request)."""
+        self = cls.__new__(cls)
+        self.problem = problem
+        self._desc, self._keep, self._alloc = None, None, None
+        self.handle = handle
+        self.N, self.Nc = hjbp_get_sizes(handle)
+        self.status = None
+        return self
 
     def solve(self) -> int:
         self.status = hjbp_solve(self.handle)

@@ -1,0 +1,294 @@
+// serve.cu -- batched and served solves (host orchestration, C ABI).
+//
+// hjbp_batch_solve runs many plans at once: a pool of worker threads, each
+// with its own non-blocking CUDA stream, takes plans from a shared counter and
+// runs their solves concurrently, so that problems too small to fill the GPU
+// (the batched family has sides of 65..513 nodes) overlap on the device.
+//
+// The server keeps requests in a queue, admits them while the device memory
+// they need fits in a budget (continuous batching: a request starts as soon as
+// a worker and enough memory are free, while others are still running), runs
+// them on the same kind of worker pool, and keeps each finished plan (values
+// and labels resident on the device) until the caller collects it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hjbp_device.cuh"
+#include "plan.h"
+
+namespace hjbp {
+void set_last_error_static(const char *msg);
+}
+
+namespace {
+
+hjbp_status worse(hjbp_status a, hjbp_status b) {
+    auto rank = [](hjbp_status s) { return s == HJBP_OK ? 0 : (s == HJBP_ENOCONV ? 1 : 2); };
+    return rank(b) > rank(a) ? b : a;
+}
+
+// Solve one plan on `stream` (the plan's own stream is restored afterwards).
+hjbp_status solve_on(hjbp_plan *p, cudaStream_t stream) {
+    cudaStream_t own = p->stream;
+    // work queued on the plan's stream (creation) must be done before another stream uses its memory
+    cudaStreamSynchronize(own);
+    p->stream = stream;
+    const hjbp_status s = hjbp_solve(p);
+    cudaStreamSynchronize(stream);
+    p->stream = own;
+    return s;
+}
+
+}  // namespace
+
+extern "C" hjbp_status hjbp_batch_solve(hjbp_plan *const *plans, int count, int workers, hjbp_status *statuses) {
+    if (!plans || count < 0) {
+        hjbp::set_last_error_static("plans is NULL or count negative");
+        return HJBP_EINVAL;
+    }
+    for (int i = 0; i < count; ++i)
+        if (!plans[i]) {
+            hjbp::set_last_error_static("NULL plan in the batch");
+            return HJBP_EINVAL;
+        }
+    if (workers <= 0) workers = 8;
+    workers = std::max(1, std::min(workers, count));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> next(0);
+    std::vector<hjbp_status> st(count, HJBP_OK);
+    std::vector<std::thread> pool;
+    std::atomic<int> stream_fail(0);
+    for (int w = 0; w < workers; ++w) {
+        pool.emplace_back([&, w]() {
+            cudaSetDevice(dev);
+            cudaStream_t s = nullptr;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                stream_fail = 1;
+                return;
+            }
+            for (;;) {
+                const int i = next.fetch_add(1);
+                if (i >= count) break;
+                st[i] = solve_on(plans[i], s);
+            }
+            cudaStreamDestroy(s);
+        });
+    }
+    for (auto &t : pool) t.join();
+    hjbp_status all = HJBP_OK;
+    for (int i = 0; i < count; ++i) {
+        if (statuses) statuses[i] = st[i];
+        all = worse(all, st[i]);
+    }
+    if (stream_fail && next.load() < count) {
+        hjbp::set_last_error_static("could not create worker streams");
+        return HJBP_ECUDA;
+    }
+    return all;
+}
+
+// ------------------------------------------------------------------ server --
+
+struct hjbp_server {
+    size_t budget = 0;
+    size_t in_use = 0;
+    int workers = 0;
+    int device = 0;
+    bool stopping = false;
+    uint64_t next_ticket = 1;
+    struct Req {
+        uint64_t ticket;
+        hjbp_plan *plan;
+        size_t bytes;
+        hjbp_status status;
+        double t_submit, t_start, t_done;
+    };
+    std::deque<uint64_t> queue;               // admitted order (FIFO)
+    std::map<uint64_t, Req> reqs;             // every live request
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<std::thread> pool;
+};
+
+namespace {
+
+double now_s() {
+    using clk = std::chrono::steady_clock;
+    return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+void worker_loop(hjbp_server *S) {
+    cudaSetDevice(S->device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (;;) {
+        uint64_t t = 0;
+        hjbp_plan *plan = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // first queued request whose memory fits now (FIFO among those that fit)
+            for (;;) {
+                if (S->stopping) {
+                    if (s) cudaStreamDestroy(s);
+                    return;
+                }
+                for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+                    auto &r = S->reqs[*it];
+                    if (S->in_use + r.bytes <= S->budget || S->in_use == 0) {
+                        t = *it;
+                        plan = r.plan;
+                        S->in_use += r.bytes;
+                        r.t_start = now_s();
+                        S->queue.erase(it);
+                        break;
+                    }
+                }
+                if (plan) break;
+                S->cv.wait(lk);
+            }
+        }
+        const hjbp_status st = solve_on(plan, s);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            auto &r = S->reqs[t];
+            r.status = st;
+            r.t_done = now_s();
+        }
+        S->cv.notify_all();
+    }
+}
+
+// Device bytes a plan needs while solving (outputs plus per-solve scratch).
+size_t footprint(const hjbp_problem_desc *d) {
+    int64_t N = 1, Nc = 0;
+    for (int a = 0; a < d->dim; ++a) N *= d->n[a];
+    if (d->n_coarse[0]) {
+        Nc = 1;
+        for (int a = 0; a < d->dim; ++a) Nc *= d->n_coarse[a];
+    }
+    const int rg = d->n_targets >= 4 ? 4 : d->n_targets;
+    // outputs + codes/h + value buffers + colour planes (FP32 x3, FP64 x2 per group) + phi (R planes)
+    size_t b = (size_t)N * (8 + 1 + 4 + 8 + 8 + 1 + 1 + 1 + 4 * 3 + 16);
+    if (Nc) b += (size_t)N * (8 + 1 + (size_t)rg * (4 * 3 + 8) + 8 * (size_t)d->n_targets) + (size_t)Nc * 40;
+    return b + (size_t(8) << 20);
+}
+
+}  // namespace
+
+extern "C" hjbp_status hjbp_server_create(size_t device_budget_bytes, int workers, hjbp_server **out) {
+    if (!out) {
+        hjbp::set_last_error_static("out is NULL");
+        return HJBP_EINVAL;
+    }
+    *out = nullptr;
+    hjbp_server *S = new (std::nothrow) hjbp_server();
+    if (!S) {
+        hjbp::set_last_error_static("host allocation failed");
+        return HJBP_ENOMEM;
+    }
+    if (device_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        device_budget_bytes = fr / 2;
+    }
+    S->budget = device_budget_bytes;
+    S->workers = workers > 0 ? workers : 8;
+    cudaGetDevice(&S->device);
+    for (int w = 0; w < S->workers; ++w) S->pool.emplace_back(worker_loop, S);
+    *out = S;
+    return HJBP_OK;
+}
+
+extern "C" hjbp_status hjbp_server_submit(hjbp_server *S, const hjbp_problem_desc *desc, uint64_t *ticket) {
+    if (!S || !desc || !ticket) {
+        hjbp::set_last_error_static("NULL argument");
+        return HJBP_EINVAL;
+    }
+    const size_t bytes = footprint(desc);
+    if (bytes > S->budget) {
+        hjbp::set_last_error_static("request needs more device memory than the server budget");
+        return HJBP_EBUSY;
+    }
+    hjbp_plan *plan = nullptr;
+    // plans are created on the legacy stream and synchronised; workers run them on their own streams
+    const hjbp_status st = hjbp_create(desc, nullptr, nullptr, &plan);
+    if (st != HJBP_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        const uint64_t t = S->next_ticket++;
+        S->reqs[t] = hjbp_server::Req{t, plan, bytes, HJBP_EBUSY, now_s(), 0.0, 0.0};
+        S->queue.push_back(t);
+        *ticket = t;
+    }
+    S->cv.notify_all();
+    return HJBP_OK;
+}
+
+extern "C" hjbp_status hjbp_server_poll(hjbp_server *S, uint64_t ticket, hjbp_plan **done, double *latency_s) {
+    if (!S || !done) {
+        hjbp::set_last_error_static("NULL argument");
+        return HJBP_EINVAL;
+    }
+    *done = nullptr;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) {
+        hjbp::set_last_error_static("unknown ticket");
+        return HJBP_EINVAL;
+    }
+    auto &r = it->second;
+    if (r.t_done == 0.0) return HJBP_OK;  // still queued or running
+    *done = r.plan;
+    if (latency_s) *latency_s = r.t_done - r.t_submit;
+    const hjbp_status st = r.status;
+    S->in_use -= r.bytes;
+    S->reqs.erase(it);
+    S->cv.notify_all();
+    return st;
+}
+
+extern "C" hjbp_status hjbp_server_stats(hjbp_server *S, int *queued, int *running, size_t *bytes_in_use) {
+    if (!S) {
+        hjbp::set_last_error_static("server is NULL");
+        return HJBP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    int run = 0;
+    for (auto &kv : S->reqs)
+        if (kv.second.t_start != 0.0 && kv.second.t_done == 0.0) ++run;
+    if (queued) *queued = (int)S->queue.size();
+    if (running) *running = run;
+    if (bytes_in_use) *bytes_in_use = S->in_use;
+    return HJBP_OK;
+}
+
+extern "C" void hjbp_server_destroy(hjbp_server *S) {
+    if (!S) return;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        // let running requests finish; queued ones are dropped
+        S->queue.clear();
+        S->cv.wait(lk, [&] {
+            for (auto &kv : S->reqs)
+                if (kv.second.t_start != 0.0 && kv.second.t_done == 0.0) return false;
+            return true;
+        });
+        S->stopping = true;
+    }
+    S->cv.notify_all();
+    for (auto &t : S->pool) t.join();
+    for (auto &kv : S->reqs) hjbp_destroy(kv.second.plan);
+    delete S;
+}

@@ -1,0 +1,46 @@
+"""Host-side checks of the batched / served API that need no GPU: admission
+refuses requests that can never fit the memory budget (EBUSY), malformed
+requests are rejected at submit (EINVAL), and a server with nothing running
+shuts down cleanly."""
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as pkg
+
+    return pkg
+
+
+def test_admission_refuses_oversized_request(P):
+    srv = P.hjbp_server_create(budget_bytes=1 << 20, workers=2)
+    try:
+        d, keep = P.desc_from_problem(W.sincos2d(0, n=1025, n_coarse=33))
+        with pytest.raises(P.HjbpError) as ei:
+            P.hjbp_server_submit(srv, d)
+        assert ei.value.status == 6          # EBUSY
+        assert P.hjbp_server_stats(srv) == (0, 0, 0)
+    finally:
+        P.hjbp_server_destroy(srv)
+
+
+def test_malformed_request_is_rejected(P):
+    srv = P.hjbp_server_create(budget_bytes=1 << 30, workers=1)
+    try:
+        d, keep = P.desc_from_problem(W.sincos2d(0, n=65, n_coarse=17).with_(tol=-1.0))
+        with pytest.raises(P.HjbpError) as ei:
+            P.hjbp_server_submit(srv, d)
+        assert ei.value.status == 1          # EINVAL
+    finally:
+        P.hjbp_server_destroy(srv)
+
+
+def test_batch_rejects_null_plan(P):
+    with pytest.raises(P.HjbpError) as ei:
+        P.hjbp_batch_solve([0, 0])
+    assert ei.value.status == 1

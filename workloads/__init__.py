@@ -143,8 +143,9 @@ def place_targets(rng: np.random.Generator, dim: int, count: int, lo: float, hi:
 
 
 def coarse_side(n: int) -> int:
-    """Coarse side used by the batched and served families."""
-    return max(33, int(math.ceil((n - 1) / 8)) + 1)
+    """Coarse side used by the batched and served families: 33, or (n-1)/8 + 1
+    for large grids, never more than the fine side itself."""
+    return min(n, max(33, int(math.ceil((n - 1) / 8)) + 1))
 
 
 # ---------------------------------------------------------------------------
