@@ -151,6 +151,25 @@ def oracle_sample(p, rows: int):
     return int(upd.sum()) * p.n_controls, dt
 
 
+def aggregate(dist, local_ms: float, local_units: float, device: str):
+    """Whole-job numbers of a weak-scaling run: the slowest rank's time (max)
+    and the units all ranks processed (sum).  One rank: the local numbers."""
+    if dist is None:
+        return local_ms, local_units
+    import torch
+
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank solves its own seeded instance of the workload (replicas)."""
+    return rank
+
+
 # --------------------------------------------------------- reference arm --
 
 def run_reference(args, rank, world):
@@ -193,7 +212,7 @@ def run_ours(args, rank, world, dist):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream().cuda_stream
-    p = problem(rank)
+    p = problem(rank_seed(rank))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # CPU baseline first (rank 0 at N = 1 only), before the GPU work starts
@@ -233,17 +252,8 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = float(sum(ms_steps))
-    ncu_local = sum(s["node_control_updates"] for s in stats)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([float(ncu_local)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        ncu_all = float(c.item())
-    else:
-        ncu_all = float(ncu_local)
+    total_ms, ncu_all = aggregate(dist, float(sum(ms_steps)), float(sum(s["node_control_updates"] for s in stats)),
+                                  "cuda")
     value = ncu_all / (total_ms / 1e3)
     s0 = stats[-1]
 

@@ -95,7 +95,8 @@ typedef struct {
     int flags;          /* HJBP_FLAG_* bits */
     int tune[4];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
                            launch of the value sweep (2), [1] of the colour transport (3),
-                           [2] passes per launch of the reachability sweep (1), [3] reserved */
+                           [2] passes per launch of the reachability sweep (1), [3] warps
+                           per 32x32 tile of the 2D value sweep (1; 1, 2 or 4) */
 } hjbp_problem_desc;
 
 /* flags: HJBP_FLAG_TIME_SWEEPS records a CUDA event pair around every launch

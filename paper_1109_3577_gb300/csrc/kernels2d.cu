@@ -133,10 +133,10 @@ template <typename T> struct TileSmem {
     int8_t c[kTile + 2][kTile + 4];
 };
 
-template <typename T>
+template <typename T, class S>
 __device__ __forceinline__ void load_tile(const Grid2 &g, const TileSched &s, const int8_t *__restrict__ code,
                                           const T *__restrict__ b0, const T *__restrict__ b1, int x0, int y0,
-                                          TileSmem<T> &sm) {
+                                          S &sm) {
     const int lane = threadIdx.x;
     for (int r = 0; r < kTile + 2; ++r) {
         const int y = y0 - 1 + r;
@@ -159,9 +159,9 @@ __device__ __forceinline__ void load_tile(const Grid2 &g, const TileSched &s, co
 
 // Write the tile's interior to the buffer that is not current, return the
 // warp's max |new - old| (0 where both are +inf).
-template <typename T>
+template <typename T, class S>
 __device__ __forceinline__ float store_tile(const Grid2 &g, const TileSched &s, int t, T *__restrict__ b0,
-                                            T *__restrict__ b1, int x0, int y0, const TileSmem<T> &sm) {
+                                            T *__restrict__ b1, int x0, int y0, const S &sm) {
     const int lane = threadIdx.x;
     const int cur = s.latest[t];
     T *dst = cur ? b0 : b1;
@@ -263,10 +263,107 @@ __device__ __forceinline__ T sl_update(const TileSmem<T> &sm, int c, int r, int8
     return b01 < b23 ? b01 : b23;
 }
 
+// Tile image for the value sweep: values and codes with the halo, plus h and
+// a 9-bit usability mask per interior node (bit 3 dy + dx set when the
+// neighbour (dx-1, dy-1) belongs to the node's patch or its target part;
+// bit 15 set when the node itself is free).  Codes do not change during a
+// solve, so the masks are formed once per launch.
+template <typename T> struct TileSmemV {
+    T u[kTile + 2][kTile + 3];
+    int8_t c[kTile + 2][kTile + 4];
+    T h[kTile][kTile + 1];
+    uint16_t mk[kTile][kTile + 2];
+};
+
+// The update of sl_update with the neighbourhood masked by a precomputed
+// mask; NCLS > 0 fully unrolls the symmetric form for a table with exactly
+// NCLS classes (every class then sits in the constant bank as immediates).
+template <typename T, int NCLS, class S>
+__device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct) {
+    T nb[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+            nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+    T b0 = Num<T>::big(), b1 = Num<T>::big(), b2 = Num<T>::big(), b3 = Num<T>::big();
+    if (NCLS > 0 || ct.d4) {
+        T E[4], G[4], A[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const T a10 = nb[1][sx], a01 = nb[sy][1];
+            E[q] = a10 + a01;
+            G[q] = fabs(a10 - a01);
+            A[q] = nb[sy][sx];
+        }
+        const int ncls = NCLS > 0 ? NCLS : ct.ncls;
+#pragma unroll
+        for (int k = 0; k < (NCLS > 0 ? NCLS : 1); ++k) {
+            if (NCLS == 0) break;
+            const T kh = ct.cls_kap[k] * hh;
+            const T s = ct.cls_s[k], t = -ct.cls_t[k], w = ct.cls_kw11[k];
+            const T v0 = fma(t, G[0], fma(s, E[0], fma(w, A[0], kh)));
+            const T v1 = fma(t, G[1], fma(s, E[1], fma(w, A[1], kh)));
+            const T v2 = fma(t, G[2], fma(s, E[2], fma(w, A[2], kh)));
+            const T v3 = fma(t, G[3], fma(s, E[3], fma(w, A[3], kh)));
+            b0 = v0 < b0 ? v0 : b0;
+            b1 = v1 < b1 ? v1 : b1;
+            b2 = v2 < b2 ? v2 : b2;
+            b3 = v3 < b3 ? v3 : b3;
+        }
+        if (NCLS == 0) {
+            for (int k = 0; k < ncls; ++k) {
+                const T kh = ct.cls_kap[k] * hh;
+                const T s = ct.cls_s[k], t = -ct.cls_t[k], w = ct.cls_kw11[k];
+                const T v0 = fma(t, G[0], fma(s, E[0], fma(w, A[0], kh)));
+                const T v1 = fma(t, G[1], fma(s, E[1], fma(w, A[1], kh)));
+                const T v2 = fma(t, G[2], fma(s, E[2], fma(w, A[2], kh)));
+                const T v3 = fma(t, G[3], fma(s, E[3], fma(w, A[3], kh)));
+                b0 = v0 < b0 ? v0 : b0;
+                b1 = v1 < b1 ? v1 : b1;
+                b2 = v2 < b2 ? v2 : b2;
+                b3 = v3 < b3 ? v3 : b3;
+            }
+        }
+        if (ct.axis) {
+            const T ax = fmin(fmin(nb[1][0], nb[1][2]), fmin(nb[0][1], nb[2][1])) + hh;
+            b0 = ax < b0 ? ax : b0;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
+            int mm = ct.qbeg[q];
+            const int me = ct.qbeg[q + 1];
+            for (; mm + 3 < me; mm += 4) {
+                const T v0 = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
+                const T v1 = fma(ct.kw11[mm + 1], a11,
+                                 fma(ct.kw01[mm + 1], a01, fma(ct.kw10[mm + 1], a10, ct.kap[mm + 1] * hh)));
+                const T v2 = fma(ct.kw11[mm + 2], a11,
+                                 fma(ct.kw01[mm + 2], a01, fma(ct.kw10[mm + 2], a10, ct.kap[mm + 2] * hh)));
+                const T v3 = fma(ct.kw11[mm + 3], a11,
+                                 fma(ct.kw01[mm + 3], a01, fma(ct.kw10[mm + 3], a10, ct.kap[mm + 3] * hh)));
+                b0 = v0 < b0 ? v0 : b0;
+                b1 = v1 < b1 ? v1 : b1;
+                b2 = v2 < b2 ? v2 : b2;
+                b3 = v3 < b3 ? v3 : b3;
+            }
+            for (; mm < me; ++mm) {
+                const T v = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
+                b0 = v < b0 ? v : b0;
+            }
+        }
+    }
+    const T b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
+    return b01 < b23 ? b01 : b23;
+}
+
 // One launch of the value iteration over the active tiles.  kClamp: monotone
 // update u <- min(u, F(u)) from the start value M (bulk); without it the
-// plain update u <- F(u) (polishing from a state near the fixed point).
-template <typename T, bool kClamp>
+// plain update u <- F(u).
+template <typename T, bool kClamp, int NCLS>
 __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restrict__ code,
                                                 const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                 TileSched s, int par, int rounds, unsigned long long *updates,
@@ -275,26 +372,44 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
-    __shared__ TileSmem<T> sm;
-    load_tile(g, s, code, b0, b1, x0, y0, sm);
+    __shared__ TileSmemV<T> sm;
+    load_tile<T>(g, s, code, b0, b1, x0, y0, sm);
     const int lane = threadIdx.x;
     int nfree = 0;
-    for (int r = 1; r <= kTile; ++r) {
-        const int8_t cd = sm.c[r][1 + lane];
-        nfree += (cd >= 0 && cd < kTargetBase);
+    {
+        const int c = 1 + lane, x = x0 + lane;
+        for (int r = 1; r <= kTile; ++r) {
+            const int8_t cd = sm.c[r][c];
+            unsigned m = 0;
+            if (cd >= 0 && cd < kTargetBase) {
+                const int8_t tg = (int8_t)(cd + kTargetBase);
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
+                        m |= (unsigned)(q == cd || q == tg) << (3 * dy + dx);
+                    }
+                m |= 0x8000u;
+                ++nfree;
+            }
+            sm.mk[r - 1][lane] = (uint16_t)m;
+            const int y = y0 - 1 + r;
+            sm.h[r - 1][lane] = (m && x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
+        }
     }
+    __syncwarp();
     for (int rd = 0; rd < rounds; ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
             for (int st = 0; st < kTile; ++st) {
                 const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
                 const int c = (dir < 2) ? s1 : 1 + lane;
                 const int r = (dir < 2) ? 1 + lane : s1;
-                const int8_t cd = sm.c[r][c];
-                const bool active = cd >= 0 && cd < kTargetBase;
+                const unsigned m = sm.mk[r - 1][c - 1];
+                const bool active = (m & 0x8000u) != 0;
                 T nw = sm.u[r][c];
                 if (active) {
-                    const int64_t i = (int64_t)(y0 - 1 + r) * g.n0 + (x0 - 1 + c);
-                    const T best = sl_update(sm, c, r, cd, h[i], ct);
+                    const T best = sl_update_m<T, NCLS>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
                     if (best < Num<T>::thresh()) nw = kClamp ? (best < nw ? best : nw) : best;
                 }
                 __syncwarp();
@@ -303,12 +418,190 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
             }
         }
     }
-    const float mc = store_tile(g, s, t, b0, b1, x0, y0, sm);
+    const float mc = store_tile<T>(g, s, t, b0, b1, x0, y0, sm);
     const int nf = warp_sum(nfree);
     if (lane == 0) {
         s.chg[par][t] = mc;
         s.processed[t] = 1;
         if (updates) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+    }
+}
+
+// Partial minimum over warp w's share of the controls (W warps per tile).
+// Symmetric form: classes [w ncls / W, (w+1) ncls / W), the last warp also
+// takes the axis directions; generic form: each quadrant's range split in W.
+template <typename T, int W, class S>
+__device__ __forceinline__ T sl_partial(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct, int w) {
+    T nb[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+            nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+    T b0 = Num<T>::big(), b1 = Num<T>::big(), b2 = Num<T>::big(), b3 = Num<T>::big();
+    if (ct.d4) {
+        T E[4], G[4], A[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const T a10 = nb[1][sx], a01 = nb[sy][1];
+            E[q] = a10 + a01;
+            G[q] = fabs(a10 - a01);
+            A[q] = nb[sy][sx];
+        }
+        const int k0 = (w * ct.ncls) / W, k1 = ((w + 1) * ct.ncls) / W;
+        for (int k = k0; k < k1; ++k) {
+            const T kh = ct.cls_kap[k] * hh;
+            const T s = ct.cls_s[k], t = -ct.cls_t[k], wk = ct.cls_kw11[k];
+            const T v0 = fma(t, G[0], fma(s, E[0], fma(wk, A[0], kh)));
+            const T v1 = fma(t, G[1], fma(s, E[1], fma(wk, A[1], kh)));
+            const T v2 = fma(t, G[2], fma(s, E[2], fma(wk, A[2], kh)));
+            const T v3 = fma(t, G[3], fma(s, E[3], fma(wk, A[3], kh)));
+            b0 = v0 < b0 ? v0 : b0;
+            b1 = v1 < b1 ? v1 : b1;
+            b2 = v2 < b2 ? v2 : b2;
+            b3 = v3 < b3 ? v3 : b3;
+        }
+        if (ct.axis && w == W - 1) {
+            const T ax = fmin(fmin(nb[1][0], nb[1][2]), fmin(nb[0][1], nb[2][1])) + hh;
+            b0 = ax < b0 ? ax : b0;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
+            const int qb = ct.qbeg[q], qn = ct.qbeg[q + 1] - qb;
+            int mm = qb + (w * qn) / W;
+            const int me = qb + ((w + 1) * qn) / W;
+            for (; mm + 1 < me; mm += 2) {
+                const T v0 = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
+                const T v1 = fma(ct.kw11[mm + 1], a11,
+                                 fma(ct.kw01[mm + 1], a01, fma(ct.kw10[mm + 1], a10, ct.kap[mm + 1] * hh)));
+                b0 = v0 < b0 ? v0 : b0;
+                b1 = v1 < b1 ? v1 : b1;
+            }
+            if (mm < me) {
+                const T v = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
+                b2 = v < b2 ? v : b2;
+            }
+        }
+    }
+    const T b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
+    return b01 < b23 ? b01 : b23;
+}
+
+template <typename T> struct TileSmemW {
+    T u[kTile + 2][kTile + 3];
+    int8_t c[kTile + 2][kTile + 4];
+    T h[kTile][kTile + 1];
+    uint16_t mk[kTile][kTile + 2];
+    T part[4][kTile];
+    float red[4];
+};
+
+// The value sweep with W warps per tile: in every step each warp evaluates
+// its share of the controls for the same 32 nodes (lane = node), the partial
+// minima meet in shared memory and warp 0 writes the update.  Same result as
+// k_value2d; the step latency (the critical path of the front) is shorter
+// and a tile keeps W warps busy.
+template <typename T, bool kClamp, int W>
+__global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__restrict__ code,
+                                                      const T *__restrict__ h, T *__restrict__ b0,
+                                                      T *__restrict__ b1, TileSched s, int par, int rounds,
+                                                      unsigned long long *updates, const CtlTable2<T> ct) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = s.list[par][blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    __shared__ TileSmemW<T> sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < (kTile + 2) * (kTile + 2); e += 32 * W) {
+        const int r = e / (kTile + 2), c = e % (kTile + 2);
+        const int x = x0 - 1 + c, y = y0 - 1 + r;
+        T v = Num<T>::big();
+        int8_t cd = kHard;
+        if (x < g.n0 && y < g.n1) {
+            const int64_t i = (int64_t)y * g.n0 + x;
+            cd = code[i];
+            const int tt = tile_of(g, x, y);
+            v = (tt >= 0 && s.latest[tt]) ? b1[i] : b0[i];
+        }
+        sm.u[r][c] = v;
+        sm.c[r][c] = cd;
+    }
+    __syncthreads();
+    int nfree = 0;
+    for (int rr = w; rr < kTile; rr += W) {
+        const int r = 1 + rr, c = 1 + lane, x = x0 + lane, y = y0 + rr;
+        const int8_t cd = sm.c[r][c];
+        unsigned m = 0;
+        if (cd >= 0 && cd < kTargetBase) {
+            const int8_t tg = (int8_t)(cd + kTargetBase);
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
+                    m |= (unsigned)(q == cd || q == tg) << (3 * dy + dx);
+                }
+            m |= 0x8000u;
+            ++nfree;
+        }
+        sm.mk[rr][lane] = (uint16_t)m;
+        sm.h[rr][lane] = (m && x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
+    }
+    __syncthreads();
+    for (int rd = 0; rd < rounds; ++rd) {
+        for (int dir = 0; dir < 4; ++dir) {
+            for (int st = 0; st < kTile; ++st) {
+                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+                const int c = (dir < 2) ? s1 : 1 + lane;
+                const int r = (dir < 2) ? 1 + lane : s1;
+                const unsigned m = sm.mk[r - 1][c - 1];
+                const bool active = (m & 0x8000u) != 0;
+                if (active) sm.part[w][lane] = sl_partial<T, W>(sm, c, r, m, sm.h[r - 1][c - 1], ct, w);
+                __syncthreads();
+                if (w == 0 && active) {
+                    T best = sm.part[0][lane];
+#pragma unroll
+                    for (int q = 1; q < W; ++q) best = sm.part[q][lane] < best ? sm.part[q][lane] : best;
+                    const T old = sm.u[r][c];
+                    if (best < Num<T>::thresh()) sm.u[r][c] = kClamp ? (best < old ? best : old) : best;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // store (warp-strided rows) and block max of the change
+    const int cur = s.latest[t];
+    T *dst = cur ? b0 : b1;
+    const T *src = cur ? b1 : b0;
+    float mc = 0.f;
+    const int x = x0 + lane;
+    for (int rr = w; rr < kTile; rr += W) {
+        const int y = y0 + rr;
+        if (y > g.n1 - 2 || x > g.n0 - 2) continue;
+        const int64_t i = (int64_t)y * g.n0 + x;
+        const T v = sm.u[1 + rr][1 + lane];
+        const T o = src[i];
+        dst[i] = v;
+        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
+        const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        mc = fmaxf(mc, d);
+    }
+    mc = warp_max(mc);
+    const int nf = warp_sum(nfree);
+    if (lane == 0) {
+        sm.red[w] = mc;
+        if (updates && nf) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = sm.red[0];
+        for (int q = 1; q < W; ++q) mm = fmaxf(mm, sm.red[q]);
+        s.chg[par][t] = mm;
+        s.processed[t] = 1;
     }
 }
 
@@ -403,6 +696,30 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
         }
     }
     __syncwarp();
+    // per interior node: bits 0..8 usable neighbour (3 dy + dx), bits 9..17
+    // neighbour is the node's own target part, bit 31 node free and unreached
+    __shared__ uint32_t mk[kTile][kTile + 1];
+    {
+        const int c = 1 + lane;
+        for (int r = 1; r <= kTile; ++r) {
+            const int8_t cd = sc[r][c];
+            uint32_t m = 0;
+            if (cd >= 0 && cd < kTargetBase && !sr[r][c]) {
+                const int8_t tg = (int8_t)(cd + kTargetBase);
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int8_t q = sc[r - 1 + dy][c - 1 + dx];
+                        m |= (uint32_t)(q == cd || q == tg) << (3 * dy + dx);
+                        m |= (uint32_t)(q == tg) << (9 + 3 * dy + dx);
+                    }
+                m |= 0x80000000u;
+            }
+            mk[r - 1][lane] = m;
+        }
+    }
+    __syncwarp();
     int flips = 0;
     for (int pass = 0; pass < passes; ++pass)
         for (int dir = 0; dir < 4; ++dir) {
@@ -410,23 +727,23 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                 const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
                 const int c = (dir < 2) ? s1 : 1 + lane;
                 const int r = (dir < 2) ? 1 + lane : s1;
-                const int8_t cd = sc[r][c];
+                const uint32_t m = mk[r - 1][c - 1];
                 bool hit = false;
-                if (cd >= 0 && cd < kTargetBase && !sr[r][c]) {
-                    const int8_t tg = (int8_t)(cd + kTargetBase);
+                if ((m & 0x80000000u) && !sr[r][c]) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
-                        const int8_t q10 = sc[r][c + sx], q01 = sc[r + sy][c], q11 = sc[r + sy][c + sx];
-                        const unsigned us = (unsigned)(q10 == cd || q10 == tg) | ((unsigned)(q01 == cd || q01 == tg) << 1) |
-                                            ((unsigned)(q11 == cd || q11 == tg) << 2);
-                        const unsigned rb = (unsigned)(q10 == tg || (q10 == cd && sr[r][c + sx])) |
-                                            ((unsigned)(q01 == tg || (q01 == cd && sr[r + sy][c])) << 1) |
-                                            ((unsigned)(q11 == tg || (q11 == cd && sr[r + sy][c + sx])) << 2);
+                        const int b10 = 3 * 1 + (1 + sx), b01 = 3 * (1 + sy) + 1, b11 = 3 * (1 + sy) + (1 + sx);
+                        const unsigned us = ((m >> b10) & 1u) | (((m >> b01) & 1u) << 1) | (((m >> b11) & 1u) << 2);
+                        const unsigned tgt =
+                            ((m >> (9 + b10)) & 1u) | (((m >> (9 + b01)) & 1u) << 1) | (((m >> (9 + b11)) & 1u) << 2);
+                        const unsigned rr = (unsigned)(sr[r][c + sx] != 0) | ((unsigned)(sr[r + sy][c] != 0) << 1) |
+                                            ((unsigned)(sr[r + sy][c + sx] != 0) << 2);
+                        const unsigned rb = tgt | (us & rr);
                         const unsigned pres = rt.present[q];
-                        for (unsigned m = 1; m < 8; ++m)
-                            if ((pres >> m) & 1u)
-                                if ((us & m) == m && (rb & m)) hit = true;
+                        for (unsigned k = 1; k < 8; ++k)
+                            if ((pres >> k) & 1u)
+                                if ((us & k) == k && (rb & k)) hit = true;
                     }
                 }
                 __syncwarp();
@@ -588,6 +905,9 @@ template <int RG> struct PhiSmem {
     float src[RG][kTile][kTile + 1];
     int8_t c[kTile + 2][kTile + 4];
     uint8_t a[kTile][kTile + 4];
+    // the control table, so that per-node lookups hit shared memory
+    float kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls], kap[kMaxControls];
+    int8_t sx[kMaxControls], sy[kMaxControls];
 };
 
 // One FP32 launch over the active tiles for RG colours, each node solved for
@@ -608,6 +928,14 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     const int64_t N = (int64_t)g.n0 * g.n1;
     __shared__ PhiSmem<RG> sm;
     const int lane = threadIdx.x;
+    for (int m = lane; m < kMaxControls; m += 32) {
+        sm.kw10[m] = pc->kw10[m];
+        sm.kw01[m] = pc->kw01[m];
+        sm.kw11[m] = pc->kw11[m];
+        sm.kap[m] = pc->kap[m];
+        sm.sx[m] = pc->sx[m];
+        sm.sy[m] = pc->sy[m];
+    }
     for (int r = 0; r < kTile + 2; ++r) {
         const int y = y0 - 1 + r;
         for (int c = lane; c < kTile + 2; c += 32) {
@@ -648,9 +976,9 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
                 const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
                 float nw[RG];
                 if (active) {
-                    const int sx = pc->sx[a], sy = pc->sy[a];
-                    const float w10 = pc->kw10[a], w01 = pc->kw01[a], w11 = pc->kw11[a];
-                    const float kp = pc->kap[a];
+                    const int sx = sm.sx[a], sy = sm.sy[a];
+                    const float w10 = sm.kw10[a], w01 = sm.kw01[a], w11 = sm.kw11[a];
+                    const float kp = sm.kap[a];
 #pragma unroll
                     for (int q = 0; q < RG; ++q) {
                         float v = w10 * sm.u[q][r][c + sx];
@@ -972,10 +1300,16 @@ __global__ void k_finalize(int64_t N, const double *__restrict__ in, double *__r
 
 template __global__ void k_init_values2d<float>(int64_t, const int8_t *, const double *, float, float *, float *);
 template __global__ void k_init_values2d<double>(int64_t, const int8_t *, const double *, double, double *, double *);
-template __global__ void k_value2d<float, true>(Grid2, const int8_t *, const float *, float *, float *, TileSched, int,
-                                                int, unsigned long long *, const CtlTable2<float>);
-template __global__ void k_value2d<double, true>(Grid2, const int8_t *, const double *, double *, double *, TileSched,
-                                                 int, int, unsigned long long *, const CtlTable2<double>);
+template __global__ void k_value2d<float, true, 0>(Grid2, const int8_t *, const float *, float *, float *, TileSched,
+                                                   int, int, unsigned long long *, const CtlTable2<float>);
+template __global__ void k_value2d<float, true, 4>(Grid2, const int8_t *, const float *, float *, float *, TileSched,
+                                                   int, int, unsigned long long *, const CtlTable2<float>);
+template __global__ void k_value2d<float, true, 8>(Grid2, const int8_t *, const float *, float *, float *, TileSched,
+                                                   int, int, unsigned long long *, const CtlTable2<float>);
+template __global__ void k_value2d<double, true, 0>(Grid2, const int8_t *, const double *, double *, double *,
+                                                    TileSched, int, int, unsigned long long *, const CtlTable2<double>);
+template __global__ void k_value2d<double, true, 8>(Grid2, const int8_t *, const double *, double *, double *,
+                                                    TileSched, int, int, unsigned long long *, const CtlTable2<double>);
 template __global__ void k_value_wide2d<double>(Grid2, const int8_t *, const double *, const double *, double *,
                                                 float *, int, const CtlSelf2<double>);
 template __global__ void k_gather2d<float>(Grid2, const uint8_t *, const float *, const float *, float *, double *);
@@ -991,7 +1325,7 @@ void launch_init_values2d_f64(int blocks, cudaStream_t st, int64_t N, const int8
 
 void launch_value2d_f64(int ntiles, cudaStream_t st, Grid2 g, const int8_t *code, const double *h, double *b0,
                         double *b1, TileSched s, int par, int rounds, const CtlTable2<double> &ct) {
-    k_value2d<double, true><<<ntiles, 32, 0, st>>>(g, code, h, b0, b1, s, par, rounds, nullptr, ct);
+    k_value2d<double, true, 0><<<ntiles, 32, 0, st>>>(g, code, h, b0, b1, s, par, rounds, nullptr, ct);
 }
 
 void launch_gather2d_f64(int blocks, cudaStream_t st, Grid2 g, const uint8_t *latest, const double *b0,
@@ -1333,6 +1667,7 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     ++p.stats.kernel_launches;
     const CtlTable2<T> ct = make_table<T>(p);
     const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
+    const int warps = p.desc.tune[3] > 0 ? p.desc.tune[3] : 1;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
     RunResult rr = run_tiles(p, g, s, (float)tol, cap, [&](int par, int) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -1341,7 +1676,16 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
             check_cuda(cudaEventCreate(&b), "event");
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
-        k_value2d<T, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        if (warps == 4)
+            k_value2d_w<T, true, 4><<<s.ntiles, 128, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        else if (warps == 2)
+            k_value2d_w<T, true, 2><<<s.ntiles, 64, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        else if (ct.d4 && ct.ncls == 8)
+            k_value2d<T, true, 8><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        else if (ct.d4 && ct.ncls == 4 && std::is_same<T, float>::value)
+            k_value2d<T, true, 4><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        else
+            k_value2d<T, true, 0><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
         ++p.stats.kernel_launches;
         if (fine) ++p.stats.sweep_kernel_launches;
         if (timed) {

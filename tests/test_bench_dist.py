@@ -1,0 +1,51 @@
+"""The multi-rank host logic of bench.py on CPU with the gloo backend
+(world size 2): every rank gets its own seed, the job time is the slowest
+rank's, and the work is summed over ranks."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+
+        ms, units = bench.aggregate(dist, local_ms=10.0 + rank, local_units=100.0 * (rank + 1), device="cpu")
+        q.put((rank, bench.rank_seed(rank), ms, units))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_like_the_bench():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    out = sorted(q.get(timeout=10) for _ in range(2))
+    assert [o[1] for o in out] == [0, 1]                 # distinct seeds
+    assert all(o[2] == 11.0 for o in out)                 # max time over ranks
+    assert all(o[3] == 300.0 for o in out)                # summed work
+
+
+def test_single_rank_passthrough():
+    import bench
+
+    assert bench.aggregate(None, 5.0, 7.0, "cpu") == (5.0, 7.0)
