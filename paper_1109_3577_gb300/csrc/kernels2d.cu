@@ -363,6 +363,21 @@ __device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, 
 // One launch of the value iteration over the active tiles.  kClamp: monotone
 // update u <- min(u, F(u)) from the start value M (bulk); without it the
 // plain update u <- F(u).
+// Parities of the 3x3 tile neighbourhood of tile (tx, ty) as a 9-bit mask
+// (bit 3 (dy+1) + (dx+1)); tiles off the grid read 0 like the ghost ring.
+__device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched &s, int tx, int ty) {
+    unsigned m = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int ux = tx + dx, uy = ty + dy;
+            if (ux >= 0 && uy >= 0 && ux < g.ntx && uy < g.nty && s.latest[uy * g.ntx + ux])
+                m |= 1u << (3 * (dy + 1) + (dx + 1));
+        }
+    return m;
+}
+
 template <typename T, bool kClamp, int NCLS>
 __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restrict__ code,
                                                 const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
@@ -371,10 +386,36 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
-    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     __shared__ TileSmemV<T> sm;
-    load_tile<T>(g, s, code, b0, b1, x0, y0, sm);
+    __shared__ T u0[kTile][kTile + 1];
     const int lane = threadIdx.x;
+    // load: the parity of every halo node follows from its position in the
+    // 3x3 tile neighbourhood, so all value loads are independent
+    const unsigned pm = nbr_parities(g, s, tx, ty);
+    for (int c = lane; c < kTile + 2; c += 32) {
+        const int x = x0 - 1 + c;
+        const int px = (c == 0) ? 0 : (c == kTile + 1 ? 2 : 1);
+        const bool xin = x < g.n0 && x >= 1 && x <= g.n0 - 2;
+#pragma unroll 4
+        for (int r = 0; r < kTile + 2; ++r) {
+            const int y = y0 - 1 + r;
+            const int py = (r == 0) ? 0 : (r == kTile + 1 ? 2 : 1);
+            T v = Num<T>::big();
+            int8_t cd = kHard;
+            if (x < g.n0 && y < g.n1) {
+                const int64_t i = (int64_t)y * g.n0 + x;
+                cd = code[i];
+                const bool inner = xin && y >= 1 && y <= g.n1 - 2;
+                const bool odd = inner && ((pm >> (3 * py + px)) & 1u);
+                v = odd ? b1[i] : b0[i];
+            }
+            sm.u[r][c] = v;
+            sm.c[r][c] = cd;
+        }
+    }
+    __syncwarp();
     int nfree = 0;
     {
         const int c = 1 + lane, x = x0 + lane;
@@ -396,6 +437,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
             sm.mk[r - 1][lane] = (uint16_t)m;
             const int y = y0 - 1 + r;
             sm.h[r - 1][lane] = (m && x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
+            u0[r - 1][lane] = sm.u[r][c];
         }
     }
     __syncwarp();
@@ -418,7 +460,22 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
             }
         }
     }
-    const float mc = store_tile<T>(g, s, t, b0, b1, x0, y0, sm);
+    // store into the buffer that is not current; change against the start values
+    T *dst = ((pm >> 4) & 1u) ? b0 : b1;
+    float mc = 0.f;
+    const int x = x0 + lane;
+    for (int r = 1; r <= kTile; ++r) {
+        const int y = y0 - 1 + r;
+        if (y > g.n1 - 2) break;
+        if (x > g.n0 - 2) continue;
+        const T v = sm.u[r][1 + lane];
+        const T o = u0[r - 1][lane];
+        dst[(int64_t)y * g.n0 + x] = v;
+        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
+        const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        mc = fmaxf(mc, d);
+    }
+    mc = warp_max(mc);
     const int nf = warp_sum(nfree);
     if (lane == 0) {
         s.chg[par][t] = mc;
