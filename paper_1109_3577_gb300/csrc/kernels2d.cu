@@ -957,9 +957,9 @@ __global__ void k_phi_init2d(int64_t N, const int8_t *__restrict__ code, int j0,
     }
 }
 
-template <int RG> struct PhiSmem {
+template <int RG, bool kSource> struct PhiSmem {
     float u[RG][kTile + 2][kTile + 3];
-    float src[RG][kTile][kTile + 1];
+    float src[kSource ? RG : 1][kSource ? kTile : 1][kTile + 1];
     int8_t c[kTile + 2][kTile + 4];
     uint8_t a[kTile][kTile + 4];
     // the control table, so that per-node lookups hit shared memory
@@ -981,9 +981,10 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
-    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     const int64_t N = (int64_t)g.n0 * g.n1;
-    __shared__ PhiSmem<RG> sm;
+    __shared__ PhiSmem<RG, kSource> sm;
     const int lane = threadIdx.x;
     for (int m = lane; m < kMaxControls; m += 32) {
         sm.kw10[m] = pc->kw10[m];
@@ -993,20 +994,30 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
         sm.sx[m] = pc->sx[m];
         sm.sy[m] = pc->sy[m];
     }
-    for (int r = 0; r < kTile + 2; ++r) {
-        const int y = y0 - 1 + r;
-        for (int c = lane; c < kTile + 2; c += 32) {
-            const int x = x0 - 1 + c;
+    const unsigned pm = nbr_parities(g, s, tx, ty);
+    unsigned alive = 0;   // colours with a nonzero value (or source) in the tile or its halo
+    for (int c = lane; c < kTile + 2; c += 32) {
+        const int x = x0 - 1 + c;
+        const int px = (c == 0) ? 0 : (c == kTile + 1 ? 2 : 1);
+        const bool xin = x >= 1 && x <= g.n0 - 2;
+#pragma unroll 2
+        for (int r = 0; r < kTile + 2; ++r) {
+            const int y = y0 - 1 + r;
+            const int py = (r == 0) ? 0 : (r == kTile + 1 ? 2 : 1);
             const bool in = x < g.n0 && y < g.n1;
             const bool inner = r >= 1 && r <= kTile && c >= 1 && c <= kTile;
             const int64_t i = (int64_t)y * g.n0 + x;
             int8_t cd = kHard;
             if (in) {
                 cd = code[i];
-                const int tt = tile_of(g, x, y);
-                const float *bsrc = (tt >= 0 && s.latest[tt]) ? b1 : b0;
+                const bool odd = xin && y >= 1 && y <= g.n1 - 2 && ((pm >> (3 * py + px)) & 1u);
+                const float *bs = odd ? b1 : b0;
 #pragma unroll
-                for (int q = 0; q < RG; ++q) sm.u[q][r][c] = bsrc[(int64_t)q * N + i];
+                for (int q = 0; q < RG; ++q) {
+                    const float v = bs[(int64_t)q * N + i];
+                    sm.u[q][r][c] = v;
+                    alive |= (unsigned)(v != 0.0f) << q;
+                }
             } else {
 #pragma unroll
                 for (int q = 0; q < RG; ++q) sm.u[q][r][c] = 0.0f;
@@ -1015,50 +1026,62 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
                 sm.a[r - 1][c - 1] = in ? astar[i] : kNoControl;
                 if (kSource) {
 #pragma unroll
-                    for (int q = 0; q < RG; ++q) sm.src[q][r - 1][c - 1] = in ? src[(int64_t)q * N + i] : 0.0f;
+                    for (int q = 0; q < RG; ++q) {
+                        const float v = in ? src[(int64_t)q * N + i] : 0.0f;
+                        sm.src[q][r - 1][c - 1] = v;
+                        alive |= (unsigned)(v != 0.0f) << q;
+                    }
                 }
             }
             sm.c[r][c] = cd;
         }
     }
+    alive = __reduce_or_sync(0xffffffffu, alive);
     __syncwarp();
-    for (int rd = 0; rd < rounds; ++rd) {
-        for (int dir = 0; dir < 4; ++dir) {
-            for (int st = 0; st < kTile; ++st) {
-                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
-                const int c = (dir < 2) ? s1 : 1 + lane;
-                const int r = (dir < 2) ? 1 + lane : s1;
-                const int8_t cd = sm.c[r][c];
-                const uint8_t a = sm.a[r - 1][c - 1];
-                const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
-                float nw[RG];
-                if (active) {
-                    const int sx = sm.sx[a], sy = sm.sy[a];
-                    const float w10 = sm.kw10[a], w01 = sm.kw01[a], w11 = sm.kw11[a];
-                    const float kp = sm.kap[a];
+    if (alive) {
+        for (int rd = 0; rd < rounds; ++rd) {
+            for (int dir = 0; dir < 4; ++dir) {
+                for (int st = 0; st < kTile; ++st) {
+                    const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+                    const int c = (dir < 2) ? s1 : 1 + lane;
+                    const int r = (dir < 2) ? 1 + lane : s1;
+                    const int8_t cd = sm.c[r][c];
+                    const uint8_t a = sm.a[r - 1][c - 1];
+                    const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
+                    float nw[RG];
+                    if (active) {
+                        const int sx = sm.sx[a], sy = sm.sy[a];
+                        const float w10 = sm.kw10[a], w01 = sm.kw01[a], w11 = sm.kw11[a];
+                        const float kp = sm.kap[a];
 #pragma unroll
-                    for (int q = 0; q < RG; ++q) {
-                        float v = w10 * sm.u[q][r][c + sx];
-                        v = fmaf(w01, sm.u[q][r + sy][c], v);
-                        v = fmaf(w11, sm.u[q][r + sy][c + sx], v);
-                        if (kSource) {
-                            nw[q] = fmaf(kp, sm.src[q][r - 1][c - 1], v);
-                        } else {
-                            const float o = sm.u[q][r][c];
-                            nw[q] = v > o ? v : o;
+                        for (int q = 0; q < RG; ++q) {
+                            if (!((alive >> q) & 1u)) {
+                                nw[q] = 0.0f;
+                                continue;
+                            }
+                            float v = w10 * sm.u[q][r][c + sx];
+                            v = fmaf(w01, sm.u[q][r + sy][c], v);
+                            v = fmaf(w11, sm.u[q][r + sy][c + sx], v);
+                            if (kSource) {
+                                nw[q] = fmaf(kp, sm.src[q][r - 1][c - 1], v);
+                            } else {
+                                const float o = sm.u[q][r][c];
+                                nw[q] = v > o ? v : o;
+                            }
                         }
                     }
-                }
-                __syncwarp();
-                if (active) {
+                    __syncwarp();
+                    if (active) {
 #pragma unroll
-                    for (int q = 0; q < RG; ++q) sm.u[q][r][c] = nw[q];
+                        for (int q = 0; q < RG; ++q)
+                            if ((alive >> q) & 1u) sm.u[q][r][c] = nw[q];
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
         }
     }
-    const int cur = s.latest[t];
+    const int cur = (pm >> 4) & 1u;
     float *dst = cur ? b0 : b1;
     const float *old = cur ? b1 : b0;
     float mc = 0.f;
@@ -1071,9 +1094,8 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
 #pragma unroll
         for (int q = 0; q < RG; ++q) {
             const float v = sm.u[q][r][1 + lane];
-            const float o = old[(int64_t)q * N + i];
             dst[(int64_t)q * N + i] = v;
-            mc = fmaxf(mc, fabsf(v - o));
+            if ((alive >> q) & 1u) mc = fmaxf(mc, fabsf(v - old[(int64_t)q * N + i]));
         }
     }
     mc = warp_max(mc);
