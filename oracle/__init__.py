@@ -12,7 +12,10 @@ Every function follows the paper (Cacace, Cristiani, Falcone, Picarelli,
 * ``sl_apply``       -- the operator F of Eq. (SLscheme), one application.
 * ``iterate``/``global_solve`` -- Eq. (iterativeSLscheme) to the sup-norm
   stopping test of Sec. 2.2 (Step 4), Gauss-Seidel or Jacobi.
-* ``patchy_solve``   -- the patchy algorithm of Sec. 3 (Steps 1-4).
+* ``patchy_solve``   -- the patchy algorithm of Sec. 3 (Steps 1-4), with the
+  Dirichlet patch boundary of Eq. (dbc) and the add-ons AO1-AO3 of Sec. 6 as
+  options.
+* ``iterate_reduced`` -- ``iterate`` over the AO3 control cones.
 * ``interp``         -- the interpolation operator I of Sec. 2.1.
 
 Pins (tests/test_oracle_*.py): eikonal closed form, Dijkstra on the axis
@@ -57,6 +60,16 @@ class _Problem(C.Structure):
     ]
 
 
+class _Addons(C.Structure):
+    _fields_ = [
+        ("dirichlet", C.c_int),
+        ("warm", C.c_int),
+        ("causal", C.c_int),
+        ("reduce_r", C.c_double),
+        ("data", C.POINTER(C.c_double)),
+    ]
+
+
 class _Stats(C.Structure):
     _fields_ = [
         ("sweeps_coarse", C.c_int),
@@ -97,11 +110,16 @@ def _load():
         lib.og_sl_apply.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, dp, C.c_int]
         lib.og_iterate.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, C.c_double, C.c_int, C.c_int,
                                    P(C.c_int), dp]
+        lib.og_iterate_reduced.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, C.c_double, C.c_int, C.c_int,
+                                           P(C.c_int), C.c_double, P(C.c_int), dp]
         lib.og_reachable.argtypes = [P(_Problem), P(C.c_ubyte), dp, P(C.c_ubyte)]
         lib.og_global_solve.argtypes = [P(_Problem), C.c_double, C.c_int, C.c_int, dp, P(C.c_int), dp]
         lib.og_patchy_solve.argtypes = [P(_Problem), P(C.c_int), C.c_double, C.c_double, C.c_double,
                                         C.c_int, C.c_int, dp, P(C.c_byte), dp, dp, P(C.c_int), dp, dp,
                                         P(_Stats)]
+        lib.og_patchy_solve_ex.argtypes = [P(_Problem), P(C.c_int), C.c_double, C.c_double, C.c_double,
+                                           C.c_int, C.c_int, P(_Addons), dp, P(C.c_byte), dp, dp, P(C.c_int),
+                                           dp, dp, P(_Stats)]
         _lib = lib
     return _lib
 
@@ -214,6 +232,23 @@ def iterate(p: Problem, U0: np.ndarray, upd: np.ndarray, tol: float, max_sweeps:
     return IterResult(U, sw.value, res.value, rc == 0)
 
 
+def iterate_reduced(p: Problem, U0: np.ndarray, upd: np.ndarray, astar: np.ndarray, r: float, tol: float,
+                    max_sweeps: int = 100000, order: int = 1) -> IterResult:
+    """``iterate`` with the AO3 control cones (Sec. 6): at node i only the
+    controls a with a . a_{astar[i]} >= cos(pi / r) (astar[i] = -1: all)."""
+    d = _Desc(p)
+    _, _, h = setup(p)
+    U = np.array(U0, dtype=np.float64).reshape(-1).copy()
+    upd = np.ascontiguousarray(upd, dtype=np.uint8).reshape(-1)
+    ast = np.ascontiguousarray(astar, dtype=np.int32).reshape(-1)
+    sw = C.c_int(0)
+    res = C.c_double(0)
+    rc = _load().og_iterate_reduced(C.byref(d.s), _ptr(upd, C.c_ubyte), _ptr(h, C.c_double),
+                                    _ptr(U, C.c_double), tol, max_sweeps, order, _ptr(ast, C.c_int), float(r),
+                                    C.byref(sw), C.byref(res))
+    return IterResult(U, sw.value, res.value, rc == 0)
+
+
 def global_solve(p: Problem, tol: Optional[float] = None, order: int = 1,
                  max_sweeps: Optional[int] = None) -> IterResult:
     """Global SL fixed point (Eq. iterativeSLscheme), U^(0) = 0 / +inf."""
@@ -243,9 +278,15 @@ class PatchyResult:
 
 
 def patchy_solve(p: Problem, order: int = 1, keep_phi: bool = False, tol: Optional[float] = None,
-                 max_sweeps: Optional[int] = None) -> PatchyResult:
-    """The patchy algorithm of Sec. 3 with state constraints on patch
-    boundaries (Steps 1, 2, 3.1, 3.2, 4)."""
+                 max_sweeps: Optional[int] = None, dirichlet: bool = False, warm: bool = False,
+                 causal: bool = False, reduce_r: float = 0.0,
+                 bc_data: Optional[np.ndarray] = None) -> PatchyResult:
+    """The patchy algorithm of Sec. 3 (Steps 1, 2, 3.1, 3.2, 4).  Patch
+    boundaries carry state constraints, or with ``dirichlet`` the data
+    U_P^(0) of Eq. (dbc) (``bc_data`` replaces it, for tests).  Add-ons of
+    Sec. 6: ``warm`` (AO1, start from U_P^(0)), ``causal`` (AO2, visit nodes
+    by increasing U_P^(0)), ``reduce_r`` (AO3, control cones of half-angle
+    pi / r around the coarse feedback; 0 = off)."""
     if p.n_coarse is None:
         raise ValueError("patchy_solve needs n_coarse")
     d = _Desc(p)
@@ -260,9 +301,20 @@ def patchy_solve(p: Problem, order: int = 1, keep_phi: bool = False, tol: Option
     phi = np.zeros((R, N)) if keep_phi else None
     st = _Stats()
     ncs = (C.c_int * 3)(*[int(v) for v in p.n_coarse])
-    rc = _load().og_patchy_solve(
+    ao = _Addons()
+    ao.dirichlet = int(bool(dirichlet))
+    ao.warm = int(bool(warm))
+    ao.causal = int(bool(causal))
+    ao.reduce_r = float(reduce_r)
+    data = None
+    if bc_data is not None:
+        data = np.ascontiguousarray(bc_data, dtype=np.float64).reshape(-1)
+        if data.size != N:
+            raise ValueError("bc_data must hold one value per fine node")
+    ao.data = _ptr(data, C.c_double)
+    rc = _load().og_patchy_solve_ex(
         C.byref(d.s), ncs, p.tol if tol is None else tol, p.tol_coarse, p.tol_phi,
-        p.max_sweeps if max_sweeps is None else max_sweeps, order, _ptr(u, C.c_double),
+        p.max_sweeps if max_sweeps is None else max_sweeps, order, C.byref(ao), _ptr(u, C.c_double),
         _ptr(lab, C.c_byte), _ptr(uc, C.c_double), _ptr(u0, C.c_double), _ptr(ast, C.c_int),
         _ptr(gap, C.c_double), _ptr(phi, C.c_double), C.byref(st))
     if rc < 0:

@@ -81,6 +81,24 @@
  *       and decreases to it (a start from 0 also converges, but then the
  *       minimum over controls picks up values that are still too small and
  *       Gauss-Seidel needs O(n) sweeps).
+ *   R16 Dirichlet patch boundary (Eq. dbc, Sec. 5): while patch j is solved,
+ *       every node outside patch j and outside Omega_0^j holds the fixed
+ *       value U_P^(0) of Step 2 (0 on every target part, +inf on the ghost
+ *       ring and on nodes Step 2 leaves unreachable); nodes of patch j that
+ *       are off S* stay +inf.  Nodes with a finite fixed value count as
+ *       target for S* (R14).
+ *   R17 AO1 (Sec. 6): the nodes of S* start from U_P^(0) where it is
+ *       finite and from M elsewhere; the iteration is the plain U <- F(U)
+ *       and reaches the same fixed point (R14: unique on S*).
+ *   R18 AO2 (Sec. 6): Gauss-Seidel visits the nodes of a patch in
+ *       increasing U_P^(0) (ties: increasing node index; +inf last), the
+ *       same order every sweep.
+ *   R19 AO3 (Sec. 6): at node i the minimum runs over
+ *       A_r(i) = { a : a . a*_{k~}(x_i) >= cos(pi/r) }, with a*_{k~} from
+ *       Step 2; the comparison has a slack of 1e-12 so that a control at
+ *       exactly the angle pi/r is kept whatever the rounding of the dot
+ *       product.  Nodes without a* keep the full set.  Labels (Step 3.1) do
+ *       not change.
  */
 #include <math.h>
 #include <stdint.h>
@@ -117,7 +135,31 @@ typedef struct {
     int64_t uncovered_left;
 } og_patchy_stats;
 
+/* Per-node control filter of AO3 (R19); a NULL filter keeps every control. */
+typedef struct {
+    const int *astar;   /* per node; -1 keeps the full set */
+    double cos_r;       /* cos(pi / r) - 1e-12 */
+} og_filter;
+
+/* Options of the patchy solve beyond the basic algorithm of Sec. 3. */
+typedef struct {
+    int dirichlet;        /* R16: Eq. dbc instead of state constraints */
+    int warm;             /* R17: AO1 */
+    int causal;           /* R18: AO2 */
+    double reduce_r;      /* R19: AO3 reduction factor r > 1; 0 = off */
+    const double *data;   /* optional Dirichlet data replacing U_P^(0) (N) */
+} og_addons;
+
 static const double OG_PI = 3.14159265358979323846;
+
+static int og_allowed(const og_problem *p, const og_filter *f, int64_t i, int m) {
+    if (!f || !f->astar || f->astar[i] < 0) return 1;
+    const double *a = p->controls + (size_t)m * p->dim;
+    const double *b = p->controls + (size_t)f->astar[i] * p->dim;
+    double dot = 0.0;
+    for (int d = 0; d < p->dim; ++d) dot += a[d] * b[d];
+    return dot >= f->cos_r;
+}
 
 /* ---------------------------------------------------------------- grid --- */
 
@@ -279,12 +321,13 @@ int og_interp_points(const og_problem *p, const double *U, int64_t npts, const d
    Returns the minimum; *arg gets the argmin (lowest index on ties, R10) and
    *gap the gap between the best and second-best values (both optional). */
 static double og_F_node(const og_problem *p, const double *U, const double *h, int64_t i, int mode,
-                        int *arg, double *gap) {
+                        const og_filter *flt, int *arg, double *gap) {
     int idx[3];
     og_index3(p, i, idx);
     double best = INFINITY, second = INFINITY;
     int besta = -1;
     for (int m = 0; m < p->n_controls; ++m) {
+        if (!og_allowed(p, flt, i, m)) continue;
         const double *a = p->controls + (size_t)m * p->dim;
         double xi[3] = {0.0, 0.0, 0.0};
         for (int d = 0; d < p->dim; ++d) xi[d] = (double)idx[d] + a[d];
@@ -346,7 +389,7 @@ static double og_F_node(const og_problem *p, const double *U, const double *h, i
 int og_sl_apply(const og_problem *p, const unsigned char *upd, const double *h, const double *Uin,
                 double *Uout, int mode) {
     int64_t N = og_count(p);
-    for (int64_t i = 0; i < N; ++i) Uout[i] = upd[i] ? og_F_node(p, Uin, h, i, mode, NULL, NULL) : Uin[i];
+    for (int64_t i = 0; i < N; ++i) Uout[i] = upd[i] ? og_F_node(p, Uin, h, i, mode, NULL, NULL, NULL) : Uin[i];
     return 0;
 }
 
@@ -403,7 +446,8 @@ static int og_support(const og_problem *p, int64_t i, const double *a, int64_t *
    already known to reach the target.  C shrinks to the set reached, and the
    two steps repeat until C no longer changes (the classical fixed point for
    almost-sure reachability in Markov decision processes). */
-int og_reachable(const og_problem *p, const unsigned char *upd, const double *U, unsigned char *inS) {
+static int og_reachable_f(const og_problem *p, const unsigned char *upd, const double *U, const og_filter *flt,
+                          unsigned char *inS) {
     const int64_t N = og_count(p);
     unsigned char *C = (unsigned char *)malloc((size_t)N);
     if (!C) return -1;
@@ -419,6 +463,7 @@ int og_reachable(const og_problem *p, const unsigned char *upd, const double *U,
                 int64_t i = og_visit(p, 1, pass, q);
                 if (!C[i] || inS[i]) continue;
                 for (int m = 0; m < p->n_controls && !inS[i]; ++m) {
+                    if (!og_allowed(p, flt, i, m)) continue;
                     int cnt = og_support(p, i, p->controls + (size_t)m * p->dim, sup);
                     if (cnt < 0) continue;
                     int admissible = 1, hits = 0;
@@ -443,19 +488,26 @@ int og_reachable(const og_problem *p, const unsigned char *upd, const double *U,
     return 0;
 }
 
+int og_reachable(const og_problem *p, const unsigned char *upd, const double *U, unsigned char *inS) {
+    return og_reachable_f(p, upd, U, NULL, inS);
+}
+
 /* Start value on S* (R14): any finite start converges to the unique fixed
    point on S*; a start above the solution converges fastest, because the
    minimum over controls ignores values that are still too large. */
 #define OG_START 1.0e6
 
 /* Fixed-point iteration of Eq. (iterativeSLscheme) on the nodes with upd[i]
-   = 1 (R14): nodes outside S* are set to +inf, nodes of S* start from M and
-   the iteration U <- F(U) runs in place (Gauss-Seidel, orders 0 and 1) or as
-   U^{n+1} = F(U^n) (order 2) until the sup-norm change of one sweep is
-   below tol (Sec. 2.2, Step 4).  Values of nodes with upd[i] = 0 are read
-   as given (0 on the target, +inf elsewhere). */
-int og_iterate(const og_problem *p, const unsigned char *upd, const double *h, double *U, double tol,
-               int max_sweeps, int order, int *sweeps_out, double *res_out) {
+   = 1 (R14): nodes outside S* are set to +inf, nodes of S* start from M (or
+   from warm[i] where warm is given and finite, R17) and the iteration
+   U <- F(U) runs in place (Gauss-Seidel: orders 0 and 1, or the fixed visit
+   list perm of R18 when given) or as U^{n+1} = F(U^n) (order 2) until the
+   sup-norm change of one sweep is below tol (Sec. 2.2, Step 4).  Values of
+   nodes with upd[i] = 0 are read as given (0 on the target, +inf or fixed
+   boundary data elsewhere).  flt restricts the controls (R19). */
+static int og_iterate_ex(const og_problem *p, const unsigned char *upd, const double *h, double *U, double tol,
+                         int max_sweeps, int order, const int64_t *perm, int64_t nperm, const double *warm,
+                         const og_filter *flt, int *sweeps_out, double *res_out) {
     int64_t N = og_count(p);
     unsigned char *inS = (unsigned char *)malloc((size_t)N);
     double *tmp = (double *)malloc(sizeof(double) * (size_t)N);
@@ -463,25 +515,26 @@ int og_iterate(const og_problem *p, const unsigned char *upd, const double *h, d
         free(inS); free(tmp);
         return -1;
     }
-    og_reachable(p, upd, U, inS);
+    og_reachable_f(p, upd, U, flt, inS);
     for (int64_t i = 0; i < N; ++i)
-        if (upd[i]) U[i] = inS[i] ? OG_START : INFINITY;
+        if (upd[i]) U[i] = inS[i] ? ((warm && isfinite(warm[i])) ? warm[i] : OG_START) : INFINITY;
     int s = 0;
     double res = INFINITY;
     while (s < max_sweeps) {
         res = 0.0;
         if (order == 2) {
-            og_sl_apply(p, inS, h, U, tmp, 0);
+            for (int64_t i = 0; i < N; ++i) tmp[i] = inS[i] ? og_F_node(p, U, h, i, 0, flt, NULL, NULL) : U[i];
             for (int64_t i = 0; i < N; ++i) {
                 double c = og_change(tmp[i], U[i]);
                 if (c > res) res = c;
                 U[i] = tmp[i];
             }
         } else {
-            for (int64_t q = 0; q < N; ++q) {
-                int64_t i = og_visit(p, order, s, q);
+            const int64_t nv = perm ? nperm : N;
+            for (int64_t q = 0; q < nv; ++q) {
+                int64_t i = perm ? perm[q] : og_visit(p, order, s, q);
                 if (!inS[i]) continue;
-                double v = og_F_node(p, U, h, i, 0, NULL, NULL);
+                double v = og_F_node(p, U, h, i, 0, flt, NULL, NULL);
                 double c = og_change(v, U[i]);
                 if (c > res) res = c;
                 U[i] = v;
@@ -495,6 +548,19 @@ int og_iterate(const og_problem *p, const unsigned char *upd, const double *h, d
     if (sweeps_out) *sweeps_out = s;
     if (res_out) *res_out = res;
     return res < tol ? 0 : 1;
+}
+
+int og_iterate(const og_problem *p, const unsigned char *upd, const double *h, double *U, double tol,
+               int max_sweeps, int order, int *sweeps_out, double *res_out) {
+    return og_iterate_ex(p, upd, h, U, tol, max_sweeps, order, NULL, 0, NULL, NULL, sweeps_out, res_out);
+}
+
+/* The same iteration with the AO3 control cones of R19 around a given
+   per-node control index field astar (-1: full set) and factor r. */
+int og_iterate_reduced(const og_problem *p, const unsigned char *upd, const double *h, double *U, double tol,
+                       int max_sweeps, int order, const int *astar, double r, int *sweeps_out, double *res_out) {
+    og_filter f = {astar, cos(OG_PI / r) - 1e-12};
+    return og_iterate_ex(p, upd, h, U, tol, max_sweeps, order, NULL, 0, NULL, &f, sweeps_out, res_out);
 }
 
 /* Global SL solve (Eq. iterativeSLscheme on the whole grid): U^(0) = 0 on
@@ -558,10 +624,22 @@ static int og_phi_iterate(const og_problem *p, const unsigned char *upd, const i
    unreachable, j on patch j and on target part j).  Optional outputs (NULL to
    skip): Ucoarse (coarse N~), U0 = U_P^(0) (N), astar (N; -1 where
    undefined), gap (N; best-vs-second control gap of Step 2), phi (R x N). */
-int og_patchy_solve(const og_problem *p, const int n_coarse[3], double tol, double tol_coarse,
-                    double tol_phi, int max_sweeps, int order, double *u, signed char *labels,
-                    double *Ucoarse_out, double *U0_out, int *astar_out, double *gap_out, double *phi_out,
-                    og_patchy_stats *st) {
+typedef struct {
+    double key;
+    int64_t i;
+} og_keyed;
+
+static int og_keyed_cmp(const void *a, const void *b) {
+    const og_keyed *x = (const og_keyed *)a, *y = (const og_keyed *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, double tol_coarse,
+                       double tol_phi, int max_sweeps, int order, const og_addons *ao, double *u,
+                       signed char *labels, double *Ucoarse_out, double *U0_out, int *astar_out,
+                       double *gap_out, double *phi_out, og_patchy_stats *st) {
     const int64_t N = og_count(p);
     const int R = p->n_targets;
     if (R < 1 || R > 64) return -2;
@@ -636,7 +714,7 @@ int og_patchy_solve(const og_problem *p, const int n_coarse[3], double tol, doub
         if (kind[i] != OG_FREE || isinf(U0[i])) continue;
         int arg;
         double gap;
-        og_F_node(p, U0, h, i, 0, &arg, &gap);
+        og_F_node(p, U0, h, i, 0, NULL, &arg, &gap);
         astar[i] = arg;
         if (gap_out) gap_out[i] = gap;
     }
@@ -689,22 +767,59 @@ int og_patchy_solve(const og_problem *p, const int n_coarse[3], double tol, doub
     for (int64_t i = 0; i < N; ++i)
         if (upd[i] && labels[i] < 0) st->uncovered_left++;
 
-    /* ---- Step 3.2: each patch solved on its own, state constraints on its
-       boundary (every node outside patch j and outside Omega_0^j is +inf). */
-    for (int64_t i = 0; i < N; ++i) u[i] = kind[i] == OG_TARGET ? 0.0 : INFINITY;
-    for (int j = 0; j < R; ++j) {
-        int64_t cnt = 0;
-        for (int64_t i = 0; i < N; ++i) {
-            upd[i] = kind[i] == OG_FREE && labels[i] == j;
-            cnt += upd[i];
-            W[i] = (kind[i] == OG_TARGET && part[i] == j) ? 0.0 : INFINITY;
+    /* ---- Step 3.2: each patch solved on its own.  State constraints on its
+       boundary (every node outside patch j and outside Omega_0^j is +inf),
+       or the Dirichlet data of Eq. (dbc) there (R16); add-ons AO1-AO3 of
+       Sec. 6 (R17-R19). */
+    {
+        const int dir = ao && ao->dirichlet;
+        const double *D = (ao && ao->data) ? ao->data : U0;
+        og_filter flt = {astar, 0.0};
+        const og_filter *fp = NULL;
+        if (ao && ao->reduce_r > 0.0) {
+            flt.cos_r = cos(OG_PI / ao->reduce_r) - 1e-12;
+            fp = &flt;
         }
-        st->patch_nodes[j] = cnt;
-        if (og_iterate(p, upd, h, W, tol, max_sweeps, order, &st->sweeps_patch[j], &st->residual_patch[j]))
-            rc = 1;
-        /* ---- Step 4: merge. */
-        for (int64_t i = 0; i < N; ++i)
-            if (upd[i]) u[i] = W[i];
+        og_keyed *kv = NULL;
+        int64_t *perm = NULL;
+        if (ao && ao->causal) {
+            kv = (og_keyed *)malloc(sizeof(og_keyed) * (size_t)N);
+            perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+            if (!kv || !perm) {
+                free(kv); free(perm);
+                rc = -1;
+                goto done;
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) u[i] = kind[i] == OG_TARGET ? 0.0 : INFINITY;
+        for (int j = 0; j < R && rc >= 0; ++j) {
+            int64_t cnt = 0;
+            for (int64_t i = 0; i < N; ++i) {
+                upd[i] = kind[i] == OG_FREE && labels[i] == j;
+                if (upd[i] && kv) {
+                    kv[cnt].key = U0[i];   /* +inf sorts last */
+                    kv[cnt].i = i;
+                }
+                cnt += upd[i];
+                if (kind[i] == OG_TARGET && part[i] == j) W[i] = 0.0;
+                else W[i] = (dir && !upd[i]) ? D[i] : INFINITY;
+            }
+            st->patch_nodes[j] = cnt;
+            if (kv) {
+                qsort(kv, (size_t)cnt, sizeof(og_keyed), og_keyed_cmp);
+                for (int64_t q = 0; q < cnt; ++q) perm[q] = kv[q].i;
+            }
+            int r2 = og_iterate_ex(p, upd, h, W, tol, max_sweeps, order, perm, cnt,
+                                   (ao && ao->warm) ? U0 : NULL, fp, &st->sweeps_patch[j],
+                                   &st->residual_patch[j]);
+            if (r2 < 0) rc = -1;
+            else if (r2 && rc == 0) rc = 1;
+            /* ---- Step 4: merge. */
+            for (int64_t i = 0; i < N; ++i)
+                if (upd[i]) u[i] = W[i];
+        }
+        free(kv);
+        free(perm);
     }
 
 done:
@@ -712,4 +827,12 @@ done:
     free(kind); free(upd); free(part); free(h); free(U0); free(astar); free(phi); free(phimax);
     free(lab2); free(W);
     return rc;
+}
+
+int og_patchy_solve(const og_problem *p, const int n_coarse[3], double tol, double tol_coarse,
+                    double tol_phi, int max_sweeps, int order, double *u, signed char *labels,
+                    double *Ucoarse_out, double *U0_out, int *astar_out, double *gap_out, double *phi_out,
+                    og_patchy_stats *st) {
+    return og_patchy_solve_ex(p, n_coarse, tol, tol_coarse, tol_phi, max_sweeps, order, NULL, u, labels,
+                              Ucoarse_out, U0_out, astar_out, gap_out, phi_out, st);
 }
