@@ -227,7 +227,10 @@ def run_ours(args, rank, world, dist):
                "sample": f"{tu // 64} node updates x 64 controls: applications of F (Eq. SLscheme) by the "
                          f"single-threaded FP64 C oracle on 48-row bands of the same {N_FINE}^2 grid, {tt:.1f} s"}
 
-    plan = P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS)
+    # patch boundary and add-ons of Sec. 6 (defaults: state constraints, none)
+    aflags = (P.HJBP_FLAG_DIRICHLET if args.bc == "dirichlet" else 0) | (P.HJBP_FLAG_WARM_START if args.warm else 0)
+    plan = P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS | aflags,
+                  reduce_r=args.reduce_r)
     for _ in range(args.warmup):
         plan.solve()
     torch.cuda.synchronize()
@@ -283,7 +286,7 @@ def run_ours(args, rank, world, dist):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream) as ep:
+        with P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=aflags, reduce_r=args.reduce_r) as ep:
             ep.solve()
             u = ep.values()
             lab = ep.labels()
@@ -316,7 +319,8 @@ def run_ours(args, rank, world, dist):
             "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": p.n_controls,
                        "n_targets": p.n_targets,
                        "tol": 1e-6, "seed": "rank", "precision": "FP32 sweeps, FP64 coarse/feedback/labels/polish",
-                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
+                       "patch_bc": args.bc, "warm_start": bool(args.warm), "reduce_r": args.reduce_r},
             "solves_per_s": world * 1e3 * args.steps / total_ms,
             "plain_sl_solves_per_s": 1e3 / statistics.mean(gms),
             "plain_sl_ms": statistics.mean(gms),
@@ -439,6 +443,10 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--n", type=int, default=0, help="fine nodes per side (default 2049 / 257)")
     ap.add_argument("--nc", type=int, default=0, help="coarse nodes per side (default 65 / 33)")
+    ap.add_argument("--bc", default="state", choices=["state", "dirichlet"],
+                    help="patch boundary of Step 3.2: state constraints (Sec. 3) or U_P^(0) (Eq. dbc)")
+    ap.add_argument("--warm", action="store_true", help="add-on AO1: start Step 3.2 from U_P^(0)")
+    ap.add_argument("--reduce-r", type=float, default=0.0, help="add-on AO3: control cones of half-angle pi/r")
     args = ap.parse_args()
     global N_FINE, N_COARSE, WORKLOAD, FAMILY
     FAMILY = args.workload

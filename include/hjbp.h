@@ -97,12 +97,30 @@ typedef struct {
                            launch of the value sweep (2), [1] of the colour transport (3),
                            [2] passes per launch of the reachability sweep (1), [3] warps
                            per 32x32 tile of the 2D value sweep (1; 1, 2 or 4) */
+    double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
+                           minimum of Step 3.2 at node i to the controls a with
+                           a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse
+                           feedback of Step 2, Eq. feedbackcontrol); nodes without a
+                           feedback keep every control.  0 keeps every control.  On the
+                           2D path the control set must have at most 64 members.      */
 } hjbp_problem_desc;
 
 /* flags: HJBP_FLAG_TIME_SWEEPS records a CUDA event pair around every launch
  * of the fine-grid value-sweep kernel (on the plan's stream) and reports their
  * summed duration in hjbp_stats.ms_sweep_kernel.                              */
 #define HJBP_FLAG_TIME_SWEEPS 1
+/* HJBP_FLAG_DIRICHLET (patchy solves only): while patch j is solved in Step
+ * 3.2, every node outside patch j and outside Omega_0^j holds the value
+ * U_P^(0) of Step 2 (Eq. dbc, Sec. 5-6: 0 on every target part, +inf on the
+ * ghost ring and where Step 2 finds no finite value) instead of +inf (the
+ * state constraints of Sec. 3).  Patch nodes that can reach neither their
+ * target part nor a finite boundary value stay +inf.
+ * HJBP_FLAG_WARM_START (patchy solves only): add-on AO1 of Sec. 6, Step 3.2
+ * starts from U_P^(0) where it is finite (the bound 1e6 elsewhere) and runs
+ * the plain update u <- F(u); the fixed point is the same (it is unique on the
+ * reachable set), only the iteration count changes.                         */
+#define HJBP_FLAG_DIRICHLET 2
+#define HJBP_FLAG_WARM_START 4
 
 /* Device allocator hooks (optional).  alloc returns device memory of at least
  * `bytes` usable on `stream`, or NULL; release returns it.  ctx is passed back

@@ -7,7 +7,9 @@ raises.
 """
 from ._binding import (  # noqa: F401
     HJBP_FP32_POLISH64,
+    HJBP_FLAG_DIRICHLET,
     HJBP_FLAG_TIME_SWEEPS,
+    HJBP_FLAG_WARM_START,
     HJBP_FP64,
     HJBP_OUT_ASTAR,
     HJBP_OUT_PHI,

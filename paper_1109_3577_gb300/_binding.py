@@ -47,6 +47,7 @@ class Desc(C.Structure):
         ("max_sweeps", C.c_int),
         ("flags", C.c_int),
         ("tune", C.c_int * 4),
+        ("reduce_r", C.c_double),
     ]
 
 
@@ -308,9 +309,12 @@ def torch_allocator() -> Allocator:
 
 
 HJBP_FLAG_TIME_SWEEPS = 1
+HJBP_FLAG_DIRICHLET = 2
+HJBP_FLAG_WARM_START = 4
 
 
-def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0, tune=None):
+def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0, tune=None,
+                      reduce_r: float = 0.0):
     """Build an hjbp_problem_desc from a workloads.Problem.  Returns the
     struct plus the arrays it points into (keep both alive)."""
     controls = np.ascontiguousarray(p.controls, dtype=np.float64)
@@ -337,6 +341,7 @@ def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 
     d.flags = int(flags)
     for i, v in enumerate(tune or ()):
         d.tune[i] = int(v)
+    d.reduce_r = float(reduce_r)
     return d, (controls, targets)
 
 
@@ -345,9 +350,10 @@ class Plan:
     ``labels()`` / ``stats()``."""
 
     def __init__(self, problem, precision: int = HJBP_FP32_POLISH64, stream: Optional[int] = None,
-                 use_torch_allocator: bool = False, max_sweeps: int = 0, flags: int = 0, tune=None):
+                 use_torch_allocator: bool = False, max_sweeps: int = 0, flags: int = 0, tune=None,
+                 reduce_r: float = 0.0):
         self.problem = problem
-        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps, flags, tune)
+        self._desc, self._keep = desc_from_problem(problem, precision, max_sweeps, flags, tune, reduce_r)
         if stream is None:
             stream = 0
             try:

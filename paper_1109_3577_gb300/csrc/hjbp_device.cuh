@@ -33,10 +33,12 @@ template <typename T> struct Num;
 template <> struct Num<float> {
     static __host__ __device__ constexpr float big() { return 1.0e30f; }
     static __host__ __device__ constexpr float thresh() { return 1.0e25f; }
+    static __host__ __device__ constexpr double noise() { return 0x1p-21; }  // 4 units in the last place
 };
 template <> struct Num<double> {
     static __host__ __device__ constexpr double big() { return 1.0e300; }
     static __host__ __device__ constexpr double thresh() { return 1.0e290; }
+    static __host__ __device__ constexpr double noise() { return 0x1p-50; }
 };
 constexpr double kStartValue = 1.0e6;     // M, above every solution value (R14)
 constexpr double kU0Bound = 1.0e6;        // bound replacing +inf inside U_P^(0) (R7)
@@ -100,6 +102,18 @@ struct CtlLiteral2 {
 // set when some control of quadrant q needs exactly mask m.
 struct ReachTable2 {
     uint8_t present[4];
+};
+
+// Control cones of add-on AO3 (Sec. 6) for 2D sets of at most 64 controls:
+// for a coarse feedback a* (entry nc: no feedback, every control), mask[a*]
+// has bit q set when the control at position q of the quadrant-sorted table
+// (CtlTable2 order) satisfies a . a* >= cos(pi / r) - 1e-12, and reach[a*]
+// holds, per quadrant (8 bits each), the corner patterns of those controls in
+// the encoding of ReachTable2.
+struct Cone2 {
+    unsigned long long mask[65];
+    uint32_t reach[65];
+    int nc;
 };
 
 // Speed field c(x) (hjbp_speed_kind) and its parameters, passed by value.

@@ -67,17 +67,18 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
     }
 }
 
-// Start values of a value solve (R14): M on free nodes, the fixed value on
-// targets, +inf on hard nodes; written to both buffers.
+// Start values of a value solve (R14): M on free nodes (or, with a warm
+// start, the given value where it is finite: add-on AO1 of Sec. 6), the fixed
+// value on targets, +inf on hard nodes; written to both buffers.
 template <typename T>
 __global__ void k_init_values2d(int64_t N, const int8_t *__restrict__ code, const double *__restrict__ fixed,
-                                T start, T *__restrict__ b0, T *__restrict__ b1) {
+                                T start, T *__restrict__ b0, T *__restrict__ b1, const double *__restrict__ warm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
         T v;
         if (c < 0) v = Num<T>::big();
         else if (c >= kTargetBase) v = fixed ? (T)fixed[i] : (T)0;
-        else v = start;
+        else v = (warm && warm[i] < kU0Bound) ? (T)warm[i] : start;
         b0[i] = v;
         b1[i] = v;
     }
@@ -268,24 +269,31 @@ __device__ __forceinline__ T sl_update(const TileSmem<T> &sm, int c, int r, int8
 // neighbour (dx-1, dy-1) belongs to the node's patch or its target part;
 // bit 15 set when the node itself is free).  Codes do not change during a
 // solve, so the masks are formed once per launch.
-template <typename T> struct TileSmemV {
+template <typename T, bool kDir> struct TileSmemV {
     T u[kTile + 2][kTile + 3];
     int8_t c[kTile + 2][kTile + 4];
     T h[kTile][kTile + 1];
     uint16_t mk[kTile][kTile + 2];
+    T d[kDir ? kTile + 2 : 1][kDir ? kTile + 3 : 1];  // Dirichlet data of the halo image (Eq. dbc)
 };
 
 // The update of sl_update with the neighbourhood masked by a precomputed
 // mask; NCLS > 0 fully unrolls the symmetric form for a table with exactly
 // NCLS classes (every class then sits in the constant bank as immediates).
-template <typename T, int NCLS, class S>
+// A neighbour outside the mask reads +inf (state constraints) or, with kDir,
+// its fixed Dirichlet value (Eq. dbc).
+template <typename T, int NCLS, bool kDir, class S>
 __device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct) {
     T nb[3][3];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx)
-            nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+        for (int dx = 0; dx < 3; ++dx) {
+            if constexpr (kDir)
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : sm.d[r - 1 + dy][c - 1 + dx];
+            else
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+        }
     T b0 = Num<T>::big(), b1 = Num<T>::big(), b2 = Num<T>::big(), b3 = Num<T>::big();
     if (NCLS > 0 || ct.d4) {
         T E[4], G[4], A[4];
@@ -360,9 +368,51 @@ __device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, 
     return b01 < b23 ? b01 : b23;
 }
 
-// One launch of the value iteration over the active tiles.  kClamp: monotone
-// update u <- min(u, F(u)) from the start value M (bulk); without it the
-// plain update u <- F(u).
+// The update over a per-node subset of the controls (AO3 cones).  mine: the
+// node's mask over table positions; uni: the union of the masks of the warp's
+// lanes (warp-uniform, so every lane walks the same positions); tab: kap-scaled
+// weights per position.
+template <typename T> struct Ctl4 {
+    T kw10, kw01, kw11, kap;
+};
+// Quadrant ranges of the table, copied by value (taking the address of a
+// kernel parameter would move the whole table to local memory).
+struct QBeg {
+    int v[5];
+};
+
+template <typename T, bool kDir, class S>
+__device__ __forceinline__ T sl_update_cone(const S &sm, int c, int r, unsigned m, T hh, unsigned long long mine,
+                                            unsigned long long uni, const QBeg qbeg, const Ctl4<T> *tab) {
+    T nb[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            if constexpr (kDir)
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : sm.d[r - 1 + dy][c - 1 + dx];
+            else
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+        }
+    T best = Num<T>::big();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+        const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
+        const int lo = qbeg.v[q], hi = qbeg.v[q + 1];
+        const unsigned long long below_hi = hi >= 64 ? ~0ull : ((1ull << hi) - 1ull);
+        unsigned long long uq = uni & below_hi & ~((1ull << lo) - 1ull);
+        while (uq) {
+            const int pos = __ffsll((long long)uq) - 1;
+            uq &= uq - 1ull;
+            const Ctl4<T> w = tab[pos];
+            const T v = fma(w.kw11, a11, fma(w.kw01, a01, fma(w.kw10, a10, w.kap * hh)));
+            if ((mine >> pos) & 1ull) best = v < best ? v : best;
+        }
+    }
+    return best;
+}
+
 // Parities of the 3x3 tile neighbourhood of tile (tx, ty) as a 9-bit mask
 // (bit 3 (dy+1) + (dx+1)); tiles off the grid read 0 like the ghost ring.
 __device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched &s, int tx, int ty) {
@@ -378,19 +428,36 @@ __device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched
     return m;
 }
 
-template <typename T, bool kClamp, int NCLS>
+// One launch of the value iteration over the active tiles.  clamp != 0: the
+// monotone update u <- min(u, F(u)) from the start value M; clamp == 0: the
+// plain update u <- F(u) (warm start, add-on AO1).  kDir: nodes outside the
+// node's patch read the Dirichlet data dval (Eq. dbc) instead of +inf.  A
+// node's own patch includes its target part and its own pruned nodes (code
+// -2 - patch, value +inf).
+// kCone: the minimum runs over each node's AO3 cone (astar, cone).
+template <typename T, int NCLS, bool kDir, bool kCone = false>
 __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restrict__ code,
                                                 const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                 TileSched s, int par, int rounds, unsigned long long *updates,
-                                                const CtlTable2<T> ct) {
+                                                const CtlTable2<T> ct, int clamp, const T *__restrict__ dval,
+                                                const uint8_t *__restrict__ astar = nullptr,
+                                                const Cone2 *__restrict__ cone = nullptr) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
-    __shared__ TileSmemV<T> sm;
+    __shared__ TileSmemV<T, kDir> sm;
     __shared__ T u0[kTile][kTile + 1];
+    __shared__ uint8_t sa[kCone ? kTile : 1][kCone ? kTile + 1 : 1];
+    __shared__ unsigned long long cmask[kCone ? 65 : 1];
+    __shared__ Ctl4<T> ctab[kCone ? 64 : 1];
     const int lane = threadIdx.x;
+    const QBeg qb{{ct.qbeg[0], ct.qbeg[1], ct.qbeg[2], ct.qbeg[3], ct.qbeg[4]}};
+    if constexpr (kCone) {
+        for (int q = lane; q <= cone->nc; q += 32) cmask[q] = cone->mask[q];
+        for (int q = lane; q < ct.nc; q += 32) ctab[q] = Ctl4<T>{ct.kw10[q], ct.kw01[q], ct.kw11[q], ct.kap[q]};
+    }
     // load: the parity of every halo node follows from its position in the
     // 3x3 tile neighbourhood, so all value loads are independent
     const unsigned pm = nbr_parities(g, s, tx, ty);
@@ -402,7 +469,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         for (int r = 0; r < kTile + 2; ++r) {
             const int y = y0 - 1 + r;
             const int py = (r == 0) ? 0 : (r == kTile + 1 ? 2 : 1);
-            T v = Num<T>::big();
+            T v = Num<T>::big(), dv = Num<T>::big();
             int8_t cd = kHard;
             if (x < g.n0 && y < g.n1) {
                 const int64_t i = (int64_t)y * g.n0 + x;
@@ -410,9 +477,11 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                 const bool inner = xin && y >= 1 && y <= g.n1 - 2;
                 const bool odd = inner && ((pm >> (3 * py + px)) & 1u);
                 v = odd ? b1[i] : b0[i];
+                if constexpr (kDir) dv = dval[i];
             }
             sm.u[r][c] = v;
             sm.c[r][c] = cd;
+            if constexpr (kDir) sm.d[r][c] = dv;
         }
     }
     __syncwarp();
@@ -423,13 +492,13 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
             const int8_t cd = sm.c[r][c];
             unsigned m = 0;
             if (cd >= 0 && cd < kTargetBase) {
-                const int8_t tg = (int8_t)(cd + kTargetBase);
+                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
-                        m |= (unsigned)(q == cd || q == tg) << (3 * dy + dx);
+                        m |= (unsigned)(q == cd || q == tg || q == pr) << (3 * dy + dx);
                     }
                 m |= 0x8000u;
                 ++nfree;
@@ -437,6 +506,10 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
             sm.mk[r - 1][lane] = (uint16_t)m;
             const int y = y0 - 1 + r;
             sm.h[r - 1][lane] = (m && x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
+            if constexpr (kCone) {
+                const int a = (m && x < g.n0 && y < g.n1) ? astar[(int64_t)y * g.n0 + x] : kNoControl;
+                sa[r - 1][lane] = (uint8_t)(a < cone->nc ? a : cone->nc);
+            }
             u0[r - 1][lane] = sm.u[r][c];
         }
     }
@@ -450,9 +523,18 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                 const unsigned m = sm.mk[r - 1][c - 1];
                 const bool active = (m & 0x8000u) != 0;
                 T nw = sm.u[r][c];
-                if (active) {
-                    const T best = sl_update_m<T, NCLS>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
-                    if (best < Num<T>::thresh()) nw = kClamp ? (best < nw ? best : nw) : best;
+                if constexpr (kCone) {
+                    const unsigned long long mine = active ? cmask[sa[r - 1][c - 1]] : 0ull;
+                    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mine);
+                    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mine >> 32));
+                    const unsigned long long uni = ((unsigned long long)hi << 32) | lo;
+                    if (active) {
+                        const T best = sl_update_cone<T, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], mine, uni, qb, ctab);
+                        if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
+                    }
+                } else if (active) {
+                    const T best = sl_update_m<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
+                    if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
                 }
                 __syncwarp();
                 if (active) sm.u[r][c] = nw;
@@ -472,7 +554,10 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         const T o = u0[r - 1][lane];
         dst[(int64_t)y * g.n0 + x] = v;
         const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-        const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        // the plain update is not monotone and may keep moving by a few units
+        // in the last place; such moves count as no change
+        if (!clamp && d <= (float)(Num<T>::noise() * fabs((double)v))) d = 0.f;
         mc = fmaxf(mc, d);
     }
     mc = warp_max(mc);
@@ -725,51 +810,71 @@ __global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T
 
 // Positive-probability reachability within the candidate set: a free node
 // becomes reached when some control whose positive-weight corners (other than
-// the node) are all usable puts positive weight on a reached node or on its
-// own target part (R14).  In place; monotone, so the order does not matter.
+// the node) are all usable puts positive weight on a reached node or on a
+// terminal node (R14).  Terminal: the node's own target part, and with
+// Dirichlet data (dterm != NULL, Eq. dbc) every node outside the patch whose
+// data is finite.  With AO3 cones (cone != NULL) a node uses only the controls
+// of its cone.  In place; monotone, so the order does not matter.
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restrict__ code,
                                                 uint8_t *__restrict__ rch, TileSched s, int par,
-                                                ReachTable2 rt, int passes) {
+                                                ReachTable2 rt, int passes, const double *__restrict__ dterm,
+                                                const uint8_t *__restrict__ astar, const Cone2 *__restrict__ cone) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = s.list[par][blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
     __shared__ uint8_t sr[kTile + 2][kTile + 4];
     __shared__ int8_t sc[kTile + 2][kTile + 4];
+    __shared__ uint8_t sd[kTile + 2][kTile + 4];
     const int lane = threadIdx.x;
     for (int r = 0; r < kTile + 2; ++r) {
         const int y = y0 - 1 + r;
         for (int c = lane; c < kTile + 2; c += 32) {
             const int x = x0 - 1 + c;
-            uint8_t v = 0;
+            uint8_t v = 0, df = 0;
             int8_t cd = kHard;
             if (x < g.n0 && y < g.n1) {
                 const int64_t i = (int64_t)y * g.n0 + x;
                 cd = code[i];
                 v = rch[i];
+                if (dterm) df = dterm[i] < kU0Bound;
             }
             sr[r][c] = v;
             sc[r][c] = cd;
+            sd[r][c] = df;
         }
     }
     __syncwarp();
     // per interior node: bits 0..8 usable neighbour (3 dy + dx), bits 9..17
-    // neighbour is the node's own target part, bit 31 node free and unreached
+    // neighbour is terminal, bit 31 node free and unreached; pres: the corner
+    // patterns of the node's controls per quadrant
     __shared__ uint32_t mk[kTile][kTile + 1];
+    __shared__ uint32_t pres4[kTile][kTile + 1];
     {
         const int c = 1 + lane;
+        const uint32_t all = (uint32_t)rt.present[0] | ((uint32_t)rt.present[1] << 8) |
+                             ((uint32_t)rt.present[2] << 16) | ((uint32_t)rt.present[3] << 24);
         for (int r = 1; r <= kTile; ++r) {
             const int8_t cd = sc[r][c];
+            uint32_t pw = all;
+            if (cone) {
+                const int x = x0 + lane, y = y0 - 1 + r;
+                const int a = (cd >= 0 && cd < kTargetBase && x < g.n0 && y < g.n1) ? astar[(int64_t)y * g.n0 + x]
+                                                                                     : kNoControl;
+                pw = cone->reach[a < cone->nc ? a : cone->nc];
+            }
+            pres4[r - 1][lane] = pw;
             uint32_t m = 0;
             if (cd >= 0 && cd < kTargetBase && !sr[r][c]) {
-                const int8_t tg = (int8_t)(cd + kTargetBase);
+                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int8_t q = sc[r - 1 + dy][c - 1 + dx];
-                        m |= (uint32_t)(q == cd || q == tg) << (3 * dy + dx);
-                        m |= (uint32_t)(q == tg) << (9 + 3 * dy + dx);
+                        const bool term = q == tg || (q != cd && q != pr && sd[r - 1 + dy][c - 1 + dx]);
+                        m |= (uint32_t)(q == cd || term) << (3 * dy + dx);
+                        m |= (uint32_t)term << (9 + 3 * dy + dx);
                     }
                 m |= 0x80000000u;
             }
@@ -785,6 +890,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                 const int c = (dir < 2) ? s1 : 1 + lane;
                 const int r = (dir < 2) ? 1 + lane : s1;
                 const uint32_t m = mk[r - 1][c - 1];
+                const uint32_t pw = pres4[r - 1][c - 1];
                 bool hit = false;
                 if ((m & 0x80000000u) && !sr[r][c]) {
 #pragma unroll
@@ -797,7 +903,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                         const unsigned rr = (unsigned)(sr[r][c + sx] != 0) | ((unsigned)(sr[r + sy][c] != 0) << 1) |
                                             ((unsigned)(sr[r + sy][c + sx] != 0) << 2);
                         const unsigned rb = tgt | (us & rr);
-                        const unsigned pres = rt.present[q];
+                        const unsigned pres = (pw >> (8 * q)) & 0xffu;
                         for (unsigned k = 1; k < 8; ++k)
                             if ((pres >> k) & 1u)
                                 if ((us & k) == k && (rb & k)) hit = true;
@@ -825,14 +931,16 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     }
 }
 
-// Free nodes not reached leave the candidate set (become hard); counts them.
+// Free nodes not reached leave the candidate set: their code becomes
+// -2 - patch (not free, value +inf, still known to belong to the patch, which
+// the Dirichlet boundary needs); counts them.
 __global__ void k_reach_prune(int64_t N, int8_t *__restrict__ code, const uint8_t *__restrict__ rch,
                               unsigned long long *removed) {
     unsigned long long cnt = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
         if (c >= 0 && c < kTargetBase && !rch[i]) {
-            code[i] = kHard;
+            code[i] = (int8_t)(-2 - c);
             ++cnt;
         }
     }
@@ -1271,7 +1379,9 @@ __global__ void __launch_bounds__(32) k_compact2d(Grid2 g, const int8_t *__restr
 // over all controls at close to FP32 cost.
 __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const double *__restrict__ h,
                            const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
-                           const CtlTable2<float> c32, const CtlTable2<double> c64) {
+                           const CtlTable2<float> c32, const CtlTable2<double> c64,
+                           const double *__restrict__ dval, const uint8_t *__restrict__ astar,
+                           const Cone2 *__restrict__ cone) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     float mc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1279,7 +1389,7 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
         double v = uin[i];
         if (cd >= 0 && cd < kTargetBase) {
             const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
-            const int8_t tg = (int8_t)(cd + kTargetBase);
+            const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
             double nb[3][3];
             float nf[3][3];
             float amax = 0.f;
@@ -1289,14 +1399,22 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
                 for (int dx = 0; dx < 3; ++dx) {
                     const int64_t j = (int64_t)(iy - 1 + dy) * g.n0 + (ix - 1 + dx);
                     const int8_t q = code[j];
-                    const double w = uin[j];
-                    const bool fin = (q == cd || q == tg) && w < Num<double>::thresh();
+                    // outside the patch: +inf, or the Dirichlet data (Eq. dbc)
+                    const bool same = q == cd || q == tg || q == pr;
+                    const double w = same ? uin[j] : (dval ? dval[j] : Num<double>::big());
+                    const bool fin = w < Num<double>::thresh();
                     nb[dy][dx] = fin ? w : Num<double>::big();
                     nf[dy][dx] = fin ? (float)w : Num<float>::big();
                     if (fin) amax = fmaxf(amax, fabsf((float)w));
                 }
             const double hh = h[i];
             const float hf = (float)hh;
+            // AO3: the node's cone over table positions (every control without)
+            unsigned long long allow = ~0ull;
+            if (cone) {
+                const int a = astar[i];
+                allow = cone->mask[a < cone->nc ? a : cone->nc];
+            }
             // pass 1: FP32 minimum
             float b32 = Num<float>::big();
 #pragma unroll
@@ -1304,6 +1422,7 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
                 const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
                 const float a10 = nf[1][sx], a01 = nf[sy][1], a11 = nf[sy][sx];
                 for (int m = c32.qbeg[q]; m < c32.qbeg[q + 1]; ++m) {
+                    if (cone && !((allow >> m) & 1ull)) continue;
                     const float w = fmaf(c32.kw11[m], a11, fmaf(c32.kw01[m], a01, fmaf(c32.kw10[m], a10, c32.kap[m] * hf)));
                     b32 = w < b32 ? w : b32;
                 }
@@ -1318,6 +1437,7 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
                     const float a10 = nf[1][sx], a01 = nf[sy][1], a11 = nf[sy][sx];
                     const double d10 = nb[1][sx], d01 = nb[sy][1], d11 = nb[sy][sx];
                     for (int m = c32.qbeg[q]; m < c32.qbeg[q + 1]; ++m) {
+                        if (cone && !((allow >> m) & 1ull)) continue;
                         const float w =
                             fmaf(c32.kw11[m], a11, fmaf(c32.kw01[m], a01, fmaf(c32.kw10[m], a10, c32.kap[m] * hf)));
                         if (w <= lim) {
@@ -1375,20 +1495,20 @@ __global__ void k_finalize(int64_t N, const double *__restrict__ in, double *__r
     }
 }
 
+// Dirichlet data of Eq. (dbc) in the sweep's precision: U_P^(0), with the
+// bound 1e6 and above (no finite value) mapped to the +inf sentinel.
+template <typename T>
+__global__ void k_dirichlet_data(int64_t N, const double *__restrict__ u0, T *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = u0[i] < kU0Bound ? (T)u0[i] : Num<T>::big();
+}
+
 // ---------------------------------------------------------- instantiation --
 
-template __global__ void k_init_values2d<float>(int64_t, const int8_t *, const double *, float, float *, float *);
-template __global__ void k_init_values2d<double>(int64_t, const int8_t *, const double *, double, double *, double *);
-template __global__ void k_value2d<float, true, 0>(Grid2, const int8_t *, const float *, float *, float *, TileSched,
-                                                   int, int, unsigned long long *, const CtlTable2<float>);
-template __global__ void k_value2d<float, true, 4>(Grid2, const int8_t *, const float *, float *, float *, TileSched,
-                                                   int, int, unsigned long long *, const CtlTable2<float>);
-template __global__ void k_value2d<float, true, 8>(Grid2, const int8_t *, const float *, float *, float *, TileSched,
-                                                   int, int, unsigned long long *, const CtlTable2<float>);
-template __global__ void k_value2d<double, true, 0>(Grid2, const int8_t *, const double *, double *, double *,
-                                                    TileSched, int, int, unsigned long long *, const CtlTable2<double>);
-template __global__ void k_value2d<double, true, 8>(Grid2, const int8_t *, const double *, double *, double *,
-                                                    TileSched, int, int, unsigned long long *, const CtlTable2<double>);
+template __global__ void k_init_values2d<float>(int64_t, const int8_t *, const double *, float, float *, float *,
+                                                 const double *);
+template __global__ void k_init_values2d<double>(int64_t, const int8_t *, const double *, double, double *, double *,
+                                                  const double *);
 template __global__ void k_value_wide2d<double>(Grid2, const int8_t *, const double *, const double *, double *,
                                                 float *, int, const CtlSelf2<double>);
 template __global__ void k_gather2d<float>(Grid2, const uint8_t *, const float *, const float *, float *, double *);
@@ -1399,12 +1519,12 @@ template __global__ void k_gather2d<double>(Grid2, const uint8_t *, const double
 // (the no-allocation entry point launches the same kernels as hjbp_solve).
 void launch_init_values2d_f64(int blocks, cudaStream_t st, int64_t N, const int8_t *code, double start, double *b0,
                               double *b1) {
-    k_init_values2d<double><<<blocks, 256, 0, st>>>(N, code, nullptr, start, b0, b1);
+    k_init_values2d<double><<<blocks, 256, 0, st>>>(N, code, nullptr, start, b0, b1, nullptr);
 }
 
 void launch_value2d_f64(int ntiles, cudaStream_t st, Grid2 g, const int8_t *code, const double *h, double *b0,
                         double *b1, TileSched s, int par, int rounds, const CtlTable2<double> &ct) {
-    k_value2d<double, true, 0><<<ntiles, 32, 0, st>>>(g, code, h, b0, b1, s, par, rounds, nullptr, ct);
+    k_value2d<double, 0, false><<<ntiles, 32, 0, st>>>(g, code, h, b0, b1, s, par, rounds, nullptr, ct, 1, nullptr);
 }
 
 void launch_gather2d_f64(int blocks, cudaStream_t st, Grid2 g, const uint8_t *latest, const double *b0,
@@ -1662,6 +1782,49 @@ ReachTable2 make_reach(const hjbp_plan &p) {
     return rt;
 }
 
+// AO3 cones (Sec. 6) over the positions of the quadrant-sorted table of
+// make_table; entry nc is the full set (nodes without a coarse feedback).
+Cone2 make_cones(const hjbp_plan &p, double *mean_size) {
+    Cone2 cn;
+    std::memset(&cn, 0, sizeof(cn));
+    const int nc = p.desc.n_controls;
+    cn.nc = nc;
+    std::vector<int> pos(nc);
+    int at = 0;
+    for (int q = 0; q < 4; ++q)
+        for (int m = 0; m < nc; ++m) {
+            const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+            if ((ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0) == q) pos[m] = at++;
+        }
+    const double cr = std::cos(3.14159265358979323846 / p.desc.reduce_r) - 1e-12;
+    double total = 0.0;
+    for (int a = 0; a <= nc; ++a) {
+        unsigned long long mask = 0;
+        uint32_t reach = 0;
+        for (int m = 0; m < nc; ++m) {
+            const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+            bool ok = true;
+            if (a < nc) {
+                double dot = 0.0;
+                dot += ax * p.controls[2 * a];
+                dot += ay * p.controls[2 * a + 1];
+                ok = dot >= cr;
+            }
+            if (!ok) continue;
+            mask |= 1ull << pos[m];
+            const double bx = std::fabs(ax), by = std::fabs(ay);
+            const unsigned need = (unsigned)(bx * (1.0 - by) > 0.0) | ((unsigned)((1.0 - bx) * by > 0.0) << 1) |
+                                  ((unsigned)(bx * by > 0.0) << 2);
+            if (need) reach |= (1u << need) << (8 * ((ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0)));
+        }
+        cn.mask[a] = mask;
+        cn.reach[a] = reach;
+        if (a < nc) total += (double)__builtin_popcountll(mask);
+    }
+    if (mean_size) *mean_size = total / nc;
+    return cn;
+}
+
 SpeedParams make_speed(const hjbp_plan &p) {
     SpeedParams sp;
     sp.kind = p.desc.speed;
@@ -1712,15 +1875,19 @@ float ms_between(const Ev &a, const Ev &b) {
 }
 
 // S* on the current codes (R14): reach from the targets, prune, repeat.
-int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, int cap, int64_t N) {
+int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, int cap, int64_t N,
+            const double *dterm = nullptr, const Cone2 *cone = nullptr) {
     const int passes = p.desc.tune[2] > 0 ? p.desc.tune[2] : 1;
     const ReachTable2 rt = make_reach(p);
     unsigned long long *removed = alloc_n<unsigned long long>(p, 1);
     int total = 0;
-    for (int round = 0; round < 64; ++round) {
+    // each round prunes at least one node or ends the loop, so it ends after at
+    // most N rounds
+    for (int64_t round = 0;; ++round) {
+        if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         RunResult rr = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
-            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt, passes);
+            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt, passes, dterm, p.astar, cone);
             ++p.stats.kernel_launches;
         });
         total += rr.launches;
@@ -1736,13 +1903,15 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
     return total;
 }
 
-// Value iteration from M on S* (R14), monotone, to the sup-norm tolerance.
+// Value iteration on S* (R14) to the sup-norm tolerance: monotone from M, or
+// plain from the warm start (AO1); dval: Dirichlet data (Eq. dbc) or NULL.
 template <typename T>
 RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, const double *fixed, T *b0, T *b1,
                   Sched &s, double tol, int cap, int rounds, T *out_t, double *out64, unsigned long long *updates,
-                  bool fine) {
+                  bool fine, const T *dval = nullptr, const double *warm = nullptr, const Cone2 *cone = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1;
-    k_init_values2d<T><<<grid_for(N), 256, 0, p.stream>>>(N, code, fixed, (T)kStartValue, b0, b1);
+    k_init_values2d<T><<<grid_for(N), 256, 0, p.stream>>>(N, code, fixed, (T)kStartValue, b0, b1, warm);
+    const int clamp = warm ? 0 : 1;
     ++p.stats.kernel_launches;
     const CtlTable2<T> ct = make_table<T>(p);
     const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
@@ -1755,16 +1924,32 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
             check_cuda(cudaEventCreate(&b), "event");
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
-        if (warps == 4)
+        const bool plain = clamp && !dval && !cone;  // the multi-warp variant has none of the options
+        if (cone && dval)
+            k_value2d<T, 0, true, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
+                                                                       ct, clamp, dval, p.astar, cone);
+        else if (cone)
+            k_value2d<T, 0, false, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
+                                                                        ct, clamp, nullptr, p.astar, cone);
+        else if (warps == 4 && plain)
             k_value2d_w<T, true, 4><<<s.ntiles, 128, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
-        else if (warps == 2)
+        else if (warps == 2 && plain)
             k_value2d_w<T, true, 2><<<s.ntiles, 64, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        else if (dval && ct.d4 && ct.ncls == 8)
+            k_value2d<T, 8, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                 clamp, dval);
+        else if (dval)
+            k_value2d<T, 0, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                 clamp, dval);
         else if (ct.d4 && ct.ncls == 8)
-            k_value2d<T, true, 8><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+            k_value2d<T, 8, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                  clamp, nullptr);
         else if (ct.d4 && ct.ncls == 4 && std::is_same<T, float>::value)
-            k_value2d<T, true, 4><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+            k_value2d<T, 4, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                  clamp, nullptr);
         else
-            k_value2d<T, true, 0><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+            k_value2d<T, 0, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                  clamp, nullptr);
         ++p.stats.kernel_launches;
         if (fine) ++p.stats.sweep_kernel_launches;
         if (timed) {
@@ -1799,7 +1984,7 @@ RunResult value_wide2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const d
                        double *b0, double *b1, double tol, int cap, double *out64) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     cudaStream_t st = p.stream;
-    k_init_values2d<double><<<grid_for(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1);
+    k_init_values2d<double><<<grid_for(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1, nullptr);
     ++p.stats.kernel_launches;
     const CtlSelf2<double> cs = make_self<double>(p);
     const int chunk = 16;
@@ -2023,17 +2208,40 @@ hjbp_status solve2d(hjbp_plan &p) {
         ++p.stats.kernel_launches;
     }
 
-    // ---- Step 3.2 (or the global solve): S*, then the value iteration
+    // ---- Step 3.2 (or the global solve): S*, then the value iteration.
+    // Patch boundaries: state constraints, or U_P^(0) (Eq. dbc); start: M, or
+    // U_P^(0) (AO1).
+    const bool dirichlet = p.patchy && (d.flags & HJBP_FLAG_DIRICHLET);
+    const double *warm = (p.patchy && (d.flags & HJBP_FLAG_WARM_START)) ? p.u0 : nullptr;
+    const double *d64 = dirichlet ? p.u0 : nullptr;
+    // AO3: control cones around the coarse feedback
+    Cone2 *cone = nullptr;
+    double cone_size = d.n_controls;
+    if (p.patchy && d.reduce_r > 0.0) {
+        const Cone2 hc = make_cones(p, &cone_size);
+        cone = static_cast<Cone2 *>(p.dev_alloc(sizeof(Cone2)));
+        check_cuda(cudaMemcpyAsync(cone, &hc, sizeof(Cone2), cudaMemcpyHostToDevice, st), "cones");
+        // the host copy goes out of scope: let the copy land first
+        check_cuda(cudaStreamSynchronize(st), "cones sync");
+    }
     Ev f0(st);
-    S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N);
+    S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N, d64, cone);
     Ev fr(st);
     RunResult rv;
     if (fp32) {
         float *b0 = alloc_n<float>(p, N), *b1 = alloc_n<float>(p, N);
-        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, true);
+        float *d32 = nullptr;
+        if (dirichlet) {
+            d32 = alloc_n<float>(p, N);
+            k_dirichlet_data<float><<<grid_for(N), 256, 0, st>>>(N, p.u0, d32);
+            ++p.stats.kernel_launches;
+        }
+        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, true,
+                            d32, warm, cone);
     } else {
         double *b0 = alloc_n<double>(p, N), *b1 = alloc_n<double>(p, N);
-        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates, true);
+        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates,
+                             true, d64, warm, cone);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
@@ -2062,7 +2270,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         int it = 0;
         for (; it < 8; ++it) {
             check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
-            k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ctf, ct);
+            k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ctf, ct, d64, p.astar, cone);
             ++p.stats.kernel_launches;
             check_cuda(cudaGetLastError(), "polish");
             std::swap(pa, pb);
@@ -2092,7 +2300,8 @@ hjbp_status solve2d(hjbp_plan &p) {
     check_cuda(cudaMemcpy(&hun, unreach, sizeof(hun), cudaMemcpyDeviceToHost), "unreachable");
     S.unreachable = (int64_t)hun;
     S.node_updates = (int64_t)hu;
-    S.node_control_updates = (int64_t)hu * d.n_controls;
+    // with AO3 a node evaluates its cone only (the mean cone size)
+    S.node_control_updates = (int64_t)((double)hu * cone_size + 0.5);
     S.n_patches = p.patchy ? R : 1;
     S.ms_setup = ms_between(e0, e1);
     S.ms_fine = ms_between(f0, f1);

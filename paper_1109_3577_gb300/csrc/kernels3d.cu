@@ -1059,7 +1059,10 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
     const ReachTable3 rt = make_reach3(p);
     unsigned long long *removed = alloc3<unsigned long long>(p, 1);
     int total = 0;
-    for (int round = 0; round < 64; ++round) {
+    // each round prunes at least one node or ends the loop, so it ends after at
+    // most N rounds
+    for (int64_t round = 0;; ++round) {
+        if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
             k_reach3d<<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt);

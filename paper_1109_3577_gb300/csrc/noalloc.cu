@@ -33,7 +33,8 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
                           float *h32, double *h64, double *fixed);
 __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
-                                                ReachTable2 rt, int passes);
+                                                ReachTable2 rt, int passes, const double *dterm,
+                                                const uint8_t *astar, const Cone2 *cone);
 __global__ void k_reach_prune(int64_t N, int8_t *code, const uint8_t *rch, unsigned long long *removed);
 __global__ void k_merge_targets(int64_t N, int8_t *code);
 __global__ void k_final_labels(int64_t N, const int8_t *code0, const int8_t *code, int8_t *label,
@@ -293,10 +294,12 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
 
     // S*: reach from the target, prune, repeat until nothing is pruned.
     bool conv = false;
-    for (int round = 0; round < 64; ++round) {
+    // each round prunes at least one node or ends the loop (at most N rounds)
+    for (int64_t round = 0;; ++round) {
+        if (round > N) return fail_static(HJBP_ECUDA, "reachability pruning did not settle");
         NA_CHECK(cudaMemsetAsync(rch, 0, (size_t)N, st));
         hjbp_status rs = run(st, g, s, ntiles, iota, 0.5f, 1 << 18, &conv, [&](int par) {
-            k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt, 2);
+            k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt, 2, nullptr, nullptr, nullptr);
         });
         if (rs != HJBP_OK) return rs;
         if (!conv) return fail_static(HJBP_ECUDA, "reachability sweep did not settle");

@@ -64,6 +64,22 @@ def test_create_rejects_bad_descriptors(lib):
         with pytest.raises(pkg.HjbpError) as ei:
             pkg.hjbp_create(d, 0, None)
         assert ei.value.status == 1, q
+    # patch-boundary options and control cones need a patchy solve; cones need
+    # r >= 1 and at most 64 controls in 2D
+    g = p.with_(n_coarse=None)
+    bad_opts = [
+        (g, {"flags": pkg.HJBP_FLAG_DIRICHLET}),
+        (g, {"flags": pkg.HJBP_FLAG_WARM_START}),
+        (g, {"reduce_r": 4.0}),
+        (p, {"reduce_r": 0.5}),
+        (p, {"reduce_r": float("nan")}),
+        (p.with_(controls=W.controls_2d(128)), {"reduce_r": 4.0}),
+    ]
+    for q, kw in bad_opts:
+        d, keep = pkg.desc_from_problem(q, **kw)
+        with pytest.raises(pkg.HjbpError) as ei:
+            pkg.hjbp_create(d, 0, None)
+        assert ei.value.status == 1, kw
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -1,0 +1,103 @@
+"""GPU parity for the Dirichlet patch boundary (Eq. dbc) and the add-ons AO1
+(warm start) and AO3 (control cones) of Sec. 6: the CUDA path through the C
+ABI against the FP64 oracle run with the same options, same tolerances as the
+basic patchy tests (max |u_gpu - u_oracle| <= 1e-4 max u on the reachable
+nodes, equal reachable sets)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as P
+
+    torch.cuda.set_device(0)
+    return P
+
+
+def _run(pkg, p, precision=None, **kw):
+    prec = pkg.HJBP_FP32_POLISH64 if precision is None else precision
+    with pkg.Plan(p, precision=prec, **kw) as plan:
+        st = plan.solve()
+        return {"status": st, "u": plan.values(), "labels": plan.labels(), "stats": plan.stats(),
+                "astar": plan.intermediate(pkg.HJBP_OUT_ASTAR)}
+
+
+def _assert_values(u, ref, rel=REL_TOL):
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(u)), (
+        f"reachable sets differ: gpu-only {np.sum(np.isfinite(u) & ~fin)}, oracle-only {np.sum(fin & ~np.isfinite(u))}")
+    err = np.abs(u[fin] - ref[fin]).max() if fin.any() else 0.0
+    assert err <= rel * ref[fin].max(), f"max err {err} vs bound {rel * ref[fin].max()}"
+    return err
+
+
+CASES = [(0, 129, 33, 4, 0.2), (1, 193, 25, 3, 0.1), (2, 257, 33, 4, 0.05)]
+
+
+@pytest.mark.parametrize("seed,n,nc,R,radius", CASES)
+def test_dirichlet_matches_oracle(pkg, seed, n, nc, R, radius):
+    p = W.sincos2d(seed, n=n, n_coarse=nc, n_targets=R, radius=radius)
+    r = _run(pkg, p, flags=pkg.HJBP_FLAG_DIRICHLET)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=True)
+    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    _assert_values(r["u"], ref.u)
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_warm_start_reaches_the_same_fixed_point(pkg, dirichlet):
+    """AO1 starts from U_P^(0) and runs the plain update; the fixed point is
+    the oracle's basic one."""
+    p = W.sincos2d(3, n=193, n_coarse=25, n_targets=4, radius=0.1)
+    flags = pkg.HJBP_FLAG_WARM_START | (pkg.HJBP_FLAG_DIRICHLET if dirichlet else 0)
+    r = _run(pkg, p, flags=flags)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet)
+    _assert_values(r["u"], ref.u)
+
+
+def test_dirichlet_warm_fp64(pkg):
+    p = W.sincos2d(4, n=129, n_coarse=17, n_targets=3, radius=0.2)
+    r = _run(pkg, p, precision=pkg.HJBP_FP64, flags=pkg.HJBP_FLAG_DIRICHLET | pkg.HJBP_FLAG_WARM_START)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=True)
+    err = _assert_values(r["u"], ref.u)
+    assert err < 1e-5
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+@pytest.mark.parametrize("r_fac", [2.0, 4.0])
+def test_control_cones_match_oracle(pkg, dirichlet, r_fac):
+    """AO3 changes the result; the reference is the oracle with the same cones
+    around the same coarse feedback (equal except at near-ties, checked)."""
+    p = W.sincos2d(5, n=193, n_coarse=25, n_targets=4, radius=0.1)
+    flags = pkg.HJBP_FLAG_DIRICHLET if dirichlet else 0
+    r = _run(pkg, p, flags=flags, reduce_r=r_fac)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet, reduce_r=r_fac)
+    tie = ref.gap < 1e-9 * np.maximum(1.0, np.where(np.isfinite(ref.u0), ref.u0, 1.0))
+    assert np.all((r["astar"] == ref.astar) | tie)
+    _assert_values(r["u"], ref.u)
+    # fewer controls per node than the full set
+    assert r["stats"]["node_control_updates"] < r["stats"]["node_updates"] * p.controls.shape[0]
+
+
+def test_control_cones_with_every_control(pkg):
+    """r = 1 keeps every control: the result equals the plain patchy solve."""
+    p = W.sincos2d(6, n=129, n_coarse=17, n_targets=3, radius=0.2)
+    a = _run(pkg, p)
+    b = _run(pkg, p, reduce_r=1.0)
+    _assert_values(b["u"], a["u"], rel=1e-6)
