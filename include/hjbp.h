@@ -121,6 +121,14 @@ typedef struct {
  * reachable set), only the iteration count changes.                         */
 #define HJBP_FLAG_DIRICHLET 2
 #define HJBP_FLAG_WARM_START 4
+/* HJBP_FLAG_CAUSAL_SWEEPS (patchy solves only): add-on AO2 of Sec. 6 in the
+ * form the tiled GPU iteration can use.  The paper orders the nodes of a
+ * patch so that the update follows the characteristics; here each 32x32 tile
+ * runs only the Gauss-Seidel directions along which the coarse feedback
+ * a*_{k~} of Step 2 carries information (a node depends on its foot
+ * x_i + k a*, so the sweep moves against a*), in Step 3.1 and Step 3.2.  The
+ * fixed point is the same; the solve stays deterministic.                    */
+#define HJBP_FLAG_CAUSAL_SWEEPS 8
 
 /* Device allocator hooks (optional).  alloc returns device memory of at least
  * `bytes` usable on `stream`, or NULL; release returns it.  ctx is passed back

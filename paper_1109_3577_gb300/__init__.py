@@ -7,6 +7,7 @@ raises.
 """
 from ._binding import (  # noqa: F401
     HJBP_FP32_POLISH64,
+    HJBP_FLAG_CAUSAL_SWEEPS,
     HJBP_FLAG_DIRICHLET,
     HJBP_FLAG_TIME_SWEEPS,
     HJBP_FLAG_WARM_START,

@@ -311,6 +311,7 @@ def torch_allocator() -> Allocator:
 HJBP_FLAG_TIME_SWEEPS = 1
 HJBP_FLAG_DIRICHLET = 2
 HJBP_FLAG_WARM_START = 4
+HJBP_FLAG_CAUSAL_SWEEPS = 8
 
 
 def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0, tune=None,

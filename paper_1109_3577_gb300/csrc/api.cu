@@ -108,8 +108,8 @@ static std::string validate(const hjbp_problem_desc *d) {
             if (!std::isfinite(d->targets[j * (d->dim + 1) + a])) return "target entry not finite";
     if (!(d->tol > 0.0)) return "tol must be positive";
     if (d->precision != HJBP_FP64 && d->precision != HJBP_FP32_POLISH64) return "unknown precision";
-    if ((d->flags & (HJBP_FLAG_DIRICHLET | HJBP_FLAG_WARM_START)) && d->n_coarse[0] == 0)
-        return "Dirichlet patch boundaries and the warm start need a patchy solve (n_coarse)";
+    if ((d->flags & (HJBP_FLAG_DIRICHLET | HJBP_FLAG_WARM_START | HJBP_FLAG_CAUSAL_SWEEPS)) && d->n_coarse[0] == 0)
+        return "Dirichlet patch boundaries, the warm start and causal sweeps need a patchy solve (n_coarse)";
     if (!(d->reduce_r == 0.0 || d->reduce_r >= 1.0) || !std::isfinite(d->reduce_r))
         return "reduce_r must be 0 or at least 1";
     if (d->reduce_r != 0.0 && d->n_coarse[0] == 0) return "reduce_r needs a patchy solve (n_coarse)";

@@ -171,6 +171,7 @@ struct TileSched {
     uint64_t *patch_hist; // per-launch mask of patches with an active tile
     float *res_hist;      // per-launch max change
     int *count_hist;      // per-launch number of active tiles
+    const uint8_t *dirs;  // per-tile Gauss-Seidel directions (bit d: run direction d); NULL: all
 };
 
 __device__ __forceinline__ int tile_of(const Grid2 &g, int x, int y) {

@@ -459,35 +459,48 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         for (int q = lane; q < ct.nc; q += 32) ctab[q] = Ctl4<T>{ct.kw10[q], ct.kw01[q], ct.kw11[q], ct.kap[q]};
     }
     // load: the parity of every halo node follows from its position in the
-    // 3x3 tile neighbourhood, so all value loads are independent
+    // 3x3 tile neighbourhood, so all loads are independent; the 34 x 34 halo
+    // image is spread over the lanes cell by cell and fully unrolled so that
+    // every load is in flight at once, then h (and a*) of the interior
     const unsigned pm = nbr_parities(g, s, tx, ty);
-    for (int c = lane; c < kTile + 2; c += 32) {
-        const int x = x0 - 1 + c;
-        const int px = (c == 0) ? 0 : (c == kTile + 1 ? 2 : 1);
-        const bool xin = x < g.n0 && x >= 1 && x <= g.n0 - 2;
-#pragma unroll 4
-        for (int r = 0; r < kTile + 2; ++r) {
-            const int y = y0 - 1 + r;
-            const int py = (r == 0) ? 0 : (r == kTile + 1 ? 2 : 1);
-            T v = Num<T>::big(), dv = Num<T>::big();
-            int8_t cd = kHard;
-            if (x < g.n0 && y < g.n1) {
-                const int64_t i = (int64_t)y * g.n0 + x;
-                cd = code[i];
-                const bool inner = xin && y >= 1 && y <= g.n1 - 2;
-                const bool odd = inner && ((pm >> (3 * py + px)) & 1u);
-                v = odd ? b1[i] : b0[i];
-                if constexpr (kDir) dv = dval[i];
+    {
+        constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + 31) / 32;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int q = lane + 32 * k;
+            if (q < kCells) {
+                const int r = q / kH, c = q - r * kH;
+                const int x = x0 - 1 + c, y = y0 - 1 + r;
+                T v = Num<T>::big(), dv = Num<T>::big();
+                int8_t cd = kHard;
+                if (x < g.n0 && y < g.n1) {
+                    const int64_t i = (int64_t)y * g.n0 + x;
+                    cd = code[i];
+                    const int px = (c == 0) ? 0 : (c == kH - 1 ? 2 : 1);
+                    const int py = (r == 0) ? 0 : (r == kH - 1 ? 2 : 1);
+                    const bool inner = x >= 1 && x <= g.n0 - 2 && y >= 1 && y <= g.n1 - 2;
+                    const bool odd = inner && ((pm >> (3 * py + px)) & 1u);
+                    v = odd ? b1[i] : b0[i];
+                    if constexpr (kDir) dv = dval[i];
+                }
+                sm.u[r][c] = v;
+                sm.c[r][c] = cd;
+                if constexpr (kDir) sm.d[r][c] = dv;
             }
-            sm.u[r][c] = v;
-            sm.c[r][c] = cd;
-            if constexpr (kDir) sm.d[r][c] = dv;
+        }
+        const int x = x0 + lane;
+#pragma unroll
+        for (int r = 0; r < kTile; ++r) {
+            const int y = y0 + r;
+            const bool in = x < g.n0 && y < g.n1;
+            sm.h[r][lane] = in ? h[(int64_t)y * g.n0 + x] : (T)0;
+            if constexpr (kCone) sa[r][lane] = in ? astar[(int64_t)y * g.n0 + x] : (uint8_t)kNoControl;
         }
     }
     __syncwarp();
     int nfree = 0;
     {
-        const int c = 1 + lane, x = x0 + lane;
+        const int c = 1 + lane;
         for (int r = 1; r <= kTile; ++r) {
             const int8_t cd = sm.c[r][c];
             unsigned m = 0;
@@ -504,18 +517,18 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                 ++nfree;
             }
             sm.mk[r - 1][lane] = (uint16_t)m;
-            const int y = y0 - 1 + r;
-            sm.h[r - 1][lane] = (m && x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
             if constexpr (kCone) {
-                const int a = (m && x < g.n0 && y < g.n1) ? astar[(int64_t)y * g.n0 + x] : kNoControl;
+                const int a = m ? sa[r - 1][lane] : kNoControl;
                 sa[r - 1][lane] = (uint8_t)(a < cone->nc ? a : cone->nc);
             }
             u0[r - 1][lane] = sm.u[r][c];
         }
     }
     __syncwarp();
+    const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
     for (int rd = 0; rd < rounds; ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
+            if (!((tdirs >> dir) & 1u)) continue;
             for (int st = 0; st < kTile; ++st) {
                 const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
                 const int c = (dir < 2) ? s1 : 1 + lane;
@@ -1032,11 +1045,61 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
     }
 }
 
+// Causal sweep directions per tile (AO2 on the tiled iteration).  A node
+// depends on its foot x_i + k a*, so information travels against a*: where
+// (at least a fraction frac of) the tile's feedback has a*_x < 0 the x sweep
+// runs in increasing x only (direction 0), where it has a*_x > 0 in
+// decreasing x only (direction 1), otherwise both; the same for y
+// (directions 2, 3).  Tiles without feedback run all four.
+struct DirCtl {
+    int8_t sx[kMaxControls], sy[kMaxControls];
+};
+
+__global__ void __launch_bounds__(32) k_tile_dirs2d(Grid2 g, const int8_t *__restrict__ code,
+                                                    const uint8_t *__restrict__ astar, const DirCtl dc, float frac,
+                                                    uint8_t *__restrict__ dirs) {
+    const int t = blockIdx.x;
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    const int lane = threadIdx.x, x = x0 + lane;
+    int xp = 0, xm = 0, yp = 0, ym = 0;
+    if (x <= g.n0 - 2)
+        for (int r = 0; r < kTile; ++r) {
+            const int y = y0 + r;
+            if (y > g.n1 - 2) break;
+            const int64_t i = (int64_t)y * g.n0 + x;
+            const int8_t c = code[i];
+            const uint8_t a = astar[i];
+            if (c < 0 || c >= kTargetBase || a == kNoControl) continue;
+            xp += dc.sx[a] > 0;
+            xm += dc.sx[a] < 0;
+            yp += dc.sy[a] > 0;
+            ym += dc.sy[a] < 0;
+        }
+    xp = warp_sum(xp);
+    xm = warp_sum(xm);
+    yp = warp_sum(yp);
+    ym = warp_sum(ym);
+    if (lane == 0) {
+        unsigned m = 0;
+        const int tx = xp + xm, ty = yp + ym;
+        if (tx == 0) m |= 0x3u;
+        else if ((float)xm >= frac * (float)tx) m |= 0x1u;
+        else if ((float)xp >= frac * (float)tx) m |= 0x2u;
+        else m |= 0x3u;
+        if (ty == 0) m |= 0xCu;
+        else if ((float)ym >= frac * (float)ty) m |= 0x4u;
+        else if ((float)yp >= frac * (float)ty) m |= 0x8u;
+        else m |= 0xCu;
+        dirs[t] = (uint8_t)m;
+    }
+}
+
 // --------------------------------------------------- Step 3.1: colours phi --
 
 // Controls in the caller's order for the colour transport: literal Q1
 // weights (FP64 residual) and the self-solved weights kw = kap w in FP32.
 struct PhiCtl {
+    int nc;
     int8_t sx[kMaxControls], sy[kMaxControls];
     double w00[kMaxControls], w10[kMaxControls], w01[kMaxControls], w11[kMaxControls];
     float kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls], kap[kMaxControls];
@@ -1094,7 +1157,8 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     const int64_t N = (int64_t)g.n0 * g.n1;
     __shared__ PhiSmem<RG, kSource> sm;
     const int lane = threadIdx.x;
-    for (int m = lane; m < kMaxControls; m += 32) {
+    const int ncu = pc->nc;
+    for (int m = lane; m < ncu; m += 32) {
         sm.kw10[m] = pc->kw10[m];
         sm.kw01[m] = pc->kw01[m];
         sm.kw11[m] = pc->kw11[m];
@@ -1104,51 +1168,63 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     }
     const unsigned pm = nbr_parities(g, s, tx, ty);
     unsigned alive = 0;   // colours with a nonzero value (or source) in the tile or its halo
-    for (int c = lane; c < kTile + 2; c += 32) {
-        const int x = x0 - 1 + c;
-        const int px = (c == 0) ? 0 : (c == kTile + 1 ? 2 : 1);
-        const bool xin = x >= 1 && x <= g.n0 - 2;
-#pragma unroll 2
-        for (int r = 0; r < kTile + 2; ++r) {
-            const int y = y0 - 1 + r;
-            const int py = (r == 0) ? 0 : (r == kTile + 1 ? 2 : 1);
-            const bool in = x < g.n0 && y < g.n1;
-            const bool inner = r >= 1 && r <= kTile && c >= 1 && c <= kTile;
-            const int64_t i = (int64_t)y * g.n0 + x;
-            int8_t cd = kHard;
-            if (in) {
-                cd = code[i];
-                const bool odd = xin && y >= 1 && y <= g.n1 - 2 && ((pm >> (3 * py + px)) & 1u);
-                const float *bs = odd ? b1 : b0;
+    {
+        // halo image cell by cell over the lanes, fully unrolled so that the
+        // loads are all in flight together; then a* (and the source) of the interior
+        constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + 31) / 32;
 #pragma unroll
-                for (int q = 0; q < RG; ++q) {
-                    const float v = bs[(int64_t)q * N + i];
-                    sm.u[q][r][c] = v;
-                    alive |= (unsigned)(v != 0.0f) << q;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < RG; ++q) sm.u[q][r][c] = 0.0f;
-            }
-            if (inner) {
-                sm.a[r - 1][c - 1] = in ? astar[i] : kNoControl;
-                if (kSource) {
+        for (int k = 0; k < kPer; ++k) {
+            const int q0 = lane + 32 * k;
+            if (q0 < kCells) {
+                const int r = q0 / kH, c = q0 - r * kH;
+                const int x = x0 - 1 + c, y = y0 - 1 + r;
+                const bool in = x < g.n0 && y < g.n1;
+                const int64_t i = (int64_t)y * g.n0 + x;
+                int8_t cd = kHard;
+                if (in) {
+                    cd = code[i];
+                    const int px = (c == 0) ? 0 : (c == kH - 1 ? 2 : 1);
+                    const int py = (r == 0) ? 0 : (r == kH - 1 ? 2 : 1);
+                    const bool odd = x >= 1 && x <= g.n0 - 2 && y >= 1 && y <= g.n1 - 2 &&
+                                     ((pm >> (3 * py + px)) & 1u);
+                    const float *bs = odd ? b1 : b0;
 #pragma unroll
                     for (int q = 0; q < RG; ++q) {
-                        const float v = in ? src[(int64_t)q * N + i] : 0.0f;
-                        sm.src[q][r - 1][c - 1] = v;
+                        const float v = bs[(int64_t)q * N + i];
+                        sm.u[q][r][c] = v;
                         alive |= (unsigned)(v != 0.0f) << q;
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) sm.u[q][r][c] = 0.0f;
+                }
+                sm.c[r][c] = cd;
+            }
+        }
+        const int x = x0 + lane;
+#pragma unroll
+        for (int r = 0; r < kTile; ++r) {
+            const int y = y0 + r;
+            const bool in = x < g.n0 && y < g.n1;
+            const int64_t i = (int64_t)y * g.n0 + x;
+            sm.a[r][lane] = in ? astar[i] : kNoControl;
+            if (kSource) {
+#pragma unroll
+                for (int q = 0; q < RG; ++q) {
+                    const float v = in ? src[(int64_t)q * N + i] : 0.0f;
+                    sm.src[q][r][lane] = v;
+                    alive |= (unsigned)(v != 0.0f) << q;
                 }
             }
-            sm.c[r][c] = cd;
         }
     }
     alive = __reduce_or_sync(0xffffffffu, alive);
     __syncwarp();
     if (alive) {
+        const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
         for (int rd = 0; rd < rounds; ++rd) {
             for (int dir = 0; dir < 4; ++dir) {
+                if (!((tdirs >> dir) & 1u)) continue;
                 for (int st = 0; st < kTile; ++st) {
                     const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
                     const int c = (dir < 2) ? s1 : 1 + lane;
@@ -2084,11 +2160,26 @@ hjbp_status solve2d(hjbp_plan &p) {
         k_feedback2d<<<grid_for(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, make_literal(p));
         ++p.stats.kernel_launches;
         check_cuda(cudaGetLastError(), "feedback");
+        // AO2: causal sweep directions per tile from the feedback (Step 3.1 and 3.2)
+        if ((d.flags & HJBP_FLAG_CAUSAL_SWEEPS) && sched.ntiles) {
+            DirCtl dc;
+            for (int m = 0; m < d.n_controls; ++m) {
+                const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+                dc.sx[m] = (int8_t)(ax > 1e-12 ? 1 : (ax < -1e-12 ? -1 : 0));
+                dc.sy[m] = (int8_t)(ay > 1e-12 ? 1 : (ay < -1e-12 ? -1 : 0));
+            }
+            uint8_t *dirs = alloc_n<uint8_t>(p, sched.ntiles);
+            k_tile_dirs2d<<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, dc, 0.9f, dirs);
+            ++p.stats.kernel_launches;
+            check_cuda(cudaGetLastError(), "tile directions");
+            sched.d.dirs = dirs;
+        }
         Ev e3(st);
         // ---- Step 3.1: colours phi^j, projection, Remark 3.1 fill
         {
             PhiCtl hpc;
             std::memset(&hpc, 0, sizeof(hpc));
+            hpc.nc = d.n_controls;
             for (int m = 0; m < d.n_controls; ++m) {
                 const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
                 const double bx = std::fabs(ax), by = std::fabs(ay);

@@ -101,3 +101,19 @@ def test_control_cones_with_every_control(pkg):
     a = _run(pkg, p)
     b = _run(pkg, p, reduce_r=1.0)
     _assert_values(b["u"], a["u"], rel=1e-6)
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_causal_sweeps_reach_the_same_fixed_point(pkg, dirichlet):
+    """AO2 on tiles changes only the Gauss-Seidel directions each tile runs;
+    values, labels and the phi fixed point are the oracle's, and the solve
+    stays deterministic."""
+    p = W.sincos2d(7, n=257, n_coarse=33, n_targets=4, radius=0.05)
+    flags = pkg.HJBP_FLAG_CAUSAL_SWEEPS | (pkg.HJBP_FLAG_DIRICHLET if dirichlet else 0)
+    r = _run(pkg, p, flags=flags)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet)
+    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    _assert_values(r["u"], ref.u)
+    again = _run(pkg, p, flags=flags)
+    assert np.array_equal(r["u"], again["u"]) and np.array_equal(r["labels"], again["labels"])
