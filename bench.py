@@ -229,7 +229,7 @@ def run_ours(args, rank, world, dist):
 
     # patch boundary and add-ons of Sec. 6 (defaults: state constraints, none)
     aflags = ((P.HJBP_FLAG_DIRICHLET if args.bc == "dirichlet" else 0) | (P.HJBP_FLAG_WARM_START if args.warm else 0)
-              | (P.HJBP_FLAG_CAUSAL_SWEEPS if args.causal else 0))
+              | (P.HJBP_FLAG_CAUSAL_SWEEPS if args.causal else 0) | (P.HJBP_FLAG_TILE_QUEUE if args.queue else 0))
     tune = [int(v) for v in args.tune.split(",")] if args.tune else None
     plan = P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS | aflags,
                   reduce_r=args.reduce_r, tune=tune)
@@ -324,6 +324,7 @@ def run_ours(args, rank, world, dist):
                        "tol": 1e-6, "seed": "rank", "precision": "FP32 sweeps, FP64 coarse/feedback/labels/polish",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
                        "patch_bc": args.bc, "warm_start": bool(args.warm), "causal_sweeps": bool(args.causal),
+                       "tile_queue": bool(args.queue),
                        "reduce_r": args.reduce_r, "tune": args.tune or "default"},
             "solves_per_s": world * 1e3 * args.steps / total_ms,
             "plain_sl_solves_per_s": 1e3 / statistics.mean(gms),
@@ -452,6 +453,8 @@ def main():
     ap.add_argument("--warm", action="store_true", help="add-on AO1: start Step 3.2 from U_P^(0)")
     ap.add_argument("--reduce-r", type=float, default=0.0, help="add-on AO3: control cones of half-angle pi/r")
     ap.add_argument("--tune", default="", help="launch shape: value rounds, phi rounds, reach passes, warps per tile")
+    ap.add_argument("--queue", action="store_true",
+                    help="value iteration as one persistent launch over a device tile queue")
     ap.add_argument("--causal", action="store_true",
                     help="add-on AO2 on tiles: per-tile Gauss-Seidel directions from the coarse feedback")
     args = ap.parse_args()

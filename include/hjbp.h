@@ -93,10 +93,12 @@ typedef struct {
     int precision;
     int max_sweeps;
     int flags;          /* HJBP_FLAG_* bits */
-    int tune[4];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
+    int tune[8];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
                            launch of the value sweep (2), [1] of the colour transport (3),
                            [2] passes per launch of the reachability sweep (1), [3] warps
-                           per 32x32 tile of the 2D value sweep (1; 1, 2 or 4) */
+                           per 32x32 tile of the 2D value sweep (1; 1, 2 or 4), [4] resident
+                           warps per SM of the tile-queue sweep (occupancy limit), [5..7]
+                           reserved (0) */
     double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
                            minimum of Step 3.2 at node i to the controls a with
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse
@@ -129,6 +131,14 @@ typedef struct {
  * x_i + k a*, so the sweep moves against a*), in Step 3.1 and Step 3.2.  The
  * fixed point is the same; the solve stays deterministic.                    */
 #define HJBP_FLAG_CAUSAL_SWEEPS 8
+/* HJBP_FLAG_TILE_QUEUE (2D): the value iteration of Step 3.2 (or of the
+ * global solve) runs as one persistent launch in which resident warps take
+ * 32x32 tiles from a device work queue; a tile whose boundary changed queues
+ * the neighbours that read it.  Values are updated in place, so the order of
+ * the updates, and the last bits of the result, depend on timing (the fixed
+ * point and the tolerance do not).  Ignored with HJBP_FLAG_WARM_START or
+ * reduce_r (their updates are not monotone or not tiled the same way).      */
+#define HJBP_FLAG_TILE_QUEUE 16
 
 /* Device allocator hooks (optional).  alloc returns device memory of at least
  * `bytes` usable on `stream`, or NULL; release returns it.  ctx is passed back

@@ -9,6 +9,7 @@ from ._binding import (  # noqa: F401
     HJBP_FP32_POLISH64,
     HJBP_FLAG_CAUSAL_SWEEPS,
     HJBP_FLAG_DIRICHLET,
+    HJBP_FLAG_TILE_QUEUE,
     HJBP_FLAG_TIME_SWEEPS,
     HJBP_FLAG_WARM_START,
     HJBP_FP64,

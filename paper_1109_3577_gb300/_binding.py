@@ -46,7 +46,7 @@ class Desc(C.Structure):
         ("precision", C.c_int),
         ("max_sweeps", C.c_int),
         ("flags", C.c_int),
-        ("tune", C.c_int * 4),
+        ("tune", C.c_int * 8),
         ("reduce_r", C.c_double),
     ]
 
@@ -312,6 +312,7 @@ HJBP_FLAG_TIME_SWEEPS = 1
 HJBP_FLAG_DIRICHLET = 2
 HJBP_FLAG_WARM_START = 4
 HJBP_FLAG_CAUSAL_SWEEPS = 8
+HJBP_FLAG_TILE_QUEUE = 16
 
 
 def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 0, flags: int = 0, tune=None,

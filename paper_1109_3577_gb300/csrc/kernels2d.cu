@@ -104,18 +104,18 @@ __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launc
         for (int dx = -1; dx <= 1; ++dx) {
             const int ux = tx + dx, uy = ty + dy;
             if (ux < 0 || uy < 0 || ux >= g.ntx || uy >= g.nty) continue;
-            if (s.chg[par][uy * g.ntx + ux] > tol) act = true;
+            if ((par ? s.chg[1] : s.chg[0])[uy * g.ntx + ux] > tol) act = true;
         }
     if (act) {
         const int k = atomicAdd(&s.count[par ^ 1], 1);
-        s.list[par ^ 1][k] = t;
+        (par ? s.list[0] : s.list[1])[k] = t;
     }
-    const float my = s.chg[par][t];
+    const float my = (par ? s.chg[1] : s.chg[0])[t];
     if (my > tol && s.tile_patch && s.patch_hist)
         atomicOr(reinterpret_cast<unsigned long long *>(&s.patch_hist[launch]),
                  (unsigned long long)s.tile_patch[t]);
     if (my > 0.f && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
-    s.chg[par ^ 1][t] = 0.f;
+    (par ? s.chg[0] : s.chg[1])[t] = 0.f;
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                                                 const Cone2 *__restrict__ cone = nullptr) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     __shared__ TileSmemV<T, kDir> sm;
@@ -576,9 +576,262 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     mc = warp_max(mc);
     const int nf = warp_sum(nfree);
     if (lane == 0) {
-        s.chg[par][t] = mc;
+        (par ? s.chg[1] : s.chg[0])[t] = mc;
         s.processed[t] = 1;
         if (updates) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+    }
+}
+
+// ------------------------------------------------- persistent tile queue --
+//
+// The wave launches above advance the front by one tile per launch and every
+// launch lasts as long as its slowest tile.  The persistent sweep instead keeps
+// one warp per resident block popping tiles from a device work queue: a tile
+// whose boundary nodes changed queues the neighbours that read them, a tile
+// that has not settled inside queues itself again, and the solve ends when no
+// tile is queued or running.  Values live in one buffer updated in place;
+// the update is monotone (u <- min(u, F(u))), so reading a neighbour's old or
+// new value is both safe, and the chaotic relaxation reaches the same fixed
+// point as the ordered one (R8).  Every wait is bounded: when one runs out the
+// kernel records an error and returns.
+
+struct TileQueue {
+    int *slot;                    // ring of cap entries, -1 when empty
+    unsigned *head, *tail;        // pop / push counters
+    int *state;                   // per tile: kQIdle, kQQueued, kQRunning, kQDirty
+    int *pending;                 // tiles queued or running
+    int *err;                     // nonzero: a wait ran out (which one)
+    unsigned long long *visits;   // tiles processed
+    int cap;
+};
+
+constexpr int kQIdle = 0, kQQueued = 1, kQRunning = 2, kQDirty = 3;
+constexpr long kSpinLimit = 1l << 22;
+
+__device__ __forceinline__ void q_enqueue(const TileQueue &q, int t) {
+    const unsigned pos = atomicAdd(q.tail, 1u) % (unsigned)q.cap;
+    volatile int *sl = q.slot + pos;
+    // the ring holds twice the tile count, so the slot is free unless its
+    // previous occupant's consumer has not read it yet
+    for (long it = 0; *sl != -1; ++it) {
+        if (it > kSpinLimit) {
+            atomicExch(q.err, 1);
+            return;
+        }
+        __nanosleep(64);
+    }
+    *sl = t;
+    __threadfence();
+}
+
+// Queue tile t unless it is queued already; a running tile is marked to run
+// again when it finishes.
+__device__ __forceinline__ void q_push(const TileQueue &q, int t) {
+    for (int it = 0; it < 1024; ++it) {
+        const int st = atomicAdd(q.state + t, 0);
+        if (st == kQIdle) {
+            if (atomicCAS(q.state + t, kQIdle, kQQueued) == kQIdle) {
+                atomicAdd(q.pending, 1);
+                q_enqueue(q, t);
+                return;
+            }
+        } else if (st == kQRunning) {
+            if (atomicCAS(q.state + t, kQRunning, kQDirty) == kQRunning) return;
+        } else {
+            return;
+        }
+    }
+    atomicExch(q.err, 2);
+}
+
+// Next tile to run; -1 when no tile is queued or running, -2 after an error.
+__device__ __forceinline__ int q_pop(const TileQueue &q) {
+    volatile unsigned *vh = q.head, *vt = q.tail;
+    volatile int *vp = q.pending, *ve = q.err;
+    unsigned nap = 32;   // idle back-off (ns), doubled up to 4 us: idle warps must not crowd the queue words
+    for (long it = 0; it < kSpinLimit; ++it) {
+        const unsigned h = *vh;
+        if (h < *vt) {
+            if (atomicCAS(q.head, h, h + 1u) == h) {
+                volatile int *sl = q.slot + (h % (unsigned)q.cap);
+                int t = *sl;
+                for (long w = 0; t == -1; ++w) {
+                    if (w > kSpinLimit) {
+                        atomicExch(q.err, 3);
+                        return -2;
+                    }
+                    __nanosleep(32);
+                    t = *sl;
+                }
+                *sl = -1;
+                atomicExch(q.state + t, kQRunning);
+                __threadfence();
+                return t;
+            }
+            continue;
+        }
+        if (*vp == 0) return -1;
+        if (*ve) return -2;
+        __nanosleep(nap);
+        nap = nap < 4096u ? 2u * nap : 4096u;
+    }
+    atomicExch(q.err, 4);
+    return -2;
+}
+
+__device__ __forceinline__ void q_finish(const TileQueue &q, int t) {
+    if (atomicCAS(q.state + t, kQRunning, kQIdle) == kQRunning) {
+        atomicSub(q.pending, 1);
+    } else {
+        // changed by a neighbour while it ran: run it again (still pending)
+        atomicExch(q.state + t, kQQueued);
+        q_enqueue(q, t);
+    }
+}
+
+template <typename T, int NCLS, bool kDir>
+__global__ void __launch_bounds__(32) k_value2d_async(Grid2 g, const int8_t *__restrict__ code,
+                                                      const T *__restrict__ h, T *u, TileQueue q, int rounds,
+                                                      float tol, unsigned long long *updates, const CtlTable2<T> ct,
+                                                      const T *__restrict__ dval) {
+    __shared__ TileSmemV<T, kDir> sm;
+    __shared__ T u0[kTile][kTile + 1];
+    const int lane = threadIdx.x;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = q_pop(q);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t < 0) break;
+        const int tx = t % g.ntx, ty = t / g.ntx;
+        const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
+        {
+            constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + 31) / 32;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int qq = lane + 32 * k;
+                if (qq < kCells) {
+                    const int r = qq / kH, c = qq - r * kH;
+                    const int x = x0 - 1 + c, y = y0 - 1 + r;
+                    T v = Num<T>::big(), dv = Num<T>::big();
+                    int8_t cd = kHard;
+                    if (x < g.n0 && y < g.n1) {
+                        const int64_t i = (int64_t)y * g.n0 + x;
+                        cd = code[i];
+                        v = __ldcg(u + i);   // other blocks write u: read through L2
+                        if constexpr (kDir) dv = dval[i];
+                    }
+                    sm.u[r][c] = v;
+                    sm.c[r][c] = cd;
+                    if constexpr (kDir) sm.d[r][c] = dv;
+                }
+            }
+            const int x = x0 + lane;
+#pragma unroll
+            for (int r = 0; r < kTile; ++r) {
+                const int y = y0 + r;
+                sm.h[r][lane] = (x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
+            }
+        }
+        __syncwarp();
+        int nfree = 0;
+        {
+            const int c = 1 + lane;
+            for (int r = 1; r <= kTile; ++r) {
+                const int8_t cd = sm.c[r][c];
+                unsigned m = 0;
+                if (cd >= 0 && cd < kTargetBase) {
+                    const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const int8_t qc = sm.c[r - 1 + dy][c - 1 + dx];
+                            m |= (unsigned)(qc == cd || qc == tg || qc == pr) << (3 * dy + dx);
+                        }
+                    m |= 0x8000u;
+                    ++nfree;
+                }
+                sm.mk[r - 1][lane] = (uint16_t)m;
+                u0[r - 1][lane] = sm.u[r][c];
+            }
+        }
+        __syncwarp();
+        float last = 0.f;   // largest change in the last round
+        for (int rd = 0; rd < rounds; ++rd) {
+            for (int dir = 0; dir < 4; ++dir) {
+                for (int st = 0; st < kTile; ++st) {
+                    const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+                    const int c = (dir < 2) ? s1 : 1 + lane;
+                    const int r = (dir < 2) ? 1 + lane : s1;
+                    const unsigned m = sm.mk[r - 1][c - 1];
+                    const bool active = (m & 0x8000u) != 0;
+                    const T old = sm.u[r][c];
+                    T nw = old;
+                    if (active) {
+                        const T best = sl_update_m<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
+                        if (best < nw) nw = best;
+                        if (rd == rounds - 1 && nw < old)
+                            last = fmaxf(last, old >= Num<T>::thresh() ? 3.0e38f : (float)(old - nw));
+                    }
+                    __syncwarp();
+                    if (active) sm.u[r][c] = nw;
+                    __syncwarp();
+                }
+            }
+        }
+        // store in place; change per side decides which neighbours run again
+        const int x = x0 + lane;
+        float colmax = 0.f, row1 = 0.f, rowL = 0.f;
+        const int rlast = min(kTile, g.n1 - 2 - y0 + 1);
+        for (int r = 1; r <= kTile; ++r) {
+            const int y = y0 - 1 + r;
+            if (y > g.n1 - 2) break;
+            if (x > g.n0 - 2) continue;
+            const T v = sm.u[r][1 + lane];
+            const T o = u0[r - 1][lane];
+            if (v != o) __stcg(u + (int64_t)y * g.n0 + x, v);
+            const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
+            const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+            colmax = fmaxf(colmax, d);
+            if (r == 1) row1 = d;
+            if (r == rlast) rowL = d;
+        }
+        __threadfence();
+        const unsigned bS = __ballot_sync(0xffffffffu, row1 > tol), bN = __ballot_sync(0xffffffffu, rowL > tol);
+        const unsigned bC = __ballot_sync(0xffffffffu, colmax > tol);
+        last = warp_max(last);
+        const int nf = warp_sum(nfree);
+        if (lane == 0) {
+            atomicAdd(q.visits, 1ull);
+            if (updates) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+            const bool w = tx > 0, e = tx < g.ntx - 1, sth = ty > 0, nth = ty < g.nty - 1;
+            if (w && (bC & 1u)) q_push(q, t - 1);
+            if (e && (bC >> 31)) q_push(q, t + 1);
+            if (sth && bS) q_push(q, t - g.ntx);
+            if (nth && bN) q_push(q, t + g.ntx);
+            if (w && sth && (bS & 1u)) q_push(q, t - g.ntx - 1);
+            if (e && sth && (bS >> 31)) q_push(q, t - g.ntx + 1);
+            if (w && nth && (bN & 1u)) q_push(q, t + g.ntx - 1);
+            if (e && nth && (bN >> 31)) q_push(q, t + g.ntx + 1);
+            if (last > tol) q_push(q, t);
+            q_finish(q, t);
+        }
+        __syncwarp();
+    }
+}
+
+// Every tile queued once, in index order.
+__global__ void k_queue_init(TileQueue q, int ntiles) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.cap; i += gridDim.x * blockDim.x) {
+        q.slot[i] = i < ntiles ? i : -1;
+        if (i < ntiles) q.state[i] = kQQueued;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *q.head = 0u;
+        *q.tail = (unsigned)ntiles;
+        *q.pending = ntiles;
+        *q.err = 0;
+        *q.visits = 0ull;
     }
 }
 
@@ -667,7 +920,7 @@ __global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__r
                                                       unsigned long long *updates, const CtlTable2<T> ct) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
     __shared__ TileSmemW<T> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -755,7 +1008,7 @@ __global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__r
     if (threadIdx.x == 0) {
         float mm = sm.red[0];
         for (int q = 1; q < W; ++q) mm = fmaxf(mm, sm.red[q]);
-        s.chg[par][t] = mm;
+        (par ? s.chg[1] : s.chg[0])[t] = mm;
         s.processed[t] = 1;
     }
 }
@@ -834,7 +1087,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                                                 const uint8_t *__restrict__ astar, const Cone2 *__restrict__ cone) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
     __shared__ uint8_t sr[kTile + 2][kTile + 4];
     __shared__ int8_t sc[kTile + 2][kTile + 4];
@@ -939,7 +1192,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     }
     const int nf = warp_sum(flips);
     if (lane == 0) {
-        s.chg[par][t] = nf > 0 ? 1.f : 0.f;
+        (par ? s.chg[1] : s.chg[0])[t] = nf > 0 ? 1.f : 0.f;
         s.processed[t] = 1;
     }
 }
@@ -1151,7 +1404,7 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
                                               int par, int rounds, const PhiCtl *__restrict__ pc) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     const int64_t N = (int64_t)g.n0 * g.n1;
@@ -1284,7 +1537,7 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     }
     mc = warp_max(mc);
     if (lane == 0) {
-        s.chg[par][t] = mc;
+        (par ? s.chg[1] : s.chg[0])[t] = mc;
         s.processed[t] = 1;
     }
 }
@@ -2055,6 +2308,87 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     return rr;
 }
 
+// The same solve with the persistent tile queue (monotone update from M; no
+// warm start, no control cones).  Returns launches = 1.
+template <typename T, int NCLS, bool kDir>
+void launch_async(hjbp_plan &p, int ntiles, const Grid2 &g, const int8_t *code, const T *h, T *u,
+                  const TileQueue &q, int rounds, float tol, unsigned long long *updates, const CtlTable2<T> &ct,
+                  const T *dval) {
+    int per_sm = 0, sms = 0, dev = 0;
+    check_cuda(cudaGetDevice(&dev), "device");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_value2d_async<T, NCLS, kDir>, 32, 0),
+               "occupancy");
+    // resident warps: the occupancy limit, or tune[4] per SM
+    const int want = p.desc.tune[4] > 0 ? std::min(p.desc.tune[4], std::max(1, per_sm)) : std::max(1, per_sm);
+    const int grid = std::max(1, std::min(ntiles, want * sms));
+    k_value2d_async<T, NCLS, kDir><<<grid, 32, 0, p.stream>>>(g, code, h, u, q, rounds, tol, updates, ct, dval);
+}
+
+template <typename T>
+RunResult value2d_async(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, T *b0, T *b1, Sched &s,
+                        double tol, int rounds, T *out_t, double *out64, unsigned long long *updates,
+                        const T *dval) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    cudaStream_t st = p.stream;
+    RunResult rr;
+    k_init_values2d<T><<<grid_for(N), 256, 0, st>>>(N, code, nullptr, (T)kStartValue, b0, b1, nullptr);
+    ++p.stats.kernel_launches;
+    const int nt = s.ntiles;
+    if (nt > 0) {
+        TileQueue q;
+        q.cap = 2 * nt;
+        q.slot = alloc_n<int>(p, q.cap);
+        q.head = alloc_n<unsigned>(p, 1);
+        q.tail = alloc_n<unsigned>(p, 1);
+        q.state = alloc_n<int>(p, nt);
+        q.pending = alloc_n<int>(p, 1);
+        q.err = alloc_n<int>(p, 1);
+        q.visits = alloc_n<unsigned long long>(p, 1);
+        k_queue_init<<<grid_for(q.cap), 256, 0, st>>>(q, nt);
+        ++p.stats.kernel_launches;
+        const CtlTable2<T> ct = make_table<T>(p);
+        const bool timed = p.desc.flags & HJBP_FLAG_TIME_SWEEPS;
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timed) {
+            check_cuda(cudaEventCreate(&a), "event");
+            check_cuda(cudaEventCreate(&b), "event");
+            check_cuda(cudaEventRecord(a, st), "event");
+        }
+        const float ftol = (float)tol;
+        if (dval && ct.d4 && ct.ncls == 8) launch_async<T, 8, true>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, dval);
+        else if (dval) launch_async<T, 0, true>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, dval);
+        else if (ct.d4 && ct.ncls == 8) launch_async<T, 8, false>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, nullptr);
+        else launch_async<T, 0, false>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, nullptr);
+        check_cuda(cudaGetLastError(), "queue sweep launch");
+        ++p.stats.kernel_launches;
+        ++p.stats.sweep_kernel_launches;
+        if (timed) check_cuda(cudaEventRecord(b, st), "event");
+        int herr = 0;
+        unsigned long long hv = 0;
+        check_cuda(cudaMemcpyAsync(&herr, q.err, sizeof(int), cudaMemcpyDeviceToHost, st), "queue err");
+        check_cuda(cudaMemcpyAsync(&hv, q.visits, sizeof(hv), cudaMemcpyDeviceToHost, st), "queue visits");
+        check_cuda(cudaStreamSynchronize(st), "queue sync");
+        if (timed) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            p.stats.ms_sweep_kernel += ms;
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+        if (herr) throw HjbpError{HJBP_ECUDA, "persistent tile sweep: a bounded wait ran out"};
+        rr.tile_visits = (int64_t)hv;
+        p.stats.sweep_tile_visits += (int64_t)hv;
+    }
+    rr.launches = 1;
+    rr.converged = true;
+    check_cuda(cudaMemsetAsync(s.d.latest, 0, std::max(1, nt), st), "latest");
+    k_gather2d<T><<<grid_for(N), 256, 0, st>>>(g, s.d.latest, b0, b1, out_t, out64);
+    ++p.stats.kernel_launches;
+    check_cuda(cudaGetLastError(), "gather");
+    return rr;
+}
+
 // Jacobi value iteration of a small grid with one warp per node (FP64).
 RunResult value_wide2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const double *h, const double *fixed,
                        double *b0, double *b1, double tol, int cap, double *out64) {
@@ -2315,6 +2649,8 @@ hjbp_status solve2d(hjbp_plan &p) {
         // the host copy goes out of scope: let the copy land first
         check_cuda(cudaStreamSynchronize(st), "cones sync");
     }
+    // persistent tile queue: monotone update only (no warm start, no cones)
+    const bool queue_ok = (d.flags & HJBP_FLAG_TILE_QUEUE) && !warm && !cone;
     Ev f0(st);
     S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N, d64, cone);
     Ev fr(st);
@@ -2327,12 +2663,18 @@ hjbp_status solve2d(hjbp_plan &p) {
             k_dirichlet_data<float><<<grid_for(N), 256, 0, st>>>(N, p.u0, d32);
             ++p.stats.kernel_launches;
         }
-        rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, true,
-                            d32, warm, cone);
+        if (queue_ok)
+            rv = value2d_async<float>(p, g, code, h32, b0, b1, sched, d.tol, vrounds, p.u32, nullptr, updates, d32);
+        else
+            rv = value2d<float>(p, g, code, h32, nullptr, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates,
+                                true, d32, warm, cone);
     } else {
         double *b0 = alloc_n<double>(p, N), *b1 = alloc_n<double>(p, N);
-        rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates,
-                             true, d64, warm, cone);
+        if (queue_ok)
+            rv = value2d_async<double>(p, g, code, h64, b0, b1, sched, d.tol, vrounds, nullptr, p.u_out, updates, d64);
+        else
+            rv = value2d<double>(p, g, code, h64, nullptr, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out,
+                                 updates, true, d64, warm, cone);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;

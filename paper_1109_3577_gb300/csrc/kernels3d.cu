@@ -154,21 +154,21 @@ __global__ void k_schedule3d(Grid3 g, TileSched s, int par, float tol, int launc
             for (int dx = -1; dx <= 1; ++dx) {
                 const int ux = tx + dx, uy = ty + dy, uz = tz + dz;
                 if (ux < 0 || uy < 0 || uz < 0 || ux >= g.ntx || uy >= g.nty || uz >= g.ntz) continue;
-                if (s.chg[par][(uz * g.nty + uy) * g.ntx + ux] > tol) {
+                if ((par ? s.chg[1] : s.chg[0])[(uz * g.nty + uy) * g.ntx + ux] > tol) {
                     act = true;
                     break;
                 }
             }
     if (act) {
         const int k = atomicAdd(&s.count[par ^ 1], 1);
-        s.list[par ^ 1][k] = t;
+        (par ? s.list[0] : s.list[1])[k] = t;
     }
-    const float my = s.chg[par][t];
+    const float my = (par ? s.chg[1] : s.chg[0])[t];
     if (my > tol && s.tile_patch && s.patch_hist)
         atomicOr(reinterpret_cast<unsigned long long *>(&s.patch_hist[launch]),
                  (unsigned long long)s.tile_patch[t]);
     if (my > 0.f && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
-    s.chg[par ^ 1][t] = 0.f;
+    (par ? s.chg[0] : s.chg[1])[t] = 0.f;
 }
 
 // Tile image in shared memory: u[z][y][x] with a one-node halo.
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                                                   const CtlTable3<T> ct) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     __shared__ Tile3<T> sm;
     load_tile3(g, s, code, b0, b1, x0, y0, z0, sm);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     if ((tid & 31) == 0 && updates && nfree)
         atomicAdd(updates, (unsigned long long)nfree * 6ull * (unsigned long long)rounds);
     if (tid == 0) {
-        s.chg[par][t] = mc;
+        (par ? s.chg[1] : s.chg[0])[t] = mc;
         s.processed[t] = 1;
     }
 }
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
                                                   uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     constexpr int E = kT3 + 2;
     __shared__ uint8_t sr[E][E][E + 2];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
     if (flips) atomicAdd(&flips_s, flips);
     __syncthreads();
     if (tid == 0) {
-        s.chg[par][t] = flips_s > 0 ? 1.f : 0.f;
+        (par ? s.chg[1] : s.chg[0])[t] = flips_s > 0 ? 1.f : 0.f;
         s.processed[t] = 1;
     }
 }
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                                                 int par, int rounds, const Ctl3 *__restrict__ pc) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
-    const int t = s.list[par][blockIdx.x];
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     __shared__ Phi3Smem<RG> sm;
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     }
     mc = block_max64(mc, sm.red);
     if (tid == 0) {
-        s.chg[par][t] = mc;
+        (par ? s.chg[1] : s.chg[0])[t] = mc;
         s.processed[t] = 1;
     }
 }

@@ -32,7 +32,7 @@ def _run(pkg, p, precision=None, **kw):
     with pkg.Plan(p, precision=prec, **kw) as plan:
         st = plan.solve()
         return {"status": st, "u": plan.values(), "labels": plan.labels(), "stats": plan.stats(),
-                "astar": plan.intermediate(pkg.HJBP_OUT_ASTAR)}
+                "astar": plan.intermediate(pkg.HJBP_OUT_ASTAR) if p.n_coarse else None}
 
 
 def _assert_values(u, ref, rel=REL_TOL):
@@ -117,3 +117,26 @@ def test_causal_sweeps_reach_the_same_fixed_point(pkg, dirichlet):
     _assert_values(r["u"], ref.u)
     again = _run(pkg, p, flags=flags)
     assert np.array_equal(r["u"], again["u"]) and np.array_equal(r["labels"], again["labels"])
+
+
+@pytest.mark.parametrize("mode", ["global", "patchy", "patchy_dirichlet", "patchy_fp64"])
+def test_tile_queue_matches_oracle(pkg, mode):
+    """The persistent tile-queue sweep updates values in place in an order set
+    by timing; the fixed point, and so the parity bound, are unchanged."""
+    p = W.sincos2d(8, n=257, n_coarse=33, n_targets=4, radius=0.05)
+    kw = {"flags": pkg.HJBP_FLAG_TILE_QUEUE}
+    if mode == "global":
+        p = p.with_(n_coarse=None)
+        ref = oracle.global_solve(p, tol=1e-12).u
+    else:
+        dirichlet = mode == "patchy_dirichlet"
+        if dirichlet:
+            kw["flags"] |= pkg.HJBP_FLAG_DIRICHLET
+        ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet).u
+    prec = pkg.HJBP_FP64 if mode == "patchy_fp64" else None
+    r = _run(pkg, p, precision=prec, **kw)
+    assert r["status"] == 0
+    err = _assert_values(r["u"], ref)
+    if mode == "patchy_fp64":
+        assert err < 1e-5
+    assert r["stats"]["sweep_tile_visits"] > 0
