@@ -86,7 +86,8 @@ template <typename T> struct CtlSelf2 {
     T kap[kMaxControls];
 };
 
-// Literal Q1 weights in the caller's control order, for Eq. (feedbackcontrol).
+// Literal Q1 weights in the caller's control order, for Eq. (feedbackcontrol),
+// in FP64 and rounded to FP32 (the FP32 copy only filters candidates).
 struct CtlLiteral2 {
     int nc;
     int8_t sx[kMaxControls];
@@ -95,6 +96,10 @@ struct CtlLiteral2 {
     double w10[kMaxControls];
     double w01[kMaxControls];
     double w11[kMaxControls];
+    float f00[kMaxControls];
+    float f10[kMaxControls];
+    float f01[kMaxControls];
+    float f11[kMaxControls];
 };
 
 // Support masks for the almost-sure reachability sweep: bit 0 corner 10,

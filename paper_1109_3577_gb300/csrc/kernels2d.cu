@@ -1281,17 +1281,56 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
                                                                          : Num<double>::big();
             }
         const double hh = h[i];
+        // Pass 1 in FP32 finds the minimum up to its rounding; pass 2 evaluates
+        // in FP64, in index order, only the controls whose FP32 value is within
+        // a bound of that error of the FP32 minimum, so the FP64 argmin (lowest
+        // index on ties, R10) is the one a full FP64 pass would find.  Values
+        // are at most 1e6 (R7) and the weights sum to 1, so each FP32 value
+        // is within 8 units in the last place of (h + max |U|) of its FP64
+        // value; the margin 2^-18 (h + max |U|) is twice that bound.
+        float nf[3][3];
+        float amax = 0.f;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const bool fin = nb[dy][dx] < Num<double>::thresh();
+                nf[dy][dx] = fin ? (float)nb[dy][dx] : Num<float>::big();
+                if (fin) amax = fmaxf(amax, fabsf((float)nb[dy][dx]));
+            }
+        const float hf = (float)hh;
+        // corner values by quadrant, selected without indexing (registers)
+        auto corners32 = [&](int m, float &a10, float &a01, float &a11) {
+            const bool px = cl.sx[m] > 0, py = cl.sy[m] > 0;
+            a10 = px ? nf[1][2] : nf[1][0];
+            a01 = py ? nf[2][1] : nf[0][1];
+            a11 = px ? (py ? nf[2][2] : nf[0][2]) : (py ? nf[2][0] : nf[0][0]);
+        };
+        float b32 = Num<float>::big();
+        for (int m = 0; m < cl.nc; ++m) {
+            float a10, a01, a11;
+            corners32(m, a10, a01, a11);
+            const float v = cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf;
+            b32 = v < b32 ? v : b32;
+        }
         double best = Num<double>::big();
         int arg = kNoControl;
-        for (int m = 0; m < cl.nc; ++m) {
-            const int sx = cl.sx[m] > 0 ? 2 : 0, sy = cl.sy[m] > 0 ? 2 : 0;
-            double a10, a01, a11;
-            if (sx) { a10 = nb[1][2]; } else { a10 = nb[1][0]; }
-            if (sy) { a01 = nb[2][1]; a11 = sx ? nb[2][2] : nb[2][0]; } else { a01 = nb[0][1]; a11 = sx ? nb[0][2] : nb[0][0]; }
-            const double v = cl.w00[m] * nb[1][1] + cl.w10[m] * a10 + cl.w01[m] * a01 + cl.w11[m] * a11 + hh;
-            if (v < best) {
-                best = v;
-                arg = m;
+        if (b32 < Num<float>::thresh()) {
+            const float lim = b32 + ldexpf(hf + amax, -18);
+            for (int m = 0; m < cl.nc; ++m) {
+                float a10, a01, a11;
+                corners32(m, a10, a01, a11);
+                const float v32 = cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf;
+                if (v32 > lim) continue;
+                const bool px = cl.sx[m] > 0, py = cl.sy[m] > 0;
+                const double d10 = px ? nb[1][2] : nb[1][0];
+                const double d01 = py ? nb[2][1] : nb[0][1];
+                const double d11 = px ? (py ? nb[2][2] : nb[0][2]) : (py ? nb[2][0] : nb[0][0]);
+                const double v = cl.w00[m] * nb[1][1] + cl.w10[m] * d10 + cl.w01[m] * d01 + cl.w11[m] * d11 + hh;
+                if (v < best) {
+                    best = v;
+                    arg = m;
+                }
             }
         }
         astar[i] = best < Num<double>::thresh() ? (uint8_t)arg : kNoControl;
@@ -1523,16 +1562,20 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     const float *old = cur ? b1 : b0;
     float mc = 0.f;
     const int x = x0 + lane;
-    for (int r = 1; r <= kTile; ++r) {
-        const int y = y0 - 1 + r;
-        if (y > g.n1 - 2) break;
-        if (x > g.n0 - 2) continue;
-        const int64_t i = (int64_t)y * g.n0 + x;
+    // predicated and unrolled so that the reads of the previous values are
+    // all in flight together
 #pragma unroll
-        for (int q = 0; q < RG; ++q) {
-            const float v = sm.u[q][r][1 + lane];
-            dst[(int64_t)q * N + i] = v;
-            if ((alive >> q) & 1u) mc = fmaxf(mc, fabsf(v - old[(int64_t)q * N + i]));
+    for (int q = 0; q < RG; ++q) {
+        const bool live = (alive >> q) & 1u;
+#pragma unroll 16
+        for (int r = 1; r <= kTile; ++r) {
+            const int y = y0 - 1 + r;
+            if (y <= g.n1 - 2 && x <= g.n0 - 2) {
+                const int64_t i = (int64_t)q * N + (int64_t)y * g.n0 + x;
+                const float v = sm.u[q][r][1 + lane];
+                dst[i] = v;
+                if (live) mc = fmaxf(mc, fabsf(v - old[i]));
+            }
         }
     }
     mc = warp_max(mc);
@@ -2094,6 +2137,10 @@ CtlLiteral2 make_literal(const hjbp_plan &p) {
         cl.w10[m] = bx * (1.0 - by);
         cl.w01[m] = (1.0 - bx) * by;
         cl.w11[m] = bx * by;
+        cl.f00[m] = (float)cl.w00[m];
+        cl.f10[m] = (float)cl.w10[m];
+        cl.f01[m] = (float)cl.w01[m];
+        cl.f11[m] = (float)cl.w11[m];
     }
     return cl;
 }
