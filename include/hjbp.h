@@ -210,6 +210,22 @@ hjbp_status hjbp_get_labels(hjbp_plan *plan, int8_t *host_out);
 enum { HJBP_OUT_UCOARSE = 0, HJBP_OUT_U0 = 1, HJBP_OUT_ASTAR = 2, HJBP_OUT_PHI = 3, HJBP_OUT_U32 = 4 };
 hjbp_status hjbp_get_intermediate(hjbp_plan *plan, int which, void *host_out, size_t bytes);
 
+/* Waits for the plan's stream and returns the status of its last hjbp_solve
+ * (HJBP_ESTATE if it was never solved).  hjbp_solve itself returns once its
+ * stream work is done; hjbp_sync serves callers that hold only the plan.    */
+hjbp_status hjbp_sync(hjbp_plan *plan);
+
+/* Start values for the value iteration of the following solves (Step 3.2, or
+ * the global solve): N doubles in node order (index i = i1 + n1 i2), each
+ * >= 0 or +INFINITY.  On S* the iteration starts from them where they are
+ * finite (from the bound 1e6 elsewhere) and runs the plain update
+ * u <- F(u); the fixed point on S* is unique (Sec. 2.2 with R14), so the
+ * result is the same as from the default start, only the work changes: a
+ * resume from an earlier solution, or add-on AO1 of Sec. 6 with the caller's
+ * own guess.  Copied into the plan; NULL clears them.  2D plans only
+ * (HJBP_EINVAL otherwise).                                                 */
+hjbp_status hjbp_set_initial(hjbp_plan *plan, const double *u_init);
+
 /* Borrowed device pointers (valid until destroy): FP64 values and int8 labels. */
 hjbp_status hjbp_get_device_views(hjbp_plan *plan, const double **u, const int8_t **labels);
 

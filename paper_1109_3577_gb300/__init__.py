@@ -32,7 +32,9 @@ from ._binding import (  # noqa: F401
     hjbp_get_stats,
     hjbp_get_values,
     hjbp_last_error,
+    hjbp_set_initial,
     hjbp_solve,
+    hjbp_sync,
     hjbp_solve_global2d_noalloc,
     HJBP_NOALLOC_MAX_NODES,
     hjbp_server_create,

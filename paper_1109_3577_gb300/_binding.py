@@ -121,6 +121,10 @@ def library():
         lib.hjbp_create.restype = C.c_int
         lib.hjbp_solve.argtypes = [vp]
         lib.hjbp_solve.restype = C.c_int
+        lib.hjbp_sync.argtypes = [vp]
+        lib.hjbp_sync.restype = C.c_int
+        lib.hjbp_set_initial.argtypes = [vp, vp]
+        lib.hjbp_set_initial.restype = C.c_int
         lib.hjbp_get_values.argtypes = [vp, vp]
         lib.hjbp_get_values.restype = C.c_int
         lib.hjbp_get_labels.argtypes = [vp, vp]
@@ -187,6 +191,23 @@ def hjbp_solve(plan: int) -> int:
     if st not in (HJBP_OK, HJBP_ENOCONV):
         _check(st)
     return st
+
+
+def hjbp_sync(plan: int) -> int:
+    """Status of the plan's last solve (OK or ENOCONV); raises otherwise."""
+    st = library().hjbp_sync(C.c_void_p(plan))
+    if st not in (HJBP_OK, HJBP_ENOCONV):
+        _check(st)
+    return st
+
+
+def hjbp_set_initial(plan: int, u_init: Optional[np.ndarray]) -> None:
+    """Start values of the value iteration (N doubles, >= 0 or +inf); None clears."""
+    if u_init is None:
+        _check(library().hjbp_set_initial(C.c_void_p(plan), None))
+        return
+    u = np.ascontiguousarray(u_init, dtype=np.float64)
+    _check(library().hjbp_set_initial(C.c_void_p(plan), u.ctypes.data_as(C.c_void_p)))
 
 
 def hjbp_get_values(plan: int, out: np.ndarray) -> None:
@@ -383,6 +404,14 @@ class Plan:
     def solve(self) -> int:
         self.status = hjbp_solve(self.handle)
         return self.status
+
+    def sync(self) -> int:
+        return hjbp_sync(self.handle)
+
+    def set_initial(self, u_init: Optional[np.ndarray]) -> None:
+        if u_init is not None and np.asarray(u_init).size != self.N:
+            raise ValueError("start values need one entry per fine node")
+        hjbp_set_initial(self.handle, u_init)
 
     def values(self) -> np.ndarray:
         out = np.empty(self.N, np.float64)

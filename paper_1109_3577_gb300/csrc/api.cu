@@ -207,15 +207,43 @@ hjbp_status hjbp_solve(hjbp_plan *p) {
         }
         hjbp::check_cuda(cudaStreamSynchronize(p->stream), "solve");
         p->solved = true;
+        p->last_status = s;
         if (s == HJBP_ENOCONV) hjbp::set_last_error("sweep cap reached before convergence");
         return s;
     } catch (const HjbpError &e) {
         cudaStreamSynchronize(p->stream);
         cudaGetLastError();
+        p->last_status = e.status;
         return fail(e.status, e.msg);
+    } catch (const std::bad_alloc &) {
+        p->last_status = HJBP_ENOMEM;
+        return fail(HJBP_ENOMEM, "host allocation failed");
+    }
+}
+
+hjbp_status hjbp_sync(hjbp_plan *p) {
+    if (!p) return fail(HJBP_EINVAL, "plan is NULL");
+    const cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(HJBP_ECUDA, cudaGetErrorString(e));
+    if (!p->solved && p->last_status == HJBP_ESTATE) return fail(HJBP_ESTATE, "plan has not been solved");
+    return p->last_status;
+}
+
+hjbp_status hjbp_set_initial(hjbp_plan *p, const double *u_init) {
+    if (!p) return fail(HJBP_EINVAL, "plan is NULL");
+    if (p->desc.dim != 2) return fail(HJBP_EINVAL, "start values are implemented for 2D plans");
+    try {
+        if (!u_init) {
+            p->init.clear();
+            return HJBP_OK;
+        }
+        for (int64_t i = 0; i < p->N; ++i)
+            if (std::isnan(u_init[i]) || u_init[i] < 0.0) return fail(HJBP_EINVAL, "start values must be >= 0 or +inf");
+        p->init.assign(u_init, u_init + p->N);
     } catch (const std::bad_alloc &) {
         return fail(HJBP_ENOMEM, "host allocation failed");
     }
+    return HJBP_OK;
 }
 
 static hjbp_status copy_out(hjbp_plan *p, void *host, const void *dev, size_t bytes) {

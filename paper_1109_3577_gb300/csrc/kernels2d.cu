@@ -2685,6 +2685,12 @@ hjbp_status solve2d(hjbp_plan &p) {
     // U_P^(0) (AO1).
     const bool dirichlet = p.patchy && (d.flags & HJBP_FLAG_DIRICHLET);
     const double *warm = (p.patchy && (d.flags & HJBP_FLAG_WARM_START)) ? p.u0 : nullptr;
+    if (!p.init.empty()) {
+        // the caller's start values (hjbp_set_initial), +inf mapped above the bound
+        double *iv = alloc_n<double>(p, N);
+        check_cuda(cudaMemcpyAsync(iv, p.init.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "start values");
+        warm = iv;
+    }
     const double *d64 = dirichlet ? p.u0 : nullptr;
     // AO3: control cones around the coarse feedback
     Cone2 *cone = nullptr;

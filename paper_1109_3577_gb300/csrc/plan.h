@@ -23,7 +23,9 @@ struct hjbp_plan {
     hjbp_allocator alloc{};
     bool has_alloc = false;
     bool solved = false;
+    hjbp_status last_status = HJBP_ESTATE;
     hjbp_stats stats{};
+    std::vector<double> init;       // caller's start values (hjbp_set_initial), empty: none
 
     // --- device arrays owned by the plan ---
     struct Block {

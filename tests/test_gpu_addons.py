@@ -140,3 +140,28 @@ def test_tile_queue_matches_oracle(pkg, mode):
     if mode == "patchy_fp64":
         assert err < 1e-5
     assert r["stats"]["sweep_tile_visits"] > 0
+
+
+def test_set_initial_resume_and_sync(pkg):
+    """hjbp_set_initial: resuming from the converged values converges at once
+    to the same values; a start from the oracle's solution plus noise reaches
+    the oracle's fixed point too; hjbp_sync reports the last solve."""
+    p = W.sincos2d(9, n=129, n_coarse=17, n_targets=3, radius=0.2)
+    ref = oracle.patchy_solve(p, tol=1e-12).u
+    with pkg.Plan(p) as plan:
+        assert plan.solve() == 0
+        u1 = plan.values()
+        n1 = plan.stats()["node_updates"]
+        plan.set_initial(u1)
+        assert plan.solve() == 0 and plan.sync() == 0
+        u2 = plan.values()
+        assert plan.stats()["node_updates"] < n1
+        _assert_values(u2, ref)
+        rng = np.random.default_rng(0)
+        noisy = np.where(np.isfinite(ref), ref * (1.0 + 0.05 * rng.standard_normal(ref.size)).clip(0.5), np.inf)
+        plan.set_initial(noisy)
+        assert plan.solve() == 0
+        _assert_values(plan.values(), ref)
+        plan.set_initial(None)
+        assert plan.solve() == 0
+        _assert_values(plan.values(), ref)
