@@ -34,7 +34,7 @@ from typing import Optional
 
 import numpy as np
 
-from workloads import SPEED_KINDS, Problem
+from workloads import DYN_KINDS, SPEED_KINDS, TARGET_KINDS, Problem
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hjbp_oracle.c")
@@ -57,6 +57,10 @@ class _Problem(C.Structure):
         ("controls", C.POINTER(C.c_double)),
         ("n_targets", C.c_int),
         ("targets", C.POINTER(C.c_double)),
+        ("dyn_kind", C.c_int),
+        ("drift", C.c_double * 4),
+        ("target_kind", C.c_int),
+        ("n_parts", C.c_int),
     ]
 
 
@@ -150,6 +154,11 @@ class _Desc:
         s.controls = _ptr(self.controls, C.c_double)
         s.n_targets = self.targets.shape[0]
         s.targets = _ptr(self.targets, C.c_double)
+        s.dyn_kind = DYN_KINDS[p.dyn]
+        for i in range(4):
+            s.drift[i] = float(p.drift[i])
+        s.target_kind = TARGET_KINDS[p.target_kind]
+        s.n_parts = int(p.n_parts)
         self.s = s
         self.N = int(np.prod([s.n[d] for d in range(p.dim)]))
         self.shape = tuple(int(s.n[d]) for d in reversed(range(p.dim)))  # (n3, n2, n1) / (n2, n1)
@@ -291,7 +300,7 @@ def patchy_solve(p: Problem, order: int = 1, keep_phi: bool = False, tol: Option
         raise ValueError("patchy_solve needs n_coarse")
     d = _Desc(p)
     dc = _Desc(p, n=p.n_coarse)
-    N, R = d.N, p.n_targets
+    N, R = d.N, p.n_patches
     u = np.zeros(N)
     lab = np.zeros(N, np.int8)
     uc = np.zeros(dc.N)

@@ -99,6 +99,24 @@
  *       exactly the angle pi/r is kept whatever the rounding of the dot
  *       product.  Nodes without a* keep the full set.  Labels (Step 3.1) do
  *       not change.
+ *   R20 Dynamics other than c(x) a (Table 1): with |h f| = k (R1) the foot
+ *       is x_i + k f/|f| and h_{i,a} = k/|f(x_i,a)|.  For the drift dynamics
+ *       f = s a + w (Zermelo) both are fixed per control; components of f/|f|
+ *       below 1e-15 are snapped to 0.  A control with |f| <= 1e-15 is not
+ *       admissible.
+ *   R21 A node where the speed c(x) is at most 1e-12 (the line where the Fan
+ *       field vanishes) cannot move: it is treated like the ghost ring (+inf,
+ *       colour 0, label -1) unless it is a target node.
+ *   R22 Target split into R parts (Sec. 3, "the target is divided in R
+ *       parts"; Table 1): one ball split into R equal angular sectors, part
+ *       j = floor(R theta / (2 pi) + 1e-9) mod R with theta = atan2 of the
+ *       offset from the centre in [0, 2 pi); or the slab |x_1 - v| <= r (a
+ *       line target of half-width r) split into R equal pieces along x_2 over
+ *       the box, part j = floor(R (x_2 - lo_2) / (hi_2 - lo_2) + 1e-9),
+ *       clamped.  The 1e-9 puts nodes exactly on a sector boundary into the
+ *       upper part whatever the last bit of atan2.  On the coarse grid (R6) the
+ *       ball or slab is widened by k~ sqrt(d)/2 with boundary value
+ *       max(0, distance - r)/c(x).
  */
 #include <math.h>
 #include <stdint.h>
@@ -120,6 +138,12 @@ typedef struct {
     const double *controls;    /* n_controls x dim unit vectors */
     int n_targets;
     const double *targets;     /* n_targets x (dim + 1): centre, radius */
+    int dyn_kind;              /* 0: f = c(x) a; 1: f = s a + w (R20) */
+    double drift[4];           /* dyn_kind 1: s, w_1, w_2, w_3 */
+    int target_kind;           /* 0: each row a ball and a part; 1: row 0 a ball in
+                                  n_parts sectors; 2: row 0 = (v, ., r) the slab
+                                  |x_1 - v| <= r in n_parts pieces (R22) */
+    int n_parts;               /* parts of target kinds 1 and 2 */
 } og_problem;
 
 typedef struct {
@@ -192,6 +216,9 @@ double og_speed(const og_problem *p, const double x[3]) {
         return 1.0 + q[0] * sin(2.0 * OG_PI * x[0]) * cos(2.0 * OG_PI * x[1]);
     case 2:
         return 1.0 + q[0] * sin(OG_PI * x[0]) * sin(OG_PI * x[1]) * sin(OG_PI * x[2]);
+    case 4:
+        /* Fan (Table 1): c(x) = |q0 + q1 x1 + q2 x2 + q3 x3| */
+        return fabs(q[0] + q[1] * x[0] + q[2] * x[1] + q[3] * x[2]);
     case 3: {
         /* g(x) = sum_{p,q=0..3} a_pq cos(pi p x1/2 + th_pq) cos(pi q x2/2 + ps_pq) / sum |a_pq| */
         double g = 0.0, norm = 0.0;
@@ -208,9 +235,56 @@ double og_speed(const og_problem *p, const double x[3]) {
     }
 }
 
-/* Node kinds (R4, R5): target part (>= 0) or -1; kind FREE / TARGET / GHOST.
-   h_i = k / c(x_i) on every node (R1).  radius_extra enlarges every target
-   ball (R6, used on the coarse grid). */
+/* Number of patches R: one per target row, or n_parts for a split target. */
+int og_parts(const og_problem *p) {
+    return p->target_kind == 0 ? p->n_targets : p->n_parts;
+}
+
+/* Target part of the point x (R5, R22), -1 outside the target; the balls or
+   slab widened by extra (R6).  *gap gets the distance from x to the
+   un-widened target (0 inside). */
+static int og_target_part(const og_problem *p, const double x[3], double extra, double *gap) {
+    const int R = og_parts(p);
+    if (p->target_kind == 0) {
+        for (int j = 0; j < p->n_targets; ++j) {
+            const double *t = p->targets + (size_t)j * (p->dim + 1);
+            double r2 = 0.0;
+            for (int d = 0; d < p->dim; ++d) r2 += (x[d] - t[d]) * (x[d] - t[d]);
+            const double dist = sqrt(r2);
+            if (dist <= t[p->dim] + extra) {
+                if (gap) *gap = dist > t[p->dim] ? dist - t[p->dim] : 0.0;
+                return j;
+            }
+        }
+        return -1;
+    }
+    const double *t = p->targets;
+    if (p->target_kind == 1) {
+        const double dx = x[0] - t[0], dy = x[1] - t[1];
+        const double dist = sqrt(dx * dx + dy * dy);
+        if (!(dist <= t[p->dim] + extra)) return -1;
+        double th = atan2(dy, dx);
+        if (th < 0.0) th += 2.0 * OG_PI;
+        int j = (int)floor((double)R * th / (2.0 * OG_PI) + 1e-9);
+        if (j >= R) j -= R;
+        if (j < 0) j = 0;
+        if (gap) *gap = dist > t[p->dim] ? dist - t[p->dim] : 0.0;
+        return j;
+    }
+    /* slab |x_1 - v| <= r split along x_2 */
+    const double dist = fabs(x[0] - t[0]);
+    if (!(dist <= t[p->dim] + extra)) return -1;
+    const double lo1 = p->lo[1], hi1 = p->lo[1] + (double)(p->n[1] - 1) * p->k;
+    int j = (int)floor((double)R * (x[1] - lo1) / (hi1 - lo1) + 1e-9);
+    if (j >= R) j = R - 1;
+    if (j < 0) j = 0;
+    if (gap) *gap = dist > t[p->dim] ? dist - t[p->dim] : 0.0;
+    return j;
+}
+
+/* Node kinds (R4, R5, R21, R22): target part (>= 0) or -1; kind FREE /
+   TARGET / GHOST.  h_i = k / c(x_i) on every node (R1); +inf where the node
+   cannot move.  radius_extra widens the target (R6, on the coarse grid). */
 int og_setup(const og_problem *p, double radius_extra, unsigned char *kind, int *part, double *h) {
     int64_t N = og_count(p);
     for (int64_t i = 0; i < N; ++i) {
@@ -218,22 +292,41 @@ int og_setup(const og_problem *p, double radius_extra, unsigned char *kind, int 
         double x[3];
         og_index3(p, i, idx);
         og_coords(p, idx, x);
-        int pj = -1;
-        for (int j = 0; j < p->n_targets && pj < 0; ++j) {
-            const double *t = p->targets + (size_t)j * (p->dim + 1);
-            double r2 = 0.0;
-            for (int d = 0; d < p->dim; ++d) r2 += (x[d] - t[d]) * (x[d] - t[d]);
-            double rad = t[p->dim] + radius_extra;
-            if (sqrt(r2) <= rad) pj = j;
-        }
+        int pj = og_target_part(p, x, radius_extra, NULL);
         int ring = 0;
         for (int d = 0; d < p->dim; ++d)
             if (idx[d] == 0 || idx[d] == p->n[d] - 1) ring = 1;
+        const double c = og_speed(p, x);
+        const int stopped = !(c > 1e-12);   /* R21 */
         part[i] = pj;
-        kind[i] = (pj >= 0) ? OG_TARGET : (ring ? OG_GHOST : OG_FREE);
-        h[i] = p->k / og_speed(p, x);
+        kind[i] = (pj >= 0) ? OG_TARGET : ((ring || stopped) ? OG_GHOST : OG_FREE);
+        h[i] = stopped ? INFINITY : p->k / c;
     }
     return 0;
+}
+
+/* Direction of the foot and time step of control m at node i (R1, R20):
+   d = f/|f| and the return value h_{i,m} = k/|f| (+inf: not admissible).
+   For f = c(x) a these are a and the node's h[i]. */
+static double og_dir(const og_problem *p, const double *h, int64_t i, int m, double dv[3]) {
+    const double *a = p->controls + (size_t)m * p->dim;
+    dv[0] = dv[1] = dv[2] = 0.0;
+    if (p->dyn_kind == 1) {
+        double f[3] = {0.0, 0.0, 0.0}, n2 = 0.0;
+        for (int d = 0; d < p->dim; ++d) {
+            f[d] = p->drift[0] * a[d] + p->drift[1 + d];
+            n2 += f[d] * f[d];
+        }
+        const double nf = sqrt(n2);
+        if (!(nf > 1e-15)) return INFINITY;
+        for (int d = 0; d < p->dim; ++d) {
+            const double v = f[d] / nf;
+            dv[d] = fabs(v) < 1e-15 ? 0.0 : v;
+        }
+        return p->k / nf;
+    }
+    for (int d = 0; d < p->dim; ++d) dv[d] = a[d];
+    return h ? h[i] : p->k;
 }
 
 /* ------------------------------------------------------- interpolation --- */
@@ -328,12 +421,14 @@ static double og_F_node(const og_problem *p, const double *U, const double *h, i
     int besta = -1;
     for (int m = 0; m < p->n_controls; ++m) {
         if (!og_allowed(p, flt, i, m)) continue;
-        const double *a = p->controls + (size_t)m * p->dim;
+        double a[3];
+        const double hm = og_dir(p, h, i, m, a);
+        if (isinf(hm)) continue;
         double xi[3] = {0.0, 0.0, 0.0};
         for (int d = 0; d < p->dim; ++d) xi[d] = (double)idx[d] + a[d];
         double v;
         if (mode == 0) {
-            v = og_interp(p, U, xi) + h[i];
+            v = og_interp(p, U, xi) + hm;
         } else {
             int base[3] = {0, 0, 0};
             double t[3] = {0.0, 0.0, 0.0};
@@ -367,7 +462,7 @@ static double og_F_node(const og_problem *p, const double *U, const double *h, i
                     rest += w * U[ci];
                 }
             }
-            v = (wself < 1.0) ? (rest + h[i]) / (1.0 - wself) : INFINITY;
+            v = (wself < 1.0) ? (rest + hm) / (1.0 - wself) : INFINITY;
         }
         if (v < best) {
             second = best;
@@ -464,7 +559,9 @@ static int og_reachable_f(const og_problem *p, const unsigned char *upd, const d
                 if (!C[i] || inS[i]) continue;
                 for (int m = 0; m < p->n_controls && !inS[i]; ++m) {
                     if (!og_allowed(p, flt, i, m)) continue;
-                    int cnt = og_support(p, i, p->controls + (size_t)m * p->dim, sup);
+                    double dv[3];
+                    if (isinf(og_dir(p, NULL, i, m, dv))) continue;
+                    int cnt = og_support(p, i, dv, sup);
                     if (cnt < 0) continue;
                     int admissible = 1, hits = 0;
                     for (int c = 0; c < cnt; ++c) {
@@ -604,7 +701,8 @@ static int og_phi_iterate(const og_problem *p, const unsigned char *upd, const i
             if (!upd[i]) continue;
             int idx[3];
             og_index3(p, i, idx);
-            const double *a = p->controls + (size_t)astar[i] * p->dim;
+            double a[3];
+            og_dir(p, NULL, i, astar[i], a);
             double xi[3] = {0.0, 0.0, 0.0};
             for (int d = 0; d < p->dim; ++d) xi[d] = (double)idx[d] + a[d];
             double v = og_interp(p, phi, xi);
@@ -641,7 +739,7 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
                        signed char *labels, double *Ucoarse_out, double *U0_out, int *astar_out,
                        double *gap_out, double *phi_out, og_patchy_stats *st) {
     const int64_t N = og_count(p);
-    const int R = p->n_targets;
+    const int R = og_parts(p);
     if (R < 1 || R > 64) return -2;
     og_patchy_stats local;
     if (!st) st = &local;
@@ -680,12 +778,10 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
         Uc[i] = INFINITY;
         if (ckind[i] == OG_TARGET) {   /* R6: boundary value dist / c */
             int idx[3];
-            double x[3], r2 = 0.0;
+            double x[3], gap = 0.0;
             og_index3(&pc, i, idx);
             og_coords(&pc, idx, x);
-            const double *tj = p->targets + (size_t)cpart[i] * (p->dim + 1);
-            for (int d = 0; d < p->dim; ++d) r2 += (x[d] - tj[d]) * (x[d] - tj[d]);
-            double gap = sqrt(r2) - tj[p->dim];
+            og_target_part(&pc, x, pc.k * sqrt((double)p->dim) / 2.0, &gap);
             Uc[i] = gap > 0.0 ? gap / og_speed(&pc, x) : 0.0;
         }
     }

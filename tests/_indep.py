@@ -23,6 +23,8 @@ def speed_np(p, x: np.ndarray) -> np.ndarray:
         return 1.0 + q[0] * np.sin(2 * math.pi * x[:, 0]) * np.cos(2 * math.pi * x[:, 1])
     if p.speed == "sin3d":
         return 1.0 + q[0] * np.sin(math.pi * x[:, 0]) * np.sin(math.pi * x[:, 1]) * np.sin(math.pi * x[:, 2])
+    if p.speed == "fan":
+        return np.abs(q[0] + q[1] * x[:, 0] + q[2] * x[:, 1] + (q[3] * x[:, 2] if x.shape[1] > 2 else 0.0))
     if p.speed == "fourier2d":
         a = q[:16].reshape(4, 4)
         th = q[16:32].reshape(4, 4)
@@ -53,20 +55,61 @@ def linear(p, idx):
     return out
 
 
+def target_parts(p, x):
+    """Target part of each point (-1 outside): balls, one ball in R angular
+    sectors, or the slab |x1 - v| <= r in R pieces along x2."""
+    N = x.shape[0]
+    part = np.full(N, -1)
+    if p.target_kind == "balls":
+        for j in range(p.n_targets - 1, -1, -1):
+            c, r = p.targets[j, : p.dim], p.targets[j, p.dim]
+            part[np.linalg.norm(x - c, axis=1) <= r] = j
+        return part
+    R = p.n_parts
+    t = p.targets[0]
+    if p.target_kind == "sectors":
+        off = x[:, :2] - t[:2]
+        inside = np.hypot(off[:, 0], off[:, 1]) <= t[p.dim]
+        th = np.mod(np.arctan2(off[:, 1], off[:, 0]), 2 * math.pi)
+        j = np.floor(R * th / (2 * math.pi) + 1e-9).astype(int) % R
+        part[inside] = j[inside]
+        return part
+    inside = np.abs(x[:, 0] - t[0]) <= t[p.dim]
+    j = np.clip(np.floor(R * (x[:, 1] - p.lo[1]) / (p.hi[1] - p.lo[1]) + 1e-9).astype(int), 0, R - 1)
+    part[inside] = j[inside]
+    return part
+
+
 def kinds(p):
-    """0 free, 1 target (part >= 0), 2 ghost; h = k / c(x)."""
+    """0 free, 1 target (part >= 0), 2 ghost (ring, or a node whose speed
+    vanishes); h = k / c(x)."""
     idx, x = node_grid(p)
     N = idx.shape[0]
-    part = np.full(N, -1)
-    for j in range(p.n_targets - 1, -1, -1):
-        c, r = p.targets[j, : p.dim], p.targets[j, p.dim]
-        part[np.linalg.norm(x - c, axis=1) <= r] = j
+    part = target_parts(p, x)
     ring = np.zeros(N, bool)
     for d in range(p.dim):
         ring |= (idx[:, d] == 0) | (idx[:, d] == p.n[d] - 1)
-    kind = np.where(part >= 0, 1, np.where(ring, 2, 0))
-    h = p.spacing / speed_np(p, x)
+    c = speed_np(p, x)
+    stopped = ~(c > 1e-12)
+    kind = np.where(part >= 0, 1, np.where(ring | stopped, 2, 0))
+    with np.errstate(divide="ignore"):
+        h = np.where(stopped, np.inf, p.spacing / np.where(stopped, 1.0, c))
     return kind, part, h
+
+
+def control_steps(p):
+    """Per control: the unit direction of f and the factor g with
+    h_{i,a} = g * h_i (h_i = k / c(x_i) for f = c(x) a, g = 1; for the drift
+    f = s a + w: h_i = k and g = 1 / |s a + w|)."""
+    a = np.asarray(p.controls, float)
+    if p.dyn == "speed":
+        return a, np.ones(a.shape[0])
+    s, w = p.drift[0], np.asarray(p.drift[1: 1 + p.dim])
+    f = s * a + w
+    nf = np.linalg.norm(f, axis=1)
+    dirs = f / nf[:, None]
+    dirs[np.abs(dirs) < 1e-15] = 0.0
+    return dirs, 1.0 / nf
 
 
 def q1_corners(p, node_idx, a):

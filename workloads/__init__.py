@@ -6,12 +6,16 @@ balls Omega_0^j.  It holds none of the scheme's arithmetic (no interpolation,
 no time step, no fixed-point iteration); both the CPU oracle and the CUDA
 library read the same descriptions and evaluate everything else themselves.
 
-Problem families (all with dynamics f(x, a) = c(x) a, |a| = 1):
+Problem families (dynamics f(x, a) = c(x) a, |a| = 1, unless stated):
 
 * ``eikonal2d``     c = 1, one disk target (closed form u = max(|x| - r, 0)).
 * ``sincos2d``      c = 1 + A sin(2 pi x1) cos(2 pi x2).
 * ``sin3d``         c = 1 + A sin(pi x1) sin(pi x2) sin(pi x3).
 * ``fourier2d``     c = 1 + 0.5 g(x), g a normalised random 4x4 Fourier field.
+* the paper's own 2D tests (Table 1), with the target split into R parts:
+  ``eikonal_sectors`` (f = a, one disk in R sectors), ``zermelo`` (f = 2.1 a
+  + (2, 0), a drift, one disk in R sectors) and ``fan`` (c = |x1 + x2 + 0.1|,
+  the line x1 = 0 in R pieces).
 
 Control sets: 2D -- unit vectors at angles 2 pi m / N_c (the paper
 discretises A = B_2(0,1) with N_c points, Sec. 2.1 and Table 1); 3D -- a
@@ -27,7 +31,9 @@ from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3}
+SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3, "fan": 4}
+DYN_KINDS = {"speed": 0, "drift": 1}
+TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2}
 SNAP = 1e-15
 
 
@@ -54,6 +60,14 @@ class Problem:
     tol_phi: float = 1e-10
     max_sweeps: int = 100000
     name: str = ""
+    # dynamics: "speed" f = c(x) a; "drift" f = s a + w with drift = (s, w1, w2, w3)
+    dyn: str = "speed"
+    drift: Tuple[float, float, float, float] = (1.0, 0.0, 0.0, 0.0)
+    # target: "balls" (row j = ball j = part j), "sectors" (row 0 = one ball in
+    # n_parts angular sectors), "slab" (row 0 = (v, ., r): |x1 - v| <= r in
+    # n_parts pieces along x2)
+    target_kind: str = "balls"
+    n_parts: int = 0
 
     @property
     def spacing(self) -> float:
@@ -70,6 +84,11 @@ class Problem:
     @property
     def n_targets(self) -> int:
         return int(self.targets.shape[0])
+
+    @property
+    def n_patches(self) -> int:
+        """R: one patch per target row, or n_parts for a split target."""
+        return self.n_targets if self.target_kind == "balls" else int(self.n_parts)
 
     def with_(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
@@ -272,3 +291,38 @@ def random_speed_problem(seed: int, n: int = 9, n_c: int = 8, dim: int = 2,
     return Problem(dim=3, n=(n, n, n), lo=(-box,) * 3, hi=(box,) * 3, speed="sin3d",
                    speed_params=_params([0.3]), controls=ctl, targets=tg, tol=1e-13,
                    name=f"tiny3d_s{seed}")
+
+
+# ------------------------------------------------- the paper's 2D tests --
+
+def eikonal_sectors(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, radius: float = 0.5,
+                    tol: float = 1e-6) -> Problem:
+    """Table 1, Eikonal: f = a on [-2,2]^2, target B(0, 0.5) split into R equal
+    angular sectors (one patch each)."""
+    return Problem(dim=2, n=(n, n, 1), lo=(-2.0, -2.0, 0.0), hi=(2.0, 2.0, 0.0), speed="one",
+                   speed_params=np.zeros(64), controls=controls_2d(n_c),
+                   targets=np.array([[0.0, 0.0, radius]]), tol=tol, n_coarse=(n_coarse, n_coarse, 1),
+                   name=f"eikonal_sectors{n}", target_kind="sectors", n_parts=parts)
+
+
+def zermelo(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, radius: float = 0.5,
+            s: float = 2.1, w: Tuple[float, float] = (2.0, 0.0), tol: float = 1e-6) -> Problem:
+    """Table 1, Zermelo: f = s a + w (s = 2.1, w = (2, 0)) on [-2,2]^2, target
+    B(0, 0.5) split into R sectors."""
+    return Problem(dim=2, n=(n, n, 1), lo=(-2.0, -2.0, 0.0), hi=(2.0, 2.0, 0.0), speed="one",
+                   speed_params=np.zeros(64), controls=controls_2d(n_c),
+                   targets=np.array([[0.0, 0.0, radius]]), tol=tol, n_coarse=(n_coarse, n_coarse, 1),
+                   name=f"zermelo{n}", dyn="drift", drift=(s, w[0], w[1], 0.0), target_kind="sectors",
+                   n_parts=parts)
+
+
+def fan(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, half_width: float = 1e-9,
+        tol: float = 1e-6) -> Problem:
+    """Table 1, Fan: c(x) = |x1 + x2 + 0.1| on [-2,2]^2, target the line x1 = 0
+    (a slab of half-width ``half_width``) split into R pieces along x2."""
+    q = np.zeros(64)
+    q[:4] = (0.1, 1.0, 1.0, 0.0)
+    return Problem(dim=2, n=(n, n, 1), lo=(-2.0, -2.0, 0.0), hi=(2.0, 2.0, 0.0), speed="fan",
+                   speed_params=q, controls=controls_2d(n_c), targets=np.array([[0.0, 0.0, half_width]]),
+                   tol=tol, n_coarse=(n_coarse, n_coarse, 1), name=f"fan{n}", target_kind="slab",
+                   n_parts=parts)
