@@ -48,8 +48,34 @@ typedef enum {
  *  HJBP_C_SIN3D      c = 1 + p0 sin(pi x1) sin(pi x2) sin(pi x3)
  *  HJBP_C_FOURIER2D  c = 1 + 0.5 g(x),  g = sum_{p,q=0..3} a_pq cos(pi p x1/2 + th_pq)
  *                                       cos(pi q x2/2 + ps_pq) / sum |a_pq|,
- *                    params = [a (16, row-major in p,q), th (16), ps (16)]          */
-typedef enum { HJBP_C_ONE = 0, HJBP_C_SINCOS2D = 1, HJBP_C_SIN3D = 2, HJBP_C_FOURIER2D = 3 } hjbp_speed_kind;
+ *                    params = [a (16, row-major in p,q), th (16), ps (16)]
+ *  HJBP_C_FAN        c = |p0 + p1 x1 + p2 x2 + p3 x3|   (Fan, Table 1: p = 0.1, 1, 1, 0);
+ *                    a node where c <= 1e-12 cannot move and is treated like the
+ *                    ghost ring (+inf, label -1) unless it is a target node        */
+typedef enum {
+    HJBP_C_ONE = 0,
+    HJBP_C_SINCOS2D = 1,
+    HJBP_C_SIN3D = 2,
+    HJBP_C_FOURIER2D = 3,
+    HJBP_C_FAN = 4
+} hjbp_speed_kind;
+
+/* Dynamics (Table 1).  HJBP_DYN_SPEED: f(x, a) = c(x) a with the speed field
+ * above.  HJBP_DYN_DRIFT: f(x, a) = s a + w (Zermelo: s = 2.1, w = (2, 0)),
+ * drift = {s, w_1, w_2, w_3}, speed must be HJBP_C_ONE, 2D only; every control
+ * needs |s a + w| > 1e-15.  With |h f| = k (Sec. 2.1) the foot of control a is
+ * x_i + k f/|f| and its time step k/|f|.                                    */
+typedef enum { HJBP_DYN_SPEED = 0, HJBP_DYN_DRIFT = 1 } hjbp_dyn_kind;
+
+/* Target Omega_0 and its parts Omega_0^j (one patch each, Sec. 3).
+ * HJBP_TARGET_BALLS: every row of targets is a ball (centre, radius) and a part.
+ * HJBP_TARGET_SECTORS (2D): row 0 is one ball split into n_parts equal angular
+ *   sectors, part j = floor(n_parts theta / (2 pi) + 1e-9) mod n_parts with
+ *   theta the angle of x - centre in [0, 2 pi).
+ * HJBP_TARGET_SLAB (2D): row 0 = (v, unused, r): the slab |x_1 - v| <= r (a line
+ *   target of half-width r) split into n_parts equal pieces along x_2 over the
+ *   box, part j = floor(n_parts (x_2 - lo_2) / (hi_2 - lo_2) + 1e-9), clamped. */
+typedef enum { HJBP_TARGET_BALLS = 0, HJBP_TARGET_SECTORS = 1, HJBP_TARGET_SLAB = 2 } hjbp_target_kind;
 
 /* Arithmetic of the fine-grid sweeps.  HJBP_FP64: every sweep in FP64.
  * HJBP_FP32_POLISH64: bulk sweeps in FP32, then FP64 polishing sweeps.      */
@@ -105,6 +131,10 @@ typedef struct {
                            feedback of Step 2, Eq. feedbackcontrol); nodes without a
                            feedback keep every control.  0 keeps every control.  On the
                            2D path the control set must have at most 64 members.      */
+    int dyn;            /* hjbp_dyn_kind */
+    double drift[4];    /* HJBP_DYN_DRIFT: s, w_1, w_2, w_3 */
+    int target_kind;    /* hjbp_target_kind */
+    int n_parts;        /* parts (patches) of HJBP_TARGET_SECTORS / SLAB, 1..64 */
 } hjbp_problem_desc;
 
 /* flags: HJBP_FLAG_TIME_SWEEPS records a CUDA event pair around every launch

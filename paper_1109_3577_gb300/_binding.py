@@ -17,7 +17,9 @@ HJBP_OK, HJBP_EINVAL, HJBP_ENOMEM, HJBP_ENOCONV, HJBP_ETIMEOUT, HJBP_ECUDA, HJBP
 HJBP_FP64, HJBP_FP32_POLISH64 = 0, 1
 HJBP_OUT_UCOARSE, HJBP_OUT_U0, HJBP_OUT_ASTAR, HJBP_OUT_PHI, HJBP_OUT_U32 = range(5)
 MAX_CONTROLS, MAX_TARGETS = 256, 64
-SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3}
+SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3, "fan": 4}
+DYN_KINDS = {"speed": 0, "drift": 1}
+TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2}
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ETIMEOUT", 5: "ECUDA", 6: "EBUSY", 7: "ESTATE"}
 
 
@@ -48,6 +50,10 @@ class Desc(C.Structure):
         ("flags", C.c_int),
         ("tune", C.c_int * 8),
         ("reduce_r", C.c_double),
+        ("dyn", C.c_int),
+        ("drift", C.c_double * 4),
+        ("target_kind", C.c_int),
+        ("n_parts", C.c_int),
     ]
 
 
@@ -365,6 +371,11 @@ def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 
     for i, v in enumerate(tune or ()):
         d.tune[i] = int(v)
     d.reduce_r = float(reduce_r)
+    d.dyn = DYN_KINDS[getattr(p, "dyn", "speed")]
+    for i, v in enumerate(getattr(p, "drift", (1.0, 0.0, 0.0, 0.0))):
+        d.drift[i] = float(v)
+    d.target_kind = TARGET_KINDS[getattr(p, "target_kind", "balls")]
+    d.n_parts = int(getattr(p, "n_parts", 0))
     return d, (controls, targets)
 
 
@@ -424,7 +435,7 @@ class Plan:
         return out
 
     def intermediate(self, which: int) -> np.ndarray:
-        R = self.problem.n_targets
+        R = self.problem.n_patches
         if which == HJBP_OUT_UCOARSE:
             out = np.empty(self.Nc, np.float64)
         elif which == HJBP_OUT_U0:

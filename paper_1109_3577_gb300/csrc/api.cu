@@ -87,7 +87,7 @@ static std::string validate(const hjbp_problem_desc *d) {
             if (d->n_coarse[a] > d->n[a]) return "coarse grid finer than the fine grid";
         }
     }
-    if (d->speed < HJBP_C_ONE || d->speed > HJBP_C_FOURIER2D) return "unknown speed field";
+    if (d->speed < HJBP_C_ONE || d->speed > HJBP_C_FAN) return "unknown speed field";
     if (d->speed == HJBP_C_SIN3D && d->dim != 3) return "SIN3D needs dim 3";
     if ((d->speed == HJBP_C_SINCOS2D || d->speed == HJBP_C_FOURIER2D) && d->dim != 2) return "2D speed field with dim 3";
     if (d->n_controls < 1 || d->n_controls > HJBP_MAX_CONTROLS) return "n_controls out of range";
@@ -102,6 +102,18 @@ static std::string validate(const hjbp_problem_desc *d) {
         if (std::fabs(std::sqrt(s) - 1.0) > 1e-9) return "controls must be unit vectors";
     }
     if (d->n_targets < 1 || d->n_targets > HJBP_MAX_TARGETS) return "n_targets out of range";
+    if (d->target_kind < HJBP_TARGET_BALLS || d->target_kind > HJBP_TARGET_SLAB) return "unknown target kind";
+    if (d->target_kind != HJBP_TARGET_BALLS) {
+        if (d->dim != 2) return "split targets (sectors, slab) are 2D";
+        if (d->n_parts < 1 || d->n_parts > HJBP_MAX_TARGETS) return "n_parts out of range";
+    }
+    if (d->dyn != HJBP_DYN_SPEED && d->dyn != HJBP_DYN_DRIFT) return "unknown dynamics";
+    if (d->dyn == HJBP_DYN_DRIFT) {
+        if (d->dim != 2) return "drift dynamics are 2D";
+        if (d->speed != HJBP_C_ONE) return "drift dynamics take the speed field HJBP_C_ONE";
+        for (int a = 0; a < 4; ++a)
+            if (!std::isfinite(d->drift[a])) return "drift not finite";
+    }
     if (!d->targets) return "targets is NULL";
     for (int j = 0; j < d->n_targets; ++j)
         for (int a = 0; a <= d->dim; ++a)
@@ -146,6 +158,34 @@ hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const 
         p->targets.assign(desc->targets, desc->targets + (size_t)desc->n_targets * (desc->dim + 1));
         p->desc.controls = p->controls.data();
         p->desc.targets = p->targets.data();
+        p->R = desc->target_kind == HJBP_TARGET_BALLS ? desc->n_targets : desc->n_parts;
+        // per-control direction of f and time-step factor (|h f| = k, Sec. 2.1)
+        p->dirs.assign((size_t)desc->n_controls * desc->dim, 0.0);
+        p->hfac.assign((size_t)desc->n_controls, 1.0);
+        for (int m = 0; m < desc->n_controls; ++m) {
+            const double *a = desc->controls + (size_t)m * desc->dim;
+            double *dv = p->dirs.data() + (size_t)m * desc->dim;
+            if (desc->dyn == HJBP_DYN_DRIFT) {
+                double f[3] = {0.0, 0.0, 0.0}, n2 = 0.0;
+                for (int c = 0; c < desc->dim; ++c) {
+                    f[c] = desc->drift[0] * a[c];
+                    f[c] += desc->drift[1 + c];
+                    n2 += f[c] * f[c];
+                }
+                const double nf = std::sqrt(n2);
+                if (!(nf > 1e-15)) {
+                    delete p;
+                    return fail(HJBP_EINVAL, "a control has zero velocity under the drift");
+                }
+                for (int c = 0; c < desc->dim; ++c) {
+                    const double v = f[c] / nf;
+                    dv[c] = std::fabs(v) < 1e-15 ? 0.0 : v;
+                }
+                p->hfac[m] = 1.0 / nf;
+            } else {
+                for (int c = 0; c < desc->dim; ++c) dv[c] = a[c];
+            }
+        }
         p->stream = static_cast<cudaStream_t>(cuda_stream);
         if (allocator && allocator->alloc && allocator->release) {
             p->alloc = *allocator;
@@ -170,7 +210,7 @@ hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const 
             p->u_coarse = static_cast<double *>(p->dev_alloc(sizeof(double) * p->Nc));
             p->u0 = static_cast<double *>(p->dev_alloc(sizeof(double) * p->N));
             p->astar = static_cast<uint8_t *>(p->dev_alloc(p->N));
-            p->phi = static_cast<double *>(p->dev_alloc(sizeof(double) * p->N * desc->n_targets));
+            p->phi = static_cast<double *>(p->dev_alloc(sizeof(double) * p->N * p->R));
         }
         hjbp::check_cuda(cudaStreamSynchronize(p->stream), "create");
     } catch (const HjbpError &e) {
@@ -274,7 +314,7 @@ hjbp_status hjbp_get_intermediate(hjbp_plan *p, int which, void *host_out, size_
     case HJBP_OUT_UCOARSE: src = p->u_coarse; need = sizeof(double) * p->Nc; break;
     case HJBP_OUT_U0: src = p->u0; need = sizeof(double) * p->N; break;
     case HJBP_OUT_ASTAR: src = p->astar; need = (size_t)p->N; break;
-    case HJBP_OUT_PHI: src = p->phi; need = sizeof(double) * p->N * p->desc.n_targets; break;
+    case HJBP_OUT_PHI: src = p->phi; need = sizeof(double) * p->N * p->R; break;
     case HJBP_OUT_U32: src = p->u32; need = sizeof(float) * p->N; break;
     default: return fail(HJBP_EINVAL, "unknown intermediate id");
     }

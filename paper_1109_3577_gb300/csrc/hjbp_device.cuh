@@ -73,6 +73,7 @@ template <typename T> struct CtlTable2 {
     T cls_s[kMaxControls / 4];
     T cls_t[kMaxControls / 4];
     T cls_kw11[kMaxControls / 4];
+    float hfmax;   // max over controls of the time-step factor (kap holds kap * factor)
 };
 
 // Per-control self-solved weights in any order (one control per lane).
@@ -100,6 +101,9 @@ struct CtlLiteral2 {
     float f10[kMaxControls];
     float f01[kMaxControls];
     float f11[kMaxControls];
+    double hf[kMaxControls];   // time-step factor: h_{i,a} = hf[a] h_i (1 for f = c(x) a)
+    float hff[kMaxControls];
+    float hfmax;               // max over controls of hf
 };
 
 // Support masks for the almost-sure reachability sweep: bit 0 corner 10,
@@ -127,9 +131,12 @@ struct SpeedParams {
     double p[64];
 };
 
-// Target balls: centres (c0, c1, c2) and radii, passed by value.
+// Target balls: centres (c0, c1, c2) and radii, passed by value; kind and
+// nparts select a split target (hjbp_target_kind), row 0 then describes it.
 struct TargetSet {
     int n;
+    int kind;
+    int nparts;
     double c0[kMaxTargets], c1[kMaxTargets], c2[kMaxTargets], r[kMaxTargets];
 };
 
@@ -153,10 +160,18 @@ __device__ inline double speed_at(const SpeedParams &sp, double x0, double x1, d
             }
         return 1.0 + 0.5 * g / norm;
     }
+    case HJBP_C_FAN:
+        // |p0 + p1 x1 + p2 x2 + p3 x3|, rounded in this order (no contraction)
+        return fabs(__dadd_rn(__dadd_rn(__dadd_rn(sp.p[0], __dmul_rn(sp.p[1], x0)), __dmul_rn(sp.p[2], x1)),
+                              __dmul_rn(sp.p[3], x2)));
     default:
         return nan("");
     }
 }
+
+// A node whose speed is at most this cannot move (it is treated like the
+// ghost ring unless it is a target node).
+constexpr double kStoppedSpeed = 1e-12;
 
 // Geometry of a 2D grid and its tiling of the interior nodes 1..n-2.
 struct Grid2 {
@@ -164,6 +179,47 @@ struct Grid2 {
     int ntx, nty;      // tiles per side
     double lo0, lo1, k;
 };
+
+// Target part of the 2D point (x0, x1), -1 outside the target; the target is
+// widened by extra (the coarse grid's boundary band); *gap = distance to the
+// un-widened target (0 inside).  Explicitly rounded operations, so that the
+// decisions follow x = lo + i k and the definitions of hjbp_target_kind.
+__device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x0, double x1, double extra,
+                                   double *gap) {
+    const double pi = 3.14159265358979323846;
+    if (ts.kind == HJBP_TARGET_BALLS) {
+        for (int j = 0; j < ts.n; ++j) {
+            const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]);
+            const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)));
+            if (d <= __dadd_rn(ts.r[j], extra)) {
+                *gap = d > ts.r[j] ? __dsub_rn(d, ts.r[j]) : 0.0;
+                return j;
+            }
+        }
+        return -1;
+    }
+    const int R = ts.nparts;
+    if (ts.kind == HJBP_TARGET_SECTORS) {
+        const double d0 = __dsub_rn(x0, ts.c0[0]), d1 = __dsub_rn(x1, ts.c1[0]);
+        const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)));
+        if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+        double th = atan2(d1, d0);
+        if (th < 0.0) th = __dadd_rn(th, 2.0 * pi);
+        int j = (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)R, th), 2.0 * pi), 1e-9));
+        if (j >= R) j -= R;
+        if (j < 0) j = 0;
+        *gap = d > ts.r[0] ? __dsub_rn(d, ts.r[0]) : 0.0;
+        return j;
+    }
+    const double d = fabs(__dsub_rn(x0, ts.c0[0]));
+    if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+    const double hi1 = __dadd_rn(g.lo1, __dmul_rn((double)(g.n1 - 1), g.k));
+    int j = (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)R, __dsub_rn(x1, g.lo1)), __dsub_rn(hi1, g.lo1)), 1e-9));
+    if (j >= R) j = R - 1;
+    if (j < 0) j = 0;
+    *gap = d > ts.r[0] ? __dsub_rn(d, ts.r[0]) : 0.0;
+    return j;
+}
 
 // Device-side state of one tile-sweep phase (active list, parities, ...).
 struct TileSched {

@@ -46,24 +46,16 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
         const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
         const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
         const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
-        int part = -1;
-        double dist = 0.0;
-        for (int j = 0; j < ts.n && part < 0; ++j) {
-            const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]);
-            const double r2 = __dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1));
-            const double d = __dsqrt_rn(r2);
-            if (d <= __dadd_rn(ts.r[j], extra)) {
-                part = j;
-                dist = __dsub_rn(d, ts.r[j]);
-            }
-        }
+        double gap = 0.0;
+        const int part = target_part2(ts, g, x0, x1, extra, &gap);
         const bool ring = ix == 0 || iy == 0 || ix == g.n0 - 1 || iy == g.n1 - 1;
         const double c = speed_at(sp, x0, x1, 0.0);
-        const double hh = __ddiv_rn(g.k, c);
-        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : (ring ? kHard : (int8_t)0);
+        const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
+        const double hh = stopped ? (double)INFINITY : __ddiv_rn(g.k, c);
+        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped) ? kHard : (int8_t)0);
         if (h32) h32[i] = (float)hh;
         if (h64) h64[i] = hh;
-        if (fixed) fixed[i] = (part >= 0 && boundary_values && dist > 0.0) ? __ddiv_rn(dist, c) : 0.0;
+        if (fixed) fixed[i] = (part >= 0 && boundary_values && gap > 0.0) ? __ddiv_rn(gap, c) : 0.0;
     }
 }
 
@@ -1310,23 +1302,25 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
         for (int m = 0; m < cl.nc; ++m) {
             float a10, a01, a11;
             corners32(m, a10, a01, a11);
-            const float v = cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf;
+            const float v = cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf * cl.hff[m];
             b32 = v < b32 ? v : b32;
         }
         double best = Num<double>::big();
         int arg = kNoControl;
         if (b32 < Num<float>::thresh()) {
-            const float lim = b32 + ldexpf(hf + amax, -18);
+            const float lim = b32 + ldexpf(hf * cl.hfmax + amax, -18);
             for (int m = 0; m < cl.nc; ++m) {
                 float a10, a01, a11;
                 corners32(m, a10, a01, a11);
-                const float v32 = cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf;
+                const float v32 =
+                    cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf * cl.hff[m];
                 if (v32 > lim) continue;
                 const bool px = cl.sx[m] > 0, py = cl.sy[m] > 0;
                 const double d10 = px ? nb[1][2] : nb[1][0];
                 const double d01 = py ? nb[2][1] : nb[0][1];
                 const double d11 = px ? (py ? nb[2][2] : nb[0][2]) : (py ? nb[2][0] : nb[0][0]);
-                const double v = cl.w00[m] * nb[1][1] + cl.w10[m] * d10 + cl.w01[m] * d01 + cl.w11[m] * d11 + hh;
+                const double v =
+                    cl.w00[m] * nb[1][1] + cl.w10[m] * d10 + cl.w01[m] * d01 + cl.w11[m] * d11 + hh * cl.hf[m];
                 if (v < best) {
                     best = v;
                     arg = m;
@@ -1800,7 +1794,7 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
                 }
             }
             if (b32 < Num<float>::thresh() && v < Num<double>::thresh()) {
-                const float lim = b32 + ldexpf(hf + amax, -18);
+                const float lim = b32 + ldexpf(hf * c32.hfmax + amax, -18);
                 // pass 2: FP64 over the candidates
                 double best = Num<double>::big();
 #pragma unroll
@@ -2040,21 +2034,23 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
 template <typename T> void build_d4(const hjbp_plan &p, CtlTable2<T> &ct) {
     ct.d4 = 0;
     const int nc = p.desc.n_controls;
+    for (int m = 0; m < nc; ++m)
+        if (p.hfac[m] != 1.0) return;   // the pair form shares kap h between mirrored controls
     const double tol = 1e-12;
     auto has = [&](double x, double y) {
         for (int m = 0; m < nc; ++m)
-            if (std::fabs(p.controls[2 * m] - x) < tol && std::fabs(p.controls[2 * m + 1] - y) < tol) return true;
+            if (std::fabs(p.dirs[2 * m] - x) < tol && std::fabs(p.dirs[2 * m + 1] - y) < tol) return true;
         return false;
     };
     for (int m = 0; m < nc; ++m) {
-        const double x = p.controls[2 * m], y = p.controls[2 * m + 1];
+        const double x = p.dirs[2 * m], y = p.dirs[2 * m + 1];
         const double img[8][2] = {{x, y}, {-x, y}, {x, -y}, {-x, -y}, {y, x}, {-y, x}, {y, -x}, {-y, -x}};
         for (auto &v : img)
             if (!has(v[0], v[1])) return;
     }
     int axis = 0, ncls = 0, count = 0;
     for (int m = 0; m < nc; ++m) {
-        const double x = p.controls[2 * m], y = p.controls[2 * m + 1];
+        const double x = p.dirs[2 * m], y = p.dirs[2 * m + 1];
         if (x > 0.0 && y == 0.0) {
             axis = 1;
             count += 4;
@@ -2084,24 +2080,26 @@ template <typename T> CtlTable2<T> make_table(const hjbp_plan &p) {
     ct.nc = nc;
     std::vector<int> order[4];
     for (int m = 0; m < nc; ++m) {
-        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
         order[(ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0)].push_back(m);
     }
     int pos = 0;
     for (int q = 0; q < 4; ++q) {
         ct.qbeg[q] = pos;
         for (int m : order[q]) {
-            const double ax = std::fabs(p.controls[2 * m]), ay = std::fabs(p.controls[2 * m + 1]);
+            const double ax = std::fabs(p.dirs[2 * m]), ay = std::fabs(p.dirs[2 * m + 1]);
             const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
             const double kap = 1.0 / (1.0 - w00);
             ct.kw10[pos] = (T)(kap * w10);
             ct.kw01[pos] = (T)(kap * w01);
             ct.kw11[pos] = (T)(kap * w11);
-            ct.kap[pos] = (T)kap;
+            ct.kap[pos] = (T)(kap * p.hfac[m]);   // kap h_{i,a} = kap hfac[a] h_i
             ++pos;
         }
     }
     ct.qbeg[4] = pos;
+    ct.hfmax = 0.f;
+    for (int m = 0; m < nc; ++m) ct.hfmax = std::max(ct.hfmax, (float)p.hfac[m]);
     build_d4(p, ct);
     return ct;
 }
@@ -2111,7 +2109,7 @@ template <typename T> CtlSelf2<T> make_self(const hjbp_plan &p) {
     std::memset(&cs, 0, sizeof(cs));
     cs.nc = p.desc.n_controls;
     for (int m = 0; m < cs.nc; ++m) {
-        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
         const double bx = std::fabs(ax), by = std::fabs(ay);
         const double kap = 1.0 / (1.0 - (1.0 - bx) * (1.0 - by));
         cs.sx[m] = ax >= 0.0 ? 1 : -1;
@@ -2119,7 +2117,7 @@ template <typename T> CtlSelf2<T> make_self(const hjbp_plan &p) {
         cs.kw10[m] = (T)(kap * bx * (1.0 - by));
         cs.kw01[m] = (T)(kap * (1.0 - bx) * by);
         cs.kw11[m] = (T)(kap * bx * by);
-        cs.kap[m] = (T)kap;
+        cs.kap[m] = (T)(kap * p.hfac[m]);
     }
     return cs;
 }
@@ -2129,7 +2127,7 @@ CtlLiteral2 make_literal(const hjbp_plan &p) {
     std::memset(&cl, 0, sizeof(cl));
     cl.nc = p.desc.n_controls;
     for (int m = 0; m < cl.nc; ++m) {
-        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
         const double bx = std::fabs(ax), by = std::fabs(ay);
         cl.sx[m] = ax >= 0.0 ? 1 : -1;
         cl.sy[m] = ay >= 0.0 ? 1 : -1;
@@ -2141,6 +2139,9 @@ CtlLiteral2 make_literal(const hjbp_plan &p) {
         cl.f10[m] = (float)cl.w10[m];
         cl.f01[m] = (float)cl.w01[m];
         cl.f11[m] = (float)cl.w11[m];
+        cl.hf[m] = p.hfac[m];
+        cl.hff[m] = (float)p.hfac[m];
+        cl.hfmax = std::max(cl.hfmax, cl.hff[m]);
     }
     return cl;
 }
@@ -2149,7 +2150,7 @@ ReachTable2 make_reach(const hjbp_plan &p) {
     ReachTable2 rt;
     std::memset(&rt, 0, sizeof(rt));
     for (int m = 0; m < p.desc.n_controls; ++m) {
-        const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+        const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
         const double bx = std::fabs(ax), by = std::fabs(ay);
         const unsigned need = (unsigned)(bx * (1.0 - by) > 0.0) | ((unsigned)((1.0 - bx) * by > 0.0) << 1) |
                               ((unsigned)(bx * by > 0.0) << 2);
@@ -2169,7 +2170,7 @@ Cone2 make_cones(const hjbp_plan &p, double *mean_size) {
     int at = 0;
     for (int q = 0; q < 4; ++q)
         for (int m = 0; m < nc; ++m) {
-            const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+            const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
             if ((ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0) == q) pos[m] = at++;
         }
     const double cr = std::cos(3.14159265358979323846 / p.desc.reduce_r) - 1e-12;
@@ -2178,12 +2179,13 @@ Cone2 make_cones(const hjbp_plan &p, double *mean_size) {
         unsigned long long mask = 0;
         uint32_t reach = 0;
         for (int m = 0; m < nc; ++m) {
-            const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+            const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
             bool ok = true;
             if (a < nc) {
+                // the cone is a set of controls a (Sec. 6), not of directions of f
                 double dot = 0.0;
-                dot += ax * p.controls[2 * a];
-                dot += ay * p.controls[2 * a + 1];
+                dot += p.controls[2 * m] * p.controls[2 * a];
+                dot += p.controls[2 * m + 1] * p.controls[2 * a + 1];
                 ok = dot >= cr;
             }
             if (!ok) continue;
@@ -2213,6 +2215,8 @@ TargetSet make_targets(const hjbp_plan &p) {
     std::memset(&ts, 0, sizeof(ts));
     const int d = p.desc.dim;
     ts.n = p.desc.n_targets;
+    ts.kind = p.desc.target_kind;
+    ts.nparts = p.R;
     for (int j = 0; j < ts.n; ++j) {
         ts.c0[j] = p.targets[(d + 1) * j + 0];
         ts.c1[j] = p.targets[(d + 1) * j + 1];
@@ -2493,7 +2497,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     const int cap = d.max_sweeps > 0 ? d.max_sweeps : 1000000;
     const int hist = std::max(std::min(cap, 1 << 20), kReachCap);
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
-    const int R = d.n_targets;
+    const int R = p.R;
     const int vrounds = d.tune[0] > 0 ? d.tune[0] : 2;
     const int prounds = d.tune[1] > 0 ? d.tune[1] : 3;
     hjbp_stats &S = p.stats;
@@ -2545,7 +2549,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         if ((d.flags & HJBP_FLAG_CAUSAL_SWEEPS) && sched.ntiles) {
             DirCtl dc;
             for (int m = 0; m < d.n_controls; ++m) {
-                const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+                const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
                 dc.sx[m] = (int8_t)(ax > 1e-12 ? 1 : (ax < -1e-12 ? -1 : 0));
                 dc.sy[m] = (int8_t)(ay > 1e-12 ? 1 : (ay < -1e-12 ? -1 : 0));
             }
@@ -2562,7 +2566,7 @@ hjbp_status solve2d(hjbp_plan &p) {
             std::memset(&hpc, 0, sizeof(hpc));
             hpc.nc = d.n_controls;
             for (int m = 0; m < d.n_controls; ++m) {
-                const double ax = p.controls[2 * m], ay = p.controls[2 * m + 1];
+                const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
                 const double bx = std::fabs(ax), by = std::fabs(ay);
                 const double w00 = (1.0 - bx) * (1.0 - by), w10 = bx * (1.0 - by), w01 = (1.0 - bx) * by;
                 const double w11 = bx * by, kap = 1.0 / (1.0 - w00);

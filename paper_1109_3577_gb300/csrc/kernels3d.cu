@@ -114,8 +114,9 @@ __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, i
         }
         const bool ring = ix == 0 || iy == 0 || iz == 0 || ix == g.n0 - 1 || iy == g.n1 - 1 || iz == g.n2 - 1;
         const double c = speed_at(sp, x0, x1, x2);
-        const double hh = __ddiv_rn(g.k, c);
-        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : (ring ? kHard : (int8_t)0);
+        const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
+        const double hh = stopped ? (double)INFINITY : __ddiv_rn(g.k, c);
+        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped) ? kHard : (int8_t)0);
         if (h32) h32[i] = (float)hh;
         if (h64) h64[i] = hh;
         if (fixed) fixed[i] = (part >= 0 && boundary_values && dist > 0.0) ? __ddiv_rn(dist, c) : 0.0;
@@ -1189,7 +1190,7 @@ hjbp_status solve3d(hjbp_plan &p) {
     const int cap = d.max_sweeps > 0 ? d.max_sweeps : 1000000;
     const int hist = std::max(std::min(cap, 1 << 20), kReachCap3);
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
-    const int R = d.n_targets;
+    const int R = p.R;
     const int vrounds = d.tune[0] > 0 ? d.tune[0] : 1;
     const int prounds = d.tune[1] > 0 ? d.tune[1] : 2;
     hjbp_stats &S = p.stats;

@@ -132,7 +132,8 @@ const char *check_desc(const hjbp_problem_desc *d) {
     const double k0 = (d->hi[0] - d->lo[0]) / (d->n[0] - 1), k1 = (d->hi[1] - d->lo[1]) / (d->n[1] - 1);
     if (std::fabs(k1 - k0) > 1e-12 * k0) return "grid spacing must be equal on every axis";
     if ((int64_t)d->n[0] * d->n[1] > (int64_t)HJBP_NOALLOC_MAX_NODES) return "grid exceeds HJBP_NOALLOC_MAX_NODES";
-    if (d->speed != HJBP_C_ONE && d->speed != HJBP_C_SINCOS2D && d->speed != HJBP_C_FOURIER2D)
+    if (d->speed != HJBP_C_ONE && d->speed != HJBP_C_SINCOS2D && d->speed != HJBP_C_FOURIER2D &&
+        d->speed != HJBP_C_FAN)
         return "speed field must be a 2D one";
     if (d->n_controls < 1 || d->n_controls > HJBP_MAX_CONTROLS || !d->controls) return "bad control set";
     for (int m = 0; m < d->n_controls; ++m) {
@@ -144,6 +145,8 @@ const char *check_desc(const hjbp_problem_desc *d) {
     for (int j = 0; j < 3 * d->n_targets; ++j)
         if (!std::isfinite(d->targets[j])) return "target entry not finite";
     if (!(d->tol > 0.0)) return "tol must be positive";
+    if (d->dyn != HJBP_DYN_SPEED || d->target_kind != HJBP_TARGET_BALLS)
+        return "the no-allocation entry point takes f = c(x) a and ball targets";
     if (d->speed == HJBP_C_FOURIER2D) {
         double norm = 0.0;
         for (int i = 0; i < 16; ++i) norm += std::fabs(d->speed_params[i]);

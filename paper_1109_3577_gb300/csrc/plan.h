@@ -14,6 +14,9 @@ struct hjbp_plan {
     hjbp_problem_desc desc;
     std::vector<double> controls;   // n_controls x dim
     std::vector<double> targets;    // n_targets x (dim + 1)
+    int R = 0;                      // patches (target parts)
+    std::vector<double> dirs;       // per control: unit direction of f (dim each)
+    std::vector<double> hfac;       // per control: h_{i,a} = hfac[a] h_i
     bool patchy = false;
     int64_t N = 0, Nc = 0;          // fine / coarse node counts
     double k = 0.0, kc = 0.0;       // fine / coarse spacing

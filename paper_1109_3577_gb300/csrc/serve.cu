@@ -178,10 +178,11 @@ size_t footprint(const hjbp_problem_desc *d) {
         Nc = 1;
         for (int a = 0; a < d->dim; ++a) Nc *= d->n_coarse[a];
     }
-    const int rg = d->n_targets >= 4 ? 4 : d->n_targets;
+    const int R = d->target_kind == HJBP_TARGET_BALLS ? d->n_targets : d->n_parts;
+    const int rg = R >= 4 ? 4 : R;
     // outputs + codes/h + value buffers + colour planes (FP32 x3, FP64 x2 per group) + phi (R planes)
     size_t b = (size_t)N * (8 + 1 + 4 + 8 + 8 + 1 + 1 + 1 + 4 * 3 + 16);
-    if (Nc) b += (size_t)N * (8 + 1 + (size_t)rg * (4 * 3 + 8) + 8 * (size_t)d->n_targets) + (size_t)Nc * 40;
+    if (Nc) b += (size_t)N * (8 + 1 + (size_t)rg * (4 * 3 + 8) + 8 * (size_t)R) + (size_t)Nc * 40;
     return b + (size_t(8) << 20);
 }
 
