@@ -48,9 +48,15 @@ OPS_PER_UPDATE_3D = 8       # canonical trilinear update: 7 FMA + 1 min
 FAMILY = "sincos2d"
 
 
+PAPER_FAMILIES = {"paper-eikonal": W.eikonal_sectors, "paper-fan": W.fan, "paper-zermelo": W.zermelo}
+
+
 def problem(seed: int):
     if FAMILY == "sin3d":
         return W.sin3d(seed, n=N_FINE, n_coarse=N_COARSE, n_c=98, n_targets=8, radius=0.05, tol=1e-6)
+    if FAMILY in PAPER_FAMILIES:
+        # the paper's own tests (Table 1) at its Tables 5-9 sizes; no seed
+        return PAPER_FAMILIES[FAMILY](n=N_FINE, n_coarse=N_COARSE, n_c=32, parts=16, tol=1e-6)
     return W.sincos2d(seed, n=N_FINE, n_coarse=N_COARSE, n_c=64, n_targets=4, radius=0.05, tol=1e-6)
 
 
@@ -224,7 +230,7 @@ def run_ours(args, rank, world, dist):
             tu += u
             tt += t
         cpu = {"value": tu / tt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{tu // 64} node updates x 64 controls: applications of F (Eq. SLscheme) by the "
+               "sample": f"{tu // p.n_controls} node updates x {p.n_controls} controls: applications of F (Eq. SLscheme) by the "
                          f"single-threaded FP64 C oracle on 48-row bands of the same {N_FINE}^2 grid, {tt:.1f} s"}
 
     # patch boundary and add-ons of Sec. 6 (defaults: state constraints, none)
@@ -277,6 +283,12 @@ def run_ours(args, rank, world, dist):
         e1.synchronize()
         gms.append(e0.elapsed_time(e1))
     gstats = gplan.stats()
+    # patchy error E = U_P - U_global on the same fine grid (Sec. 4.2), both from the GPU
+    up, ug = plan.values(), gplan.values()
+    both = np.isfinite(up) & np.isfinite(ug)
+    ev = np.abs(up[both] - ug[both])
+    patchy_error = {"E1": float(ev.mean()) if ev.size else None, "Einf": float(ev.max()) if ev.size else None,
+                    "nodes": int(both.sum())}
     gplan.close()
 
     # end to end through the public API with host buffers
@@ -320,7 +332,7 @@ def run_ours(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": p.n_controls,
-                       "n_targets": p.n_targets,
+                       "n_targets": p.n_targets, "n_patches": p.n_patches, "family": FAMILY,
                        "tol": 1e-6, "seed": "rank", "precision": "FP32 sweeps, FP64 coarse/feedback/labels/polish",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
                        "patch_bc": args.bc, "warm_start": bool(args.warm), "causal_sweeps": bool(args.causal),
@@ -330,6 +342,7 @@ def run_ours(args, rank, world, dist):
             "plain_sl_solves_per_s": 1e3 / statistics.mean(gms),
             "plain_sl_ms": statistics.mean(gms),
             "plain_sl_node_control_updates": gstats["node_control_updates"],
+            "patchy_error_vs_plain": patchy_error,
             "node_control_updates_per_solve": s0["node_control_updates"],
             "sweeps": {k: s0[k] for k in ("sweeps_coarse", "sweeps_phi", "sweeps_reach", "sweeps_fine",
                                            "sweeps_polish", "sweeps_patch", "phi_refinements")},
@@ -439,9 +452,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--workload", default="sincos2d", choices=["sincos2d", "sin3d", "batched", "serving"],
+    ap.add_argument("--workload", default="sincos2d",
+                    choices=["sincos2d", "sin3d", "batched", "serving", "paper-eikonal", "paper-fan", "paper-zermelo"],
                     help="sincos2d: 2D patchy workload (default); sin3d: 3D patchy workload; batched: 512 "
-                         "problems, batch vs one at a time; serving: Poisson request stream, p50/p99")
+                         "problems, batch vs one at a time; serving: Poisson request stream, p50/p99; "
+                         "paper-*: the paper's Table 1 tests at 801^2 / 101^2, R = 16, 32 controls")
     ap.add_argument("--count", type=int, default=0, help="problems (batched: 512) / requests (serving: 2000)")
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
@@ -469,6 +484,10 @@ def main():
     if FAMILY == "sin3d":
         N_FINE, N_COARSE = args.n or 257, args.nc or 33
         WORKLOAD = f"patchy3d_sin_n{N_FINE}_c{N_COARSE}_nc98_R8"
+    elif FAMILY in PAPER_FAMILIES:
+        # the paper's "100^2 -> 800^2" (cells), R = 16, N_c = 32
+        N_FINE, N_COARSE = args.n or 801, args.nc or 101
+        WORKLOAD = f"{FAMILY}_n{N_FINE}_c{N_COARSE}_nc32_R16"
     else:
         N_FINE, N_COARSE = args.n or 2049, args.nc or 65
         WORKLOAD = f"patchy2d_sincos_n{N_FINE}_c{N_COARSE}_nc64_R4"

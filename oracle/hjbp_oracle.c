@@ -36,8 +36,11 @@
  *   R5  Target part j = nodes with |x - c_j| <= r_j (lowest j on overlap).
  *   R6  The coarse grid cannot resolve a ball thinner than its spacing k~.
  *       Coarse nodes with |x - c_j| <= r_j + k~ sqrt(d)/2 are boundary nodes
- *       of Step 1 with the value max(0, |x - c_j| - r_j) / c(x) (the time to
- *       reach the ball at the local speed; 0 inside it), lowest j first.
+ *       of Step 1 with the value max(0, |x - c_j| - r_j) / v(x) (the time to
+ *       reach the ball moving straight at it; 0 inside it), lowest j first;
+ *       v is the largest speed f allows towards the target: c(x) for
+ *       f = c(x) a, and for the drift f = s a + w the largest v with
+ *       |v e - w| = s, e the unit vector towards the target.
  *       With the value 0 on the whole enlarged set, U_P^(0) would vanish on
  *       a plateau around the ball where the feedback of Step 2 is all ties
  *       and its trajectories circle instead of reaching Omega_0^j.
@@ -235,6 +238,22 @@ double og_speed(const og_problem *p, const double x[3]) {
     }
 }
 
+/* Largest speed along the unit direction e that the dynamics allow at x
+   (R6): c(x) for f = c(x) a; for f = s a + w the v >= 0 with |v e - w| = s
+   (0 when e cannot be followed). */
+static double og_approach_speed(const og_problem *p, const double x[3], const double e[3]) {
+    if (p->dyn_kind != 1) return og_speed(p, x);
+    double ew = 0.0, ww = 0.0;
+    for (int d = 0; d < p->dim; ++d) {
+        ew += e[d] * p->drift[1 + d];
+        ww += p->drift[1 + d] * p->drift[1 + d];
+    }
+    const double disc = ew * ew + p->drift[0] * p->drift[0] - ww;
+    if (disc < 0.0) return 0.0;
+    const double v = ew + sqrt(disc);
+    return v > 0.0 ? v : 0.0;
+}
+
 /* Number of patches R: one per target row, or n_parts for a split target. */
 int og_parts(const og_problem *p) {
     return p->target_kind == 0 ? p->n_targets : p->n_parts;
@@ -243,8 +262,9 @@ int og_parts(const og_problem *p) {
 /* Target part of the point x (R5, R22), -1 outside the target; the balls or
    slab widened by extra (R6).  *gap gets the distance from x to the
    un-widened target (0 inside). */
-static int og_target_part(const og_problem *p, const double x[3], double extra, double *gap) {
+static int og_target_part(const og_problem *p, const double x[3], double extra, double *gap, double e[3]) {
     const int R = og_parts(p);
+    if (e) e[0] = e[1] = e[2] = 0.0;
     if (p->target_kind == 0) {
         for (int j = 0; j < p->n_targets; ++j) {
             const double *t = p->targets + (size_t)j * (p->dim + 1);
@@ -253,6 +273,8 @@ static int og_target_part(const og_problem *p, const double x[3], double extra, 
             const double dist = sqrt(r2);
             if (dist <= t[p->dim] + extra) {
                 if (gap) *gap = dist > t[p->dim] ? dist - t[p->dim] : 0.0;
+                if (e && dist > 0.0)
+                    for (int d = 0; d < p->dim; ++d) e[d] = (t[d] - x[d]) / dist;
                 return j;
             }
         }
@@ -263,6 +285,10 @@ static int og_target_part(const og_problem *p, const double x[3], double extra, 
         const double dx = x[0] - t[0], dy = x[1] - t[1];
         const double dist = sqrt(dx * dx + dy * dy);
         if (!(dist <= t[p->dim] + extra)) return -1;
+        if (e && dist > 0.0) {
+            e[0] = -dx / dist;
+            e[1] = -dy / dist;
+        }
         double th = atan2(dy, dx);
         if (th < 0.0) th += 2.0 * OG_PI;
         int j = (int)floor((double)R * th / (2.0 * OG_PI) + 1e-9);
@@ -274,6 +300,7 @@ static int og_target_part(const og_problem *p, const double x[3], double extra, 
     /* slab |x_1 - v| <= r split along x_2 */
     const double dist = fabs(x[0] - t[0]);
     if (!(dist <= t[p->dim] + extra)) return -1;
+    if (e && dist > 0.0) e[0] = x[0] < t[0] ? 1.0 : -1.0;
     const double lo1 = p->lo[1], hi1 = p->lo[1] + (double)(p->n[1] - 1) * p->k;
     int j = (int)floor((double)R * (x[1] - lo1) / (hi1 - lo1) + 1e-9);
     if (j >= R) j = R - 1;
@@ -292,7 +319,7 @@ int og_setup(const og_problem *p, double radius_extra, unsigned char *kind, int 
         double x[3];
         og_index3(p, i, idx);
         og_coords(p, idx, x);
-        int pj = og_target_part(p, x, radius_extra, NULL);
+        int pj = og_target_part(p, x, radius_extra, NULL, NULL);
         int ring = 0;
         for (int d = 0; d < p->dim; ++d)
             if (idx[d] == 0 || idx[d] == p->n[d] - 1) ring = 1;
@@ -778,11 +805,11 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
         Uc[i] = INFINITY;
         if (ckind[i] == OG_TARGET) {   /* R6: boundary value dist / c */
             int idx[3];
-            double x[3], gap = 0.0;
+            double x[3], gap = 0.0, e[3];
             og_index3(&pc, i, idx);
             og_coords(&pc, idx, x);
-            og_target_part(&pc, x, pc.k * sqrt((double)p->dim) / 2.0, &gap);
-            Uc[i] = gap > 0.0 ? gap / og_speed(&pc, x) : 0.0;
+            og_target_part(&pc, x, pc.k * sqrt((double)p->dim) / 2.0, &gap, e);
+            Uc[i] = gap > 0.0 ? gap / og_approach_speed(&pc, x, e) : 0.0;
         }
     }
     if (og_iterate(&pc, cupd, ch, Uc, tol_coarse, max_sweeps, order, &st->sweeps_coarse, &st->residual_coarse))

@@ -169,6 +169,25 @@ __device__ inline double speed_at(const SpeedParams &sp, double x0, double x1, d
     }
 }
 
+// Dynamics of the set-up (hjbp_dyn_kind): for HJBP_DYN_DRIFT, f = s a + w.
+struct DynParams {
+    int kind;
+    double s, w[3];
+};
+
+// Largest speed the dynamics allow along the unit direction e at a node of
+// speed c (the coarse boundary values): c for f = c(x) a; for f = s a + w the
+// v >= 0 with |v e - w| = s (0 when e cannot be followed).
+__device__ inline double approach_speed2(const DynParams &dp, double c, double e0, double e1) {
+    if (dp.kind != HJBP_DYN_DRIFT) return c;
+    const double ew = __dadd_rn(__dmul_rn(e0, dp.w[0]), __dmul_rn(e1, dp.w[1]));
+    const double ww = __dadd_rn(__dmul_rn(dp.w[0], dp.w[0]), __dmul_rn(dp.w[1], dp.w[1]));
+    const double disc = __dsub_rn(__dadd_rn(__dmul_rn(ew, ew), __dmul_rn(dp.s, dp.s)), ww);
+    if (disc < 0.0) return 0.0;
+    const double v = __dadd_rn(ew, __dsqrt_rn(disc));
+    return v > 0.0 ? v : 0.0;
+}
+
 // A node whose speed is at most this cannot move (it is treated like the
 // ghost ring unless it is a target node).
 constexpr double kStoppedSpeed = 1e-12;
@@ -184,15 +203,21 @@ struct Grid2 {
 // widened by extra (the coarse grid's boundary band); *gap = distance to the
 // un-widened target (0 inside).  Explicitly rounded operations, so that the
 // decisions follow x = lo + i k and the definitions of hjbp_target_kind.
+// *e (optional) gets the unit direction from the point towards the target.
 __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x0, double x1, double extra,
-                                   double *gap) {
+                                   double *gap, double *e = nullptr) {
     const double pi = 3.14159265358979323846;
+    if (e) e[0] = e[1] = 0.0;
     if (ts.kind == HJBP_TARGET_BALLS) {
         for (int j = 0; j < ts.n; ++j) {
             const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]);
             const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)));
             if (d <= __dadd_rn(ts.r[j], extra)) {
                 *gap = d > ts.r[j] ? __dsub_rn(d, ts.r[j]) : 0.0;
+                if (e && d > 0.0) {
+                    e[0] = __ddiv_rn(__dsub_rn(ts.c0[j], x0), d);
+                    e[1] = __ddiv_rn(__dsub_rn(ts.c1[j], x1), d);
+                }
                 return j;
             }
         }
@@ -203,6 +228,10 @@ __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x
         const double d0 = __dsub_rn(x0, ts.c0[0]), d1 = __dsub_rn(x1, ts.c1[0]);
         const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)));
         if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+        if (e && d > 0.0) {
+            e[0] = __ddiv_rn(-d0, d);
+            e[1] = __ddiv_rn(-d1, d);
+        }
         double th = atan2(d1, d0);
         if (th < 0.0) th = __dadd_rn(th, 2.0 * pi);
         int j = (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)R, th), 2.0 * pi), 1e-9));
@@ -213,6 +242,7 @@ __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x
     }
     const double d = fabs(__dsub_rn(x0, ts.c0[0]));
     if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+    if (e && d > 0.0) e[0] = x0 < ts.c0[0] ? 1.0 : -1.0;
     const double hi1 = __dadd_rn(g.lo1, __dmul_rn((double)(g.n1 - 1), g.k));
     int j = (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)R, __dsub_rn(x1, g.lo1)), __dsub_rn(hi1, g.lo1)), 1e-9));
     if (j >= R) j = R - 1;

@@ -40,14 +40,14 @@ namespace hjbp {
 // membership is decided exactly as x = lo + i k, r^2 = sum (x - c)^2 dictate.
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
                           int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
-                          double *__restrict__ fixed) {
+                          double *__restrict__ fixed, DynParams dp) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
         const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
         const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
-        double gap = 0.0;
-        const int part = target_part2(ts, g, x0, x1, extra, &gap);
+        double gap = 0.0, e[2];
+        const int part = target_part2(ts, g, x0, x1, extra, &gap, e);
         const bool ring = ix == 0 || iy == 0 || ix == g.n0 - 1 || iy == g.n1 - 1;
         const double c = speed_at(sp, x0, x1, 0.0);
         const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
@@ -55,7 +55,10 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
         code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped) ? kHard : (int8_t)0);
         if (h32) h32[i] = (float)hh;
         if (h64) h64[i] = hh;
-        if (fixed) fixed[i] = (part >= 0 && boundary_values && gap > 0.0) ? __ddiv_rn(gap, c) : 0.0;
+        // coarse boundary value (R6): the gap over the speed towards the target
+        if (fixed)
+            fixed[i] = (part >= 0 && boundary_values && gap > 0.0) ? __ddiv_rn(gap, approach_speed2(dp, c, e[0], e[1]))
+                                                                  : 0.0;
     }
 }
 
@@ -2203,6 +2206,14 @@ Cone2 make_cones(const hjbp_plan &p, double *mean_size) {
     return cn;
 }
 
+DynParams make_dyn(const hjbp_plan &p) {
+    DynParams dp;
+    dp.kind = p.desc.dyn;
+    dp.s = p.desc.drift[0];
+    for (int i = 0; i < 3; ++i) dp.w[i] = p.desc.drift[1 + i];
+    return dp;
+}
+
 SpeedParams make_speed(const hjbp_plan &p) {
     SpeedParams sp;
     sp.kind = p.desc.speed;
@@ -2512,7 +2523,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     float *h32 = fp32 ? alloc_n<float>(p, N) : nullptr;
     unsigned long long *updates = alloc_n<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
-    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr);
+    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr, make_dyn(p));
     ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "setup");
     Sched sched = make_sched(p, g, hist);
@@ -2528,7 +2539,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         double *cfix = alloc_n<double>(p, Nc);
         double *cb0 = alloc_n<double>(p, Nc), *cb1 = alloc_n<double>(p, Nc);
         k_setup2d<<<grid_for(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(2.0) / 2.0, 1, ccode, nullptr, ch64,
-                                                cfix);
+                                                cfix, make_dyn(p));
                                                 ++p.stats.kernel_launches;
         k_merge_targets<<<grid_for(Nc), 256, 0, st>>>(Nc, ccode);
         ++p.stats.kernel_launches;

@@ -30,7 +30,7 @@ namespace hjbp {
 
 // Kernels defined in kernels2d.cu (the same ones hjbp_solve launches).
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values, int8_t *code,
-                          float *h32, double *h64, double *fixed);
+                          float *h32, double *h64, double *fixed, DynParams dp);
 __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
                                                 ReachTable2 rt, int passes, const double *dterm,
@@ -288,7 +288,9 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     const int cap = desc->max_sweeps > 0 ? desc->max_sweeps : 1000000;
 
     // Set-up: node codes and h, all target parts merged (one global target).
-    k_setup2d<<<blocks_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, nullptr, h64, nullptr);
+    DynParams dp;
+    std::memset(&dp, 0, sizeof(dp));   // f = c(x) a
+    k_setup2d<<<blocks_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, nullptr, h64, nullptr, dp);
     NA_CHECK(cudaGetLastError());
     NA_CHECK(cudaMemcpyAsync(code, code0, (size_t)N, cudaMemcpyDeviceToDevice, st));
     k_merge_targets<<<blocks_for(N), 256, 0, st>>>(N, code);
