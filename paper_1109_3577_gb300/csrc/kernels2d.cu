@@ -1444,7 +1444,10 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     const int64_t N = (int64_t)g.n0 * g.n1;
-    __shared__ PhiSmem<RG, kSource> sm;
+    // dynamic shared memory: the image of 8 colours with its source exceeds
+    // the 48 KB of static shared memory
+    extern __shared__ __align__(16) unsigned char phi_smem_raw[];
+    PhiSmem<RG, kSource> &sm = *reinterpret_cast<PhiSmem<RG, kSource> *>(phi_smem_raw);
     const int lane = threadIdx.x;
     const int ncu = pc->nc;
     for (int m = lane; m < ncu; m += 32) {
@@ -2594,7 +2597,8 @@ hjbp_status solve2d(hjbp_plan &p) {
             }
             PhiCtl *dpc = static_cast<PhiCtl *>(p.dev_alloc(sizeof(PhiCtl)));
             check_cuda(cudaMemcpyAsync(dpc, &hpc, sizeof(PhiCtl), cudaMemcpyHostToDevice, st), "phi ctl");
-            const int RG = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+            // colours per transport pass: up to 8 (one front propagation per group)
+            const int RG = R > 4 ? 8 : (R >= 3 ? 4 : (R == 2 ? 2 : 1));
             float *f0 = alloc_n<float>(p, N * RG), *f1 = alloc_n<float>(p, N * RG), *r32 = alloc_n<float>(p, N * RG);
             double *phig = alloc_n<double>(p, N * RG);
             float *rmax = alloc_n<float>(p, 1);
@@ -2602,15 +2606,19 @@ hjbp_status solve2d(hjbp_plan &p) {
             for (int j0 = 0; j0 < R; j0 += RG) {
                 const int rg = std::min(RG, R - j0);
                 // colours past R in the last group see no target and stay 0
-                const int rgl = rg >= 4 ? 4 : (rg == 3 ? 4 : rg);
+                const int rgl = rg > 4 ? 8 : (rg >= 3 ? 4 : rg);
                 auto launch_group = [&](auto tag) {
                     constexpr int G = decltype(tag)::value;
+                    check_cuda(cudaFuncSetAttribute(k_phi2d<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)sizeof(PhiSmem<G, false>)), "phi smem");
+                    check_cuda(cudaFuncSetAttribute(k_phi2d<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)sizeof(PhiSmem<G, true>)), "phi smem");
                     // FP32 bulk solve
                     k_phi_init2d<G><<<grid_for(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++p.stats.kernel_launches;
                     RunResult rp = run_tiles(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par, int) {
-                        k_phi2d<G, false><<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d,
-                                                                       par, prounds, dpc);
+                        k_phi2d<G, false><<<sched.ntiles, 32, sizeof(PhiSmem<G, false>), st>>>(
+                            g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc);
                         ++p.stats.kernel_launches;
                     });
                     S.sweeps_phi += rp.launches;
@@ -2631,8 +2639,8 @@ hjbp_status solve2d(hjbp_plan &p) {
                         ++p.stats.kernel_launches;
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         RunResult rc = run_tiles(p, g, sched, told, cap, [&](int par, int) {
-                            k_phi2d<G, true><<<sched.ntiles, 32, 0, st>>>(g, code0, p.astar, f0, f1, r32, sched.d,
-                                                                          par, prounds, dpc);
+                            k_phi2d<G, true><<<sched.ntiles, 32, sizeof(PhiSmem<G, true>), st>>>(
+                                g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dpc);
                             ++p.stats.kernel_launches;
                         });
                         S.sweeps_phi += rc.launches;
@@ -2642,7 +2650,8 @@ hjbp_status solve2d(hjbp_plan &p) {
                     check_cuda(cudaMemcpyAsync(p.phi + (int64_t)j0 * N, phig, sizeof(double) * N * rg,
                                                cudaMemcpyDeviceToDevice, st), "phi copy");
                 };
-                if (rgl == 4) launch_group(std::integral_constant<int, 4>());
+                if (rgl == 8) launch_group(std::integral_constant<int, 8>());
+                else if (rgl == 4) launch_group(std::integral_constant<int, 4>());
                 else if (rgl == 2) launch_group(std::integral_constant<int, 2>());
                 else launch_group(std::integral_constant<int, 1>());
             }
