@@ -68,6 +68,16 @@ struct Ctl3 {
     float kw[8][kMaxControls];   // kw[0] = kap, kw[b] = kap w_b
 };
 
+// Literal weights in the octant order of CtlTable3 (FP64, and rounded to FP32
+// for the filter pass), with each control's index in the caller's order.
+struct CtlLit3 {
+    int nc;
+    int obeg[9];
+    int16_t idx[kMaxControls];
+    double w[8][kMaxControls];
+    float f[8][kMaxControls];
+};
+
 // Masks of positive-weight corners (bits 0..6 for b = 1..7) present in each octant.
 struct ReachTable3 {
     uint32_t present[8][4];
@@ -235,20 +245,44 @@ __device__ __forceinline__ void plane_node(int dir, int st, int tid, int &lx, in
 
 // --------------------------------------------------------- value sweep 3D --
 
+// One control's weights in shared memory, k[0..6] = kap w_b (b = 1..7) and
+// k[7] = kap, aligned so that they load as two (FP32) or four (FP64)
+// 16-byte vectors.
+template <typename T> struct alignas(16) W3 {
+    T k[8];
+};
+
+template <typename T> __device__ __forceinline__ void load_w3(const W3<T> &w, T out[8]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = reinterpret_cast<const float4 *>(w.k)[0], b = reinterpret_cast<const float4 *>(w.k)[1];
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+        out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 a = reinterpret_cast<const double2 *>(w.k)[q];
+            out[2 * q] = a.x;
+            out[2 * q + 1] = a.y;
+        }
+    }
+}
+
+// The update of node (lx, ly, lz); mask has bit 9 dz + 3 dy + dx set when the
+// neighbour (dx-1, dy-1, dz-1) belongs to the node's patch or target part
+// (formed once per launch), everything else reads +inf.  tab: the weights in
+// shared memory, in the octant order of ct.
 template <typename T>
-__device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int lz, int8_t cd, T hh,
-                                        const CtlTable3<T> &ct) {
-    const int8_t tg = (int8_t)(cd + kTargetBase);
+__device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int lz, uint32_t mask, T hh,
+                                        const CtlTable3<T> &ct, const W3<T> *tab) {
     T nb[3][3][3];
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const int8_t q = sm.c[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx];
-                nb[dz][dy][dx] = (q == cd || q == tg) ? sm.u[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx] : Num<T>::big();
-            }
+            for (int dx = 0; dx < 3; ++dx)
+                nb[dz][dy][dx] = ((mask >> (9 * dz + 3 * dy + dx)) & 1u) ? sm.u[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]
+                                                                        : Num<T>::big();
     T b0 = Num<T>::big(), b1 = Num<T>::big();
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -259,19 +293,24 @@ __device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int 
         int m = ct.obeg[o];
         const int me = ct.obeg[o + 1];
         for (; m + 1 < me; m += 2) {
-            T v0 = ct.kap[m] * hh, v1 = ct.kap[m + 1] * hh;
+            T w0[8], w1[8];
+            load_w3(tab[m], w0);
+            load_w3(tab[m + 1], w1);
+            T v0 = w0[7] * hh, v1 = w1[7] * hh;
 #pragma unroll
             for (int b = 0; b < 7; ++b) {
-                v0 = fma(ct.kw[b][m], c[b], v0);
-                v1 = fma(ct.kw[b][m + 1], c[b], v1);
+                v0 = fma(w0[b], c[b], v0);
+                v1 = fma(w1[b], c[b], v1);
             }
             b0 = v0 < b0 ? v0 : b0;
             b1 = v1 < b1 ? v1 : b1;
         }
         if (m < me) {
-            T v0 = ct.kap[m] * hh;
+            T w0[8];
+            load_w3(tab[m], w0);
+            T v0 = w0[7] * hh;
 #pragma unroll
-            for (int b = 0; b < 7; ++b) v0 = fma(ct.kw[b][m], c[b], v0);
+            for (int b = 0; b < 7; ++b) v0 = fma(w0[b], c[b], v0);
             b0 = v0 < b0 ? v0 : b0;
         }
     }
@@ -288,24 +327,51 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     __shared__ Tile3<T> sm;
-    load_tile3(g, s, code, b0, b1, x0, y0, z0, sm);
+    // per interior node: neighbour mask (bit 31: the node is free) and h
+    __shared__ uint32_t mk[kT3][kT3][kT3];
+    __shared__ T hs[kT3][kT3][kT3];
+    __shared__ W3<T> tab[kMaxControls];
+    for (int m = threadIdx.x; m < ct.nc; m += blockDim.x) {
+        for (int b = 0; b < 7; ++b) tab[m].k[b] = ct.kw[b][m];
+        tab[m].k[7] = ct.kap[m];
+    }
+    load_tile3(g, s, code, b0, b1, x0, y0, z0, sm);   // ends with a block barrier
     const int tid = threadIdx.x;
     int nfree = 0;
     for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
-        const int8_t cd = sm.c[e / 64 + 1][(e / 8) % 8 + 1][e % 8 + 1];
-        nfree += (cd >= 0 && cd < kTargetBase);
+        const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
+        const int8_t cd = sm.c[lz + 1][ly + 1][lx + 1];
+        uint32_t m = 0;
+        T hv = (T)0;
+        if (cd >= 0 && cd < kTargetBase) {
+            const int8_t tg = (int8_t)(cd + kTargetBase);
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int8_t q = sm.c[lz + dz][ly + dy][lx + dx];
+                        m |= (uint32_t)(q == cd || q == tg) << (9 * dz + 3 * dy + dx);
+                    }
+            m |= 0x80000000u;
+            ++nfree;
+            hv = h[((int64_t)(z0 + lz) * g.n1 + (y0 + ly)) * g.n0 + (x0 + lx)];
+        }
+        mk[lz][ly][lx] = m;
+        hs[lz][ly][lx] = hv;
     }
+    __syncthreads();
     for (int rd = 0; rd < rounds; ++rd)
         for (int dir = 0; dir < 6; ++dir)
             for (int st = 0; st < kT3; ++st) {
                 int lx, ly, lz;
                 plane_node(dir, st, tid, lx, ly, lz);
-                const int8_t cd = sm.c[lz][ly][lx];
-                const bool active = cd >= 0 && cd < kTargetBase;
+                const uint32_t m = mk[lz - 1][ly - 1][lx - 1];
+                const bool active = (m & 0x80000000u) != 0;
                 T nw = sm.u[lz][ly][lx];
                 if (active) {
-                    const int64_t i = ((int64_t)(z0 - 1 + lz) * g.n1 + (y0 - 1 + ly)) * g.n0 + (x0 - 1 + lx);
-                    const T best = sl_update3(sm, lx, ly, lz, cd, h[i], ct);
+                    const T best = sl_update3(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
                     if (best < Num<T>::thresh()) nw = best < nw ? best : nw;
                 }
                 __syncthreads();
@@ -506,28 +572,102 @@ __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, cons
 }
 
 // Eq. (feedbackcontrol) with literal trilinear weights, lowest index on ties.
+// Pass 1 in FP32 over every control finds the minimum up to its rounding;
+// pass 2 evaluates in FP64 only the controls whose FP32 value is within
+// 2^-17 (h + max |U|) of it (more than twice the FP32 error bound of an
+// 8-term convex combination plus h), so the FP64 argmin is the one a full
+// FP64 pass finds; exact FP64 ties go to the lowest caller index.
 __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
-                             const double *__restrict__ u0, uint8_t *__restrict__ astar, const Ctl3 *__restrict__ ct) {
+                             const double *__restrict__ u0, uint8_t *__restrict__ astar,
+                             const CtlLit3 *__restrict__ cl) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
+    // the weights in shared memory, loaded as 16-byte vectors
+    __shared__ W3<float> wf[kMaxControls];
+    __shared__ W3<double> wd[kMaxControls];
+    __shared__ int16_t widx[kMaxControls];
+    __shared__ int obeg[9];
+    for (int m = threadIdx.x; m < cl->nc; m += blockDim.x) {
+        for (int b = 0; b < 8; ++b) {
+            wf[m].k[b] = cl->f[b][m];
+            wd[m].k[b] = cl->w[b][m];
+        }
+        widx[m] = cl->idx[m];
+    }
+    if (threadIdx.x < 9) obeg[threadIdx.x] = cl->obeg[threadIdx.x];
+    __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
         if (c < 0 || c >= kTargetBase || u0[i] >= Num<double>::thresh()) {
             astar[i] = kNoControl;
             continue;
         }
+        // free nodes are interior, so the 3x3x3 neighbourhood lies in the grid
+        double nb[3][3][3];
+        float nf[3][3][3];
+        float amax = 0.f;
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const double v = u0[i + (dz - 1) * sz + (dy - 1) * sy + (dx - 1)];
+                    const bool fin = v < Num<double>::thresh();
+                    nb[dz][dy][dx] = v;
+                    nf[dz][dy][dx] = fin ? (float)v : Num<float>::big();
+                    if (fin) amax = fmaxf(amax, fabsf((float)v));
+                }
         const double hh = h[i];
+        const float hf = (float)hh;
+        float b32 = Num<float>::big();
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
+            float c8[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
+            for (int m = obeg[o]; m < obeg[o + 1]; ++m) {
+                float w[8];
+                load_w3(wf[m], w);
+                float v = hf;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) v = fmaf(w[b], c8[b], v);
+                b32 = v < b32 ? v : b32;
+            }
+        }
         double best = Num<double>::big();
         int arg = kNoControl;
-        for (int m = 0; m < ct->nc; ++m) {
-            const int64_t dx = ct->sx[m], dy = (int64_t)ct->sy[m] * g.n0, dz = (int64_t)ct->sz[m] * g.n0 * g.n1;
-            double v = hh;
-            for (int b = 0; b < 8; ++b) {
-                const int64_t j = i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0);
-                v += ct->w[b][m] * u0[j];
-            }
-            if (v < best) {
-                best = v;
-                arg = m;
+        if (b32 < Num<float>::thresh()) {
+            const float lim = b32 + ldexpf(hf + amax, -17);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
+                float c8[8];
+                double d8[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
+                    d8[b] = nb[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
+                }
+                for (int m = obeg[o]; m < obeg[o + 1]; ++m) {
+                    float w[8];
+                    load_w3(wf[m], w);
+                    float v32 = hf;
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) v32 = fmaf(w[b], c8[b], v32);
+                    if (v32 > lim) continue;
+                    double wdv[8];
+                    load_w3(wd[m], wdv);
+                    double v = hh;
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) v += wdv[b] * d8[b];
+                    const int idx = widx[m];
+                    if (v < best || (v == best && idx < arg)) {
+                        best = v;
+                        arg = idx;
+                    }
+                }
             }
         }
         astar[i] = best < Num<double>::thresh() ? (uint8_t)arg : kNoControl;
@@ -550,11 +690,15 @@ __global__ void k_phi_init3d(int64_t N, const int8_t *__restrict__ code, int j0,
     }
 }
 
-template <int RG> struct Phi3Smem {
+template <int RG, bool kS> struct Phi3Smem {
     float u[RG][kT3 + 2][kT3 + 2][kT3 + 3];
-    float src[RG][kT3][kT3][kT3 + 1];
+    float src[kS ? RG : 1][kS ? kT3 : 1][kS ? kT3 : 1][kS ? kT3 + 1 : 1];   // correction source only
     int8_t c[kT3 + 2][kT3 + 2][kT3 + 4];
     uint8_t a[kT3][kT3][kT3 + 4];
+    // the control table: weights kw[0..7] (two 16-byte vectors) and corner
+    // signs (bit 0..2: x, y, z positive) of every control
+    float4 tw[kMaxControls][2];
+    uint8_t toff[kMaxControls];
     float red[2];
 };
 
@@ -569,9 +713,13 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
-    __shared__ Phi3Smem<RG> sm;
+    __shared__ Phi3Smem<RG, kSource> sm;
+    __shared__ unsigned salive;   // colours nonzero somewhere in the tile image or its source
     constexpr int E = kT3 + 2;
     const int tid = threadIdx.x;
+    if (tid == 0) salive = 0u;
+    __syncthreads();
+    unsigned alive = 0;
     for (int e = tid; e < E * E * E; e += blockDim.x) {
         const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
         const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
@@ -584,7 +732,11 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
             const int tt = tile_of3(g, x, y, z);
             const float *bs = (tt >= 0 && s.latest[tt]) ? b1 : b0;
 #pragma unroll
-            for (int q = 0; q < RG; ++q) sm.u[q][lz][ly][lx] = bs[(int64_t)q * N + i];
+            for (int q = 0; q < RG; ++q) {
+                const float v = bs[(int64_t)q * N + i];
+                sm.u[q][lz][ly][lx] = v;
+                alive |= (unsigned)(v != 0.0f) << q;
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < RG; ++q) sm.u[q][lz][ly][lx] = 0.0f;
@@ -593,13 +745,26 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
             sm.a[lz - 1][ly - 1][lx - 1] = in ? astar[i] : kNoControl;
             if (kSource) {
 #pragma unroll
-                for (int q = 0; q < RG; ++q) sm.src[q][lz - 1][ly - 1][lx - 1] = in ? src[(int64_t)q * N + i] : 0.0f;
+                for (int q = 0; q < RG; ++q) {
+                    const float v = in ? src[(int64_t)q * N + i] : 0.0f;
+                    sm.src[q][lz - 1][ly - 1][lx - 1] = v;
+                    alive |= (unsigned)(v != 0.0f) << q;
+                }
             }
         }
         sm.c[lz][ly][lx] = cd;
     }
     __syncthreads();
-    for (int rd = 0; rd < rounds; ++rd)
+    if (alive) atomicOr(&salive, alive);
+    for (int m = tid; m < pc->nc; m += blockDim.x) {
+        sm.toff[m] = (uint8_t)((pc->sx[m] > 0 ? 1u : 0u) | (pc->sy[m] > 0 ? 2u : 0u) | (pc->sz[m] > 0 ? 4u : 0u));
+        sm.tw[m][0] = make_float4(pc->kw[0][m], pc->kw[1][m], pc->kw[2][m], pc->kw[3][m]);
+        sm.tw[m][1] = make_float4(pc->kw[4][m], pc->kw[5][m], pc->kw[6][m], pc->kw[7][m]);
+    }
+    __syncthreads();
+    // a colour that is zero over the whole image stays zero: skip it (uniform per tile)
+    const unsigned live = salive;
+    for (int rd = 0; rd < rounds && live; ++rd)
         for (int dir = 0; dir < 6; ++dir)
             for (int st = 0; st < kT3; ++st) {
                 int lx, ly, lz;
@@ -609,16 +774,23 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                 const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
                 float nw[RG];
                 if (active) {
-                    const int sx = pc->sx[a], sy = pc->sy[a], sz = pc->sz[a];
+                    const unsigned of = sm.toff[a];
+                    const int sx = (of & 1u) ? 1 : -1, sy = (of & 2u) ? 1 : -1, sz = (of & 4u) ? 1 : -1;
+                    const float4 w0 = sm.tw[a][0], w1 = sm.tw[a][1];
+                    const float kw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                     for (int q = 0; q < RG; ++q) {
+                        if (!((live >> q) & 1u)) {
+                            nw[q] = 0.0f;
+                            continue;
+                        }
                         float v = 0.0f;
 #pragma unroll
                         for (int b = 1; b < 8; ++b)
-                            v = fmaf(pc->kw[b][a],
+                            v = fmaf(kw[b],
                                      sm.u[q][lz + ((b & 4) ? sz : 0)][ly + ((b & 2) ? sy : 0)][lx + ((b & 1) ? sx : 0)], v);
                         if (kSource) {
-                            nw[q] = fmaf(pc->kw[0][a], sm.src[q][lz - 1][ly - 1][lx - 1], v);
+                            nw[q] = fmaf(kw[0], sm.src[q][lz - 1][ly - 1][lx - 1], v);
                         } else {
                             const float o = sm.u[q][lz][ly][lx];
                             nw[q] = v > o ? v : o;
@@ -628,7 +800,8 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                 __syncthreads();
                 if (active) {
 #pragma unroll
-                    for (int q = 0; q < RG; ++q) sm.u[q][lz][ly][lx] = nw[q];
+                    for (int q = 0; q < RG; ++q)
+                        if ((live >> q) & 1u) sm.u[q][lz][ly][lx] = nw[q];
                 }
                 __syncthreads();
             }
@@ -636,17 +809,21 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     float *dst = cur ? b0 : b1;
     const float *old = cur ? b1 : b0;
     float mc = 0.f;
-    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
+    // predicated and unrolled so that the reads of the previous values overlap
+#pragma unroll
+    for (int k = 0; k < kT3 * kT3 * kT3 / kT3n; ++k) {
+        const int e = tid + k * kT3n;
         const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
-        const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+        if (x <= g.n0 - 2 && y <= g.n1 - 2 && z <= g.n2 - 2) {
+            const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
 #pragma unroll
-        for (int q = 0; q < RG; ++q) {
-            const float v = sm.u[q][lz + 1][ly + 1][lx + 1];
-            const float o = old[(int64_t)q * N + i];
-            dst[(int64_t)q * N + i] = v;
-            mc = fmaxf(mc, fabsf(v - o));
+            for (int q = 0; q < RG; ++q) {
+                const float v = sm.u[q][lz + 1][ly + 1][lx + 1];
+                const float o = old[(int64_t)q * N + i];
+                dst[(int64_t)q * N + i] = v;
+                mc = fmaxf(mc, fabsf(v - o));
+            }
         }
     }
     mc = block_max64(mc, sm.red);
@@ -768,6 +945,18 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                            const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
                            const CtlTable3<float> c32, const CtlTable3<double> c64) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    // the weights in shared memory (k[0..6] = kap w_b, k[7] = kap), 16-byte vectors
+    __shared__ W3<float> t32[kMaxControls];
+    __shared__ W3<double> t64[kMaxControls];
+    for (int m = threadIdx.x; m < c32.nc; m += blockDim.x) {
+        for (int b = 0; b < 7; ++b) {
+            t32[m].k[b] = c32.kw[b][m];
+            t64[m].k[b] = c64.kw[b][m];
+        }
+        t32[m].k[7] = c32.kap[m];
+        t64[m].k[7] = c64.kap[m];
+    }
+    __syncthreads();
     float mc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t cd = code[i];
@@ -804,9 +993,11 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
 #pragma unroll
                 for (int b = 1; b < 8; ++b) c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
                 for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
-                    float w = c32.kap[m] * hf;
+                    float t[8];
+                    load_w3(t32[m], t);
+                    float w = t[7] * hf;
 #pragma unroll
-                    for (int b = 0; b < 7; ++b) w = fmaf(c32.kw[b][m], c[b], w);
+                    for (int b = 0; b < 7; ++b) w = fmaf(t[b], c[b], w);
                     b32 = w < b32 ? w : b32;
                 }
             }
@@ -824,13 +1015,17 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                         cdd[b - 1] = nb[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
                     }
                     for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
-                        float w = c32.kap[m] * hf;
+                        float t[8];
+                        load_w3(t32[m], t);
+                        float w = t[7] * hf;
 #pragma unroll
-                        for (int b = 0; b < 7; ++b) w = fmaf(c32.kw[b][m], c[b], w);
+                        for (int b = 0; b < 7; ++b) w = fmaf(t[b], c[b], w);
                         if (w <= lim) {
-                            double x = c64.kap[m] * hh;
+                            double td[8];
+                            load_w3(t64[m], td);
+                            double x = td[7] * hh;
 #pragma unroll
-                            for (int b = 0; b < 7; ++b) x = fma(c64.kw[b][m], cdd[b], x);
+                            for (int b = 0; b < 7; ++b) x = fma(td[b], cdd[b], x);
                             best = x < best ? x : best;
                         }
                     }
@@ -1004,6 +1199,31 @@ Ctl3 make_ctl3(const hjbp_plan &p) {
         c.kw[0][m] = (float)kap;
         for (int cc = 1; cc < 8; ++cc) c.kw[cc][m] = (float)(kap * w[cc]);
     }
+    return c;
+}
+
+CtlLit3 make_lit3(const hjbp_plan &p) {
+    CtlLit3 c;
+    std::memset(&c, 0, sizeof(c));
+    c.nc = p.desc.n_controls;
+    int pos = 0;
+    for (int o = 0; o < 8; ++o) {
+        c.obeg[o] = pos;
+        for (int m = 0; m < c.nc; ++m) {
+            const double *a = &p.controls[3 * m];
+            if ((a[0] >= 0.0 ? 1 : 0) + (a[1] >= 0.0 ? 2 : 0) + (a[2] >= 0.0 ? 4 : 0) != o) continue;
+            const double b[3] = {std::fabs(a[0]), std::fabs(a[1]), std::fabs(a[2])};
+            for (int cc = 0; cc < 8; ++cc) {
+                double w = 1.0;
+                for (int d = 0; d < 3; ++d) w *= (cc >> d & 1) ? b[d] : 1.0 - b[d];
+                c.w[cc][pos] = w;
+                c.f[cc][pos] = (float)w;
+            }
+            c.idx[pos] = (int16_t)m;
+            ++pos;
+        }
+    }
+    c.obeg[8] = pos;
     return c;
 }
 
@@ -1235,7 +1455,12 @@ hjbp_status solve3d(hjbp_plan &p) {
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev3 e2(st);
         k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0);
-        k_feedback3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, dct);
+        {
+            const CtlLit3 hl = make_lit3(p);
+            CtlLit3 *dl = static_cast<CtlLit3 *>(p.dev_alloc(sizeof(CtlLit3)));
+            check_cuda(cudaMemcpyAsync(dl, &hl, sizeof(CtlLit3), cudaMemcpyHostToDevice, st), "feedback table");
+            k_feedback3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, dl);
+        }
         S.kernel_launches += 2;
         check_cuda(cudaGetLastError(), "feedback3");
         Ev3 e3(st);
