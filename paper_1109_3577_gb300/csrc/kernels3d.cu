@@ -602,8 +602,10 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
             astar[i] = kNoControl;
             continue;
         }
-        // free nodes are interior, so the 3x3x3 neighbourhood lies in the grid
-        double nb[3][3][3];
+        // free nodes are interior, so the 3x3x3 neighbourhood lies in the grid.
+        // Only FP32 copies stay live (one conversion each, the finiteness test
+        // on the FP32 value: FP64 compares and conversions run at 1/64 rate);
+        // the rare FP64 candidates re-read their corners.
         float nf[3][3][3];
         float amax = 0.f;
 #pragma unroll
@@ -612,11 +614,10 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx) {
-                    const double v = u0[i + (dz - 1) * sz + (dy - 1) * sy + (dx - 1)];
-                    const bool fin = v < Num<double>::thresh();
-                    nb[dz][dy][dx] = v;
-                    nf[dz][dy][dx] = fin ? (float)v : Num<float>::big();
-                    if (fin) amax = fmaxf(amax, fabsf((float)v));
+                    const float f = (float)u0[i + (dz - 1) * sz + (dy - 1) * sy + (dx - 1)];
+                    const bool fin = f < Num<float>::thresh();   // U0 is finite below 1e6, +inf is 1e300
+                    nf[dz][dy][dx] = fin ? f : Num<float>::big();
+                    if (fin) amax = fmaxf(amax, fabsf(f));
                 }
         const double hh = h[i];
         const float hf = (float)hh;
@@ -644,12 +645,8 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
             for (int o = 0; o < 8; ++o) {
                 const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
                 float c8[8];
-                double d8[8];
 #pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
-                    d8[b] = nb[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
-                }
+                for (int b = 0; b < 8; ++b) c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
                 for (int m = obeg[o]; m < obeg[o + 1]; ++m) {
                     float w[8];
                     load_w3(wf[m], w);
@@ -661,7 +658,11 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
                     load_w3(wd[m], wdv);
                     double v = hh;
 #pragma unroll
-                    for (int b = 0; b < 8; ++b) v += wdv[b] * d8[b];
+                    for (int b = 0; b < 8; ++b) {
+                        const int64_t j = i + (int64_t)(((b & 4) ? oz : 1) - 1) * sz +
+                                          (int64_t)(((b & 2) ? oy : 1) - 1) * sy + (((b & 1) ? ox : 1) - 1);
+                        v += wdv[b] * u0[j];
+                    }
                     const int idx = widx[m];
                     if (v < best || (v == best && idx < arg)) {
                         best = v;
@@ -966,8 +967,10 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
             const int64_t r = i / g.n0;
             const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
             const int8_t tg = (int8_t)(cd + kTargetBase);
-            double nb[3][3][3];
+            // only FP32 copies and a usability mask stay live (FP64 compares and
+            // conversions run at 1/64 rate); FP64 candidates re-read their corners
             float nf[3][3][3];
+            uint32_t use = 0;
             float amax = 0.f;
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz)
@@ -977,11 +980,11 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                     for (int dx = 0; dx < 3; ++dx) {
                         const int64_t j = ((int64_t)(iz - 1 + dz) * g.n1 + (iy - 1 + dy)) * g.n0 + (ix - 1 + dx);
                         const int8_t q = code[j];
-                        const double w = uin[j];
-                        const bool fin = (q == cd || q == tg) && w < Num<double>::thresh();
-                        nb[dz][dy][dx] = fin ? w : Num<double>::big();
-                        nf[dz][dy][dx] = fin ? (float)w : Num<float>::big();
-                        if (fin) amax = fmaxf(amax, fabsf((float)w));
+                        const float f = (float)uin[j];
+                        const bool fin = (q == cd || q == tg) && f < Num<float>::thresh();
+                        nf[dz][dy][dx] = fin ? f : Num<float>::big();
+                        use |= (uint32_t)fin << (9 * dz + 3 * dy + dx);
+                        if (fin) amax = fmaxf(amax, fabsf(f));
                     }
             const double hh = h[i];
             const float hf = (float)hh;
@@ -1008,12 +1011,8 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                 for (int o = 0; o < 8; ++o) {
                     const int sx = (o & 1) ? 2 : 0, sy = (o & 2) ? 2 : 0, sz = (o & 4) ? 2 : 0;
                     float c[7];
-                    double cdd[7];
 #pragma unroll
-                    for (int b = 1; b < 8; ++b) {
-                        c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
-                        cdd[b - 1] = nb[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
-                    }
+                    for (int b = 1; b < 8; ++b) c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
                     for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
                         float t[8];
                         load_w3(t32[m], t);
@@ -1025,7 +1024,13 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                             load_w3(t64[m], td);
                             double x = td[7] * hh;
 #pragma unroll
-                            for (int b = 0; b < 7; ++b) x = fma(td[b], cdd[b], x);
+                            for (int b = 1; b < 8; ++b) {
+                                const int ddz = (b & 4) ? sz : 1, ddy = (b & 2) ? sy : 1, ddx = (b & 1) ? sx : 1;
+                                const int64_t j =
+                                    ((int64_t)(iz - 1 + ddz) * g.n1 + (iy - 1 + ddy)) * g.n0 + (ix - 1 + ddx);
+                                const double cv = ((use >> (9 * ddz + 3 * ddy + ddx)) & 1u) ? uin[j] : Num<double>::big();
+                                x = fma(td[b - 1], cv, x);
+                            }
                             best = x < best ? x : best;
                         }
                     }
