@@ -318,7 +318,8 @@ def run_ours(args, rank, world, dist):
     ops_per_launch = s0["node_control_updates"] * (OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D) / launches
     avg_launch_s = s0["ms_sweep_kernel"] / 1e3 / launches
     achieved = ops_per_launch / avg_launch_s if avg_launch_s > 0 else None
-    traffic = profile_traffic() if p.dim == 2 else None  # the committed capture is of the 2D kernel
+    # the committed capture is of the 2D sweep on the default workload only
+    traffic = profile_traffic() if (FAMILY == "sincos2d" and N_FINE == 2049 and args.bc == "state" and not args.reduce_r) else None
     roofline = {"bound": "alu", "kernel": "k_value2d<float>" if p.dim == 2 else "k_value3d<float>", "achieved": achieved / 1e12 if achieved else None,
                 "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
