@@ -348,7 +348,7 @@ def run_ours(args, rank, world, dist):
             "sweeps": {k: s0[k] for k in ("sweeps_coarse", "sweeps_phi", "sweeps_reach", "sweeps_fine",
                                            "sweeps_polish", "sweeps_patch", "phi_refinements")},
             "ms_phases": {k: round(s0[k], 3) for k in ("ms_setup", "ms_coarse", "ms_feedback", "ms_labels",
-                                                        "ms_compact", "ms_fine", "ms_polish", "ms_total")},
+                                                        "ms_compact", "ms_fine", "ms_reach", "ms_polish", "ms_total")},
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": statistics.mean(e2e_ms)},

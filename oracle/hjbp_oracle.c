@@ -86,10 +86,11 @@
  *       Gauss-Seidel needs O(n) sweeps).
  *   R16 Dirichlet patch boundary (Eq. dbc, Sec. 5): while patch j is solved,
  *       every node outside patch j and outside Omega_0^j holds the fixed
- *       value U_P^(0) of Step 2 (0 on every target part, +inf on the ghost
- *       ring and on nodes Step 2 leaves unreachable); nodes of patch j that
- *       are off S* stay +inf.  Nodes with a finite fixed value count as
- *       target for S* (R14).
+ *       value U_P^(0) = I[U~_P] of Step 2 read literally (R2, R3: +inf where a
+ *       positive-weight coarse corner is +inf; the bound M of R7 serves the
+ *       feedback only, its M-weighted values are no data), 0 on every target
+ *       part, +inf on the ghost ring; nodes of patch j that are off S* stay
+ *       +inf.  Nodes with a finite fixed value count as target for S* (R14).
  *   R17 AO1 (Sec. 6): the nodes of S* start from U_P^(0) where it is
  *       finite and from M elsewhere; the iteration is the plain U <- F(U)
  *       and reaches the same fixed point (R14: unique on S*).
@@ -793,9 +794,10 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
     double *phimax = (double *)malloc(sizeof(double) * (size_t)N);
     signed char *lab2 = (signed char *)malloc((size_t)N);
     double *W = (double *)malloc(sizeof(double) * (size_t)N);
+    double *Dlit = (double *)malloc(sizeof(double) * (size_t)N);   /* literal I[U~] (R16) */
     int rc = 0;
     if (!ckind || !cupd || !cpart || !ch || !Uc || !kind || !upd || !part || !h || !U0 || !astar || !phi ||
-        !phimax || !lab2 || !W) {
+        !phimax || !lab2 || !W || !Dlit) {
         rc = -1;
         goto done;
     }
@@ -820,8 +822,8 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
        a*_{k~}(x_i) of Eq. (feedbackcontrol) at every free fine node. */
     og_setup(p, 0.0, kind, part, h);
     for (int64_t i = 0; i < N; ++i) {
-        if (kind[i] == OG_TARGET) { U0[i] = 0.0; continue; }
-        if (kind[i] == OG_GHOST) { U0[i] = INFINITY; continue; }
+        if (kind[i] == OG_TARGET) { U0[i] = 0.0; Dlit[i] = 0.0; continue; }
+        if (kind[i] == OG_GHOST) { U0[i] = INFINITY; Dlit[i] = INFINITY; continue; }
         int idx[3];
         og_index3(p, i, idx);
         double xi[3] = {0.0, 0.0, 0.0};
@@ -829,6 +831,7 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
             xi[d] = (double)idx[d] * (double)(n_coarse[d] - 1) / (double)(p->n[d] - 1);
         U0[i] = og_interp_bounded(&pc, Uc, xi);
         if (U0[i] >= OG_U0_BOUND) U0[i] = INFINITY;
+        Dlit[i] = og_interp(&pc, Uc, xi);
     }
     st->unreachable = 0;
     for (int64_t i = 0; i < N; ++i) {
@@ -896,7 +899,7 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
        Sec. 6 (R17-R19). */
     {
         const int dir = ao && ao->dirichlet;
-        const double *D = (ao && ao->data) ? ao->data : U0;
+        const double *D = (ao && ao->data) ? ao->data : Dlit;
         og_filter flt = {astar, 0.0};
         const og_filter *fp = NULL;
         if (ao && ao->reduce_r > 0.0) {
@@ -948,7 +951,7 @@ int og_patchy_solve_ex(const og_problem *p, const int n_coarse[3], double tol, d
 done:
     free(ckind); free(cupd); free(cpart); free(ch); free(Uc);
     free(kind); free(upd); free(part); free(h); free(U0); free(astar); free(phi); free(phimax);
-    free(lab2); free(W);
+    free(lab2); free(W); free(Dlit);
     return rc;
 }
 

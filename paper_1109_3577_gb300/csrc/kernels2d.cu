@@ -1229,13 +1229,23 @@ __global__ void k_gather2d(Grid2 g, const uint8_t *__restrict__ latest, const T 
 // U_P^(0)(x_i) = Q1 of the coarse values at the fine node (R7: a coarse +inf
 // enters as the bound M; >= M means unreachable); 0 on fine targets, +inf on
 // the fine ghost ring.
+// dlit (optional): the literal interpolation, +inf where a positive-weight
+// coarse corner is +inf (the Dirichlet data of Eq. dbc, R16).
 __global__ void k_u0_2d(Grid2 g, Grid2 gc, const int8_t *__restrict__ code, const double *__restrict__ uc,
-                        double *__restrict__ u0) {
+                        double *__restrict__ u0, double *__restrict__ dlit) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
-        if (c >= kTargetBase) { u0[i] = 0.0; continue; }
-        if (c < 0) { u0[i] = Num<double>::big(); continue; }
+        if (c >= kTargetBase) {
+            u0[i] = 0.0;
+            if (dlit) dlit[i] = 0.0;
+            continue;
+        }
+        if (c < 0) {
+            u0[i] = Num<double>::big();
+            if (dlit) dlit[i] = Num<double>::big();
+            continue;
+        }
         const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
         const double xi0 = (double)ix * (double)(gc.n0 - 1) / (double)(g.n0 - 1);
         const double xi1 = (double)iy * (double)(gc.n1 - 1) / (double)(g.n1 - 1);
@@ -1244,13 +1254,16 @@ __global__ void k_u0_2d(Grid2 g, Grid2 gc, const int8_t *__restrict__ code, cons
         b1 = min(max(b1, 0), gc.n1 - 2);
         const double t0 = xi0 - b0, t1 = xi1 - b1;
         double sum = 0.0;
+        bool inf_corner = false;
         for (int cc = 0; cc < 4; ++cc) {
             const double w = ((cc & 1) ? t0 : 1.0 - t0) * ((cc & 2) ? t1 : 1.0 - t1);
             if (w > 0.0) {
                 const double v = uc[(int64_t)(b1 + ((cc >> 1) & 1)) * gc.n0 + b0 + (cc & 1)];
+                inf_corner |= v >= Num<double>::thresh();
                 sum += w * (v >= Num<double>::thresh() ? kU0Bound : v);
             }
         }
+        if (dlit) dlit[i] = inf_corner ? Num<double>::big() : sum;
         u0[i] = sum >= kU0Bound ? Num<double>::big() : sum;
     }
 }
@@ -2532,6 +2545,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     Sched sched = make_sched(p, g, hist);
     Ev e1(st);
 
+    double *dlit = nullptr;   // literal U_P^(0): the Dirichlet data (R16)
     if (p.patchy) {
         // ---- Step 1: coarse solve (FP64)
         const Grid2 gc = make_grid(d.n_coarse[0], d.n_coarse[1], d.lo[0], d.lo[1], p.kc);
@@ -2554,7 +2568,8 @@ hjbp_status solve2d(hjbp_plan &p) {
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev e2(st);
         // ---- Step 2: U_P^(0) and the coarse feedback a*
-        k_u0_2d<<<grid_for(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0);
+        if (d.flags & HJBP_FLAG_DIRICHLET) dlit = alloc_n<double>(p, N);
+        k_u0_2d<<<grid_for(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0, dlit);
         ++p.stats.kernel_launches;
         k_feedback2d<<<grid_for(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, make_literal(p));
         ++p.stats.kernel_launches;
@@ -2715,7 +2730,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         check_cuda(cudaMemcpyAsync(iv, p.init.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "start values");
         warm = iv;
     }
-    const double *d64 = dirichlet ? p.u0 : nullptr;
+    const double *d64 = dirichlet ? dlit : nullptr;
     // AO3: control cones around the coarse feedback
     Cone2 *cone = nullptr;
     double cone_size = d.n_controls;
@@ -2737,7 +2752,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         float *d32 = nullptr;
         if (dirichlet) {
             d32 = alloc_n<float>(p, N);
-            k_dirichlet_data<float><<<grid_for(N), 256, 0, st>>>(N, p.u0, d32);
+            k_dirichlet_data<float><<<grid_for(N), 256, 0, st>>>(N, dlit, d32);
             ++p.stats.kernel_launches;
         }
         if (queue_ok)

@@ -133,18 +133,27 @@ __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, i
     }
 }
 
+// Start values (R14): M on free nodes, or the warm start where it is finite
+// (AO1); the fixed value on targets; +inf on hard nodes.
 template <typename T>
 __global__ void k_init3d(int64_t N, const int8_t *__restrict__ code, const double *__restrict__ fixed, T start,
-                         T *__restrict__ b0, T *__restrict__ b1) {
+                         T *__restrict__ b0, T *__restrict__ b1, const double *__restrict__ warm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
         T v;
         if (c < 0) v = Num<T>::big();
         else if (c >= kTargetBase) v = fixed ? (T)fixed[i] : (T)0;
-        else v = start;
+        else v = (warm && warm[i] < kU0Bound) ? (T)warm[i] : start;
         b0[i] = v;
         b1[i] = v;
     }
+}
+
+// Dirichlet data of Eq. (dbc) in FP32: U_P^(0), the bound 1e6 and above
+// (no finite value) mapped to the +inf sentinel.
+__global__ void k_narrow_data3(int64_t N, const double *__restrict__ u0, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = u0[i] < kU0Bound ? (float)u0[i] : Num<float>::big();
 }
 
 // ------------------------------------------------------------ scheduling --
@@ -183,37 +192,41 @@ __global__ void k_schedule3d(Grid3 g, TileSched s, int par, float tol, int launc
 }
 
 // Tile image in shared memory: u[z][y][x] with a one-node halo.
-template <typename T> struct Tile3 {
+template <typename T, bool kDir = false> struct Tile3 {
     T u[kT3 + 2][kT3 + 2][kT3 + 3];
     int8_t c[kT3 + 2][kT3 + 2][kT3 + 4];
+    T d[kDir ? kT3 + 2 : 1][kDir ? kT3 + 2 : 1][kDir ? kT3 + 3 : 1];   // Dirichlet data (Eq. dbc)
     float red[2];
 };
 
-template <typename T>
+template <typename T, bool kDir>
 __device__ __forceinline__ void load_tile3(const Grid3 &g, const TileSched &s, const int8_t *__restrict__ code,
                                            const T *__restrict__ b0, const T *__restrict__ b1, int x0, int y0, int z0,
-                                           Tile3<T> &sm) {
+                                           Tile3<T, kDir> &sm, const T *__restrict__ dval = nullptr) {
     constexpr int E = kT3 + 2;
     for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
         const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
         const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
-        T v = Num<T>::big();
+        T v = Num<T>::big(), dv = Num<T>::big();
         int8_t cd = kHard;
         if (x < g.n0 && y < g.n1 && z < g.n2) {
             const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
             cd = code[i];
             const int tt = tile_of3(g, x, y, z);
             v = (tt >= 0 && s.latest[tt]) ? b1[i] : b0[i];
+            if constexpr (kDir) dv = dval[i];
         }
         sm.u[lz][ly][lx] = v;
         sm.c[lz][ly][lx] = cd;
+        if constexpr (kDir) sm.d[lz][ly][lx] = dv;
     }
     __syncthreads();
 }
 
-template <typename T>
+template <typename T, bool kDir>
 __device__ __forceinline__ float store_tile3(const Grid3 &g, const TileSched &s, int t, T *__restrict__ b0,
-                                             T *__restrict__ b1, int x0, int y0, int z0, Tile3<T> &sm) {
+                                             T *__restrict__ b1, int x0, int y0, int z0, Tile3<T, kDir> &sm,
+                                             int clamp = 1) {
     const int cur = s.latest[t];
     T *dst = cur ? b0 : b1;
     const T *src = cur ? b1 : b0;
@@ -227,7 +240,9 @@ __device__ __forceinline__ float store_tile3(const Grid3 &g, const TileSched &s,
         const T o = src[i];
         dst[i] = v;
         const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-        const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        // the plain update (warm start) may move by a few units in the last place
+        if (!clamp && d <= (float)(Num<T>::noise() * fabs((double)v))) d = 0.f;
         mc = fmaxf(mc, d);
     }
     return block_max64(mc, sm.red);
@@ -271,8 +286,8 @@ template <typename T> __device__ __forceinline__ void load_w3(const W3<T> &w, T 
 // neighbour (dx-1, dy-1, dz-1) belongs to the node's patch or target part
 // (formed once per launch), everything else reads +inf.  tab: the weights in
 // shared memory, in the octant order of ct.
-template <typename T>
-__device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int lz, uint32_t mask, T hh,
+template <typename T, bool kDir>
+__device__ __forceinline__ T sl_update3(const Tile3<T, kDir> &sm, int lx, int ly, int lz, uint32_t mask, T hh,
                                         const CtlTable3<T> &ct, const W3<T> *tab) {
     T nb[3][3][3];
 #pragma unroll
@@ -280,9 +295,13 @@ __device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int 
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx)
+            for (int dx = 0; dx < 3; ++dx) {
+                T other;
+                if constexpr (kDir) other = sm.d[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx];   // Eq. (dbc)
+                else other = Num<T>::big();
                 nb[dz][dy][dx] = ((mask >> (9 * dz + 3 * dy + dx)) & 1u) ? sm.u[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]
-                                                                        : Num<T>::big();
+                                                                        : other;
+            }
     T b0 = Num<T>::big(), b1 = Num<T>::big();
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -317,16 +336,20 @@ __device__ __forceinline__ T sl_update3(const Tile3<T> &sm, int lx, int ly, int 
     return b0 < b1 ? b0 : b1;
 }
 
-template <typename T>
+// clamp != 0: monotone update from M; clamp == 0: the plain update of the
+// warm start (AO1).  kDir: neighbours outside the patch read the Dirichlet
+// data dval (Eq. dbc); a node's own pruned nodes (code -2 - patch) read +inf.
+template <typename T, bool kDir = false>
 __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restrict__ code,
                                                   const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                   TileSched s, int par, int rounds, unsigned long long *updates,
-                                                  const CtlTable3<T> ct) {
+                                                  const CtlTable3<T> ct, int clamp = 1,
+                                                  const T *__restrict__ dval = nullptr) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
-    __shared__ Tile3<T> sm;
+    __shared__ Tile3<T, kDir> sm;
     // per interior node: neighbour mask (bit 31: the node is free) and h
     __shared__ uint32_t mk[kT3][kT3][kT3];
     __shared__ T hs[kT3][kT3][kT3];
@@ -335,7 +358,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
         for (int b = 0; b < 7; ++b) tab[m].k[b] = ct.kw[b][m];
         tab[m].k[7] = ct.kap[m];
     }
-    load_tile3(g, s, code, b0, b1, x0, y0, z0, sm);   // ends with a block barrier
+    load_tile3(g, s, code, b0, b1, x0, y0, z0, sm, dval);   // ends with a block barrier
     const int tid = threadIdx.x;
     int nfree = 0;
     for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
@@ -344,7 +367,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
         uint32_t m = 0;
         T hv = (T)0;
         if (cd >= 0 && cd < kTargetBase) {
-            const int8_t tg = (int8_t)(cd + kTargetBase);
+            const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
@@ -352,7 +375,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int8_t q = sm.c[lz + dz][ly + dy][lx + dx];
-                        m |= (uint32_t)(q == cd || q == tg) << (9 * dz + 3 * dy + dx);
+                        m |= (uint32_t)(q == cd || q == tg || q == pr) << (9 * dz + 3 * dy + dx);
                     }
             m |= 0x80000000u;
             ++nfree;
@@ -371,14 +394,14 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                 const bool active = (m & 0x80000000u) != 0;
                 T nw = sm.u[lz][ly][lx];
                 if (active) {
-                    const T best = sl_update3(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
-                    if (best < Num<T>::thresh()) nw = best < nw ? best : nw;
+                    const T best = sl_update3<T, kDir>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
+                    if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
                 }
                 __syncthreads();
                 if (active) sm.u[lz][ly][lx] = nw;
                 __syncthreads();
             }
-    const float mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm);
+    const float mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm, clamp);
     nfree = __reduce_add_sync(0xffffffffu, nfree);
     if ((tid & 31) == 0 && updates && nfree)
         atomicAdd(updates, (unsigned long long)nfree * 6ull * (unsigned long long)rounds);
@@ -390,8 +413,11 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
 
 // ---------------------------------------------------------- reach (S*) 3D --
 
+// dterm (optional): Dirichlet data (Eq. dbc); a node outside the patch with
+// finite data is a terminal, like the patch's own target part.
 __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restrict__ code,
-                                                  uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt) {
+                                                  uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt,
+                                                  const double *__restrict__ dterm) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -399,21 +425,24 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
     constexpr int E = kT3 + 2;
     __shared__ uint8_t sr[E][E][E + 2];
     __shared__ int8_t sc[E][E][E + 2];
+    __shared__ uint8_t sdf[E][E][E + 2];
     __shared__ int flips_s;
     const int tid = threadIdx.x;
     if (tid == 0) flips_s = 0;
     for (int e = tid; e < E * E * E; e += blockDim.x) {
         const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
         const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
-        uint8_t v = 0;
+        uint8_t v = 0, df = 0;
         int8_t cd = kHard;
         if (x < g.n0 && y < g.n1 && z < g.n2) {
             const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
             cd = code[i];
             v = rch[i];
+            if (dterm) df = dterm[i] < kU0Bound;
         }
         sr[lz][ly][lx] = v;
         sc[lz][ly][lx] = cd;
+        sdf[lz][ly][lx] = df;
     }
     __syncthreads();
     int flips = 0;
@@ -424,16 +453,17 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
             const int8_t cd = sc[lz][ly][lx];
             bool hit = false;
             if (cd >= 0 && cd < kTargetBase && !sr[lz][ly][lx]) {
-                const int8_t tg = (int8_t)(cd + kTargetBase);
+                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
                 for (int o = 0; o < 8 && !hit; ++o) {
                     const int sx = (o & 1) ? 1 : -1, sy = (o & 2) ? 1 : -1, sz = (o & 4) ? 1 : -1;
                     unsigned us = 0, rb = 0;
                     for (int b = 1; b < 8; ++b) {
                         const int zz = lz + ((b & 4) ? sz : 0), yy = ly + ((b & 2) ? sy : 0), xx = lx + ((b & 1) ? sx : 0);
                         const int8_t q = sc[zz][yy][xx];
-                        const bool usable = q == cd || q == tg;
+                        const bool term = q == tg || (q != cd && q != pr && sdf[zz][yy][xx]);
+                        const bool usable = q == cd || term;
                         us |= (unsigned)usable << (b - 1);
-                        rb |= (unsigned)(q == tg || (q == cd && sr[zz][yy][xx])) << (b - 1);
+                        rb |= (unsigned)(term || (q == cd && sr[zz][yy][xx])) << (b - 1);
                     }
                     for (int w = 0; w < 4 && !hit; ++w) {
                         uint32_t pres = rt.present[o][w];
@@ -534,13 +564,23 @@ __global__ void k_value_wide3d(Grid3 g, const int8_t *__restrict__ code, const T
 
 // ---------------------------------------------------- Step 2: U_P^(0), a* --
 
+// dlit (optional): the literal interpolation, +inf where a positive-weight
+// coarse corner is +inf (the Dirichlet data of Eq. dbc, R16).
 __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, const double *__restrict__ uc,
-                        double *__restrict__ u0) {
+                        double *__restrict__ u0, double *__restrict__ dlit) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
-        if (c >= kTargetBase) { u0[i] = 0.0; continue; }
-        if (c < 0) { u0[i] = Num<double>::big(); continue; }
+        if (c >= kTargetBase) {
+            u0[i] = 0.0;
+            if (dlit) dlit[i] = 0.0;
+            continue;
+        }
+        if (c < 0) {
+            u0[i] = Num<double>::big();
+            if (dlit) dlit[i] = Num<double>::big();
+            continue;
+        }
         const int ix = (int)(i % g.n0);
         const int64_t r = i / g.n0;
         const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
@@ -557,6 +597,7 @@ __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, cons
             tt[d] = xi[d] - b;
         }
         double sum = 0.0;
+        bool inf_corner = false;
         for (int cc = 0; cc < 8; ++cc) {
             double w = 1.0;
             for (int d = 0; d < 3; ++d) w *= (cc >> d & 1) ? tt[d] : 1.0 - tt[d];
@@ -564,9 +605,11 @@ __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, cons
                 const int64_t j = ((int64_t)(bb[2] + (cc >> 2 & 1)) * gc.n1 + (bb[1] + (cc >> 1 & 1))) * gc.n0 + bb[0] +
                                   (cc & 1);
                 const double v = uc[j];
+                inf_corner |= v >= Num<double>::thresh();
                 sum += w * (v >= Num<double>::thresh() ? kU0Bound : v);
             }
         }
+        if (dlit) dlit[i] = inf_corner ? Num<double>::big() : sum;
         u0[i] = sum >= kU0Bound ? Num<double>::big() : sum;
     }
 }
@@ -944,7 +987,8 @@ __global__ void __launch_bounds__(kT3n) k_compact3d(Grid3 g, const int8_t *__res
 // covers the eight-term trilinear sum.
 __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
                            const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
-                           const CtlTable3<float> c32, const CtlTable3<double> c64) {
+                           const CtlTable3<float> c32, const CtlTable3<double> c64,
+                           const double *__restrict__ dval) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     // the weights in shared memory (k[0..6] = kap w_b, k[7] = kap), 16-byte vectors
     __shared__ W3<float> t32[kMaxControls];
@@ -966,11 +1010,12 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
             const int ix = (int)(i % g.n0);
             const int64_t r = i / g.n0;
             const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
-            const int8_t tg = (int8_t)(cd + kTargetBase);
-            // only FP32 copies and a usability mask stay live (FP64 compares and
-            // conversions run at 1/64 rate); FP64 candidates re-read their corners
+            const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+            // only FP32 copies and masks stay live (FP64 compares and conversions
+            // run at 1/64 rate); FP64 candidates re-read their corners.  Outside
+            // the patch: +inf, or the Dirichlet data (Eq. dbc).
             float nf[3][3][3];
-            uint32_t use = 0;
+            uint32_t use = 0, fromd = 0;
             float amax = 0.f;
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz)
@@ -980,10 +1025,12 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                     for (int dx = 0; dx < 3; ++dx) {
                         const int64_t j = ((int64_t)(iz - 1 + dz) * g.n1 + (iy - 1 + dy)) * g.n0 + (ix - 1 + dx);
                         const int8_t q = code[j];
-                        const float f = (float)uin[j];
-                        const bool fin = (q == cd || q == tg) && f < Num<float>::thresh();
+                        const bool same = q == cd || q == tg || q == pr;
+                        const float f = same ? (float)uin[j] : (dval ? (float)dval[j] : Num<float>::big());
+                        const bool fin = f < Num<float>::thresh();
                         nf[dz][dy][dx] = fin ? f : Num<float>::big();
                         use |= (uint32_t)fin << (9 * dz + 3 * dy + dx);
+                        fromd |= (uint32_t)(!same) << (9 * dz + 3 * dy + dx);
                         if (fin) amax = fmaxf(amax, fabsf(f));
                     }
             const double hh = h[i];
@@ -1028,7 +1075,9 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                                 const int ddz = (b & 4) ? sz : 1, ddy = (b & 2) ? sy : 1, ddx = (b & 1) ? sx : 1;
                                 const int64_t j =
                                     ((int64_t)(iz - 1 + ddz) * g.n1 + (iy - 1 + ddy)) * g.n0 + (ix - 1 + ddx);
-                                const double cv = ((use >> (9 * ddz + 3 * ddy + ddx)) & 1u) ? uin[j] : Num<double>::big();
+                                const int bit = 9 * ddz + 3 * ddy + ddx;
+                                const double cv = ((use >> bit) & 1u) ? (((fromd >> bit) & 1u) ? dval[j] : uin[j])
+                                                                      : Num<double>::big();
                                 x = fma(td[b - 1], cv, x);
                             }
                             best = x < best ? x : best;
@@ -1281,7 +1330,8 @@ float ms3(const Ev3 &a, const Ev3 &b) {
     return ms;
 }
 
-int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, int64_t N) {
+int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, int64_t N,
+           const double *dterm = nullptr) {
     const ReachTable3 rt = make_reach3(p);
     unsigned long long *removed = alloc3<unsigned long long>(p, 1);
     int total = 0;
@@ -1291,7 +1341,7 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
         if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
-            k_reach3d<<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt);
+            k_reach3d<<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm);
             ++p.stats.kernel_launches;
         });
         total += rr.launches;
@@ -1307,11 +1357,15 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
     return total;
 }
 
+// dval: Dirichlet data (Eq. dbc) or NULL; warm: start values of AO1 or NULL
+// (then the plain update instead of the monotone one).
 template <typename T>
 Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0, T *b1, Sched3 &s, double tol,
-            int cap, int rounds, T *out_t, double *out64, unsigned long long *updates) {
+            int cap, int rounds, T *out_t, double *out64, unsigned long long *updates, const T *dval = nullptr,
+            const double *warm = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
-    k_init3d<T><<<grid_for3(N), 256, 0, p.stream>>>(N, code, nullptr, (T)kStartValue, b0, b1);
+    k_init3d<T><<<grid_for3(N), 256, 0, p.stream>>>(N, code, nullptr, (T)kStartValue, b0, b1, warm);
+    const int clamp = warm ? 0 : 1;
     ++p.stats.kernel_launches;
     const CtlTable3<T> ct = make_table3<T>(p);
     const bool timed = (p.desc.flags & HJBP_FLAG_TIME_SWEEPS) != 0;
@@ -1323,7 +1377,12 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
             check_cuda(cudaEventCreate(&b), "event");
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
-        k_value3d<T><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        if (dval)
+            k_value3d<T, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                 clamp, dval);
+        else
+            k_value3d<T, false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
+                                                                  clamp, nullptr);
         ++p.stats.kernel_launches;
         ++p.stats.sweep_kernel_launches;
         if (timed) {
@@ -1356,7 +1415,7 @@ Run3 wide3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const double *h, co
            double *b1, double tol, int cap, const Ctl3 *dct, double *out64) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     cudaStream_t st = p.stream;
-    k_init3d<double><<<grid_for3(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1);
+    k_init3d<double><<<grid_for3(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1, nullptr);
     ++p.stats.kernel_launches;
     const int chunk = 16;
     float *res = alloc3<float>(p, chunk);
@@ -1440,6 +1499,7 @@ hjbp_status solve3d(hjbp_plan &p) {
     Sched3 sched = make_sched3(p, g, hist);
     Ev3 e1(st);
 
+    double *dlit = nullptr;   // literal U_P^(0): the Dirichlet data (R16)
     if (p.patchy) {
         const Grid3 gc = make_grid3(d.n_coarse, d.lo, p.kc);
         const int64_t Nc = p.Nc;
@@ -1459,7 +1519,8 @@ hjbp_status solve3d(hjbp_plan &p) {
         S.sweeps_coarse = rc.launches;
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev3 e2(st);
-        k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0);
+        if (d.flags & HJBP_FLAG_DIRICHLET) dlit = alloc3<double>(p, N);
+        k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0, dlit);
         {
             const CtlLit3 hl = make_lit3(p);
             CtlLit3 *dl = static_cast<CtlLit3 *>(p.dev_alloc(sizeof(CtlLit3)));
@@ -1570,15 +1631,26 @@ hjbp_status solve3d(hjbp_plan &p) {
     }
 
     Ev3 f0(st);
-    S.sweeps_reach += reach3(p, g, code, rch, sched, N);
+    // patch boundary: state constraints, or U_P^(0) (Eq. dbc); start: M or U_P^(0) (AO1)
+    const bool dirichlet = p.patchy && (d.flags & HJBP_FLAG_DIRICHLET);
+    const double *warm = (p.patchy && (d.flags & HJBP_FLAG_WARM_START)) ? p.u0 : nullptr;
+    const double *d64 = dirichlet ? dlit : nullptr;
+    S.sweeps_reach += reach3(p, g, code, rch, sched, N, d64);
     Ev3 fr(st);
     Run3 rv;
     if (fp32) {
         float *b0 = alloc3<float>(p, N), *b1 = alloc3<float>(p, N);
-        rv = value3<float>(p, g, code, h32, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates);
+        float *d32 = nullptr;
+        if (dirichlet) {
+            d32 = alloc3<float>(p, N);
+            k_narrow_data3<<<grid_for3(N), 256, 0, st>>>(N, dlit, d32);
+            ++S.kernel_launches;
+        }
+        rv = value3<float>(p, g, code, h32, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, d32, warm);
     } else {
         double *b0 = alloc3<double>(p, N), *b1 = alloc3<double>(p, N);
-        rv = value3<double>(p, g, code, h64, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates);
+        rv = value3<double>(p, g, code, h64, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates, d64,
+                            warm);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
@@ -1604,7 +1676,7 @@ hjbp_status solve3d(hjbp_plan &p) {
         int it = 0;
         for (; it < 8; ++it) {
             check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
-            k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64);
+            k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64, d64);
             ++S.kernel_launches;
             check_cuda(cudaGetLastError(), "polish3");
             std::swap(pa, pb);
@@ -1644,7 +1716,9 @@ hjbp_status solve3d(hjbp_plan &p) {
 }
 
 // ---------------------------------------------------------- instantiation --
-template __global__ void k_init3d<float>(int64_t, const int8_t *, const double *, float, float *, float *);
-template __global__ void k_init3d<double>(int64_t, const int8_t *, const double *, double, double *, double *);
+template __global__ void k_init3d<float>(int64_t, const int8_t *, const double *, float, float *, float *,
+                                          const double *);
+template __global__ void k_init3d<double>(int64_t, const int8_t *, const double *, double, double *, double *,
+                                           const double *);
 
 }  // namespace hjbp

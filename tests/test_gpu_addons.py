@@ -165,3 +165,17 @@ def test_set_initial_resume_and_sync(pkg):
         plan.set_initial(None)
         assert plan.solve() == 0
         _assert_values(plan.values(), ref)
+
+
+@pytest.mark.parametrize("mode", ["dirichlet", "warm", "dirichlet_warm"])
+def test_3d_dirichlet_and_warm_start(pkg, mode):
+    """The 3D path with the Dirichlet patch boundary (Eq. dbc) and the AO1
+    warm start, against the oracle with the same patch boundary."""
+    p = W.sin3d(0, n=41, n_coarse=11, n_targets=4, radius=0.12)
+    flags = (pkg.HJBP_FLAG_DIRICHLET if "dirichlet" in mode else 0) | \
+        (pkg.HJBP_FLAG_WARM_START if "warm" in mode else 0)
+    r = _run(pkg, p, flags=flags)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet="dirichlet" in mode)
+    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    _assert_values(r["u"], ref.u)

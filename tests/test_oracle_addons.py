@@ -53,6 +53,19 @@ def test_dirichlet_below_state_constraints():
     assert np.array_equal(sc.labels, dr.labels)
 
 
+def test_dirichlet_data_is_the_literal_interpolation():
+    """Eq. (dbc) reads U_P^(0) = I[U~] literally: where a coarse corner of
+    positive weight is +inf the data is +inf, never a value mixed with the
+    bound the feedback uses near the ghost ring.  So every finite Dirichlet
+    value stays within the range of the global solution's values (plus the
+    coarse error), in 2D and 3D."""
+    for p in (_small(8, n=65, nc=9, R=3, radius=0.2), _small(1, n=25, nc=7, R=3, radius=0.15, dim=3)):
+        g = oracle.global_solve(p.with_(n_coarse=None), tol=1e-12)
+        dr = oracle.patchy_solve(p, tol=1e-12, dirichlet=True)
+        fin = np.isfinite(dr.u)
+        assert dr.u[fin].max() <= 2.0 * g.u[np.isfinite(g.u)].max()
+
+
 def test_dirichlet_single_patch_equals_state_constraints():
     """R = 1: outside the patch there are only the target, the ghost ring and
     unreachable nodes, where U_P^(0) is 0, +inf and +inf, so Eq. (dbc) and
