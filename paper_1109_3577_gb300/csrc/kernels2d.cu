@@ -1110,7 +1110,6 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     // neighbour is terminal, bit 31 node free and unreached; pres: the corner
     // patterns of the node's controls per quadrant
     __shared__ uint32_t mk[kTile][kTile + 1];
-    __shared__ uint32_t pres4[kTile][kTile + 1];
     {
         const int c = 1 + lane;
         const uint32_t all = (uint32_t)rt.present[0] | ((uint32_t)rt.present[1] << 8) |
@@ -1124,20 +1123,40 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                                                                                      : kNoControl;
                 pw = cone->reach[a < cone->nc ? a : cone->nc];
             }
-            pres4[r - 1][lane] = pw;
             uint32_t m = 0;
             if (cd >= 0 && cd < kTargetBase && !sr[r][c]) {
                 const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+                uint32_t same = 0, term = 0;
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int8_t q = sc[r - 1 + dy][c - 1 + dx];
-                        const bool term = q == tg || (q != cd && q != pr && sd[r - 1 + dy][c - 1 + dx]);
-                        m |= (uint32_t)(q == cd || term) << (3 * dy + dx);
-                        m |= (uint32_t)term << (9 + 3 * dy + dx);
+                        const bool t = q == tg || (q != cd && q != pr && sd[r - 1 + dy][c - 1 + dx]);
+                        same |= (uint32_t)(q == cd) << (3 * dy + dx);
+                        term |= (uint32_t)t << (3 * dy + dx);
                     }
-                m |= 0x80000000u;
+                // the corners that can reach the node: per quadrant the union of
+                // its patterns whose corners are all usable (a pattern with all
+                // corners usable and one terminal-or-reached corner exists iff
+                // such a corner lies in that union)
+                const uint32_t usable = same | term;
+                uint32_t cand = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
+                    const int b10 = 3 * 1 + (1 + sx), b01 = 3 * (1 + sy) + 1, b11 = 3 * (1 + sy) + (1 + sx);
+                    const unsigned us =
+                        ((usable >> b10) & 1u) | (((usable >> b01) & 1u) << 1) | (((usable >> b11) & 1u) << 2);
+                    const unsigned pres = (pw >> (8 * q)) & 0xffu;
+                    unsigned u = 0;
+#pragma unroll
+                    for (unsigned k = 1; k < 8; ++k)
+                        if (((pres >> k) & 1u) && (k & ~us) == 0) u |= k;
+                    cand |= ((u & 1u) << b10) | (((u >> 1) & 1u) << b01) | (((u >> 2) & 1u) << b11);
+                }
+                // bits 0..8: candidate corners in the patch; bit 9: a candidate is terminal
+                m = (cand & same) | ((uint32_t)((cand & term) != 0) << 9) | 0x80000000u;
             }
             mk[r - 1][lane] = m;
         }
@@ -1151,24 +1170,12 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                 const int c = (dir < 2) ? s1 : 1 + lane;
                 const int r = (dir < 2) ? 1 + lane : s1;
                 const uint32_t m = mk[r - 1][c - 1];
-                const uint32_t pw = pres4[r - 1][c - 1];
                 bool hit = false;
                 if ((m & 0x80000000u) && !sr[r][c]) {
+                    hit = (m >> 9) & 1u;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
-                        const int b10 = 3 * 1 + (1 + sx), b01 = 3 * (1 + sy) + 1, b11 = 3 * (1 + sy) + (1 + sx);
-                        const unsigned us = ((m >> b10) & 1u) | (((m >> b01) & 1u) << 1) | (((m >> b11) & 1u) << 2);
-                        const unsigned tgt =
-                            ((m >> (9 + b10)) & 1u) | (((m >> (9 + b01)) & 1u) << 1) | (((m >> (9 + b11)) & 1u) << 2);
-                        const unsigned rr = (unsigned)(sr[r][c + sx] != 0) | ((unsigned)(sr[r + sy][c] != 0) << 1) |
-                                            ((unsigned)(sr[r + sy][c + sx] != 0) << 2);
-                        const unsigned rb = tgt | (us & rr);
-                        const unsigned pres = (pw >> (8 * q)) & 0xffu;
-                        for (unsigned k = 1; k < 8; ++k)
-                            if ((pres >> k) & 1u)
-                                if ((us & k) == k && (rb & k)) hit = true;
-                    }
+                    for (int b = 0; b < 9; ++b)
+                        if ((m >> b) & 1u) hit |= sr[r - 1 + b / 3][c - 1 + b % 3] != 0;
                 }
                 __syncwarp();
                 if (hit) {

@@ -79,8 +79,14 @@ struct CtlLit3 {
 };
 
 // Masks of positive-weight corners (bits 0..6 for b = 1..7) present in each octant.
+// uni[o][us]: the union of the corner masks (bits 0..6 for b = 1..7) of the
+// octant-o patterns whose corners all lie in the usable set us.  A node is
+// reached with positive probability iff some corner in the union over the
+// octants is terminal or reached: a pattern with all corners usable and one
+// such corner exists iff that corner lies in one of the unions.
 struct ReachTable3 {
     uint32_t present[8][4];
+    uint8_t uni[8][128];
 };
 
 __device__ __forceinline__ float warp_max3(float v) {
@@ -445,37 +451,74 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
         sdf[lz][ly][lx] = df;
     }
     __syncthreads();
+    // once per launch (codes do not change): per interior node the corners
+    // that reach it (cand, 27-bit over the 3x3x3 neighbourhood), whether one
+    // of them is terminal, and which of them are in the patch
+    __shared__ uint32_t cand[kT3 * kT3 * kT3];
+    __shared__ uint8_t hit0[kT3 * kT3 * kT3];
+    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int lx = 1 + e % kT3, ly = 1 + (e / kT3) % kT3, lz = 1 + e / (kT3 * kT3);
+        const int8_t cd = sc[lz][ly][lx];
+        uint32_t cs = 0;
+        uint8_t h0 = 0;
+        if (cd >= 0 && cd < kTargetBase && !sr[lz][ly][lx]) {
+            const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+            uint32_t same = 0, term = 0;
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int8_t q = sc[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx];
+                        const int bit = 9 * dz + 3 * dy + dx;
+                        same |= (uint32_t)(q == cd) << bit;
+                        term |= (uint32_t)(q == tg || (q != cd && q != pr && sdf[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]))
+                                << bit;
+                    }
+            const uint32_t usable = same | term;
+            uint32_t c = 0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
+                unsigned us = 0;
+#pragma unroll
+                for (int b = 1; b < 8; ++b) {
+                    const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
+                    us |= ((usable >> bit) & 1u) << (b - 1);
+                }
+                const unsigned u = rt.uni[o][us];
+#pragma unroll
+                for (int b = 1; b < 8; ++b) {
+                    const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
+                    c |= ((u >> (b - 1)) & 1u) << bit;
+                }
+            }
+            h0 = (c & term) != 0;
+            cs = c & same;
+            if (!h0 && !cs) cs = 0;
+            cs |= 0x80000000u;   // the node is free and unreached
+        }
+        cand[e] = cs;
+        hit0[e] = h0;
+    }
+    __syncthreads();
     int flips = 0;
     for (int dir = 0; dir < 6; ++dir)
         for (int st = 0; st < kT3; ++st) {
             int lx, ly, lz;
             plane_node(dir, st, tid, lx, ly, lz);
-            const int8_t cd = sc[lz][ly][lx];
+            const int e = ((lz - 1) * kT3 + (ly - 1)) * kT3 + (lx - 1);
+            const uint32_t cs = cand[e];
             bool hit = false;
-            if (cd >= 0 && cd < kTargetBase && !sr[lz][ly][lx]) {
-                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
-                for (int o = 0; o < 8 && !hit; ++o) {
-                    const int sx = (o & 1) ? 1 : -1, sy = (o & 2) ? 1 : -1, sz = (o & 4) ? 1 : -1;
-                    unsigned us = 0, rb = 0;
-                    for (int b = 1; b < 8; ++b) {
-                        const int zz = lz + ((b & 4) ? sz : 0), yy = ly + ((b & 2) ? sy : 0), xx = lx + ((b & 1) ? sx : 0);
-                        const int8_t q = sc[zz][yy][xx];
-                        const bool term = q == tg || (q != cd && q != pr && sdf[zz][yy][xx]);
-                        const bool usable = q == cd || term;
-                        us |= (unsigned)usable << (b - 1);
-                        rb |= (unsigned)(term || (q == cd && sr[zz][yy][xx])) << (b - 1);
-                    }
-                    for (int w = 0; w < 4 && !hit; ++w) {
-                        uint32_t pres = rt.present[o][w];
-                        while (pres) {
-                            const unsigned m = (unsigned)(w * 32 + __ffs(pres) - 1);
-                            pres &= pres - 1;
-                            if ((us & m) == m && (rb & m)) {
-                                hit = true;
-                                break;
-                            }
-                        }
-                    }
+            if ((cs & 0x80000000u) && !sr[lz][ly][lx]) {
+                hit = hit0[e] != 0;
+                uint32_t rest = cs & 0x7ffffffu;
+                while (!hit && rest) {
+                    const int bit = __ffs(rest) - 1;
+                    rest &= rest - 1u;
+                    const int dz = bit / 9, dy = (bit / 3) % 3, dx = bit % 3;
+                    hit = sr[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx] != 0;
                 }
             }
             __syncthreads();
@@ -1296,6 +1339,13 @@ ReachTable3 make_reach3(const hjbp_plan &p) {
         }
         if (need) rt.present[o][need >> 5] |= 1u << (need & 31);
     }
+    for (int o = 0; o < 8; ++o)
+        for (unsigned us = 0; us < 128; ++us) {
+            unsigned u = 0;
+            for (unsigned m = 1; m < 128; ++m)
+                if (((rt.present[o][m >> 5] >> (m & 31)) & 1u) && (m & ~us) == 0) u |= m;
+            rt.uni[o][us] = (uint8_t)u;
+        }
     return rt;
 }
 

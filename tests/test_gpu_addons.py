@@ -179,3 +179,13 @@ def test_3d_dirichlet_and_warm_start(pkg, mode):
     ref = oracle.patchy_solve(p, tol=1e-12, dirichlet="dirichlet" in mode)
     assert np.mean(r["labels"] == ref.labels) >= 0.999
     _assert_values(r["u"], ref.u)
+
+
+def test_control_cones_state_constraints_larger(pkg):
+    """AO3 with state constraints at 385^2: the reduced sets make S* prune in
+    many rounds; reachable sets and values must still be the oracle's."""
+    p = W.sincos2d(5, n=385, n_coarse=49, n_targets=4, radius=0.05)
+    r = _run(pkg, p, reduce_r=4.0)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, reduce_r=4.0)
+    _assert_values(r["u"], ref.u)
