@@ -61,6 +61,8 @@ class _Problem(C.Structure):
         ("drift", C.c_double * 4),
         ("target_kind", C.c_int),
         ("n_parts", C.c_int),
+        ("n_obstacles", C.c_int),
+        ("obstacles", C.POINTER(C.c_double)),
     ]
 
 
@@ -159,6 +161,10 @@ class _Desc:
             s.drift[i] = float(p.drift[i])
         s.target_kind = TARGET_KINDS[p.target_kind]
         s.n_parts = int(p.n_parts)
+        obs = getattr(p, "obstacles", None)
+        self.obstacles = np.ascontiguousarray(np.zeros((0, 7)) if obs is None else obs, dtype=np.float64)
+        s.n_obstacles = self.obstacles.shape[0]
+        s.obstacles = _ptr(self.obstacles, C.c_double) if s.n_obstacles else C.POINTER(C.c_double)()
         self.s = s
         self.N = int(np.prod([s.n[d] for d in range(p.dim)]))
         self.shape = tuple(int(s.n[d]) for d in reversed(range(p.dim)))  # (n3, n2, n1) / (n2, n1)

@@ -121,6 +121,11 @@
  *       upper part whatever the last bit of atan2.  On the coarse grid (R6) the
  *       ball or slab is widened by k~ sqrt(d)/2 with boundary value
  *       max(0, distance - r)/c(x).
+ *   R23 Obstacles (Sec. 4, "Patchy method with obstacles"): closed balls
+ *       |x - c|^2 <= r^2 and closed boxes lo <= x <= hi (per axis) of the
+ *       state space.  A node inside one is a state constraint like the ghost
+ *       ring (+inf, never updated, colour 0, label -1) unless it is a target
+ *       node; on the coarse grid of Step 1 the same rule holds for its nodes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -148,6 +153,10 @@ typedef struct {
                                   n_parts sectors; 2: row 0 = (v, ., r) the slab
                                   |x_1 - v| <= r in n_parts pieces (R22) */
     int n_parts;               /* parts of target kinds 1 and 2 */
+    int n_obstacles;           /* R23 */
+    const double *obstacles;   /* n_obstacles x 7: kind (0 ball, 1 box), then a
+                                  ball's centre (3) and radius, or a box's lower
+                                  (3) and upper (3) corners */
 } og_problem;
 
 typedef struct {
@@ -310,7 +319,25 @@ static int og_target_part(const og_problem *p, const double x[3], double extra, 
     return j;
 }
 
-/* Node kinds (R4, R5, R21, R22): target part (>= 0) or -1; kind FREE /
+/* Is x inside an obstacle (R23)? */
+static int og_in_obstacle(const og_problem *p, const double x[3]) {
+    for (int o = 0; o < p->n_obstacles; ++o) {
+        const double *b = p->obstacles + (size_t)o * 7;
+        if (b[0] == 0.0) {
+            double r2 = 0.0;
+            for (int d = 0; d < p->dim; ++d) r2 += (x[d] - b[1 + d]) * (x[d] - b[1 + d]);
+            if (r2 <= b[4] * b[4]) return 1;
+        } else {
+            int in = 1;
+            for (int d = 0; d < p->dim; ++d)
+                if (!(x[d] >= b[1 + d] && x[d] <= b[4 + d])) in = 0;
+            if (in) return 1;
+        }
+    }
+    return 0;
+}
+
+/* Node kinds (R4, R5, R21, R22, R23): target part (>= 0) or -1; kind FREE /
    TARGET / GHOST.  h_i = k / c(x_i) on every node (R1); +inf where the node
    cannot move.  radius_extra widens the target (R6, on the coarse grid). */
 int og_setup(const og_problem *p, double radius_extra, unsigned char *kind, int *part, double *h) {
@@ -327,7 +354,8 @@ int og_setup(const og_problem *p, double radius_extra, unsigned char *kind, int 
         const double c = og_speed(p, x);
         const int stopped = !(c > 1e-12);   /* R21 */
         part[i] = pj;
-        kind[i] = (pj >= 0) ? OG_TARGET : ((ring || stopped) ? OG_GHOST : OG_FREE);
+        const int blocked = og_in_obstacle(p, x);   /* R23 */
+        kind[i] = (pj >= 0) ? OG_TARGET : ((ring || stopped || blocked) ? OG_GHOST : OG_FREE);
         h[i] = stopped ? INFINITY : p->k / c;
     }
     return 0;

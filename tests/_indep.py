@@ -80,9 +80,23 @@ def target_parts(p, x):
     return part
 
 
+def in_obstacles(p, x):
+    """Points inside a closed obstacle ball or box."""
+    out = np.zeros(x.shape[0], bool)
+    obs = getattr(p, "obstacles", None)
+    if obs is None:
+        return out
+    for row in np.asarray(obs, float):
+        if row[0] == 0.0:
+            out |= np.sum((x - row[1: 1 + p.dim]) ** 2, axis=1) <= row[4] ** 2
+        else:
+            out |= np.all((x >= row[1: 1 + p.dim]) & (x <= row[4: 4 + p.dim]), axis=1)
+    return out
+
+
 def kinds(p):
-    """0 free, 1 target (part >= 0), 2 ghost (ring, or a node whose speed
-    vanishes); h = k / c(x)."""
+    """0 free, 1 target (part >= 0), 2 ghost (ring, obstacle, or a node whose
+    speed vanishes); h = k / c(x)."""
     idx, x = node_grid(p)
     N = idx.shape[0]
     part = target_parts(p, x)
@@ -91,7 +105,7 @@ def kinds(p):
         ring |= (idx[:, d] == 0) | (idx[:, d] == p.n[d] - 1)
     c = speed_np(p, x)
     stopped = ~(c > 1e-12)
-    kind = np.where(part >= 0, 1, np.where(ring | stopped, 2, 0))
+    kind = np.where(part >= 0, 1, np.where(ring | stopped | in_obstacles(p, x), 2, 0))
     with np.errstate(divide="ignore"):
         h = np.where(stopped, np.inf, p.spacing / np.where(stopped, 1.0, c))
     return kind, part, h

@@ -68,6 +68,10 @@ class Problem:
     # n_parts pieces along x2)
     target_kind: str = "balls"
     n_parts: int = 0
+    # obstacles: rows (kind, p0..p5), kind 0 = closed ball (centre p0..p2,
+    # radius p3), kind 1 = closed box (lower corner p0..p2, upper p3..p5);
+    # their nodes are state constraints like the ghost ring
+    obstacles: Optional[np.ndarray] = None
 
     @property
     def spacing(self) -> float:
@@ -314,6 +318,27 @@ def zermelo(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, ra
                    targets=np.array([[0.0, 0.0, radius]]), tol=tol, n_coarse=(n_coarse, n_coarse, 1),
                    name=f"zermelo{n}", dyn="drift", drift=(s, w[0], w[1], 0.0), target_kind="sectors",
                    n_parts=parts)
+
+
+def obstacle_ball(centre, radius) -> List[float]:
+    c = list(centre) + [0.0] * (3 - len(centre))
+    return [0.0, c[0], c[1], c[2], float(radius), 0.0, 0.0]
+
+
+def obstacle_box(lo, hi) -> List[float]:
+    a = list(lo) + [0.0] * (3 - len(lo))
+    b = list(hi) + [0.0] * (3 - len(hi))
+    return [1.0, a[0], a[1], a[2], b[0], b[1], b[2]]
+
+
+def eikonal_obstacles(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 8, radius: float = 0.5,
+                      tol: float = 1e-6) -> Problem:
+    """Sec. 4, eikonal with obstacles: f = a on [-2,2]^2, target B(0, 0.5) in R
+    sectors, one disk and one rectangle as obstacles (the paper gives no
+    sizes: disk B((1.1, 0.9), 0.35), box [-1.6, -0.9] x [-1.3, 0.5])."""
+    obs = np.array([obstacle_ball((1.1, 0.9), 0.35), obstacle_box((-1.6, -1.3), (-0.9, 0.5))])
+    return eikonal_sectors(n=n, n_coarse=n_coarse, n_c=n_c, parts=parts, radius=radius, tol=tol).with_(
+        obstacles=obs, name=f"eikonal_obstacles{n}")
 
 
 def fan(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, half_width: float = 1e-9,
