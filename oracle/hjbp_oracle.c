@@ -118,7 +118,10 @@
  *       line target of half-width r) split into R equal pieces along x_2 over
  *       the box, part j = floor(R (x_2 - lo_2) / (hi_2 - lo_2) + 1e-9),
  *       clamped.  The 1e-9 puts nodes exactly on a sector boundary into the
- *       upper part whatever the last bit of atan2.  On the coarse grid (R6) the
+ *       upper part whatever the last bit of atan2.  In 3D (Sec. 7, R = 8) a
+ *       ball's sectors are the wedges of the azimuth theta of (x_1, x_2)
+ *       around the x_3 axis through the centre, and the plane slab's pieces
+ *       are strips along x_2, by the same formulas.  On the coarse grid (R6) the
  *       ball or slab is widened by k~ sqrt(d)/2 with boundary value
  *       max(0, distance - r)/c(x).
  *   R23 Obstacles (Sec. 4, "Patchy method with obstacles"): closed balls
@@ -293,11 +296,13 @@ static int og_target_part(const og_problem *p, const double x[3], double extra, 
     const double *t = p->targets;
     if (p->target_kind == 1) {
         const double dx = x[0] - t[0], dy = x[1] - t[1];
-        const double dist = sqrt(dx * dx + dy * dy);
+        const double dz = p->dim == 3 ? x[2] - t[2] : 0.0;
+        const double dist = sqrt(p->dim == 3 ? dx * dx + dy * dy + dz * dz : dx * dx + dy * dy);
         if (!(dist <= t[p->dim] + extra)) return -1;
         if (e && dist > 0.0) {
             e[0] = -dx / dist;
             e[1] = -dy / dist;
+            e[2] = -dz / dist;
         }
         double th = atan2(dy, dx);
         if (th < 0.0) th += 2.0 * OG_PI;

@@ -69,7 +69,7 @@ def target_parts(p, x):
     t = p.targets[0]
     if p.target_kind == "sectors":
         off = x[:, :2] - t[:2]
-        inside = np.hypot(off[:, 0], off[:, 1]) <= t[p.dim]
+        inside = np.linalg.norm(x - t[: p.dim], axis=1) <= t[p.dim]
         th = np.mod(np.arctan2(off[:, 1], off[:, 0]), 2 * math.pi)
         j = np.floor(R * th / (2 * math.pi) + 1e-9).astype(int) % R
         part[inside] = j[inside]

@@ -215,3 +215,57 @@ def test_patchy_error_matches_paper_tables(dyn):
     e1, einf = oracle.patchy_error(r.u, g.u)
     assert row[3] / 10 <= e1 <= row[3] * 10, (e1, row)
     assert einf >= e1
+
+
+def test_3d_target_parts_follow_the_definitions():
+    """Sec. 7 targets in 3D: the ball in R wedges around the x3 axis and the
+    plane x1 = 0 in R strips along x2 equal the independent restatement;
+    every part is used and the Fan speed's zero plane holds no node here."""
+    for p in (W.eikonal3d(n=33, n_coarse=9, n_c=14), W.fan3d(n=33, n_coarse=9, n_c=14)):
+        kind, part, _ = oracle.setup(p)
+        ik, ipart, _ = I.kinds(p)
+        assert np.array_equal(kind, ik)
+        assert np.array_equal(part, ipart)
+        assert set(part[part >= 0]) == set(range(8))
+
+
+def test_fan3d_axis_controls_equal_dijkstra():
+    """Fan 3D with the six axis controls: the fixed point is Dijkstra on the
+    axis graph with cost h_i = k / c(x_i) leaving node i."""
+    p = W.fan3d(n=21, n_coarse=7).with_(n_coarse=None, controls=W.controls_axes(3), tol=1e-14)
+    kind, _, h = I.kinds(p)
+    idx, _ = I.node_grid(p)
+    N = kind.size
+    rows, cols, vals = [], [], []
+    for i in np.nonzero(kind == 0)[0]:
+        for d in np.vstack([np.eye(3, dtype=int), -np.eye(3, dtype=int)]):
+            j = int(I.linear(p, idx[i] + d)[0])
+            if kind[j] != 2:
+                rows.append(i)
+                cols.append(j)
+                vals.append(h[i])
+    G = sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+    dist = dijkstra(G.T, directed=True, indices=np.nonzero(kind == 1)[0], min_only=True)
+    ref = np.where(kind == 2, np.inf, dist)
+    r = oracle.global_solve(p)
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(r.u))
+    np.testing.assert_allclose(r.u[fin], ref[fin], rtol=0, atol=1e-11)
+
+
+def test_eikonal3d_sector_labels_follow_the_azimuth():
+    """Eikonal 3D, ball in 8 wedges: characteristics are radial, so a node's
+    patch is the wedge of its azimuth except within a few nodes of a wedge
+    boundary plane (the colour transport smears the labels over a band that
+    is wider in 3D, with 50 directions, than in 2D)."""
+    p = W.eikonal3d(n=33, n_coarse=17, n_c=50).with_(tol=1e-10)
+    r = oracle.patchy_solve(p)
+    x = oracle.grid_coords(p)
+    th = np.mod(np.arctan2(x[:, 1], x[:, 0]), 2 * math.pi)
+    wedge = np.floor(8 * th / (2 * math.pi) + 1e-9).astype(int) % 8
+    ok = r.labels >= 0
+    assert np.mean(r.labels[ok] == wedge[ok]) >= 0.75
+    rho = np.hypot(x[:, 0], x[:, 1])
+    bnd = np.abs(((8 * th / (2 * math.pi) + 0.5) % 1.0) - 0.5) * (2 * math.pi / 8) * rho
+    bad = ok & (r.labels != wedge)
+    assert np.all(bnd[bad] <= 7 * p.spacing)

@@ -320,6 +320,30 @@ def zermelo(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, ra
                    n_parts=parts)
 
 
+# ------------------------------------------------- the paper's 3D tests --
+
+def eikonal3d(n: int = 101, n_coarse: int = 51, n_c: int = 189, parts: int = 8, radius: float = 0.5,
+              tol: float = 1e-6) -> Problem:
+    """Sec. 7, Eikonal 3D: f = a on [-2,2]^3, target B(0, 0.5) split into R
+    wedges by the azimuth around the x3 axis; N_c Fibonacci controls (the
+    paper's 189 geosphere vertices, count kept)."""
+    return Problem(dim=3, n=(n, n, n), lo=(-2.0,) * 3, hi=(2.0,) * 3, speed="one", speed_params=np.zeros(64),
+                   controls=controls_fibonacci(n_c), targets=np.array([[0.0, 0.0, 0.0, radius]]), tol=tol,
+                   n_coarse=(n_coarse,) * 3, name=f"eikonal3d_{n}", target_kind="sectors", n_parts=parts)
+
+
+def fan3d(n: int = 101, n_coarse: int = 51, n_c: int = 189, parts: int = 8, half_width: float = 1e-9,
+          tol: float = 1e-6) -> Problem:
+    """Sec. 7, Fan 3D: c(x) = |x1 + x2 + x3 + 0.1| on [-2,2]^3, target the
+    plane x1 = 0 (a slab of half-width ``half_width``) split into R strips
+    along x2; N_c Fibonacci controls."""
+    q = np.zeros(64)
+    q[:4] = (0.1, 1.0, 1.0, 1.0)
+    return Problem(dim=3, n=(n, n, n), lo=(-2.0,) * 3, hi=(2.0,) * 3, speed="fan", speed_params=q,
+                   controls=controls_fibonacci(n_c), targets=np.array([[0.0, 0.0, 0.0, half_width]]), tol=tol,
+                   n_coarse=(n_coarse,) * 3, name=f"fan3d_{n}", target_kind="slab", n_parts=parts)
+
+
 def obstacle_ball(centre, radius) -> List[float]:
     c = list(centre) + [0.0] * (3 - len(centre))
     return [0.0, c[0], c[1], c[2], float(radius), 0.0, 0.0]
