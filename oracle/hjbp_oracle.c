@@ -121,7 +121,8 @@
  *       upper part whatever the last bit of atan2.  In 3D (Sec. 7, R = 8) a
  *       ball's sectors are the wedges of the azimuth theta of (x_1, x_2)
  *       around the x_3 axis through the centre, and the plane slab's pieces
- *       are strips along x_2, by the same formulas.  On the coarse grid (R6) the
+ *       are strips along x_2, by the same formulas.  A ball may instead be
+ *       split into its 2^d orthants: part j has bit d set iff x_d >= c_d.  On the coarse grid (R6) the
  *       ball or slab is widened by k~ sqrt(d)/2 with boundary value
  *       max(0, distance - r)/c(x).
  *   R23 Obstacles (Sec. 4, "Patchy method with obstacles"): closed balls
@@ -154,7 +155,8 @@ typedef struct {
     double drift[4];           /* dyn_kind 1: s, w_1, w_2, w_3 */
     int target_kind;           /* 0: each row a ball and a part; 1: row 0 a ball in
                                   n_parts sectors; 2: row 0 = (v, ., r) the slab
-                                  |x_1 - v| <= r in n_parts pieces (R22) */
+                                  |x_1 - v| <= r in n_parts pieces; 3: row 0 a
+                                  ball in its 2^dim orthants (R22) */
     int n_parts;               /* parts of target kinds 1 and 2 */
     int n_obstacles;           /* R23 */
     const double *obstacles;   /* n_obstacles x 7: kind (0 ball, 1 box), then a
@@ -309,6 +311,19 @@ static int og_target_part(const og_problem *p, const double x[3], double extra, 
         int j = (int)floor((double)R * th / (2.0 * OG_PI) + 1e-9);
         if (j >= R) j -= R;
         if (j < 0) j = 0;
+        if (gap) *gap = dist > t[p->dim] ? dist - t[p->dim] : 0.0;
+        return j;
+    }
+    if (p->target_kind == 3) {
+        double r2 = 0.0;
+        for (int d = 0; d < p->dim; ++d) r2 += (x[d] - t[d]) * (x[d] - t[d]);
+        const double dist = sqrt(r2);
+        if (!(dist <= t[p->dim] + extra)) return -1;
+        int j = 0;
+        for (int d = 0; d < p->dim; ++d) {
+            if (x[d] >= t[d]) j |= 1 << d;
+            if (e && dist > 0.0) e[d] = (t[d] - x[d]) / dist;
+        }
         if (gap) *gap = dist > t[p->dim] ? dist - t[p->dim] : 0.0;
         return j;
     }

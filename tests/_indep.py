@@ -74,6 +74,11 @@ def target_parts(p, x):
         j = np.floor(R * th / (2 * math.pi) + 1e-9).astype(int) % R
         part[inside] = j[inside]
         return part
+    if p.target_kind == "orthants":
+        inside = np.linalg.norm(x - t[: p.dim], axis=1) <= t[p.dim]
+        j = sum(((x[:, d] >= t[d]).astype(int) << d) for d in range(p.dim))
+        part[inside] = j[inside]
+        return part
     inside = np.abs(x[:, 0] - t[0]) <= t[p.dim]
     j = np.clip(np.floor(R * (x[:, 1] - p.lo[1]) / (p.hi[1] - p.lo[1]) + 1e-9).astype(int), 0, R - 1)
     part[inside] = j[inside]

@@ -218,15 +218,18 @@ def test_patchy_error_matches_paper_tables(dyn):
 
 
 def test_3d_target_parts_follow_the_definitions():
-    """Sec. 7 targets in 3D: the ball in R wedges around the x3 axis and the
-    plane x1 = 0 in R strips along x2 equal the independent restatement;
+    """Sec. 7 targets in 3D: the ball in R wedges around the x3 axis or in its
+    octants (and a disk in its quadrants) and the plane x1 = 0 in R strips
+    along x2 equal the independent restatement;
     every part is used and the Fan speed's zero plane holds no node here."""
-    for p in (W.eikonal3d(n=33, n_coarse=9, n_c=14), W.fan3d(n=33, n_coarse=9, n_c=14)):
+    for p in (W.eikonal3d(n=33, n_coarse=9, n_c=14, split="sectors"), W.eikonal3d(n=33, n_coarse=9, n_c=14),
+              W.fan3d(n=33, n_coarse=9, n_c=14), W.eikonal_sectors(n=41, n_coarse=11).with_(target_kind="orthants",
+                                                                                         n_parts=4)):
         kind, part, _ = oracle.setup(p)
         ik, ipart, _ = I.kinds(p)
         assert np.array_equal(kind, ik)
         assert np.array_equal(part, ipart)
-        assert set(part[part >= 0]) == set(range(8))
+        assert set(part[part >= 0]) == set(range(p.n_parts))
 
 
 def test_fan3d_axis_controls_equal_dijkstra():
@@ -258,7 +261,7 @@ def test_eikonal3d_sector_labels_follow_the_azimuth():
     patch is the wedge of its azimuth except within a few nodes of a wedge
     boundary plane (the colour transport smears the labels over a band that
     is wider in 3D, with 50 directions, than in 2D)."""
-    p = W.eikonal3d(n=33, n_coarse=17, n_c=50).with_(tol=1e-10)
+    p = W.eikonal3d(n=33, n_coarse=17, n_c=50, split="sectors").with_(tol=1e-10)
     r = oracle.patchy_solve(p)
     x = oracle.grid_coords(p)
     th = np.mod(np.arctan2(x[:, 1], x[:, 0]), 2 * math.pi)
@@ -269,3 +272,17 @@ def test_eikonal3d_sector_labels_follow_the_azimuth():
     bnd = np.abs(((8 * th / (2 * math.pi) + 0.5) % 1.0) - 0.5) * (2 * math.pi / 8) * rho
     bad = ok & (r.labels != wedge)
     assert np.all(bnd[bad] <= 7 * p.spacing)
+
+
+def test_eikonal3d_octant_labels_follow_the_signs():
+    """Eikonal 3D, ball in its octants: characteristics are radial, so a
+    node's patch is the octant of x itself except within a few nodes of a
+    coordinate plane (the band the colour transport smears, as for wedges)."""
+    p = W.eikonal3d(n=33, n_coarse=17, n_c=50).with_(tol=1e-10)
+    r = oracle.patchy_solve(p)
+    x = oracle.grid_coords(p)
+    octant = (x[:, 0] >= 0).astype(int) | ((x[:, 1] >= 0).astype(int) << 1) | ((x[:, 2] >= 0).astype(int) << 2)
+    ok = r.labels >= 0
+    assert np.mean(r.labels[ok] == octant[ok]) >= 0.8
+    bad = ok & (r.labels != octant)
+    assert np.all(np.abs(x[bad]).min(axis=1) <= 7 * p.spacing)

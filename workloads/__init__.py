@@ -33,7 +33,7 @@ import numpy as np
 
 SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3, "fan": 4}
 DYN_KINDS = {"speed": 0, "drift": 1}
-TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2}
+TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2, "orthants": 3}
 SNAP = 1e-15
 
 
@@ -323,13 +323,16 @@ def zermelo(n: int = 201, n_coarse: int = 51, n_c: int = 32, parts: int = 16, ra
 # ------------------------------------------------- the paper's 3D tests --
 
 def eikonal3d(n: int = 101, n_coarse: int = 51, n_c: int = 189, parts: int = 8, radius: float = 0.5,
-              tol: float = 1e-6) -> Problem:
-    """Sec. 7, Eikonal 3D: f = a on [-2,2]^3, target B(0, 0.5) split into R
-    wedges by the azimuth around the x3 axis; N_c Fibonacci controls (the
-    paper's 189 geosphere vertices, count kept)."""
+              tol: float = 1e-6, split: str = "orthants") -> Problem:
+    """Sec. 7, Eikonal 3D: f = a on [-2,2]^3, target B(0, 0.5) split into its
+    8 octants (split="orthants") or into R wedges by the azimuth around the
+    x3 axis (split="sectors"); N_c Fibonacci controls (the paper's 189
+    geosphere vertices, count kept)."""
+    if split == "orthants":
+        parts = 8
     return Problem(dim=3, n=(n, n, n), lo=(-2.0,) * 3, hi=(2.0,) * 3, speed="one", speed_params=np.zeros(64),
                    controls=controls_fibonacci(n_c), targets=np.array([[0.0, 0.0, 0.0, radius]]), tol=tol,
-                   n_coarse=(n_coarse,) * 3, name=f"eikonal3d_{n}", target_kind="sectors", n_parts=parts)
+                   n_coarse=(n_coarse,) * 3, name=f"eikonal3d_{n}", target_kind=split, n_parts=parts)
 
 
 def fan3d(n: int = 101, n_coarse: int = 51, n_c: int = 189, parts: int = 8, half_width: float = 1e-9,
