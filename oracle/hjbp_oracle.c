@@ -125,6 +125,14 @@
  *       split into its 2^d orthants: part j has bit d set iff x_d >= c_d.  On the coarse grid (R6) the
  *       ball or slab is widened by k~ sqrt(d)/2 with boundary value
  *       max(0, distance - r)/c(x).
+ *   R24 Brockett's integrator (Sec. 7): f(x, a) = (a1, a2, x1 a2 - x2 a1)
+ *       with a in {-5, 0, 5}^2 (rows (a1, a2, unused) of the control table,
+ *       speed field c = 1).  As in R20 the foot is x_i + k f/|f| and h_{i,a} =
+ *       k/|f|, now per node: x1 a2 - x2 a1 is formed at the node, |f| as
+ *       sqrt(f1^2 + f2^2 + f3^2) summed in that order; a = 0 is not
+ *       admissible.  The coarse boundary values of R6 use the largest |f(x, a)|
+ *       over the controls as the speed (a lower bound on the time: the
+ *       dynamics cannot head straight for the ball in general).
  *   R23 Obstacles (Sec. 4, "Patchy method with obstacles"): closed balls
  *       |x - c|^2 <= r^2 and closed boxes lo <= x <= hi (per axis) of the
  *       state space.  A node inside one is a state constraint like the ghost
@@ -151,7 +159,8 @@ typedef struct {
     const double *controls;    /* n_controls x dim unit vectors */
     int n_targets;
     const double *targets;     /* n_targets x (dim + 1): centre, radius */
-    int dyn_kind;              /* 0: f = c(x) a; 1: f = s a + w (R20) */
+    int dyn_kind;              /* 0: f = c(x) a; 1: f = s a + w (R20);
+                                  2: Brockett f = (a1, a2, x1 a2 - x2 a1) (R24) */
     double drift[4];           /* dyn_kind 1: s, w_1, w_2, w_3 */
     int target_kind;           /* 0: each row a ball and a part; 1: row 0 a ball in
                                   n_parts sectors; 2: row 0 = (v, ., r) the slab
@@ -257,6 +266,17 @@ double og_speed(const og_problem *p, const double x[3]) {
    (R6): c(x) for f = c(x) a; for f = s a + w the v >= 0 with |v e - w| = s
    (0 when e cannot be followed). */
 static double og_approach_speed(const og_problem *p, const double x[3], const double e[3]) {
+    if (p->dyn_kind == 2) {
+        /* R24: the largest |f(x, a)| over the controls */
+        double best = 0.0;
+        for (int m = 0; m < p->n_controls; ++m) {
+            const double *a = p->controls + (size_t)m * p->dim;
+            const double f2 = x[0] * a[1] - x[1] * a[0];
+            const double nf = sqrt(a[0] * a[0] + a[1] * a[1] + f2 * f2);
+            if (nf > best) best = nf;
+        }
+        return best;
+    }
     if (p->dyn_kind != 1) return og_speed(p, x);
     double ew = 0.0, ww = 0.0;
     for (int d = 0; d < p->dim; ++d) {
@@ -387,6 +407,21 @@ int og_setup(const og_problem *p, double radius_extra, unsigned char *kind, int 
 static double og_dir(const og_problem *p, const double *h, int64_t i, int m, double dv[3]) {
     const double *a = p->controls + (size_t)m * p->dim;
     dv[0] = dv[1] = dv[2] = 0.0;
+    if (p->dyn_kind == 2) {
+        /* Brockett (Sec. 7, R24): f = (a1, a2, x1 a2 - x2 a1) at the node */
+        int idx[3];
+        double x[3];
+        og_index3(p, i, idx);
+        og_coords(p, idx, x);
+        const double f[3] = {a[0], a[1], x[0] * a[1] - x[1] * a[0]};
+        const double nf = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(nf > 1e-15)) return INFINITY;
+        for (int d = 0; d < 3; ++d) {
+            const double v = f[d] / nf;
+            dv[d] = fabs(v) < 1e-15 ? 0.0 : v;
+        }
+        return p->k / nf;
+    }
     if (p->dyn_kind == 1) {
         double f[3] = {0.0, 0.0, 0.0}, n2 = 0.0;
         for (int d = 0; d < p->dim; ++d) {

@@ -131,6 +131,26 @@ def control_steps(p):
     return dirs, 1.0 / nf
 
 
+def node_control_steps(p, x):
+    """Per node (rows of x) and control: the unit direction of f and the time
+    step h = k / |f| (+inf where f = 0).  Brockett's f = (a1, a2, x1 a2 -
+    x2 a1); otherwise the per-control steps of control_steps times h_i."""
+    a = np.asarray(p.controls, float)
+    if p.dyn != "brockett":
+        dirs, g = control_steps(p)
+        _, _, h = kinds(p)
+        return np.broadcast_to(dirs, (x.shape[0],) + dirs.shape), h[:, None] * g[None, :]
+    f = np.stack([np.broadcast_to(a[:, 0], (x.shape[0], a.shape[0])),
+                  np.broadcast_to(a[:, 1], (x.shape[0], a.shape[0])),
+                  x[:, 0:1] * a[None, :, 1] - x[:, 1:2] * a[None, :, 0]], axis=2)
+    nf = np.linalg.norm(f, axis=2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dirs = np.where(nf[..., None] > 1e-15, f / nf[..., None], 0.0)
+        h = np.where(nf > 1e-15, p.spacing / nf, np.inf)
+    dirs[np.abs(dirs) < 1e-15] = 0.0
+    return dirs, h
+
+
 def q1_corners(p, node_idx, a):
     """Corners and bilinear/trilinear weights of the foot node_idx + a (grid
     coordinates); zero weights dropped."""

@@ -286,3 +286,99 @@ def test_eikonal3d_octant_labels_follow_the_signs():
     assert np.mean(r.labels[ok] == octant[ok]) >= 0.8
     bad = ok & (r.labels != octant)
     assert np.all(np.abs(x[bad]).min(axis=1) <= 7 * p.spacing)
+
+
+def _policy_iteration_nodewise(p):
+    """Exact fixed point of F with per-(node, control) directions and time
+    steps.  S* (R14) is restated as the greatest set S of free nodes from
+    which the target is reached with controls whose positive-weight corners
+    all lie in S or the target: reach breadth-first from the target, drop
+    what was not reached, repeat.  The control that first reached a node
+    moves it to an earlier node with positive probability, so that policy is
+    proper; policy iteration with dense linear solves then gives the exact
+    fixed point on S*, +inf elsewhere."""
+    kind, _, _ = I.kinds(p)
+    idx, x = I.node_grid(p)
+    dirs, hs = I.node_control_steps(p, x)
+    free = np.nonzero(kind == 0)[0]
+    corners = {int(i): [None if not np.isfinite(hs[i, m]) else I.q1_corners(p, idx[i], dirs[i, m])
+                        for m in range(dirs.shape[1])] for i in free}
+    S = set(int(i) for i in free)
+    while True:
+        ok = lambda j: kind[j] == 1 or j in S
+        level, first = {}, {}
+        frontier = True
+        while frontier:
+            frontier = False
+            for i in sorted(S - set(level)):
+                for m, cs in enumerate(corners[i]):
+                    if cs is None or not all(ok(j) for j, _ in cs):
+                        continue
+                    if any(kind[j] == 1 or (j in level and j != i) for j, _ in cs):
+                        level[i], first[i] = len(level), m
+                        frontier = True
+                        break
+        if set(level) == S:
+            break
+        S = set(level)
+    Sl = sorted(S)
+    pos = {i: q for q, i in enumerate(Sl)}
+    usable = lambda i, m: corners[i][m] is not None and all(kind[j] == 1 or j in S for j, _ in corners[i][m])
+    pol = dict(first)
+    for _ in range(300):
+        A = np.eye(len(Sl))
+        b = np.zeros(len(Sl))
+        for i in Sl:
+            m = pol[i]
+            b[pos[i]] = hs[i, m]
+            for j, w in corners[i][m]:
+                if j in pos:
+                    A[pos[i], pos[j]] -= w
+        v = np.linalg.solve(A, b)
+        full = np.where(kind == 1, 0.0, np.inf)
+        full[Sl] = v
+        changed = False
+        for i in Sl:
+            q = [hs[i, m] + sum(w * full[j] for j, w in corners[i][m]) if usable(i, m) else np.inf
+                 for m in range(dirs.shape[1])]
+            m = int(np.argmin(q))
+            if q[m] < q[pol[i]] - 1e-13:
+                pol[i] = m
+                changed = True
+        if not changed:
+            return full
+    raise AssertionError("policy iteration did not stop")
+
+
+def test_brockett_policy_iteration_9x9x9():
+    """Brute force on 9^3 (343 free nodes) for Brockett's integrator: value
+    iteration equals exact policy iteration over the per-node directions
+    f/|f| and steps k/|f| with f = (a1, a2, x1 a2 - x2 a1)."""
+    p = W.brockett3d(n=9, n_coarse=5, radius=0.6).with_(n_coarse=None, tol=1e-14)
+    ref = _policy_iteration_nodewise(p)
+    r = oracle.global_solve(p, tol=1e-14)
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(r.u))
+    np.testing.assert_allclose(r.u[fin], ref[fin], rtol=0, atol=1e-11)
+
+
+def test_brockett_symmetries_and_axis():
+    """Brockett's f is equivariant under the rotation (x1, x2, x3) ->
+    (-x2, x1, x3) (controls rotated alike) and the reflection (x1, x2, x3) ->
+    (x2, x1, -x3) (controls swapped), and the control set and target are
+    invariant, so the solution is too; a wrong sign in x1 a2 - x2 a1 breaks
+    the reflection.  On the x1 axis the fastest motion is straight along it
+    at speed 5 (a1 = -5 keeps x2 = x3 = 0), which lands on nodes: there the
+    scheme gives the exact time (|x1| - 0.25) / 5."""
+    n = 33
+    p = W.brockett3d(n=n, n_coarse=17).with_(n_coarse=None)
+    U = oracle.global_solve(p, tol=1e-13).u.reshape(n, n, n)   # [x3, x2, x1]
+    fin = np.isfinite(U)
+    rot = np.stack([U[z].T[:, ::-1] for z in range(n)])
+    refl = U[::-1].transpose(0, 2, 1)
+    for V in (rot, refl):
+        assert np.array_equal(fin, np.isfinite(V))
+        assert np.abs(U[fin] - V[fin]).max() <= 1e-12
+    x1 = -2.0 + 4.0 * np.arange(n) / (n - 1)
+    axis = U[n // 2, n // 2, 1:-1]
+    np.testing.assert_allclose(axis, np.maximum(np.abs(x1[1:-1]) - 0.25, 0.0) / 5.0, rtol=0, atol=1e-12)

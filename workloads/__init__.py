@@ -32,7 +32,7 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3, "fan": 4}
-DYN_KINDS = {"speed": 0, "drift": 1}
+DYN_KINDS = {"speed": 0, "drift": 1, "brockett": 2}
 TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2, "orthants": 3}
 SNAP = 1e-15
 
@@ -345,6 +345,22 @@ def fan3d(n: int = 101, n_coarse: int = 51, n_c: int = 189, parts: int = 8, half
     return Problem(dim=3, n=(n, n, n), lo=(-2.0,) * 3, hi=(2.0,) * 3, speed="fan", speed_params=q,
                    controls=controls_fibonacci(n_c), targets=np.array([[0.0, 0.0, 0.0, half_width]]), tol=tol,
                    n_coarse=(n_coarse,) * 3, name=f"fan3d_{n}", target_kind="slab", n_parts=parts)
+
+
+def controls_brockett(amax: float = 5.0) -> np.ndarray:
+    """Sec. 7, Brockett: the nine controls {-amax, 0, amax}^2 as rows
+    (a1, a2, 0) (the third entry is unused; a = 0 cannot move)."""
+    v = (-amax, 0.0, amax)
+    return np.array([[a1, a2, 0.0] for a2 in v for a1 in v], dtype=np.float64)
+
+
+def brockett3d(n: int = 101, n_coarse: int = 51, amax: float = 5.0, radius: float = 0.25,
+               tol: float = 1e-6, split: str = "orthants") -> Problem:
+    """Sec. 7, Brockett 3D: f = (a1, a2, x1 a2 - x2 a1), a in {-5, 0, 5}^2, on
+    [-2,2]^3, target B(0, 0.25) split into its 8 octants."""
+    return Problem(dim=3, n=(n, n, n), lo=(-2.0,) * 3, hi=(2.0,) * 3, speed="one", speed_params=np.zeros(64),
+                   controls=controls_brockett(amax), targets=np.array([[0.0, 0.0, 0.0, radius]]), tol=tol,
+                   n_coarse=(n_coarse,) * 3, name=f"brockett3d_{n}", dyn="brockett", target_kind=split, n_parts=8)
 
 
 def obstacle_ball(centre, radius) -> List[float]:
