@@ -48,7 +48,10 @@ OPS_PER_UPDATE_3D = 8       # canonical trilinear update: 7 FMA + 1 min
 FAMILY = "sincos2d"
 
 
-PAPER_FAMILIES = {"paper-eikonal": W.eikonal_sectors, "paper-fan": W.fan, "paper-zermelo": W.zermelo}
+PAPER_FAMILIES = {"paper-eikonal": W.eikonal_sectors, "paper-fan": W.fan, "paper-zermelo": W.zermelo,
+                  "paper-obstacles": W.eikonal_obstacles}
+PAPER_FAMILIES_3D = {"paper-eikonal3d": W.eikonal3d, "paper-fan3d": W.fan3d,
+                     "paper-brockett3d": lambda n_c=9, parts=8, **kw: W.brockett3d(**kw)}
 
 
 def problem(seed: int):
@@ -57,6 +60,9 @@ def problem(seed: int):
     if FAMILY in PAPER_FAMILIES:
         # the paper's own tests (Table 1) at its Tables 5-9 sizes; no seed
         return PAPER_FAMILIES[FAMILY](n=N_FINE, n_coarse=N_COARSE, n_c=32, parts=16, tol=1e-6)
+    if FAMILY in PAPER_FAMILIES_3D:
+        # the paper's 3D tests (Sec. 7) at "50^3 -> 100^3", R = 8, 189 controls (Brockett: 9)
+        return PAPER_FAMILIES_3D[FAMILY](n=N_FINE, n_coarse=N_COARSE, n_c=189, parts=8, tol=1e-6)
     return W.sincos2d(seed, n=N_FINE, n_coarse=N_COARSE, n_c=64, n_targets=4, radius=0.05, tol=1e-6)
 
 
@@ -454,10 +460,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
     ap.add_argument("--workload", default="sincos2d",
-                    choices=["sincos2d", "sin3d", "batched", "serving", "paper-eikonal", "paper-fan", "paper-zermelo"],
+                    choices=["sincos2d", "sin3d", "batched", "serving"] + sorted(PAPER_FAMILIES) + sorted(PAPER_FAMILIES_3D),
                     help="sincos2d: 2D patchy workload (default); sin3d: 3D patchy workload; batched: 512 "
                          "problems, batch vs one at a time; serving: Poisson request stream, p50/p99; "
-                         "paper-*: the paper's Table 1 tests at 801^2 / 101^2, R = 16, 32 controls")
+                         "paper-*: the paper's Table 1 tests at 801^2 / 101^2, R = 16, 32 controls (obstacles: "
+                         "the eikonal with a disk and a box); paper-*3d: its 3D tests at 101^3 / 51^3, R = 8, "
+                         "189 controls")
     ap.add_argument("--count", type=int, default=0, help="problems (batched: 512) / requests (serving: 2000)")
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
@@ -489,6 +497,9 @@ def main():
         # the paper's "100^2 -> 800^2" (cells), R = 16, N_c = 32
         N_FINE, N_COARSE = args.n or 801, args.nc or 101
         WORKLOAD = f"{FAMILY}_n{N_FINE}_c{N_COARSE}_nc32_R16"
+    elif FAMILY in PAPER_FAMILIES_3D:
+        N_FINE, N_COARSE = args.n or 101, args.nc or 51
+        WORKLOAD = f"{FAMILY}_n{N_FINE}_c{N_COARSE}_nc{9 if 'brockett' in FAMILY else 189}_R8"
     else:
         N_FINE, N_COARSE = args.n or 2049, args.nc or 65
         WORKLOAD = f"patchy2d_sincos_n{N_FINE}_c{N_COARSE}_nc64_R4"

@@ -65,17 +65,32 @@ typedef enum {
  * drift = {s, w_1, w_2, w_3}, speed must be HJBP_C_ONE, 2D only; every control
  * needs |s a + w| > 1e-15.  With |h f| = k (Sec. 2.1) the foot of control a is
  * x_i + k f/|f| and its time step k/|f|.                                    */
-typedef enum { HJBP_DYN_SPEED = 0, HJBP_DYN_DRIFT = 1 } hjbp_dyn_kind;
+/* HJBP_DYN_BROCKETT (Sec. 7, 3D only, speed HJBP_C_ONE): Brockett's integrator
+ * f(x, a) = (a_1, a_2, x_1 a_2 - x_2 a_1); control rows are (a_1, a_2, unused),
+ * any finite values (the paper's set is {-5, 0, 5}^2); a = 0 cannot move and
+ * is never evaluated.  The foot x_i + k f/|f| and the step k/|f| depend on the
+ * node; the coarse boundary values of Step 1 divide the distance to the
+ * target by the largest |f(x, a)| over the controls.                        */
+typedef enum { HJBP_DYN_SPEED = 0, HJBP_DYN_DRIFT = 1, HJBP_DYN_BROCKETT = 2 } hjbp_dyn_kind;
 
 /* Target Omega_0 and its parts Omega_0^j (one patch each, Sec. 3).
  * HJBP_TARGET_BALLS: every row of targets is a ball (centre, radius) and a part.
- * HJBP_TARGET_SECTORS (2D): row 0 is one ball split into n_parts equal angular
+ * HJBP_TARGET_SECTORS: row 0 is one ball split into n_parts equal angular
  *   sectors, part j = floor(n_parts theta / (2 pi) + 1e-9) mod n_parts with
- *   theta the angle of x - centre in [0, 2 pi).
- * HJBP_TARGET_SLAB (2D): row 0 = (v, unused, r): the slab |x_1 - v| <= r (a line
- *   target of half-width r) split into n_parts equal pieces along x_2 over the
- *   box, part j = floor(n_parts (x_2 - lo_2) / (hi_2 - lo_2) + 1e-9), clamped. */
-typedef enum { HJBP_TARGET_BALLS = 0, HJBP_TARGET_SECTORS = 1, HJBP_TARGET_SLAB = 2 } hjbp_target_kind;
+ *   theta the angle of (x_1 - c_1, x_2 - c_2) in [0, 2 pi) (in 3D: wedges
+ *   around the x_3 axis through the centre).
+ * HJBP_TARGET_SLAB (2D and 3D): row 0 = (v, unused.., r): the slab |x_1 - v| <= r
+ *   (a line or plane target of half-width r) split into n_parts equal pieces
+ *   along x_2 over the box, part j = floor(n_parts (x_2 - lo_2) / (hi_2 - lo_2)
+ *   + 1e-9), clamped.
+ * HJBP_TARGET_ORTHANTS: row 0 is one ball split into its 2^dim orthants
+ *   (n_parts must be 2^dim): part j has bit d set iff x_{d+1} >= c_{d+1}.    */
+typedef enum {
+    HJBP_TARGET_BALLS = 0,
+    HJBP_TARGET_SECTORS = 1,
+    HJBP_TARGET_SLAB = 2,
+    HJBP_TARGET_ORTHANTS = 3
+} hjbp_target_kind;
 
 /* Arithmetic of the fine-grid sweeps.  HJBP_FP64: every sweep in FP64.
  * HJBP_FP32_POLISH64: bulk sweeps in FP32, then FP64 polishing sweeps.      */
@@ -90,6 +105,7 @@ typedef enum { HJBP_FP64 = 0, HJBP_FP32_POLISH64 = 1 } hjbp_precision;
  *   speed, speed_params[64]   c(x), see hjbp_speed_kind
  *   n_controls, controls      discrete control set A: n_controls x dim unit
  *                  vectors (row-major), 1 <= n_controls <= HJBP_MAX_CONTROLS
+ *                  (Brockett's integrator: rows (a_1, a_2, unused))
  *   n_targets, targets        Omega_0 = union of balls: n_targets x (dim+1)
  *                  rows (centre, radius); ball j is target part Omega_0^j and
  *                  seeds patch j (1 <= n_targets <= HJBP_MAX_TARGETS)
@@ -101,6 +117,7 @@ typedef enum { HJBP_FP64 = 0, HJBP_FP32_POLISH64 = 1 } hjbp_precision;
  *   max_sweeps     cap on tile sweeps per phase (<= 0 selects 1e6)            */
 #define HJBP_MAX_CONTROLS 256
 #define HJBP_MAX_TARGETS 64
+#define HJBP_MAX_OBSTACLES 16
 typedef struct {
     int dim;
     int n[3];
@@ -135,6 +152,14 @@ typedef struct {
     double drift[4];    /* HJBP_DYN_DRIFT: s, w_1, w_2, w_3 */
     int target_kind;    /* hjbp_target_kind */
     int n_parts;        /* parts (patches) of HJBP_TARGET_SECTORS / SLAB, 1..64 */
+    int n_obstacles;    /* obstacles (Sec. 4, "Patchy method with obstacles"), 0..HJBP_MAX_OBSTACLES */
+    const double *obstacles;  /* n_obstacles x 7 rows, caller-owned, copied at create:
+                           (0, c_1, c_2, c_3, r, -, -) the closed ball |x - c|^2 <= r^2, or
+                           (1, l_1, l_2, l_3, u_1, u_2, u_3) the closed box l <= x <= u (the
+                           third coordinate ignored in 2D).  A node inside an obstacle is a
+                           state constraint like the ghost ring (+inf, label -1) unless it
+                           is a target node; the coarse grid of Step 1 follows the same
+                           rule.  NULL when n_obstacles is 0.                           */
 } hjbp_problem_desc;
 
 /* flags: HJBP_FLAG_TIME_SWEEPS records a CUDA event pair around every launch

@@ -18,8 +18,8 @@ HJBP_FP64, HJBP_FP32_POLISH64 = 0, 1
 HJBP_OUT_UCOARSE, HJBP_OUT_U0, HJBP_OUT_ASTAR, HJBP_OUT_PHI, HJBP_OUT_U32 = range(5)
 MAX_CONTROLS, MAX_TARGETS = 256, 64
 SPEED_KINDS = {"one": 0, "sincos2d": 1, "sin3d": 2, "fourier2d": 3, "fan": 4}
-DYN_KINDS = {"speed": 0, "drift": 1}
-TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2}
+DYN_KINDS = {"speed": 0, "drift": 1, "brockett": 2}
+TARGET_KINDS = {"balls": 0, "sectors": 1, "slab": 2, "orthants": 3}
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ETIMEOUT", 5: "ECUDA", 6: "EBUSY", 7: "ESTATE"}
 
 
@@ -54,6 +54,8 @@ class Desc(C.Structure):
         ("drift", C.c_double * 4),
         ("target_kind", C.c_int),
         ("n_parts", C.c_int),
+        ("n_obstacles", C.c_int),
+        ("obstacles", C.POINTER(C.c_double)),
     ]
 
 
@@ -376,7 +378,11 @@ def desc_from_problem(p, precision: int = HJBP_FP32_POLISH64, max_sweeps: int = 
         d.drift[i] = float(v)
     d.target_kind = TARGET_KINDS[getattr(p, "target_kind", "balls")]
     d.n_parts = int(getattr(p, "n_parts", 0))
-    return d, (controls, targets)
+    obs = getattr(p, "obstacles", None)
+    obstacles = np.ascontiguousarray(np.zeros((0, 7)) if obs is None else obs, dtype=np.float64)
+    d.n_obstacles = obstacles.shape[0]
+    d.obstacles = obstacles.ctypes.data_as(C.POINTER(C.c_double)) if d.n_obstacles else C.POINTER(C.c_double)()
+    return d, (controls, targets, obstacles)
 
 
 class Plan:

@@ -92,6 +92,7 @@ static std::string validate(const hjbp_problem_desc *d) {
     if ((d->speed == HJBP_C_SINCOS2D || d->speed == HJBP_C_FOURIER2D) && d->dim != 2) return "2D speed field with dim 3";
     if (d->n_controls < 1 || d->n_controls > HJBP_MAX_CONTROLS) return "n_controls out of range";
     if (!d->controls) return "controls is NULL";
+    bool moving = false;
     for (int m = 0; m < d->n_controls; ++m) {
         double s = 0.0;
         for (int a = 0; a < d->dim; ++a) {
@@ -99,15 +100,27 @@ static std::string validate(const hjbp_problem_desc *d) {
             if (!std::isfinite(v)) return "control component not finite";
             s += v * v;
         }
-        if (std::fabs(std::sqrt(s) - 1.0) > 1e-9) return "controls must be unit vectors";
+        if (d->dyn == HJBP_DYN_BROCKETT) {
+            // rows (a1, a2, unused); a = 0 is allowed but cannot move
+            if (d->controls[m * d->dim] != 0.0 || d->controls[m * d->dim + 1] != 0.0) moving = true;
+        } else if (std::fabs(std::sqrt(s) - 1.0) > 1e-9) {
+            return "controls must be unit vectors";
+        }
     }
+    if (d->dyn == HJBP_DYN_BROCKETT && !moving) return "Brockett's controls are all zero";
     if (d->n_targets < 1 || d->n_targets > HJBP_MAX_TARGETS) return "n_targets out of range";
-    if (d->target_kind < HJBP_TARGET_BALLS || d->target_kind > HJBP_TARGET_SLAB) return "unknown target kind";
+    if (d->target_kind < HJBP_TARGET_BALLS || d->target_kind > HJBP_TARGET_ORTHANTS) return "unknown target kind";
+    if (d->target_kind == HJBP_TARGET_ORTHANTS && d->n_parts != (1 << d->dim)) return "orthant targets need n_parts = 2^dim";
     if (d->target_kind != HJBP_TARGET_BALLS) {
-        if (d->dim != 2) return "split targets (sectors, slab) are 2D";
         if (d->n_parts < 1 || d->n_parts > HJBP_MAX_TARGETS) return "n_parts out of range";
     }
-    if (d->dyn != HJBP_DYN_SPEED && d->dyn != HJBP_DYN_DRIFT) return "unknown dynamics";
+    if (d->dyn != HJBP_DYN_SPEED && d->dyn != HJBP_DYN_DRIFT && d->dyn != HJBP_DYN_BROCKETT)
+        return "unknown dynamics";
+    if (d->dyn == HJBP_DYN_BROCKETT) {
+        if (d->dim != 3) return "Brockett's integrator is 3D";
+        if (d->speed != HJBP_C_ONE) return "Brockett's integrator takes the speed field HJBP_C_ONE";
+        if (d->flags & HJBP_FLAG_TILE_QUEUE) return "the tile queue runs the 2D path";
+    }
     if (d->dyn == HJBP_DYN_DRIFT) {
         if (d->dim != 2) return "drift dynamics are 2D";
         if (d->speed != HJBP_C_ONE) return "drift dynamics take the speed field HJBP_C_ONE";
@@ -118,6 +131,7 @@ static std::string validate(const hjbp_problem_desc *d) {
     for (int j = 0; j < d->n_targets; ++j)
         for (int a = 0; a <= d->dim; ++a)
             if (!std::isfinite(d->targets[j * (d->dim + 1) + a])) return "target entry not finite";
+    if (const char *e = hjbp::check_obstacles(d)) return e;
     if (!(d->tol > 0.0)) return "tol must be positive";
     if (d->precision != HJBP_FP64 && d->precision != HJBP_FP32_POLISH64) return "unknown precision";
     if ((d->flags & (HJBP_FLAG_DIRICHLET | HJBP_FLAG_WARM_START | HJBP_FLAG_CAUSAL_SWEEPS)) && d->n_coarse[0] == 0)
@@ -158,6 +172,9 @@ hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const 
         p->targets.assign(desc->targets, desc->targets + (size_t)desc->n_targets * (desc->dim + 1));
         p->desc.controls = p->controls.data();
         p->desc.targets = p->targets.data();
+        if (desc->n_obstacles > 0)
+            p->obstacles.assign(desc->obstacles, desc->obstacles + (size_t)desc->n_obstacles * 7);
+        p->desc.obstacles = p->obstacles.empty() ? nullptr : p->obstacles.data();
         p->R = desc->target_kind == HJBP_TARGET_BALLS ? desc->n_targets : desc->n_parts;
         // per-control direction of f and time-step factor (|h f| = k, Sec. 2.1)
         p->dirs.assign((size_t)desc->n_controls * desc->dim, 0.0);

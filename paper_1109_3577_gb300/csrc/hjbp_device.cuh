@@ -11,7 +11,9 @@
 // patch boundary, Sec. 3 "Details on boundary conditions").
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "../../include/hjbp.h"
@@ -140,6 +142,68 @@ struct TargetSet {
     double c0[kMaxTargets], c1[kMaxTargets], c2[kMaxTargets], r[kMaxTargets];
 };
 
+// Obstacles (Sec. 4): closed balls and boxes whose nodes are state
+// constraints like the ghost ring.
+constexpr int kMaxObstacles = HJBP_MAX_OBSTACLES;
+struct ObstacleSet {
+    int n;
+    int dim;
+    int kind[kMaxObstacles];                // 0 ball, 1 box
+    double a[kMaxObstacles][3];             // ball centre / box lower corner
+    double b[kMaxObstacles][3];             // ball radius in b[.][0] / box upper corner
+};
+
+// Is the node x inside an obstacle?  |x - c|^2 is summed in axis order with
+// each product and sum rounded, so membership is decided exactly.
+__device__ inline bool in_obstacle(const ObstacleSet &os, double x0, double x1, double x2) {
+    for (int o = 0; o < os.n; ++o) {
+        if (os.kind[o] == 0) {
+            const double d0 = __dsub_rn(x0, os.a[o][0]), d1 = __dsub_rn(x1, os.a[o][1]);
+            double r2 = __dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1));
+            if (os.dim == 3) {
+                const double d2 = __dsub_rn(x2, os.a[o][2]);
+                r2 = __dadd_rn(r2, __dmul_rn(d2, d2));
+            }
+            if (r2 <= __dmul_rn(os.b[o][0], os.b[o][0])) return true;
+        } else {
+            bool in = x0 >= os.a[o][0] && x0 <= os.b[o][0] && x1 >= os.a[o][1] && x1 <= os.b[o][1];
+            if (os.dim == 3) in = in && x2 >= os.a[o][2] && x2 <= os.b[o][2];
+            if (in) return true;
+        }
+    }
+    return false;
+}
+
+// Host side: the checks of the obstacle rows and their device form.
+inline const char *check_obstacles(const hjbp_problem_desc *d) {
+    if (d->n_obstacles < 0 || d->n_obstacles > HJBP_MAX_OBSTACLES) return "n_obstacles out of range";
+    if (d->n_obstacles > 0 && !d->obstacles) return "obstacles is NULL";
+    for (int o = 0; o < d->n_obstacles; ++o) {
+        const double *r = d->obstacles + 7 * o;
+        if (r[0] != 0.0 && r[0] != 1.0) return "obstacle kind must be 0 (ball) or 1 (box)";
+        for (int c = 1; c < 7; ++c)
+            if (!std::isfinite(r[c])) return "obstacle entry not finite";
+        if (r[0] == 0.0 && !(r[4] >= 0.0)) return "obstacle radius must be >= 0";
+    }
+    return nullptr;
+}
+
+inline ObstacleSet make_obstacles(int dim, int n, const double *rows) {
+    ObstacleSet os;
+    std::memset(&os, 0, sizeof(os));
+    os.n = n;
+    os.dim = dim;
+    for (int o = 0; o < n; ++o) {
+        const double *r = rows + 7 * o;
+        os.kind[o] = r[0] == 0.0 ? 0 : 1;
+        for (int c = 0; c < 3; ++c) os.a[o][c] = r[1 + c];
+        if (os.kind[o] == 0) os.b[o][0] = r[4];
+        else
+            for (int c = 0; c < 3; ++c) os.b[o][c] = r[4 + c];
+    }
+    return os;
+}
+
 // c(x) of f(x, a) = c(x) a (fixed menu, see hjbp_speed_kind).
 __device__ inline double speed_at(const SpeedParams &sp, double x0, double x1, double x2) {
     const double pi = 3.14159265358979323846;
@@ -204,6 +268,56 @@ struct Grid2 {
 // un-widened target (0 inside).  Explicitly rounded operations, so that the
 // decisions follow x = lo + i k and the definitions of hjbp_target_kind.
 // *e (optional) gets the unit direction from the point towards the target.
+// Target part of a 3D node (-1 outside), the target widened by extra; *gap
+// the distance to the un-widened target (0 inside).  Balls; one ball in R
+// wedges by the azimuth of (x_1, x_2) around the x_3 axis; the plane slab
+// |x_1 - v| <= r in R strips along x_2 (Sec. 7).
+__device__ inline int target_part3(const TargetSet &ts, double lo1, int n1, double k, double x0, double x1, double x2,
+                                   double extra, double *gap) {
+    const double pi = 3.14159265358979323846;
+    *gap = 0.0;
+    if (ts.kind == HJBP_TARGET_BALLS) {
+        for (int j = 0; j < ts.n; ++j) {
+            const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]), d2 = __dsub_rn(x2, ts.c2[j]);
+            const double d =
+                __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+            if (d <= __dadd_rn(ts.r[j], extra)) {
+                *gap = d > ts.r[j] ? __dsub_rn(d, ts.r[j]) : 0.0;
+                return j;
+            }
+        }
+        return -1;
+    }
+    const int R = ts.nparts;
+    if (ts.kind == HJBP_TARGET_ORTHANTS) {
+        const double d0 = __dsub_rn(x0, ts.c0[0]), d1 = __dsub_rn(x1, ts.c1[0]), d2 = __dsub_rn(x2, ts.c2[0]);
+        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+        if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+        *gap = d > ts.r[0] ? __dsub_rn(d, ts.r[0]) : 0.0;
+        return (x0 >= ts.c0[0] ? 1 : 0) | (x1 >= ts.c1[0] ? 2 : 0) | (x2 >= ts.c2[0] ? 4 : 0);
+    }
+    if (ts.kind == HJBP_TARGET_SECTORS) {
+        const double d0 = __dsub_rn(x0, ts.c0[0]), d1 = __dsub_rn(x1, ts.c1[0]), d2 = __dsub_rn(x2, ts.c2[0]);
+        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+        if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+        double th = atan2(d1, d0);
+        if (th < 0.0) th = __dadd_rn(th, 2.0 * pi);
+        int j = (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)R, th), 2.0 * pi), 1e-9));
+        if (j >= R) j -= R;
+        if (j < 0) j = 0;
+        *gap = d > ts.r[0] ? __dsub_rn(d, ts.r[0]) : 0.0;
+        return j;
+    }
+    const double d = fabs(__dsub_rn(x0, ts.c0[0]));
+    if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+    const double hi1 = __dadd_rn(lo1, __dmul_rn((double)(n1 - 1), k));
+    int j = (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)R, __dsub_rn(x1, lo1)), __dsub_rn(hi1, lo1)), 1e-9));
+    if (j >= R) j = R - 1;
+    if (j < 0) j = 0;
+    *gap = d > ts.r[0] ? __dsub_rn(d, ts.r[0]) : 0.0;
+    return j;
+}
+
 __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x0, double x1, double extra,
                                    double *gap, double *e = nullptr) {
     const double pi = 3.14159265358979323846;
@@ -224,6 +338,17 @@ __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x
         return -1;
     }
     const int R = ts.nparts;
+    if (ts.kind == HJBP_TARGET_ORTHANTS) {
+        const double d0 = __dsub_rn(x0, ts.c0[0]), d1 = __dsub_rn(x1, ts.c1[0]);
+        const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)));
+        if (!(d <= __dadd_rn(ts.r[0], extra))) return -1;
+        if (e && d > 0.0) {
+            e[0] = __ddiv_rn(-d0, d);
+            e[1] = __ddiv_rn(-d1, d);
+        }
+        *gap = d > ts.r[0] ? __dsub_rn(d, ts.r[0]) : 0.0;
+        return (x0 >= ts.c0[0] ? 1 : 0) | (x1 >= ts.c1[0] ? 2 : 0);
+    }
     if (ts.kind == HJBP_TARGET_SECTORS) {
         const double d0 = __dsub_rn(x0, ts.c0[0]), d1 = __dsub_rn(x1, ts.c1[0]);
         const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)));

@@ -33,14 +33,14 @@ namespace hjbp {
 // ------------------------------------------------------------------ set-up --
 
 // Node codes, h_i = k / c(x_i) (|h f| = k, Sec. 2.1) and the fixed values of
-// target nodes.  Target part j: |x - c_j| <= r_j + extra (lowest j).  With
+// target nodes; nodes in an obstacle (Sec. 4) are hard like the ghost ring.  Target part j: |x - c_j| <= r_j + extra (lowest j).  With
 // boundary_values, a target node outside its ball gets the time
 // (|x - c_j| - r_j) / c(x) to reach it (the coarse grid, Step 1); otherwise 0.
 // Coordinates and distances use explicitly rounded operations so that target
 // membership is decided exactly as x = lo + i k, r^2 = sum (x - c)^2 dictate.
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
                           int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
-                          double *__restrict__ fixed, DynParams dp) {
+                          double *__restrict__ fixed, DynParams dp, ObstacleSet os) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
@@ -51,8 +51,9 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
         const bool ring = ix == 0 || iy == 0 || ix == g.n0 - 1 || iy == g.n1 - 1;
         const double c = speed_at(sp, x0, x1, 0.0);
         const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
+        const bool blocked = part < 0 && in_obstacle(os, x0, x1, 0.0);
         const double hh = stopped ? (double)INFINITY : __ddiv_rn(g.k, c);
-        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped) ? kHard : (int8_t)0);
+        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped || blocked) ? kHard : (int8_t)0);
         if (h32) h32[i] = (float)hh;
         if (h64) h64[i] = hh;
         // coarse boundary value (R6): the gap over the speed towards the target
@@ -2528,6 +2529,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     const Grid2 g = make_grid(d.n[0], d.n[1], d.lo[0], d.lo[1], p.k);
     const SpeedParams sp = make_speed(p);
     const TargetSet ts = make_targets(p);
+    const ObstacleSet os = make_obstacles(2, d.n_obstacles, d.obstacles);
     const int cap = d.max_sweeps > 0 ? d.max_sweeps : 1000000;
     const int hist = std::max(std::min(cap, 1 << 20), kReachCap);
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
@@ -2546,7 +2548,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     float *h32 = fp32 ? alloc_n<float>(p, N) : nullptr;
     unsigned long long *updates = alloc_n<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
-    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr, make_dyn(p));
+    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr, make_dyn(p), os);
     ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "setup");
     Sched sched = make_sched(p, g, hist);
@@ -2563,8 +2565,8 @@ hjbp_status solve2d(hjbp_plan &p) {
         double *cfix = alloc_n<double>(p, Nc);
         double *cb0 = alloc_n<double>(p, Nc), *cb1 = alloc_n<double>(p, Nc);
         k_setup2d<<<grid_for(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(2.0) / 2.0, 1, ccode, nullptr, ch64,
-                                                cfix, make_dyn(p));
-                                                ++p.stats.kernel_launches;
+                                                cfix, make_dyn(p), os);
+        ++p.stats.kernel_launches;
         k_merge_targets<<<grid_for(Nc), 256, 0, st>>>(Nc, ccode);
         ++p.stats.kernel_launches;
         Sched csched = make_sched(p, gc, hist);

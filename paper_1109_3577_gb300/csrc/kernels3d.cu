@@ -89,6 +89,12 @@ struct ReachTable3 {
     uint8_t uni[8][128];
 };
 
+// Controls (a1, a2) of Brockett's integrator (R24).
+struct GenCtl {
+    int nc;
+    double a1[kMaxControls], a2[kMaxControls];
+};
+
 __device__ __forceinline__ float warp_max3(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -106,9 +112,11 @@ __device__ __forceinline__ float block_max64(float v, float *scratch) {
 
 // ------------------------------------------------------------------ set-up --
 
+// gctl (Brockett, R24): the coarse boundary values divide by the largest
+// |f(x, a)| over the controls instead of c(x).
 __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
                           int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
-                          double *__restrict__ fixed) {
+                          double *__restrict__ fixed, ObstacleSet os, const GenCtl *__restrict__ gctl = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % g.n0);
@@ -117,25 +125,28 @@ __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, i
         const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
         const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
         const double x2 = __dadd_rn(g.lo2, __dmul_rn((double)iz, g.k));
-        int part = -1;
         double dist = 0.0;
-        for (int j = 0; j < ts.n && part < 0; ++j) {
-            const double d0 = __dsub_rn(x0, ts.c0[j]), d1 = __dsub_rn(x1, ts.c1[j]), d2 = __dsub_rn(x2, ts.c2[j]);
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-            const double dd = __dsqrt_rn(r2);
-            if (dd <= __dadd_rn(ts.r[j], extra)) {
-                part = j;
-                dist = __dsub_rn(dd, ts.r[j]);
-            }
-        }
+        const int part = target_part3(ts, g.lo1, g.n1, g.k, x0, x1, x2, extra, &dist);
         const bool ring = ix == 0 || iy == 0 || iz == 0 || ix == g.n0 - 1 || iy == g.n1 - 1 || iz == g.n2 - 1;
         const double c = speed_at(sp, x0, x1, x2);
         const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
+        const bool blocked = part < 0 && in_obstacle(os, x0, x1, x2);   // obstacle (Sec. 4)
         const double hh = stopped ? (double)INFINITY : __ddiv_rn(g.k, c);
-        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped) ? kHard : (int8_t)0);
+        code[i] = part >= 0 ? (int8_t)(kTargetBase + part) : ((ring || stopped || blocked) ? kHard : (int8_t)0);
         if (h32) h32[i] = (float)hh;
         if (h64) h64[i] = hh;
-        if (fixed) fixed[i] = (part >= 0 && boundary_values && dist > 0.0) ? __ddiv_rn(dist, c) : 0.0;
+        double v = c;
+        if (gctl && fixed) {
+            v = 0.0;
+            for (int m = 0; m < gctl->nc; ++m) {
+                const double a1 = gctl->a1[m], a2 = gctl->a2[m];
+                const double f2 = __dsub_rn(__dmul_rn(x0, a2), __dmul_rn(x1, a1));
+                const double nf =
+                    __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2)), __dmul_rn(f2, f2)));
+                v = nf > v ? nf : v;
+            }
+        }
+        if (fixed) fixed[i] = (part >= 0 && boundary_values && dist > 0.0) ? __ddiv_rn(dist, v) : 0.0;
     }
 }
 
@@ -153,6 +164,14 @@ __global__ void k_init3d(int64_t N, const int8_t *__restrict__ code, const doubl
         b0[i] = v;
         b1[i] = v;
     }
+}
+
+// Target nodes get back their exact FP64 values (0, or the coarse boundary
+// values of R6) after an FP32 solve.
+__global__ void k_restore_fixed3(int64_t N, const int8_t *__restrict__ code, const double *__restrict__ fixed,
+                                 double *__restrict__ u) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        if (code[i] >= kTargetBase) u[i] = fixed ? fixed[i] : 0.0;
 }
 
 // Dirichlet data of Eq. (dbc) in FP32: U_P^(0), the bound 1e6 and above
@@ -342,15 +361,158 @@ __device__ __forceinline__ T sl_update3(const Tile3<T, kDir> &sm, int lx, int ly
     return b0 < b1 ? b0 : b1;
 }
 
+// ------------------------------------------- per-node dynamics (Brockett) --
+
+// Brockett's integrator f(x, a) = (a1, a2, x1 a2 - x2 a1) (Sec. 7, R24): the
+// foot x + k f/|f| and the step k/|f| depend on the node through (x1, x2)
+// only, so the tables hold one row per grid column c = iy n0 + ix and
+// control m, at index c nc + m.  Corner b (bits 0..2: a step along x, y, z)
+// of the foot's cell lies at the node plus (b0 sx, b1 sy, b2 sz), s = +1 where
+// the component of f/|f| is >= 0, and has weight w_b = prod_d (b_d ? t_d :
+// 1 - t_d), t = |f|/|f| componentwise; w_0 belongs to the node itself.
+struct Gen3 {
+    int nc;
+    const double4 *dh;       // f/|f| (x, y, z) and h = k/|f| (+inf: a = 0, not admissible)
+    const W3<float> *v32;    // k[0..6] = kap w_b (b = 1..7), k[7] = kap h, kap = 1/(1 - w_0)
+    const W3<double> *v64;   // the same in FP64
+    const W3<float> *p32;    // k[0] = kap, k[b] = kap w_b (b = 1..7): the colour transport
+    const uint8_t *oct;      // bit 0..2 set where sx, sy, sz = +1
+    const uint32_t *cset;    // positive-weight corners other than the node (bit 9 dz + 3 dy + dx,
+                             // offsets dz - 1 ..); 0 when a is not admissible
+};
+
+// Literal Q1 weights (w_0 .. w_7) and corner offsets of the foot of the per-node
+// control row e (Brockett, R24), in FP64.
+__device__ __forceinline__ void gen_weights(const Gen3 &gen, int64_t e, double w[8], int &sx, int &sy, int &sz) {
+    const double4 q = gen.dh[e];
+    const double t[3] = {fabs(q.x), fabs(q.y), fabs(q.z)};
+    sx = q.x >= 0.0 ? 1 : -1;
+    sy = q.y >= 0.0 ? 1 : -1;
+    sz = q.z >= 0.0 ? 1 : -1;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        double v = 1.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v *= ((b >> d) & 1) ? t[d] : 1.0 - t[d];
+        w[b] = v;
+    }
+}
+
+// The column tables, formed in FP64 with each operation rounded in the order
+// x_d = lo_d + i_d k, f3 = x1 a2 - x2 a1, |f| = sqrt(a1^2 + a2^2 + f3^2).
+__global__ void k_gen_table3(Grid3 g, GenCtl gc, double4 *__restrict__ dh, W3<float> *__restrict__ v32,
+                             W3<double> *__restrict__ v64, W3<float> *__restrict__ p32, uint8_t *__restrict__ oct,
+                             uint32_t *__restrict__ cset) {
+    const int64_t total = (int64_t)g.n0 * g.n1 * gc.nc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e % gc.nc);
+        const int64_t col = e / gc.nc;
+        const int ix = (int)(col % g.n0), iy = (int)(col / g.n0);
+        const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
+        const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
+        const double a1 = gc.a1[m], a2 = gc.a2[m];
+        const double f[3] = {a1, a2, __dsub_rn(__dmul_rn(x0, a2), __dmul_rn(x1, a1))};
+        const double nf =
+            __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(f[0], f[0]), __dmul_rn(f[1], f[1])), __dmul_rn(f[2], f[2])));
+        W3<float> w32, q32;
+        W3<double> w64;
+        if (!(nf > 1e-15)) {
+            dh[e] = make_double4(0.0, 0.0, 0.0, (double)INFINITY);
+            for (int b = 0; b < 8; ++b) {
+                w32.k[b] = 0.f;
+                q32.k[b] = 0.f;
+                w64.k[b] = 0.0;
+            }
+            v32[e] = w32;
+            v64[e] = w64;
+            p32[e] = q32;
+            oct[e] = 0;
+            cset[e] = 0;
+            continue;
+        }
+        double dv[3], t[3];
+        uint8_t o = 0;
+        for (int d = 0; d < 3; ++d) {
+            const double v = __ddiv_rn(f[d], nf);
+            dv[d] = fabs(v) < 1e-15 ? 0.0 : v;
+            t[d] = fabs(dv[d]);
+            if (dv[d] >= 0.0) o |= (uint8_t)(1u << d);
+        }
+        const double h = __ddiv_rn(g.k, nf);
+        dh[e] = make_double4(dv[0], dv[1], dv[2], h);
+        double w[8];
+        uint32_t cs = 0;
+        for (int b = 0; b < 8; ++b) {
+            w[b] = 1.0;
+            for (int d = 0; d < 3; ++d) w[b] *= ((b >> d) & 1) ? t[d] : 1.0 - t[d];
+            if (b > 0 && w[b] > 0.0) {
+                const int dx = (b & 1) ? ((o & 1) ? 1 : -1) : 0, dy = (b & 2) ? ((o & 2) ? 1 : -1) : 0,
+                          dz = (b & 4) ? ((o & 4) ? 1 : -1) : 0;
+                cs |= 1u << (9 * (dz + 1) + 3 * (dy + 1) + (dx + 1));
+            }
+        }
+        const double kap = 1.0 / (1.0 - w[0]);
+        for (int b = 1; b < 8; ++b) {
+            w64.k[b - 1] = kap * w[b];
+            w32.k[b - 1] = (float)(kap * w[b]);
+            q32.k[b] = (float)(kap * w[b]);
+        }
+        w64.k[7] = kap * h;
+        w32.k[7] = (float)(kap * h);
+        q32.k[0] = (float)kap;
+        v32[e] = w32;
+        v64[e] = w64;
+        p32[e] = q32;
+        oct[e] = o;
+        cset[e] = cs;
+    }
+}
+
+// The update of node (lx, ly, lz) with per-node feet: rows e0 .. e0 + nc - 1
+// of the column tables (read through the L1 cache); mask as in sl_update3.
+template <typename T, bool kDir>
+__device__ __forceinline__ T sl_update3g(const Tile3<T, kDir> &sm, int lx, int ly, int lz, uint32_t mask,
+                                         int64_t e0, const Gen3 &gen) {
+    const W3<T> *tab;
+    if constexpr (sizeof(T) == 4) tab = gen.v32;
+    else tab = gen.v64;
+    T best = Num<T>::big();
+    for (int m = 0; m < gen.nc; ++m) {
+        const uint32_t cs = __ldg(&gen.cset[e0 + m]);
+        if (!cs) continue;
+        if constexpr (!kDir) {
+            if (cs & ~mask) continue;   // a positive-weight corner outside the patch: +inf
+        }
+        const unsigned of = __ldg(&gen.oct[e0 + m]);
+        const int sx = (of & 1u) ? 1 : -1, sy = (of & 2u) ? 1 : -1, sz = (of & 4u) ? 1 : -1;
+        T w[8];
+        load_w3(tab[e0 + m], w);
+        T v = w[7];
+#pragma unroll
+        for (int b = 1; b < 8; ++b) {
+            const int dx = (b & 1) ? sx : 0, dy = (b & 2) ? sy : 0, dz = (b & 4) ? sz : 0;
+            const int bit = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
+            T c;
+            if ((mask >> bit) & 1u) c = sm.u[lz + dz][ly + dy][lx + dx];
+            else if constexpr (kDir) c = sm.d[lz + dz][ly + dy][lx + dx];   // Eq. (dbc)
+            else c = Num<T>::big();
+            v = fma(w[b - 1], c, v);
+        }
+        best = v < best ? v : best;
+    }
+    return best;
+}
+
 // clamp != 0: monotone update from M; clamp == 0: the plain update of the
 // warm start (AO1).  kDir: neighbours outside the patch read the Dirichlet
 // data dval (Eq. dbc); a node's own pruned nodes (code -2 - patch) read +inf.
-template <typename T, bool kDir = false>
+// kGen: per-node feet from the column tables of gen (h is then unused).
+template <typename T, bool kDir = false, bool kGen = false>
 __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restrict__ code,
                                                   const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                   TileSched s, int par, int rounds, unsigned long long *updates,
                                                   const CtlTable3<T> ct, int clamp = 1,
-                                                  const T *__restrict__ dval = nullptr) {
+                                                  const T *__restrict__ dval = nullptr, const Gen3 gen = Gen3{}) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -359,11 +521,12 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     // per interior node: neighbour mask (bit 31: the node is free) and h
     __shared__ uint32_t mk[kT3][kT3][kT3];
     __shared__ T hs[kT3][kT3][kT3];
-    __shared__ W3<T> tab[kMaxControls];
-    for (int m = threadIdx.x; m < ct.nc; m += blockDim.x) {
-        for (int b = 0; b < 7; ++b) tab[m].k[b] = ct.kw[b][m];
-        tab[m].k[7] = ct.kap[m];
-    }
+    __shared__ W3<T> tab[kGen ? 1 : kMaxControls];
+    if constexpr (!kGen)
+        for (int m = threadIdx.x; m < ct.nc; m += blockDim.x) {
+            for (int b = 0; b < 7; ++b) tab[m].k[b] = ct.kw[b][m];
+            tab[m].k[7] = ct.kap[m];
+        }
     load_tile3(g, s, code, b0, b1, x0, y0, z0, sm, dval);   // ends with a block barrier
     const int tid = threadIdx.x;
     int nfree = 0;
@@ -385,7 +548,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                     }
             m |= 0x80000000u;
             ++nfree;
-            hv = h[((int64_t)(z0 + lz) * g.n1 + (y0 + ly)) * g.n0 + (x0 + lx)];
+            if constexpr (!kGen) hv = h[((int64_t)(z0 + lz) * g.n1 + (y0 + ly)) * g.n0 + (x0 + lx)];
         }
         mk[lz][ly][lx] = m;
         hs[lz][ly][lx] = hv;
@@ -400,7 +563,12 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                 const bool active = (m & 0x80000000u) != 0;
                 T nw = sm.u[lz][ly][lx];
                 if (active) {
-                    const T best = sl_update3<T, kDir>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
+                    T best;
+                    if constexpr (kGen)
+                        best = sl_update3g<T, kDir>(sm, lx, ly, lz, m,
+                                                    ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc, gen);
+                    else
+                        best = sl_update3<T, kDir>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
                     if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
                 }
                 __syncthreads();
@@ -421,9 +589,11 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
 
 // dterm (optional): Dirichlet data (Eq. dbc); a node outside the patch with
 // finite data is a terminal, like the patch's own target part.
+// kGen: the corner sets of the per-node feet from the column tables.
+template <bool kGen>
 __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restrict__ code,
                                                   uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt,
-                                                  const double *__restrict__ dterm) {
+                                                  const double *__restrict__ dterm, const Gen3 gen) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -478,6 +648,13 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
                     }
             const uint32_t usable = same | term;
             uint32_t c = 0;
+            if constexpr (kGen) {
+                const int64_t e0 = ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc;
+                for (int m = 0; m < gen.nc; ++m) {
+                    const uint32_t need = __ldg(&gen.cset[e0 + m]);
+                    if (need && (need & ~usable) == 0) c |= need;
+                }
+            } else {
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
                 const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
@@ -493,6 +670,7 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
                     const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
                     c |= ((u >> (b - 1)) & 1u) << bit;
                 }
+            }
             }
             h0 = (c & term) != 0;
             cs = c & same;
@@ -555,54 +733,6 @@ __global__ void k_gather3d(Grid3 g, const uint8_t *__restrict__ latest, const T 
         if (out_t) out_t[i] = v;
         if (out64) out64[i] = v >= Num<T>::thresh() ? (double)INFINITY : (double)v;
     }
-}
-
-// ------------------------------------------- small grids: one warp per node --
-
-template <typename T>
-__global__ void k_value_wide3d(Grid3 g, const int8_t *__restrict__ code, const T *__restrict__ h,
-                               const T *__restrict__ uin, T *__restrict__ uout, float *__restrict__ res, int launch,
-                               const Ctl3 *__restrict__ ct) {
-    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    float mc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
-        const int8_t cd = code[i];
-        const T old = uin[i];
-        T nw = old;
-        if (cd >= 0 && cd < kTargetBase) {
-            const int8_t tg = (int8_t)(cd + kTargetBase);
-            const T hh = h[i];
-            T best = Num<T>::big();
-            for (int m = lane; m < ct->nc; m += 32) {
-                const int64_t dx = ct->sx[m], dy = (int64_t)ct->sy[m] * g.n0, dz = (int64_t)ct->sz[m] * g.n0 * g.n1;
-                const double kap = 1.0 / (1.0 - ct->w[0][m]);
-                T v = (T)kap * hh;
-                for (int b = 1; b < 8; ++b) {
-                    const int64_t j = i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0);
-                    const int8_t q = code[j];
-                    const T a = (q == cd || q == tg) ? uin[j] : Num<T>::big();
-                    v = fma((T)(kap * ct->w[b][m]), a, v);
-                }
-                best = v < best ? v : best;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T other = __shfl_xor_sync(0xffffffffu, best, o);
-                best = other < best ? other : best;
-            }
-            if (best < Num<T>::thresh()) nw = best < old ? best : old;
-        }
-        if (lane == 0) {
-            uout[i] = nw;
-            const bool vi = nw >= Num<T>::thresh(), oi = old >= Num<T>::thresh();
-            const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)nw - (double)old));
-            mc = fmaxf(mc, d);
-        }
-    }
-    mc = warp_max3(mc);
-    if (lane == 0 && mc > 0.f) atomic_max_pos(&res[launch], mc);
 }
 
 // ---------------------------------------------------- Step 2: U_P^(0), a* --
@@ -761,6 +891,81 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
     }
 }
 
+// Eq. (feedbackcontrol) with per-node feet (Brockett, R24): a* = argmin_a
+// { I[U0](x_i + k f/|f|) + k/|f| }, literal Q1 in FP64, lowest index on ties.
+__global__ void k_feedback3g(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ u0,
+                             uint8_t *__restrict__ astar, const Gen3 gen) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t c = code[i];
+        if (c < 0 || c >= kTargetBase || u0[i] >= Num<double>::thresh()) {
+            astar[i] = kNoControl;
+            continue;
+        }
+        const int64_t e0 = (i % sz) * gen.nc;
+        double best = Num<double>::big();
+        int arg = kNoControl;
+        for (int m = 0; m < gen.nc; ++m) {
+            if (!gen.cset[e0 + m]) continue;
+            double w[8];
+            int sx, sy1, sz1;
+            gen_weights(gen, e0 + m, w, sx, sy1, sz1);
+            double v = gen.dh[e0 + m].w;
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                if (w[b] > 0.0)
+                    v += w[b] * u0[i + ((b & 1) ? sx : 0) + ((b & 2) ? sy1 * sy : 0) + ((b & 4) ? sz1 * sz : 0)];
+            if (v < best) {
+                best = v;
+                arg = m;
+            }
+        }
+        astar[i] = best < Num<double>::thresh() ? (uint8_t)arg : kNoControl;
+    }
+}
+
+// FP64 Jacobi sweep with per-node feet (the polish of Brockett's problem;
+// eight controls need no FP32 filter).  Outside the patch: +inf, or the
+// Dirichlet data (Eq. dbc).
+__global__ void k_polish3g(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ uin,
+                           double *__restrict__ uout, float *maxchg, const double *__restrict__ dval, const Gen3 gen) {
+    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
+    const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
+    float mc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t cd = code[i];
+        double v = uin[i];
+        if (cd >= 0 && cd < kTargetBase && v < Num<double>::thresh()) {
+            const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+            const int64_t e0 = (i % sz) * gen.nc;
+            double best = Num<double>::big();
+            for (int m = 0; m < gen.nc; ++m) {
+                if (!gen.cset[e0 + m]) continue;
+                const unsigned of = gen.oct[e0 + m];
+                const int64_t ox = (of & 1u) ? 1 : -1, oy = (of & 2u) ? sy : -sy, oz = (of & 4u) ? sz : -sz;
+                const W3<double> wt = gen.v64[e0 + m];
+                double x = wt.k[7];
+#pragma unroll
+                for (int b = 1; b < 8; ++b) {
+                    const int64_t j = i + ((b & 1) ? ox : 0) + ((b & 2) ? oy : 0) + ((b & 4) ? oz : 0);
+                    const int8_t q = code[j];
+                    const double cv = (q == cd || q == tg || q == pr) ? uin[j] : (dval ? dval[j] : Num<double>::big());
+                    x = fma(wt.k[b - 1], cv, x);
+                }
+                best = x < best ? x : best;
+            }
+            if (best < Num<double>::thresh()) {
+                mc = fmaxf(mc, (float)fabs(best - v));
+                v = best;
+            }
+        }
+        uout[i] = v;
+    }
+    mc = warp_max3(mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(maxchg, mc);
+}
+
 // --------------------------------------------------- Step 3.1: colours phi --
 
 template <int RG>
@@ -790,11 +995,13 @@ template <int RG, bool kS> struct Phi3Smem {
 };
 
 // FP32 colour transport (bulk: monotone max from 0; correction: with source).
-template <int RG, bool kSource>
+// kGen: the weights of a node's a* from its column's row of gen.p32.
+template <int RG, bool kSource, bool kGen = false>
 __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restrict__ code,
                                                 const uint8_t *__restrict__ astar, float *__restrict__ b0,
                                                 float *__restrict__ b1, const float *__restrict__ src, TileSched s,
-                                                int par, int rounds, const Ctl3 *__restrict__ pc) {
+                                                int par, int rounds, const Ctl3 *__restrict__ pc,
+                                                const Gen3 gen = Gen3{}) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -843,11 +1050,12 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     }
     __syncthreads();
     if (alive) atomicOr(&salive, alive);
-    for (int m = tid; m < pc->nc; m += blockDim.x) {
-        sm.toff[m] = (uint8_t)((pc->sx[m] > 0 ? 1u : 0u) | (pc->sy[m] > 0 ? 2u : 0u) | (pc->sz[m] > 0 ? 4u : 0u));
-        sm.tw[m][0] = make_float4(pc->kw[0][m], pc->kw[1][m], pc->kw[2][m], pc->kw[3][m]);
-        sm.tw[m][1] = make_float4(pc->kw[4][m], pc->kw[5][m], pc->kw[6][m], pc->kw[7][m]);
-    }
+    if constexpr (!kGen)
+        for (int m = tid; m < pc->nc; m += blockDim.x) {
+            sm.toff[m] = (uint8_t)((pc->sx[m] > 0 ? 1u : 0u) | (pc->sy[m] > 0 ? 2u : 0u) | (pc->sz[m] > 0 ? 4u : 0u));
+            sm.tw[m][0] = make_float4(pc->kw[0][m], pc->kw[1][m], pc->kw[2][m], pc->kw[3][m]);
+            sm.tw[m][1] = make_float4(pc->kw[4][m], pc->kw[5][m], pc->kw[6][m], pc->kw[7][m]);
+        }
     __syncthreads();
     // a colour that is zero over the whole image stays zero: skip it (uniform per tile)
     const unsigned live = salive;
@@ -861,9 +1069,20 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                 const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
                 float nw[RG];
                 if (active) {
-                    const unsigned of = sm.toff[a];
+                    unsigned of;
+                    float4 w0, w1;
+                    if constexpr (kGen) {
+                        const int64_t e = ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc + a;
+                        of = __ldg(&gen.oct[e]);
+                        const float4 *q = reinterpret_cast<const float4 *>(gen.p32[e].k);
+                        w0 = __ldg(q);
+                        w1 = __ldg(q + 1);
+                    } else {
+                        of = sm.toff[a];
+                        w0 = sm.tw[a][0];
+                        w1 = sm.tw[a][1];
+                    }
                     const int sx = (of & 1u) ? 1 : -1, sy = (of & 2u) ? 1 : -1, sz = (of & 4u) ? 1 : -1;
-                    const float4 w0 = sm.tw[a][0], w1 = sm.tw[a][1];
                     const float kw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                     for (int q = 0; q < RG; ++q) {
@@ -939,10 +1158,10 @@ __global__ void k_phi_collect3d(Grid3 g, const uint8_t *__restrict__ latest, con
     }
 }
 
-template <int RG>
+template <int RG, bool kGen = false>
 __global__ void k_phi_residual3d(Grid3 g, const int8_t *__restrict__ code, const uint8_t *__restrict__ astar,
                                  const double *__restrict__ phi, float *__restrict__ r32, float *rmax,
-                                 const Ctl3 *__restrict__ pc) {
+                                 const Ctl3 *__restrict__ pc, const Gen3 gen = Gen3{}) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     float mc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -953,13 +1172,26 @@ __global__ void k_phi_residual3d(Grid3 g, const int8_t *__restrict__ code, const
             for (int q = 0; q < RG; ++q) r32[(int64_t)q * N + i] = 0.0f;
             continue;
         }
-        const int64_t dx = pc->sx[a], dy = (int64_t)pc->sy[a] * g.n0, dz = (int64_t)pc->sz[a] * g.n0 * g.n1;
+        double w[8];
+        int64_t dx, dy, dz;
+        if constexpr (kGen) {
+            int sx, sy, sz;
+            gen_weights(gen, (i % ((int64_t)g.n0 * g.n1)) * gen.nc + a, w, sx, sy, sz);
+            dx = sx;
+            dy = (int64_t)sy * g.n0;
+            dz = (int64_t)sz * g.n0 * g.n1;
+        } else {
+            for (int b = 0; b < 8; ++b) w[b] = pc->w[b][a];
+            dx = pc->sx[a];
+            dy = (int64_t)pc->sy[a] * g.n0;
+            dz = (int64_t)pc->sz[a] * g.n0 * g.n1;
+        }
 #pragma unroll
         for (int q = 0; q < RG; ++q) {
             const double *f = phi + (int64_t)q * N;
             double v = 0.0;
             for (int b = 0; b < 8; ++b)
-                v += pc->w[b][a] * f[i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0)];
+                v += w[b] * f[i + ((b & 1) ? dx : 0) + ((b & 2) ? dy : 0) + ((b & 4) ? dz : 0)];
             const double r = v - f[i];
             r32[(int64_t)q * N + i] = (float)r;
             mc = fmaxf(mc, (float)fabs(r));
@@ -1381,7 +1613,7 @@ float ms3(const Ev3 &a, const Ev3 &b) {
 }
 
 int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, int64_t N,
-           const double *dterm = nullptr) {
+           const double *dterm = nullptr, const Gen3 *gen = nullptr) {
     const ReachTable3 rt = make_reach3(p);
     unsigned long long *removed = alloc3<unsigned long long>(p, 1);
     int total = 0;
@@ -1391,7 +1623,8 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
         if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
-            k_reach3d<<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm);
+            if (gen) k_reach3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, *gen);
+            else k_reach3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, Gen3{});
             ++p.stats.kernel_launches;
         });
         total += rr.launches;
@@ -1412,9 +1645,9 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
 template <typename T>
 Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0, T *b1, Sched3 &s, double tol,
             int cap, int rounds, T *out_t, double *out64, unsigned long long *updates, const T *dval = nullptr,
-            const double *warm = nullptr) {
+            const double *warm = nullptr, const double *fixed = nullptr, const Gen3 *gen = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
-    k_init3d<T><<<grid_for3(N), 256, 0, p.stream>>>(N, code, nullptr, (T)kStartValue, b0, b1, warm);
+    k_init3d<T><<<grid_for3(N), 256, 0, p.stream>>>(N, code, fixed, (T)kStartValue, b0, b1, warm);
     const int clamp = warm ? 0 : 1;
     ++p.stats.kernel_launches;
     const CtlTable3<T> ct = make_table3<T>(p);
@@ -1427,7 +1660,13 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
             check_cuda(cudaEventCreate(&b), "event");
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
-        if (dval)
+        if (gen && dval)
+            k_value3d<T, true, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
+                                                                       ct, clamp, dval, *gen);
+        else if (gen)
+            k_value3d<T, false, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
+                                                                        ct, clamp, nullptr, *gen);
+        else if (dval)
             k_value3d<T, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
                                                                  clamp, dval);
         else
@@ -1461,44 +1700,101 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
     return rr;
 }
 
-Run3 wide3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const double *h, const double *fixed, double *b0,
-           double *b1, double tol, int cap, const Ctl3 *dct, double *out64) {
-    const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
-    cudaStream_t st = p.stream;
-    k_init3d<double><<<grid_for3(N), 256, 0, st>>>(N, code, fixed, kStartValue, b0, b1, nullptr);
+GenCtl make_genctl(const hjbp_plan &p) {
+    GenCtl c;
+    std::memset(&c, 0, sizeof(c));
+    c.nc = p.desc.n_controls;
+    for (int m = 0; m < c.nc; ++m) {
+        c.a1[m] = p.controls[3 * m];
+        c.a2[m] = p.controls[3 * m + 1];
+    }
+    return c;
+}
+
+// The column tables of the per-node feet on grid g (Brockett, R24).
+Gen3 make_gen3(hjbp_plan &p, const Grid3 &g) {
+    const GenCtl hc = make_genctl(p);
+    const int64_t rows = (int64_t)g.n0 * g.n1 * hc.nc;
+    double4 *dh = alloc3<double4>(p, rows);
+    W3<float> *v32 = alloc3<W3<float>>(p, rows);
+    W3<double> *v64 = alloc3<W3<double>>(p, rows);
+    W3<float> *p32 = alloc3<W3<float>>(p, rows);
+    uint8_t *oct = alloc3<uint8_t>(p, rows);
+    uint32_t *cset = alloc3<uint32_t>(p, rows);
+    k_gen_table3<<<grid_for3(rows), 256, 0, p.stream>>>(g, hc, dh, v32, v64, p32, oct, cset);
     ++p.stats.kernel_launches;
-    const int chunk = 16;
+    check_cuda(cudaGetLastError(), "column tables");
+    Gen3 r;
+    r.nc = hc.nc;
+    r.dh = dh;
+    r.v32 = v32;
+    r.v64 = v64;
+    r.p32 = p32;
+    r.oct = oct;
+    r.cset = cset;
+    return r;
+}
+
+// Step 1 on the coarse grid: FP32 Gauss-Seidel tiles to 1e-6 from M, then
+// the FP32-filtered FP64 Jacobi sweep of the polish from that result (R17:
+// the plain iteration reaches the same fixed point on S*) until the sup-norm
+// change is below tol.  The fine-sweep statistics are left as they were.
+Run3 coarse3(hjbp_plan &p, const Grid3 &gc, const int8_t *code, const float *h32, const double *h64,
+             const double *fixed, Sched3 &s, double tol, int cap, double *out64, const Gen3 *gen = nullptr) {
+    const int64_t Nc = (int64_t)gc.n0 * gc.n1 * gc.n2;
+    cudaStream_t st = p.stream;
+    hjbp_stats &S = p.stats;
+    const int64_t launches = S.sweep_kernel_launches, visits = S.sweep_tile_visits;
+    const double ms = S.ms_sweep_kernel;
+    const int rounds = p.desc.tune[0] > 0 ? p.desc.tune[0] : 1;
+    float *f0 = alloc3<float>(p, Nc), *f1 = alloc3<float>(p, Nc);
+    double *pa = alloc3<double>(p, Nc), *pb = alloc3<double>(p, Nc);
+    unsigned long long *cnt = alloc3<unsigned long long>(p, 1);
+    check_cuda(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st), "memset");
+    Run3 rr = value3<float>(p, gc, code, h32, f0, f1, s, std::max(tol, 1e-6), cap, rounds, nullptr, pa, cnt,
+                            nullptr, nullptr, fixed, gen);
+    S.sweep_kernel_launches = launches;
+    S.sweep_tile_visits = visits;
+    S.ms_sweep_kernel = ms;
+    k_restore_fixed3<<<grid_for3(Nc), 256, 0, st>>>(Nc, code, fixed, pa);
+    ++S.kernel_launches;
+    const CtlTable3<double> c64 = make_table3<double>(p);
+    const CtlTable3<float> c32 = make_table3<float>(p);
+    constexpr int chunk = 8;
     float *res = alloc3<float>(p, chunk);
-    std::vector<float> hres(chunk);
-    Run3 rr;
-    const int blocks = (int)std::min<int64_t>((N + 7) / 8, 152 * 16);
+    float hres[chunk];
+    // Jacobi moves information one cell per sweep; the cap covers many
+    // crossings of the grid
+    const int pcap = std::min(cap, 8 * (gc.n0 + gc.n1 + gc.n2) + 64);
+    bool done = false;
     int L = 0;
-    while (L < cap) {
-        check_cuda(cudaMemsetAsync(res, 0, sizeof(float) * chunk, st), "memset");
-        const int n = std::min(chunk, cap - L);
-        for (int l = 0; l < n; ++l) {
-            const double *in = ((L + l) & 1) ? b1 : b0;
-            double *out = ((L + l) & 1) ? b0 : b1;
-            k_value_wide3d<double><<<blocks, 256, 0, st>>>(g, code, h, in, out, res, l, dct);
-            ++p.stats.kernel_launches;
+    while (!done && L < pcap) {
+        check_cuda(cudaMemsetAsync(res, 0, sizeof(res[0]) * chunk, st), "memset");
+        for (int l = 0; l < chunk; ++l) {
+            if (gen)
+                k_polish3g<<<grid_for3(Nc, 128), 128, 0, st>>>(gc, code, (l & 1) ? pb : pa, (l & 1) ? pa : pb,
+                                                               res + l, nullptr, *gen);
+            else
+                k_polish3d<<<grid_for3(Nc, 128), 128, 0, st>>>(gc, code, h64, (l & 1) ? pb : pa, (l & 1) ? pa : pb,
+                                                               res + l, c32, c64, nullptr);
+            ++S.kernel_launches;
         }
-        check_cuda(cudaGetLastError(), "wide3");
-        check_cuda(cudaMemcpyAsync(hres.data(), res, sizeof(float) * chunk, cudaMemcpyDeviceToHost, st), "res");
-        check_cuda(cudaStreamSynchronize(st), "wide3 sync");
-        for (int l = 0; l < n; ++l) {
-            rr.launches = L + l + 1;
+        check_cuda(cudaGetLastError(), "coarse polish");
+        check_cuda(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, st), "coarse res");
+        check_cuda(cudaStreamSynchronize(st), "coarse sync");
+        for (int l = 0; l < chunk && !done; ++l) {
+            ++L;
             rr.last_res = hres[l];
-            if (hres[l] <= tol) {
-                rr.converged = true;
-                break;
+            if (hres[l] < tol) {
+                done = true;
+                // the sweeps after the converged one changed less: keep the last
             }
         }
-        L += n;
-        if (rr.converged) break;
     }
-    const double *fin = (rr.launches & 1) ? b1 : b0;
-    k_finalize<<<grid_for3(N), 256, 0, st>>>(N, fin, out64);
-    ++p.stats.kernel_launches;
+    rr.launches += L;
+    rr.converged = rr.converged && done;
+    k_finalize<<<grid_for3(Nc), 256, 0, st>>>(Nc, pa, out64);   // chunk is even: pa holds the last sweep
+    ++S.kernel_launches;
     return rr;
 }
 
@@ -1515,6 +1811,8 @@ hjbp_status solve3d(hjbp_plan &p) {
     TargetSet ts;
     std::memset(&ts, 0, sizeof(ts));
     ts.n = d.n_targets;
+    ts.kind = d.target_kind;
+    ts.nparts = p.R;
     for (int j = 0; j < ts.n; ++j) {
         ts.c0[j] = p.targets[4 * j];
         ts.c1[j] = p.targets[4 * j + 1];
@@ -1534,6 +1832,17 @@ hjbp_status solve3d(hjbp_plan &p) {
     Ctl3 hct = make_ctl3(p);
     Ctl3 *dct = static_cast<Ctl3 *>(p.dev_alloc(sizeof(Ctl3)));
     check_cuda(cudaMemcpyAsync(dct, &hct, sizeof(Ctl3), cudaMemcpyHostToDevice, st), "ctl3");
+    // Brockett's integrator (R24): feet per node from column tables
+    const bool per_node = d.dyn == HJBP_DYN_BROCKETT;
+    GenCtl *dgc = nullptr;
+    Gen3 gfine{};
+    if (per_node) {
+        const GenCtl hgc = make_genctl(p);
+        dgc = static_cast<GenCtl *>(p.dev_alloc(sizeof(GenCtl)));
+        check_cuda(cudaMemcpyAsync(dgc, &hgc, sizeof(GenCtl), cudaMemcpyHostToDevice, st), "controls");
+        gfine = make_gen3(p, g);
+    }
+    const Gen3 *gf = per_node ? &gfine : nullptr;
 
     Ev3 e0(st);
     int8_t *code0 = alloc3<int8_t>(p, N);
@@ -1543,7 +1852,8 @@ hjbp_status solve3d(hjbp_plan &p) {
     float *h32 = fp32 ? alloc3<float>(p, N) : nullptr;
     unsigned long long *updates = alloc3<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
-    k_setup3d<<<grid_for3(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr);
+    k_setup3d<<<grid_for3(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr,
+                                            make_obstacles(3, d.n_obstacles, d.obstacles));
     ++S.kernel_launches;
     check_cuda(cudaGetLastError(), "setup3");
     Sched3 sched = make_sched3(p, g, hist);
@@ -1557,21 +1867,26 @@ hjbp_status solve3d(hjbp_plan &p) {
         uint8_t *crch = alloc3<uint8_t>(p, Nc);
         double *ch64 = alloc3<double>(p, Nc);
         double *cfix = alloc3<double>(p, Nc);
-        double *cb0 = alloc3<double>(p, Nc), *cb1 = alloc3<double>(p, Nc);
-        k_setup3d<<<grid_for3(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(3.0) / 2.0, 1, ccode, nullptr, ch64,
-                                                 cfix);
+        float *ch32 = alloc3<float>(p, Nc);
+        k_setup3d<<<grid_for3(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(3.0) / 2.0, 1, ccode, ch32, ch64,
+                                                 cfix, make_obstacles(3, d.n_obstacles, d.obstacles), dgc);
         k_merge_targets<<<grid_for3(Nc), 256, 0, st>>>(Nc, ccode);
         S.kernel_launches += 2;
+        Gen3 gcoarse{};
+        if (per_node) gcoarse = make_gen3(p, gc);
+        const Gen3 *gcp = per_node ? &gcoarse : nullptr;
         Sched3 csched = make_sched3(p, gc, hist);
-        S.sweeps_reach += reach3(p, gc, ccode, crch, csched, Nc);
+        S.sweeps_reach += reach3(p, gc, ccode, crch, csched, Nc, nullptr, gcp);
         const double tolc = d.tol_coarse > 0 ? d.tol_coarse : 1e-12;
-        Run3 rc = wide3(p, gc, ccode, ch64, cfix, cb0, cb1, tolc, cap, dct, p.u_coarse);
+        Run3 rc = coarse3(p, gc, ccode, ch32, ch64, cfix, csched, tolc, cap, p.u_coarse, gcp);
         S.sweeps_coarse = rc.launches;
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev3 e2(st);
         if (d.flags & HJBP_FLAG_DIRICHLET) dlit = alloc3<double>(p, N);
         k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0, dlit);
-        {
+        if (per_node) {
+            k_feedback3g<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, p.u0, p.astar, gfine);
+        } else {
             const CtlLit3 hl = make_lit3(p);
             CtlLit3 *dl = static_cast<CtlLit3 *>(p.dev_alloc(sizeof(CtlLit3)));
             check_cuda(cudaMemcpyAsync(dl, &hl, sizeof(CtlLit3), cudaMemcpyHostToDevice, st), "feedback table");
@@ -1594,8 +1909,12 @@ hjbp_status solve3d(hjbp_plan &p) {
                     k_phi_init3d<G><<<grid_for3(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++S.kernel_launches;
                     Run3 rp = run_tiles3(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par) {
-                        k_phi3d<G, false><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d,
-                                                                         par, prounds, dct);
+                        if (per_node)
+                            k_phi3d<G, false, true><<<sched.ntiles, kT3n, 0, st>>>(
+                                g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dct, gfine);
+                        else
+                            k_phi3d<G, false><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, nullptr,
+                                                                             sched.d, par, prounds, dct);
                         ++S.kernel_launches;
                     });
                     S.sweeps_phi += rp.launches;
@@ -1604,7 +1923,12 @@ hjbp_status solve3d(hjbp_plan &p) {
                     ++S.kernel_launches;
                     for (int it = 0; it < 6; ++it) {
                         check_cuda(cudaMemsetAsync(rmax, 0, sizeof(float), st), "memset");
-                        k_phi_residual3d<G><<<grid_for3(N), 256, 0, st>>>(g, code0, p.astar, phig, r32, rmax, dct);
+                        if (per_node)
+                            k_phi_residual3d<G, true><<<grid_for3(N), 256, 0, st>>>(g, code0, p.astar, phig, r32,
+                                                                                     rmax, dct, gfine);
+                        else
+                            k_phi_residual3d<G><<<grid_for3(N), 256, 0, st>>>(g, code0, p.astar, phig, r32, rmax,
+                                                                              dct);
                         ++S.kernel_launches;
                         float hr = 0.f;
                         check_cuda(cudaMemcpyAsync(&hr, rmax, sizeof(float), cudaMemcpyDeviceToHost, st), "rmax");
@@ -1615,8 +1939,12 @@ hjbp_status solve3d(hjbp_plan &p) {
                         ++S.kernel_launches;
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         Run3 rc2 = run_tiles3(p, g, sched, told, cap, [&](int par) {
-                            k_phi3d<G, true><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, r32, sched.d,
-                                                                            par, prounds, dct);
+                            if (per_node)
+                                k_phi3d<G, true, true><<<sched.ntiles, kT3n, 0, st>>>(
+                                    g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dct, gfine);
+                            else
+                                k_phi3d<G, true><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, r32,
+                                                                                sched.d, par, prounds, dct);
                             ++S.kernel_launches;
                         });
                         S.sweeps_phi += rc2.launches;
@@ -1685,7 +2013,7 @@ hjbp_status solve3d(hjbp_plan &p) {
     const bool dirichlet = p.patchy && (d.flags & HJBP_FLAG_DIRICHLET);
     const double *warm = (p.patchy && (d.flags & HJBP_FLAG_WARM_START)) ? p.u0 : nullptr;
     const double *d64 = dirichlet ? dlit : nullptr;
-    S.sweeps_reach += reach3(p, g, code, rch, sched, N, d64);
+    S.sweeps_reach += reach3(p, g, code, rch, sched, N, d64, gf);
     Ev3 fr(st);
     Run3 rv;
     if (fp32) {
@@ -1696,11 +2024,12 @@ hjbp_status solve3d(hjbp_plan &p) {
             k_narrow_data3<<<grid_for3(N), 256, 0, st>>>(N, dlit, d32);
             ++S.kernel_launches;
         }
-        rv = value3<float>(p, g, code, h32, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, d32, warm);
+        rv = value3<float>(p, g, code, h32, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, d32, warm,
+                           nullptr, gf);
     } else {
         double *b0 = alloc3<double>(p, N), *b1 = alloc3<double>(p, N);
         rv = value3<double>(p, g, code, h64, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates, d64,
-                            warm);
+                            warm, nullptr, gf);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
@@ -1726,7 +2055,10 @@ hjbp_status solve3d(hjbp_plan &p) {
         int it = 0;
         for (; it < 8; ++it) {
             check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
-            k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64, d64);
+            if (per_node)
+                k_polish3g<<<grid_for3(N, 128), 128, 0, st>>>(g, code, pa, pb, mc, d64, gfine);
+            else
+                k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64, d64);
             ++S.kernel_launches;
             check_cuda(cudaGetLastError(), "polish3");
             std::swap(pa, pb);
@@ -1755,7 +2087,11 @@ hjbp_status solve3d(hjbp_plan &p) {
     check_cuda(cudaStreamSynchronize(st), "final sync");
     S.unreachable = (int64_t)hun;
     S.node_updates = (int64_t)hu;
-    S.node_control_updates = (int64_t)hu * d.n_controls;
+    int admissible = d.n_controls;   // Brockett's a = 0 cannot move and is never evaluated
+    if (per_node)
+        for (int m = 0; m < d.n_controls; ++m)
+            if (p.controls[3 * m] == 0.0 && p.controls[3 * m + 1] == 0.0) --admissible;
+    S.node_control_updates = (int64_t)hu * admissible;
     S.n_patches = p.patchy ? R : 1;
     S.ms_setup = ms3(e0, e1);
     S.ms_fine = ms3(f0, f1);

@@ -30,7 +30,7 @@ namespace hjbp {
 
 // Kernels defined in kernels2d.cu (the same ones hjbp_solve launches).
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values, int8_t *code,
-                          float *h32, double *h64, double *fixed, DynParams dp);
+                          float *h32, double *h64, double *fixed, DynParams dp, ObstacleSet os);
 __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
                                                 ReachTable2 rt, int passes, const double *dterm,
@@ -145,6 +145,7 @@ const char *check_desc(const hjbp_problem_desc *d) {
     for (int j = 0; j < 3 * d->n_targets; ++j)
         if (!std::isfinite(d->targets[j])) return "target entry not finite";
     if (!(d->tol > 0.0)) return "tol must be positive";
+    if (const char *e = check_obstacles(d)) return e;
     if (d->dyn != HJBP_DYN_SPEED || d->target_kind != HJBP_TARGET_BALLS)
         return "the no-allocation entry point takes f = c(x) a and ball targets";
     if (d->speed == HJBP_C_FOURIER2D) {
@@ -290,7 +291,8 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     // Set-up: node codes and h, all target parts merged (one global target).
     DynParams dp;
     std::memset(&dp, 0, sizeof(dp));   // f = c(x) a
-    k_setup2d<<<blocks_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, nullptr, h64, nullptr, dp);
+    k_setup2d<<<blocks_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, nullptr, h64, nullptr, dp,
+                                             make_obstacles(2, desc->n_obstacles, desc->obstacles));
     NA_CHECK(cudaGetLastError());
     NA_CHECK(cudaMemcpyAsync(code, code0, (size_t)N, cudaMemcpyDeviceToDevice, st));
     k_merge_targets<<<blocks_for(N), 256, 0, st>>>(N, code);

@@ -14,6 +14,7 @@ struct hjbp_plan {
     hjbp_problem_desc desc;
     std::vector<double> controls;   // n_controls x dim
     std::vector<double> targets;    // n_targets x (dim + 1)
+    std::vector<double> obstacles;  // n_obstacles x 7
     int R = 0;                      // patches (target parts)
     std::vector<double> dirs;       // per control: unit direction of f (dim each)
     std::vector<double> hfac;       // per control: h_{i,a} = hfac[a] h_i
