@@ -1200,6 +1200,108 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     }
 }
 
+// Peel for S* (R14): a free node none of whose controls (its cone under
+// AO3) has all its positive-weight corners in the patch or terminal cannot
+// be in S*; it is pruned (code -2 - patch).  Gauss-Seidel passes inside the
+// tile, the schedule carries removals across tiles; codes only move from free
+// to pruned, so a stale halo value only delays a removal.
+__global__ void __launch_bounds__(32) k_peel2d(Grid2 g, int8_t *__restrict__ code, TileSched s, int par,
+                                               ReachTable2 rt, const double *__restrict__ dterm,
+                                               const uint8_t *__restrict__ astar, const Cone2 *__restrict__ cone) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
+    __shared__ int8_t sc[kTile + 2][kTile + 4];
+    __shared__ uint8_t sd[kTile + 2][kTile + 4];
+    __shared__ uint32_t pws[kTile][kTile + 1];   // per node: its patterns per quadrant
+    const int lane = threadIdx.x;
+    for (int r = 0; r < kTile + 2; ++r) {
+        const int y = y0 - 1 + r;
+        for (int c = lane; c < kTile + 2; c += 32) {
+            const int x = x0 - 1 + c;
+            uint8_t df = 0;
+            int8_t cd = kHard;
+            if (x < g.n0 && y < g.n1) {
+                const int64_t i = (int64_t)y * g.n0 + x;
+                cd = code[i];
+                if (dterm) df = dterm[i] < kU0Bound;
+            }
+            sc[r][c] = cd;
+            sd[r][c] = df;
+        }
+    }
+    {
+        const uint32_t all = (uint32_t)rt.present[0] | ((uint32_t)rt.present[1] << 8) |
+                             ((uint32_t)rt.present[2] << 16) | ((uint32_t)rt.present[3] << 24);
+        for (int r = 1; r <= kTile; ++r) {
+            const int8_t cd = sc[r][1 + lane];
+            uint32_t pw = all;
+            if (cone) {
+                const int x = x0 + lane, y = y0 - 1 + r;
+                const int a = (cd >= 0 && cd < kTargetBase && x < g.n0 && y < g.n1) ? astar[(int64_t)y * g.n0 + x]
+                                                                                     : kNoControl;
+                pw = cone->reach[a < cone->nc ? a : cone->nc];
+            }
+            pws[r - 1][lane] = pw;
+        }
+    }
+    __syncwarp();
+    int flips = 0;
+    for (int dir = 0; dir < 4; ++dir)
+        for (int st = 0; st < kTile; ++st) {
+            const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+            const int c = (dir < 2) ? s1 : 1 + lane;
+            const int r = (dir < 2) ? 1 + lane : s1;
+            const int8_t cd = sc[r][c];
+            bool kill = false;
+            if (cd >= 0 && cd < kTargetBase && x0 + c - 1 <= g.n0 - 2 && y0 + r - 1 <= g.n1 - 2) {
+                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+                uint32_t usable = 0;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int8_t q = sc[r - 1 + dy][c - 1 + dx];
+                        const bool u = q == cd || q == tg || (q != cd && q != pr && sd[r - 1 + dy][c - 1 + dx]);
+                        usable |= (uint32_t)u << (3 * dy + dx);
+                    }
+                const uint32_t pw = pws[r - 1][c - 1];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
+                    const int b10 = 3 * 1 + (1 + sx), b01 = 3 * (1 + sy) + 1, b11 = 3 * (1 + sy) + (1 + sx);
+                    const unsigned us =
+                        ((usable >> b10) & 1u) | (((usable >> b01) & 1u) << 1) | (((usable >> b11) & 1u) << 2);
+                    const unsigned pres = (pw >> (8 * q)) & 0xffu;
+#pragma unroll
+                    for (unsigned k = 1; k < 8; ++k)
+                        if (((pres >> k) & 1u) && (k & ~us) == 0) any = true;
+                }
+                kill = !any;
+            }
+            __syncwarp();
+            if (kill) {
+                sc[r][c] = (int8_t)(-2 - cd);
+                ++flips;
+            }
+            __syncwarp();
+        }
+    const int x = x0 + lane;
+    for (int r = 1; r <= kTile; ++r) {
+        const int y = y0 - 1 + r;
+        if (y > g.n1 - 2) break;
+        if (x > g.n0 - 2) continue;
+        code[(int64_t)y * g.n0 + x] = sc[r][1 + lane];
+    }
+    const int nf = warp_sum(flips);
+    if (lane == 0) {
+        (par ? s.chg[1] : s.chg[0])[t] = nf > 0 ? 1.f : 0.f;
+        s.processed[t] = 1;
+    }
+}
+
 // Free nodes not reached leave the candidate set: their code becomes
 // -2 - patch (not free, value +inf, still known to belong to the patch, which
 // the Dirichlet boundary needs); counts them.
@@ -2300,6 +2402,13 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
     // most N rounds
     for (int64_t round = 0;; ++round) {
         if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
+        // peel the nodes left without any control first (they cannot be in S*)
+        RunResult pe = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
+            k_peel2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, s.d, par, rt, dterm, p.astar, cone);
+            ++p.stats.kernel_launches;
+        });
+        total += pe.launches;
+        if (!pe.converged) throw HjbpError{HJBP_ECUDA, "peeling did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         RunResult rr = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
             k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt, passes, dterm, p.astar, cone);

@@ -589,6 +589,43 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
 
 // dterm (optional): Dirichlet data (Eq. dbc); a node outside the patch with
 // finite data is a terminal, like the patch's own target part.
+// Union, over the controls whose positive-weight corners other than the node
+// all lie in `usable` (27-bit over the 3x3x3 neighbourhood), of those
+// corners; 0 when the node has no such control.  (lx, ly, lz): local
+// coordinates 1..8 of a node of the tile whose first interior node is
+// (x0, y0, .).
+template <bool kGen>
+__device__ __forceinline__ uint32_t usable_union3(uint32_t usable, int lx, int ly, int lz, int x0, int y0,
+                                                  const Grid3 &g, const ReachTable3 &rt, const Gen3 &gen) {
+    uint32_t c = 0;
+    if constexpr (kGen) {
+        const int64_t e0 = ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc;
+        for (int m = 0; m < gen.nc; ++m) {
+            const uint32_t need = __ldg(&gen.cset[e0 + m]);
+            if (need && (need & ~usable) == 0) c |= need;
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
+            unsigned us = 0;
+#pragma unroll
+            for (int b = 1; b < 8; ++b) {
+                const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
+                us |= ((usable >> bit) & 1u) << (b - 1);
+            }
+            const unsigned u = rt.uni[o][us];
+#pragma unroll
+            for (int b = 1; b < 8; ++b) {
+                const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
+                c |= ((u >> (b - 1)) & 1u) << bit;
+            }
+        }
+    }
+    (void)lz;
+    return c;
+}
+
 // kGen: the corner sets of the per-node feet from the column tables.
 template <bool kGen>
 __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restrict__ code,
@@ -646,32 +683,7 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
                         term |= (uint32_t)(q == tg || (q != cd && q != pr && sdf[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]))
                                 << bit;
                     }
-            const uint32_t usable = same | term;
-            uint32_t c = 0;
-            if constexpr (kGen) {
-                const int64_t e0 = ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc;
-                for (int m = 0; m < gen.nc; ++m) {
-                    const uint32_t need = __ldg(&gen.cset[e0 + m]);
-                    if (need && (need & ~usable) == 0) c |= need;
-                }
-            } else {
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
-                unsigned us = 0;
-#pragma unroll
-                for (int b = 1; b < 8; ++b) {
-                    const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
-                    us |= ((usable >> bit) & 1u) << (b - 1);
-                }
-                const unsigned u = rt.uni[o][us];
-#pragma unroll
-                for (int b = 1; b < 8; ++b) {
-                    const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
-                    c |= ((u >> (b - 1)) & 1u) << bit;
-                }
-            }
-            }
+            const uint32_t c = usable_union3<kGen>(same | term, lx, ly, lz, x0, y0, g, rt, gen);
             h0 = (c & term) != 0;
             cs = c & same;
             if (!h0 && !cs) cs = 0;
@@ -711,6 +723,84 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
         rch[((int64_t)z * g.n1 + y) * g.n0 + x] = sr[lz + 1][ly + 1][lx + 1];
+    }
+    if (flips) atomicAdd(&flips_s, flips);
+    __syncthreads();
+    if (tid == 0) {
+        (par ? s.chg[1] : s.chg[0])[t] = flips_s > 0 ? 1.f : 0.f;
+        s.processed[t] = 1;
+    }
+}
+
+// Peel for S* (R14): a free node none of whose controls has all its
+// positive-weight corners in the patch or terminal cannot be in S*; it is
+// pruned (code -2 - patch), which may leave a neighbour without a control in
+// turn, so the tile repeats Gauss-Seidel passes and the schedule carries the
+// removals across tiles.  Codes only move from free to pruned, so a stale
+// halo value only delays a removal.  dterm: Dirichlet data, as in k_reach3d.
+template <bool kGen>
+__global__ void __launch_bounds__(kT3n) k_peel3d(Grid3 g, int8_t *__restrict__ code, TileSched s, int par,
+                                                 ReachTable3 rt, const double *__restrict__ dterm, const Gen3 gen) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
+    if ((int)blockIdx.x >= s.count[par]) return;
+    const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
+    const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
+    constexpr int E = kT3 + 2;
+    __shared__ int8_t sc[E][E][E + 2];
+    __shared__ uint8_t sdf[E][E][E + 2];
+    __shared__ int flips_s;
+    const int tid = threadIdx.x;
+    if (tid == 0) flips_s = 0;
+    for (int e = tid; e < E * E * E; e += blockDim.x) {
+        const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        uint8_t df = 0;
+        int8_t cd = kHard;
+        if (x < g.n0 && y < g.n1 && z < g.n2) {
+            const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+            cd = code[i];
+            if (dterm) df = dterm[i] < kU0Bound;
+        }
+        sc[lz][ly][lx] = cd;
+        sdf[lz][ly][lx] = df;
+    }
+    __syncthreads();
+    int flips = 0;
+    for (int dir = 0; dir < 6; ++dir)
+        for (int st = 0; st < kT3; ++st) {
+            int lx, ly, lz;
+            plane_node(dir, st, tid, lx, ly, lz);
+            const int8_t cd = sc[lz][ly][lx];
+            bool kill = false;
+            if (cd >= 0 && cd < kTargetBase && x0 + lx - 1 <= g.n0 - 2 && y0 + ly - 1 <= g.n1 - 2 &&
+                z0 + lz - 1 <= g.n2 - 2) {
+                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+                uint32_t usable = 0;
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const int8_t q = sc[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx];
+                            const bool u = q == cd || q == tg ||
+                                           (q != pr && q != cd && sdf[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]);
+                            usable |= (uint32_t)u << (9 * dz + 3 * dy + dx);
+                        }
+                kill = usable_union3<kGen>(usable, lx, ly, lz, x0, y0, g, rt, gen) == 0;
+            }
+            __syncthreads();
+            if (kill) {
+                sc[lz][ly][lx] = (int8_t)(-2 - cd);
+                ++flips;
+            }
+            __syncthreads();
+        }
+    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        code[((int64_t)z * g.n1 + y) * g.n0 + x] = sc[lz + 1][ly + 1][lx + 1];
     }
     if (flips) atomicAdd(&flips_s, flips);
     __syncthreads();
@@ -1621,6 +1711,14 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
     // most N rounds
     for (int64_t round = 0;; ++round) {
         if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
+        // peel the nodes left without any control first (they cannot be in S*)
+        Run3 pe = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
+            if (gen) k_peel3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, s.d, par, rt, dterm, *gen);
+            else k_peel3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, s.d, par, rt, dterm, Gen3{});
+            ++p.stats.kernel_launches;
+        });
+        total += pe.launches;
+        if (!pe.converged) throw HjbpError{HJBP_ECUDA, "peeling did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
             if (gen) k_reach3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, *gen);
