@@ -147,7 +147,8 @@ typedef struct {
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse
                            feedback of Step 2, Eq. feedbackcontrol); nodes without a
                            feedback keep every control.  0 keeps every control.  On the
-                           2D path the control set must have at most 64 members.      */
+                           2D path the control set must have at most 64 members; not
+                           with HJBP_DYN_BROCKETT.                                     */
     int dyn;            /* hjbp_dyn_kind */
     double drift[4];    /* HJBP_DYN_DRIFT: s, w_1, w_2, w_3 */
     int target_kind;    /* hjbp_target_kind */

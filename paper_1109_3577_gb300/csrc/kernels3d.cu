@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <type_traits>
 #include <vector>
 
@@ -87,6 +88,16 @@ struct CtlLit3 {
 struct ReachTable3 {
     uint32_t present[8][4];
     uint8_t uni[8][128];
+};
+
+// Add-on AO3 (Sec. 6, R19) in 3D: per coarse feedback a* (row nc: no
+// feedback, every control) the controls a with a . a* >= cos(pi / r) - 1e-12
+// as bits over the octant-sorted table positions, and the union tables of
+// their corner patterns per octant (as ReachTable3.uni).
+struct Cone3 {
+    int nc;
+    uint64_t mask[kMaxControls + 1][4];
+    uint8_t uni[kMaxControls + 1][8][128];
 };
 
 // Controls (a1, a2) of Brockett's integrator (R24).
@@ -311,9 +322,9 @@ template <typename T> __device__ __forceinline__ void load_w3(const W3<T> &w, T 
 // neighbour (dx-1, dy-1, dz-1) belongs to the node's patch or target part
 // (formed once per launch), everything else reads +inf.  tab: the weights in
 // shared memory, in the octant order of ct.
-template <typename T, bool kDir>
+template <typename T, bool kDir, bool kCone = false>
 __device__ __forceinline__ T sl_update3(const Tile3<T, kDir> &sm, int lx, int ly, int lz, uint32_t mask, T hh,
-                                        const CtlTable3<T> &ct, const W3<T> *tab) {
+                                        const CtlTable3<T> &ct, const W3<T> *tab, const uint64_t *cm = nullptr) {
     T nb[3][3][3];
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
@@ -336,6 +347,19 @@ __device__ __forceinline__ T sl_update3(const Tile3<T, kDir> &sm, int lx, int ly
         for (int b = 1; b < 8; ++b) c[b - 1] = nb[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
         int m = ct.obeg[o];
         const int me = ct.obeg[o + 1];
+        if constexpr (kCone) {
+            // the node's cone (AO3): only the controls whose bit is set
+            for (; m < me; ++m) {
+                if (!((cm[m >> 6] >> (m & 63)) & 1ull)) continue;
+                T w0[8];
+                load_w3(tab[m], w0);
+                T v0 = w0[7] * hh;
+#pragma unroll
+                for (int b = 0; b < 7; ++b) v0 = fma(w0[b], c[b], v0);
+                b0 = v0 < b0 ? v0 : b0;
+            }
+            continue;
+        }
         for (; m + 1 < me; m += 2) {
             T w0[8], w1[8];
             load_w3(tab[m], w0);
@@ -507,12 +531,15 @@ __device__ __forceinline__ T sl_update3g(const Tile3<T, kDir> &sm, int lx, int l
 // warm start (AO1).  kDir: neighbours outside the patch read the Dirichlet
 // data dval (Eq. dbc); a node's own pruned nodes (code -2 - patch) read +inf.
 // kGen: per-node feet from the column tables of gen (h is then unused).
-template <typename T, bool kDir = false, bool kGen = false>
+// kCone: add-on AO3, the minimum over the node's cone (cone, astar).
+template <typename T, bool kDir = false, bool kGen = false, bool kCone = false>
 __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restrict__ code,
                                                   const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                   TileSched s, int par, int rounds, unsigned long long *updates,
                                                   const CtlTable3<T> ct, int clamp = 1,
-                                                  const T *__restrict__ dval = nullptr, const Gen3 gen = Gen3{}) {
+                                                  const T *__restrict__ dval = nullptr, const Gen3 gen = Gen3{},
+                                                  const Cone3 *__restrict__ cone = nullptr,
+                                                  const uint8_t *__restrict__ astar = nullptr) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -521,6 +548,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     // per interior node: neighbour mask (bit 31: the node is free) and h
     __shared__ uint32_t mk[kT3][kT3][kT3];
     __shared__ T hs[kT3][kT3][kT3];
+    __shared__ uint8_t as[kCone ? kT3 : 1][kCone ? kT3 : 1][kCone ? kT3 : 1];   // a* per node (AO3)
     __shared__ W3<T> tab[kGen ? 1 : kMaxControls];
     if constexpr (!kGen)
         for (int m = threadIdx.x; m < ct.nc; m += blockDim.x) {
@@ -550,6 +578,11 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
             ++nfree;
             if constexpr (!kGen) hv = h[((int64_t)(z0 + lz) * g.n1 + (y0 + ly)) * g.n0 + (x0 + lx)];
         }
+        if constexpr (kCone) {
+            uint8_t a = kNoControl;
+            if (m) a = astar[((int64_t)(z0 + lz) * g.n1 + (y0 + ly)) * g.n0 + (x0 + lx)];
+            as[lz][ly][lx] = a < cone->nc ? a : (uint8_t)cone->nc;
+        }
         mk[lz][ly][lx] = m;
         hs[lz][ly][lx] = hv;
     }
@@ -567,6 +600,9 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                     if constexpr (kGen)
                         best = sl_update3g<T, kDir>(sm, lx, ly, lz, m,
                                                     ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc, gen);
+                    else if constexpr (kCone)
+                        best = sl_update3<T, kDir, true>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab,
+                                                         cone->mask[as[lz - 1][ly - 1][lx - 1]]);
                     else
                         best = sl_update3<T, kDir>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
                     if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
@@ -596,7 +632,8 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
 // (x0, y0, .).
 template <bool kGen>
 __device__ __forceinline__ uint32_t usable_union3(uint32_t usable, int lx, int ly, int lz, int x0, int y0,
-                                                  const Grid3 &g, const ReachTable3 &rt, const Gen3 &gen) {
+                                                  const Grid3 &g, const ReachTable3 &rt, const Gen3 &gen,
+                                                  const uint8_t *cu = nullptr) {
     uint32_t c = 0;
     if constexpr (kGen) {
         const int64_t e0 = ((int64_t)(y0 + ly - 1) * g.n0 + (x0 + lx - 1)) * gen.nc;
@@ -614,7 +651,7 @@ __device__ __forceinline__ uint32_t usable_union3(uint32_t usable, int lx, int l
                 const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
                 us |= ((usable >> bit) & 1u) << (b - 1);
             }
-            const unsigned u = rt.uni[o][us];
+            const unsigned u = cu ? cu[o * 128 + us] : rt.uni[o][us];
 #pragma unroll
             for (int b = 1; b < 8; ++b) {
                 const int bit = 9 * ((b & 4) ? oz : 1) + 3 * ((b & 2) ? oy : 1) + ((b & 1) ? ox : 1);
@@ -630,7 +667,8 @@ __device__ __forceinline__ uint32_t usable_union3(uint32_t usable, int lx, int l
 template <bool kGen>
 __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restrict__ code,
                                                   uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt,
-                                                  const double *__restrict__ dterm, const Gen3 gen) {
+                                                  const double *__restrict__ dterm, const Gen3 gen,
+                                                  const Cone3 *__restrict__ cone, const uint8_t *__restrict__ astar) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -683,7 +721,12 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
                         term |= (uint32_t)(q == tg || (q != cd && q != pr && sdf[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]))
                                 << bit;
                     }
-            const uint32_t c = usable_union3<kGen>(same | term, lx, ly, lz, x0, y0, g, rt, gen);
+            const uint8_t *cu = nullptr;
+            if (cone) {
+                const uint8_t a = astar[((int64_t)(z0 + lz - 1) * g.n1 + (y0 + ly - 1)) * g.n0 + (x0 + lx - 1)];
+                cu = &cone->uni[a < cone->nc ? a : cone->nc][0][0];
+            }
+            const uint32_t c = usable_union3<kGen>(same | term, lx, ly, lz, x0, y0, g, rt, gen, cu);
             h0 = (c & term) != 0;
             cs = c & same;
             if (!h0 && !cs) cs = 0;
@@ -740,7 +783,8 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
 // halo value only delays a removal.  dterm: Dirichlet data, as in k_reach3d.
 template <bool kGen>
 __global__ void __launch_bounds__(kT3n) k_peel3d(Grid3 g, int8_t *__restrict__ code, TileSched s, int par,
-                                                 ReachTable3 rt, const double *__restrict__ dterm, const Gen3 gen) {
+                                                 ReachTable3 rt, const double *__restrict__ dterm, const Gen3 gen,
+                                                 const Cone3 *__restrict__ cone, const uint8_t *__restrict__ astar) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -787,7 +831,12 @@ __global__ void __launch_bounds__(kT3n) k_peel3d(Grid3 g, int8_t *__restrict__ c
                                            (q != pr && q != cd && sdf[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]);
                             usable |= (uint32_t)u << (9 * dz + 3 * dy + dx);
                         }
-                kill = usable_union3<kGen>(usable, lx, ly, lz, x0, y0, g, rt, gen) == 0;
+                const uint8_t *cu = nullptr;
+                if (cone) {
+                    const uint8_t a = astar[((int64_t)(z0 + lz - 1) * g.n1 + (y0 + ly - 1)) * g.n0 + (x0 + lx - 1)];
+                    cu = &cone->uni[a < cone->nc ? a : cone->nc][0][0];
+                }
+                kill = usable_union3<kGen>(usable, lx, ly, lz, x0, y0, g, rt, gen, cu) == 0;
             }
             __syncthreads();
             if (kill) {
@@ -1350,10 +1399,12 @@ __global__ void __launch_bounds__(kT3n) k_compact3d(Grid3 g, const int8_t *__res
 
 // FP64 polish with the FP32 filter (see k_polish2d): margin 2^-17 (h + max|a|)
 // covers the eight-term trilinear sum.
+// cone (AO3): the minimum over the node's cone of astar.
 __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
                            const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
                            const CtlTable3<float> c32, const CtlTable3<double> c64,
-                           const double *__restrict__ dval) {
+                           const double *__restrict__ dval, const Cone3 *__restrict__ cone = nullptr,
+                           const uint8_t *__restrict__ astar = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     // the weights in shared memory (k[0..6] = kap w_b, k[7] = kap), 16-byte vectors
     __shared__ W3<float> t32[kMaxControls];
@@ -1400,6 +1451,11 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                     }
             const double hh = h[i];
             const float hf = (float)hh;
+            const uint64_t *cm = nullptr;
+            if (cone) {
+                const uint8_t a = astar[i];
+                cm = cone->mask[a < cone->nc ? a : cone->nc];
+            }
             float b32 = Num<float>::big();
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
@@ -1408,6 +1464,7 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
 #pragma unroll
                 for (int b = 1; b < 8; ++b) c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
                 for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
+                    if (cm && !((cm[m >> 6] >> (m & 63)) & 1ull)) continue;
                     float t[8];
                     load_w3(t32[m], t);
                     float w = t[7] * hf;
@@ -1426,6 +1483,7 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
 #pragma unroll
                     for (int b = 1; b < 8; ++b) c[b - 1] = nf[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
                     for (int m = c32.obeg[o]; m < c32.obeg[o + 1]; ++m) {
+                        if (cm && !((cm[m >> 6] >> (m & 63)) & 1ull)) continue;
                         float t[8];
                         load_w3(t32[m], t);
                         float w = t[7] * hf;
@@ -1671,6 +1729,59 @@ ReachTable3 make_reach3(const hjbp_plan &p) {
     return rt;
 }
 
+// The cones of AO3 (R19) over the octant-sorted control table; returns the
+// mean cone size.
+double make_cones3(const hjbp_plan &p, Cone3 &cn) {
+    std::memset(&cn, 0, sizeof(cn));
+    const int nc = p.desc.n_controls;
+    cn.nc = nc;
+    std::vector<int> pos(nc);
+    std::vector<int> oct(nc);
+    std::vector<unsigned> need(nc);
+    int at = 0;
+    for (int o = 0; o < 8; ++o)
+        for (int m = 0; m < nc; ++m) {
+            const double *a = &p.controls[3 * m];
+            if ((a[0] >= 0.0 ? 1 : 0) + (a[1] >= 0.0 ? 2 : 0) + (a[2] >= 0.0 ? 4 : 0) != o) continue;
+            pos[m] = at++;
+            oct[m] = o;
+            const double b[3] = {std::fabs(a[0]), std::fabs(a[1]), std::fabs(a[2])};
+            unsigned nd = 0;
+            for (int c = 1; c < 8; ++c) {
+                double w = 1.0;
+                for (int d = 0; d < 3; ++d) w *= (c >> d & 1) ? b[d] : 1.0 - b[d];
+                if (w > 0.0) nd |= 1u << (c - 1);
+            }
+            need[m] = nd;
+        }
+    const double cr = std::cos(3.14159265358979323846 / p.desc.reduce_r) - 1e-12;
+    double total = 0.0;
+    for (int a = 0; a <= nc; ++a) {
+        uint32_t present[8][4];
+        std::memset(present, 0, sizeof(present));
+        int cnt = 0;
+        for (int m = 0; m < nc; ++m) {
+            if (a < nc) {
+                double dot = 0.0;
+                for (int d = 0; d < 3; ++d) dot += p.controls[3 * m + d] * p.controls[3 * a + d];
+                if (!(dot >= cr)) continue;
+            }
+            cn.mask[a][pos[m] >> 6] |= 1ull << (pos[m] & 63);
+            ++cnt;
+            if (need[m]) present[oct[m]][need[m] >> 5] |= 1u << (need[m] & 31);
+        }
+        for (int o = 0; o < 8; ++o)
+            for (unsigned us = 0; us < 128; ++us) {
+                unsigned u = 0;
+                for (unsigned k = 1; k < 128; ++k)
+                    if (((present[o][k >> 5] >> (k & 31)) & 1u) && (k & ~us) == 0) u |= k;
+                cn.uni[a][o][us] = (uint8_t)u;
+            }
+        if (a < nc) total += cnt;
+    }
+    return total / nc;
+}
+
 Grid3 make_grid3(const int n[3], const double lo[3], double k) {
     Grid3 g;
     g.n0 = n[0];
@@ -1703,7 +1814,7 @@ float ms3(const Ev3 &a, const Ev3 &b) {
 }
 
 int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, int64_t N,
-           const double *dterm = nullptr, const Gen3 *gen = nullptr) {
+           const double *dterm = nullptr, const Gen3 *gen = nullptr, const Cone3 *cone = nullptr) {
     const ReachTable3 rt = make_reach3(p);
     unsigned long long *removed = alloc3<unsigned long long>(p, 1);
     int total = 0;
@@ -1713,16 +1824,19 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
         if (round > N) throw HjbpError{HJBP_ECUDA, "reachability pruning did not settle"};
         // peel the nodes left without any control first (they cannot be in S*)
         Run3 pe = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
-            if (gen) k_peel3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, s.d, par, rt, dterm, *gen);
-            else k_peel3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, s.d, par, rt, dterm, Gen3{});
+            if (gen) k_peel3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, s.d, par, rt, dterm, *gen, cone, p.astar);
+            else k_peel3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, s.d, par, rt, dterm, Gen3{}, cone, p.astar);
             ++p.stats.kernel_launches;
         });
         total += pe.launches;
         if (!pe.converged) throw HjbpError{HJBP_ECUDA, "peeling did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
         Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
-            if (gen) k_reach3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, *gen);
-            else k_reach3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, Gen3{});
+            if (gen)
+                k_reach3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, *gen, cone, p.astar);
+            else
+                k_reach3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, Gen3{}, cone,
+                                                                  p.astar);
             ++p.stats.kernel_launches;
         });
         total += rr.launches;
@@ -1743,7 +1857,8 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
 template <typename T>
 Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0, T *b1, Sched3 &s, double tol,
             int cap, int rounds, T *out_t, double *out64, unsigned long long *updates, const T *dval = nullptr,
-            const double *warm = nullptr, const double *fixed = nullptr, const Gen3 *gen = nullptr) {
+            const double *warm = nullptr, const double *fixed = nullptr, const Gen3 *gen = nullptr,
+            const Cone3 *cone = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     k_init3d<T><<<grid_for3(N), 256, 0, p.stream>>>(N, code, fixed, (T)kStartValue, b0, b1, warm);
     const int clamp = warm ? 0 : 1;
@@ -1758,7 +1873,13 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
             check_cuda(cudaEventCreate(&b), "event");
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
-        if (gen && dval)
+        if (cone && dval)
+            k_value3d<T, true, false, true><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval, Gen3{}, cone, p.astar);
+        else if (cone)
+            k_value3d<T, false, false, true><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, nullptr, Gen3{}, cone, p.astar);
+        else if (gen && dval)
             k_value3d<T, true, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
                                                                        ct, clamp, dval, *gen);
         else if (gen)
@@ -2111,7 +2232,17 @@ hjbp_status solve3d(hjbp_plan &p) {
     const bool dirichlet = p.patchy && (d.flags & HJBP_FLAG_DIRICHLET);
     const double *warm = (p.patchy && (d.flags & HJBP_FLAG_WARM_START)) ? p.u0 : nullptr;
     const double *d64 = dirichlet ? dlit : nullptr;
-    S.sweeps_reach += reach3(p, g, code, rch, sched, N, d64, gf);
+    // AO3: the cones of the coarse feedback (Step 3.2 only; labels keep every control)
+    Cone3 *cone = nullptr;
+    double cone_size = 0.0;   // mean controls per node under AO3 (0: every control)
+    if (p.patchy && d.reduce_r != 0.0) {
+        std::unique_ptr<Cone3> hc(new Cone3);
+        cone_size = make_cones3(p, *hc);
+        cone = static_cast<Cone3 *>(p.dev_alloc(sizeof(Cone3)));
+        check_cuda(cudaMemcpyAsync(cone, hc.get(), sizeof(Cone3), cudaMemcpyHostToDevice, st), "cones");
+        check_cuda(cudaStreamSynchronize(st), "cones sync");   // the host copy is freed next
+    }
+    S.sweeps_reach += reach3(p, g, code, rch, sched, N, d64, gf, cone);
     Ev3 fr(st);
     Run3 rv;
     if (fp32) {
@@ -2123,11 +2254,11 @@ hjbp_status solve3d(hjbp_plan &p) {
             ++S.kernel_launches;
         }
         rv = value3<float>(p, g, code, h32, b0, b1, sched, d.tol, cap, vrounds, p.u32, nullptr, updates, d32, warm,
-                           nullptr, gf);
+                           nullptr, gf, cone);
     } else {
         double *b0 = alloc3<double>(p, N), *b1 = alloc3<double>(p, N);
         rv = value3<double>(p, g, code, h64, b0, b1, sched, d.tol, cap, vrounds, nullptr, p.u_out, updates, d64,
-                            warm, nullptr, gf);
+                            warm, nullptr, gf, cone);
     }
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
@@ -2156,7 +2287,8 @@ hjbp_status solve3d(hjbp_plan &p) {
             if (per_node)
                 k_polish3g<<<grid_for3(N, 128), 128, 0, st>>>(g, code, pa, pb, mc, d64, gfine);
             else
-                k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64, d64);
+                k_polish3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, c32, c64, d64, cone,
+                                                              p.astar);
             ++S.kernel_launches;
             check_cuda(cudaGetLastError(), "polish3");
             std::swap(pa, pb);
@@ -2189,7 +2321,7 @@ hjbp_status solve3d(hjbp_plan &p) {
     if (per_node)
         for (int m = 0; m < d.n_controls; ++m)
             if (p.controls[3 * m] == 0.0 && p.controls[3 * m + 1] == 0.0) --admissible;
-    S.node_control_updates = (int64_t)hu * admissible;
+    S.node_control_updates = cone ? (int64_t)((double)hu * cone_size + 0.5) : (int64_t)hu * admissible;
     S.n_patches = p.patchy ? R : 1;
     S.ms_setup = ms3(e0, e1);
     S.ms_fine = ms3(f0, f1);

@@ -189,3 +189,25 @@ def test_control_cones_state_constraints_larger(pkg):
     assert r["status"] == 0
     ref = oracle.patchy_solve(p, tol=1e-12, reduce_r=4.0)
     _assert_values(r["u"], ref.u)
+
+
+@pytest.mark.parametrize("mode", ["state", "dirichlet"])
+@pytest.mark.parametrize("r_fac", [2.0, 4.0])
+def test_3d_control_cones_match_oracle(pkg, mode, r_fac):
+    """AO3 on the 3D path (the paper's 3D tests reduce the controls by r = 4):
+    the minimum over the cone a . a* >= cos(pi / r) of the coarse feedback,
+    S* on the reduced sets, against the oracle's reduced iteration."""
+    p = W.eikonal3d(n=41, n_coarse=11, n_c=50)
+    flags = pkg.HJBP_FLAG_DIRICHLET if mode == "dirichlet" else 0
+    r = _run(pkg, p, flags=flags, reduce_r=r_fac)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=mode == "dirichlet", reduce_r=r_fac)
+    _assert_values(r["u"], ref.u)
+
+
+def test_3d_control_cones_fan(pkg):
+    p = W.fan3d(n=37, n_coarse=13, n_c=50)
+    r = _run(pkg, p, reduce_r=4.0)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, reduce_r=4.0)
+    _assert_values(r["u"], ref.u)
