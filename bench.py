@@ -145,22 +145,30 @@ class Clocks:
 
 def oracle_sample(p, rows: int):
     """Time one application of F (Eq. SLscheme) by the C oracle on a band of
-    ``rows`` grid rows of the workload; returns (node-control updates, s)."""
+    ``rows`` x n1 consecutive nodes at the middle of the workload's grid (grid
+    rows in 2D, rows of the middle plane in 3D); returns (node-control
+    updates, s).  Brockett's zero control is not admissible and not counted."""
     import oracle
 
     kind, _, _ = oracle.setup(p)
     x = oracle.grid_coords(p)
     U = np.where(kind == oracle.GHOST, np.inf, np.linalg.norm(x, axis=1))
     U[kind == oracle.TARGET] = 0.0
-    n = p.n[0]
-    r0 = n // 2 - rows // 2
+    count = rows * p.n[0]
+    s0 = max(0, kind.size // 2 - count // 2)
     band = np.zeros(kind.size, bool)
-    band[r0 * n:(r0 + rows) * n] = True
+    band[s0:s0 + count] = True
     upd = band & (kind == oracle.FREE)
     t = time.perf_counter()
     oracle.sl_apply(p, U, upd=upd, mode=0)
     dt = time.perf_counter() - t
-    return int(upd.sum()) * p.n_controls, dt
+    return int(upd.sum()) * admissible_controls(p), dt
+
+
+def admissible_controls(p) -> int:
+    if getattr(p, "dyn", "speed") == "brockett":
+        return int(np.sum(np.any(p.controls[:, :2] != 0.0, axis=1)))
+    return p.n_controls
 
 
 def aggregate(dist, local_ms: float, local_units: float, device: str):
@@ -197,14 +205,14 @@ def run_reference(args, rank, world):
         tot_u += u
         tot_t += t
     v = tot_u / tot_t
-    sample = (f"one application of F (Eq. SLscheme) by the single-threaded FP64 C oracle on a band of {rows} rows "
-              f"x {N_FINE} nodes of the {WORKLOAD} workload, 64 controls, per step")
+    sample = (f"one application of F (Eq. SLscheme) by the single-threaded FP64 C oracle on {rows} x {N_FINE} "
+              f"consecutive nodes at the middle of the {WORKLOAD} grid, {admissible_controls(p)} controls, per step")
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": 64, "n_targets": 4,
-                   "tol": 1e-6, "seed": 0},
+        "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": p.n_controls,
+                   "n_targets": p.n_targets, "n_patches": p.n_patches, "tol": p.tol, "seed": 0},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -235,9 +243,11 @@ def run_ours(args, rank, world, dist):
             u, t = oracle_sample(p, 48)
             tu += u
             tt += t
+        nc = admissible_controls(p)
         cpu = {"value": tu / tt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{tu // p.n_controls} node updates x {p.n_controls} controls: applications of F (Eq. SLscheme) by the "
-                         f"single-threaded FP64 C oracle on 48-row bands of the same {N_FINE}^2 grid, {tt:.1f} s"}
+               "sample": f"{tu // nc} node updates x {nc} controls: applications of F (Eq. SLscheme) by the "
+                         f"single-threaded FP64 C oracle on 48 x {N_FINE} consecutive nodes at the middle of "
+                         f"the same {WORKLOAD} grid, {tt:.1f} s"}
 
     # patch boundary and add-ons of Sec. 6 (defaults: state constraints, none)
     aflags = ((P.HJBP_FLAG_DIRICHLET if args.bc == "dirichlet" else 0) | (P.HJBP_FLAG_WARM_START if args.warm else 0)
