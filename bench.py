@@ -482,8 +482,9 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--n", type=int, default=0, help="fine nodes per side (default 2049 / 257)")
     ap.add_argument("--nc", type=int, default=0, help="coarse nodes per side (default 65 / 33)")
-    ap.add_argument("--bc", default="state", choices=["state", "dirichlet"],
-                    help="patch boundary of Step 3.2: state constraints (Sec. 3) or U_P^(0) (Eq. dbc)")
+    ap.add_argument("--bc", default=None, choices=["state", "dirichlet"],
+                    help="patch boundary of Step 3.2: state constraints (Sec. 3) or U_P^(0) (Eq. dbc); default "
+                         "state, Dirichlet for Brockett 3D (its trajectories cannot stay inside a patch)")
     ap.add_argument("--warm", action="store_true", help="add-on AO1: start Step 3.2 from U_P^(0)")
     ap.add_argument("--reduce-r", type=float, default=0.0, help="add-on AO3: control cones of half-angle pi/r")
     ap.add_argument("--tune", default="", help="launch shape: value rounds, phi rounds, reach passes, warps per tile")
@@ -494,6 +495,8 @@ def main():
     args = ap.parse_args()
     global N_FINE, N_COARSE, WORKLOAD, FAMILY
     FAMILY = args.workload
+    if args.bc is None:
+        args.bc = "dirichlet" if FAMILY == "paper-brockett3d" else "state"
     if FAMILY == "batched":
         args.count = args.count or 512
         return run_batched(args)
