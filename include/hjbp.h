@@ -181,8 +181,9 @@ typedef struct {
 #define HJBP_FLAG_WARM_START 4
 /* HJBP_FLAG_CAUSAL_SWEEPS (patchy solves only): add-on AO2 of Sec. 6 in the
  * form the tiled GPU iteration can use.  The paper orders the nodes of a
- * patch so that the update follows the characteristics; here each 32x32 tile
- * runs only the Gauss-Seidel directions along which the coarse feedback
+ * patch so that the update follows the characteristics; here each tile (32x32
+ * in 2D, 8x8x8 in 3D) runs only the Gauss-Seidel directions along which the
+ * coarse feedback
  * a*_{k~} of Step 2 carries information (a node depends on its foot
  * x_i + k a*, so the sweep moves against a*), in Step 3.1 and Step 3.2.  The
  * fixed point is the same; the solve stays deterministic.                    */

@@ -140,7 +140,6 @@ static std::string validate(const hjbp_problem_desc *d) {
         return "reduce_r must be 0 or at least 1";
     if (d->reduce_r != 0.0 && d->n_coarse[0] == 0) return "reduce_r needs a patchy solve (n_coarse)";
     if (d->reduce_r != 0.0 && d->dim == 2 && d->n_controls > 64) return "reduce_r on the 2D path needs <= 64 controls";
-    if (d->dim == 3 && (d->flags & HJBP_FLAG_CAUSAL_SWEEPS)) return "causal sweeps are implemented for 2D problems";
     if (d->reduce_r != 0.0 && d->dyn == HJBP_DYN_BROCKETT) return "control cones need f = c(x) a or the drift";
     if (d->speed == HJBP_C_FOURIER2D) {
         double norm = 0.0;

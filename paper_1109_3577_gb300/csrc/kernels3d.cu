@@ -587,8 +587,10 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
         hs[lz][ly][lx] = hv;
     }
     __syncthreads();
+    const unsigned tdirs = s.dirs ? s.dirs[t] : 0x3Fu;   // AO2: the tile's sweep directions
     for (int rd = 0; rd < rounds; ++rd)
-        for (int dir = 0; dir < 6; ++dir)
+        for (int dir = 0; dir < 6; ++dir) {
+            if (!((tdirs >> dir) & 1u)) continue;
             for (int st = 0; st < kT3; ++st) {
                 int lx, ly, lz;
                 plane_node(dir, st, tid, lx, ly, lz);
@@ -611,6 +613,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                 if (active) sm.u[lz][ly][lx] = nw;
                 __syncthreads();
             }
+        }
     const float mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm, clamp);
     nfree = __reduce_add_sync(0xffffffffu, nfree);
     if ((tid & 31) == 0 && updates && nfree)
@@ -871,6 +874,66 @@ __global__ void k_gather3d(Grid3 g, const uint8_t *__restrict__ latest, const T 
         const T v = (tt >= 0 && latest[tt]) ? b1[i] : b0[i];
         if (out_t) out_t[i] = v;
         if (out64) out64[i] = v >= Num<T>::thresh() ? (double)INFINITY : (double)v;
+    }
+}
+
+// Causal sweep directions per tile (AO2 on the tiled iteration, as in 2D):
+// information travels against a*, so where at least a fraction frac of the
+// tile's feedback has a*_x < 0 the x sweep runs in increasing x only
+// (direction 0), where it has a*_x > 0 in decreasing x only (direction 1),
+// otherwise both; the same for y (2, 3) and z (4, 5).  With per-node feet
+// (gen.nc > 0) the signs are those of the node's f/|f|.
+struct DirCtl3 {
+    int8_t s[3][kMaxControls];
+};
+
+__global__ void __launch_bounds__(kT3n) k_tile_dirs3d(Grid3 g, const int8_t *__restrict__ code,
+                                                      const uint8_t *__restrict__ astar, const DirCtl3 dc,
+                                                      const Gen3 gen, float frac, uint8_t *__restrict__ dirs) {
+    const int t = blockIdx.x;
+    const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
+    __shared__ int cnt[6];
+    if (threadIdx.x < 6) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int c[6] = {0, 0, 0, 0, 0, 0};   // per axis: count with the component < 0, > 0
+    for (int e = threadIdx.x; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int x = x0 + e % kT3, y = y0 + (e / kT3) % kT3, z = z0 + e / (kT3 * kT3);
+        if (x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+        const int8_t cd = code[i];
+        const uint8_t a = astar[i];
+        if (cd < 0 || cd >= kTargetBase || a == kNoControl) continue;
+        int sg[3];
+        if (gen.nc > 0) {
+            const double4 q = gen.dh[((int64_t)y * g.n0 + x) * gen.nc + a];
+            sg[0] = q.x > 1e-12 ? 1 : (q.x < -1e-12 ? -1 : 0);
+            sg[1] = q.y > 1e-12 ? 1 : (q.y < -1e-12 ? -1 : 0);
+            sg[2] = q.z > 1e-12 ? 1 : (q.z < -1e-12 ? -1 : 0);
+        } else {
+            sg[0] = dc.s[0][a];
+            sg[1] = dc.s[1][a];
+            sg[2] = dc.s[2][a];
+        }
+        for (int d = 0; d < 3; ++d) {
+            c[2 * d] += sg[d] < 0;
+            c[2 * d + 1] += sg[d] > 0;
+        }
+    }
+    for (int k = 0; k < 6; ++k) {
+        const int v = __reduce_add_sync(0xffffffffu, c[k]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&cnt[k], v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned m = 0;
+        for (int d = 0; d < 3; ++d) {
+            const int neg = cnt[2 * d], pos = cnt[2 * d + 1], tot = neg + pos;
+            if (tot == 0) m |= 3u << (2 * d);
+            else if ((float)neg >= frac * (float)tot) m |= 1u << (2 * d);
+            else if ((float)pos >= frac * (float)tot) m |= 2u << (2 * d);
+            else m |= 3u << (2 * d);
+        }
+        dirs[t] = (uint8_t)m;
     }
 }
 
@@ -1198,8 +1261,10 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     __syncthreads();
     // a colour that is zero over the whole image stays zero: skip it (uniform per tile)
     const unsigned live = salive;
+    const unsigned tdirs = s.dirs ? s.dirs[t] : 0x3Fu;   // AO2: the tile's sweep directions
     for (int rd = 0; rd < rounds && live; ++rd)
-        for (int dir = 0; dir < 6; ++dir)
+        for (int dir = 0; dir < 6; ++dir) {
+            if (!((tdirs >> dir) & 1u)) continue;
             for (int st = 0; st < kT3; ++st) {
                 int lx, ly, lz;
                 plane_node(dir, st, tid, lx, ly, lz);
@@ -1250,6 +1315,7 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                 }
                 __syncthreads();
             }
+        }
     const int cur = s.latest[t];
     float *dst = cur ? b0 : b1;
     const float *old = cur ? b1 : b0;
@@ -2113,6 +2179,21 @@ hjbp_status solve3d(hjbp_plan &p) {
         }
         S.kernel_launches += 2;
         check_cuda(cudaGetLastError(), "feedback3");
+        // AO2: causal sweep directions per tile from the feedback (Step 3.1 and 3.2)
+        if ((d.flags & HJBP_FLAG_CAUSAL_SWEEPS) && sched.ntiles) {
+            DirCtl3 dc;
+            std::memset(&dc, 0, sizeof(dc));
+            for (int m = 0; m < d.n_controls && !per_node; ++m)
+                for (int c = 0; c < 3; ++c) {
+                    const double v = p.controls[3 * m + c];
+                    dc.s[c][m] = (int8_t)(v > 1e-12 ? 1 : (v < -1e-12 ? -1 : 0));
+                }
+            uint8_t *dirs = alloc3<uint8_t>(p, sched.ntiles);
+            k_tile_dirs3d<<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, dc, gfine, 0.9f, dirs);
+            ++S.kernel_launches;
+            check_cuda(cudaGetLastError(), "tile directions");
+            sched.d.dirs = dirs;
+        }
         Ev3 e3(st);
         {
             const int RG = R >= 4 ? 4 : (R >= 2 ? 2 : 1);

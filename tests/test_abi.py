@@ -74,9 +74,8 @@ def test_create_rejects_bad_descriptors(lib):
         (p, {"reduce_r": 0.5}),
         (p, {"reduce_r": float("nan")}),
         (p.with_(controls=W.controls_2d(128)), {"reduce_r": 4.0}),
-        # cones are defined on unit controls; causal sweeps run the 2D tiles
+        # cones are defined on unit controls
         (W.brockett3d(n=17, n_coarse=9), {"reduce_r": 4.0}),
-        (W.eikonal3d(n=17, n_coarse=9, n_c=14), {"flags": pkg.HJBP_FLAG_CAUSAL_SWEEPS}),
     ]
     for q, kw in bad_opts:
         d, keep = pkg.desc_from_problem(q, **kw)

@@ -211,3 +211,16 @@ def test_3d_control_cones_fan(pkg):
     assert r["status"] == 0
     ref = oracle.patchy_solve(p, tol=1e-12, reduce_r=4.0)
     _assert_values(r["u"], ref.u)
+
+
+@pytest.mark.parametrize("family", ["eikonal3d", "brockett3d"])
+def test_3d_causal_sweeps_reach_the_same_fixed_point(pkg, family):
+    """AO2 on the 3D tiles: per-tile sweep directions against the coarse
+    feedback (Brockett: the node's own f/|f|); same fixed point as the oracle."""
+    p = W.eikonal3d(n=41, n_coarse=11, n_c=50) if family == "eikonal3d" else W.brockett3d(n=34, n_coarse=17)
+    flags = pkg.HJBP_FLAG_CAUSAL_SWEEPS | (pkg.HJBP_FLAG_DIRICHLET if family == "brockett3d" else 0)
+    r = _run(pkg, p, flags=flags)
+    assert r["status"] == 0
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=family == "brockett3d")
+    _assert_values(r["u"], ref.u)
+    assert np.mean(r["labels"] == ref.labels) >= 0.999
