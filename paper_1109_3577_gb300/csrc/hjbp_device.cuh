@@ -125,6 +125,14 @@ struct Cone2 {
     unsigned long long mask[65];
     uint32_t reach[65];
     int nc;
+    // the same cones in the symmetric pair form of the 8-class control set:
+    // bit 16 q + 2 k + member for class k in quadrant q (member 0: the
+    // control with |a_x| >= |a_y|, member 1 its mirror), and the axis
+    // controls in amask (bit 0 +x, 1 -x, 2 +y, 3 -y); pairs = 0 when the
+    // control set has no such form
+    unsigned long long pmask[65];
+    uint8_t amask[65];
+    int pairs;
 };
 
 // Speed field c(x) (hjbp_speed_kind) and its parameters, passed by value.

@@ -409,6 +409,53 @@ __device__ __forceinline__ T sl_update_cone(const S &sm, int c, int r, unsigned 
     return best;
 }
 
+// AO3 in the symmetric pair form: class k of quadrant q holds the control
+// a = (sx X, sy Y), X >= Y, and its mirror a' = (sx Y, sy X); with
+// E = u10 + u01, D = u10 - u01 their values are base + t D and base - t D
+// (base = kap h + kap w11 u11 + s E), so one pair costs the same three FMAs
+// whichever members the node's cone keeps (both: base - t |D|).  Quadrants
+// no lane of the warp uses (quni) are skipped warp-uniformly.
+template <typename T, int NCLS, bool kDir, class S>
+__device__ __forceinline__ T sl_update_pcone(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct,
+                                             unsigned long long pm, unsigned am, unsigned quni) {
+    T nb[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            if constexpr (kDir)
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : sm.d[r - 1 + dy][c - 1 + dx];
+            else
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
+        }
+    T b[4] = {Num<T>::big(), Num<T>::big(), Num<T>::big(), Num<T>::big()};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!((quni >> q) & 1u)) continue;
+        const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+        const T a10 = nb[1][sx], a01 = nb[sy][1], A = nb[sy][sx];
+        const T E = a10 + a01, D = a10 - a01, G = fabs(D);
+        const unsigned bits = (unsigned)(pm >> (16 * q));
+#pragma unroll
+        for (int k = 0; k < NCLS; ++k) {
+            const unsigned cb = (bits >> (2 * k)) & 3u;
+            const T base = fma(ct.cls_kw11[k], A, fma(ct.cls_s[k], E, ct.cls_kap[k] * hh));
+            const T x = cb == 3u ? -G : (cb == 1u ? D : -D);
+            const T v = cb ? fma(ct.cls_t[k], x, base) : Num<T>::big();
+            b[q] = v < b[q] ? v : b[q];
+        }
+    }
+    if (am) {
+        // axis controls land on the neighbour: kap = 1
+        if (am & 1u) b[0] = fmin(b[0], nb[1][2] + hh);
+        if (am & 2u) b[1] = fmin(b[1], nb[1][0] + hh);
+        if (am & 4u) b[2] = fmin(b[2], nb[2][1] + hh);
+        if (am & 8u) b[3] = fmin(b[3], nb[0][1] + hh);
+    }
+    const T b01 = b[0] < b[1] ? b[0] : b[1], b23 = b[2] < b[3] ? b[2] : b[3];
+    return b01 < b23 ? b01 : b23;
+}
+
 // Parities of the 3x3 tile neighbourhood of tile (tx, ty) as a 9-bit mask
 // (bit 3 (dy+1) + (dx+1)); tiles off the grid read 0 like the ghost ring.
 __device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched &s, int tx, int ty) {
@@ -447,10 +494,17 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     __shared__ T u0[kTile][kTile + 1];
     __shared__ uint8_t sa[kCone ? kTile : 1][kCone ? kTile + 1 : 1];
     __shared__ unsigned long long cmask[kCone ? 65 : 1];
-    __shared__ Ctl4<T> ctab[kCone ? 64 : 1];
+    __shared__ Ctl4<T> ctab[kCone && NCLS == 0 ? 64 : 1];
+    __shared__ uint8_t camask[kCone && NCLS > 0 ? 65 : 1];
     const int lane = threadIdx.x;
     const QBeg qb{{ct.qbeg[0], ct.qbeg[1], ct.qbeg[2], ct.qbeg[3], ct.qbeg[4]}};
-    if constexpr (kCone) {
+    if constexpr (kCone && NCLS > 0) {
+        // the pair form: per feedback the pair and axis masks
+        for (int q = lane; q <= cone->nc; q += 32) {
+            cmask[q] = cone->pmask[q];
+            camask[q] = cone->amask[q];
+        }
+    } else if constexpr (kCone) {
         for (int q = lane; q <= cone->nc; q += 32) cmask[q] = cone->mask[q];
         for (int q = lane; q < ct.nc; q += 32) ctab[q] = Ctl4<T>{ct.kw10[q], ct.kw01[q], ct.kw11[q], ct.kap[q]};
     }
@@ -532,7 +586,19 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                 const unsigned m = sm.mk[r - 1][c - 1];
                 const bool active = (m & 0x8000u) != 0;
                 T nw = sm.u[r][c];
-                if constexpr (kCone) {
+                if constexpr (kCone && NCLS > 0) {
+                    const int ai = sa[r - 1][c - 1];
+                    const unsigned long long pm = active ? cmask[ai] : 0ull;
+                    const unsigned am = active ? camask[ai] : 0u;
+                    unsigned qb = am ? 16u : 0u;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) qb |= ((pm >> (16 * q)) & 0xffffull) ? (1u << q) : 0u;
+                    const unsigned quni = __reduce_or_sync(0xffffffffu, qb);
+                    if (active) {
+                        const T best = sl_update_pcone<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct, pm, am, quni);
+                        if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
+                    }
+                } else if constexpr (kCone) {
                     const unsigned long long mine = active ? cmask[sa[r - 1][c - 1]] : 0ull;
                     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mine);
                     const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mine >> 32));
@@ -2329,6 +2395,50 @@ Cone2 make_cones(const hjbp_plan &p, double *mean_size) {
         if (a < nc) total += (double)__builtin_popcountll(mask);
     }
     if (mean_size) *mean_size = total / nc;
+    // the pair form: the classes of the 8-class symmetric set in the order the
+    // pair table enumerates them (controls with x > 0, y > 0, x >= y)
+    const CtlTable2<float> ct = make_table<float>(p);
+    if (ct.d4 && ct.ncls == 8) {
+        const double tol = 1e-12;
+        std::vector<std::pair<double, double>> reps;
+        for (int m = 0; m < nc; ++m) {
+            const double x = p.dirs[2 * m], y = p.dirs[2 * m + 1];
+            if (x > 0.0 && y > 0.0 && x >= y - tol) reps.emplace_back(x, y);
+        }
+        std::vector<int> bit(nc, -1), abit(nc, -1);
+        bool ok = reps.size() == 8;
+        for (int m = 0; m < nc && ok; ++m) {
+            const double ax = p.dirs[2 * m], ay = p.dirs[2 * m + 1];
+            if (ay == 0.0 || ax == 0.0) {
+                abit[m] = ay == 0.0 ? (ax > 0.0 ? 0 : 1) : (ay > 0.0 ? 2 : 3);
+                continue;
+            }
+            const int q = (ax >= 0.0 ? 1 : 0) + (ay >= 0.0 ? 2 : 0);
+            const double X = std::fabs(ax), Y = std::fabs(ay);
+            const bool diag = std::fabs(X - Y) < tol;
+            const int member = (X >= Y || diag) ? 0 : 1;
+            const double rx = member ? Y : X, ry = member ? X : Y;
+            int k = -1;
+            for (int c = 0; c < 8; ++c)
+                if (std::fabs(reps[c].first - rx) < tol && std::fabs(reps[c].second - ry) < tol) k = c;
+            if (k < 0) ok = false;
+            else bit[m] = 16 * q + 2 * k + member;
+        }
+        if (ok) {
+            for (int a = 0; a <= nc; ++a) {
+                unsigned long long pmk = 0;
+                unsigned amk = 0;
+                for (int m = 0; m < nc; ++m) {
+                    if (!((cn.mask[a] >> pos[m]) & 1ull)) continue;
+                    if (abit[m] >= 0) amk |= 1u << abit[m];
+                    else pmk |= 1ull << bit[m];
+                }
+                cn.pmask[a] = pmk;
+                cn.amask[a] = (uint8_t)amk;
+            }
+            cn.pairs = 1;
+        }
+    }
     return cn;
 }
 
@@ -2440,6 +2550,7 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     const CtlTable2<T> ct = make_table<T>(p);
     const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
     const int warps = p.desc.tune[3] > 0 ? p.desc.tune[3] : 1;
+    const bool pairs = cone && ct.d4 && ct.ncls == 8 && p.cone_pairs;   // AO3 in the pair form
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
     RunResult rr = run_tiles(p, g, s, (float)tol, cap, [&](int par, int) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -2449,7 +2560,13 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
         const bool plain = clamp && !dval && !cone;  // the multi-warp variant has none of the options
-        if (cone && dval)
+        if (cone && pairs && dval)
+            k_value2d<T, 8, true, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
+                                                                       ct, clamp, dval, p.astar, cone);
+        else if (cone && pairs)
+            k_value2d<T, 8, false, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
+                                                                        ct, clamp, nullptr, p.astar, cone);
+        else if (cone && dval)
             k_value2d<T, 0, true, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
                                                                        ct, clamp, dval, p.astar, cone);
         else if (cone)
@@ -2854,6 +2971,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     double cone_size = d.n_controls;
     if (p.patchy && d.reduce_r > 0.0) {
         const Cone2 hc = make_cones(p, &cone_size);
+        p.cone_pairs = hc.pairs != 0;
         cone = static_cast<Cone2 *>(p.dev_alloc(sizeof(Cone2)));
         check_cuda(cudaMemcpyAsync(cone, &hc, sizeof(Cone2), cudaMemcpyHostToDevice, st), "cones");
         // the host copy goes out of scope: let the copy land first

@@ -30,6 +30,7 @@ struct hjbp_plan {
     hjbp_status last_status = HJBP_ESTATE;
     hjbp_stats stats{};
     std::vector<double> init;       // caller's start values (hjbp_set_initial), empty: none
+    bool cone_pairs = false;        // AO3 cones available in the symmetric pair form
 
     // --- device arrays owned by the plan ---
     struct Block {

@@ -47,6 +47,13 @@ def test_batch_solve_matches_one_at_a_time(P):
         for pl, (s0, u0, l0) in zip(plans, refs):
             _same(pl.values(), u0)
             assert np.array_equal(pl.labels(), l0)
+        # the batch's Fourier-field problems against the FP64 oracle (the three smallest)
+        import oracle
+
+        for k in sorted(range(len(probs)), key=lambda q: probs[q].n_nodes)[:3]:
+            ref = oracle.patchy_solve(probs[k], tol=1e-12)
+            _same(plans[k].values(), ref.u)
+            assert np.mean(plans[k].labels() == ref.labels) >= 0.999
     finally:
         for pl in plans:
             pl.close()
