@@ -388,7 +388,16 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     probs = W.batched(seed=0, count=args.count)
-    plans = [P.Plan(p, stream=0) for p in probs]
+    # launch shapes per problem class from the autotuner, before the timed region
+    tunes, classes, t_tune = [None] * len(probs), 0, 0.0
+    if not args.no_tune:
+        t = time.perf_counter()
+        for q, p in enumerate(probs):
+            d, keep = P.desc_from_problem(p)
+            tunes[q], cached = P.hjbp_autotune(d, 0)
+            classes += 0 if cached else 1
+        t_tune = time.perf_counter() - t
+    plans = [P.Plan(p, stream=0, tune=tunes[q]) for q, p in enumerate(probs)]
     nodes = sum(p.n_nodes for p in probs)
     for pl in plans[: min(8, len(plans))]:
         pl.solve()
@@ -409,7 +418,8 @@ def run_batched(args):
            "value": len(probs) / bat, "unit": "solves/s", "one_at_a_time_solves_per_s": len(probs) / seq,
            "speedup": seq / bat, "batched_s": bat, "one_at_a_time_s": seq, "workers": args.workers,
            "total_nodes": nodes, "node_control_updates_per_s_batched": ncu_bat / bat,
-           "node_control_updates_per_s_one_at_a_time": ncu_seq / seq, "data": "synthetic", "dtype": "f32"}
+           "node_control_updates_per_s_one_at_a_time": ncu_seq / seq, "data": "synthetic", "dtype": "f32",
+           "autotuned": {"classes": classes, "seconds": t_tune} if not args.no_tune else None}
     for pl in plans:
         pl.close()
     print(json.dumps(out))
@@ -478,6 +488,7 @@ def main():
                          "189 controls")
     ap.add_argument("--count", type=int, default=0, help="problems (batched: 512) / requests (serving: 2000)")
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--no-tune", action="store_true", help="batched: default launch shapes instead of the autotuner's")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--n", type=int, default=0, help="fine nodes per side (default 2049 / 257)")

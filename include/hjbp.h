@@ -305,6 +305,19 @@ const char *hjbp_last_error(void);
  * one (an error, else ENOCONV, else OK).                                     */
 hjbp_status hjbp_batch_solve(hjbp_plan *const *plans, int count, int workers, hjbp_status *statuses);
 
+/* hjbp_autotune: the launch shape (tune[0..3] of hjbp_problem_desc: Gauss-
+ * Seidel rounds per launch of the value sweep and of the colour transport,
+ * reach passes, warps per tile) for problems of the class of `desc`: its
+ * dimension, log2 of its cells per side and of its control count, patchy or
+ * not, its boundary and add-on options.  The first call for a class solves
+ * `desc` (on `cuda_stream`) once per candidate shape after a warm-up solve
+ * and keeps the fastest by GPU solve time; later calls for the class return
+ * the kept shape (*from_cache = 1).  cache_path (optional) names a text file
+ * read before the lookup and appended with each new class.  Errors: EINVAL for
+ * a NULL argument, else the status of the failing solve.                    */
+hjbp_status hjbp_autotune(const hjbp_problem_desc *desc, void *cuda_stream, const char *cache_path, int tune_out[4],
+                          int *from_cache);
+
 /* Serving.  A server owns a pool of `workers` threads (<= 0 selects 8) with
  * their own streams and a device-memory budget (0 selects half of the free
  * memory).  submit validates and copies a problem, estimates the device bytes

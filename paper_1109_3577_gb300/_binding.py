@@ -153,6 +153,8 @@ def library():
         lib.hjbp_solve_global2d_noalloc.restype = C.c_int
         lib.hjbp_batch_solve.argtypes = [P(vp), C.c_int, C.c_int, P(C.c_int)]
         lib.hjbp_batch_solve.restype = C.c_int
+        lib.hjbp_autotune.argtypes = [P(Desc), vp, C.c_char_p, P(C.c_int), P(C.c_int)]
+        lib.hjbp_autotune.restype = C.c_int
         lib.hjbp_server_create.argtypes = [C.c_size_t, C.c_int, P(vp)]
         lib.hjbp_server_create.restype = C.c_int
         lib.hjbp_server_submit.argtypes = [vp, P(Desc), P(C.c_uint64)]
@@ -260,6 +262,16 @@ def hjbp_batch_solve(plans, workers: int = 0):
     if rc not in (HJBP_OK, HJBP_ENOCONV):
         _check(rc)
     return list(st)
+
+
+def hjbp_autotune(desc, stream: int = 0, cache_path: Optional[str] = None):
+    """The launch shape (tune[0..3]) for problems of desc's class, and
+    whether it came from the cache."""
+    t = (C.c_int * 4)()
+    fc = C.c_int(0)
+    path = cache_path.encode() if cache_path else None
+    _check(library().hjbp_autotune(C.byref(desc), C.c_void_p(stream), path, t, C.byref(fc)))
+    return list(t), bool(fc.value)
 
 
 def hjbp_server_create(budget_bytes: int = 0, workers: int = 0) -> int:

@@ -90,3 +90,25 @@ def test_served_result_is_the_same_alone_and_in_the_mix(P):
             pl.close()
     finally:
         P.hjbp_server_destroy(srv)
+
+
+def test_autotune_picks_a_shape_and_caches_it(P, tmp_path):
+    """The tuner times candidate launch shapes once per problem class, keeps
+    the fastest in the process and in the cache file, and the tuned solve
+    reaches the oracle's fixed point."""
+    import oracle
+
+    p = W.sincos2d(11, n=161, n_coarse=21, n_targets=2, radius=0.1)
+    d, keep = P.desc_from_problem(p, flags=P.HJBP_FLAG_DIRICHLET)
+    path = str(tmp_path / "tune.txt")
+    t, cached = P.hjbp_autotune(d, 0, path)
+    assert not cached and t[0] in (1, 2, 3) and t[1] in (2, 3, 4)
+    t2, cached2 = P.hjbp_autotune(d, 0, path)
+    assert cached2 and t2 == t
+    fields = open(path).read().split()
+    assert len(fields) == 9 and [int(v) for v in fields[5:9]] == t
+    with P.Plan(p, tune=t, flags=P.HJBP_FLAG_DIRICHLET) as pl:
+        assert pl.solve() == 0
+        u = pl.values()
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=True)
+    _same(u, ref.u)
