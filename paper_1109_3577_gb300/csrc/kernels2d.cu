@@ -2184,8 +2184,10 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
     reset_sched(p, s);
     cap = std::min(cap, s.hist);
     int par = 0, L = 0;
-    int *pinned = nullptr;
-    check_cuda(cudaMallocHost(&pinned, sizeof(int)), "pinned");
+    // one pinned word per plan, kept for its lifetime (allocating and freeing
+    // pinned memory per loop costs more than a short sweep)
+    if (!p.pinned_count) check_cuda(cudaMallocHost(&p.pinned_count, sizeof(int)), "pinned");
+    int *pinned = p.pinned_count;
     int check_every = 4;
     while (L < cap) {
         sweep(par, L);
@@ -2206,7 +2208,6 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
             check_every = std::min(check_every * 2, 16);
         }
     }
-    cudaFreeHost(pinned);
     std::vector<int> ch(L);
     std::vector<float> rh(L);
     if (L) {

@@ -1668,10 +1668,11 @@ template <class Sweep> Run3 run_tiles3(hjbp_plan &p, const Grid3 &g, Sched3 &s, 
         par ^= 1;
         ++L;
         if (L % check_every == 0 || L == cap) {
-            int left = 0;
-            check_cuda(cudaMemcpyAsync(&left, s.d.count + par, sizeof(int), cudaMemcpyDeviceToHost, st), "count");
+            if (!p.pinned_count) check_cuda(cudaMallocHost(&p.pinned_count, sizeof(int)), "pinned");
+            check_cuda(cudaMemcpyAsync(p.pinned_count, s.d.count + par, sizeof(int), cudaMemcpyDeviceToHost, st),
+                       "count");
             check_cuda(cudaStreamSynchronize(st), "sweep3 sync");
-            if (left == 0) {
+            if (*p.pinned_count == 0) {
                 rr.converged = true;
                 break;
             }

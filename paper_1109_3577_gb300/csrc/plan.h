@@ -31,6 +31,10 @@ struct hjbp_plan {
     hjbp_stats stats{};
     std::vector<double> init;       // caller's start values (hjbp_set_initial), empty: none
     bool cone_pairs = false;        // AO3 cones available in the symmetric pair form
+    int *pinned_count = nullptr;    // pinned host word for the sweep loops' readbacks (lazy)
+    ~hjbp_plan() {
+        if (pinned_count) cudaFreeHost(pinned_count);
+    }
 
     // --- device arrays owned by the plan ---
     struct Block {
