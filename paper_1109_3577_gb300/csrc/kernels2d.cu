@@ -3055,11 +3055,10 @@ hjbp_status solve2d(hjbp_plan &p) {
     k_final_labels<<<grid_for(N), 256, 0, st>>>(N, code0, code, p.patchy ? nullptr : p.label_out, unreach);
     ++p.stats.kernel_launches;
     Ev f2(st);
-    unsigned long long hu = 0;
+    unsigned long long hu = 0, hun = 0;
     check_cuda(cudaMemcpyAsync(&hu, updates, sizeof(hu), cudaMemcpyDeviceToHost, st), "updates");
+    check_cuda(cudaMemcpyAsync(&hun, unreach, sizeof(hun), cudaMemcpyDeviceToHost, st), "unreachable");
     check_cuda(cudaStreamSynchronize(st), "final sync");
-    unsigned long long hun = 0;
-    check_cuda(cudaMemcpy(&hun, unreach, sizeof(hun), cudaMemcpyDeviceToHost), "unreachable");
     S.unreachable = (int64_t)hun;
     S.node_updates = (int64_t)hu;
     // with AO3 a node evaluates its cone only (the mean cone size)
