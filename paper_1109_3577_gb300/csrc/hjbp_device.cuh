@@ -396,6 +396,8 @@ struct TileSched {
     float *res_hist;      // per-launch max change
     int *count_hist;      // per-launch number of active tiles
     const uint8_t *dirs;  // per-tile Gauss-Seidel directions (bit d: run direction d); NULL: all
+    int alt;              // 3D without dirs: launches alternate the increasing and the
+                          // decreasing pass of each axis (half the passes per launch)
 };
 
 __device__ __forceinline__ int tile_of(const Grid2 &g, int x, int y) {

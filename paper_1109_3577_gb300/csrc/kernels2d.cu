@@ -640,7 +640,8 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     if (lane == 0) {
         (par ? s.chg[1] : s.chg[0])[t] = mc;
         s.processed[t] = 1;
-        if (updates) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+        // node updates: one per pass actually run (AO2 may skip passes)
+        if (updates) atomicAdd(updates, (unsigned long long)nf * (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
     }
 }
 

@@ -587,7 +587,8 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
         hs[lz][ly][lx] = hv;
     }
     __syncthreads();
-    const unsigned tdirs = s.dirs ? s.dirs[t] : 0x3Fu;   // AO2: the tile's sweep directions
+    // AO2: the tile's sweep directions; or alternating halves
+    const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0x2Au : 0x15u) : 0x3Fu);
     for (int rd = 0; rd < rounds; ++rd)
         for (int dir = 0; dir < 6; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     const float mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm, clamp);
     nfree = __reduce_add_sync(0xffffffffu, nfree);
     if ((tid & 31) == 0 && updates && nfree)
-        atomicAdd(updates, (unsigned long long)nfree * 6ull * (unsigned long long)rounds);
+        atomicAdd(updates, (unsigned long long)nfree * (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
     if (tid == 0) {
         (par ? s.chg[1] : s.chg[0])[t] = mc;
         s.processed[t] = 1;
@@ -1261,7 +1262,8 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     __syncthreads();
     // a colour that is zero over the whole image stays zero: skip it (uniform per tile)
     const unsigned live = salive;
-    const unsigned tdirs = s.dirs ? s.dirs[t] : 0x3Fu;   // AO2: the tile's sweep directions
+    // AO2: the tile's sweep directions; or alternating halves
+    const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0x2Au : 0x15u) : 0x3Fu);
     for (int rd = 0; rd < rounds && live; ++rd)
         for (int dir = 0; dir < 6; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
@@ -2143,6 +2145,9 @@ hjbp_status solve3d(hjbp_plan &p) {
     ++S.kernel_launches;
     check_cuda(cudaGetLastError(), "setup3");
     Sched3 sched = make_sched3(p, g, hist);
+    // fine-grid sweeps alternate the increasing and decreasing pass of each
+    // axis from launch to launch (tune[5] = 2: all six passes every launch)
+    sched.d.alt = d.tune[5] == 2 ? 0 : 1;
     Ev3 e1(st);
 
     double *dlit = nullptr;   // literal U_P^(0): the Dirichlet data (R16)
