@@ -140,10 +140,11 @@ typedef struct {
                            launch of the value sweep (2), [1] of the colour transport (3),
                            [2] passes per launch of the reachability sweep (1), [3] warps
                            per 32x32 tile of the 2D value sweep (1; 1, 2 or 4), [4] resident
-                           warps per SM of the tile-queue sweep (occupancy limit), [5] 3D:
-                           each fine-grid launch runs the increasing or (alternately) the
-                           decreasing pass of every axis (0, default) or all six passes (2),
-                           [6..7] reserved (0) */
+                           warps per SM of the tile-queue sweep (occupancy limit), [5] the
+                           fine-grid launches run the increasing or (alternately) the
+                           decreasing pass of every axis: 3D default (0; 2 runs all six
+                           passes), 2D only with 1 (measured slower there), [6..7]
+                           reserved (0) */
     double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
                            minimum of Step 3.2 at node i to the controls a with
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse

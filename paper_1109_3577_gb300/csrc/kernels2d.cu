@@ -575,7 +575,8 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         }
     }
     __syncwarp();
-    const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
+    // AO2: the tile's sweep directions; or alternating halves (TileSched.alt)
+    const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0xAu : 0x5u) : 0xFu);
     for (int rd = 0; rd < rounds; ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
@@ -2780,6 +2781,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "setup");
     Sched sched = make_sched(p, g, hist);
+    sched.d.alt = d.tune[5] == 1 ? 1 : 0;   // 2D: alternating halves only on request
     Ev e1(st);
 
     double *dlit = nullptr;   // literal U_P^(0): the Dirichlet data (R16)
