@@ -105,6 +105,7 @@ typedef enum { HJBP_FP64 = 0, HJBP_FP32_POLISH64 = 1 } hjbp_precision;
  *   speed, speed_params[64]   c(x), see hjbp_speed_kind
  *   n_controls, controls      discrete control set A: n_controls x dim unit
  *                  vectors (row-major), 1 <= n_controls <= HJBP_MAX_CONTROLS
+ *                  (patchy solves: <= 255, the feedback a* being one byte)
  *                  (Brockett's integrator: rows (a_1, a_2, unused))
  *   n_targets, targets        Omega_0 = union of balls: n_targets x (dim+1)
  *                  rows (centre, radius); ball j is target part Omega_0^j and

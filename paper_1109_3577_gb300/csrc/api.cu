@@ -91,6 +91,8 @@ static std::string validate(const hjbp_problem_desc *d) {
     if (d->speed == HJBP_C_SIN3D && d->dim != 3) return "SIN3D needs dim 3";
     if ((d->speed == HJBP_C_SINCOS2D || d->speed == HJBP_C_FOURIER2D) && d->dim != 2) return "2D speed field with dim 3";
     if (d->n_controls < 1 || d->n_controls > HJBP_MAX_CONTROLS) return "n_controls out of range";
+    // the coarse feedback a* is one byte per node, 255 meaning "no feedback"
+    if (d->n_coarse[0] != 0 && d->n_controls > 255) return "patchy solves take at most 255 controls";
     if (!d->controls) return "controls is NULL";
     bool moving = false;
     for (int m = 0; m < d->n_controls; ++m) {

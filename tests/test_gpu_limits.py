@@ -1,0 +1,104 @@
+"""The CUDA path at the limits of the ABI and in degenerate cases, against the
+FP64 oracle: the largest control sets (HJBP_MAX_CONTROLS = 256 for the global
+solve; 255 for patchy solves, whose feedback a* is one byte) in 2D and 3D,
+the largest number of patches (HJBP_MAX_TARGETS = 64: one disk in 64
+sectors, eight colour groups of the transport), a target that holds no node
+(nothing is reachable) and the smallest 3D grid."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as P
+
+    torch.cuda.set_device(0)
+    return P
+
+
+def _run(pkg, p, **kw):
+    with pkg.Plan(p, precision=pkg.HJBP_FP32_POLISH64, **kw) as plan:
+        st = plan.solve()
+        return st, plan.values(), plan.labels()
+
+
+def _assert_values(u, ref, rel=1e-4):
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(u))
+    if fin.any():
+        assert np.abs(u[fin] - ref[fin]).max() <= rel * ref[fin].max()
+
+
+@pytest.mark.parametrize("patchy", [False, True])
+def test_largest_control_sets_2d(pkg, patchy):
+    p = W.sincos2d(4, n=97, n_coarse=25, n_c=255 if patchy else 256, n_targets=3, radius=0.15)
+    if not patchy:
+        p = p.with_(n_coarse=None)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.patchy_solve(p, tol=1e-12) if patchy else oracle.global_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    if patchy:
+        assert np.mean(lab == ref.labels) >= 0.999
+
+
+def test_patchy_rejects_256_controls(pkg):
+    d, keep = pkg.desc_from_problem(W.sincos2d(4, n=97, n_coarse=25, n_c=256, n_targets=3, radius=0.15))
+    with pytest.raises(pkg.HjbpError) as ei:
+        pkg.hjbp_create(d, 0, None)
+    assert ei.value.status == 1
+
+
+def test_largest_control_set_3d(pkg):
+    p = W.sin3d(1, n=25, n_coarse=9, n_c=255, n_targets=2, radius=0.2)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.patchy_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    assert np.mean(lab == ref.labels) >= 0.999
+
+
+def test_64_patches(pkg):
+    p = W.eikonal_sectors(n=129, n_coarse=33, parts=64)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.patchy_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    assert np.mean(lab == ref.labels) >= 0.999
+    assert len(set(ref.labels[ref.labels >= 0])) == 64
+
+
+@pytest.mark.parametrize("patchy", [False, True])
+def test_target_without_nodes(pkg, patchy):
+    """A disk thinner than the grid, between nodes: no target node, so no node
+    reaches the target and every value is +inf (label -1)."""
+    k = 4.0 / 64
+    p = W.eikonal2d(n=65).with_(targets=np.array([[0.5 * k, 0.5 * k, 0.1 * k]]))
+    if patchy:
+        p = p.with_(n_coarse=(17, 17, 1))
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    assert np.all(np.isinf(u)) and np.all(lab == -1)
+    ref = oracle.patchy_solve(p, tol=1e-12) if patchy else oracle.global_solve(p, tol=1e-12)
+    assert np.all(np.isinf(ref.u))
+
+
+def test_smallest_3d_grid(pkg):
+    """3 x 3 x 3: one interior node, which is the target."""
+    p = W.sin3d(0, n=3, n_coarse=3, n_targets=1, radius=0.1).with_(
+        targets=np.array([[0.0, 0.0, 0.0, 0.1]]), n_coarse=None)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.global_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    assert u[13] == 0.0
