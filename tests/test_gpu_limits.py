@@ -102,3 +102,50 @@ def test_smallest_3d_grid(pkg):
     ref = oracle.global_solve(p, tol=1e-12)
     _assert_values(u, ref.u)
     assert u[13] == 0.0
+
+
+def test_256_controls_3d_global(pkg):
+    p = W.sin3d(1, n=21, n_coarse=9, n_c=256, n_targets=2, radius=0.2).with_(n_coarse=None)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.global_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+
+
+@pytest.mark.parametrize("patchy", [False, True])
+def test_non_square_grid_2d(pkg, patchy):
+    """Different node counts per axis at equal spacing: [-2, 2] x [-1, 1.5]
+    with 129 x 81 nodes (x fastest), targets placed inside."""
+    p = W.sincos2d(2, n=129, n_coarse=33, n_targets=2, radius=0.12).with_(
+        n=(129, 81, 1), hi=(2.0, 1.5, 0.0), lo=(-2.0, -1.0, 0.0),
+        targets=np.array([[1.0, 0.5, 0.12], [-0.8, -0.3, 0.12]]))
+    p = p.with_(n_coarse=(33, 21, 1) if patchy else None)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.patchy_solve(p, tol=1e-12) if patchy else oracle.global_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    if patchy:
+        assert np.mean(lab == ref.labels) >= 0.999
+
+
+@pytest.mark.parametrize("patchy", [False, True])
+def test_non_square_grid_3d(pkg, patchy):
+    p = W.sin3d(3, n=33, n_coarse=9, n_c=26, n_targets=2, radius=0.15).with_(
+        n=(33, 25, 21), lo=(-1.0, -1.0, -1.0), hi=(1.0, 0.5, 0.25),
+        targets=np.array([[0.4, -0.3, -0.2, 0.15], [-0.5, 0.1, 0.0, 0.15]]))
+    p = p.with_(n_coarse=(9, 7, 6) if patchy else None)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.patchy_solve(p, tol=1e-12) if patchy else oracle.global_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    if patchy:
+        assert np.mean(lab == ref.labels) >= 0.999
+
+
+def test_64_patches_3d(pkg):
+    p = W.eikonal3d(n=33, n_coarse=17, n_c=26, split="sectors", parts=64)
+    st, u, lab = _run(pkg, p)
+    assert st == 0
+    ref = oracle.patchy_solve(p, tol=1e-12)
+    _assert_values(u, ref.u)
+    assert np.mean(lab == ref.labels) >= 0.999
