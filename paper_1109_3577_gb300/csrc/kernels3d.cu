@@ -942,19 +942,24 @@ __global__ void __launch_bounds__(kT3n) k_tile_dirs3d(Grid3 g, const int8_t *__r
 
 // dlit (optional): the literal interpolation, +inf where a positive-weight
 // coarse corner is +inf (the Dirichlet data of Eq. dbc, R16).
+// u0f (optional): an FP32 copy of U0 (+inf as the FP32 sentinel) for the
+// FP32 filter of the feedback, so that it converts nothing (conversions run
+// on the FP64 pipe).
 __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, const double *__restrict__ uc,
-                        double *__restrict__ u0, double *__restrict__ dlit) {
+                        double *__restrict__ u0, double *__restrict__ dlit, float *__restrict__ u0f = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
         if (c >= kTargetBase) {
             u0[i] = 0.0;
             if (dlit) dlit[i] = 0.0;
+            if (u0f) u0f[i] = 0.f;
             continue;
         }
         if (c < 0) {
             u0[i] = Num<double>::big();
             if (dlit) dlit[i] = Num<double>::big();
+            if (u0f) u0f[i] = Num<float>::big();
             continue;
         }
         const int ix = (int)(i % g.n0);
@@ -987,6 +992,7 @@ __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, cons
         }
         if (dlit) dlit[i] = inf_corner ? Num<double>::big() : sum;
         u0[i] = sum >= kU0Bound ? Num<double>::big() : sum;
+        if (u0f) u0f[i] = sum >= kU0Bound ? Num<float>::big() : (float)sum;
     }
 }
 
@@ -998,7 +1004,7 @@ __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, cons
 // FP64 pass finds; exact FP64 ties go to the lowest caller index.
 __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
                              const double *__restrict__ u0, uint8_t *__restrict__ astar,
-                             const CtlLit3 *__restrict__ cl) {
+                             const CtlLit3 *__restrict__ cl, const float *__restrict__ u0f) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
     // the weights in shared memory, loaded as 16-byte vectors
@@ -1017,7 +1023,7 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t c = code[i];
-        if (c < 0 || c >= kTargetBase || u0[i] >= Num<double>::thresh()) {
+        if (c < 0 || c >= kTargetBase || u0f[i] >= Num<float>::thresh()) {
             astar[i] = kNoControl;
             continue;
         }
@@ -1026,46 +1032,58 @@ __global__ void k_feedback3d(Grid3 g, const int8_t *__restrict__ code, const dou
         // on the FP32 value: FP64 compares and conversions run at 1/64 rate);
         // the rare FP64 candidates re-read their corners.
         float nf[3][3][3];
-        float amax = 0.f;
 #pragma unroll
         for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx) {
-                    const float f = (float)u0[i + (dz - 1) * sz + (dy - 1) * sy + (dx - 1)];
-                    const bool fin = f < Num<float>::thresh();   // U0 is finite below 1e6, +inf is 1e300
-                    nf[dz][dy][dx] = fin ? f : Num<float>::big();
-                    if (fin) amax = fmaxf(amax, fabsf(f));
+                    const float f = u0f[i + (dz - 1) * sz + (dy - 1) * sy + (dx - 1)];
+                    nf[dz][dy][dx] = f < Num<float>::thresh() ? f : Num<float>::big();   // U0 is finite below 1e6
                 }
         const double hh = h[i];
         const float hf = (float)hh;
-        float b32 = Num<float>::big();
+        // FP32 evaluation error of a control of octant o: at most 2^-18 (h +
+        // max |U0| over its corners); per octant, so that the bound M of U0
+        // near the ghost ring (R7) widens only the octants that touch it
+        float eo[8];
+        float b32 = Num<float>::big(), eb = 0.f;
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
             float c8[8];
+            float am = 0.f;
 #pragma unroll
-            for (int b = 0; b < 8; ++b) c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
+            for (int b = 0; b < 8; ++b) {
+                c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
+                if (c8[b] < Num<float>::thresh()) am = fmaxf(am, fabsf(c8[b]));
+            }
+            eo[o] = ldexpf(hf + am, -18);
             for (int m = obeg[o]; m < obeg[o + 1]; ++m) {
                 float w[8];
                 load_w3(wf[m], w);
                 float v = hf;
 #pragma unroll
                 for (int b = 0; b < 8; ++b) v = fmaf(w[b], c8[b], v);
-                b32 = v < b32 ? v : b32;
+                if (v < b32) {
+                    b32 = v;
+                    eb = eo[o];
+                }
             }
         }
         double best = Num<double>::big();
         int arg = kNoControl;
         if (b32 < Num<float>::thresh()) {
-            const float lim = b32 + ldexpf(hf + amax, -17);
+            // a control can be the FP64 minimum (or tie with it) only if its FP32
+            // value minus its bound is at most b32 plus the bound of b32's control
+            const float base = b32 + eb;
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
                 const int ox = (o & 1) ? 2 : 0, oy = (o & 2) ? 2 : 0, oz = (o & 4) ? 2 : 0;
                 float c8[8];
 #pragma unroll
                 for (int b = 0; b < 8; ++b) c8[b] = nf[(b & 4) ? oz : 1][(b & 2) ? oy : 1][(b & 1) ? ox : 1];
+                const float lim = base + eo[o];
                 for (int m = obeg[o]; m < obeg[o + 1]; ++m) {
                     float w[8];
                     load_w3(wf[m], w);
@@ -2174,14 +2192,15 @@ hjbp_status solve3d(hjbp_plan &p) {
         if (!rc.converged) status = HJBP_ENOCONV;
         Ev3 e2(st);
         if (d.flags & HJBP_FLAG_DIRICHLET) dlit = alloc3<double>(p, N);
-        k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0, dlit);
+        float *u0f = per_node ? nullptr : alloc3<float>(p, N);
+        k_u0_3d<<<grid_for3(N), 256, 0, st>>>(g, gc, code0, p.u_coarse, p.u0, dlit, u0f);
         if (per_node) {
             k_feedback3g<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, p.u0, p.astar, gfine);
         } else {
             const CtlLit3 hl = make_lit3(p);
             CtlLit3 *dl = static_cast<CtlLit3 *>(p.dev_alloc(sizeof(CtlLit3)));
             check_cuda(cudaMemcpyAsync(dl, &hl, sizeof(CtlLit3), cudaMemcpyHostToDevice, st), "feedback table");
-            k_feedback3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, dl);
+            k_feedback3d<<<grid_for3(N, 128), 128, 0, st>>>(g, code0, h64, p.u0, p.astar, dl, u0f);
         }
         S.kernel_launches += 2;
         check_cuda(cudaGetLastError(), "feedback3");
