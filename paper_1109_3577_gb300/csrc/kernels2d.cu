@@ -1475,16 +1475,28 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
         // is within 8 units in the last place of (h + max |U|) of its FP64
         // value; the margin 2^-18 (h + max |U|) is twice that bound.
         float nf[3][3];
-        float amax = 0.f;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
                 const bool fin = nb[dy][dx] < Num<double>::thresh();
                 nf[dy][dx] = fin ? (float)nb[dy][dx] : Num<float>::big();
-                if (fin) amax = fmaxf(amax, fabsf((float)nb[dy][dx]));
             }
         const float hf = (float)hh;
+        // the bound per quadrant (half the margin above, over the quadrant's
+        // own corners), so that the bound M of U0 near the ghost ring (R7)
+        // widens only the quadrants that touch it
+        float eq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+            const float c4[4] = {nf[1][1], nf[1][sx], nf[sy][1], nf[sy][sx]};
+            float am = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (c4[b] < Num<float>::thresh()) am = fmaxf(am, fabsf(c4[b]));
+            eq[q] = ldexpf(hf * cl.hfmax + am, -19);
+        }
         // corner values by quadrant, selected without indexing (registers)
         auto corners32 = [&](int m, float &a10, float &a01, float &a11) {
             const bool px = cl.sx[m] > 0, py = cl.sy[m] > 0;
@@ -1492,23 +1504,28 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
             a01 = py ? nf[2][1] : nf[0][1];
             a11 = px ? (py ? nf[2][2] : nf[0][2]) : (py ? nf[2][0] : nf[0][0]);
         };
-        float b32 = Num<float>::big();
+        float b32 = Num<float>::big(), eb = 0.f;
         for (int m = 0; m < cl.nc; ++m) {
             float a10, a01, a11;
             corners32(m, a10, a01, a11);
             const float v = cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf * cl.hff[m];
-            b32 = v < b32 ? v : b32;
+            if (v < b32) {
+                b32 = v;
+                eb = eq[(cl.sx[m] > 0 ? 1 : 0) + (cl.sy[m] > 0 ? 2 : 0)];
+            }
         }
         double best = Num<double>::big();
         int arg = kNoControl;
         if (b32 < Num<float>::thresh()) {
-            const float lim = b32 + ldexpf(hf * cl.hfmax + amax, -18);
+            // a control can be the FP64 minimum (or tie with it) only if its FP32
+            // value minus its bound is at most b32 plus the bound of b32's control
+            const float base = b32 + eb;
             for (int m = 0; m < cl.nc; ++m) {
                 float a10, a01, a11;
                 corners32(m, a10, a01, a11);
                 const float v32 =
                     cl.f00[m] * nf[1][1] + cl.f10[m] * a10 + cl.f01[m] * a01 + cl.f11[m] * a11 + hf * cl.hff[m];
-                if (v32 > lim) continue;
+                if (v32 > base + eq[(cl.sx[m] > 0 ? 1 : 0) + (cl.sy[m] > 0 ? 2 : 0)]) continue;
                 const bool px = cl.sx[m] > 0, py = cl.sy[m] > 0;
                 const double d10 = px ? nb[1][2] : nb[1][0];
                 const double d01 = py ? nb[2][1] : nb[0][1];
