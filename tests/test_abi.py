@@ -91,3 +91,26 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding, "_LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         _binding.library()
+
+
+def test_autotune_reads_its_cache_file_without_a_gpu(lib, tmp_path):
+    """A problem class already in the cache file is answered from it, with no
+    solve (so no GPU): the class key is (dim, round(log2(cells per side)),
+    round(log2(controls)), patchy, options)."""
+    import math
+
+    import paper_1109_3577_gb300 as pkg
+    import workloads as W
+
+    p = W.sincos2d(0, n=513, n_coarse=33, n_c=48)
+    d, keep = pkg.desc_from_problem(p, flags=pkg.HJBP_FLAG_WARM_START)
+    key = (2, round(math.log2(512)), round(math.log2(48)), 1, pkg.HJBP_FLAG_WARM_START)
+    path = tmp_path / "tune.txt"
+    path.write_text("%d %d %d %d %d 3 4 0 0\n" % key)
+    tune, cached = pkg.hjbp_autotune(d, 0, str(path))
+    assert cached and tune == [3, 4, 0, 0]
+    # a NULL descriptor or output is EINVAL (1), not a crash
+    fn = lib.hjbp_autotune
+    fn.argtypes = [ctypes.c_void_p] * 5
+    fn.restype = ctypes.c_int
+    assert fn(None, None, None, None, None) == 1
