@@ -230,3 +230,20 @@ def test_reduced_controls_never_lower_the_value(dirichlet):
     assert np.all(fa[fb])
     assert np.all(b.u[fb] >= a.u[fb] - 1e-12)
     assert np.array_equal(a.labels, b.labels)
+
+
+def test_addons_in_3d():
+    """The add-ons on a 3D problem: r = 1 keeps every control (bitwise), r = 4
+    never lowers a value and keeps the labels, AO1 and AO2 reach the basic
+    fixed point."""
+    p = _small(2, n=21, nc=7, R=2, radius=0.25, dim=3)
+    a = oracle.patchy_solve(p, tol=1e-13)
+    assert np.array_equal(a.u, oracle.patchy_solve(p, tol=1e-13, reduce_r=1.0).u)
+    b = oracle.patchy_solve(p, tol=1e-13, reduce_r=4.0)
+    fa, fb = np.isfinite(a.u), np.isfinite(b.u)
+    assert np.all(fa[fb]) and np.all(b.u[fb] >= a.u[fb] - 1e-12)
+    assert np.array_equal(a.labels, b.labels)
+    for kw in ({"warm": True}, {"causal": True}):
+        r = oracle.patchy_solve(p, tol=1e-13, **kw)
+        assert np.array_equal(np.isfinite(r.u), fa), kw
+        np.testing.assert_allclose(r.u[fa], a.u[fa], rtol=0, atol=1e-10, err_msg=str(kw))
