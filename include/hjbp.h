@@ -324,15 +324,19 @@ hjbp_status hjbp_autotune(const hjbp_problem_desc *desc, void *cuda_stream, cons
 
 /* Serving.  A server owns a pool of `workers` threads (<= 0 selects 8) with
  * their own streams and a device-memory budget (0 selects half of the free
- * memory).  submit validates and copies a problem, estimates the device bytes
- * its solve needs, and queues it; EBUSY if it can never fit the budget.  A
- * queued request starts as soon as a worker is idle and its bytes fit next to
- * the requests in flight (continuous batching).  poll returns OK with
- * *done = NULL while the request is queued or running; once finished it hands
- * over the plan (values and labels resident on the device; the caller
- * destroys it), returns that solve's status and the latency from submit to
- * completion in seconds.  destroy waits for running requests, drops queued
- * ones and destroys plans nobody collected.                                  */
+ * memory).  submit validates and copies a problem (EINVAL as hjbp_create),
+ * estimates the device bytes its solve needs, and queues it; EBUSY if it can
+ * never fit the budget.  A queued request holds no device memory.  It starts
+ * as soon as a worker is idle and its bytes fit next to the requests in
+ * flight (continuous batching); that worker creates the plan and solves it.
+ * poll returns OK with *done = NULL while the request is queued or running;
+ * once finished it hands over the plan (values and labels resident on the
+ * device; the caller destroys it), returns that solve's status and the
+ * latency from submit to completion in seconds.  A request whose plan could
+ * not be created finishes with the create's status (ENOMEM, ECUDA) and
+ * *done = NULL; hjbp_last_error then gives its message in the polling
+ * thread.  destroy waits for running requests, drops queued ones and destroys
+ * plans nobody collected.                                                    */
 typedef struct hjbp_server hjbp_server;
 hjbp_status hjbp_server_create(size_t device_budget_bytes, int workers, hjbp_server **out);
 hjbp_status hjbp_server_submit(hjbp_server *server, const hjbp_problem_desc *desc, uint64_t *ticket);

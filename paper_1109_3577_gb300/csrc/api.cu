@@ -69,7 +69,10 @@ static hjbp_status fail(hjbp_status s, const std::string &msg) {
     return s;
 }
 
-static std::string validate(const hjbp_problem_desc *d) {
+// The descriptor checks of hjbp_create, host arithmetic only ("" when valid);
+// the server runs them at submit, before it queues a request.
+namespace hjbp {
+std::string validate_desc(const hjbp_problem_desc *d) {
     if (!d) return "descriptor is NULL";
     if (d->dim != 2 && d->dim != 3) return "dim must be 2 or 3";
     for (int a = 0; a < d->dim; ++a) {
@@ -128,6 +131,15 @@ static std::string validate(const hjbp_problem_desc *d) {
         if (d->speed != HJBP_C_ONE) return "drift dynamics take the speed field HJBP_C_ONE";
         for (int a = 0; a < 4; ++a)
             if (!std::isfinite(d->drift[a])) return "drift not finite";
+        if (d->controls)
+            for (int m = 0; m < d->n_controls; ++m) {
+                double n2 = 0.0;
+                for (int c = 0; c < d->dim; ++c) {
+                    const double f = d->drift[0] * d->controls[m * d->dim + c] + d->drift[1 + c];
+                    n2 += f * f;
+                }
+                if (!(std::sqrt(n2) > 1e-15)) return "a control has zero velocity under the drift";
+            }
     }
     if (!d->targets) return "targets is NULL";
     for (int j = 0; j < d->n_targets; ++j)
@@ -150,6 +162,7 @@ static std::string validate(const hjbp_problem_desc *d) {
     }
     return "";
 }
+}  // namespace hjbp
 
 extern "C" {
 
@@ -163,7 +176,7 @@ hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const 
                         hjbp_plan **out) {
     if (!out) return fail(HJBP_EINVAL, "out is NULL");
     *out = nullptr;
-    const std::string err = validate(desc);
+    const std::string err = hjbp::validate_desc(desc);
     if (!err.empty()) return fail(HJBP_EINVAL, err);
     hjbp_plan *p = new (std::nothrow) hjbp_plan();
     if (!p) return fail(HJBP_ENOMEM, "host allocation failed");

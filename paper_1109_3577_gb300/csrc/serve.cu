@@ -5,11 +5,13 @@
 // runs their solves concurrently, so that problems too small to fill the GPU
 // (the batched family has sides of 65..513 nodes) overlap on the device.
 //
-// The server keeps requests in a queue, admits them while the device memory
-// they need fits in a budget (continuous batching: a request starts as soon as
-// a worker and enough memory are free, while others are still running), runs
-// them on the same kind of worker pool, and keeps each finished plan (values
-// and labels resident on the device) until the caller collects it.
+// The server keeps requests in a queue as validated copies of their
+// descriptors, holding no device memory, and admits them while the device
+// memory they need fits in a budget (continuous batching: a request starts as
+// soon as a worker and enough memory are free, while others are still
+// running).  The admitting worker creates the plan, so its device arrays are
+// allocated only then, solves it, and the finished plan (values and labels
+// resident on the device) waits until the caller collects it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,7 +30,9 @@
 #include "plan.h"
 
 namespace hjbp {
+void set_last_error(const std::string &msg);
 void set_last_error_static(const char *msg);
+std::string validate_desc(const hjbp_problem_desc *d);
 }
 
 namespace {
@@ -109,11 +113,14 @@ struct hjbp_server {
     bool stopping = false;
     uint64_t next_ticket = 1;
     struct Req {
-        uint64_t ticket;
-        hjbp_plan *plan;
-        size_t bytes;
-        hjbp_status status;
-        double t_submit, t_start, t_done;
+        uint64_t ticket = 0;
+        hjbp_problem_desc desc{};          // copy; its arrays point into the vectors below
+        std::vector<double> controls, targets, obstacles;
+        hjbp_plan *plan = nullptr;         // created by the admitting worker
+        size_t bytes = 0;
+        hjbp_status status = HJBP_EBUSY;
+        std::string error;                 // message of a failed create or solve
+        double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
     };
     std::deque<uint64_t> queue;               // admitted order (FIFO)
     std::map<uint64_t, Req> reqs;             // every live request
@@ -134,8 +141,7 @@ void worker_loop(hjbp_server *S) {
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (;;) {
-        uint64_t t = 0;
-        hjbp_plan *plan = nullptr;
+        hjbp_server::Req *req = nullptr;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             // first queued request whose memory fits now (FIFO among those that fit)
@@ -147,24 +153,31 @@ void worker_loop(hjbp_server *S) {
                 for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
                     auto &r = S->reqs[*it];
                     if (S->in_use + r.bytes <= S->budget || S->in_use == 0) {
-                        t = *it;
-                        plan = r.plan;
+                        req = &r;
                         S->in_use += r.bytes;
                         r.t_start = now_s();
                         S->queue.erase(it);
                         break;
                     }
                 }
-                if (plan) break;
+                if (req) break;
                 S->cv.wait(lk);
             }
         }
-        const hjbp_status st = solve_on(plan, s);
+        // The request is running: nobody else touches it until t_done is set
+        // (poll only takes finished requests, destroy waits for running ones).
+        // Plans are created on the legacy stream and synchronised; the worker
+        // runs the solve on its own stream.
+        hjbp_plan *plan = nullptr;
+        hjbp_status st = hjbp_create(&req->desc, nullptr, nullptr, &plan);
+        if (st == HJBP_OK) st = solve_on(plan, s);
+        const std::string err = st == HJBP_OK ? std::string() : std::string(hjbp_last_error());
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            auto &r = S->reqs[t];
-            r.status = st;
-            r.t_done = now_s();
+            req->plan = plan;
+            req->status = st;
+            req->error = err;
+            req->t_done = now_s();
         }
         S->cv.notify_all();
     }
@@ -217,21 +230,38 @@ extern "C" hjbp_status hjbp_server_submit(hjbp_server *S, const hjbp_problem_des
         hjbp::set_last_error_static("NULL argument");
         return HJBP_EINVAL;
     }
+    const std::string err = hjbp::validate_desc(desc);
+    if (!err.empty()) {
+        hjbp::set_last_error(err);
+        return HJBP_EINVAL;
+    }
     const size_t bytes = footprint(desc);
     if (bytes > S->budget) {
         hjbp::set_last_error_static("request needs more device memory than the server budget");
         return HJBP_EBUSY;
     }
-    hjbp_plan *plan = nullptr;
-    // plans are created on the legacy stream and synchronised; workers run them on their own streams
-    const hjbp_status st = hjbp_create(desc, nullptr, nullptr, &plan);
-    if (st != HJBP_OK) return st;
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        const uint64_t t = S->next_ticket++;
-        S->reqs[t] = hjbp_server::Req{t, plan, bytes, HJBP_EBUSY, now_s(), 0.0, 0.0};
-        S->queue.push_back(t);
-        *ticket = t;
+    try {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            const uint64_t t = S->next_ticket++;
+            auto &r = S->reqs[t];
+            r.ticket = t;
+            r.desc = *desc;
+            r.controls.assign(desc->controls, desc->controls + (size_t)desc->n_controls * desc->dim);
+            r.targets.assign(desc->targets, desc->targets + (size_t)desc->n_targets * (desc->dim + 1));
+            if (desc->n_obstacles > 0)
+                r.obstacles.assign(desc->obstacles, desc->obstacles + (size_t)desc->n_obstacles * 7);
+            r.desc.controls = r.controls.data();
+            r.desc.targets = r.targets.data();
+            r.desc.obstacles = r.obstacles.empty() ? nullptr : r.obstacles.data();
+            r.bytes = bytes;
+            r.t_submit = now_s();
+            S->queue.push_back(t);
+            *ticket = t;
+        }
+    } catch (const std::bad_alloc &) {
+        hjbp::set_last_error_static("host allocation failed");
+        return HJBP_ENOMEM;
     }
     S->cv.notify_all();
     return HJBP_OK;
@@ -251,9 +281,10 @@ extern "C" hjbp_status hjbp_server_poll(hjbp_server *S, uint64_t ticket, hjbp_pl
     }
     auto &r = it->second;
     if (r.t_done == 0.0) return HJBP_OK;  // still queued or running
-    *done = r.plan;
+    *done = r.plan;  // NULL when the plan could not be created
     if (latency_s) *latency_s = r.t_done - r.t_submit;
     const hjbp_status st = r.status;
+    if (st != HJBP_OK) hjbp::set_last_error(r.error);
     S->in_use -= r.bytes;
     S->reqs.erase(it);
     S->cv.notify_all();

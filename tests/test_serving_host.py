@@ -44,3 +44,35 @@ def test_batch_rejects_null_plan(P):
     with pytest.raises(P.HjbpError) as ei:
         P.hjbp_batch_solve([0, 0])
     assert ei.value.status == 1
+
+
+def test_failed_create_finishes_the_request_without_a_plan(P):
+    """Submit only validates and copies a request; the admitting worker creates
+    the plan.  Without a GPU that create fails, and the request finishes with
+    its status (the allocation's ENOMEM or ECUDA) and no plan, the message
+    carried to the polling thread."""
+    import time
+
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("needs a process without a GPU")
+    srv = P.hjbp_server_create(budget_bytes=1 << 30, workers=2)
+    try:
+        d, keep = P.desc_from_problem(W.sincos2d(0, n=65, n_coarse=17))
+        t = P.hjbp_server_submit(srv, d)
+        del d, keep                              # the server holds its own copy
+        t0 = time.time()
+        while True:
+            try:
+                st, h, _ = P.hjbp_server_poll(srv, t)
+            except P.HjbpError as e:
+                assert e.status in (2, 5)           # ENOMEM / ECUDA
+                assert "cudaMalloc" in str(e) or "CUDA" in str(e), str(e)
+                break
+            assert h is None and st == 0
+            assert time.time() - t0 < 60
+            time.sleep(0.01)
+        assert P.hjbp_server_stats(srv) == (0, 0, 0)
+    finally:
+        P.hjbp_server_destroy(srv)
