@@ -90,11 +90,19 @@ def profile_traffic():
 
 
 class Clocks:
-    """nvidia-smi sampling (200 ms) while the timed region runs."""
+    """nvidia-smi sampling (200 ms) while the timed region runs.  ``first`` is
+    set once nvidia-smi has printed its first sample, i.e. once its start-up,
+    which competes with the solve's host round trips, is over."""
 
     def __init__(self):
         self.proc = None
         self.lines = []
+        self.first = threading.Event()
+        self.start = 0
+
+    def mark(self):
+        """Start of the timed region: the summary prefers the samples after it."""
+        self.start = len(self.lines)
 
     def __enter__(self):
         try:
@@ -113,6 +121,8 @@ class Clocks:
     def _read(self):
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
+            self.first.set()
+        self.first.set()
 
     def __exit__(self, *a):
         if self.proc:
@@ -123,8 +133,18 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self, device: int = 0):
+        out = self._summary(self.lines[self.start:], device)
+        if out["samples"]:
+            out["window"] = "timed region"
+            return out
+        out = self._summary(self.lines, device)
+        out["window"] = "warm-up and timed region"
+        return out
+
+    @staticmethod
+    def _summary(lines, device):
         sm, mx, reasons = [], [], set()
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9 or f[0] != str(device):
                 continue
@@ -255,16 +275,22 @@ def run_ours(args, rank, world, dist):
     tune = [int(v) for v in args.tune.split(",")] if args.tune else None
     plan = P.Plan(p, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS | aflags,
                   reduce_r=args.reduce_r, tune=tune)
-    for _ in range(args.warmup):
-        plan.solve()
-    torch.cuda.synchronize()
-
     st = torch.cuda.current_stream()
     ms_steps, stats = [], []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # the sampler starts with the warm-up, which goes on (untimed, at most 5 s
+    # more) until nvidia-smi's first sample: its start-up stays out of the
+    # timed region and every sample is taken under load
     with Clocks() as clk:
+        for _ in range(args.warmup):
+            plan.solve()
+        t_w = time.perf_counter()
+        while clk.proc is not None and not clk.first.is_set() and time.perf_counter() - t_w < 5.0:
+            plan.solve()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark()
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
