@@ -76,6 +76,8 @@ def test_create_rejects_bad_descriptors(lib):
         (p.with_(controls=W.controls_2d(128)), {"reduce_r": 4.0}),
         # cones are defined on unit controls
         (W.brockett3d(n=17, n_coarse=9), {"reduce_r": 4.0}),
+        # s = 2 against the wind w = (2, 0): the control (-1, 0) cannot move
+        (W.zermelo(n=33, n_coarse=9, n_c=8, parts=4, s=2.0), {}),
     ]
     for q, kw in bad_opts:
         d, keep = pkg.desc_from_problem(q, **kw)

@@ -32,10 +32,13 @@ def test_admission_refuses_oversized_request(P):
 def test_malformed_request_is_rejected(P):
     srv = P.hjbp_server_create(budget_bytes=1 << 30, workers=1)
     try:
-        d, keep = P.desc_from_problem(W.sincos2d(0, n=65, n_coarse=17).with_(tol=-1.0))
-        with pytest.raises(P.HjbpError) as ei:
-            P.hjbp_server_submit(srv, d)
-        assert ei.value.status == 1          # EINVAL
+        for q in (W.sincos2d(0, n=65, n_coarse=17).with_(tol=-1.0),
+                  W.zermelo(n=33, n_coarse=9, n_c=8, parts=4, s=2.0)):   # a control that cannot move
+            d, keep = P.desc_from_problem(q)
+            with pytest.raises(P.HjbpError) as ei:
+                P.hjbp_server_submit(srv, d)
+            assert ei.value.status == 1      # EINVAL
+        assert P.hjbp_server_stats(srv) == (0, 0, 0)
     finally:
         P.hjbp_server_destroy(srv)
 
