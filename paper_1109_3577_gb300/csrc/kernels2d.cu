@@ -124,142 +124,6 @@ __device__ __forceinline__ int warp_sum(int v) {
     return v;
 }
 
-// Shared-memory image of one tile plus its halo.
-template <typename T> struct TileSmem {
-    T u[kTile + 2][kTile + 3];
-    int8_t c[kTile + 2][kTile + 4];
-};
-
-template <typename T, class S>
-__device__ __forceinline__ void load_tile(const Grid2 &g, const TileSched &s, const int8_t *__restrict__ code,
-                                          const T *__restrict__ b0, const T *__restrict__ b1, int x0, int y0,
-                                          S &sm) {
-    const int lane = threadIdx.x;
-    for (int r = 0; r < kTile + 2; ++r) {
-        const int y = y0 - 1 + r;
-        for (int c = lane; c < kTile + 2; c += 32) {
-            const int x = x0 - 1 + c;
-            T v = Num<T>::big();
-            int8_t cd = kHard;
-            if (x < g.n0 && y < g.n1) {
-                const int64_t i = (int64_t)y * g.n0 + x;
-                cd = code[i];
-                const int tt = tile_of(g, x, y);
-                v = (tt >= 0 && s.latest[tt]) ? b1[i] : b0[i];
-            }
-            sm.u[r][c] = v;
-            sm.c[r][c] = cd;
-        }
-    }
-    __syncwarp();
-}
-
-// Write the tile's interior to the buffer that is not current, return the
-// warp's max |new - old| (0 where both are +inf).
-template <typename T, class S>
-__device__ __forceinline__ float store_tile(const Grid2 &g, const TileSched &s, int t, T *__restrict__ b0,
-                                            T *__restrict__ b1, int x0, int y0, const S &sm) {
-    const int lane = threadIdx.x;
-    const int cur = s.latest[t];
-    T *dst = cur ? b0 : b1;
-    const T *src = cur ? b1 : b0;
-    float mc = 0.f;
-    const int x = x0 + lane;
-    for (int r = 1; r <= kTile; ++r) {
-        const int y = y0 - 1 + r;
-        if (y > g.n1 - 2) break;
-        if (x > g.n0 - 2) continue;
-        const int64_t i = (int64_t)y * g.n0 + x;
-        const T v = sm.u[r][1 + lane];
-        const T o = src[i];
-        dst[i] = v;
-        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-        float d;
-        if (vi && oi) d = 0.f;
-        else if (vi || oi) d = 3.0e38f;
-        else d = (float)fabs((double)v - (double)o);
-        mc = fmaxf(mc, d);
-    }
-    return warp_max(mc);
-}
-
-// --------------------------------------------------- value sweep (a6, a0) --
-
-// Self-solved SL update (R13) of node (c, r) of the tile for patch code cd:
-//   min over controls of kap (w10 u10 + w01 u01 + w11 u11 + h_i);
-// neighbours outside patch cd and its target part read +inf.  Returns the
-// +inf sentinel when no control has all its positive-weight corners finite.
-// Four independent minimum accumulators keep the FMA chains of different
-// controls in flight together.
-template <typename T>
-__device__ __forceinline__ T sl_update(const TileSmem<T> &sm, int c, int r, int8_t cd, T hh,
-                                       const CtlTable2<T> &ct) {
-    const int8_t tg = (int8_t)(cd + kTargetBase);
-    T nb[3][3];
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-            const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
-            nb[dy][dx] = (q == cd || q == tg) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
-        }
-    T b0 = Num<T>::big(), b1 = Num<T>::big(), b2 = Num<T>::big(), b3 = Num<T>::big();
-    if (ct.d4) {
-        T E[4], G[4], A[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
-            const T a10 = nb[1][sx], a01 = nb[sy][1];
-            E[q] = a10 + a01;
-            G[q] = fabs(a10 - a01);
-            A[q] = nb[sy][sx];
-        }
-        for (int k = 0; k < ct.ncls; ++k) {
-            const T kh = ct.cls_kap[k] * hh;
-            const T s = ct.cls_s[k], t = -ct.cls_t[k], w = ct.cls_kw11[k];
-            T v0 = fma(t, G[0], fma(s, E[0], fma(w, A[0], kh)));
-            T v1 = fma(t, G[1], fma(s, E[1], fma(w, A[1], kh)));
-            T v2 = fma(t, G[2], fma(s, E[2], fma(w, A[2], kh)));
-            T v3 = fma(t, G[3], fma(s, E[3], fma(w, A[3], kh)));
-            b0 = v0 < b0 ? v0 : b0;
-            b1 = v1 < b1 ? v1 : b1;
-            b2 = v2 < b2 ? v2 : b2;
-            b3 = v3 < b3 ? v3 : b3;
-        }
-        if (ct.axis) {
-            const T ax = fmin(fmin(nb[1][0], nb[1][2]), fmin(nb[0][1], nb[2][1])) + hh;
-            b0 = ax < b0 ? ax : b0;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
-            const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
-            int m = ct.qbeg[q];
-            const int me = ct.qbeg[q + 1];
-            for (; m + 3 < me; m += 4) {
-                const T v0 = fma(ct.kw11[m], a11, fma(ct.kw01[m], a01, fma(ct.kw10[m], a10, ct.kap[m] * hh)));
-                const T v1 =
-                    fma(ct.kw11[m + 1], a11, fma(ct.kw01[m + 1], a01, fma(ct.kw10[m + 1], a10, ct.kap[m + 1] * hh)));
-                const T v2 =
-                    fma(ct.kw11[m + 2], a11, fma(ct.kw01[m + 2], a01, fma(ct.kw10[m + 2], a10, ct.kap[m + 2] * hh)));
-                const T v3 =
-                    fma(ct.kw11[m + 3], a11, fma(ct.kw01[m + 3], a01, fma(ct.kw10[m + 3], a10, ct.kap[m + 3] * hh)));
-                b0 = v0 < b0 ? v0 : b0;
-                b1 = v1 < b1 ? v1 : b1;
-                b2 = v2 < b2 ? v2 : b2;
-                b3 = v3 < b3 ? v3 : b3;
-            }
-            for (; m < me; ++m) {
-                const T v = fma(ct.kw11[m], a11, fma(ct.kw01[m], a01, fma(ct.kw10[m], a10, ct.kap[m] * hh)));
-                b0 = v < b0 ? v : b0;
-            }
-        }
-    }
-    const T b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
-    return b01 < b23 ? b01 : b23;
-}
-
 // Tile image for the value sweep: values and codes with the halo, plus h and
 // a 9-bit usability mask per interior node (bit 3 dy + dx set when the
 // neighbour (dx-1, dy-1) belongs to the node's patch or its target part;
@@ -273,11 +137,16 @@ template <typename T, bool kDir> struct TileSmemV {
     T d[kDir ? kTile + 2 : 1][kDir ? kTile + 3 : 1];  // Dirichlet data of the halo image (Eq. dbc)
 };
 
-// The update of sl_update with the neighbourhood masked by a precomputed
-// mask; NCLS > 0 fully unrolls the symmetric form for a table with exactly
-// NCLS classes (every class then sits in the constant bank as immediates).
-// A neighbour outside the mask reads +inf (state constraints) or, with kDir,
-// its fixed Dirichlet value (Eq. dbc).
+// Self-solved SL update (R13) of node (c, r) of the tile:
+//   min over controls of kap (w10 u10 + w01 u01 + w11 u11 + h_i),
+// the neighbourhood masked by the node's precomputed usability mask: a
+// neighbour outside the mask reads +inf (state constraints) or, with kDir,
+// its fixed Dirichlet value (Eq. dbc).  Returns the +inf sentinel when no
+// control has all its positive-weight corners finite.  Four independent
+// minimum accumulators keep the FMA chains of different controls in flight
+// together; NCLS > 0 fully unrolls the symmetric form for a table with
+// exactly NCLS classes (every class then sits in the constant bank as
+// immediates).
 template <typename T, int NCLS, bool kDir, class S>
 __device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct) {
     T nb[3][3];
