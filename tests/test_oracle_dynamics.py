@@ -382,3 +382,47 @@ def test_brockett_symmetries_and_axis():
     x1 = -2.0 + 4.0 * np.arange(n) / (n - 1)
     axis = U[n // 2, n // 2, 1:-1]
     np.testing.assert_allclose(axis, np.maximum(np.abs(x1[1:-1]) - 0.25, 0.0) / 5.0, rtol=0, atol=1e-12)
+
+
+def _coarse_band(p, r):
+    """Coarse nodes in the widened target band of R6 (outside the ball, within
+    r + k~ sqrt(d)/2 of its centre, clear of the band's edges), with their
+    coordinates, gap to the ball and unit direction towards the centre."""
+    q = p.with_(n=p.n_coarse)
+    _, x = I.node_grid(q)
+    c, rad = p.targets[0][: p.dim], p.targets[0][p.dim]
+    dist = np.linalg.norm(x - c, axis=1)
+    edge = rad + q.spacing * math.sqrt(p.dim) / 2.0
+    band = (dist > rad + 1e-9) & (dist < edge - 1e-9)
+    e = (c - x[band]) / dist[band, None]
+    return band, x[band], dist[band] - rad, e, r.ucoarse[band]
+
+
+def test_coarse_boundary_values_follow_the_approach_speed():
+    """R6 and R24: the widened coarse target holds gap / v, v the largest
+    speed the dynamics allow towards the target.  Checked by the defining
+    property of v, not by its formula: for c(x) a, U c(x) = gap; for the
+    drift s a + w, v = gap / U is the largest speed with a unit control
+    (|v e - w| = s, and a larger v needs |a| > 1); for Brockett, v is the
+    largest |f(x, a)| over the controls."""
+    # speed field: sincos2d on the sectors problem
+    p = W.eikonal_sectors(n=65, n_coarse=17, parts=4).with_(speed="sincos2d", speed_params=W._params([0.5]))
+    band, x, gap, e, U = _coarse_band(p, oracle.patchy_solve(p, tol=1e-10))
+    assert band.sum() >= 8
+    np.testing.assert_allclose(U * I.speed_np(p, x), gap, rtol=1e-9, atol=0)
+    # Zermelo drift
+    p = W.zermelo(n=65, n_coarse=17, parts=4)
+    band, x, gap, e, U = _coarse_band(p, oracle.patchy_solve(p, tol=1e-10))
+    assert band.sum() >= 8
+    s, w = p.drift[0], np.array(p.drift[1:3])
+    v = gap / U
+    np.testing.assert_allclose(np.linalg.norm(v[:, None] * e - w, axis=1), s, rtol=1e-9)
+    assert np.all(np.linalg.norm((v + 1e-6)[:, None] * e - w, axis=1) > s)
+    # Brockett: the largest |(a1, a2, x1 a2 - x2 a1)|, through nodes off the x3 axis
+    p = W.brockett3d(n=17, n_coarse=9)
+    band, x, gap, e, U = _coarse_band(p, oracle.patchy_solve(p, tol=1e-10))
+    a = np.asarray(p.controls, float)[:, :2]
+    f3 = x[:, :1] * a[None, :, 1] - x[:, 1:2] * a[None, :, 0]
+    vmax = np.sqrt(a[None, :, 0] ** 2 + a[None, :, 1] ** 2 + f3 ** 2).max(axis=1)
+    assert band.sum() >= 6 and np.any(np.abs(x[:, :2]).max(axis=1) > 0)
+    np.testing.assert_allclose(U * vmax, gap, rtol=1e-9, atol=0)
