@@ -394,6 +394,9 @@ def _coarse_band(p, r):
     dist = np.linalg.norm(x - c, axis=1)
     edge = rad + q.spacing * math.sqrt(p.dim) / 2.0
     band = (dist > rad + 1e-9) & (dist < edge - 1e-9)
+    # the grids are chosen so that the band holds nodes farther than half a
+    # coarse cell from the ball: the widening is k~ sqrt(d) / 2, not k~ / 2
+    assert np.any(dist[band] > rad + q.spacing / 2.0 + 1e-9)
     e = (c - x[band]) / dist[band, None]
     return band, x[band], dist[band] - rad, e, r.ucoarse[band]
 
@@ -406,12 +409,12 @@ def test_coarse_boundary_values_follow_the_approach_speed():
     (|v e - w| = s, and a larger v needs |a| > 1); for Brockett, v is the
     largest |f(x, a)| over the controls."""
     # speed field: sincos2d on the sectors problem
-    p = W.eikonal_sectors(n=65, n_coarse=17, parts=4).with_(speed="sincos2d", speed_params=W._params([0.5]))
+    p = W.eikonal_sectors(n=81, n_coarse=21, parts=4).with_(speed="sincos2d", speed_params=W._params([0.5]))
     band, x, gap, e, U = _coarse_band(p, oracle.patchy_solve(p, tol=1e-10))
     assert band.sum() >= 8
     np.testing.assert_allclose(U * I.speed_np(p, x), gap, rtol=1e-9, atol=0)
     # Zermelo drift
-    p = W.zermelo(n=65, n_coarse=17, parts=4)
+    p = W.zermelo(n=81, n_coarse=21, parts=4)
     band, x, gap, e, U = _coarse_band(p, oracle.patchy_solve(p, tol=1e-10))
     assert band.sum() >= 8
     s, w = p.drift[0], np.array(p.drift[1:3])
@@ -419,7 +422,7 @@ def test_coarse_boundary_values_follow_the_approach_speed():
     np.testing.assert_allclose(np.linalg.norm(v[:, None] * e - w, axis=1), s, rtol=1e-9)
     assert np.all(np.linalg.norm((v + 1e-6)[:, None] * e - w, axis=1) > s)
     # Brockett: the largest |(a1, a2, x1 a2 - x2 a1)|, through nodes off the x3 axis
-    p = W.brockett3d(n=17, n_coarse=9)
+    p = W.brockett3d(n=21, n_coarse=11)
     band, x, gap, e, U = _coarse_band(p, oracle.patchy_solve(p, tol=1e-10))
     a = np.asarray(p.controls, float)[:, :2]
     f3 = x[:, :1] * a[None, :, 1] - x[:, 1:2] * a[None, :, 0]

@@ -143,3 +143,32 @@ def test_patchy_with_obstacles_invariants():
     fin = np.isfinite(g.u)
     assert np.array_equal(fin, np.isfinite(a.u))
     np.testing.assert_allclose(a.u[fin], g.u[fin], rtol=0, atol=1e-9)
+
+
+def test_enclosed_pocket_has_no_feedback():
+    """R7 with an unreachable region: a pocket enclosed by a box frame two
+    coarse cells thick holds no target, so its coarse values are +inf,
+    U_P^(0) = +inf there, no feedback is defined (a* = -1) and its nodes end
+    unlabelled at +inf.  The pocket comes from a flood fill over the free
+    nodes, independent of the scheme."""
+    frame = np.array([W.obstacle_box((-1.6, -1.6), (-1.2, 0.2)), W.obstacle_box((-0.2, -1.6), (0.2, 0.2)),
+                      W.obstacle_box((-1.2, -1.6), (-0.2, -1.2)), W.obstacle_box((-1.2, -0.2), (-0.2, 0.2))])
+    p = W.eikonal_obstacles(n=81, n_coarse=21, n_c=16).with_(
+        target_kind="balls", n_parts=0, targets=np.array([[1.2, 1.2, 0.3]]), obstacles=frame, tol=1e-10)
+    kind, _, _ = I.kinds(p)
+    n = p.n[0]
+    seen = kind == 1
+    stack = list(np.nonzero(seen)[0])
+    while stack:
+        i = stack.pop()
+        for j in (i - 1, i + 1, i - n, i + n):
+            if 0 <= j < kind.size and not seen[j] and kind[j] == 0:
+                seen[j] = True
+                stack.append(j)
+    pocket = (kind == 0) & ~seen
+    assert pocket.sum() >= 300
+    r = oracle.patchy_solve(p)
+    assert np.all(np.isinf(r.u0[pocket])) and np.all(r.astar[pocket] == -1)
+    assert np.all(r.labels[pocket] == -1) and np.all(np.isinf(r.u[pocket]))
+    # outside the pocket every free node reaches the target
+    assert np.all(np.isfinite(r.u[(kind == 0) & seen]))

@@ -452,3 +452,81 @@ def test_patchy_error_concentrates_on_patch_boundaries():
     E[fin] = np.abs(rp.u[fin] - rg.u[fin])
     assert near.mean() < 0.5
     assert E[near].sum() >= 0.95 * E.sum()
+
+
+def _q1_values(n, lo_idx, U, dim):
+    """Q1 interpolation of U (nodes per side n, +inf allowed) at grid-index
+    points lo_idx (M, dim): +inf where a positive-weight corner is +inf or
+    the point leaves the grid."""
+    n = np.asarray(n[:dim])
+    inside = np.all((lo_idx >= 0.0) & (lo_idx <= n - 1), axis=1)
+    base = np.clip(np.floor(lo_idx).astype(np.int64), 0, n - 2)
+    t = lo_idx - base
+    val = np.zeros(lo_idx.shape[0])
+    bad = ~inside
+    for bits in range(1 << dim):
+        w = np.ones(lo_idx.shape[0])
+        j = np.zeros(lo_idx.shape[0], np.int64)
+        mul = 1
+        for d in range(dim):
+            b = (bits >> d) & 1
+            w *= t[:, d] if b else 1.0 - t[:, d]
+            j += np.clip(base[:, d] + b, 0, n[d] - 1) * mul
+            mul *= n[d]
+        pos = w > 0.0
+        uj = U[j]
+        bad |= pos & np.isinf(uj)
+        val += np.where(pos & np.isfinite(uj), w * np.where(np.isfinite(uj), uj, 0.0), 0.0)
+    return np.where(bad, np.inf, val)
+
+
+@pytest.mark.parametrize("make", [lambda: W.sincos2d(3, n=65, n_coarse=17, n_c=16, n_targets=2, radius=0.15),
+                                  lambda: W.zermelo(n=65, n_coarse=17, n_c=16, parts=4)])
+def test_step2_u0_and_feedback_follow_their_definitions(make):
+    """Step 2 restated with an independent Q1.  U_P^(0) is the Q1 of the
+    coarse values at each free fine node, a +inf corner counting as the bound
+    M = 1e6 and U_P^(0) >= M meaning unreachable (R7).  a* is the argmin over
+    controls of I[U_P^(0)](x_i + k f/|f|) + h_{i,a} (Eq. feedbackcontrol),
+    and gap its margin to the second best."""
+    p = make()
+    r = oracle.patchy_solve(p, tol=1e-10)
+    kind, _, _ = I.kinds(p)
+    idx, x = I.node_grid(p)
+    d = p.dim
+    free = np.nonzero(kind == 0)[0]
+    scale = (np.array(p.n_coarse[:d]) - 1.0) / (np.array(p.n[:d]) - 1.0)
+    M = 1.0e6
+    u0 = _q1_values(p.n_coarse, idx[free] * scale, np.where(np.isinf(r.ucoarse), M, r.ucoarse), d)
+    u0 = np.where(u0 >= M, np.inf, u0)
+    fin = np.isfinite(u0)
+    assert fin.mean() > 0.9
+    assert np.array_equal(fin, np.isfinite(r.u0[free]))
+    np.testing.assert_allclose(r.u0[free][fin], u0[fin], rtol=1e-12, atol=1e-12)
+    # the feedback at the free nodes with a finite U_P^(0)
+    U0 = np.where(kind == 1, 0.0, np.inf)
+    U0[free] = u0
+    nodes = free[fin]
+    dirs, h = I.node_control_steps(p, x[nodes])
+    if h.shape[0] != nodes.size:   # per-control steps come for every node
+        h = h[nodes]
+    vals = np.stack([_q1_values(p.n, idx[nodes] + dirs[:, m], U0, d) + h[:, m]
+                     for m in range(p.n_controls)], axis=1)
+    order = np.argsort(vals, axis=1, kind="stable")
+    best = np.take_along_axis(vals, order[:, :1], axis=1)[:, 0]
+    second = np.take_along_axis(vals, order[:, 1:2], axis=1)[:, 0]
+    gap = second - best
+    has = np.isfinite(best)
+    assert np.array_equal(r.astar[nodes] >= 0, has)
+    # the chosen control attains the minimum; where no other control comes
+    # within rounding of it, it is the unique argmin (the drift's mirrored
+    # control pairs tie at a fifth of the nodes)
+    tol = 1e-9 * np.maximum(1.0, best[has])
+    chosen = np.take_along_axis(vals[has], r.astar[nodes][has, None].astype(np.int64), axis=1)[:, 0]
+    assert np.all(chosen <= best[has] + tol)
+    clear = has & (gap > 1e-9 * np.maximum(1.0, best))
+    assert clear.mean() > 0.5
+    assert np.array_equal(r.astar[nodes][clear], order[clear, 0])
+    g = r.gap[nodes][has]
+    assert np.array_equal(np.isinf(g), np.isinf(gap[has]))
+    ok = np.isfinite(g)
+    np.testing.assert_allclose(g[ok], gap[has][ok], rtol=0, atol=1e-9)
