@@ -223,7 +223,11 @@ def test_order_independence():
     """Lexicographic Gauss-Seidel, alternating orders and Jacobi reach the same
     fixed point (Sec. 2.2: Gauss-Seidel only speeds the iteration up)."""
     p = W.sincos2d(2, n=41, n_coarse=11).with_(n_coarse=None, tol=1e-13)
-    us = [oracle.global_solve(p, order=o).u for o in (0, 1, 2)]
+    rs = [oracle.global_solve(p, order=o) for o in (0, 1, 2)]
+    # every order stops by itself: the ghost ring stays +inf, and an unchanged
+    # +inf counts as no change (R9)
+    assert all(r.converged for r in rs)
+    us = [r.u for r in rs]
     fin = np.isfinite(us[0])
     for u in us[1:]:
         assert np.array_equal(fin, np.isfinite(u))
@@ -403,11 +407,16 @@ def test_patchy_single_target_equals_global():
     assert np.array_equal(rp.u, rg.u)
 
 
-def test_patchy_not_below_global_and_invariant():
+@pytest.mark.parametrize("make", [lambda: _small_patchy(5, n=49, nc=13, R=4),
+                                  lambda: W.eikonal_sectors(n=49, n_coarse=13, n_c=16, parts=4),
+                                  lambda: W.fan(n=49, n_coarse=13, n_c=16, parts=4)])
+def test_patchy_not_below_global_and_invariant(make):
     """State constraints on patch boundaries only remove admissible paths, so
     U_P >= U_global; and every finite patch value is reached through corners
-    inside its own patch or its own target part (patch invariance)."""
-    p = _small_patchy(5, n=49, nc=13, R=4).with_(tol=1e-12)
+    inside its own patch or its own target part (patch invariance).  With a
+    target split into parts (a disk in sectors, Fan's line in pieces) the
+    neighbouring parts touch each patch, and they are not terminals of it."""
+    p = make().with_(tol=1e-12)
     rp = oracle.patchy_solve(p)
     rg = oracle.global_solve(p.with_(n_coarse=None))
     fin = np.isfinite(rg.u)
@@ -530,3 +539,21 @@ def test_step2_u0_and_feedback_follow_their_definitions(make):
     assert np.array_equal(np.isinf(g), np.isinf(gap[has]))
     ok = np.isfinite(g)
     np.testing.assert_allclose(g[ok], gap[has][ok], rtol=0, atol=1e-9)
+
+
+def test_uncovered_nodes_join_a_neighbouring_patch():
+    """Remark 3.1: a node with a feedback that no colour reaches (every
+    phi^j = 0) still joins a patch, one of its axis neighbours'.  A coarse
+    grid of 5^2 nodes under the Zermelo drift leaves such nodes."""
+    p = W.zermelo(n=65, n_coarse=5, parts=4).with_(tol=1e-10)
+    r = oracle.patchy_solve(p, keep_phi=True)
+    kind, _, _ = I.kinds(p)
+    act = (kind == 0) & (r.astar >= 0)
+    bare = act & (r.phi.max(axis=0) == 0.0)
+    assert bare.sum() >= 50
+    assert np.all(r.labels[act] >= 0)
+    n = p.n[0]
+    for i in np.nonzero(bare)[0]:
+        nb = [j for j in (i - 1, i + 1, i - n, i + n) if 0 <= j < kind.size]
+        assert r.labels[i] in r.labels[nb]
+    assert r.converged
