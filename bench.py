@@ -68,6 +68,31 @@ def problem(seed: int):
 
 # ----------------------------------------------------------------- helpers --
 
+def oracle_parity(p, u, labels):
+    """Error of a GPU result against the FP64 oracle's patchy solution of the
+    same problem (state constraints, no add-ons), as stored under tests/golden
+    by make_golden.py from the oracle alone: 20,000 sampled values and the full
+    label map.  None when nothing is stored for this problem."""
+    seed = (getattr(p, "name", "") or "").rsplit("_s", 1)[-1]
+    path = os.path.join(ROOT, "tests", "golden", f"{FAMILY}_n{p.n[0]}_s{seed}.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    meta = json.loads(str(g["meta"]))
+    ref = getattr(W, meta["family"])(meta["seed"], **meta["kw"])
+    same = (list(ref.n) == list(p.n) and list(ref.n_coarse) == list(p.n_coarse) and ref.speed == p.speed
+            and np.array_equal(ref.speed_params, p.speed_params) and np.array_equal(ref.controls, p.controls)
+            and np.array_equal(ref.targets, p.targets))
+    if not same:
+        return None
+    idx = g["idx"]
+    err = float(np.abs(u[idx] - g["u"]).max())
+    return {"max_abs_err": err, "rel_err": err / meta["max_u"], "bound_rel": 1e-4,
+            "label_agreement": float(np.mean(labels == g["labels"])),
+            "reachable_equal": int(np.isfinite(u).sum()) == int(meta["reachable"]),
+            "nodes_sampled": int(idx.size), "source": "FP64 oracle, tests/golden/" + os.path.basename(path)}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -327,6 +352,7 @@ def run_ours(args, rank, world, dist):
     gstats = gplan.stats()
     # patchy error E = U_P - U_global on the same fine grid (Sec. 4.2), both from the GPU
     up, ug = plan.values(), gplan.values()
+    parity = oracle_parity(p, up, plan.labels()) if (args.bc == "state" and not args.reduce_r) else None
     both = np.isfinite(up) & np.isfinite(ug)
     ev = np.abs(up[both] - ug[both])
     patchy_error = {"E1": float(ev.mean()) if ev.size else None, "Einf": float(ev.max()) if ev.size else None,
@@ -386,6 +412,7 @@ def run_ours(args, rank, world, dist):
             "plain_sl_ms": statistics.mean(gms),
             "plain_sl_node_control_updates": gstats["node_control_updates"],
             "patchy_error_vs_plain": patchy_error,
+            "error_vs_oracle": parity,
             "node_control_updates_per_solve": s0["node_control_updates"],
             "sweeps": {k: s0[k] for k in ("sweeps_coarse", "sweeps_phi", "sweeps_reach", "sweeps_fine",
                                            "sweeps_polish", "sweeps_patch", "phi_refinements")},

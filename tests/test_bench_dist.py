@@ -49,3 +49,23 @@ def test_single_rank_passthrough():
     import bench
 
     assert bench.aggregate(None, 5.0, 7.0, "cpu") == (5.0, 7.0)
+
+
+def test_oracle_parity_reads_the_stored_oracle_solution():
+    """bench.py states each default-workload result's error against the FP64
+    oracle's stored solution of the same problem, and nothing for another."""
+    import numpy as np
+
+    import bench
+    import workloads as W
+
+    p = bench.problem(0)
+    g = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sincos2d_n2049_s0.npz"))
+    u = np.full(p.n_nodes, np.inf)
+    u[g["idx"]] = g["u"]
+    r = bench.oracle_parity(p, u, g["labels"])
+    assert r["max_abs_err"] == 0.0 and r["label_agreement"] == 1.0 and r["nodes_sampled"] == g["idx"].size
+    u[g["idx"][7]] += 1e-3
+    assert bench.oracle_parity(p, u, g["labels"])["max_abs_err"] == pytest.approx(1e-3)
+    assert bench.oracle_parity(W.sincos2d(0, n=1025, n_coarse=33), u, g["labels"]) is None
+    assert bench.oracle_parity(W.sincos2d(1), u, g["labels"]) is None
