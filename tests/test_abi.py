@@ -116,3 +116,45 @@ def test_autotune_reads_its_cache_file_without_a_gpu(lib, tmp_path):
     fn.argtypes = [ctypes.c_void_p] * 5
     fn.restype = ctypes.c_int
     assert fn(None, None, None, None, None) == 1
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "hjbp.h"
+int main(void) {
+    hjbp_problem_desc d;
+    hjbp_plan *plan = (hjbp_plan *)&d;
+    hjbp_status s;
+    printf("version %d\n", hjbp_version());
+    memset(&d, 0, sizeof d);
+    d.dim = 4;
+    s = hjbp_create(&d, NULL, NULL, &plan);
+    printf("create %d null_out %d msg %s\n", (int)s, plan == NULL, hjbp_last_error());
+    s = hjbp_create(NULL, NULL, NULL, &plan);
+    printf("null_desc %d\n", (int)s);
+    return 0;
+}
+"""
+
+
+def test_plain_c_program_uses_the_abi(lib, tmp_path):
+    """The header is plain C11 (compiles with -Wall -Wextra -pedantic -Werror)
+    and a C program links the library and gets statuses and messages back
+    without Python or a GPU."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.join(root, "paper_1109_3577_gb300")
+    src, exe = tmp_path / "abi.c", tmp_path / "abi"
+    src.write_text(C_PROGRAM)
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I" + os.path.join(root, "include"), str(src), "-L" + libdir, "-lhjbp",
+                           "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout.splitlines()
+    assert out[0] == "version 100"
+    assert out[1] == "create 1 null_out 1 msg dim must be 2 or 3"
+    assert out[2] == "null_desc 1"
