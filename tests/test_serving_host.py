@@ -79,3 +79,52 @@ def test_failed_create_finishes_the_request_without_a_plan(P):
         assert P.hjbp_server_stats(srv) == (0, 0, 0)
     finally:
         P.hjbp_server_destroy(srv)
+
+
+def test_admission_waits_for_memory_to_be_collected(P):
+    """Continuous batching by device memory: a request that does not fit next
+    to the bytes held by earlier ones waits in the queue, holding nothing,
+    and is admitted once the earlier request is collected.  Without a GPU
+    every admitted request fails at plan creation, which still exercises the
+    queue and the accounting."""
+    import time
+
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("needs a process without a GPU")
+
+    def wait_for(srv, want, limit=30.0):
+        t0 = time.time()
+        while P.hjbp_server_stats(srv) != want:
+            assert time.time() - t0 < limit, P.hjbp_server_stats(srv)
+            time.sleep(0.005)
+
+    d, keep = P.desc_from_problem(W.sincos2d(0, n=129, n_coarse=17))
+    # the request's footprint, read from a server with room to spare
+    srv = P.hjbp_server_create(budget_bytes=1 << 40, workers=1)
+    try:
+        P.hjbp_server_submit(srv, d)
+        t0 = time.time()
+        while P.hjbp_server_stats(srv)[2] == 0 or P.hjbp_server_stats(srv)[1] != 0:
+            assert time.time() - t0 < 30.0
+            time.sleep(0.005)
+        fp = P.hjbp_server_stats(srv)[2]
+    finally:
+        P.hjbp_server_destroy(srv)
+    assert fp > 0
+    srv = P.hjbp_server_create(budget_bytes=fp + fp // 2, workers=2)
+    try:
+        a = P.hjbp_server_submit(srv, d)
+        b = P.hjbp_server_submit(srv, d)
+        wait_for(srv, (1, 0, fp))             # a finished and uncollected, b queued
+        time.sleep(0.05)
+        assert P.hjbp_server_stats(srv) == (1, 0, fp)
+        with pytest.raises(P.HjbpError):      # a's plan could not be created
+            P.hjbp_server_poll(srv, a)
+        wait_for(srv, (0, 0, fp))             # b admitted and finished
+        with pytest.raises(P.HjbpError):
+            P.hjbp_server_poll(srv, b)
+        assert P.hjbp_server_stats(srv) == (0, 0, 0)
+    finally:
+        P.hjbp_server_destroy(srv)
