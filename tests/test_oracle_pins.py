@@ -490,7 +490,8 @@ def _q1_values(n, lo_idx, U, dim):
 
 
 @pytest.mark.parametrize("make", [lambda: W.sincos2d(3, n=65, n_coarse=17, n_c=16, n_targets=2, radius=0.15),
-                                  lambda: W.zermelo(n=65, n_coarse=17, n_c=16, parts=4)])
+                                  lambda: W.zermelo(n=65, n_coarse=17, n_c=16, parts=4),
+                                  lambda: W.sin3d(1, n=17, n_coarse=9, n_c=26, n_targets=2, radius=0.3)])
 def test_step2_u0_and_feedback_follow_their_definitions(make):
     """Step 2 restated with an independent Q1.  U_P^(0) is the Q1 of the
     coarse values at each free fine node, a +inf corner counting as the bound
