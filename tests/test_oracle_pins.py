@@ -332,14 +332,16 @@ def _small_patchy(seed=0, n=33, nc=9, R=3):
     return W.sincos2d(seed, n=n, n_coarse=nc, n_targets=R, radius=0.2)
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_phi_is_absorption_probability(seed):
+@pytest.mark.parametrize("make", [lambda: _small_patchy(0), lambda: _small_patchy(1),
+                                  lambda: W.sin3d(2, n=13, n_coarse=7, n_c=26, n_targets=2, radius=0.3)])
+def test_phi_is_absorption_probability(make):
     """Step 3.1: phi^j solves a linear fixed point whose solution is the
     probability that the chain with the Q1 transitions of the coarse feedback
     is absorbed in Omega_0^j.  Checked against a dense linear solve on the
     nodes that can reach the target (phi = 0 elsewhere); phi in [0,1] and
-    sum_j phi^j <= 1, with equality unless the chain can be trapped."""
-    p = _small_patchy(seed)
+    sum_j phi^j <= 1, with equality unless the chain can be trapped.  2D and
+    3D (trilinear transitions)."""
+    p = make()
     r = oracle.patchy_solve(p, keep_phi=True)
     kind, part, _ = I.kinds(p)
     idx, _ = I.node_grid(p)
