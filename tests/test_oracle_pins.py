@@ -411,7 +411,8 @@ def test_patchy_single_target_equals_global():
 
 @pytest.mark.parametrize("make", [lambda: _small_patchy(5, n=49, nc=13, R=4),
                                   lambda: W.eikonal_sectors(n=49, n_coarse=13, n_c=16, parts=4),
-                                  lambda: W.fan(n=49, n_coarse=13, n_c=16, parts=4)])
+                                  lambda: W.fan(n=49, n_coarse=13, n_c=16, parts=4),
+                                  lambda: W.sin3d(2, n=17, n_coarse=9, n_c=26, n_targets=2, radius=0.3)])
 def test_patchy_not_below_global_and_invariant(make):
     """State constraints on patch boundaries only remove admissible paths, so
     U_P >= U_global; and every finite patch value is reached through corners
