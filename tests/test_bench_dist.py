@@ -69,3 +69,25 @@ def test_oracle_parity_reads_the_stored_oracle_solution():
     assert bench.oracle_parity(p, u, g["labels"])["max_abs_err"] == pytest.approx(1e-3)
     assert bench.oracle_parity(W.sincos2d(0, n=1025, n_coarse=33), u, g["labels"]) is None
     assert bench.oracle_parity(W.sincos2d(1), u, g["labels"]) is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host cores and
+    prints one JSON line with the keys the measurement contract asks for."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "node-control updates/s" and d["steps"] == 1 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "patchy2d_sincos_n2049_c65_nc64_R4"
