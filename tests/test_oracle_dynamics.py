@@ -232,10 +232,16 @@ def test_3d_target_parts_follow_the_definitions():
         assert set(part[part >= 0]) == set(range(p.n_parts))
 
 
-def test_fan3d_axis_controls_equal_dijkstra():
+@pytest.mark.parametrize("obstacles", [False, True])
+def test_fan3d_axis_controls_equal_dijkstra(obstacles):
     """Fan 3D with the six axis controls: the fixed point is Dijkstra on the
-    axis graph with cost h_i = k / c(x_i) leaving node i."""
+    axis graph with cost h_i = k / c(x_i) leaving node i; with a ball and a
+    box as obstacles (R23) their nodes leave the graph."""
     p = W.fan3d(n=21, n_coarse=7).with_(n_coarse=None, controls=W.controls_axes(3), tol=1e-14)
+    if obstacles:
+        p = p.with_(obstacles=np.array([W.obstacle_ball((0.9, 0.3, -0.2), 0.6),
+                                        W.obstacle_box((-1.4, -0.6, -1.0), (-0.5, 0.8, 1.2))]))
+        assert (I.kinds(p)[0] == 2).sum() > (I.kinds(p.with_(obstacles=None))[0] == 2).sum() + 100
     kind, _, h = I.kinds(p)
     idx, _ = I.node_grid(p)
     N = kind.size
