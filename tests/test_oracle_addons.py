@@ -22,13 +22,18 @@ def _small(seed=0, n=49, nc=13, R=3, radius=0.2, dim=2):
 
 # ------------------------------------------------------------- Dirichlet --
 
-@pytest.mark.parametrize("dim,seed", [(2, 0), (2, 1), (3, 0)])
+@pytest.mark.parametrize("dim,seed", [(2, 0), (2, 1), (3, 0), ("zermelo", 0), ("brockett", 0)])
 def test_dirichlet_with_exact_data_gives_global_solution(dim, seed):
     """With the global fixed point as boundary data, each patch's equation
     (Eq. SLscheme restricted to the patch, data outside) is solved by the
     restriction of that fixed point, and it is the only finite one on S*: the
     patchy result must equal the global solution at every node."""
-    p = _small(seed) if dim == 2 else _small(seed, n=17, nc=7, R=3, radius=0.15, dim=3)
+    if dim == "zermelo":        # per-control steps h = k/|s a + w| (R20)
+        p = W.zermelo(n=49, n_coarse=13, n_c=16, parts=4).with_(tol=1e-13)
+    elif dim == "brockett":     # per-node feet and steps (R24)
+        p = W.brockett3d(n=17, n_coarse=9).with_(tol=1e-13)
+    else:
+        p = _small(seed) if dim == 2 else _small(seed, n=17, nc=7, R=3, radius=0.15, dim=3)
     g = oracle.global_solve(p.with_(n_coarse=None), tol=1e-13)
     r = oracle.patchy_solve(p, tol=1e-13, dirichlet=True, bc_data=g.u)
     fin = np.isfinite(g.u)
