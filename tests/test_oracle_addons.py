@@ -188,6 +188,79 @@ def test_reduced_controls_match_linear_program(seed, r):
     assert np.all(ref2[off] - ref[off] > 1e-3)
 
 
+def _sure_set(p, allowed):
+    """S* (R14) restated: the greatest set S of free nodes from which the
+    target is reached with allowed controls whose positive-weight corners all
+    lie in S or on the target (reach from the target, drop what was not
+    reached, repeat)."""
+    kind, _, _ = I.kinds(p)
+    idx, _ = I.node_grid(p)
+    free = [int(i) for i in np.nonzero(kind == 0)[0]]
+    corners = {i: [I.q1_corners(p, idx[i], a) if allowed(i, m) else None for m, a in enumerate(p.controls)]
+               for i in free}
+    S = set(free)
+    while True:
+        reached, grew = set(), True
+        while grew:
+            grew = False
+            for i in sorted(S - reached):
+                for cs in corners[i]:
+                    if cs is None or not all(kind[j] == 1 or j in S for j, _ in cs):
+                        continue
+                    if any(kind[j] == 1 or (j in reached and j != i) for j, _ in cs):
+                        reached.add(i)
+                        grew = True
+                        break
+        if reached == S:
+            return S, corners
+        S = reached
+
+
+@pytest.mark.parametrize("r", [2.0, 4.0])
+def test_reduced_controls_match_linear_program_3d(r):
+    """The same in 3D (trilinear transitions among 26 Fibonacci directions;
+    cones around the global solution's minimising control, replaced by a
+    random control at a fifth of the nodes and dropped at another fifth).
+    Here a control can put a tiny positive weight on a node off S*, so the
+    capped LP over all nodes is not the comparison: S* is restated
+    independently and the LP runs over the controls that stay in it."""
+    p = W.random_speed_problem(5, n=7, n_c=26, dim=3)
+    g = oracle.global_solve(p, tol=1e-14)
+    kind, _, h = I.kinds(p)
+    idx, _ = I.node_grid(p)
+    rng = np.random.default_rng(205)
+    astar = np.full(g.u.size, -1, np.int32)
+    for i in np.nonzero((kind == 0) & np.isfinite(g.u))[0]:
+        q = [h[i] + sum(w * g.u[j] for j, w in I.q1_corners(p, idx[i], a)) for a in p.controls]
+        astar[i] = int(np.argmin(q))
+    u = rng.random(astar.size)
+    astar[u < 0.2] = rng.integers(0, 26, size=int((u < 0.2).sum()))
+    astar[u > 0.8] = -1
+    U = np.where(kind == oracle.TARGET, 0.0, np.inf)
+    it = oracle.iterate_reduced(p, U, kind == oracle.FREE, astar, r, tol=1e-14)
+    S, corners = _sure_set(p, _cones(p, astar, r))
+    fin = np.isfinite(it.u) & (kind == 0)
+    assert set(np.nonzero(fin)[0].tolist()) == S and len(S) > 10
+    Sl = sorted(S)
+    pos = {i: q for q, i in enumerate(Sl)}
+    rows, rhs = [], []
+    for i in Sl:
+        for cs in corners[i]:
+            if cs is None or not all(kind[j] == 1 or j in S for j, _ in cs):
+                continue
+            row = np.zeros(len(Sl))
+            row[pos[i]] += 1.0
+            for j, w in cs:
+                if j in pos:
+                    row[pos[j]] -= w
+            rows.append(row)
+            rhs.append(h[i])
+    res = linprog(-np.ones(len(Sl)), A_ub=np.array(rows), b_ub=np.array(rhs), bounds=(0, 1e6), method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    assert res.status == 0
+    np.testing.assert_allclose(it.u[Sl], res.x, rtol=0, atol=1e-8)
+
+
 def test_single_control_cone_is_policy_evaluation():
     """For r so large that the cone holds only a*, the fixed point is the
     value of the feedback a*: the linear system u_i = h_i + sum_c w_c u_c."""
