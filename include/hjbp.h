@@ -237,6 +237,9 @@ typedef struct {
     double ms_sweep_kernel;               /* their summed duration (HJBP_FLAG_TIME_SWEEPS), else 0 */
     int phi_refinements;                  /* FP64 residual evaluations of the colour transport */
     double ms_reach;                      /* S* computation on the fine grid (inside ms_fine) */
+    double residual_patch[HJBP_MAX_TARGETS];  /* per patch: the largest FP64 sup-norm change of its
+                                             tiles in the last launch each ran in (<= tol once the
+                                             patch retired; patchy solves, 0 otherwise)   */
 } hjbp_stats;
 
 /* Validate the descriptor, copy its arrays, allocate device memory.
@@ -292,6 +295,28 @@ hjbp_status hjbp_get_device_views(hjbp_plan *plan, const double **u, const int8_
 
 hjbp_status hjbp_get_stats(hjbp_plan *plan, hjbp_stats *out);
 
+/* Patch compaction of the last patchy solve (Sec. 3: the patches are
+ * assembled from the labels of Step 3.1 before Step 3.2 solves each one), as
+ * per-patch lists in CSR form.  The fine grid is cut into tiles of 32x32
+ * interior nodes in 2D (8x8x8 in 3D) starting at node (1,1[,1]);
+ * ntx = ceil((n[0]-2)/side), nty likewise, and tile t = tx + ntx (ty + nty tz).
+ *   tile_offsets  R+1 int64: patch j owns entries tile_offsets[j] ..
+ *                 tile_offsets[j+1]-1 of tile_ids and tile_nodes
+ *   tile_ids      int32 per entry: a tile holding a free node of patch j, in
+ *                 increasing order
+ *   tile_nodes    int32 per entry: the free nodes of patch j in that tile
+ *   node_offsets  R+1 int64: patch j owns node_ids[node_offsets[j] ..
+ *                 node_offsets[j+1]-1]
+ *   node_ids      int32 per free node of patch j: its node index, tile by tile
+ *                 in the order of tile_ids, x fastest inside a tile
+ * R = hjbp_stats.n_patches.  Free nodes are the nodes of label j that are
+ * neither target nor ghost ring; the node lists are taken before S* pruning,
+ * so node_offsets[j+1] - node_offsets[j] = hjbp_stats.patch_nodes[j].  Any
+ * pointer may be NULL (call first with the offsets alone to size the others).
+ * Host buffers, caller-owned.  Errors: ESTATE (no patchy solve yet), EINVAL. */
+hjbp_status hjbp_get_patch_lists(hjbp_plan *plan, int64_t *tile_offsets, int32_t *tile_ids, int32_t *tile_nodes,
+                                 int64_t *node_offsets, int32_t *node_ids);
+
 /* Node count N and coarse count N~ of the plan.                              */
 hjbp_status hjbp_get_sizes(hjbp_plan *plan, int64_t *n_nodes, int64_t *n_coarse_nodes);
 
@@ -344,23 +369,30 @@ hjbp_status hjbp_server_poll(hjbp_server *server, uint64_t ticket, hjbp_plan **d
 hjbp_status hjbp_server_stats(hjbp_server *server, int *queued, int *running, size_t *bytes_in_use);
 void hjbp_server_destroy(hjbp_server *server);
 
-/* Plain global 2D solve in FP64 that allocates nothing (the paper has no
- * counterpart; it serves callers that cannot allocate at solve time, e.g.
- * code running while a stream is captured into a CUDA graph, or real-time
- * loops that forbid allocation after start-up).
- *   desc        a 2D problem with n_coarse[0] == 0 (plain global solve) and at
- *               most HJBP_NOALLOC_MAX_NODES nodes; precision is ignored (FP64)
+/* Plain global 2D solve in FP64 that allocates nothing.  The paper has no
+ * counterpart: it serves callers that cannot allocate device memory at solve
+ * time, such as real-time loops that forbid allocation after start-up (an
+ * allocation may block or fail on a fragmented pool) or hosts whose memory
+ * pool belongs to another component.
+ *   desc        a 2D problem with n_coarse[0] == 0 (plain global solve), at
+ *               most HJBP_NOALLOC_MAX_NODES nodes, f = c(x) a, ball targets,
+ *               no patchy-only options (flags DIRICHLET / WARM_START /
+ *               CAUSAL_SWEEPS, reduce_r); precision is ignored (FP64)
  *   cuda_stream the stream to run on (NULL = legacy default stream)
  *   u_out       device array of N doubles: the values (+INFINITY unreachable)
  *   labels_out  device array of N int8: 0 / target part / -1, as hjbp_get_labels
- * Results equal hjbp_solve's for the same descriptor with HJBP_FP64.  Scratch
- * comes from one fixed device array inside the library (32 MiB, held by every
- * GPU that loads the library until the process exits); no cudaMalloc,
- * cudaFree or other allocator is called.  The first call on each device looks
- * up that array's device address, so make it before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race and must be
- * serialised by the caller.  Synchronises the stream before returning.
- * Errors: EINVAL (descriptor, too large, NULL outputs), ECUDA, ENOCONV.      */
+ * Runs the kernels hjbp_solve runs for the same descriptor with HJBP_FP64, in
+ * the same order, so the results agree with hjbp_solve's.  Scratch comes from
+ * one fixed device array inside the library (32 MiB, held by every GPU that
+ * loads the library until the process exits); no cudaMalloc, cudaFree or
+ * other allocator is called.  The first call on each device looks up that
+ * array's device address and the SM count and caches them for the process
+ * lifetime (one primary context per device; no cudaDeviceReset in between).
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  The call is synchronous: it reads counts back to
+ * the host between launches and synchronises the stream before returning.
+ * Errors: EINVAL (descriptor, too large, NULL outputs), ECUDA, ENOCONV
+ * (max_sweeps reached; the outputs then hold the last iterate).              */
 #define HJBP_NOALLOC_MAX_NODES (1 << 20)
 hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc, void *cuda_stream, double *u_out,
                                         int8_t *labels_out);

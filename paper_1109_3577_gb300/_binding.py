@@ -98,6 +98,7 @@ class Stats(C.Structure):
         ("ms_sweep_kernel", C.c_double),
         ("phi_refinements", C.c_int),
         ("ms_reach", C.c_double),
+        ("residual_patch", C.c_double * MAX_TARGETS),
     ]
 
     def as_dict(self) -> dict:
@@ -149,6 +150,8 @@ def library():
         lib.hjbp_destroy.restype = None
         lib.hjbp_last_error.argtypes = []
         lib.hjbp_last_error.restype = C.c_char_p
+        lib.hjbp_get_patch_lists.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.hjbp_get_patch_lists.restype = C.c_int
         lib.hjbp_solve_global2d_noalloc.argtypes = [P(Desc), vp, vp, vp]
         lib.hjbp_solve_global2d_noalloc.restype = C.c_int
         lib.hjbp_batch_solve.argtypes = [P(vp), C.c_int, C.c_int, P(C.c_int)]
@@ -320,6 +323,23 @@ def hjbp_solve_global2d_noalloc(desc: Desc, stream: int, u_out_ptr: int, labels_
     return st
 
 
+def hjbp_get_patch_lists(plan: int) -> dict:
+    """Per-patch tile and node lists of the last patchy solve (CSR):
+    tile_offsets / node_offsets (R + 1), tile_ids, tile_nodes, node_ids."""
+    lib = library()
+    R = max(1, hjbp_get_stats(plan).n_patches)
+    to = np.zeros(R + 1, np.int64)
+    no = np.zeros(R + 1, np.int64)
+    _check(lib.hjbp_get_patch_lists(C.c_void_p(plan), to.ctypes.data, None, None, no.ctypes.data, None))
+    tid = np.zeros(max(1, int(to[-1])), np.int32)
+    tn = np.zeros(max(1, int(to[-1])), np.int32)
+    nid = np.zeros(max(1, int(no[-1])), np.int32)
+    _check(lib.hjbp_get_patch_lists(C.c_void_p(plan), None, tid.ctypes.data, tn.ctypes.data, None,
+                                    nid.ctypes.data))
+    return {"tile_offsets": to, "tile_ids": tid[: int(to[-1])], "tile_nodes": tn[: int(to[-1])],
+            "node_offsets": no, "node_ids": nid[: int(no[-1])]}
+
+
 def hjbp_destroy(plan: int) -> None:
     library().hjbp_destroy(C.c_void_p(plan))
 
@@ -471,6 +491,9 @@ class Plan:
 
     def stats(self) -> dict:
         return hjbp_get_stats(self.handle).as_dict()
+
+    def patch_lists(self) -> dict:
+        return hjbp_get_patch_lists(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

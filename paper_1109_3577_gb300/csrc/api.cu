@@ -2,6 +2,7 @@
 // device memory, dispatch to the 2D / 3D drivers, result copies.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -242,6 +243,20 @@ hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const 
             p->u0 = static_cast<double *>(p->dev_alloc(sizeof(double) * p->N));
             p->astar = static_cast<uint8_t *>(p->dev_alloc(p->N));
             p->phi = static_cast<double *>(p->dev_alloc(sizeof(double) * p->N * p->R));
+            // the patch lists at their largest: every node, every (tile, patch) pair
+            const TileGeom tg = hjbp::tile_geom(*desc);
+            const int64_t nt = (int64_t)tg.ntx * tg.nty * tg.ntz;
+            PatchLists &L = p->lists;
+            L.cap_nodes = std::max<int64_t>(p->N, 1);
+            L.cap_tiles = std::max<int64_t>(nt * p->R, 1);
+            const size_t bytes = sizeof(int64_t) * 2 * (size_t)(p->R + 1) + sizeof(int) * (size_t)L.cap_nodes +
+                                 2 * sizeof(int) * (size_t)L.cap_tiles;
+            unsigned char *blk = static_cast<unsigned char *>(p->dev_alloc(bytes));
+            L.d_tile_off = reinterpret_cast<int64_t *>(blk);
+            L.d_node_off = L.d_tile_off + (p->R + 1);
+            L.d_node_ids = reinterpret_cast<int *>(L.d_node_off + (p->R + 1));
+            L.d_tile_ids = L.d_node_ids + L.cap_nodes;
+            L.d_tile_nodes = L.d_tile_ids + L.cap_tiles;
         }
         hjbp::check_cuda(cudaStreamSynchronize(p->stream), "create");
     } catch (const HjbpError &e) {
@@ -260,7 +275,7 @@ hjbp_status hjbp_create(const hjbp_problem_desc *desc, void *cuda_stream, const 
 hjbp_status hjbp_solve(hjbp_plan *p) {
     if (!p) return fail(HJBP_EINVAL, "plan is NULL");
     // per-solve scratch lives after the fixed outputs; free it from earlier solves
-    const size_t keep = (size_t)(p->patchy ? 6 : 2) + (p->u32 ? 1 : 0);
+    const size_t keep = (size_t)(p->patchy ? 7 : 2) + (p->u32 ? 1 : 0);
     try {
         while (p->blocks.size() > keep) {
             auto b = p->blocks.back();
@@ -375,6 +390,32 @@ hjbp_status hjbp_get_device_views(hjbp_plan *p, const double **u, const int8_t *
 hjbp_status hjbp_get_stats(hjbp_plan *p, hjbp_stats *out) {
     if (!p || !out) return fail(HJBP_EINVAL, "NULL argument");
     *out = p->stats;
+    return HJBP_OK;
+}
+
+hjbp_status hjbp_get_patch_lists(hjbp_plan *p, int64_t *tile_offsets, int32_t *tile_ids, int32_t *tile_nodes,
+                                 int64_t *node_offsets, int32_t *node_ids) {
+    if (!p) return fail(HJBP_EINVAL, "plan is NULL");
+    if (!p->patchy || !p->lists.built) return fail(HJBP_ESTATE, "no patchy solve has built patch lists");
+    const PatchLists &L = p->lists;
+    const int R = L.R;
+    if (tile_offsets) std::memcpy(tile_offsets, L.tile_off.data(), sizeof(int64_t) * (R + 1));
+    if (node_offsets) std::memcpy(node_offsets, L.node_off.data(), sizeof(int64_t) * (R + 1));
+    const int64_t ET = L.tile_off[R], EN = L.node_off[R];
+    try {
+        if (tile_ids && ET)
+            hjbp::check_cuda(cudaMemcpyAsync(tile_ids, L.d_tile_ids, sizeof(int32_t) * ET, cudaMemcpyDeviceToHost,
+                                             p->stream), "tile ids");
+        if (tile_nodes && ET)
+            hjbp::check_cuda(cudaMemcpyAsync(tile_nodes, L.d_tile_nodes, sizeof(int32_t) * ET, cudaMemcpyDeviceToHost,
+                                             p->stream), "tile nodes");
+        if (node_ids && EN)
+            hjbp::check_cuda(cudaMemcpyAsync(node_ids, L.d_node_ids, sizeof(int32_t) * EN, cudaMemcpyDeviceToHost,
+                                             p->stream), "node ids");
+        hjbp::check_cuda(cudaStreamSynchronize(p->stream), "patch lists");
+    } catch (const HjbpError &e) {
+        return fail(e.status, e.msg);
+    }
     return HJBP_OK;
 }
 

@@ -388,16 +388,17 @@ __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x
 struct TileSched {
     int *list[2];         // active tile lists (double-buffered by launch parity)
     int *count;           // count[2]
-    float *chg[2];        // per-tile max change of the last launch (double-buffered)
+    double *chg[2];       // per-tile max change of the last launch (FP64, double-buffered)
     uint8_t *latest;      // which value buffer holds each tile's current values
     uint8_t *processed;   // tile ran in the current launch
     uint64_t *tile_patch; // patch bitmask of each tile (for per-patch sweep counts)
     uint64_t *patch_hist; // per-launch mask of patches with an active tile
-    float *res_hist;      // per-launch max change
+    double *res_hist;     // per-launch max change (FP64)
     int *count_hist;      // per-launch number of active tiles
     const uint8_t *dirs;  // per-tile Gauss-Seidel directions (bit d: run direction d); NULL: all
     int alt;              // 3D without dirs: launches alternate the increasing and the
                           // decreasing pass of each axis (half the passes per launch)
+    double *last_chg;     // per-tile change of the last launch the tile ran in (NULL: not kept)
 };
 
 __device__ __forceinline__ int tile_of(const Grid2 &g, int x, int y) {
@@ -408,6 +409,19 @@ __device__ __forceinline__ int tile_of(const Grid2 &g, int x, int y) {
 __device__ __forceinline__ float atomic_max_pos(float *addr, float v) {
     // non-negative floats order like their bit patterns
     return __int_as_float(atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v)));
+}
+
+__device__ __forceinline__ double atomic_max_pos(double *addr, double v) {
+    // non-negative doubles order like their bit patterns
+    return __longlong_as_double(
+        (long long)atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v)));
+}
+
+// |v - o| of two values in FP64 for the sup-norm stopping test: 0 when both
+// are the +inf sentinel, a huge value when only one is.
+template <typename T> __device__ __forceinline__ double change64(T v, T o, T thresh) {
+    const bool vi = v >= thresh, oi = o >= thresh;
+    return (vi && oi) ? 0.0 : ((vi || oi) ? 1e300 : fabs((double)v - (double)o));
 }
 
 }  // namespace hjbp

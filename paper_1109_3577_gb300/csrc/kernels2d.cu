@@ -85,12 +85,13 @@ __global__ void k_init_values2d(int64_t N, const int8_t *__restrict__ code, cons
 // After each tile launch: flip the parity of the tiles that ran, activate every
 // tile whose 3x3 tile neighbourhood changed by more than tol, record the max
 // change and the patches that are still active, clear the other change buffer.
-__global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch) {
+__global__ void k_schedule2d(Grid2 g, TileSched s, int par, double tol, int launch) {
     const int ntiles = g.ntx * g.nty;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     if (t == 0 && s.count_hist) s.count_hist[launch] = s.count[par];
-    if (s.processed[t]) {
+    const bool ran = s.processed[t] != 0;
+    if (ran) {
         s.latest[t] ^= 1;
         s.processed[t] = 0;
     }
@@ -106,16 +107,22 @@ __global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launc
         const int k = atomicAdd(&s.count[par ^ 1], 1);
         (par ? s.list[0] : s.list[1])[k] = t;
     }
-    const float my = (par ? s.chg[1] : s.chg[0])[t];
+    const double my = (par ? s.chg[1] : s.chg[0])[t];
     if (my > tol && s.tile_patch && s.patch_hist)
         atomicOr(reinterpret_cast<unsigned long long *>(&s.patch_hist[launch]),
                  (unsigned long long)s.tile_patch[t]);
-    if (my > 0.f && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
-    (par ? s.chg[0] : s.chg[1])[t] = 0.f;
+    if (my > 0.0 && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
+    if (ran && s.last_chg) s.last_chg[t] = my;
+    (par ? s.chg[0] : s.chg[1])[t] = 0.0;
 }
 
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -489,7 +496,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     }
     // store into the buffer that is not current; change against the start values
     T *dst = ((pm >> 4) & 1u) ? b0 : b1;
-    float mc = 0.f;
+    double mc = 0.0;
     const int x = x0 + lane;
     for (int r = 1; r <= kTile; ++r) {
         const int y = y0 - 1 + r;
@@ -498,12 +505,11 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         const T v = sm.u[r][1 + lane];
         const T o = u0[r - 1][lane];
         dst[(int64_t)y * g.n0 + x] = v;
-        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-        float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        double d = change64(v, o, Num<T>::thresh());
         // the plain update is not monotone and may keep moving by a few units
         // in the last place; such moves count as no change
-        if (!clamp && d <= (float)(Num<T>::noise() * fabs((double)v))) d = 0.f;
-        mc = fmaxf(mc, d);
+        if (!clamp && d <= Num<T>::noise() * fabs((double)v)) d = 0.0;
+        mc = fmax(mc, d);
     }
     mc = warp_max(mc);
     const int nf = warp_sum(nfree);
@@ -625,7 +631,7 @@ __device__ __forceinline__ void q_finish(const TileQueue &q, int t) {
 template <typename T, int NCLS, bool kDir>
 __global__ void __launch_bounds__(32) k_value2d_async(Grid2 g, const int8_t *__restrict__ code,
                                                       const T *__restrict__ h, T *u, TileQueue q, int rounds,
-                                                      float tol, unsigned long long *updates, const CtlTable2<T> ct,
+                                                      double tol, unsigned long long *updates, const CtlTable2<T> ct,
                                                       const T *__restrict__ dval) {
     __shared__ TileSmemV<T, kDir> sm;
     __shared__ T u0[kTile][kTile + 1];
@@ -689,7 +695,7 @@ __global__ void __launch_bounds__(32) k_value2d_async(Grid2 g, const int8_t *__r
             }
         }
         __syncwarp();
-        float last = 0.f;   // largest change in the last round
+        double last = 0.0;  // largest change in the last round (FP64)
         for (int rd = 0; rd < rounds; ++rd) {
             for (int dir = 0; dir < 4; ++dir) {
                 for (int st = 0; st < kTile; ++st) {
@@ -704,7 +710,7 @@ __global__ void __launch_bounds__(32) k_value2d_async(Grid2 g, const int8_t *__r
                         const T best = sl_update_m<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
                         if (best < nw) nw = best;
                         if (rd == rounds - 1 && nw < old)
-                            last = fmaxf(last, old >= Num<T>::thresh() ? 3.0e38f : (float)(old - nw));
+                            last = fmax(last, old >= Num<T>::thresh() ? 1e300 : (double)old - (double)nw);
                     }
                     __syncwarp();
                     if (active) sm.u[r][c] = nw;
@@ -714,7 +720,7 @@ __global__ void __launch_bounds__(32) k_value2d_async(Grid2 g, const int8_t *__r
         }
         // store in place; change per side decides which neighbours run again
         const int x = x0 + lane;
-        float colmax = 0.f, row1 = 0.f, rowL = 0.f;
+        double colmax = 0.0, row1 = 0.0, rowL = 0.0;
         const int rlast = min(kTile, g.n1 - 2 - y0 + 1);
         for (int r = 1; r <= kTile; ++r) {
             const int y = y0 - 1 + r;
@@ -723,9 +729,8 @@ __global__ void __launch_bounds__(32) k_value2d_async(Grid2 g, const int8_t *__r
             const T v = sm.u[r][1 + lane];
             const T o = u0[r - 1][lane];
             if (v != o) __stcg(u + (int64_t)y * g.n0 + x, v);
-            const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-            const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
-            colmax = fmaxf(colmax, d);
+            const double d = change64(v, o, Num<T>::thresh());
+            colmax = fmax(colmax, d);
             if (r == 1) row1 = d;
             if (r == rlast) rowL = d;
         }
@@ -838,7 +843,7 @@ template <typename T> struct TileSmemW {
     T h[kTile][kTile + 1];
     uint16_t mk[kTile][kTile + 2];
     T part[4][kTile];
-    float red[4];
+    double red[4];
 };
 
 // The value sweep with W warps per tile: in every step each warp evaluates
@@ -918,7 +923,7 @@ __global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__r
     const int cur = s.latest[t];
     T *dst = cur ? b0 : b1;
     const T *src = cur ? b1 : b0;
-    float mc = 0.f;
+    double mc = 0.0;
     const int x = x0 + lane;
     for (int rr = w; rr < kTile; rr += W) {
         const int y = y0 + rr;
@@ -927,9 +932,7 @@ __global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__r
         const T v = sm.u[1 + rr][1 + lane];
         const T o = src[i];
         dst[i] = v;
-        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-        const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
-        mc = fmaxf(mc, d);
+        mc = fmax(mc, change64(v, o, Num<T>::thresh()));
     }
     mc = warp_max(mc);
     const int nf = warp_sum(nfree);
@@ -939,8 +942,8 @@ __global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__r
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float mm = sm.red[0];
-        for (int q = 1; q < W; ++q) mm = fmaxf(mm, sm.red[q]);
+        double mm = sm.red[0];
+        for (int q = 1; q < W; ++q) mm = fmax(mm, sm.red[q]);
         (par ? s.chg[1] : s.chg[0])[t] = mm;
         s.processed[t] = 1;
     }
@@ -955,12 +958,12 @@ __global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__r
 // max |change| of the launch into res[launch].
 template <typename T>
 __global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T *__restrict__ h,
-                               const T *__restrict__ uin, T *__restrict__ uout, float *__restrict__ res, int launch,
+                               const T *__restrict__ uin, T *__restrict__ uout, double *__restrict__ res, int launch,
                                const CtlSelf2<T> ct) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    float mc = 0.f;
+    double mc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
         const int8_t cd = code[i];
         const T old = uin[i];
@@ -996,13 +999,11 @@ __global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T
         }
         if (lane == 0) {
             uout[i] = nw;
-            const bool vi = nw >= Num<T>::thresh(), oi = old >= Num<T>::thresh();
-            const float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)nw - (double)old));
-            mc = fmaxf(mc, d);
+            mc = fmax(mc, change64(nw, old, Num<T>::thresh()));
         }
     }
     mc = warp_max(mc);
-    if (lane == 0 && mc > 0.f) atomic_max_pos(&res[launch], mc);
+    if (lane == 0 && mc > 0.0) atomic_max_pos(&res[launch], mc);
 }
 
 // -------------------------------------------- almost-sure reachability (S*) --
@@ -1132,7 +1133,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     }
     const int nf = warp_sum(flips);
     if (lane == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = nf > 0 ? 1.f : 0.f;
+        (par ? s.chg[1] : s.chg[0])[t] = nf > 0 ? 1.0 : 0.0;
         s.processed[t] = 1;
     }
 }
@@ -1234,7 +1235,7 @@ __global__ void __launch_bounds__(32) k_peel2d(Grid2 g, int8_t *__restrict__ cod
     }
     const int nf = warp_sum(flips);
     if (lane == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = nf > 0 ? 1.f : 0.f;
+        (par ? s.chg[1] : s.chg[0])[t] = nf > 0 ? 1.0 : 0.0;
         s.processed[t] = 1;
     }
 }
@@ -1774,13 +1775,16 @@ __global__ void k_patch_codes(int64_t N, const int8_t *__restrict__ code0, int8_
 
 // ------------------------------------------------------ patch compaction --
 
-// Per tile: bitmask of the patches with a free node in it and per-patch node
-// counts; per patch: its tile count.  (Step 3.1 assembles the patches; the
-// tile masks let every sweep launch report which patches are still active.)
+// Per tile: bitmask of the patches with a free node in it and the node count
+// of each (tile_cnt[t R + j], zero-filled beforehand); per patch: its node and
+// tile counts.  (Step 3.1 assembles the patches; the tile masks let every
+// sweep launch report which patches are still active, and compact.cu turns
+// masks and counts into the per-patch lists.)
 __global__ void __launch_bounds__(32) k_compact2d(Grid2 g, const int8_t *__restrict__ code,
                                                   uint64_t *__restrict__ tile_patch,
                                                   unsigned long long *__restrict__ patch_nodes,
-                                                  unsigned long long *__restrict__ patch_tiles) {
+                                                  unsigned long long *__restrict__ patch_tiles,
+                                                  int *__restrict__ tile_cnt, int R) {
     const int t = blockIdx.x;
     const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
     const int lane = threadIdx.x;
@@ -1809,6 +1813,7 @@ __global__ void __launch_bounds__(32) k_compact2d(Grid2 g, const int8_t *__restr
         if (lane == 0) {
             atomicAdd(&patch_nodes[j], (unsigned long long)cnt);
             atomicAdd(&patch_tiles[j], 1ull);
+            if (j < R) tile_cnt[(int64_t)t * R + j] = cnt;
         }
     }
     if (lane == 0) tile_patch[t] = mask;
@@ -1827,12 +1832,12 @@ __global__ void __launch_bounds__(32) k_compact2d(Grid2 g, const int8_t *__restr
 // remaining candidates are evaluated in FP64: the result is the FP64 minimum
 // over all controls at close to FP32 cost.
 __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const double *__restrict__ h,
-                           const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
+                           const double *__restrict__ uin, double *__restrict__ uout, double *maxchg,
                            const CtlTable2<float> c32, const CtlTable2<double> c64,
                            const double *__restrict__ dval, const uint8_t *__restrict__ astar,
                            const Cone2 *__restrict__ cone) {
     const int64_t N = (int64_t)g.n0 * g.n1;
-    float mc = 0.f;
+    double mc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t cd = code[i];
         double v = uin[i];
@@ -1896,14 +1901,14 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
                         }
                     }
                 }
-                mc = fmaxf(mc, (float)fabs(best - v));
+                mc = fmax(mc, fabs(best - v));
                 v = best;
             }
         }
         uout[i] = v;
     }
     mc = warp_max(mc);
-    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(maxchg, mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.0) atomic_max_pos(maxchg, mc);
 }
 
 // A global solve has one target (the union of all parts): every target node
@@ -1959,7 +1964,7 @@ template __global__ void k_init_values2d<float>(int64_t, const int8_t *, const d
 template __global__ void k_init_values2d<double>(int64_t, const int8_t *, const double *, double, double *, double *,
                                                   const double *);
 template __global__ void k_value_wide2d<double>(Grid2, const int8_t *, const double *, const double *, double *,
-                                                float *, int, const CtlSelf2<double>);
+                                                double *, int, const CtlSelf2<double>);
 template __global__ void k_gather2d<float>(Grid2, const uint8_t *, const float *, const float *, float *, double *);
 template __global__ void k_gather2d<double>(Grid2, const uint8_t *, const double *, const double *, double *,
                                             double *);
@@ -2022,13 +2027,13 @@ Sched make_sched(hjbp_plan &p, const Grid2 &g, int hist) {
     s.d.list[0] = alloc_n<int>(p, nt);
     s.d.list[1] = alloc_n<int>(p, nt);
     s.d.count = alloc_n<int>(p, 2);
-    s.d.chg[0] = alloc_n<float>(p, nt);
-    s.d.chg[1] = alloc_n<float>(p, nt);
+    s.d.chg[0] = alloc_n<double>(p, nt);
+    s.d.chg[1] = alloc_n<double>(p, nt);
     s.d.latest = alloc_n<uint8_t>(p, nt);
     s.d.processed = alloc_n<uint8_t>(p, nt);
     s.d.tile_patch = nullptr;
     s.d.patch_hist = alloc_n<uint64_t>(p, hist);
-    s.d.res_hist = alloc_n<float>(p, hist);
+    s.d.res_hist = alloc_n<double>(p, hist);
     s.count_hist = alloc_n<int>(p, hist);
     s.d.count_hist = s.count_hist;
     s.iota = alloc_n<int>(p, nt);
@@ -2043,12 +2048,12 @@ void reset_sched(hjbp_plan &p, Sched &s) {
     check_cuda(cudaMemcpyAsync(s.d.list[0], s.iota, sizeof(int) * nt, cudaMemcpyDeviceToDevice, st), "reset list");
     const int counts[2] = {s.ntiles, 0};
     check_cuda(cudaMemcpyAsync(s.d.count, counts, sizeof(counts), cudaMemcpyHostToDevice, st), "reset count");
-    check_cuda(cudaMemsetAsync(s.d.chg[0], 0, sizeof(float) * nt, st), "reset chg");
-    check_cuda(cudaMemsetAsync(s.d.chg[1], 0, sizeof(float) * nt, st), "reset chg");
+    check_cuda(cudaMemsetAsync(s.d.chg[0], 0, sizeof(double) * nt, st), "reset chg");
+    check_cuda(cudaMemsetAsync(s.d.chg[1], 0, sizeof(double) * nt, st), "reset chg");
     check_cuda(cudaMemsetAsync(s.d.latest, 0, nt, st), "reset latest");
     check_cuda(cudaMemsetAsync(s.d.processed, 0, nt, st), "reset processed");
     check_cuda(cudaMemsetAsync(s.d.patch_hist, 0, sizeof(uint64_t) * s.hist, st), "reset hist");
-    check_cuda(cudaMemsetAsync(s.d.res_hist, 0, sizeof(float) * s.hist, st), "reset hist");
+    check_cuda(cudaMemsetAsync(s.d.res_hist, 0, sizeof(double) * s.hist, st), "reset hist");
     check_cuda(cudaMemsetAsync(s.count_hist, 0, sizeof(int) * s.hist, st), "reset hist");
     // the counts copied from a host stack array must land before it goes away
     check_cuda(cudaStreamSynchronize(st), "reset sync");
@@ -2058,12 +2063,12 @@ struct RunResult {
     int64_t tile_visits = 0; // active tiles summed over launches
     int launches = 0;        // launches that had work
     bool converged = false;
-    float last_res = 0.f;
+    double last_res = 0.0;
 };
 
 // Launch sweep+schedule pairs until no tile is active or the cap is hit.
 template <class Sweep>
-RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, Sweep sweep) {
+RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, double tol, int cap, Sweep sweep) {
     RunResult rr;
     if (s.ntiles == 0) {
         rr.converged = true;
@@ -2097,10 +2102,10 @@ RunResult run_tiles(hjbp_plan &p, const Grid2 &g, Sched &s, float tol, int cap, 
         }
     }
     std::vector<int> ch(L);
-    std::vector<float> rh(L);
+    std::vector<double> rh(L);
     if (L) {
         check_cuda(cudaMemcpyAsync(ch.data(), s.count_hist, sizeof(int) * L, cudaMemcpyDeviceToHost, p.stream), "hist");
-        check_cuda(cudaMemcpyAsync(rh.data(), s.d.res_hist, sizeof(float) * L, cudaMemcpyDeviceToHost, p.stream),
+        check_cuda(cudaMemcpyAsync(rh.data(), s.d.res_hist, sizeof(double) * L, cudaMemcpyDeviceToHost, p.stream),
                    "hist");
         check_cuda(cudaStreamSynchronize(p.stream), "hist sync");
     }
@@ -2441,7 +2446,7 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     const int warps = p.desc.tune[3] > 0 ? p.desc.tune[3] : 1;
     const bool pairs = cone && ct.d4 && ct.ncls == 8 && p.cone_pairs;   // AO3 in the pair form
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
-    RunResult rr = run_tiles(p, g, s, (float)tol, cap, [&](int par, int) {
+    RunResult rr = run_tiles(p, g, s, tol, cap, [&](int par, int) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (timed) {
             check_cuda(cudaEventCreate(&a), "event");
@@ -2513,7 +2518,7 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
 // warm start, no control cones).  Returns launches = 1.
 template <typename T, int NCLS, bool kDir>
 void launch_async(hjbp_plan &p, int ntiles, const Grid2 &g, const int8_t *code, const T *h, T *u,
-                  const TileQueue &q, int rounds, float tol, unsigned long long *updates, const CtlTable2<T> &ct,
+                  const TileQueue &q, int rounds, double tol, unsigned long long *updates, const CtlTable2<T> &ct,
                   const T *dval) {
     int per_sm = 0, sms = 0, dev = 0;
     check_cuda(cudaGetDevice(&dev), "device");
@@ -2556,7 +2561,7 @@ RunResult value2d_async(hjbp_plan &p, const Grid2 &g, const int8_t *code, const 
             check_cuda(cudaEventCreate(&b), "event");
             check_cuda(cudaEventRecord(a, st), "event");
         }
-        const float ftol = (float)tol;
+        const double ftol = tol;
         if (dval && ct.d4 && ct.ncls == 8) launch_async<T, 8, true>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, dval);
         else if (dval) launch_async<T, 0, true>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, dval);
         else if (ct.d4 && ct.ncls == 8) launch_async<T, 8, false>(p, nt, g, code, h, b0, q, rounds, ftol, updates, ct, nullptr);
@@ -2599,13 +2604,13 @@ RunResult value_wide2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const d
     ++p.stats.kernel_launches;
     const CtlSelf2<double> cs = make_self<double>(p);
     const int chunk = 16;
-    float *res = alloc_n<float>(p, chunk);
-    std::vector<float> hres(chunk);
+    double *res = alloc_n<double>(p, chunk);
+    std::vector<double> hres(chunk);
     RunResult rr;
     const int blocks = (int)std::min<int64_t>((N + 7) / 8, 152 * 16);
     int L = 0;
     while (L < cap) {
-        check_cuda(cudaMemsetAsync(res, 0, sizeof(float) * chunk, st), "memset");
+        check_cuda(cudaMemsetAsync(res, 0, sizeof(double) * chunk, st), "memset");
         int n = std::min(chunk, cap - L);
         for (int l = 0; l < n; ++l) {
             const double *in = ((L + l) & 1) ? b1 : b0;
@@ -2614,7 +2619,7 @@ RunResult value_wide2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const d
             ++p.stats.kernel_launches;
         }
         check_cuda(cudaGetLastError(), "wide launch");
-        check_cuda(cudaMemcpyAsync(hres.data(), res, sizeof(float) * chunk, cudaMemcpyDeviceToHost, st), "res");
+        check_cuda(cudaMemcpyAsync(hres.data(), res, sizeof(double) * chunk, cudaMemcpyDeviceToHost, st), "res");
         check_cuda(cudaStreamSynchronize(st), "wide sync");
         for (int l = 0; l < n; ++l) {
             rr.launches = L + l + 1;
@@ -2756,7 +2761,7 @@ hjbp_status solve2d(hjbp_plan &p) {
                     // FP32 bulk solve
                     k_phi_init2d<G><<<grid_for(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++p.stats.kernel_launches;
-                    RunResult rp = run_tiles(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par, int) {
+                    RunResult rp = run_tiles(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par, int) {
                         k_phi2d<G, false><<<sched.ntiles, 32, sizeof(PhiSmem<G, false>), st>>>(
                             g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc);
                         ++p.stats.kernel_launches;
@@ -2819,9 +2824,12 @@ hjbp_status solve2d(hjbp_plan &p) {
             uint64_t *tile_patch = alloc_n<uint64_t>(p, sched.ntiles);
             unsigned long long *pn = alloc_n<unsigned long long>(p, kMaxTargets);
             unsigned long long *pt = alloc_n<unsigned long long>(p, kMaxTargets);
+            int *tcnt = alloc_n<int>(p, (int64_t)sched.ntiles * R);
             check_cuda(cudaMemsetAsync(pn, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
             check_cuda(cudaMemsetAsync(pt, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
-            if (sched.ntiles) k_compact2d<<<sched.ntiles, 32, 0, st>>>(g, code, tile_patch, pn, pt);
+            check_cuda(cudaMemsetAsync(tcnt, 0, sizeof(int) * std::max<int64_t>(1, (int64_t)sched.ntiles * R), st),
+                       "memset");
+            if (sched.ntiles) k_compact2d<<<sched.ntiles, 32, 0, st>>>(g, code, tile_patch, pn, pt, tcnt, R);
             ++p.stats.kernel_launches;
             sched.d.tile_patch = tile_patch;
             unsigned long long hn[kMaxTargets], ht[kMaxTargets];
@@ -2832,6 +2840,8 @@ hjbp_status solve2d(hjbp_plan &p) {
                 S.patch_nodes[j] = (int64_t)hn[j];
                 S.patch_tiles[j] = (int64_t)ht[j];
             }
+            // per-patch tile and node lists (CSR)
+            build_patch_lists(p, tile_geom(d), sched.ntiles, tile_patch, tcnt, S.patch_nodes, S.patch_tiles, code);
         }
         Ev e5(st);
         S.ms_coarse = ms_between(e1, e2);
@@ -2873,6 +2883,13 @@ hjbp_status solve2d(hjbp_plan &p) {
     S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N, d64, cone);
     Ev fr(st);
     RunResult rv;
+    // per-patch residual at retirement: the tiles' last changes (FP64)
+    double *last_chg = nullptr;
+    if (p.patchy && sched.ntiles && !queue_ok) {
+        last_chg = alloc_n<double>(p, sched.ntiles);
+        check_cuda(cudaMemsetAsync(last_chg, 0, sizeof(double) * sched.ntiles, st), "memset");
+        sched.d.last_chg = last_chg;
+    }
     if (fp32) {
         float *b0 = alloc_n<float>(p, N), *b1 = alloc_n<float>(p, N);
         float *d32 = nullptr;
@@ -2897,6 +2914,10 @@ hjbp_status solve2d(hjbp_plan &p) {
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
     if (!rv.converged) status = HJBP_ENOCONV;
+    if (last_chg) {
+        patch_residuals(p, sched.ntiles, sched.d.tile_patch, last_chg);
+        sched.d.last_chg = nullptr;
+    }
     // per-patch launch counts
     if (rv.launches > 0) {
         std::vector<uint64_t> ph(rv.launches);
@@ -2911,7 +2932,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     // ---- FP64 polishing
     if (fp32) {
         double *pa = alloc_n<double>(p, N), *pb = alloc_n<double>(p, N);
-        float *mc = alloc_n<float>(p, 1);
+        double *mc = alloc_n<double>(p, 1);
         k_widen<<<grid_for(N), 256, 0, st>>>(N, p.u32, pa);
         ++p.stats.kernel_launches;
         const CtlTable2<double> ct = make_table<double>(p);
@@ -2920,13 +2941,13 @@ hjbp_status solve2d(hjbp_plan &p) {
         double last = 0.0;
         int it = 0;
         for (; it < 8; ++it) {
-            check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
+            check_cuda(cudaMemsetAsync(mc, 0, sizeof(double), st), "memset");
             k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ctf, ct, d64, p.astar, cone);
             ++p.stats.kernel_launches;
             check_cuda(cudaGetLastError(), "polish");
             std::swap(pa, pb);
-            float hm = 0.f;
-            check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(float), cudaMemcpyDeviceToHost, st), "polish res");
+            double hm = 0.0;
+            check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(double), cudaMemcpyDeviceToHost, st), "polish res");
             check_cuda(cudaStreamSynchronize(st), "polish sync");
             last = hm;
             if (hm < d.tol) {

@@ -111,12 +111,17 @@ __device__ __forceinline__ float warp_max3(float v) {
     return v;
 }
 
+__device__ __forceinline__ double warp_max3(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Max over the 64 threads of the CTA (two warps).
-__device__ __forceinline__ float block_max64(float v, float *scratch) {
+template <typename V> __device__ __forceinline__ V block_max64(V v, V *scratch) {
     v = warp_max3(v);
     if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
     __syncthreads();
-    const float r = fmaxf(scratch[0], scratch[1]);
+    const V r = scratch[0] > scratch[1] ? scratch[0] : scratch[1];
     __syncthreads();
     return r;
 }
@@ -194,12 +199,13 @@ __global__ void k_narrow_data3(int64_t N, const double *__restrict__ u0, float *
 
 // ------------------------------------------------------------ scheduling --
 
-__global__ void k_schedule3d(Grid3 g, TileSched s, int par, float tol, int launch) {
+__global__ void k_schedule3d(Grid3 g, TileSched s, int par, double tol, int launch) {
     const int ntiles = g.ntx * g.nty * g.ntz;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     if (t == 0 && s.count_hist) s.count_hist[launch] = s.count[par];
-    if (s.processed[t]) {
+    const bool ran = s.processed[t] != 0;
+    if (ran) {
         s.latest[t] ^= 1;
         s.processed[t] = 0;
     }
@@ -219,12 +225,13 @@ __global__ void k_schedule3d(Grid3 g, TileSched s, int par, float tol, int launc
         const int k = atomicAdd(&s.count[par ^ 1], 1);
         (par ? s.list[0] : s.list[1])[k] = t;
     }
-    const float my = (par ? s.chg[1] : s.chg[0])[t];
+    const double my = (par ? s.chg[1] : s.chg[0])[t];
     if (my > tol && s.tile_patch && s.patch_hist)
         atomicOr(reinterpret_cast<unsigned long long *>(&s.patch_hist[launch]),
                  (unsigned long long)s.tile_patch[t]);
-    if (my > 0.f && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
-    (par ? s.chg[0] : s.chg[1])[t] = 0.f;
+    if (my > 0.0 && s.res_hist) atomic_max_pos(&s.res_hist[launch], my);
+    if (ran && s.last_chg) s.last_chg[t] = my;
+    (par ? s.chg[0] : s.chg[1])[t] = 0.0;
 }
 
 // Tile image in shared memory: u[z][y][x] with a one-node halo.
@@ -232,7 +239,7 @@ template <typename T, bool kDir = false> struct Tile3 {
     T u[kT3 + 2][kT3 + 2][kT3 + 3];
     int8_t c[kT3 + 2][kT3 + 2][kT3 + 4];
     T d[kDir ? kT3 + 2 : 1][kDir ? kT3 + 2 : 1][kDir ? kT3 + 3 : 1];   // Dirichlet data (Eq. dbc)
-    float red[2];
+    double red[2];
 };
 
 template <typename T, bool kDir>
@@ -260,13 +267,13 @@ __device__ __forceinline__ void load_tile3(const Grid3 &g, const TileSched &s, c
 }
 
 template <typename T, bool kDir>
-__device__ __forceinline__ float store_tile3(const Grid3 &g, const TileSched &s, int t, T *__restrict__ b0,
+__device__ __forceinline__ double store_tile3(const Grid3 &g, const TileSched &s, int t, T *__restrict__ b0,
                                              T *__restrict__ b1, int x0, int y0, int z0, Tile3<T, kDir> &sm,
                                              int clamp = 1) {
     const int cur = s.latest[t];
     T *dst = cur ? b0 : b1;
     const T *src = cur ? b1 : b0;
-    float mc = 0.f;
+    double mc = 0.0;
     for (int e = threadIdx.x; e < kT3 * kT3 * kT3; e += blockDim.x) {
         const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
@@ -275,11 +282,10 @@ __device__ __forceinline__ float store_tile3(const Grid3 &g, const TileSched &s,
         const T v = sm.u[lz + 1][ly + 1][lx + 1];
         const T o = src[i];
         dst[i] = v;
-        const bool vi = v >= Num<T>::thresh(), oi = o >= Num<T>::thresh();
-        float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : (float)fabs((double)v - (double)o));
+        double d = change64(v, o, Num<T>::thresh());
         // the plain update (warm start) may move by a few units in the last place
-        if (!clamp && d <= (float)(Num<T>::noise() * fabs((double)v))) d = 0.f;
-        mc = fmaxf(mc, d);
+        if (!clamp && d <= Num<T>::noise() * fabs((double)v)) d = 0.0;
+        mc = fmax(mc, d);
     }
     return block_max64(mc, sm.red);
 }
@@ -615,7 +621,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                 __syncthreads();
             }
         }
-    const float mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm, clamp);
+    const double mc = store_tile3(g, s, t, b0, b1, x0, y0, z0, sm, clamp);
     nfree = __reduce_add_sync(0xffffffffu, nfree);
     if ((tid & 31) == 0 && updates && nfree)
         atomicAdd(updates, (unsigned long long)nfree * (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
@@ -774,7 +780,7 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
     if (flips) atomicAdd(&flips_s, flips);
     __syncthreads();
     if (tid == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = flips_s > 0 ? 1.f : 0.f;
+        (par ? s.chg[1] : s.chg[0])[t] = flips_s > 0 ? 1.0 : 0.0;
         s.processed[t] = 1;
     }
 }
@@ -858,7 +864,7 @@ __global__ void __launch_bounds__(kT3n) k_peel3d(Grid3 g, int8_t *__restrict__ c
     if (flips) atomicAdd(&flips_s, flips);
     __syncthreads();
     if (tid == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = flips_s > 0 ? 1.f : 0.f;
+        (par ? s.chg[1] : s.chg[0])[t] = flips_s > 0 ? 1.0 : 0.0;
         s.processed[t] = 1;
     }
 }
@@ -1150,10 +1156,10 @@ __global__ void k_feedback3g(Grid3 g, const int8_t *__restrict__ code, const dou
 // eight controls need no FP32 filter).  Outside the patch: +inf, or the
 // Dirichlet data (Eq. dbc).
 __global__ void k_polish3g(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ uin,
-                           double *__restrict__ uout, float *maxchg, const double *__restrict__ dval, const Gen3 gen) {
+                           double *__restrict__ uout, double *maxchg, const double *__restrict__ dval, const Gen3 gen) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
-    float mc = 0.f;
+    double mc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t cd = code[i];
         double v = uin[i];
@@ -1177,14 +1183,14 @@ __global__ void k_polish3g(Grid3 g, const int8_t *__restrict__ code, const doubl
                 best = x < best ? x : best;
             }
             if (best < Num<double>::thresh()) {
-                mc = fmaxf(mc, (float)fabs(best - v));
+                mc = fmax(mc, fabs(best - v));
                 v = best;
             }
         }
         uout[i] = v;
     }
     mc = warp_max3(mc);
-    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(maxchg, mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.0) atomic_max_pos(maxchg, mc);
 }
 
 // --------------------------------------------------- Step 3.1: colours phi --
@@ -1212,7 +1218,7 @@ template <int RG, bool kS> struct Phi3Smem {
     // signs (bit 0..2: x, y, z positive) of every control
     float4 tw[kMaxControls][2];
     uint8_t toff[kMaxControls];
-    float red[2];
+    double red[2];
 };
 
 // FP32 colour transport (bulk: monotone max from 0; correction: with source).
@@ -1339,7 +1345,7 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     const int cur = s.latest[t];
     float *dst = cur ? b0 : b1;
     const float *old = cur ? b1 : b0;
-    float mc = 0.f;
+    double mc = 0.0;
     // predicated and unrolled so that the reads of the previous values overlap
 #pragma unroll
     for (int k = 0; k < kT3 * kT3 * kT3 / kT3n; ++k) {
@@ -1353,7 +1359,7 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                 const float v = sm.u[q][lz + 1][ly + 1][lx + 1];
                 const float o = old[(int64_t)q * N + i];
                 dst[(int64_t)q * N + i] = v;
-                mc = fmaxf(mc, fabsf(v - o));
+                mc = fmax(mc, (double)fabsf(v - o));
             }
         }
     }
@@ -1457,7 +1463,8 @@ __global__ void k_fill3d(Grid3 g, const int8_t *__restrict__ lin, int8_t *__rest
 __global__ void __launch_bounds__(kT3n) k_compact3d(Grid3 g, const int8_t *__restrict__ code,
                                                     uint64_t *__restrict__ tile_patch,
                                                     unsigned long long *__restrict__ patch_nodes,
-                                                    unsigned long long *__restrict__ patch_tiles) {
+                                                    unsigned long long *__restrict__ patch_tiles,
+                                                    int *__restrict__ tile_cnt, int R) {
     const int t = blockIdx.x;
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     __shared__ unsigned long long mask_s;
@@ -1479,6 +1486,7 @@ __global__ void __launch_bounds__(kT3n) k_compact3d(Grid3 g, const int8_t *__res
         if (cnt_s[j]) {
             atomicAdd(&patch_nodes[j], (unsigned long long)cnt_s[j]);
             atomicAdd(&patch_tiles[j], 1ull);
+            if (j < R) tile_cnt[(int64_t)t * R + j] = cnt_s[j];
         }
     if (threadIdx.x == 0) tile_patch[t] = mask_s;
 }
@@ -1487,7 +1495,7 @@ __global__ void __launch_bounds__(kT3n) k_compact3d(Grid3 g, const int8_t *__res
 // covers the eight-term trilinear sum.
 // cone (AO3): the minimum over the node's cone of astar.
 __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const double *__restrict__ h,
-                           const double *__restrict__ uin, double *__restrict__ uout, float *maxchg,
+                           const double *__restrict__ uin, double *__restrict__ uout, double *maxchg,
                            const CtlTable3<float> c32, const CtlTable3<double> c64,
                            const double *__restrict__ dval, const Cone3 *__restrict__ cone = nullptr,
                            const uint8_t *__restrict__ astar = nullptr) {
@@ -1504,7 +1512,7 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
         t64[m].k[7] = c64.kap[m];
     }
     __syncthreads();
-    float mc = 0.f;
+    double mc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int8_t cd = code[i];
         double v = uin[i];
@@ -1593,14 +1601,14 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
                         }
                     }
                 }
-                mc = fmaxf(mc, (float)fabs(best - v));
+                mc = fmax(mc, fabs(best - v));
                 v = best;
             }
         }
         uout[i] = v;
     }
     mc = warp_max3(mc);
-    if ((threadIdx.x & 31) == 0 && mc > 0.f) atomic_max_pos(maxchg, mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.0) atomic_max_pos(maxchg, mc);
 }
 
 // ======================================================================
@@ -1638,13 +1646,13 @@ Sched3 make_sched3(hjbp_plan &p, const Grid3 &g, int hist) {
     s.d.list[0] = alloc3<int>(p, nt);
     s.d.list[1] = alloc3<int>(p, nt);
     s.d.count = alloc3<int>(p, 2);
-    s.d.chg[0] = alloc3<float>(p, nt);
-    s.d.chg[1] = alloc3<float>(p, nt);
+    s.d.chg[0] = alloc3<double>(p, nt);
+    s.d.chg[1] = alloc3<double>(p, nt);
     s.d.latest = alloc3<uint8_t>(p, nt);
     s.d.processed = alloc3<uint8_t>(p, nt);
     s.d.tile_patch = nullptr;
     s.d.patch_hist = alloc3<uint64_t>(p, hist);
-    s.d.res_hist = alloc3<float>(p, hist);
+    s.d.res_hist = alloc3<double>(p, hist);
     s.d.count_hist = alloc3<int>(p, hist);
     s.iota = alloc3<int>(p, nt);
     k_iota3<<<grid_for3(nt), 256, 0, p.stream>>>(nt, s.iota);
@@ -1656,10 +1664,10 @@ struct Run3 {
     int64_t tile_visits = 0;
     int launches = 0;
     bool converged = false;
-    float last_res = 0.f;
+    double last_res = 0.0;
 };
 
-template <class Sweep> Run3 run_tiles3(hjbp_plan &p, const Grid3 &g, Sched3 &s, float tol, int cap, Sweep sweep) {
+template <class Sweep> Run3 run_tiles3(hjbp_plan &p, const Grid3 &g, Sched3 &s, double tol, int cap, Sweep sweep) {
     Run3 rr;
     if (s.ntiles == 0) {
         rr.converged = true;
@@ -1670,12 +1678,12 @@ template <class Sweep> Run3 run_tiles3(hjbp_plan &p, const Grid3 &g, Sched3 &s, 
     check_cuda(cudaMemcpyAsync(s.d.list[0], s.iota, sizeof(int) * nt, cudaMemcpyDeviceToDevice, st), "reset");
     const int counts[2] = {nt, 0};
     check_cuda(cudaMemcpyAsync(s.d.count, counts, sizeof(counts), cudaMemcpyHostToDevice, st), "reset");
-    check_cuda(cudaMemsetAsync(s.d.chg[0], 0, sizeof(float) * nt, st), "reset");
-    check_cuda(cudaMemsetAsync(s.d.chg[1], 0, sizeof(float) * nt, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.chg[0], 0, sizeof(double) * nt, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.chg[1], 0, sizeof(double) * nt, st), "reset");
     check_cuda(cudaMemsetAsync(s.d.latest, 0, nt, st), "reset");
     check_cuda(cudaMemsetAsync(s.d.processed, 0, nt, st), "reset");
     check_cuda(cudaMemsetAsync(s.d.patch_hist, 0, sizeof(uint64_t) * s.hist, st), "reset");
-    check_cuda(cudaMemsetAsync(s.d.res_hist, 0, sizeof(float) * s.hist, st), "reset");
+    check_cuda(cudaMemsetAsync(s.d.res_hist, 0, sizeof(double) * s.hist, st), "reset");
     check_cuda(cudaMemsetAsync(s.d.count_hist, 0, sizeof(int) * s.hist, st), "reset");
     check_cuda(cudaStreamSynchronize(st), "reset sync");
     cap = std::min(cap, s.hist);
@@ -1700,10 +1708,10 @@ template <class Sweep> Run3 run_tiles3(hjbp_plan &p, const Grid3 &g, Sched3 &s, 
         }
     }
     std::vector<int> ch(L);
-    std::vector<float> rh(L);
+    std::vector<double> rh(L);
     if (L) {
         check_cuda(cudaMemcpyAsync(ch.data(), s.d.count_hist, sizeof(int) * L, cudaMemcpyDeviceToHost, st), "hist");
-        check_cuda(cudaMemcpyAsync(rh.data(), s.d.res_hist, sizeof(float) * L, cudaMemcpyDeviceToHost, st), "hist");
+        check_cuda(cudaMemcpyAsync(rh.data(), s.d.res_hist, sizeof(double) * L, cudaMemcpyDeviceToHost, st), "hist");
         check_cuda(cudaStreamSynchronize(st), "hist sync");
     }
     for (int l = 0; l < L; ++l)
@@ -1953,7 +1961,7 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
     const CtlTable3<T> ct = make_table3<T>(p);
     const bool timed = (p.desc.flags & HJBP_FLAG_TIME_SWEEPS) != 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
-    Run3 rr = run_tiles3(p, g, s, (float)tol, cap, [&](int par) {
+    Run3 rr = run_tiles3(p, g, s, tol, cap, [&](int par) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (timed) {
             check_cuda(cudaEventCreate(&a), "event");
@@ -2067,8 +2075,8 @@ Run3 coarse3(hjbp_plan &p, const Grid3 &gc, const int8_t *code, const float *h32
     const CtlTable3<double> c64 = make_table3<double>(p);
     const CtlTable3<float> c32 = make_table3<float>(p);
     constexpr int chunk = 8;
-    float *res = alloc3<float>(p, chunk);
-    float hres[chunk];
+    double *res = alloc3<double>(p, chunk);
+    double hres[chunk];
     // Jacobi moves information one cell per sweep; the cap covers many
     // crossings of the grid
     const int pcap = std::min(cap, 8 * (gc.n0 + gc.n1 + gc.n2) + 64);
@@ -2233,7 +2241,7 @@ hjbp_status solve3d(hjbp_plan &p) {
                     constexpr int G = decltype(tag)::value;
                     k_phi_init3d<G><<<grid_for3(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++S.kernel_launches;
-                    Run3 rp = run_tiles3(p, g, sched, (float)std::max(tolp, 2e-7), cap, [&](int par) {
+                    Run3 rp = run_tiles3(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par) {
                         if (per_node)
                             k_phi3d<G, false, true><<<sched.ntiles, kT3n, 0, st>>>(
                                 g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dct, gfine);
@@ -2306,10 +2314,13 @@ hjbp_status solve3d(hjbp_plan &p) {
             uint64_t *tile_patch = alloc3<uint64_t>(p, sched.ntiles);
             unsigned long long *pn = alloc3<unsigned long long>(p, kMaxTargets);
             unsigned long long *pt = alloc3<unsigned long long>(p, kMaxTargets);
+            int *tcnt = alloc3<int>(p, (int64_t)sched.ntiles * R);
             check_cuda(cudaMemsetAsync(pn, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
             check_cuda(cudaMemsetAsync(pt, 0, sizeof(unsigned long long) * kMaxTargets, st), "memset");
+            check_cuda(cudaMemsetAsync(tcnt, 0, sizeof(int) * std::max<int64_t>(1, (int64_t)sched.ntiles * R), st),
+                       "memset");
             if (sched.ntiles) {
-                k_compact3d<<<sched.ntiles, kT3n, 0, st>>>(g, code, tile_patch, pn, pt);
+                k_compact3d<<<sched.ntiles, kT3n, 0, st>>>(g, code, tile_patch, pn, pt, tcnt, R);
                 ++S.kernel_launches;
             }
             sched.d.tile_patch = tile_patch;
@@ -2321,6 +2332,8 @@ hjbp_status solve3d(hjbp_plan &p) {
                 S.patch_nodes[j] = (int64_t)hn[j];
                 S.patch_tiles[j] = (int64_t)ht[j];
             }
+            // per-patch tile and node lists (CSR)
+            build_patch_lists(p, tile_geom(d), sched.ntiles, tile_patch, tcnt, S.patch_nodes, S.patch_tiles, code);
         }
         Ev3 e5(st);
         S.ms_coarse = ms3(e1, e2);
@@ -2351,6 +2364,13 @@ hjbp_status solve3d(hjbp_plan &p) {
     S.sweeps_reach += reach3(p, g, code, rch, sched, N, d64, gf, cone);
     Ev3 fr(st);
     Run3 rv;
+    // per-patch residual at retirement: the tiles' last changes (FP64)
+    double *last_chg = nullptr;
+    if (p.patchy && sched.ntiles) {
+        last_chg = alloc3<double>(p, sched.ntiles);
+        check_cuda(cudaMemsetAsync(last_chg, 0, sizeof(double) * sched.ntiles, st), "memset");
+        sched.d.last_chg = last_chg;
+    }
     if (fp32) {
         float *b0 = alloc3<float>(p, N), *b1 = alloc3<float>(p, N);
         float *d32 = nullptr;
@@ -2369,6 +2389,10 @@ hjbp_status solve3d(hjbp_plan &p) {
     S.sweeps_fine = rv.launches;
     S.residual_fine = rv.last_res;
     if (!rv.converged) status = HJBP_ENOCONV;
+    if (last_chg) {
+        patch_residuals(p, sched.ntiles, sched.d.tile_patch, last_chg);
+        sched.d.last_chg = nullptr;
+    }
     if (rv.launches > 0) {
         std::vector<uint64_t> ph(rv.launches);
         check_cuda(cudaMemcpyAsync(ph.data(), sched.d.patch_hist, sizeof(uint64_t) * rv.launches,
@@ -2381,7 +2405,7 @@ hjbp_status solve3d(hjbp_plan &p) {
     Ev3 f1(st);
     if (fp32) {
         double *pa = alloc3<double>(p, N), *pb = alloc3<double>(p, N);
-        float *mc = alloc3<float>(p, 1);
+        double *mc = alloc3<double>(p, 1);
         k_widen<<<grid_for3(N), 256, 0, st>>>(N, p.u32, pa);
         ++S.kernel_launches;
         const CtlTable3<double> c64 = make_table3<double>(p);
@@ -2389,7 +2413,7 @@ hjbp_status solve3d(hjbp_plan &p) {
         double last = 0.0;
         int it = 0;
         for (; it < 8; ++it) {
-            check_cuda(cudaMemsetAsync(mc, 0, sizeof(float), st), "memset");
+            check_cuda(cudaMemsetAsync(mc, 0, sizeof(double), st), "memset");
             if (per_node)
                 k_polish3g<<<grid_for3(N, 128), 128, 0, st>>>(g, code, pa, pb, mc, d64, gfine);
             else
@@ -2398,8 +2422,8 @@ hjbp_status solve3d(hjbp_plan &p) {
             ++S.kernel_launches;
             check_cuda(cudaGetLastError(), "polish3");
             std::swap(pa, pb);
-            float hm = 0.f;
-            check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(float), cudaMemcpyDeviceToHost, st), "polish res");
+            double hm = 0.0;
+            check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(double), cudaMemcpyDeviceToHost, st), "polish res");
             check_cuda(cudaStreamSynchronize(st), "polish sync");
             last = hm;
             if (hm < d.tol) {

@@ -1,19 +1,25 @@
 // noalloc.cu -- hjbp_solve_global2d_noalloc: the plain global 2D solve (FP64)
 // for callers that cannot allocate memory.
 //
-// Some callers cannot call cudaMalloc (or any allocator) at solve time: code
-// that runs while a CUDA stream is being captured into a graph, real-time
-// loops that forbid allocation after start-up, or hosts whose memory pool is
-// owned by someone else.  This entry point runs the same kernels as
-// hjbp_solve does for a global 2D FP64 problem, but takes every scratch array
-// from one file-scope device array of fixed size (kScratchBytes) instead of
-// allocating.  The caller passes the problem and the two output arrays.
+// Some callers cannot call cudaMalloc (or any allocator) at solve time:
+// real-time control loops that forbid allocation once they have started (an
+// allocation can block for an unbounded time or fail when memory is
+// fragmented), or hosts whose device memory pool is owned by someone else.
+// This entry point runs the same kernels as hjbp_solve does for a global 2D
+// FP64 problem, but takes every scratch array from one file-scope device array
+// of fixed size (kScratchBytes) instead of allocating.  The caller passes the
+// problem and the two output arrays.
+//
+// The call is synchronous: between launches it reads the active-tile and
+// pruned-node counts back into host variables and waits for them, and it
+// synchronises the stream before returning.
 //
 // The device array lives in every GPU that loads the library until the
 // process exits.  In host code its name is only a host-side stand-in: the
-// device address is obtained once per device with cudaGetSymbolAddress and
-// cached.  The first call on a device does that set-up, so the first call on
-// each device should come before any stream capture.  Every call shares the
+// device address (and the SM count used to size grids) is looked up once per
+// device index with cudaGetSymbolAddress and cached for the process lifetime,
+// which assumes one primary context per device (no cudaDeviceReset between
+// calls).  The first call on a device does that set-up.  Every call shares the
 // array and it keeps the previous call's contents, so the solve clears what
 // must start at zero; calls that overlap on the GPU (several streams or
 // threads at once) race on the array and must be serialised by the caller.
@@ -31,10 +37,12 @@ namespace hjbp {
 // Kernels defined in kernels2d.cu (the same ones hjbp_solve launches).
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values, int8_t *code,
                           float *h32, double *h64, double *fixed, DynParams dp, ObstacleSet os);
-__global__ void k_schedule2d(Grid2 g, TileSched s, int par, float tol, int launch);
+__global__ void k_schedule2d(Grid2 g, TileSched s, int par, double tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
                                                 ReachTable2 rt, int passes, const double *dterm,
                                                 const uint8_t *astar, const Cone2 *cone);
+__global__ void __launch_bounds__(32) k_peel2d(Grid2 g, int8_t *code, TileSched s, int par, ReachTable2 rt,
+                                               const double *dterm, const uint8_t *astar, const Cone2 *cone);
 __global__ void k_reach_prune(int64_t N, int8_t *code, const uint8_t *rch, unsigned long long *removed);
 __global__ void k_merge_targets(int64_t N, int8_t *code);
 __global__ void k_final_labels(int64_t N, const int8_t *code0, const int8_t *code, int8_t *label,
@@ -62,20 +70,27 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 constexpr int kMaxDevices = 128;
 void *g_addr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device.
-const char *scratch_address(void **out) {
+// Device address of g_scratch and the SM count of the current device, looked
+// up once per device index.
+const char *scratch_address(void **out, int *sms) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return "cudaGetDevice failed";
     if (dev < 0 || dev >= kMaxDevices) return "device index out of range";
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            return "cudaDeviceGetAttribute(MultiProcessorCount) failed";
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) return "cudaGetSymbolAddress of the scratch array failed";
+        g_sms[dev] = n;
         g_addr[dev] = p;
     }
     *out = g_addr[dev];
+    *sms = g_sms[dev];
     return nullptr;
 }
 
@@ -104,8 +119,8 @@ Layout layout(int64_t N, int ntiles) {
     L.list1 = take(sizeof(int) * nt);
     L.iota = take(sizeof(int) * nt);
     L.count = take(2 * sizeof(int));
-    L.chg0 = take(sizeof(float) * nt);
-    L.chg1 = take(sizeof(float) * nt);
+    L.chg0 = take(sizeof(double) * nt);
+    L.chg1 = take(sizeof(double) * nt);
     L.latest = take(nt);
     L.processed = take(nt);
     L.counters = take(2 * sizeof(unsigned long long));
@@ -117,9 +132,11 @@ __global__ void k_iota_noalloc(int n, int *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
 }
 
-int blocks_for(int64_t n) {
-    const int64_t b = (n + 255) / 256;
-    return (int)(b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b));
+// Grid of 256-thread blocks for n elements: at most 64 blocks per SM (the
+// kernels stride over the rest).
+int blocks_for(int64_t n, int sms) {
+    const int64_t b = (n + 255) / 256, most = (int64_t)sms * 64;
+    return (int)(b < 1 ? 1 : (b > most ? most : b));
 }
 
 // Host-side validation without allocating; returns a static message or null.
@@ -148,6 +165,10 @@ const char *check_desc(const hjbp_problem_desc *d) {
     if (const char *e = check_obstacles(d)) return e;
     if (d->dyn != HJBP_DYN_SPEED || d->target_kind != HJBP_TARGET_BALLS)
         return "the no-allocation entry point takes f = c(x) a and ball targets";
+    // the options hjbp_create rejects for a plain global solve
+    if (d->flags & (HJBP_FLAG_DIRICHLET | HJBP_FLAG_WARM_START | HJBP_FLAG_CAUSAL_SWEEPS))
+        return "Dirichlet patch boundaries, the warm start and causal sweeps need a patchy solve (n_coarse)";
+    if (d->reduce_r != 0.0) return "reduce_r needs a patchy solve (n_coarse)";
     if (d->speed == HJBP_C_FOURIER2D) {
         double norm = 0.0;
         for (int i = 0; i < 16; ++i) norm += std::fabs(d->speed_params[i]);
@@ -170,7 +191,7 @@ hjbp_status fail_static(hjbp_status s, const char *msg) {
 // Sweep + schedule launches until no tile is active (count read back every
 // few launches into a stack variable) or the cap is hit.
 template <class Sweep>
-hjbp_status run(cudaStream_t st, const Grid2 &g, TileSched &s, int ntiles, int *iota_list, float tol, int cap,
+hjbp_status run(cudaStream_t st, const Grid2 &g, TileSched &s, int ntiles, int *iota_list, double tol, int cap,
                 bool *converged, Sweep sweep) {
     *converged = false;
     if (ntiles == 0) {
@@ -180,8 +201,8 @@ hjbp_status run(cudaStream_t st, const Grid2 &g, TileSched &s, int ntiles, int *
     const int counts[2] = {ntiles, 0};
     NA_CHECK(cudaMemcpyAsync(s.list[0], iota_list, sizeof(int) * ntiles, cudaMemcpyDeviceToDevice, st));
     NA_CHECK(cudaMemcpyAsync(s.count, counts, sizeof(counts), cudaMemcpyHostToDevice, st));
-    NA_CHECK(cudaMemsetAsync(s.chg[0], 0, sizeof(float) * ntiles, st));
-    NA_CHECK(cudaMemsetAsync(s.chg[1], 0, sizeof(float) * ntiles, st));
+    NA_CHECK(cudaMemsetAsync(s.chg[0], 0, sizeof(double) * ntiles, st));
+    NA_CHECK(cudaMemsetAsync(s.chg[1], 0, sizeof(double) * ntiles, st));
     NA_CHECK(cudaMemsetAsync(s.latest, 0, ntiles, st));
     NA_CHECK(cudaMemsetAsync(s.processed, 0, ntiles, st));
     NA_CHECK(cudaStreamSynchronize(st));
@@ -214,7 +235,9 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     if (!u_out || !labels_out) return fail_static(HJBP_EINVAL, "output pointers must be device arrays");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     void *base = nullptr;
-    if (const char *e = scratch_address(&base)) return fail_static(HJBP_ECUDA, e);
+    int sms = 0;
+    if (const char *e = scratch_address(&base, &sms)) return fail_static(HJBP_ECUDA, e);
+    auto blocks_for = [sms](int64_t n) { return ::blocks_for(n, sms); };
 
     const int n0 = desc->n[0], n1 = desc->n[1];
     const int64_t N = (int64_t)n0 * n1;
@@ -243,8 +266,8 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     s.list[0] = reinterpret_cast<int *>(sc + L.list0);
     s.list[1] = reinterpret_cast<int *>(sc + L.list1);
     s.count = reinterpret_cast<int *>(sc + L.count);
-    s.chg[0] = reinterpret_cast<float *>(sc + L.chg0);
-    s.chg[1] = reinterpret_cast<float *>(sc + L.chg1);
+    s.chg[0] = reinterpret_cast<double *>(sc + L.chg0);
+    s.chg[1] = reinterpret_cast<double *>(sc + L.chg1);
     s.latest = sc + L.latest;
     s.processed = sc + L.processed;
     // 0..ntiles-1, copied into list0 before each phase
@@ -304,8 +327,15 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     // each round prunes at least one node or ends the loop (at most N rounds)
     for (int64_t round = 0;; ++round) {
         if (round > N) return fail_static(HJBP_ECUDA, "reachability pruning did not settle");
+        // peel the nodes left without any usable control first: they cannot be
+        // in S*, and removing them here saves one reach round per such node
+        hjbp_status ps = run(st, g, s, ntiles, iota, 0.5, 1 << 18, &conv, [&](int par) {
+            k_peel2d<<<ntiles, 32, 0, st>>>(g, code, s, par, rt, nullptr, nullptr, nullptr);
+        });
+        if (ps != HJBP_OK) return ps;
+        if (!conv) return fail_static(HJBP_ECUDA, "peeling did not settle");
         NA_CHECK(cudaMemsetAsync(rch, 0, (size_t)N, st));
-        hjbp_status rs = run(st, g, s, ntiles, iota, 0.5f, 1 << 18, &conv, [&](int par) {
+        hjbp_status rs = run(st, g, s, ntiles, iota, 0.5, 1 << 18, &conv, [&](int par) {
             k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt, 2, nullptr, nullptr, nullptr);
         });
         if (rs != HJBP_OK) return rs;
@@ -322,7 +352,7 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     // Value iteration from M on S*, FP64, to the sup-norm tolerance.
     launch_init_values2d_f64(blocks_for(N), st, N, code, kStartValue, b0, b1);
     NA_CHECK(cudaGetLastError());
-    hjbp_status vs = run(st, g, s, ntiles, iota, (float)desc->tol, cap, &conv, [&](int par) {
+    hjbp_status vs = run(st, g, s, ntiles, iota, desc->tol, cap, &conv, [&](int par) {
         launch_value2d_f64(ntiles, st, g, code, h64, b0, b1, s, par, 2, ct);
     });
     if (vs != HJBP_OK) return vs;

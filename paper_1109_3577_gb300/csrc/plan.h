@@ -9,6 +9,25 @@
 
 #include "../../include/hjbp.h"
 
+// Tiling of the fine grid for the tile sweeps and the patch lists: tiles of
+// side^dim interior nodes starting at node (1, 1[, 1]), ntx x nty [x ntz].
+struct TileGeom {
+    int dim, side, ntx, nty, ntz, n0, n1, n2;
+};
+
+// Patch compaction (Sec. 3): per patch j its tiles and nodes in CSR form
+// (see compact.cu).  The device arrays are allocated at create with their
+// largest sizes and filled by every patchy solve.
+struct PatchLists {
+    bool built = false;
+    int R = 0;
+    TileGeom geom{};
+    std::vector<int64_t> tile_off, node_off;   // host copies of the offsets (R + 1 each)
+    int64_t *d_tile_off = nullptr, *d_node_off = nullptr;
+    int *d_tile_ids = nullptr, *d_tile_nodes = nullptr, *d_node_ids = nullptr;
+    int64_t cap_tiles = 0, cap_nodes = 0;      // allocated entries
+};
+
 struct hjbp_plan {
     // --- descriptor (copied at create) ---
     hjbp_problem_desc desc;
@@ -50,6 +69,7 @@ struct hjbp_plan {
     uint8_t *astar = nullptr;       // coarse feedback (Step 2)
     double *phi = nullptr;          // R x N colour fields (Step 3.1)
     float *u32 = nullptr;           // FP32 bulk values
+    PatchLists lists;               // per-patch tile and node lists (patchy solves)
 
     void *dev_alloc(size_t bytes);  // throws std::bad_alloc on failure
     void release_all();
@@ -70,5 +90,16 @@ void set_last_error(const std::string &msg);
 // 2D and 3D drivers: run the whole solve on the plan's stream.
 hjbp_status solve2d(hjbp_plan &p);
 hjbp_status solve3d(hjbp_plan &p);
+
+// Tiling of the plan's fine grid (32^2 tiles in 2D, 8^3 in 3D).
+TileGeom tile_geom(const hjbp_problem_desc &d);
+
+// Fill p.lists from the per-tile patch masks and per-(tile, patch) node
+// counts left by the compaction kernels; counts are the per-patch totals.
+void build_patch_lists(hjbp_plan &p, const TileGeom &tg, int ntiles, const uint64_t *tile_patch, const int *tile_cnt,
+                       const int64_t *patch_nodes, const int64_t *patch_tiles, const int8_t *code);
+
+// stats.residual_patch from the tiles' last changes (FP64).
+void patch_residuals(hjbp_plan &p, int ntiles, const uint64_t *tile_patch, const double *last_chg);
 
 }  // namespace hjbp

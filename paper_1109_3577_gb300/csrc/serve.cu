@@ -195,7 +195,8 @@ size_t footprint(const hjbp_problem_desc *d) {
     const int rg = R >= 4 ? 4 : R;
     // outputs + codes/h + value buffers + colour planes (FP32 x3, FP64 x2 per group) + phi (R planes)
     size_t b = (size_t)N * (8 + 1 + 4 + 8 + 8 + 1 + 1 + 1 + 4 * 3 + 16);
-    if (Nc) b += (size_t)N * (8 + 1 + (size_t)rg * (4 * 3 + 8) + 8 * (size_t)R) + (size_t)Nc * 40;
+    // patchy: + U0, a*, colour planes, phi, the patch lists (node ids, tile entries)
+    if (Nc) b += (size_t)N * (8 + 1 + (size_t)rg * (4 * 3 + 8) + 8 * (size_t)R + 4 + 8) + (size_t)Nc * 40;
     return b + (size_t(8) << 20);
 }
 

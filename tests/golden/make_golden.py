@@ -6,10 +6,13 @@ compact sample of its output under tests/golden/:
   <name>.npz   idx (sampled node indices), u (oracle values there), labels
                (full label map, int8), gap (a* best-vs-second gap at the
                sampled nodes), phimax (max_j phi^j at the sampled nodes),
-               meta (JSON: sizes, sweeps, reachable count, max u, E1/E_inf of
-               the patchy solution against the global one when computed).
+               tie (bit-packed mask over every node: the tie nodes of the
+               label comparison, see tie_mask), meta (JSON: sizes, sweeps,
+               per-patch node counts, reachable count, max u, E1/E_inf of the
+               patchy solution against the global one when computed).
 
 Usage:  python tests/golden/make_golden.py sincos2d 0 [--global]
+        python tests/golden/make_golden.py sin3d 0 --n=129 --nc=33
 """
 from __future__ import annotations
 
@@ -25,6 +28,7 @@ sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
 import workloads as W  # noqa: E402
+from tests._labels import tie_mask  # noqa: E402  (the tie rule of the label comparison)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -43,8 +47,10 @@ def make(family: str, seed: int, with_global: bool, samples: int = 20000, **kw):
         "reachable": int(np.isfinite(r.u).sum()), "max_u": float(r.u[fin].max()),
         "label_counts": {int(k): int(v) for k, v in zip(*np.unique(r.labels, return_counts=True))},
     }
+    tie = tie_mask(r)
+    meta["tie_nodes"] = int(tie.sum())
     out = {"idx": idx, "u": r.u[idx], "labels": r.labels, "gap": r.gap[idx],
-           "phimax": r.phi.max(axis=0)[idx], "astar": r.astar[idx]}
+           "phimax": r.phi.max(axis=0)[idx], "astar": r.astar[idx], "tie": np.packbits(tie)}
     if with_global:
         t2 = time.time()
         g = oracle.global_solve(p.with_(n_coarse=None), tol=1e-10)

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import workloads as W
+from tests._labels import assert_labels
 
 pytestmark = pytest.mark.gpu
 
@@ -52,8 +53,8 @@ def test_dirichlet_matches_oracle(pkg, seed, n, nc, R, radius):
     p = W.sincos2d(seed, n=n, n_coarse=nc, n_targets=R, radius=radius)
     r = _run(pkg, p, flags=pkg.HJBP_FLAG_DIRICHLET)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=True)
-    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=True)
+    assert_labels(r["labels"], ref, p)
     _assert_values(r["u"], ref.u)
 
 
@@ -65,7 +66,7 @@ def test_warm_start_reaches_the_same_fixed_point(pkg, dirichlet):
     flags = pkg.HJBP_FLAG_WARM_START | (pkg.HJBP_FLAG_DIRICHLET if dirichlet else 0)
     r = _run(pkg, p, flags=flags)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=dirichlet)
     _assert_values(r["u"], ref.u)
 
 
@@ -73,7 +74,7 @@ def test_dirichlet_warm_fp64(pkg):
     p = W.sincos2d(4, n=129, n_coarse=17, n_targets=3, radius=0.2)
     r = _run(pkg, p, precision=pkg.HJBP_FP64, flags=pkg.HJBP_FLAG_DIRICHLET | pkg.HJBP_FLAG_WARM_START)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=True)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=True)
     err = _assert_values(r["u"], ref.u)
     assert err < 1e-5
 
@@ -87,7 +88,7 @@ def test_control_cones_match_oracle(pkg, dirichlet, r_fac):
     flags = pkg.HJBP_FLAG_DIRICHLET if dirichlet else 0
     r = _run(pkg, p, flags=flags, reduce_r=r_fac)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet, reduce_r=r_fac)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=dirichlet, reduce_r=r_fac)
     tie = ref.gap < 1e-9 * np.maximum(1.0, np.where(np.isfinite(ref.u0), ref.u0, 1.0))
     assert np.all((r["astar"] == ref.astar) | tie)
     _assert_values(r["u"], ref.u)
@@ -112,8 +113,8 @@ def test_causal_sweeps_reach_the_same_fixed_point(pkg, dirichlet):
     flags = pkg.HJBP_FLAG_CAUSAL_SWEEPS | (pkg.HJBP_FLAG_DIRICHLET if dirichlet else 0)
     r = _run(pkg, p, flags=flags)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet)
-    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=dirichlet)
+    assert_labels(r["labels"], ref, p)
     _assert_values(r["u"], ref.u)
     again = _run(pkg, p, flags=flags)
     assert np.array_equal(r["u"], again["u"]) and np.array_equal(r["labels"], again["labels"])
@@ -132,7 +133,7 @@ def test_tile_queue_matches_oracle(pkg, mode):
         dirichlet = mode == "patchy_dirichlet"
         if dirichlet:
             kw["flags"] |= pkg.HJBP_FLAG_DIRICHLET
-        ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=dirichlet).u
+        ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=dirichlet).u
     prec = pkg.HJBP_FP64 if mode == "patchy_fp64" else None
     r = _run(pkg, p, precision=prec, **kw)
     assert r["status"] == 0
@@ -147,7 +148,7 @@ def test_set_initial_resume_and_sync(pkg):
     to the same values; a start from the oracle's solution plus noise reaches
     the oracle's fixed point too; hjbp_sync reports the last solve."""
     p = W.sincos2d(9, n=129, n_coarse=17, n_targets=3, radius=0.2)
-    ref = oracle.patchy_solve(p, tol=1e-12).u
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True).u
     with pkg.Plan(p) as plan:
         assert plan.solve() == 0
         u1 = plan.values()
@@ -176,8 +177,8 @@ def test_3d_dirichlet_and_warm_start(pkg, mode):
         (pkg.HJBP_FLAG_WARM_START if "warm" in mode else 0)
     r = _run(pkg, p, flags=flags)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet="dirichlet" in mode)
-    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet="dirichlet" in mode)
+    assert_labels(r["labels"], ref, p)
     _assert_values(r["u"], ref.u)
 
 
@@ -187,7 +188,7 @@ def test_control_cones_state_constraints_larger(pkg):
     p = W.sincos2d(5, n=385, n_coarse=49, n_targets=4, radius=0.05)
     r = _run(pkg, p, reduce_r=4.0)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, reduce_r=4.0)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, reduce_r=4.0)
     _assert_values(r["u"], ref.u)
 
 
@@ -201,7 +202,7 @@ def test_3d_control_cones_match_oracle(pkg, mode, r_fac):
     flags = pkg.HJBP_FLAG_DIRICHLET if mode == "dirichlet" else 0
     r = _run(pkg, p, flags=flags, reduce_r=r_fac)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=mode == "dirichlet", reduce_r=r_fac)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=mode == "dirichlet", reduce_r=r_fac)
     _assert_values(r["u"], ref.u)
 
 
@@ -209,7 +210,7 @@ def test_3d_control_cones_fan(pkg):
     p = W.fan3d(n=37, n_coarse=13, n_c=50)
     r = _run(pkg, p, reduce_r=4.0)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, reduce_r=4.0)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, reduce_r=4.0)
     _assert_values(r["u"], ref.u)
 
 
@@ -221,6 +222,6 @@ def test_3d_causal_sweeps_reach_the_same_fixed_point(pkg, family):
     flags = pkg.HJBP_FLAG_CAUSAL_SWEEPS | (pkg.HJBP_FLAG_DIRICHLET if family == "brockett3d" else 0)
     r = _run(pkg, p, flags=flags)
     assert r["status"] == 0
-    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=family == "brockett3d")
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True, dirichlet=family == "brockett3d")
     _assert_values(r["u"], ref.u)
-    assert np.mean(r["labels"] == ref.labels) >= 0.999
+    assert_labels(r["labels"], ref, p)
