@@ -39,7 +39,6 @@ METRIC = "node-control updates/s and solves/s vs plain GPU SL at 1e-4 err; p50/p
 UNIT = "node-control updates/s"
 N_FINE, N_COARSE = 2049, 65
 WORKLOAD = "patchy2d_sincos_n2049_c65_nc64_R4"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 OPS_PER_UPDATE = 4          # canonical bilinear update: 3 FMA + 1 min per node-control pair
 OPS_PER_UPDATE_3D = 8       # canonical trilinear update: 7 FMA + 1 min
@@ -188,26 +187,63 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(p, rows: int):
-    """Time one application of F (Eq. SLscheme) by the C oracle on a band of
-    ``rows`` x n1 consecutive nodes at the middle of the workload's grid (grid
-    rows in 2D, rows of the middle plane in 3D); returns (node-control
-    updates, s).  Brockett's zero control is not admissible and not counted."""
-    import oracle
+CPU_ROWS = 256
 
-    kind, _, _ = oracle.setup(p)
-    x = oracle.grid_coords(p)
-    U = np.where(kind == oracle.GHOST, np.inf, np.linalg.norm(x, axis=1))
-    U[kind == oracle.TARGET] = 0.0
-    count = rows * p.n[0]
-    s0 = max(0, kind.size // 2 - count // 2)
-    band = np.zeros(kind.size, bool)
-    band[s0:s0 + count] = True
-    upd = band & (kind == oracle.FREE)
-    t = time.perf_counter()
-    oracle.sl_apply(p, U, upd=upd, mode=0)
-    dt = time.perf_counter() - t
-    return int(upd.sum()) * admissible_controls(p), dt
+
+class OracleSampler:
+    """Times applications of F (Eq. SLscheme) by the C oracle on a band of
+    ``rows`` x n1 consecutive nodes at the middle of the workload's grid (grid
+    rows in 2D, rows of the middle plane in 3D), with the band's nodes split
+    over all host threads (OpenMP, the paper's Method 1).  sample() returns
+    (node-control updates, s, threads).  Brockett's zero control is not
+    admissible and not counted."""
+
+    def __init__(self, p, rows: int = CPU_ROWS):
+        import oracle
+
+        self.oracle, self.p = oracle, p
+        self.setup = oracle.setup(p)
+        kind = self.setup[0]
+        x = oracle.grid_coords(p)
+        self.U = np.where(kind == oracle.GHOST, np.inf, np.linalg.norm(x, axis=1))
+        self.U[kind == oracle.TARGET] = 0.0
+        count = rows * p.n[0]
+        s0 = max(0, kind.size // 2 - count // 2)
+        band = np.zeros(kind.size, bool)
+        band[s0:s0 + count] = True
+        self.upd = band & (kind == oracle.FREE)
+        self.units = int(self.upd.sum()) * admissible_controls(p)
+
+    def sample(self):
+        t = time.perf_counter()
+        _, used = self.oracle.sl_apply_par(self.p, self.U, upd=self.upd, mode=0, setup_out=self.setup)
+        return self.units, time.perf_counter() - t, used
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def golden_seconds():
+    """Single-core full-solve times of the oracle recorded with the stored
+    full-size solution of the default workload (tests/golden/make_golden.py)."""
+    path = os.path.join(ROOT, "tests", "golden", "sincos2d_n2049_s0.npz")
+    try:
+        meta = json.loads(str(np.load(path)["meta"]))
+        return {"patchy_s": meta.get("seconds_patchy"), "global_s": meta.get("seconds_global"), "cores": 1,
+                "source": "tests/golden/sincos2d_n2049_s0.npz (oracle, tol 1e-10, one core of the machine "
+                          "that wrote it)"}
+    except Exception:
+        return None
 
 
 def admissible_controls(p) -> int:
@@ -235,30 +271,67 @@ def rank_seed(rank: int) -> int:
     return rank
 
 
+def roofline_value(s0, p, alu_peak, sms, sm_max):
+    """The FP32 value sweep (Eq. SLscheme, Step 3.2): algorithmic lane-ops of
+    one launch (node-control updates x 4 in 2D, 8 in 3D) over its average
+    CUDA-event duration."""
+    launches = max(1, s0["sweep_kernel_launches"])
+    per = OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D
+    ops_per_launch = s0["node_control_updates"] * per / launches
+    avg_launch_s = s0["ms_sweep_kernel"] / 1e3 / launches
+    achieved = ops_per_launch / avg_launch_s if avg_launch_s > 0 else None
+    return {"bound": "alu", "kernel": "k_value2d<float>" if p.dim == 2 else "k_value3d<float>",
+            "achieved": achieved / 1e12 if achieved else None, "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
+            "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+            "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_s * 1e3, "launches": launches,
+            "peak_basis": f"{sms} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock); "
+                          f"{per} lane-ops per node-control update"}
+
+
+def roofline_colour(s0, alu_peak, sms, sm_max):
+    """The 2D colour transport (Eq. HJBridotta_discreta, Step 3.1), bulk and
+    correction launches together: 4 lane-ops (1 mul + 2 FMA + 1 max or the
+    source FMA) per node-colour update, over the launches' CUDA-event time."""
+    launches = s0.get("phi_kernel_launches", 0)
+    if not launches or not s0.get("ms_phi_kernel"):
+        return None
+    ops_per_launch = 4.0 * s0["phi_node_colour_updates"] / launches
+    avg_launch_s = s0["ms_phi_kernel"] / 1e3 / launches
+    achieved = ops_per_launch / avg_launch_s
+    return {"bound": "alu", "kernel": "k_phi2d<4, *> (bulk + correction)", "achieved": achieved / 1e12,
+            "peak": alu_peak / 1e12, "unit": "Tlane-op/s", "frac": achieved / alu_peak, "traffic": None,
+            "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_s * 1e3, "launches": launches,
+            "ms_kernel_per_solve": s0["ms_phi_kernel"],
+            "peak_basis": f"{sms} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz; "
+                          f"4 lane-ops per node-colour update"}
+
+
 # --------------------------------------------------------- reference arm --
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     p = problem(0)
-    rows = 48
+    smp = OracleSampler(p)
     for _ in range(args.warmup):
-        oracle_sample(p, rows)
-    tot_u, tot_t = 0, 0.0
+        smp.sample()
+    tot_u, tot_t, used = 0, 0.0, 1
     for _ in range(args.steps):
-        u, t = oracle_sample(p, rows)
+        u, t, used = smp.sample()
         tot_u += u
         tot_t += t
     v = tot_u / tot_t
-    sample = (f"one application of F (Eq. SLscheme) by the single-threaded FP64 C oracle on {rows} x {N_FINE} "
-              f"consecutive nodes at the middle of the {WORKLOAD} grid, {admissible_controls(p)} controls, per step")
+    sample = (f"one application of F (Eq. SLscheme) by the FP64 C oracle, nodes split over {used} host threads "
+              f"(OpenMP), on {CPU_ROWS} x {N_FINE} consecutive nodes at the middle of the {WORKLOAD} grid, "
+              f"{admissible_controls(p)} controls, per step; CPU {cpu_model()}")
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_FINE, "n_coarse": N_COARSE, "n_controls": p.n_controls,
                    "n_targets": p.n_targets, "n_patches": p.n_patches, "tol": p.tol, "seed": 0},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "full_solve_single_core": golden_seconds()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -283,16 +356,19 @@ def run_ours(args, rank, world, dist):
     # CPU baseline first (rank 0 at N = 1 only), before the GPU work starts
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        tu, tt = 0, 0.0
+        smp = OracleSampler(p)
+        tu, tt, used = 0, 0.0, 1
         while tt < 10.0:
-            u, t = oracle_sample(p, 48)
+            u, t, used = smp.sample()
             tu += u
             tt += t
         nc = admissible_controls(p)
-        cpu = {"value": tu / tt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": tu / tt, "unit": UNIT, "cores": used, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"{tu // nc} node updates x {nc} controls: applications of F (Eq. SLscheme) by the "
-                         f"single-threaded FP64 C oracle on 48 x {N_FINE} consecutive nodes at the middle of "
-                         f"the same {WORKLOAD} grid, {tt:.1f} s"}
+                         f"FP64 C oracle with the nodes split over {used} host threads (OpenMP, Method 1 of "
+                         f"Sec. 3) on {CPU_ROWS} x {N_FINE} consecutive nodes at the middle of the same "
+                         f"{WORKLOAD} grid, {tt:.1f} s",
+               "full_solve_single_core": golden_seconds()}
 
     # patch boundary and add-ons of Sec. 6 (defaults: state constraints, none)
     aflags = ((P.HJBP_FLAG_DIRICHLET if args.bc == "dirichlet" else 0) | (P.HJBP_FLAG_WARM_START if args.warm else 0)
@@ -381,22 +457,16 @@ def run_ours(args, rank, world, dist):
         assert np.isfinite(u).any() and lab.size == N
     e2e_value = ncu_e / (statistics.mean(e2e_ms) / 1e3) * world
 
-    # roofline of the dominant kernel (fine-grid value sweep, FP32)
+    # roofline of the dominant kernels (fine-grid value sweep, colour transport; FP32 lane-ops)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6            # lane-ops/s
-    launches = max(1, s0["sweep_kernel_launches"])
-    ops_per_launch = s0["node_control_updates"] * (OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D) / launches
-    avg_launch_s = s0["ms_sweep_kernel"] / 1e3 / launches
-    achieved = ops_per_launch / avg_launch_s if avg_launch_s > 0 else None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * sm_max * 1e6            # lane-ops/s
+    roofline = roofline_value(s0, p, alu_peak, sms, sm_max)
     # the committed capture is of the 2D sweep on the default workload only
-    traffic = profile_traffic() if (FAMILY == "sincos2d" and N_FINE == 2049 and args.bc == "state" and not args.reduce_r) else None
-    roofline = {"bound": "alu", "kernel": "k_value2d<float>" if p.dim == 2 else "k_value3d<float>", "achieved": achieved / 1e12 if achieved else None,
-                "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
-                "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
-                "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock); "
-                              f"{OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D} lane-ops per node-control update"}
+    roofline["traffic"] = profile_traffic() if (FAMILY == "sincos2d" and N_FINE == 2049 and args.bc == "state"
+                                                and not args.reduce_r) else None
+    roofline_phi = roofline_colour(s0, alu_peak, sms, sm_max) if p.dim == 2 and p.n_coarse else None
 
     if rank == 0:
         out = {
@@ -422,6 +492,7 @@ def run_ours(args, rank, world, dist):
             "ms_phases": {k: round(s0[k], 3) for k in ("ms_setup", "ms_coarse", "ms_feedback", "ms_labels",
                                                         "ms_compact", "ms_fine", "ms_reach", "ms_polish", "ms_total")},
             "roofline": roofline,
+            "roofline_phi": roofline_phi,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": statistics.mean(e2e_ms)},
             "clocks": clk.summary(dev),
@@ -429,24 +500,38 @@ def run_ours(args, rank, world, dist):
         }
         if cpu:
             out["cpu_baseline"] = cpu
+        # the other workload families on the same GPU, after the headline measurement
+        if world == 1 and FAMILY == "sincos2d" and N_FINE == 2049 and not args.no_extra:
+            plan.close()
+            del flush
+            torch.cuda.empty_cache()
+            flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+            for key, fn in (("cfg3", lambda: cfg3_measure(P, flush, stream)),
+                            ("batched", lambda: batched_measure(P, 512, args.workers, True)),
+                            ("served", lambda: served_measure(P, 2000, 200.0, args.workers, args.budget_gb))):
+                try:
+                    out[key] = fn()
+                except Exception as e:   # a failed extra must not cost the headline line
+                    out[key] = {"unavailable": f"{type(e).__name__}: {e}"}
+            try:
+                cap = out["served"]["value"]
+                sus = served_measure(P, 1000, round(0.8 * cap, 1), args.workers, args.budget_gb)
+                sus["note"] = "offered at 0.8 x the solves/s measured under the 200/s stream (its capacity)"
+                out["served_sustainable"] = sus
+            except Exception as e:
+                out["served_sustainable"] = {"unavailable": f"{type(e).__name__}: {e}"}
         print(json.dumps(out))
 
 
-def run_batched(args):
-    """Batched family (512 seeded 2D problems of uneven size): throughput of
-    hjbp_batch_solve against the same plans solved one at a time."""
+def batched_measure(P, count: int = 512, workers: int = 8, tune: bool = True):
+    """Batched family (``count`` seeded 2D problems of uneven size): throughput
+    of hjbp_batch_solve against the same plans solved one at a time."""
     import torch
 
-    from paper_1109_3577_gb300 import build as b
-
-    b.build()
-    import paper_1109_3577_gb300 as P
-
-    torch.cuda.set_device(0)
-    probs = W.batched(seed=0, count=args.count)
+    probs = W.batched(seed=0, count=count)
     # launch shapes per problem class from the autotuner, before the timed region
     tunes, classes, t_tune = [None] * len(probs), 0, 0.0
-    if not args.no_tune:
+    if tune:
         t = time.perf_counter()
         for q, p in enumerate(probs):
             d, keep = P.desc_from_problem(p)
@@ -465,25 +550,24 @@ def run_batched(args):
     seq = time.perf_counter() - t
     ncu_seq = sum(pl.stats()["node_control_updates"] for pl in plans)
     t = time.perf_counter()
-    st = P.hjbp_batch_solve([pl.handle for pl in plans], workers=args.workers)
+    st = P.hjbp_batch_solve([pl.handle for pl in plans], workers=workers)
     torch.cuda.synchronize()
     bat = time.perf_counter() - t
     ncu_bat = sum(pl.stats()["node_control_updates"] for pl in plans)
     assert all(s == 0 for s in st), st
     out = {"metric": "solves/s, batched vs one at a time", "workload": f"batched2d_fourier_x{len(probs)}",
            "value": len(probs) / bat, "unit": "solves/s", "one_at_a_time_solves_per_s": len(probs) / seq,
-           "speedup": seq / bat, "batched_s": bat, "one_at_a_time_s": seq, "workers": args.workers,
+           "speedup": seq / bat, "batched_s": bat, "one_at_a_time_s": seq, "workers": workers,
            "total_nodes": nodes, "node_control_updates_per_s_batched": ncu_bat / bat,
            "node_control_updates_per_s_one_at_a_time": ncu_seq / seq, "data": "synthetic", "dtype": "f32",
-           "autotuned": {"classes": classes, "seconds": t_tune} if not args.no_tune else None}
+           "accuracy": "same plans, same kernels: each result equals its solve alone (tests/test_gpu_serving.py)",
+           "autotuned": {"classes": classes, "seconds": t_tune} if tune else None}
     for pl in plans:
         pl.close()
-    print(json.dumps(out))
+    return out
 
 
-def run_serving(args):
-    """Served family: Poisson arrivals (mean 200/s), 80 % 2D / 20 % 3D, replayed
-    in real time against one server; latency from submit to completion."""
+def run_batched(args):
     import torch
 
     from paper_1109_3577_gb300 import build as b
@@ -492,13 +576,20 @@ def run_serving(args):
     import paper_1109_3577_gb300 as P
 
     torch.cuda.set_device(0)
-    stream = W.serving_stream(seed=0, count=args.count, rate=args.rate)
+    print(json.dumps(batched_measure(P, args.count or 512, args.workers, not args.no_tune)))
+
+
+def served_measure(P, count: int = 2000, rate: float = 200.0, workers: int = 8, budget_gb: float = 64.0):
+    """Served family: Poisson arrivals (mean ``rate``/s), 80 % 2D / 20 % 3D,
+    replayed in real time against one server; latency from submit to
+    completion."""
+    stream = W.serving_stream(seed=0, count=count, rate=rate)
     descs = [P.desc_from_problem(p) for _, p in stream]
     # warm-up: one small 2D and one small 3D solve
     for p in (W.fourier2d(np.random.default_rng(9), 129, 32, 2), W.sin3d(0, n=33, n_coarse=17, n_targets=2)):
         with P.Plan(p, stream=0) as pl:
             pl.solve()
-    srv = P.hjbp_server_create(budget_bytes=int(args.budget_gb * (1 << 30)), workers=args.workers)
+    srv = P.hjbp_server_create(budget_bytes=int(budget_gb * (1 << 30)), workers=workers)
     lat, pending, done = [], {}, 0
     t0 = time.perf_counter()
     i = 0
@@ -520,12 +611,66 @@ def run_serving(args):
     wall = time.perf_counter() - t0
     P.hjbp_server_destroy(srv)
     lat = np.array(lat)
-    out = {"metric": "p50/p99 latency and solves/s, served", "workload": f"serving_poisson{args.rate:g}_x{len(stream)}",
-           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-           "mean_ms": 1e3 * float(lat.mean()), "value": len(stream) / wall, "unit": "solves/s",
-           "offered_rate": args.rate, "arrival_span_s": stream[-1][0], "wall_s": wall, "workers": args.workers,
-           "budget_gb": args.budget_gb, "clocks": clk.summary(0), "data": "synthetic"}
-    print(json.dumps(out))
+    return {"metric": "p50/p99 latency and solves/s, served", "workload": f"serving_poisson{rate:g}_x{len(stream)}",
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_ms": 1e3 * float(lat.mean()), "value": len(stream) / wall, "unit": "solves/s",
+            "offered_rate": rate, "arrival_span_s": stream[-1][0], "wall_s": wall, "workers": workers,
+            "budget_gb": budget_gb, "clocks": clk.summary(0), "data": "synthetic"}
+
+
+def run_serving(args):
+    import torch
+
+    from paper_1109_3577_gb300 import build as b
+
+    b.build()
+    import paper_1109_3577_gb300 as P
+
+    torch.cuda.set_device(0)
+    print(json.dumps(served_measure(P, args.count or 2000, args.rate, args.workers, args.budget_gb)))
+
+
+def cfg3_measure(P, flush, stream, steps: int = 2):
+    """The 3D patchy workload (257^3, coarse 33^3, 98 Fibonacci controls,
+    8 balls r = 0.05, tol 1e-6) and the plain 3D solve of the same input:
+    CUDA-event ms per solve (L2 flushed before each), the value-sweep
+    roofline, and the full-size fixed-point residual at sampled nodes."""
+    import torch
+
+    p = W.sin3d(0, n=257, n_coarse=33, n_c=98, n_targets=8, radius=0.05, tol=1e-6)
+    st = torch.cuda.current_stream()
+
+    def timed(q, n):
+        ms, stats = [], None
+        with P.Plan(q, precision=P.HJBP_FP32_POLISH64, stream=stream, flags=P.HJBP_FLAG_TIME_SWEEPS) as pl:
+            pl.solve()
+            for _ in range(n):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                assert pl.solve() == 0
+                e1.record(st)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            stats = pl.stats()
+            u = pl.values()
+        return statistics.mean(ms), stats, u
+
+    ms, s3, u = timed(p, steps)
+    gms, gs, _ = timed(p.with_(n_coarse=None), 1)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    roof = roofline_value(s3, p, sms * FP32_LANES_PER_SM * sm_max * 1e6, sms, sm_max)
+    return {"workload": "patchy3d_sin_n257_c33_nc98_R8", "ms_per_solve": ms, "solves_per_s": 1e3 / ms,
+            "node_control_updates_per_s": s3["node_control_updates"] / (ms / 1e3),
+            "plain_sl_ms": gms, "plain_sl_solves_per_s": 1e3 / gms,
+            "ms_phases": {k: round(s3[k], 3) for k in ("ms_setup", "ms_coarse", "ms_feedback", "ms_labels",
+                                                        "ms_compact", "ms_fine", "ms_reach", "ms_polish")},
+            "roofline": roof, "reachable": int(np.isfinite(u).sum()),
+            "parity": "129^3 of the same family against the oracle in tests/test_gpu_fullsize.py; 257^3 by the "
+                      "fixed-point residual there", "steps": steps}
 
 
 def main():
@@ -535,6 +680,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 3D, batched and served measurements appended to the default line")
     ap.add_argument("--workload", default="sincos2d",
                     choices=["sincos2d", "sin3d", "batched", "serving"] + sorted(PAPER_FAMILIES) + sorted(PAPER_FAMILIES_3D),
                     help="sincos2d: 2D patchy workload (default); sin3d: 3D patchy workload; batched: 512 "

@@ -144,8 +144,10 @@ typedef struct {
                            warps per SM of the tile-queue sweep (occupancy limit), [5] the
                            fine-grid launches run the increasing or (alternately) the
                            decreasing pass of every axis: 3D default (0; 2 runs all six
-                           passes), 2D only with 1 (measured slower there), [6..7]
-                           reserved (0) */
+                           passes), 2D only with 1 (measured slower there), [6] 2D kernel
+                           variants: 0 default, 1 the per-control FP64 polish instead of the
+                           pair-form one, 2 the two-phase Gauss-Seidel passes (same results,
+                           measured slower), [7] reserved (0) */
     double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
                            minimum of Step 3.2 at node i to the controls a with
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse
@@ -240,6 +242,9 @@ typedef struct {
     double residual_patch[HJBP_MAX_TARGETS];  /* per patch: the largest FP64 sup-norm change of its
                                              tiles in the last launch each ran in (<= tol once the
                                              patch retired; patchy solves, 0 otherwise)   */
+    int64_t phi_kernel_launches;          /* launches of the 2D colour-transport kernel that had work */
+    int64_t phi_node_colour_updates;      /* node x colour updates they executed (2D) */
+    double ms_phi_kernel;                 /* their summed duration (HJBP_FLAG_TIME_SWEEPS), else 0 */
 } hjbp_stats;
 
 /* Validate the descriptor, copy its arrays, allocate device memory.

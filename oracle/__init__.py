@@ -92,11 +92,12 @@ class _Stats(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, -O2, no FMA contraction)."""
+    """Compile the oracle with gcc (plain C11, -O2, no FMA contraction;
+    OpenMP only for og_sl_apply_par, the all-core timing of the CPU baseline)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+            subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                    _SRC, "-o", tmp, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
@@ -114,6 +115,7 @@ def _load():
         lib.og_setup.argtypes = [P(_Problem), C.c_double, P(C.c_ubyte), P(C.c_int), dp]
         lib.og_interp_points.argtypes = [P(_Problem), dp, C.c_int64, dp, dp]
         lib.og_sl_apply.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, dp, C.c_int]
+        lib.og_sl_apply_par.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, dp, C.c_int]
         lib.og_iterate.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, C.c_double, C.c_int, C.c_int,
                                    P(C.c_int), dp]
         lib.og_iterate_reduced.argtypes = [P(_Problem), P(C.c_ubyte), dp, dp, C.c_double, C.c_int, C.c_int,
@@ -213,6 +215,21 @@ def sl_apply(p: Problem, U: np.ndarray, upd: Optional[np.ndarray] = None, mode: 
     _load().og_sl_apply(C.byref(d.s), _ptr(upd, C.c_ubyte), _ptr(h, C.c_double), _ptr(U, C.c_double),
                         _ptr(out, C.c_double), mode)
     return out
+
+
+def sl_apply_par(p: Problem, U: np.ndarray, upd: Optional[np.ndarray] = None, mode: int = 0, setup_out=None):
+    """sl_apply with the nodes split over the host's threads (OpenMP; the
+    paper's Method 1).  Returns (F(U), threads used)."""
+    d = _Desc(p)
+    kind, _, h = setup(p) if setup_out is None else setup_out
+    if upd is None:
+        upd = (kind == FREE)
+    upd = np.ascontiguousarray(upd, dtype=np.uint8).reshape(-1)
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
+    out = np.zeros_like(U)
+    used = _load().og_sl_apply_par(C.byref(d.s), _ptr(upd, C.c_ubyte), _ptr(h, C.c_double), _ptr(U, C.c_double),
+                                   _ptr(out, C.c_double), mode)
+    return out, int(used)
 
 
 def reachable(p: Problem, upd: np.ndarray, U: np.ndarray) -> np.ndarray:

@@ -140,6 +140,9 @@
  *       node; on the coarse grid of Step 1 the same rule holds for its nodes.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -597,6 +600,29 @@ int og_sl_apply(const og_problem *p, const unsigned char *upd, const double *h, 
     int64_t N = og_count(p);
     for (int64_t i = 0; i < N; ++i) Uout[i] = upd[i] ? og_F_node(p, Uin, h, i, mode, NULL, NULL, NULL) : Uin[i];
     return 0;
+}
+
+/* The same application with the nodes split over the host's threads (the
+   paper's Method 1 of Sec. 3, "How to parallelize the algorithm": the nodes
+   of a sweep divided among processors).  A Jacobi application reads only
+   Uin, so the split changes no value.  Used to time the CPU baseline on all
+   host cores; returns the thread count used. */
+int og_sl_apply_par(const og_problem *p, const unsigned char *upd, const double *h, const double *Uin,
+                    double *Uout, int mode) {
+    int64_t N = og_count(p);
+    int used = 1;
+#ifdef _OPENMP
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) Uout[i] = upd[i] ? og_F_node(p, Uin, h, i, mode, NULL, NULL, NULL) : Uin[i];
+    }
+#else
+    for (int64_t i = 0; i < N; ++i) Uout[i] = upd[i] ? og_F_node(p, Uin, h, i, mode, NULL, NULL, NULL) : Uin[i];
+#endif
+    return used;
 }
 
 static double og_change(double a, double b) {

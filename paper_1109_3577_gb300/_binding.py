@@ -99,6 +99,9 @@ class Stats(C.Structure):
         ("phi_refinements", C.c_int),
         ("ms_reach", C.c_double),
         ("residual_patch", C.c_double * MAX_TARGETS),
+        ("phi_kernel_launches", C.c_int64),
+        ("phi_node_colour_updates", C.c_int64),
+        ("ms_phi_kernel", C.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -283,6 +283,7 @@ hjbp_status hjbp_solve(hjbp_plan *p) {
             else cudaFreeAsync(b.ptr, p->stream);
             p->blocks.pop_back();
         }
+        p->events_used = 0;   // the timing events of the last solve are free again
         hjbp_status s = p->desc.dim == 2 ? hjbp::solve2d(*p) : hjbp::solve3d(*p);
         // release per-solve scratch
         while (p->blocks.size() > keep) {

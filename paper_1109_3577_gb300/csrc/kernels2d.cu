@@ -332,6 +332,165 @@ __device__ __forceinline__ T sl_update_pcone(const S &sm, int c, int r, unsigned
     return b01 < b23 ? b01 : b23;
 }
 
+// Minimum of the self-solved update (R13) over the controls of quadrant q
+// (corners a10 = (sx, 0), a01 = (0, sy), a11 = (sx, sy) relative to the node),
+// in the symmetric pair form when the table has it.  Same operations as
+// sl_update_m, so the result is the same to the last bit.
+template <typename T, int NCLS>
+__device__ __forceinline__ T quad_min(const CtlTable2<T> &ct, int q, T a10, T a01, T a11, T hh) {
+    T b0 = Num<T>::big(), b1 = Num<T>::big();
+    if (NCLS > 0 || ct.d4) {
+        const T E = a10 + a01, G = fabs(a10 - a01);
+        if constexpr (NCLS > 0) {
+#pragma unroll
+            for (int k = 0; k < NCLS; ++k) {
+                const T kh = ct.cls_kap[k] * hh;
+                const T v = fma(-ct.cls_t[k], G, fma(ct.cls_s[k], E, fma(ct.cls_kw11[k], a11, kh)));
+                if (k & 1) b1 = v < b1 ? v : b1;
+                else b0 = v < b0 ? v : b0;
+            }
+        } else {
+            for (int k = 0; k < ct.ncls; ++k) {
+                const T kh = ct.cls_kap[k] * hh;
+                const T v = fma(-ct.cls_t[k], G, fma(ct.cls_s[k], E, fma(ct.cls_kw11[k], a11, kh)));
+                b0 = v < b0 ? v : b0;
+            }
+        }
+    } else {
+        int mm = ct.qbeg[q];
+        const int me = ct.qbeg[q + 1];
+        for (; mm + 1 < me; mm += 2) {
+            const T v0 = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
+            const T v1 = fma(ct.kw11[mm + 1], a11,
+                             fma(ct.kw01[mm + 1], a01, fma(ct.kw10[mm + 1], a10, ct.kap[mm + 1] * hh)));
+            b0 = v0 < b0 ? v0 : b0;
+            b1 = v1 < b1 ? v1 : b1;
+        }
+        if (mm < me) {
+            const T v = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
+            b0 = v < b0 ? v : b0;
+        }
+    }
+    return b0 < b1 ? b0 : b1;
+}
+
+// Neighbour (c + dx, r + dy) of a node through its usability mask m: the
+// value v if usable, else +inf (state constraint) or the Dirichlet data.
+template <typename T, bool kDir, class S>
+__device__ __forceinline__ T masked(const S &sm, unsigned m, T v, int c, int r, int dx, int dy) {
+    const unsigned bit = 3u * (unsigned)(dy + 1) + (unsigned)(dx + 1);
+    if constexpr (kDir) return ((m >> bit) & 1u) ? v : sm.d[r + dy][c + dx];
+    else return ((m >> bit) & 1u) ? v : Num<T>::big();
+}
+
+// One Gauss-Seidel pass of a tile in direction DIR (0/1: columns left to
+// right / right to left, lane = row; 2/3: rows bottom to top / top to bottom,
+// lane = column), split in two phases with the same result as the step loop
+// of k_value2d:
+//  A. A quadrant whose corners lie on the node's own line or ahead of it
+//     reads only values from before the pass, so for every step of the pass
+//     its minimum (and that of the axis controls ahead and across) is formed
+//     first, all steps independent of each other, into part[step][lane].
+//  B. The dependent chain: per step only the two quadrants (and the axis
+//     control) that read the line updated by the step before.  That line
+//     comes from the lanes' registers by warp shuffles, the node's own line
+//     from the pre-pass values the same way; the halo (never written during a
+//     launch) from shared memory.
+template <typename T, int NCLS, bool kDir, int DIR, class S, class P>
+__device__ __forceinline__ void sweep_split(S &sm, P &part, const CtlTable2<T> &ct, int clamp, int lane) {
+    constexpr bool kCols = DIR < 2;
+    constexpr int sd = (DIR & 1) ? -1 : 1;
+    const int a = 1 + lane;
+#pragma unroll 2
+    for (int st = 0; st < kTile; ++st) {
+        const int pp = sd > 0 ? 1 + st : kTile - st;
+        const int c = kCols ? pp : a, r = kCols ? a : pp;
+        const unsigned m = sm.mk[r - 1][c - 1];
+        T f = Num<T>::big();
+        if (m & 0x8000u) {
+            const T hh = sm.h[r - 1][c - 1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
+                if ((kCols ? sx : sy) != sd) continue;   // reads the line behind: phase B
+                const T a10 = masked<T, kDir>(sm, m, sm.u[r][c + sx], c, r, sx, 0);
+                const T a01 = masked<T, kDir>(sm, m, sm.u[r + sy][c], c, r, 0, sy);
+                const T a11 = masked<T, kDir>(sm, m, sm.u[r + sy][c + sx], c, r, sx, sy);
+                const T v = quad_min<T, NCLS>(ct, q, a10, a01, a11, hh);
+                f = v < f ? v : f;
+            }
+            if (ct.axis) {
+                T ax;
+                if constexpr (kCols)
+                    ax = fmin(masked<T, kDir>(sm, m, sm.u[r][c + sd], c, r, sd, 0),
+                              fmin(masked<T, kDir>(sm, m, sm.u[r - 1][c], c, r, 0, -1),
+                                   masked<T, kDir>(sm, m, sm.u[r + 1][c], c, r, 0, 1)));
+                else
+                    ax = fmin(masked<T, kDir>(sm, m, sm.u[r + sd][c], c, r, 0, sd),
+                              fmin(masked<T, kDir>(sm, m, sm.u[r][c - 1], c, r, -1, 0),
+                                   masked<T, kDir>(sm, m, sm.u[r][c + 1], c, r, 1, 0)));
+                const T av = ax + hh;
+                f = av < f ? av : f;
+            }
+        }
+        part[st][lane] = f;
+    }
+    __syncwarp();
+    constexpr unsigned kFull = 0xffffffffu;
+    const int p0 = sd > 0 ? 0 : kTile + 1;
+    T prev = kCols ? sm.u[a][p0] : sm.u[p0][a];
+    for (int st = 0; st < kTile; ++st) {
+        const int pp = sd > 0 ? 1 + st : kTile - st, pb = pp - sd;
+        const int c = kCols ? pp : a, r = kCols ? a : pp;
+        const unsigned m = sm.mk[r - 1][c - 1];
+        const T old = sm.u[r][c];
+        // halo values at the ends of the lines (across index 0 and kTile + 1)
+        const T hbm = kCols ? sm.u[0][pb] : sm.u[pb][0], hbp = kCols ? sm.u[kTile + 1][pb] : sm.u[pb][kTile + 1];
+        const T hom = kCols ? sm.u[0][c] : sm.u[r][0], hop = kCols ? sm.u[kTile + 1][c] : sm.u[r][kTile + 1];
+        T bm = __shfl_up_sync(kFull, prev, 1), bp = __shfl_down_sync(kFull, prev, 1);
+        T om = __shfl_up_sync(kFull, old, 1), op = __shfl_down_sync(kFull, old, 1);
+        if (lane == 0) {
+            bm = hbm;
+            om = hom;
+        }
+        if (lane == kTile - 1) {
+            bp = hbp;
+            op = hop;
+        }
+        T nw = old;
+        if (m & 0x8000u) {
+            const T hh = sm.h[r - 1][c - 1];
+            T b = part[st][lane];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
+                if ((kCols ? sx : sy) == sd) continue;   // done in phase A
+                T a10, a01, a11;
+                if constexpr (kCols) {
+                    a10 = masked<T, kDir>(sm, m, prev, c, r, sx, 0);
+                    a01 = masked<T, kDir>(sm, m, sy < 0 ? om : op, c, r, 0, sy);
+                    a11 = masked<T, kDir>(sm, m, sy < 0 ? bm : bp, c, r, sx, sy);
+                } else {
+                    a10 = masked<T, kDir>(sm, m, sx < 0 ? om : op, c, r, sx, 0);
+                    a01 = masked<T, kDir>(sm, m, prev, c, r, 0, sy);
+                    a11 = masked<T, kDir>(sm, m, sx < 0 ? bm : bp, c, r, sx, sy);
+                }
+                const T v = quad_min<T, NCLS>(ct, q, a10, a01, a11, hh);
+                b = v < b ? v : b;
+            }
+            if (ct.axis) {
+                const T av = (kCols ? masked<T, kDir>(sm, m, prev, c, r, -sd, 0)
+                                    : masked<T, kDir>(sm, m, prev, c, r, 0, -sd)) + hh;
+                b = av < b ? av : b;
+            }
+            if (b < Num<T>::thresh()) nw = clamp ? (b < old ? b : old) : b;
+            sm.u[r][c] = nw;
+        }
+        prev = nw;
+    }
+    __syncwarp();
+}
+
 // Parities of the 3x3 tile neighbourhood of tile (tx, ty) as a 9-bit mask
 // (bit 3 (dy+1) + (dx+1)); tiles off the grid read 0 like the ghost ring.
 __device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched &s, int tx, int ty) {
@@ -360,7 +519,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                                                 TileSched s, int par, int rounds, unsigned long long *updates,
                                                 const CtlTable2<T> ct, int clamp, const T *__restrict__ dval,
                                                 const uint8_t *__restrict__ astar = nullptr,
-                                                const Cone2 *__restrict__ cone = nullptr) {
+                                                const Cone2 *__restrict__ cone = nullptr, int split = 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -368,6 +527,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     __shared__ TileSmemV<T, kDir> sm;
     __shared__ T u0[kTile][kTile + 1];
+    __shared__ T part[kCone ? 1 : kTile][kCone ? 1 : kTile + 1];   // phase-A minima of sweep_split
     __shared__ uint8_t sa[kCone ? kTile : 1][kCone ? kTile + 1 : 1];
     __shared__ unsigned long long cmask[kCone ? 65 : 1];
     __shared__ Ctl4<T> ctab[kCone && NCLS == 0 ? 64 : 1];
@@ -453,7 +613,17 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     __syncwarp();
     // AO2: the tile's sweep directions; or alternating halves (TileSched.alt)
     const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0xAu : 0x5u) : 0xFu);
-    for (int rd = 0; rd < rounds; ++rd) {
+    if constexpr (!kCone) {
+        if (split) {
+            for (int rd = 0; rd < rounds; ++rd) {
+                if (tdirs & 1u) sweep_split<T, NCLS, kDir, 0>(sm, part, ct, clamp, lane);
+                if (tdirs & 2u) sweep_split<T, NCLS, kDir, 1>(sm, part, ct, clamp, lane);
+                if (tdirs & 4u) sweep_split<T, NCLS, kDir, 2>(sm, part, ct, clamp, lane);
+                if (tdirs & 8u) sweep_split<T, NCLS, kDir, 3>(sm, part, ct, clamp, lane);
+            }
+        }
+    }
+    for (int rd = 0; rd < ((kCone || !split) ? rounds : 0); ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
             for (int st = 0; st < kTile; ++st) {
@@ -1503,7 +1673,106 @@ template <int RG, bool kSource> struct PhiSmem {
     // the control table, so that per-node lookups hit shared memory
     float kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls], kap[kMaxControls];
     int8_t sx[kMaxControls], sy[kMaxControls];
+    float part[RG][kTile][kTile + 1];   // phase-A values of phi_sweep_split
 };
+
+// One Gauss-Seidel pass of the colour transport in direction DIR (as in
+// sweep_split: 0/1 columns, 2/3 rows), in two phases.  A node whose feedback
+// foot lies ahead of its line (or on it) reads only values from before the
+// pass: phase A forms its new value for every step at once.  A node whose foot
+// lies behind needs the line updated one step earlier: phase A forms the
+// product of its own-line corner, phase B adds the two corners behind, taken
+// from the lanes' registers by one indexed shuffle per colour.  Every node
+// sums its corners own line first, then the corner straight behind or ahead,
+// then the diagonal one.
+template <int RG, bool kSource, int DIR, class S>
+__device__ __forceinline__ void phi_sweep_split(S &sm, unsigned alive, int lane) {
+    constexpr bool kCols = DIR < 2;
+    constexpr int sd = (DIR & 1) ? -1 : 1;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int a = 1 + lane;
+#pragma unroll 2
+    for (int st = 0; st < kTile; ++st) {
+        const int pp = sd > 0 ? 1 + st : kTile - st;
+        const int c = kCols ? pp : a, r = kCols ? a : pp;
+        const int8_t cd = sm.c[r][c];
+        const uint8_t ai = sm.a[r - 1][c - 1];
+        if (cd >= 0 && cd < kTargetBase && ai != kNoControl) {
+            const int sx = sm.sx[ai], sy = sm.sy[ai];
+            const float w10 = sm.kw10[ai], w01 = sm.kw01[ai], w11 = sm.kw11[ai];
+            const bool ahead = (kCols ? sx : sy) == sd;
+#pragma unroll
+            for (int q = 0; q < RG; ++q) {
+                if (!((alive >> q) & 1u)) continue;
+                // own-line corner first
+                float v = kCols ? w01 * sm.u[q][r + sy][c] : w10 * sm.u[q][r][c + sx];
+                if (ahead) {
+                    v = kCols ? fmaf(w10, sm.u[q][r][c + sx], v) : fmaf(w01, sm.u[q][r + sy][c], v);
+                    v = fmaf(w11, sm.u[q][r + sy][c + sx], v);
+                    if constexpr (kSource) {
+                        v = fmaf(sm.kap[ai], sm.src[q][r - 1][c - 1], v);
+                    } else {
+                        const float o = sm.u[q][r][c];
+                        v = v > o ? v : o;
+                    }
+                }
+                sm.part[q][st][lane] = v;
+            }
+        }
+    }
+    __syncwarp();
+    const int p0 = sd > 0 ? 0 : kTile + 1;
+    float prev[RG];
+#pragma unroll
+    for (int q = 0; q < RG; ++q) prev[q] = kCols ? sm.u[q][a][p0] : sm.u[q][p0][a];
+    for (int st = 0; st < kTile; ++st) {
+        const int pp = sd > 0 ? 1 + st : kTile - st, pb = pp - sd;
+        const int c = kCols ? pp : a, r = kCols ? a : pp;
+        const int8_t cd = sm.c[r][c];
+        const uint8_t ai = sm.a[r - 1][c - 1];
+        const bool active = cd >= 0 && cd < kTargetBase && ai != kNoControl;
+        int so = 0;   // across offset of the diagonal corner behind
+        float w_st = 0.f, w_dg = 0.f, kp = 0.f;
+        bool ahead = true;
+        if (active) {
+            const int sx = sm.sx[ai], sy = sm.sy[ai];
+            ahead = (kCols ? sx : sy) == sd;
+            so = kCols ? sy : sx;
+            w_st = kCols ? sm.kw10[ai] : sm.kw01[ai];
+            w_dg = sm.kw11[ai];
+            kp = sm.kap[ai];
+        }
+        // the lane across so holds the diagonal corner behind; past the line's
+        // ends the halo (never written during a launch)
+        const int src_lane = lane + so;
+        const bool edge = src_lane < 0 || src_lane >= kTile;
+        const int hx = kCols ? pb : (so < 0 ? 0 : kTile + 1), hy = kCols ? (so < 0 ? 0 : kTile + 1) : pb;
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            if (!((alive >> q) & 1u)) continue;
+            const float dg_sh = __shfl_sync(kFull, prev[q], src_lane & 31);
+            const float old = sm.u[q][r][c];
+            float nw = old;
+            if (active) {
+                if (ahead) {
+                    nw = sm.part[q][st][lane];
+                } else {
+                    const float dg = edge ? sm.u[q][hy][hx] : dg_sh;
+                    float v = fmaf(w_st, prev[q], sm.part[q][st][lane]);
+                    v = fmaf(w_dg, dg, v);
+                    if constexpr (kSource) {
+                        nw = fmaf(kp, sm.src[q][r - 1][c - 1], v);
+                    } else {
+                        nw = v > old ? v : old;
+                    }
+                }
+                sm.u[q][r][c] = nw;
+            }
+            prev[q] = nw;
+        }
+    }
+    __syncwarp();
+}
 
 // One FP32 launch over the active tiles for RG colours, each node solved for
 // itself (R13) with its fixed coarse feedback a*_i:
@@ -1515,7 +1784,8 @@ template <int RG, bool kSource>
 __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
                                               const uint8_t *__restrict__ astar, float *__restrict__ b0,
                                               float *__restrict__ b1, const float *__restrict__ src, TileSched s,
-                                              int par, int rounds, const PhiCtl *__restrict__ pc) {
+                                              int par, int rounds, const PhiCtl *__restrict__ pc, int split = 0,
+                                              unsigned long long *updates = nullptr) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -1590,7 +1860,28 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     }
     alive = __reduce_or_sync(0xffffffffu, alive);
     __syncwarp();
-    if (alive) {
+    if (updates && alive) {
+        // node-colour updates of this launch: transported nodes x live colours x passes
+        int na = 0;
+        for (int r = 1; r <= kTile; ++r) {
+            const int8_t cd = sm.c[r][1 + lane];
+            na += (cd >= 0 && cd < kTargetBase && sm.a[r - 1][lane] != kNoControl) ? 1 : 0;
+        }
+        na = __reduce_add_sync(0xffffffffu, na);
+        const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
+        if (lane == 0 && na)
+            atomicAdd(updates, (unsigned long long)na * (unsigned long long)__popc(alive) *
+                                   (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
+    }
+    if (alive && split) {
+        const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
+        for (int rd = 0; rd < rounds; ++rd) {
+            if (tdirs & 1u) phi_sweep_split<RG, kSource, 0>(sm, alive, lane);
+            if (tdirs & 2u) phi_sweep_split<RG, kSource, 1>(sm, alive, lane);
+            if (tdirs & 4u) phi_sweep_split<RG, kSource, 2>(sm, alive, lane);
+            if (tdirs & 8u) phi_sweep_split<RG, kSource, 3>(sm, alive, lane);
+        }
+    } else if (alive) {
         const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
         for (int rd = 0; rd < rounds; ++rd) {
             for (int dir = 0; dir < 4; ++dir) {
@@ -1906,6 +2197,120 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
             }
         }
         uout[i] = v;
+    }
+    mc = warp_max(mc);
+    if ((threadIdx.x & 31) == 0 && mc > 0.0) atomic_max_pos(maxchg, mc);
+}
+
+// FP64 polish in the symmetric pair form (control sets with the eight
+// symmetries of the square, NCLS classes).  Same FP32-filter argument as
+// k_polish2d: pass 1 takes the FP32 minimum over the pairs (base - t |D|,
+// the smaller of the two mirrored controls), pass 2 evaluates in FP64 only
+// the pairs whose FP32 value lies within lim = b32 + 2^-18 (h hfmax + max|u|)
+// of it; the FP32 error of a pair value (about six roundings of terms
+// bounded by kap h and max|u|, kap <= sqrt 2) stays below half that margin,
+// so the pair holding the FP64 minimum is always evaluated.  The neighbours
+// come from an FP32 mirror of the values (written by the same pass), so the
+// filter converts nothing on the FP64 pipe; the FP64 corners are read only
+// for candidate pairs.
+template <int NCLS>
+__global__ void k_polish2d_pf(Grid2 g, const int8_t *__restrict__ code, const double *__restrict__ h,
+                              const double *__restrict__ uin, const float *__restrict__ uin32,
+                              double *__restrict__ uout, float *__restrict__ uout32, double *maxchg,
+                              const CtlTable2<float> c32, const CtlTable2<double> c64,
+                              const double *__restrict__ dval, const float *__restrict__ dval32) {
+    const int64_t N = (int64_t)g.n0 * g.n1;
+    double mc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int8_t cd = code[i];
+        double v = uin[i];
+        if (cd >= 0 && cd < kTargetBase && v < Num<double>::thresh()) {
+            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
+            float nf[3][3];
+            unsigned same = 0;
+            float amax = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int64_t j = (int64_t)(iy - 1 + dy) * g.n0 + (ix - 1 + dx);
+                    const int8_t q = code[j];
+                    const bool s = q == cd || q == tg || q == pr;
+                    same |= (unsigned)s << (3 * dy + dx);
+                    // outside the patch: +inf, or the Dirichlet data (Eq. dbc)
+                    const float w = s ? uin32[j] : (dval32 ? dval32[j] : Num<float>::big());
+                    const bool fin = w < Num<float>::thresh();
+                    nf[dy][dx] = fin ? w : Num<float>::big();
+                    if (fin) amax = fmaxf(amax, fabsf(w));
+                }
+            const double hh = h[i];
+            const float hf = (float)hh;
+            float E[4], G[4], A[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+                E[q] = nf[1][sx] + nf[sy][1];
+                G[q] = fabsf(nf[1][sx] - nf[sy][1]);
+                A[q] = nf[sy][sx];
+            }
+            // pass 1: FP32 minimum over the pairs (and the axis controls)
+            float b32 = Num<float>::big();
+#pragma unroll
+            for (int k = 0; k < NCLS; ++k) {
+                const float kh = c32.cls_kap[k] * hf;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float w = fmaf(-c32.cls_t[k], G[q], fmaf(c32.cls_s[k], E[q], fmaf(c32.cls_kw11[k], A[q], kh)));
+                    b32 = w < b32 ? w : b32;
+                }
+            }
+            const float ax32 = fminf(fminf(nf[1][0], nf[1][2]), fminf(nf[0][1], nf[2][1])) + hf;
+            if (c32.axis) b32 = ax32 < b32 ? ax32 : b32;
+            if (b32 < Num<float>::thresh()) {
+                const float lim = b32 + ldexpf(hf * c32.hfmax + amax, -18);
+                auto d64 = [&](int dx, int dy) -> double {
+                    const int64_t j = (int64_t)(iy - 1 + dy) * g.n0 + (ix - 1 + dx);
+                    const double w = ((same >> (3 * dy + dx)) & 1u) ? uin[j] : (dval ? dval[j] : Num<double>::big());
+                    return w < Num<double>::thresh() ? w : Num<double>::big();
+                };
+                // pass 2: FP64 over the candidate pairs
+                double best = Num<double>::big();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
+                    bool loaded = false;
+                    double e64 = 0.0, g64 = 0.0, a64 = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NCLS; ++k) {
+                        const float w = fmaf(-c32.cls_t[k], G[q],
+                                             fmaf(c32.cls_s[k], E[q], fmaf(c32.cls_kw11[k], A[q], c32.cls_kap[k] * hf)));
+                        if (w <= lim) {
+                            if (!loaded) {
+                                const double d10 = d64(sx, 1), d01 = d64(1, sy);
+                                e64 = d10 + d01;
+                                g64 = fabs(d10 - d01);
+                                a64 = d64(sx, sy);
+                                loaded = true;
+                            }
+                            const double x =
+                                fma(-c64.cls_t[k], g64, fma(c64.cls_s[k], e64, fma(c64.cls_kw11[k], a64, c64.cls_kap[k] * hh)));
+                            best = x < best ? x : best;
+                        }
+                    }
+                }
+                if (c32.axis && ax32 <= lim) {
+                    const double ax = fmin(fmin(d64(0, 1), d64(2, 1)), fmin(d64(1, 0), d64(1, 2))) + hh;
+                    best = ax < best ? ax : best;
+                }
+                if (best < Num<double>::thresh()) {
+                    mc = fmax(mc, fabs(best - v));
+                    v = best;
+                }
+            }
+        }
+        uout[i] = v;
+        uout32[i] = v < Num<double>::thresh() ? (float)v : Num<float>::big();
     }
     mc = warp_max(mc);
     if ((threadIdx.x & 31) == 0 && mc > 0.0) atomic_max_pos(maxchg, mc);
@@ -2388,6 +2793,42 @@ struct Ev {
     ~Ev() { cudaEventDestroy(e); }
 };
 
+// CUDA event pairs around kernel launches on one stream; keep(n) retains the
+// first n pairs of the last batch (launches after convergence did no work).
+struct LaunchTimer {
+    hjbp_plan &p;
+    bool on;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> cur, kept;
+    int64_t launches = 0;
+    LaunchTimer(hjbp_plan &plan, bool enabled) : p(plan), on(enabled) {}
+    void begin() {
+        if (!on) return;
+        cudaEvent_t a = p.pooled_event(), b = p.pooled_event();
+        if (!a || !b) throw HjbpError{HJBP_ECUDA, "cudaEventCreate failed"};
+        check_cuda(cudaEventRecord(a, p.stream), "event");
+        cur.emplace_back(a, b);
+    }
+    void end() {
+        if (on) check_cuda(cudaEventRecord(cur.back().second, p.stream), "event");
+    }
+    void keep(int n) {
+        for (size_t l = 0; l < cur.size() && (int)l < n; ++l) kept.push_back(cur[l]);
+        cur.clear();
+        launches += n;
+    }
+    double total_ms() {
+        double ms = 0.0;
+        if (!on) return 0.0;
+        if (!kept.empty()) check_cuda(cudaEventSynchronize(kept.back().second), "event sync");
+        for (auto &e : kept) {
+            float m = 0.f;
+            cudaEventElapsedTime(&m, e.first, e.second);
+            ms += m;
+        }
+        return ms;
+    }
+};
+
 float ms_between(const Ev &a, const Ev &b) {
     float ms = 0.f;
     cudaEventSynchronize(b.e);
@@ -2445,14 +2886,11 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
     const int warps = p.desc.tune[3] > 0 ? p.desc.tune[3] : 1;
     const bool pairs = cone && ct.d4 && ct.ncls == 8 && p.cone_pairs;   // AO3 in the pair form
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+    // tune[6] = 2: the two-phase passes of sweep_split (same result, measured slower)
+    const int split = p.desc.tune[6] == 2 ? 1 : 0;
+    LaunchTimer timer(p, timed);
     RunResult rr = run_tiles(p, g, s, tol, cap, [&](int par, int) {
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (timed) {
-            check_cuda(cudaEventCreate(&a), "event");
-            check_cuda(cudaEventCreate(&b), "event");
-            check_cuda(cudaEventRecord(a, p.stream), "event");
-        }
+        timer.begin();
         const bool plain = clamp && !dval && !cone;  // the multi-warp variant has none of the options
         if (cone && pairs && dval)
             k_value2d<T, 8, true, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
@@ -2472,42 +2910,27 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
             k_value2d_w<T, true, 2><<<s.ntiles, 64, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
         else if (dval && ct.d4 && ct.ncls == 8)
             k_value2d<T, 8, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                 clamp, dval);
+                                                                 clamp, dval, nullptr, nullptr, split);
         else if (dval)
             k_value2d<T, 0, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                 clamp, dval);
+                                                                 clamp, dval, nullptr, nullptr, split);
         else if (ct.d4 && ct.ncls == 8)
             k_value2d<T, 8, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                  clamp, nullptr);
+                                                                  clamp, nullptr, nullptr, nullptr, split);
         else if (ct.d4 && ct.ncls == 4 && std::is_same<T, float>::value)
             k_value2d<T, 4, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                  clamp, nullptr);
+                                                                  clamp, nullptr, nullptr, nullptr, split);
         else
             k_value2d<T, 0, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                  clamp, nullptr);
+                                                                  clamp, nullptr, nullptr, nullptr, split);
         ++p.stats.kernel_launches;
         if (fine) ++p.stats.sweep_kernel_launches;
-        if (timed) {
-            check_cuda(cudaEventRecord(b, p.stream), "event");
-            evs.emplace_back(a, b);
-        }
+        timer.end();
     });
     if (fine) p.stats.sweep_tile_visits += rr.tile_visits;
-    if (timed) {
-        check_cuda(cudaStreamSynchronize(p.stream), "timing sync");
-        double ms = 0.0;
-        // launches after convergence found no active tile and did no work
-        for (size_t l = 0; l < evs.size(); ++l) {
-            float m = 0.f;
-            if ((int)l < rr.launches) {
-                cudaEventElapsedTime(&m, evs[l].first, evs[l].second);
-                ms += m;
-            }
-            cudaEventDestroy(evs[l].first);
-            cudaEventDestroy(evs[l].second);
-        }
-        p.stats.ms_sweep_kernel += ms;
-    }
+    // launches after convergence found no active tile and did no work
+    timer.keep(rr.launches);
+    if (timed) p.stats.ms_sweep_kernel += timer.total_ms();
     k_gather2d<T><<<grid_for(N), 256, 0, p.stream>>>(g, s.d.latest, b0, b1, out_t, out64);
     ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "gather");
@@ -2748,6 +3171,12 @@ hjbp_status solve2d(hjbp_plan &p) {
             double *phig = alloc_n<double>(p, N * RG);
             float *rmax = alloc_n<float>(p, 1);
             const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
+            // tune[6] = 2: the two-phase passes of phi_sweep_split (measured slower)
+            const int psplit = d.tune[6] == 2 ? 1 : 0;
+            // per-launch CUDA events (HJBP_FLAG_TIME_SWEEPS) and the node-colour update count
+            LaunchTimer ptimer(p, (d.flags & HJBP_FLAG_TIME_SWEEPS) != 0);
+            unsigned long long *pupd = alloc_n<unsigned long long>(p, 1);
+            check_cuda(cudaMemsetAsync(pupd, 0, sizeof(unsigned long long), st), "memset");
             for (int j0 = 0; j0 < R; j0 += RG) {
                 const int rg = std::min(RG, R - j0);
                 // colours past R in the last group see no target and stay 0
@@ -2762,10 +3191,13 @@ hjbp_status solve2d(hjbp_plan &p) {
                     k_phi_init2d<G><<<grid_for(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++p.stats.kernel_launches;
                     RunResult rp = run_tiles(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par, int) {
+                        ptimer.begin();
                         k_phi2d<G, false><<<sched.ntiles, 32, sizeof(PhiSmem<G, false>), st>>>(
-                            g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc);
+                            g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc, psplit, pupd);
+                        ptimer.end();
                         ++p.stats.kernel_launches;
                     });
+                    ptimer.keep(rp.launches);
                     S.sweeps_phi += rp.launches;
                     if (!rp.converged) status = HJBP_ENOCONV;
                     k_phi_collect2d<G><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, f0, f1, phig, 0);
@@ -2784,10 +3216,13 @@ hjbp_status solve2d(hjbp_plan &p) {
                         ++p.stats.kernel_launches;
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         RunResult rc = run_tiles(p, g, sched, told, cap, [&](int par, int) {
+                            ptimer.begin();
                             k_phi2d<G, true><<<sched.ntiles, 32, sizeof(PhiSmem<G, true>), st>>>(
-                                g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dpc);
+                                g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dpc, psplit, pupd);
+                            ptimer.end();
                             ++p.stats.kernel_launches;
                         });
+                        ptimer.keep(rc.launches);
                         S.sweeps_phi += rc.launches;
                         k_phi_collect2d<G><<<grid_for(N), 256, 0, st>>>(g, sched.d.latest, f0, f1, phig, 1);
                         ++p.stats.kernel_launches;
@@ -2799,6 +3234,14 @@ hjbp_status solve2d(hjbp_plan &p) {
                 else if (rgl == 4) launch_group(std::integral_constant<int, 4>());
                 else if (rgl == 2) launch_group(std::integral_constant<int, 2>());
                 else launch_group(std::integral_constant<int, 1>());
+            }
+            {
+                unsigned long long hp = 0;
+                check_cuda(cudaMemcpyAsync(&hp, pupd, sizeof(hp), cudaMemcpyDeviceToHost, st), "phi updates");
+                check_cuda(cudaStreamSynchronize(st), "phi updates");
+                S.phi_node_colour_updates = (int64_t)hp;
+                S.phi_kernel_launches = ptimer.launches;
+                S.ms_phi_kernel = ptimer.total_ms();
             }
             k_label2d<<<grid_for(N), 256, 0, st>>>(N, code0, p.astar, p.phi, R, p.label_out);
             ++p.stats.kernel_launches;
@@ -2883,6 +3326,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     S.sweeps_reach += reach2d(p, g, code, rch, sched, kReachCap, N, d64, cone);
     Ev fr(st);
     RunResult rv;
+    float *d32 = nullptr;   // Dirichlet data in FP32 (FP32 sweeps and the polish filter)
     // per-patch residual at retirement: the tiles' last changes (FP64)
     double *last_chg = nullptr;
     if (p.patchy && sched.ntiles && !queue_ok) {
@@ -2892,7 +3336,6 @@ hjbp_status solve2d(hjbp_plan &p) {
     }
     if (fp32) {
         float *b0 = alloc_n<float>(p, N), *b1 = alloc_n<float>(p, N);
-        float *d32 = nullptr;
         if (dirichlet) {
             d32 = alloc_n<float>(p, N);
             k_dirichlet_data<float><<<grid_for(N), 256, 0, st>>>(N, dlit, d32);
@@ -2937,15 +3380,30 @@ hjbp_status solve2d(hjbp_plan &p) {
         ++p.stats.kernel_launches;
         const CtlTable2<double> ct = make_table<double>(p);
         CtlTable2<float> ctf = make_table<float>(p);
-        ctf.d4 = 0;
+        // the pair form with FP32 mirrors for the 8-class symmetric sets (not
+        // with AO3 cones, whose masks address single controls); tune[6] = 1 keeps
+        // the per-control kernel
+        const bool pf = !cone && ctf.d4 && ctf.ncls == 8 && ct.d4 && ct.ncls == 8 && d.tune[6] != 1;
+        float *pa32 = nullptr, *pb32 = nullptr;
+        if (pf) {
+            pa32 = alloc_n<float>(p, N);
+            pb32 = alloc_n<float>(p, N);
+            check_cuda(cudaMemcpyAsync(pa32, p.u32, sizeof(float) * N, cudaMemcpyDeviceToDevice, st), "mirror");
+        }
+        ctf.d4 = pf ? 1 : 0;
         double last = 0.0;
         int it = 0;
         for (; it < 8; ++it) {
             check_cuda(cudaMemsetAsync(mc, 0, sizeof(double), st), "memset");
-            k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ctf, ct, d64, p.astar, cone);
+            if (pf)
+                k_polish2d_pf<8><<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pa32, pb, pb32, mc, ctf, ct, d64,
+                                                                   d32);
+            else
+                k_polish2d<<<grid_for(N, 128), 128, 0, st>>>(g, code, h64, pa, pb, mc, ctf, ct, d64, p.astar, cone);
             ++p.stats.kernel_launches;
             check_cuda(cudaGetLastError(), "polish");
             std::swap(pa, pb);
+            std::swap(pa32, pb32);
             double hm = 0.0;
             check_cuda(cudaMemcpyAsync(&hm, mc, sizeof(double), cudaMemcpyDeviceToHost, st), "polish res");
             check_cuda(cudaStreamSynchronize(st), "polish sync");

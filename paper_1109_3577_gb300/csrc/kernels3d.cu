@@ -1964,8 +1964,10 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
     Run3 rr = run_tiles3(p, g, s, tol, cap, [&](int par) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (timed) {
-            check_cuda(cudaEventCreate(&a), "event");
-            check_cuda(cudaEventCreate(&b), "event");
+            // events from the plan's pool (created once, reused by every solve)
+            a = p.pooled_event();
+            b = p.pooled_event();
+            if (!a || !b) throw HjbpError{HJBP_ECUDA, "cudaEventCreate failed"};
             check_cuda(cudaEventRecord(a, p.stream), "event");
         }
         if (cone && dval)
@@ -2003,8 +2005,6 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
                 cudaEventElapsedTime(&m, evs[l].first, evs[l].second);
                 ms += m;
             }
-            cudaEventDestroy(evs[l].first);
-            cudaEventDestroy(evs[l].second);
         }
         p.stats.ms_sweep_kernel += ms;
     }

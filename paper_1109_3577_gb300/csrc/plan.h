@@ -51,8 +51,22 @@ struct hjbp_plan {
     std::vector<double> init;       // caller's start values (hjbp_set_initial), empty: none
     bool cone_pairs = false;        // AO3 cones available in the symmetric pair form
     int *pinned_count = nullptr;    // pinned host word for the sweep loops' readbacks (lazy)
+    // CUDA events for per-launch timing (HJBP_FLAG_TIME_SWEEPS), created once
+    // and reused by every solve: creating and destroying events per launch
+    // costs more host time than the launches
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    cudaEvent_t pooled_event() {
+        if (events_used == events.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            events.push_back(e);
+        }
+        return events[events_used++];
+    }
     ~hjbp_plan() {
         if (pinned_count) cudaFreeHost(pinned_count);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
     }
 
     // --- device arrays owned by the plan ---

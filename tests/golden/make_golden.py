@@ -7,7 +7,9 @@ compact sample of its output under tests/golden/:
                (full label map, int8), gap (a* best-vs-second gap at the
                sampled nodes), phimax (max_j phi^j at the sampled nodes),
                tie (bit-packed mask over every node: the tie nodes of the
-               label comparison, see tie_mask), meta (JSON: sizes, sweeps,
+               label comparison, see tests/_labels.py), astar_full (the
+               coarse feedback index at every node, 255 where undefined),
+               meta (JSON: sizes, sweeps,
                per-patch node counts, reachable count, max u, E1/E_inf of the
                patchy solution against the global one when computed).
 
@@ -47,10 +49,11 @@ def make(family: str, seed: int, with_global: bool, samples: int = 20000, **kw):
         "reachable": int(np.isfinite(r.u).sum()), "max_u": float(r.u[fin].max()),
         "label_counts": {int(k): int(v) for k, v in zip(*np.unique(r.labels, return_counts=True))},
     }
-    tie = tie_mask(r)
+    tie = tie_mask(r, p)
     meta["tie_nodes"] = int(tie.sum())
     out = {"idx": idx, "u": r.u[idx], "labels": r.labels, "gap": r.gap[idx],
-           "phimax": r.phi.max(axis=0)[idx], "astar": r.astar[idx], "tie": np.packbits(tie)}
+           "phimax": r.phi.max(axis=0)[idx], "astar": r.astar[idx], "tie": np.packbits(tie),
+           "astar_full": np.where(r.astar >= 0, r.astar, 255).astype(np.uint8)}
     if with_global:
         t2 = time.time()
         g = oracle.global_solve(p.with_(n_coarse=None), tol=1e-10)

@@ -57,7 +57,7 @@ def test_rule_rejects_a_flip_inside_a_patch(solved):
 def test_rule_rejects_a_flip_at_a_boundary_node_that_is_not_a_tie(solved):
     p, ref = solved
     near = boundary_adjacent(ref.labels, grid_shape(p))
-    tie = tie_mask(ref)
+    tie = tie_mask(ref, p)
     cand = np.nonzero(near & ~tie)[0]
     assert cand.size > 0
     lab = ref.labels.copy()
@@ -74,7 +74,7 @@ def test_rule_accepts_a_flip_at_a_tie_next_to_a_boundary():
         targets=np.array([[-1.0, 0.3, 0.2], [1.0, 0.3, 0.2]]))
     ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True)
     near = boundary_adjacent(ref.labels, grid_shape(p))
-    tie = tie_mask(ref)
+    tie = tie_mask(ref, p)
     cand = np.nonzero(near & tie)[0]
     assert cand.size > 0
     lab = ref.labels.copy()
@@ -90,3 +90,44 @@ def test_rule_rejects_too_many_disagreements(solved):
     lab[idx] = (lab[idx] + 1) % p.n_patches
     with pytest.raises(AssertionError, match="agreement"):
         assert_labels(lab, ref, p)
+
+
+@pytest.mark.parametrize("family", ["sincos2d", "brockett3d"])
+def test_restated_feedback_chain_reproduces_the_oracle_colours(family):
+    """The chain the tie rule walks (tests/_labels.py: feet of the oracle's
+    feedback, Q1 weights) is the one of Eq. (HJBridotta_discreta): its
+    absorption probabilities, from a direct sparse solve, are the oracle's
+    colours."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    from tests._labels import feedback_graph, reaches
+
+    p = W.sincos2d(2, n=129, n_coarse=33) if family == "sincos2d" else W.brockett3d(n=21, n_coarse=11)
+    ref = oracle.patchy_solve(p, tol=1e-12, keep_phi=True)
+    src, dst, N, w = feedback_graph(p, ref.astar)
+    kind, part, _ = oracle.setup(p)
+    for j in range(p.n_patches):
+        tgt = (kind == oracle.TARGET) & (part == j)
+        live = reaches(src, dst, N, tgt) & ~tgt
+        ids = np.nonzero(live)[0]
+        phi = np.where(tgt, 1.0, 0.0)
+        if ids.size:
+            P = sp.csr_matrix((w, (src, dst)), shape=(N, N))[ids]
+            A = sp.identity(ids.size, format="csc") - P[:, ids].tocsc()
+            b = np.asarray(P[:, np.nonzero(tgt)[0]].sum(axis=1)).ravel()
+            phi[ids] = spl.spsolve(A, b)
+        free = ref.astar >= 0
+        assert np.abs(phi[free] - ref.phi[j][free]).max() < 1e-8
+
+
+def test_hit_probability_on_a_small_chain():
+    from tests._labels import hit_probability
+
+    # 0 -> 1 (1/2), 0 -> 2 (1/2); 1 -> 3 (seed); 2 -> 2 (trap); 4 isolated
+    src = np.array([0, 0, 1, 2])
+    dst = np.array([1, 2, 3, 2])
+    w = np.array([0.5, 0.5, 1.0, 1.0])
+    seeds = np.array([False, False, False, True, False])
+    pi = hit_probability(src, dst, 5, w, seeds)
+    assert np.allclose(pi, [0.5, 1.0, 0.0, 1.0, 0.0])

@@ -561,3 +561,16 @@ def test_uncovered_nodes_join_a_neighbouring_patch():
         nb = [j for j in (i - 1, i + 1, i - n, i + n) if 0 <= j < kind.size]
         assert r.labels[i] in r.labels[nb]
     assert r.converged
+
+
+def test_parallel_application_equals_the_serial_one():
+    """The all-core application of F (nodes split over threads, Method 1 of
+    Sec. 3) used to time the CPU baseline computes the same values."""
+    p = W.sincos2d(0, n=129, n_coarse=17)
+    kind, _, _ = oracle.setup(p)
+    x = oracle.grid_coords(p)
+    U = np.where(kind == oracle.GHOST, np.inf, np.linalg.norm(x, axis=1))
+    U[kind == oracle.TARGET] = 0.0
+    par, used = oracle.sl_apply_par(p, U)
+    assert used >= 1
+    assert np.array_equal(par, oracle.sl_apply(p, U))
