@@ -138,7 +138,7 @@ typedef struct {
     int max_sweeps;
     int flags;          /* HJBP_FLAG_* bits */
     int tune[8];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
-                           launch of the value sweep (2), [1] of the colour transport (3),
+                           launch of the value sweep (2), [1] of the colour transport (2),
                            [2] passes per launch of the reachability sweep (1), [3] warps
                            per 32x32 tile of the 2D value sweep (1; 1, 2 or 4), [4] resident
                            warps per SM of the tile-queue sweep (occupancy limit), [5] the

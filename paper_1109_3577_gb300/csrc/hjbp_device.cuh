@@ -418,10 +418,34 @@ __device__ __forceinline__ double atomic_max_pos(double *addr, double v) {
 }
 
 // |v - o| of two values in FP64 for the sup-norm stopping test: 0 when both
-// are the +inf sentinel, a huge value when only one is.
+// are the +inf sentinel, a huge value when only one is.  (The tile sweeps use
+// node_change below; this form serves the queue sweep and the coarse grid.)
 template <typename T> __device__ __forceinline__ double change64(T v, T o, T thresh) {
     const bool vi = v >= thresh, oi = o >= thresh;
     return (vi && oi) ? 0.0 : ((vi || oi) ? 1e300 : fabs((double)v - (double)o));
+}
+
+// Per-node change of a tile sweep for the sup-norm stopping test.  FP32
+// values: their difference rounded upward, an upper bound of the exact
+// difference (which FP64 would hold) by at most one unit in the last place,
+// formed without the FP64 pipe (a GB300 SM retires two FP64 operations per
+// clock); the tile's maximum of these bounds is then widened to FP64 and the
+// reduction over tiles and the comparison with tol run in FP64.  FP64
+// values: the FP64 difference.  Both: 0 when v and o are the +inf sentinel, a
+// huge value when only one is; with the plain update (clamp = 0) a move of a
+// few units in the last place counts as no change.
+__device__ __forceinline__ float node_change(float v, float o, int clamp) {
+    const float th = Num<float>::thresh();
+    const bool vi = v >= th, oi = o >= th;
+    float d = (vi && oi) ? 0.f : ((vi || oi) ? 3.0e38f : __fsub_ru(fmaxf(v, o), fminf(v, o)));
+    if (!clamp && d <= (float)Num<float>::noise() * fabsf(v)) d = 0.f;
+    return d;
+}
+
+__device__ __forceinline__ double node_change(double v, double o, int clamp) {
+    double d = change64(v, o, Num<double>::thresh());
+    if (!clamp && d <= Num<double>::noise() * fabs(v)) d = 0.0;
+    return d;
 }
 
 }  // namespace hjbp

@@ -154,14 +154,20 @@ template <typename T, bool kDir> struct TileSmemV {
 // together; NCLS > 0 fully unrolls the symmetric form for a table with
 // exactly NCLS classes (every class then sits in the constant bank as
 // immediates).
-template <typename T, int NCLS, bool kDir, class S>
+// kMasked = false: the tile's image holds no node of another patch and no
+// other target part (every non-usable neighbour is then a node with a
+// negative code, whose value is the +inf sentinel), so the mask can be
+// skipped with the same result.
+template <typename T, int NCLS, bool kDir, class S, bool kMasked = true>
 __device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct) {
     T nb[3][3];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
-            if constexpr (kDir)
+            if constexpr (!kMasked && !kDir)
+                nb[dy][dx] = sm.u[r - 1 + dy][c - 1 + dx];
+            else if constexpr (kDir)
                 nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : sm.d[r - 1 + dy][c - 1 + dx];
             else
                 nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
@@ -237,6 +243,94 @@ __device__ __forceinline__ T sl_update_m(const S &sm, int c, int r, unsigned m, 
         }
     }
     const T b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
+    return b01 < b23 ? b01 : b23;
+}
+
+// Packed FP32 pairs (two lanes of one 64-bit register, PTX .f32x2, sm_100
+// and later): one instruction forms the same rounded FP32 operation on both
+// halves, so pairing two quadrants halves the FMA count of the symmetric
+// pair form with the same result to the last bit.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_abs(unsigned long long a) { return a & 0x7FFFFFFF7FFFFFFFull; }
+
+// sl_update_m for FP32 values and a compile-time NCLS-class symmetric table
+// with the two quadrants of each row of the neighbourhood (sy = -1 and
+// sy = +1) packed into one pair: per class one packed multiply, three packed
+// FMAs for both rows instead of eight scalar FMAs and two multiplies.
+template <int NCLS, bool kMasked, class S>
+__device__ __forceinline__ float sl_update_x2(const S &sm, int c, int r, unsigned m, float hh,
+                                              const CtlTable2<float> &ct) {
+    float nb[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            if constexpr (kMasked)
+                nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<float>::big();
+            else
+                nb[dy][dx] = sm.u[r - 1 + dy][c - 1 + dx];
+        }
+    // row pair R (sy = -1: R = 0, +1: R = 1): halves = the quadrants sx = -1, +1
+    unsigned long long E[2], G[2], A[2];
+#pragma unroll
+    for (int R = 0; R < 2; ++R) {
+        const int sy = R ? 2 : 0;
+        const unsigned long long a10 = f2_pack(nb[1][0], nb[1][2]);
+        const unsigned long long a01 = f2_pack(nb[sy][1], nb[sy][1]);
+        E[R] = f2_add(a10, a01);
+        G[R] = f2_abs(f2_sub(a10, a01));
+        A[R] = f2_pack(nb[sy][0], nb[sy][2]);
+    }
+    const unsigned long long hh2 = f2_pack(hh, hh);
+    float b0 = Num<float>::big(), b1 = Num<float>::big(), b2 = Num<float>::big(), b3 = Num<float>::big();
+#pragma unroll
+    for (int k = 0; k < NCLS; ++k) {
+        const unsigned long long kh = f2_mul(f2_pack(ct.cls_kap[k], ct.cls_kap[k]), hh2);
+        const unsigned long long s2 = f2_pack(ct.cls_s[k], ct.cls_s[k]);
+        const unsigned long long t2 = f2_pack(-ct.cls_t[k], -ct.cls_t[k]);
+        const unsigned long long w2 = f2_pack(ct.cls_kw11[k], ct.cls_kw11[k]);
+        const unsigned long long v0 = f2_fma(t2, G[0], f2_fma(s2, E[0], f2_fma(w2, A[0], kh)));
+        const unsigned long long v1 = f2_fma(t2, G[1], f2_fma(s2, E[1], f2_fma(w2, A[1], kh)));
+        float x0, x1, x2, x3;
+        f2_unpack(v0, x0, x1);
+        f2_unpack(v1, x2, x3);
+        b0 = x0 < b0 ? x0 : b0;
+        b1 = x1 < b1 ? x1 : b1;
+        b2 = x2 < b2 ? x2 : b2;
+        b3 = x3 < b3 ? x3 : b3;
+    }
+    if (ct.axis) {
+        const float ax = fminf(fminf(nb[1][0], nb[1][2]), fminf(nb[0][1], nb[2][1])) + hh;
+        b0 = ax < b0 ? ax : b0;
+    }
+    const float b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
     return b01 < b23 ? b01 : b23;
 }
 
@@ -383,114 +477,6 @@ __device__ __forceinline__ T masked(const S &sm, unsigned m, T v, int c, int r, 
     else return ((m >> bit) & 1u) ? v : Num<T>::big();
 }
 
-// One Gauss-Seidel pass of a tile in direction DIR (0/1: columns left to
-// right / right to left, lane = row; 2/3: rows bottom to top / top to bottom,
-// lane = column), split in two phases with the same result as the step loop
-// of k_value2d:
-//  A. A quadrant whose corners lie on the node's own line or ahead of it
-//     reads only values from before the pass, so for every step of the pass
-//     its minimum (and that of the axis controls ahead and across) is formed
-//     first, all steps independent of each other, into part[step][lane].
-//  B. The dependent chain: per step only the two quadrants (and the axis
-//     control) that read the line updated by the step before.  That line
-//     comes from the lanes' registers by warp shuffles, the node's own line
-//     from the pre-pass values the same way; the halo (never written during a
-//     launch) from shared memory.
-template <typename T, int NCLS, bool kDir, int DIR, class S, class P>
-__device__ __forceinline__ void sweep_split(S &sm, P &part, const CtlTable2<T> &ct, int clamp, int lane) {
-    constexpr bool kCols = DIR < 2;
-    constexpr int sd = (DIR & 1) ? -1 : 1;
-    const int a = 1 + lane;
-#pragma unroll 2
-    for (int st = 0; st < kTile; ++st) {
-        const int pp = sd > 0 ? 1 + st : kTile - st;
-        const int c = kCols ? pp : a, r = kCols ? a : pp;
-        const unsigned m = sm.mk[r - 1][c - 1];
-        T f = Num<T>::big();
-        if (m & 0x8000u) {
-            const T hh = sm.h[r - 1][c - 1];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
-                if ((kCols ? sx : sy) != sd) continue;   // reads the line behind: phase B
-                const T a10 = masked<T, kDir>(sm, m, sm.u[r][c + sx], c, r, sx, 0);
-                const T a01 = masked<T, kDir>(sm, m, sm.u[r + sy][c], c, r, 0, sy);
-                const T a11 = masked<T, kDir>(sm, m, sm.u[r + sy][c + sx], c, r, sx, sy);
-                const T v = quad_min<T, NCLS>(ct, q, a10, a01, a11, hh);
-                f = v < f ? v : f;
-            }
-            if (ct.axis) {
-                T ax;
-                if constexpr (kCols)
-                    ax = fmin(masked<T, kDir>(sm, m, sm.u[r][c + sd], c, r, sd, 0),
-                              fmin(masked<T, kDir>(sm, m, sm.u[r - 1][c], c, r, 0, -1),
-                                   masked<T, kDir>(sm, m, sm.u[r + 1][c], c, r, 0, 1)));
-                else
-                    ax = fmin(masked<T, kDir>(sm, m, sm.u[r + sd][c], c, r, 0, sd),
-                              fmin(masked<T, kDir>(sm, m, sm.u[r][c - 1], c, r, -1, 0),
-                                   masked<T, kDir>(sm, m, sm.u[r][c + 1], c, r, 1, 0)));
-                const T av = ax + hh;
-                f = av < f ? av : f;
-            }
-        }
-        part[st][lane] = f;
-    }
-    __syncwarp();
-    constexpr unsigned kFull = 0xffffffffu;
-    const int p0 = sd > 0 ? 0 : kTile + 1;
-    T prev = kCols ? sm.u[a][p0] : sm.u[p0][a];
-    for (int st = 0; st < kTile; ++st) {
-        const int pp = sd > 0 ? 1 + st : kTile - st, pb = pp - sd;
-        const int c = kCols ? pp : a, r = kCols ? a : pp;
-        const unsigned m = sm.mk[r - 1][c - 1];
-        const T old = sm.u[r][c];
-        // halo values at the ends of the lines (across index 0 and kTile + 1)
-        const T hbm = kCols ? sm.u[0][pb] : sm.u[pb][0], hbp = kCols ? sm.u[kTile + 1][pb] : sm.u[pb][kTile + 1];
-        const T hom = kCols ? sm.u[0][c] : sm.u[r][0], hop = kCols ? sm.u[kTile + 1][c] : sm.u[r][kTile + 1];
-        T bm = __shfl_up_sync(kFull, prev, 1), bp = __shfl_down_sync(kFull, prev, 1);
-        T om = __shfl_up_sync(kFull, old, 1), op = __shfl_down_sync(kFull, old, 1);
-        if (lane == 0) {
-            bm = hbm;
-            om = hom;
-        }
-        if (lane == kTile - 1) {
-            bp = hbp;
-            op = hop;
-        }
-        T nw = old;
-        if (m & 0x8000u) {
-            const T hh = sm.h[r - 1][c - 1];
-            T b = part[st][lane];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
-                if ((kCols ? sx : sy) == sd) continue;   // done in phase A
-                T a10, a01, a11;
-                if constexpr (kCols) {
-                    a10 = masked<T, kDir>(sm, m, prev, c, r, sx, 0);
-                    a01 = masked<T, kDir>(sm, m, sy < 0 ? om : op, c, r, 0, sy);
-                    a11 = masked<T, kDir>(sm, m, sy < 0 ? bm : bp, c, r, sx, sy);
-                } else {
-                    a10 = masked<T, kDir>(sm, m, sx < 0 ? om : op, c, r, sx, 0);
-                    a01 = masked<T, kDir>(sm, m, prev, c, r, 0, sy);
-                    a11 = masked<T, kDir>(sm, m, sx < 0 ? bm : bp, c, r, sx, sy);
-                }
-                const T v = quad_min<T, NCLS>(ct, q, a10, a01, a11, hh);
-                b = v < b ? v : b;
-            }
-            if (ct.axis) {
-                const T av = (kCols ? masked<T, kDir>(sm, m, prev, c, r, -sd, 0)
-                                    : masked<T, kDir>(sm, m, prev, c, r, 0, -sd)) + hh;
-                b = av < b ? av : b;
-            }
-            if (b < Num<T>::thresh()) nw = clamp ? (b < old ? b : old) : b;
-            sm.u[r][c] = nw;
-        }
-        prev = nw;
-    }
-    __syncwarp();
-}
-
 // Parities of the 3x3 tile neighbourhood of tile (tx, ty) as a 9-bit mask
 // (bit 3 (dy+1) + (dx+1)); tiles off the grid read 0 like the ghost ring.
 __device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched &s, int tx, int ty) {
@@ -519,7 +505,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                                                 TileSched s, int par, int rounds, unsigned long long *updates,
                                                 const CtlTable2<T> ct, int clamp, const T *__restrict__ dval,
                                                 const uint8_t *__restrict__ astar = nullptr,
-                                                const Cone2 *__restrict__ cone = nullptr, int split = 0) {
+                                                const Cone2 *__restrict__ cone = nullptr, int packed = 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -527,7 +513,6 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
     __shared__ TileSmemV<T, kDir> sm;
     __shared__ T u0[kTile][kTile + 1];
-    __shared__ T part[kCone ? 1 : kTile][kCone ? 1 : kTile + 1];   // phase-A minima of sweep_split
     __shared__ uint8_t sa[kCone ? kTile : 1][kCone ? kTile + 1 : 1];
     __shared__ unsigned long long cmask[kCone ? 65 : 1];
     __shared__ Ctl4<T> ctab[kCone && NCLS == 0 ? 64 : 1];
@@ -549,6 +534,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     // image is spread over the lanes cell by cell and fully unrolled so that
     // every load is in flight at once, then h (and a*) of the interior
     const unsigned pm = nbr_parities(g, s, tx, ty);
+    unsigned long long ids = 0;   // patches and target parts present in the tile's image
     {
         constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + 31) / 32;
 #pragma unroll
@@ -571,6 +557,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                 }
                 sm.u[r][c] = v;
                 sm.c[r][c] = cd;
+                if (cd >= 0) ids |= 1ull << (cd >= kTargetBase ? cd - kTargetBase : cd);
                 if constexpr (kDir) sm.d[r][c] = dv;
             }
         }
@@ -611,19 +598,12 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         }
     }
     __syncwarp();
+    const unsigned long long all_ids = ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(ids >> 32)) << 32) |
+                                       __reduce_or_sync(0xffffffffu, (unsigned)ids);
+    const bool uniform = !kDir && !kCone && __popcll(all_ids) <= 1;
     // AO2: the tile's sweep directions; or alternating halves (TileSched.alt)
     const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0xAu : 0x5u) : 0xFu);
-    if constexpr (!kCone) {
-        if (split) {
-            for (int rd = 0; rd < rounds; ++rd) {
-                if (tdirs & 1u) sweep_split<T, NCLS, kDir, 0>(sm, part, ct, clamp, lane);
-                if (tdirs & 2u) sweep_split<T, NCLS, kDir, 1>(sm, part, ct, clamp, lane);
-                if (tdirs & 4u) sweep_split<T, NCLS, kDir, 2>(sm, part, ct, clamp, lane);
-                if (tdirs & 8u) sweep_split<T, NCLS, kDir, 3>(sm, part, ct, clamp, lane);
-            }
-        }
-    }
-    for (int rd = 0; rd < ((kCone || !split) ? rounds : 0); ++rd) {
+    for (int rd = 0; rd < rounds; ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
             for (int st = 0; st < kTile; ++st) {
@@ -655,7 +635,18 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                         if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
                     }
                 } else if (active) {
-                    const T best = sl_update_m<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
+                    T best;
+                    if constexpr (std::is_same<T, float>::value && NCLS > 0 && !kDir) {
+                        if (packed)
+                            best = uniform ? sl_update_x2<NCLS, false>(sm, c, r, m, sm.h[r - 1][c - 1], ct)
+                                           : sl_update_x2<NCLS, true>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
+                        else
+                            best = uniform ? sl_update_m<T, NCLS, kDir, decltype(sm), false>(sm, c, r, m, sm.h[r - 1][c - 1], ct)
+                                           : sl_update_m<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
+                    } else {
+                        best = uniform ? sl_update_m<T, NCLS, kDir, decltype(sm), false>(sm, c, r, m, sm.h[r - 1][c - 1], ct)
+                                       : sl_update_m<T, NCLS, kDir>(sm, c, r, m, sm.h[r - 1][c - 1], ct);
+                    }
                     if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
                 }
                 __syncwarp();
@@ -666,7 +657,7 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     }
     // store into the buffer that is not current; change against the start values
     T *dst = ((pm >> 4) & 1u) ? b0 : b1;
-    double mc = 0.0;
+    T mc = 0;
     const int x = x0 + lane;
     for (int r = 1; r <= kTile; ++r) {
         const int y = y0 - 1 + r;
@@ -675,16 +666,13 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
         const T v = sm.u[r][1 + lane];
         const T o = u0[r - 1][lane];
         dst[(int64_t)y * g.n0 + x] = v;
-        double d = change64(v, o, Num<T>::thresh());
-        // the plain update is not monotone and may keep moving by a few units
-        // in the last place; such moves count as no change
-        if (!clamp && d <= Num<T>::noise() * fabs((double)v)) d = 0.0;
-        mc = fmax(mc, d);
+        const T d = node_change(v, o, clamp);
+        mc = d > mc ? d : mc;
     }
     mc = warp_max(mc);
     const int nf = warp_sum(nfree);
     if (lane == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = mc;
+        (par ? s.chg[1] : s.chg[0])[t] = (double)mc;
         s.processed[t] = 1;
         // node updates: one per pass actually run (AO2 may skip passes)
         if (updates) atomicAdd(updates, (unsigned long long)nf * (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
@@ -943,179 +931,194 @@ __global__ void k_queue_init(TileQueue q, int ntiles) {
     }
 }
 
-// Partial minimum over warp w's share of the controls (W warps per tile).
-// Symmetric form: classes [w ncls / W, (w+1) ncls / W), the last warp also
-// takes the axis directions; generic form: each quadrant's range split in W.
-template <typename T, int W, class S>
-__device__ __forceinline__ T sl_partial(const S &sm, int c, int r, unsigned m, T hh, const CtlTable2<T> &ct, int w) {
-    T nb[3][3];
+// One Gauss-Seidel pass (direction DIR: 0/1 columns left to right / right to
+// left with lane = row, 2/3 rows bottom to top / top to bottom with lane =
+// column) of a tile shared by W warps.  Warp w takes a share of the quadrants
+// of every node (W = 2: the two with sy = -1 or the two with sy = +1; W = 4:
+// quadrant w) and one or two of the axis controls; the partial minima meet in
+// shared memory behind one barrier per step, and every warp forms the node's
+// new value from them.  The line updated one step earlier is kept in the
+// lanes' registers (every warp holds the same values) and read by shuffles;
+// lines at or ahead of the step still hold their values from before the pass
+// and are read from shared memory; only warp 0 writes the new values back.
+// Same operations and the same minimum as the one-warp step loop.
+template <typename T, int NCLS, bool kDir, int W, int DIR, class S, class P>
+__device__ __forceinline__ void sweep_mw(S &sm, P &part, const CtlTable2<T> &ct, int clamp, int lane, int w) {
+    constexpr bool kCols = DIR < 2;
+    constexpr int sd = (DIR & 1) ? -1 : 1;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int a = 1 + lane;
+    const int p0 = sd > 0 ? 0 : kTile + 1;
+    T prev = kCols ? sm.u[a][p0] : sm.u[p0][a];
+    for (int st = 0; st < kTile; ++st) {
+        const int pp = sd > 0 ? 1 + st : kTile - st, pb = pp - sd;
+        const int c = kCols ? pp : a, r = kCols ? a : pp;
+        const unsigned m = sm.mk[r - 1][c - 1];
+        const T old = sm.u[r][c];
+        // the line behind at across -1, 0, +1 (halo past the ends)
+        T bm = __shfl_up_sync(kFull, prev, 1), bp = __shfl_down_sync(kFull, prev, 1);
+        if (lane == 0) bm = kCols ? sm.u[0][pb] : sm.u[pb][0];
+        if (lane == kTile - 1) bp = kCols ? sm.u[kTile + 1][pb] : sm.u[pb][kTile + 1];
+        // neighbour (c + dx, r + dy) as the step reads it
+        auto nbv = [&](int dx, int dy) -> T {
+            const int along = kCols ? dx : dy, across = kCols ? dy : dx;
+            T v;
+            if (along == -sd) v = across < 0 ? bm : (across > 0 ? bp : prev);
+            else v = sm.u[r + dy][c + dx];
+            return masked<T, kDir>(sm, m, v, c, r, dx, dy);
+        };
+        T f = Num<T>::big();
+        if (m & 0x8000u) {
+            const T hh = sm.h[r - 1][c - 1];
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx)
-            nb[dy][dx] = ((m >> (3 * dy + dx)) & 1u) ? sm.u[r - 1 + dy][c - 1 + dx] : Num<T>::big();
-    T b0 = Num<T>::big(), b1 = Num<T>::big(), b2 = Num<T>::big(), b3 = Num<T>::big();
-    if (ct.d4) {
-        T E[4], G[4], A[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
-            const T a10 = nb[1][sx], a01 = nb[sy][1];
-            E[q] = a10 + a01;
-            G[q] = fabs(a10 - a01);
-            A[q] = nb[sy][sx];
-        }
-        const int k0 = (w * ct.ncls) / W, k1 = ((w + 1) * ct.ncls) / W;
-        for (int k = k0; k < k1; ++k) {
-            const T kh = ct.cls_kap[k] * hh;
-            const T s = ct.cls_s[k], t = -ct.cls_t[k], wk = ct.cls_kw11[k];
-            const T v0 = fma(t, G[0], fma(s, E[0], fma(wk, A[0], kh)));
-            const T v1 = fma(t, G[1], fma(s, E[1], fma(wk, A[1], kh)));
-            const T v2 = fma(t, G[2], fma(s, E[2], fma(wk, A[2], kh)));
-            const T v3 = fma(t, G[3], fma(s, E[3], fma(wk, A[3], kh)));
-            b0 = v0 < b0 ? v0 : b0;
-            b1 = v1 < b1 ? v1 : b1;
-            b2 = v2 < b2 ? v2 : b2;
-            b3 = v3 < b3 ? v3 : b3;
-        }
-        if (ct.axis && w == W - 1) {
-            const T ax = fmin(fmin(nb[1][0], nb[1][2]), fmin(nb[0][1], nb[2][1])) + hh;
-            b0 = ax < b0 ? ax : b0;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int sx = (q & 1) ? 2 : 0, sy = (q & 2) ? 2 : 0;
-            const T a10 = nb[1][sx], a01 = nb[sy][1], a11 = nb[sy][sx];
-            const int qb = ct.qbeg[q], qn = ct.qbeg[q + 1] - qb;
-            int mm = qb + (w * qn) / W;
-            const int me = qb + ((w + 1) * qn) / W;
-            for (; mm + 1 < me; mm += 2) {
-                const T v0 = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
-                const T v1 = fma(ct.kw11[mm + 1], a11,
-                                 fma(ct.kw01[mm + 1], a01, fma(ct.kw10[mm + 1], a10, ct.kap[mm + 1] * hh)));
-                b0 = v0 < b0 ? v0 : b0;
-                b1 = v1 < b1 ? v1 : b1;
+            for (int q = 0; q < 4; ++q) {
+                const bool mine = W == 4 ? (q == w) : ((q >> 1) == w);
+                if (!mine) continue;
+                const int sx = (q & 1) ? 1 : -1, sy = (q & 2) ? 1 : -1;
+                const T v = quad_min<T, NCLS>(ct, q, nbv(sx, 0), nbv(0, sy), nbv(sx, sy), hh);
+                f = v < f ? v : f;
             }
-            if (mm < me) {
-                const T v = fma(ct.kw11[mm], a11, fma(ct.kw01[mm], a01, fma(ct.kw10[mm], a10, ct.kap[mm] * hh)));
-                b2 = v < b2 ? v : b2;
+            if (ct.axis) {
+                // axis controls land on one neighbour (kap = 1); W = 2: warp 0 the
+                // left and lower ones, warp 1 the right and upper ones
+                T ax;
+                if (W == 4) ax = w == 0 ? nbv(-1, 0) : (w == 1 ? nbv(1, 0) : (w == 2 ? nbv(0, -1) : nbv(0, 1)));
+                else ax = w == 0 ? fmin(nbv(-1, 0), nbv(0, -1)) : fmin(nbv(1, 0), nbv(0, 1));
+                const T av = ax + hh;
+                f = av < f ? av : f;
             }
         }
+        part[st & 1][w][lane] = f;
+        __syncthreads();
+        T b = part[st & 1][0][lane];
+#pragma unroll
+        for (int v = 1; v < W; ++v) b = part[st & 1][v][lane] < b ? part[st & 1][v][lane] : b;
+        T nw = old;
+        if ((m & 0x8000u) && b < Num<T>::thresh()) nw = clamp ? (b < old ? b : old) : b;
+        if (w == 0 && (m & 0x8000u)) sm.u[r][c] = nw;
+        prev = nw;
     }
-    const T b01 = b0 < b1 ? b0 : b1, b23 = b2 < b3 ? b2 : b3;
-    return b01 < b23 ? b01 : b23;
+    __syncthreads();
 }
 
-template <typename T> struct TileSmemW {
-    T u[kTile + 2][kTile + 3];
-    int8_t c[kTile + 2][kTile + 4];
-    T h[kTile][kTile + 1];
-    uint16_t mk[kTile][kTile + 2];
-    T part[4][kTile];
-    double red[4];
-};
-
-// The value sweep with W warps per tile: in every step each warp evaluates
-// its share of the controls for the same 32 nodes (lane = node), the partial
-// minima meet in shared memory and warp 0 writes the update.  Same result as
-// k_value2d; the step latency (the critical path of the front) is shorter
-// and a tile keeps W warps busy.
-template <typename T, bool kClamp, int W>
-__global__ void __launch_bounds__(32 * W) k_value2d_w(Grid2 g, const int8_t *__restrict__ code,
-                                                      const T *__restrict__ h, T *__restrict__ b0,
-                                                      T *__restrict__ b1, TileSched s, int par, int rounds,
-                                                      unsigned long long *updates, const CtlTable2<T> ct) {
+// The value sweep with W warps per tile (2 or 4, see sweep_mw): prologue,
+// passes and epilogue of k_value2d with the work of a step spread over the
+// warps.  Not for AO3 cones.
+template <typename T, int NCLS, bool kDir, int W>
+__global__ void __launch_bounds__(32 * W) k_value2d_mw(Grid2 g, const int8_t *__restrict__ code,
+                                                       const T *__restrict__ h, T *__restrict__ b0,
+                                                       T *__restrict__ b1, TileSched s, int par, int rounds,
+                                                       unsigned long long *updates, const CtlTable2<T> ct, int clamp,
+                                                       const T *__restrict__ dval) {
+    constexpr int NT = 32 * W;
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
-    const int x0 = 1 + (t % g.ntx) * kTile, y0 = 1 + (t / g.ntx) * kTile;
-    __shared__ TileSmemW<T> sm;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < (kTile + 2) * (kTile + 2); e += 32 * W) {
-        const int r = e / (kTile + 2), c = e % (kTile + 2);
-        const int x = x0 - 1 + c, y = y0 - 1 + r;
-        T v = Num<T>::big();
-        int8_t cd = kHard;
-        if (x < g.n0 && y < g.n1) {
-            const int64_t i = (int64_t)y * g.n0 + x;
-            cd = code[i];
-            const int tt = tile_of(g, x, y);
-            v = (tt >= 0 && s.latest[tt]) ? b1[i] : b0[i];
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int x0 = 1 + tx * kTile, y0 = 1 + ty * kTile;
+    __shared__ TileSmemV<T, kDir> sm;
+    __shared__ T u0[kTile][kTile + 1];
+    __shared__ T part[2][W][kTile];
+    __shared__ double red[W];
+    __shared__ int nfr[W];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned pm = nbr_parities(g, s, tx, ty);
+    {
+        constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + NT - 1) / NT;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int q = tid + NT * k;
+            if (q < kCells) {
+                const int r = q / kH, c = q - r * kH;
+                const int x = x0 - 1 + c, y = y0 - 1 + r;
+                T v = Num<T>::big(), dv = Num<T>::big();
+                int8_t cd = kHard;
+                if (x < g.n0 && y < g.n1) {
+                    const int64_t i = (int64_t)y * g.n0 + x;
+                    cd = code[i];
+                    const int px = (c == 0) ? 0 : (c == kH - 1 ? 2 : 1);
+                    const int py = (r == 0) ? 0 : (r == kH - 1 ? 2 : 1);
+                    const bool inner = x >= 1 && x <= g.n0 - 2 && y >= 1 && y <= g.n1 - 2;
+                    const bool odd = inner && ((pm >> (3 * py + px)) & 1u);
+                    v = odd ? b1[i] : b0[i];
+                    if constexpr (kDir) dv = dval[i];
+                }
+                sm.u[r][c] = v;
+                sm.c[r][c] = cd;
+                if constexpr (kDir) sm.d[r][c] = dv;
+            }
         }
-        sm.u[r][c] = v;
-        sm.c[r][c] = cd;
+        const int x = x0 + lane;
+#pragma unroll
+        for (int rr = 0; rr < kTile / W; ++rr) {
+            const int r = w + W * rr, y = y0 + r;
+            sm.h[r][lane] = (x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
+        }
     }
     __syncthreads();
     int nfree = 0;
-    for (int rr = w; rr < kTile; rr += W) {
-        const int r = 1 + rr, c = 1 + lane, x = x0 + lane, y = y0 + rr;
-        const int8_t cd = sm.c[r][c];
-        unsigned m = 0;
-        if (cd >= 0 && cd < kTargetBase) {
-            const int8_t tg = (int8_t)(cd + kTargetBase);
+    {
+        const int c = 1 + lane;
+        for (int rr = 0; rr < kTile / W; ++rr) {
+            const int r = 1 + w + W * rr;
+            const int8_t cd = sm.c[r][c];
+            unsigned m = 0;
+            if (cd >= 0 && cd < kTargetBase) {
+                const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
+                for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
-                    m |= (unsigned)(q == cd || q == tg) << (3 * dy + dx);
-                }
-            m |= 0x8000u;
-            ++nfree;
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int8_t q = sm.c[r - 1 + dy][c - 1 + dx];
+                        m |= (unsigned)(q == cd || q == tg || q == pr) << (3 * dy + dx);
+                    }
+                m |= 0x8000u;
+                ++nfree;
+            }
+            sm.mk[r - 1][lane] = (uint16_t)m;
+            u0[r - 1][lane] = sm.u[r][c];
         }
-        sm.mk[rr][lane] = (uint16_t)m;
-        sm.h[rr][lane] = (m && x < g.n0 && y < g.n1) ? h[(int64_t)y * g.n0 + x] : (T)0;
     }
     __syncthreads();
+    const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0xAu : 0x5u) : 0xFu);
     for (int rd = 0; rd < rounds; ++rd) {
-        for (int dir = 0; dir < 4; ++dir) {
-            for (int st = 0; st < kTile; ++st) {
-                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
-                const int c = (dir < 2) ? s1 : 1 + lane;
-                const int r = (dir < 2) ? 1 + lane : s1;
-                const unsigned m = sm.mk[r - 1][c - 1];
-                const bool active = (m & 0x8000u) != 0;
-                if (active) sm.part[w][lane] = sl_partial<T, W>(sm, c, r, m, sm.h[r - 1][c - 1], ct, w);
-                __syncthreads();
-                if (w == 0 && active) {
-                    T best = sm.part[0][lane];
-#pragma unroll
-                    for (int q = 1; q < W; ++q) best = sm.part[q][lane] < best ? sm.part[q][lane] : best;
-                    const T old = sm.u[r][c];
-                    if (best < Num<T>::thresh()) sm.u[r][c] = kClamp ? (best < old ? best : old) : best;
-                }
-                __syncthreads();
-            }
-        }
+        if (tdirs & 1u) sweep_mw<T, NCLS, kDir, W, 0>(sm, part, ct, clamp, lane, w);
+        if (tdirs & 2u) sweep_mw<T, NCLS, kDir, W, 1>(sm, part, ct, clamp, lane, w);
+        if (tdirs & 4u) sweep_mw<T, NCLS, kDir, W, 2>(sm, part, ct, clamp, lane, w);
+        if (tdirs & 8u) sweep_mw<T, NCLS, kDir, W, 3>(sm, part, ct, clamp, lane, w);
     }
-    // store (warp-strided rows) and block max of the change
-    const int cur = s.latest[t];
-    T *dst = cur ? b0 : b1;
-    const T *src = cur ? b1 : b0;
-    double mc = 0.0;
+    // store into the buffer that is not current; change against the start values
+    T *dst = ((pm >> 4) & 1u) ? b0 : b1;
+    T mc = 0;
     const int x = x0 + lane;
-    for (int rr = w; rr < kTile; rr += W) {
-        const int y = y0 + rr;
+    for (int rr = 0; rr < kTile / W; ++rr) {
+        const int r = 1 + w + W * rr, y = y0 - 1 + r;
         if (y > g.n1 - 2 || x > g.n0 - 2) continue;
-        const int64_t i = (int64_t)y * g.n0 + x;
-        const T v = sm.u[1 + rr][1 + lane];
-        const T o = src[i];
-        dst[i] = v;
-        mc = fmax(mc, change64(v, o, Num<T>::thresh()));
+        const T v = sm.u[r][1 + lane];
+        const T o = u0[r - 1][lane];
+        dst[(int64_t)y * g.n0 + x] = v;
+        const T d = node_change(v, o, clamp);
+        mc = d > mc ? d : mc;
     }
     mc = warp_max(mc);
     const int nf = warp_sum(nfree);
     if (lane == 0) {
-        sm.red[w] = mc;
-        if (updates && nf) atomicAdd(updates, (unsigned long long)nf * 4ull * (unsigned long long)rounds);
+        red[w] = (double)mc;
+        nfr[w] = nf;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double mm = sm.red[0];
-        for (int q = 1; q < W; ++q) mm = fmax(mm, sm.red[q]);
+    if (tid == 0) {
+        double mm = red[0];
+        int nt = nfr[0];
+#pragma unroll
+        for (int v = 1; v < W; ++v) {
+            mm = fmax(mm, red[v]);
+            nt += nfr[v];
+        }
         (par ? s.chg[1] : s.chg[0])[t] = mm;
         s.processed[t] = 1;
+        if (updates)
+            atomicAdd(updates, (unsigned long long)nt * (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
     }
 }
 
@@ -1673,106 +1676,7 @@ template <int RG, bool kSource> struct PhiSmem {
     // the control table, so that per-node lookups hit shared memory
     float kw10[kMaxControls], kw01[kMaxControls], kw11[kMaxControls], kap[kMaxControls];
     int8_t sx[kMaxControls], sy[kMaxControls];
-    float part[RG][kTile][kTile + 1];   // phase-A values of phi_sweep_split
 };
-
-// One Gauss-Seidel pass of the colour transport in direction DIR (as in
-// sweep_split: 0/1 columns, 2/3 rows), in two phases.  A node whose feedback
-// foot lies ahead of its line (or on it) reads only values from before the
-// pass: phase A forms its new value for every step at once.  A node whose foot
-// lies behind needs the line updated one step earlier: phase A forms the
-// product of its own-line corner, phase B adds the two corners behind, taken
-// from the lanes' registers by one indexed shuffle per colour.  Every node
-// sums its corners own line first, then the corner straight behind or ahead,
-// then the diagonal one.
-template <int RG, bool kSource, int DIR, class S>
-__device__ __forceinline__ void phi_sweep_split(S &sm, unsigned alive, int lane) {
-    constexpr bool kCols = DIR < 2;
-    constexpr int sd = (DIR & 1) ? -1 : 1;
-    constexpr unsigned kFull = 0xffffffffu;
-    const int a = 1 + lane;
-#pragma unroll 2
-    for (int st = 0; st < kTile; ++st) {
-        const int pp = sd > 0 ? 1 + st : kTile - st;
-        const int c = kCols ? pp : a, r = kCols ? a : pp;
-        const int8_t cd = sm.c[r][c];
-        const uint8_t ai = sm.a[r - 1][c - 1];
-        if (cd >= 0 && cd < kTargetBase && ai != kNoControl) {
-            const int sx = sm.sx[ai], sy = sm.sy[ai];
-            const float w10 = sm.kw10[ai], w01 = sm.kw01[ai], w11 = sm.kw11[ai];
-            const bool ahead = (kCols ? sx : sy) == sd;
-#pragma unroll
-            for (int q = 0; q < RG; ++q) {
-                if (!((alive >> q) & 1u)) continue;
-                // own-line corner first
-                float v = kCols ? w01 * sm.u[q][r + sy][c] : w10 * sm.u[q][r][c + sx];
-                if (ahead) {
-                    v = kCols ? fmaf(w10, sm.u[q][r][c + sx], v) : fmaf(w01, sm.u[q][r + sy][c], v);
-                    v = fmaf(w11, sm.u[q][r + sy][c + sx], v);
-                    if constexpr (kSource) {
-                        v = fmaf(sm.kap[ai], sm.src[q][r - 1][c - 1], v);
-                    } else {
-                        const float o = sm.u[q][r][c];
-                        v = v > o ? v : o;
-                    }
-                }
-                sm.part[q][st][lane] = v;
-            }
-        }
-    }
-    __syncwarp();
-    const int p0 = sd > 0 ? 0 : kTile + 1;
-    float prev[RG];
-#pragma unroll
-    for (int q = 0; q < RG; ++q) prev[q] = kCols ? sm.u[q][a][p0] : sm.u[q][p0][a];
-    for (int st = 0; st < kTile; ++st) {
-        const int pp = sd > 0 ? 1 + st : kTile - st, pb = pp - sd;
-        const int c = kCols ? pp : a, r = kCols ? a : pp;
-        const int8_t cd = sm.c[r][c];
-        const uint8_t ai = sm.a[r - 1][c - 1];
-        const bool active = cd >= 0 && cd < kTargetBase && ai != kNoControl;
-        int so = 0;   // across offset of the diagonal corner behind
-        float w_st = 0.f, w_dg = 0.f, kp = 0.f;
-        bool ahead = true;
-        if (active) {
-            const int sx = sm.sx[ai], sy = sm.sy[ai];
-            ahead = (kCols ? sx : sy) == sd;
-            so = kCols ? sy : sx;
-            w_st = kCols ? sm.kw10[ai] : sm.kw01[ai];
-            w_dg = sm.kw11[ai];
-            kp = sm.kap[ai];
-        }
-        // the lane across so holds the diagonal corner behind; past the line's
-        // ends the halo (never written during a launch)
-        const int src_lane = lane + so;
-        const bool edge = src_lane < 0 || src_lane >= kTile;
-        const int hx = kCols ? pb : (so < 0 ? 0 : kTile + 1), hy = kCols ? (so < 0 ? 0 : kTile + 1) : pb;
-#pragma unroll
-        for (int q = 0; q < RG; ++q) {
-            if (!((alive >> q) & 1u)) continue;
-            const float dg_sh = __shfl_sync(kFull, prev[q], src_lane & 31);
-            const float old = sm.u[q][r][c];
-            float nw = old;
-            if (active) {
-                if (ahead) {
-                    nw = sm.part[q][st][lane];
-                } else {
-                    const float dg = edge ? sm.u[q][hy][hx] : dg_sh;
-                    float v = fmaf(w_st, prev[q], sm.part[q][st][lane]);
-                    v = fmaf(w_dg, dg, v);
-                    if constexpr (kSource) {
-                        nw = fmaf(kp, sm.src[q][r - 1][c - 1], v);
-                    } else {
-                        nw = v > old ? v : old;
-                    }
-                }
-                sm.u[q][r][c] = nw;
-            }
-            prev[q] = nw;
-        }
-    }
-    __syncwarp();
-}
 
 // One FP32 launch over the active tiles for RG colours, each node solved for
 // itself (R13) with its fixed coarse feedback a*_i:
@@ -1781,11 +1685,16 @@ __device__ __forceinline__ void phi_sweep_split(S &sm, unsigned alive, int lane)
 // The bulk rises monotonically from 0; the tile's change is the max over
 // its colours.
 template <int RG, bool kSource>
-__global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
+__global__ void __launch_bounds__(32 * (RG < 4 ? RG : 4)) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
                                               const uint8_t *__restrict__ astar, float *__restrict__ b0,
                                               float *__restrict__ b1, const float *__restrict__ src, TileSched s,
-                                              int par, int rounds, const PhiCtl *__restrict__ pc, int split = 0,
+                                              int par, int rounds, const PhiCtl *__restrict__ pc,
                                               unsigned long long *updates = nullptr) {
+    // one warp per colour (up to four; with eight colours each warp takes two):
+    // the colours are independent linear systems, so the warps never wait on
+    // one another inside a pass
+    constexpr int W = RG < 4 ? RG : 4;
+    constexpr int NT = 32 * W;
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -1796,9 +1705,11 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     // the 48 KB of static shared memory
     extern __shared__ __align__(16) unsigned char phi_smem_raw[];
     PhiSmem<RG, kSource> &sm = *reinterpret_cast<PhiSmem<RG, kSource> *>(phi_smem_raw);
-    const int lane = threadIdx.x;
+    __shared__ unsigned alive_w[W];
+    __shared__ float red_w[W];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int ncu = pc->nc;
-    for (int m = lane; m < ncu; m += 32) {
+    for (int m = tid; m < ncu; m += NT) {
         sm.kw10[m] = pc->kw10[m];
         sm.kw01[m] = pc->kw01[m];
         sm.kw11[m] = pc->kw11[m];
@@ -1809,12 +1720,12 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
     const unsigned pm = nbr_parities(g, s, tx, ty);
     unsigned alive = 0;   // colours with a nonzero value (or source) in the tile or its halo
     {
-        // halo image cell by cell over the lanes, fully unrolled so that the
+        // halo image cell by cell over the threads, fully unrolled so that the
         // loads are all in flight together; then a* (and the source) of the interior
-        constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + 31) / 32;
+        constexpr int kH = kTile + 2, kCells = kH * kH, kPer = (kCells + NT - 1) / NT;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            const int q0 = lane + 32 * k;
+            const int q0 = tid + NT * k;
             if (q0 < kCells) {
                 const int r = q0 / kH, c = q0 - r * kH;
                 const int x = x0 - 1 + c, y = y0 - 1 + r;
@@ -1843,7 +1754,8 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
         }
         const int x = x0 + lane;
 #pragma unroll
-        for (int r = 0; r < kTile; ++r) {
+        for (int rr = 0; rr < kTile / W; ++rr) {
+            const int r = w + W * rr;
             const int y = y0 + r;
             const bool in = x < g.n0 && y < g.n1;
             const int64_t i = (int64_t)y * g.n0 + x;
@@ -1859,8 +1771,12 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
         }
     }
     alive = __reduce_or_sync(0xffffffffu, alive);
-    __syncwarp();
-    if (updates && alive) {
+    if (lane == 0) alive_w[w] = alive;
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < W; ++v) alive |= alive_w[v];
+    const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
+    if (updates && alive && w == 0) {
         // node-colour updates of this launch: transported nodes x live colours x passes
         int na = 0;
         for (int r = 1; r <= kTile; ++r) {
@@ -1868,21 +1784,14 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
             na += (cd >= 0 && cd < kTargetBase && sm.a[r - 1][lane] != kNoControl) ? 1 : 0;
         }
         na = __reduce_add_sync(0xffffffffu, na);
-        const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
         if (lane == 0 && na)
             atomicAdd(updates, (unsigned long long)na * (unsigned long long)__popc(alive) *
                                    (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
     }
-    if (alive && split) {
-        const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
-        for (int rd = 0; rd < rounds; ++rd) {
-            if (tdirs & 1u) phi_sweep_split<RG, kSource, 0>(sm, alive, lane);
-            if (tdirs & 2u) phi_sweep_split<RG, kSource, 1>(sm, alive, lane);
-            if (tdirs & 4u) phi_sweep_split<RG, kSource, 2>(sm, alive, lane);
-            if (tdirs & 8u) phi_sweep_split<RG, kSource, 3>(sm, alive, lane);
-        }
-    } else if (alive) {
-        const unsigned tdirs = s.dirs ? s.dirs[t] : 0xFu;
+    // the passes of this warp's colours, one colour after the other
+    for (int q = w; q < RG; q += W) {
+        if (!((alive >> q) & 1u)) continue;
+        float(*u)[kTile + 3] = sm.u[q];
         for (int rd = 0; rd < rounds; ++rd) {
             for (int dir = 0; dir < 4; ++dir) {
                 if (!((tdirs >> dir) & 1u)) continue;
@@ -1893,51 +1802,40 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
                     const int8_t cd = sm.c[r][c];
                     const uint8_t a = sm.a[r - 1][c - 1];
                     const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
-                    float nw[RG];
+                    float nw = 0.0f;
                     if (active) {
                         const int sx = sm.sx[a], sy = sm.sy[a];
-                        const float w10 = sm.kw10[a], w01 = sm.kw01[a], w11 = sm.kw11[a];
-                        const float kp = sm.kap[a];
-#pragma unroll
-                        for (int q = 0; q < RG; ++q) {
-                            if (!((alive >> q) & 1u)) {
-                                nw[q] = 0.0f;
-                                continue;
-                            }
-                            float v = w10 * sm.u[q][r][c + sx];
-                            v = fmaf(w01, sm.u[q][r + sy][c], v);
-                            v = fmaf(w11, sm.u[q][r + sy][c + sx], v);
-                            if (kSource) {
-                                nw[q] = fmaf(kp, sm.src[q][r - 1][c - 1], v);
-                            } else {
-                                const float o = sm.u[q][r][c];
-                                nw[q] = v > o ? v : o;
-                            }
+                        float v = sm.kw10[a] * u[r][c + sx];
+                        v = fmaf(sm.kw01[a], u[r + sy][c], v);
+                        v = fmaf(sm.kw11[a], u[r + sy][c + sx], v);
+                        if (kSource) {
+                            nw = fmaf(sm.kap[a], sm.src[q][r - 1][c - 1], v);
+                        } else {
+                            const float o = u[r][c];
+                            nw = v > o ? v : o;
                         }
                     }
                     __syncwarp();
-                    if (active) {
-#pragma unroll
-                        for (int q = 0; q < RG; ++q)
-                            if ((alive >> q) & 1u) sm.u[q][r][c] = nw[q];
-                    }
+                    if (active) u[r][c] = nw;
                     __syncwarp();
                 }
             }
         }
     }
+    __syncthreads();
     const int cur = (pm >> 4) & 1u;
     float *dst = cur ? b0 : b1;
     const float *old = cur ? b1 : b0;
     float mc = 0.f;
     const int x = x0 + lane;
     // predicated and unrolled so that the reads of the previous values are
-    // all in flight together
+    // all in flight together; warp w stores rows w, w + W, ...
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
         const bool live = (alive >> q) & 1u;
-#pragma unroll 16
-        for (int r = 1; r <= kTile; ++r) {
+#pragma unroll 8
+        for (int rr = 0; rr < kTile / W; ++rr) {
+            const int r = 1 + w + W * rr;
             const int y = y0 - 1 + r;
             if (y <= g.n1 - 2 && x <= g.n0 - 2) {
                 const int64_t i = (int64_t)q * N + (int64_t)y * g.n0 + x;
@@ -1948,8 +1846,13 @@ __global__ void __launch_bounds__(32) k_phi2d(Grid2 g, const int8_t *__restrict_
         }
     }
     mc = warp_max(mc);
-    if (lane == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = mc;
+    if (lane == 0) red_w[w] = mc;
+    __syncthreads();
+    if (tid == 0) {
+        float m = red_w[0];
+#pragma unroll
+        for (int v = 1; v < W; ++v) m = fmaxf(m, red_w[v]);
+        (par ? s.chg[1] : s.chg[0])[t] = m;
         s.processed[t] = 1;
     }
 }
@@ -2872,6 +2775,18 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
     return total;
 }
 
+template <typename T, int NCLS, int W>
+void launch_mw(int ntiles, cudaStream_t st, const Grid2 &g, const int8_t *code, const T *h, T *b0, T *b1,
+               const TileSched &s, int par, int rounds, unsigned long long *updates, const CtlTable2<T> &ct,
+               int clamp, const T *dval) {
+    if (dval)
+        k_value2d_mw<T, NCLS, true, W><<<ntiles, 32 * W, 0, st>>>(g, code, h, b0, b1, s, par, rounds, updates, ct,
+                                                                    clamp, dval);
+    else
+        k_value2d_mw<T, NCLS, false, W><<<ntiles, 32 * W, 0, st>>>(g, code, h, b0, b1, s, par, rounds, updates, ct,
+                                                                     clamp, nullptr);
+}
+
 // Value iteration on S* (R14) to the sup-norm tolerance: monotone from M, or
 // plain from the warm start (AO1); dval: Dirichlet data (Eq. dbc) or NULL.
 template <typename T>
@@ -2886,12 +2801,12 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
     const int warps = p.desc.tune[3] > 0 ? p.desc.tune[3] : 1;
     const bool pairs = cone && ct.d4 && ct.ncls == 8 && p.cone_pairs;   // AO3 in the pair form
-    // tune[6] = 2: the two-phase passes of sweep_split (same result, measured slower)
-    const int split = p.desc.tune[6] == 2 ? 1 : 0;
+    // tune[6] = 2: the packed FP32-pair update (sl_update_x2; same result)
+    const int packed = p.desc.tune[6] == 2 ? 1 : 0;
     LaunchTimer timer(p, timed);
     RunResult rr = run_tiles(p, g, s, tol, cap, [&](int par, int) {
         timer.begin();
-        const bool plain = clamp && !dval && !cone;  // the multi-warp variant has none of the options
+        const bool mw = !cone && (warps == 2 || warps == 4);   // several warps per tile (no AO3 cones)
         if (cone && pairs && dval)
             k_value2d<T, 8, true, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
                                                                        ct, clamp, dval, p.astar, cone);
@@ -2904,25 +2819,29 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
         else if (cone)
             k_value2d<T, 0, false, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
                                                                         ct, clamp, nullptr, p.astar, cone);
-        else if (warps == 4 && plain)
-            k_value2d_w<T, true, 4><<<s.ntiles, 128, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
-        else if (warps == 2 && plain)
-            k_value2d_w<T, true, 2><<<s.ntiles, 64, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct);
+        else if (mw && warps == 2 && ct.d4 && ct.ncls == 8)
+            launch_mw<T, 8, 2>(s.ntiles, p.stream, g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
+        else if (mw && warps == 2)
+            launch_mw<T, 0, 2>(s.ntiles, p.stream, g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
+        else if (mw && ct.d4 && ct.ncls == 8)
+            launch_mw<T, 8, 4>(s.ntiles, p.stream, g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
+        else if (mw)
+            launch_mw<T, 0, 4>(s.ntiles, p.stream, g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
         else if (dval && ct.d4 && ct.ncls == 8)
             k_value2d<T, 8, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                 clamp, dval, nullptr, nullptr, split);
+                                                                 clamp, dval);
         else if (dval)
             k_value2d<T, 0, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                 clamp, dval, nullptr, nullptr, split);
+                                                                 clamp, dval);
         else if (ct.d4 && ct.ncls == 8)
             k_value2d<T, 8, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                  clamp, nullptr, nullptr, nullptr, split);
+                                                                  clamp, nullptr, nullptr, nullptr, packed);
         else if (ct.d4 && ct.ncls == 4 && std::is_same<T, float>::value)
             k_value2d<T, 4, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                  clamp, nullptr, nullptr, nullptr, split);
+                                                                  clamp, nullptr, nullptr, nullptr, packed);
         else
             k_value2d<T, 0, false><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
-                                                                  clamp, nullptr, nullptr, nullptr, split);
+                                                                  clamp, nullptr);
         ++p.stats.kernel_launches;
         if (fine) ++p.stats.sweep_kernel_launches;
         timer.end();
@@ -3078,7 +2997,7 @@ hjbp_status solve2d(hjbp_plan &p) {
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
     const int R = p.R;
     const int vrounds = d.tune[0] > 0 ? d.tune[0] : 2;
-    const int prounds = d.tune[1] > 0 ? d.tune[1] : 3;
+    const int prounds = d.tune[1] > 0 ? d.tune[1] : 2;
     hjbp_stats &S = p.stats;
     std::memset(&S, 0, sizeof(S));
     hjbp_status status = HJBP_OK;
@@ -3171,8 +3090,6 @@ hjbp_status solve2d(hjbp_plan &p) {
             double *phig = alloc_n<double>(p, N * RG);
             float *rmax = alloc_n<float>(p, 1);
             const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
-            // tune[6] = 2: the two-phase passes of phi_sweep_split (measured slower)
-            const int psplit = d.tune[6] == 2 ? 1 : 0;
             // per-launch CUDA events (HJBP_FLAG_TIME_SWEEPS) and the node-colour update count
             LaunchTimer ptimer(p, (d.flags & HJBP_FLAG_TIME_SWEEPS) != 0);
             unsigned long long *pupd = alloc_n<unsigned long long>(p, 1);
@@ -3192,8 +3109,8 @@ hjbp_status solve2d(hjbp_plan &p) {
                     ++p.stats.kernel_launches;
                     RunResult rp = run_tiles(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par, int) {
                         ptimer.begin();
-                        k_phi2d<G, false><<<sched.ntiles, 32, sizeof(PhiSmem<G, false>), st>>>(
-                            g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc, psplit, pupd);
+                        k_phi2d<G, false><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, false>), st>>>(
+                            g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc, pupd);
                         ptimer.end();
                         ++p.stats.kernel_launches;
                     });
@@ -3217,8 +3134,8 @@ hjbp_status solve2d(hjbp_plan &p) {
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         RunResult rc = run_tiles(p, g, sched, told, cap, [&](int par, int) {
                             ptimer.begin();
-                            k_phi2d<G, true><<<sched.ntiles, 32, sizeof(PhiSmem<G, true>), st>>>(
-                                g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dpc, psplit, pupd);
+                            k_phi2d<G, true><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, true>), st>>>(
+                                g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dpc, pupd);
                             ptimer.end();
                             ++p.stats.kernel_launches;
                         });

@@ -240,6 +240,7 @@ template <typename T, bool kDir = false> struct Tile3 {
     int8_t c[kT3 + 2][kT3 + 2][kT3 + 4];
     T d[kDir ? kT3 + 2 : 1][kDir ? kT3 + 2 : 1][kDir ? kT3 + 3 : 1];   // Dirichlet data (Eq. dbc)
     double red[2];
+    T redt[2];          // per-warp maxima of the tile change (type of the values)
 };
 
 template <typename T, bool kDir>
@@ -273,7 +274,7 @@ __device__ __forceinline__ double store_tile3(const Grid3 &g, const TileSched &s
     const int cur = s.latest[t];
     T *dst = cur ? b0 : b1;
     const T *src = cur ? b1 : b0;
-    double mc = 0.0;
+    T mc = 0;
     for (int e = threadIdx.x; e < kT3 * kT3 * kT3; e += blockDim.x) {
         const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
@@ -282,12 +283,11 @@ __device__ __forceinline__ double store_tile3(const Grid3 &g, const TileSched &s
         const T v = sm.u[lz + 1][ly + 1][lx + 1];
         const T o = src[i];
         dst[i] = v;
-        double d = change64(v, o, Num<T>::thresh());
-        // the plain update (warm start) may move by a few units in the last place
-        if (!clamp && d <= Num<T>::noise() * fabs((double)v)) d = 0.0;
-        mc = fmax(mc, d);
+        const T d = node_change(v, o, clamp);
+        mc = d > mc ? d : mc;
     }
-    return block_max64(mc, sm.red);
+    // the tile's maximum in FP64 (an upper bound of the exact change, see node_change)
+    return (double)block_max64(mc, sm.redt);
 }
 
 // Local coordinates (1..8) of the node thread `tid` updates at step `st` of
@@ -1218,13 +1218,23 @@ template <int RG, bool kS> struct Phi3Smem {
     // signs (bit 0..2: x, y, z positive) of every control
     float4 tw[kMaxControls][2];
     uint8_t toff[kMaxControls];
-    double red[2];
+    float redf[8];   // per-warp maxima of the tile change
 };
 
 // FP32 colour transport (bulk: monotone max from 0; correction: with source).
 // kGen: the weights of a node's a* from its column's row of gen.p32.
+// The colours are independent linear systems: the block holds one group of
+// kT3n threads per colour (up to four groups; eight colours give each group
+// two), every group sweeps its own colours behind its own named barrier, so
+// the groups never wait on one another inside a pass.
+template <int RG> constexpr int phi3_groups() { return RG < 4 ? RG : 4; }
+
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(kT3n) : "memory");
+}
+
 template <int RG, bool kSource, bool kGen = false>
-__global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restrict__ code,
+__global__ void __launch_bounds__(kT3n * phi3_groups<RG>()) k_phi3d(Grid3 g, const int8_t *__restrict__ code,
                                                 const uint8_t *__restrict__ astar, float *__restrict__ b0,
                                                 float *__restrict__ b1, const float *__restrict__ src, TileSched s,
                                                 int par, int rounds, const Ctl3 *__restrict__ pc,
@@ -1288,16 +1298,21 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
     const unsigned live = salive;
     // AO2: the tile's sweep directions; or alternating halves
     const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0x2Au : 0x15u) : 0x3Fu);
-    for (int rd = 0; rd < rounds && live; ++rd)
+    constexpr int NG = phi3_groups<RG>(), QPG = RG / NG;   // groups, colours per group
+    const int grp = tid / kT3n, gt = tid % kT3n;
+    unsigned mine = 0;   // this group's live colours
+#pragma unroll
+    for (int k = 0; k < QPG; ++k) mine |= live & (1u << (grp + NG * k));
+    for (int rd = 0; rd < rounds && mine; ++rd)
         for (int dir = 0; dir < 6; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
             for (int st = 0; st < kT3; ++st) {
                 int lx, ly, lz;
-                plane_node(dir, st, tid, lx, ly, lz);
+                plane_node(dir, st, gt, lx, ly, lz);
                 const int8_t cd = sm.c[lz][ly][lx];
                 const uint8_t a = sm.a[lz - 1][ly - 1][lx - 1];
                 const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
-                float nw[RG];
+                float nw[QPG];
                 if (active) {
                     unsigned of;
                     float4 w0, w1;
@@ -1315,9 +1330,10 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                     const int sx = (of & 1u) ? 1 : -1, sy = (of & 2u) ? 1 : -1, sz = (of & 4u) ? 1 : -1;
                     const float kw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-                    for (int q = 0; q < RG; ++q) {
-                        if (!((live >> q) & 1u)) {
-                            nw[q] = 0.0f;
+                    for (int k = 0; k < QPG; ++k) {
+                        const int q = grp + NG * k;
+                        if (!((mine >> q) & 1u)) {
+                            nw[k] = 0.0f;
                             continue;
                         }
                         float v = 0.0f;
@@ -1326,30 +1342,34 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                             v = fmaf(kw[b],
                                      sm.u[q][lz + ((b & 4) ? sz : 0)][ly + ((b & 2) ? sy : 0)][lx + ((b & 1) ? sx : 0)], v);
                         if (kSource) {
-                            nw[q] = fmaf(kw[0], sm.src[q][lz - 1][ly - 1][lx - 1], v);
+                            nw[k] = fmaf(kw[0], sm.src[q][lz - 1][ly - 1][lx - 1], v);
                         } else {
                             const float o = sm.u[q][lz][ly][lx];
-                            nw[q] = v > o ? v : o;
+                            nw[k] = v > o ? v : o;
                         }
                     }
                 }
-                __syncthreads();
+                group_sync(grp);
                 if (active) {
 #pragma unroll
-                    for (int q = 0; q < RG; ++q)
-                        if ((live >> q) & 1u) sm.u[q][lz][ly][lx] = nw[q];
+                    for (int k = 0; k < QPG; ++k) {
+                        const int q = grp + NG * k;
+                        if ((mine >> q) & 1u) sm.u[q][lz][ly][lx] = nw[k];
+                    }
                 }
-                __syncthreads();
+                group_sync(grp);
             }
         }
+    __syncthreads();
     const int cur = s.latest[t];
     float *dst = cur ? b0 : b1;
     const float *old = cur ? b1 : b0;
-    double mc = 0.0;
-    // predicated and unrolled so that the reads of the previous values overlap
+    float mc = 0.f;
+    // predicated and unrolled so that the reads of the previous values overlap;
+    // differences rounded upward (an upper bound, no FP64 pipe per node)
 #pragma unroll
-    for (int k = 0; k < kT3 * kT3 * kT3 / kT3n; ++k) {
-        const int e = tid + k * kT3n;
+    for (int k = 0; k < kT3 * kT3 * kT3 / (kT3n * NG); ++k) {
+        const int e = tid + k * kT3n * NG;
         const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         if (x <= g.n0 - 2 && y <= g.n1 - 2 && z <= g.n2 - 2) {
@@ -1359,13 +1379,17 @@ __global__ void __launch_bounds__(kT3n) k_phi3d(Grid3 g, const int8_t *__restric
                 const float v = sm.u[q][lz + 1][ly + 1][lx + 1];
                 const float o = old[(int64_t)q * N + i];
                 dst[(int64_t)q * N + i] = v;
-                mc = fmax(mc, (double)fabsf(v - o));
+                mc = fmaxf(mc, __fsub_ru(fmaxf(v, o), fminf(v, o)));
             }
         }
     }
-    mc = block_max64(mc, sm.red);
+    mc = warp_max3(mc);
+    if ((tid & 31) == 0) sm.redf[tid >> 5] = mc;
+    __syncthreads();
     if (tid == 0) {
-        (par ? s.chg[1] : s.chg[0])[t] = mc;
+        float m = sm.redf[0];
+        for (int w = 1; w < kT3n * NG / 32; ++w) m = fmaxf(m, sm.redf[w]);
+        (par ? s.chg[1] : s.chg[0])[t] = (double)m;
         s.processed[t] = 1;
     }
 }
@@ -2243,10 +2267,10 @@ hjbp_status solve3d(hjbp_plan &p) {
                     ++S.kernel_launches;
                     Run3 rp = run_tiles3(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par) {
                         if (per_node)
-                            k_phi3d<G, false, true><<<sched.ntiles, kT3n, 0, st>>>(
+                            k_phi3d<G, false, true><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(
                                 g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dct, gfine);
                         else
-                            k_phi3d<G, false><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, nullptr,
+                            k_phi3d<G, false><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(g, code0, p.astar, f0, f1, nullptr,
                                                                              sched.d, par, prounds, dct);
                         ++S.kernel_launches;
                     });
@@ -2273,10 +2297,10 @@ hjbp_status solve3d(hjbp_plan &p) {
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         Run3 rc2 = run_tiles3(p, g, sched, told, cap, [&](int par) {
                             if (per_node)
-                                k_phi3d<G, true, true><<<sched.ntiles, kT3n, 0, st>>>(
+                                k_phi3d<G, true, true><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(
                                     g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dct, gfine);
                             else
-                                k_phi3d<G, true><<<sched.ntiles, kT3n, 0, st>>>(g, code0, p.astar, f0, f1, r32,
+                                k_phi3d<G, true><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(g, code0, p.astar, f0, f1, r32,
                                                                                 sched.d, par, prounds, dct);
                             ++S.kernel_launches;
                         });
