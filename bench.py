@@ -275,7 +275,9 @@ def roofline_value(s0, p, alu_peak, sms, sm_max):
     """The FP32 value sweep (Eq. SLscheme, Step 3.2): algorithmic lane-ops of
     one launch (node-control updates x 4 in 2D, 8 in 3D) over its average
     CUDA-event duration."""
-    launches = max(1, s0["sweep_kernel_launches"])
+    # the launches that had work (their CUDA-event times are the ones summed;
+    # launches queued after the last active tile find nothing to do)
+    launches = max(1, s0["sweeps_fine"])
     per = OPS_PER_UPDATE if p.dim == 2 else OPS_PER_UPDATE_3D
     ops_per_launch = s0["node_control_updates"] * per / launches
     avg_launch_s = s0["ms_sweep_kernel"] / 1e3 / launches

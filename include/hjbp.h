@@ -146,8 +146,8 @@ typedef struct {
                            decreasing pass of every axis: 3D default (0; 2 runs all six
                            passes), 2D only with 1 (measured slower there), [6] 2D kernel
                            variants: 0 default, 1 the per-control FP64 polish instead of the
-                           pair-form one, 2 the two-phase Gauss-Seidel passes (same results,
-                           measured slower), [7] reserved (0) */
+                           pair-form one, 2 the scalar FP32 update instead of the packed
+                           FP32x2 one (same results), [7] reserved (0) */
     double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
                            minimum of Step 3.2 at node i to the controls a with
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse

@@ -2801,8 +2801,9 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     const bool timed = fine && (p.desc.flags & HJBP_FLAG_TIME_SWEEPS);
     const int warps = p.desc.tune[3] > 0 ? p.desc.tune[3] : 1;
     const bool pairs = cone && ct.d4 && ct.ncls == 8 && p.cone_pairs;   // AO3 in the pair form
-    // tune[6] = 2: the packed FP32-pair update (sl_update_x2; same result)
-    const int packed = p.desc.tune[6] == 2 ? 1 : 0;
+    // the packed FP32-pair update (sl_update_x2, same result to the last bit);
+    // tune[6] = 2: the scalar form
+    const int packed = p.desc.tune[6] == 2 ? 0 : 1;
     LaunchTimer timer(p, timed);
     RunResult rr = run_tiles(p, g, s, tol, cap, [&](int par, int) {
         timer.begin();

@@ -76,8 +76,8 @@ def test_pair_form_polish_matches_per_control_polish(pkg):
 
 @pytest.mark.parametrize("case", ["patchy_fp32_pairs", "obstacles", "warm_start"])
 def test_packed_pair_update_equals_scalar(pkg, case):
-    """The FP32 update with two quadrants per packed FP32x2 operation
-    (tune[6] = 2) rounds every operation as the scalar form does."""
+    """The FP32 update with two quadrants per packed FP32x2 operation (the
+    default) rounds every operation as the scalar form (tune[6] = 2) does."""
     make, prec, mode = CASES[case]
     p = make()
     flags = {"dirichlet": pkg.HJBP_FLAG_DIRICHLET, "warm": pkg.HJBP_FLAG_WARM_START}.get(mode, 0)
