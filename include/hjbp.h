@@ -139,7 +139,7 @@ typedef struct {
     int flags;          /* HJBP_FLAG_* bits */
     int tune[8];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
                            launch of the value sweep (2), [1] of the colour transport (2),
-                           [2] passes per launch of the reachability sweep (1), [3] warps
+                           [2] passes per launch of the 3D reachability sweep (1; the 2D one runs bit-set rounds to the tile's fixed point), [3] warps
                            per 32x32 tile of the 2D value sweep (1; 1, 2 or 4), [4] resident
                            warps per SM of the tile-queue sweep (occupancy limit), [5] the
                            fine-grid launches run the increasing or (alternately) the

@@ -1218,10 +1218,10 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
         }
     }
     __syncwarp();
-    // per interior node: bits 0..8 usable neighbour (3 dy + dx), bits 9..17
-    // neighbour is terminal, bit 31 node free and unreached; pres: the corner
-    // patterns of the node's controls per quadrant
-    __shared__ uint32_t mk[kTile][kTile + 1];
+    // per interior node: bits 0..8 candidate corners in the patch (3 dy + dx),
+    // bit 9 a candidate is terminal, bit 31 node free and unreached; pres: the
+    // corner patterns of the node's controls per quadrant
+    uint64_t cand_b[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, term_b = 0, open_b = 0;
     {
         const int c = 1 + lane;
         const uint32_t all = (uint32_t)rt.present[0] | ((uint32_t)rt.present[1] << 8) |
@@ -1270,39 +1270,62 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                 // bits 0..8: candidate corners in the patch; bit 9: a candidate is terminal
                 m = (cand & same) | ((uint32_t)((cand & term) != 0) << 9) | 0x80000000u;
             }
-            mk[r - 1][lane] = m;
-        }
-    }
-    __syncwarp();
-    int flips = 0;
-    for (int pass = 0; pass < passes; ++pass)
-        for (int dir = 0; dir < 4; ++dir) {
-            for (int st = 0; st < kTile; ++st) {
-                const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
-                const int c = (dir < 2) ? s1 : 1 + lane;
-                const int r = (dir < 2) ? 1 + lane : s1;
-                const uint32_t m = mk[r - 1][c - 1];
-                bool hit = false;
-                if ((m & 0x80000000u) && !sr[r][c]) {
-                    hit = (m >> 9) & 1u;
+            // row r as bit sets over the columns (bit c = column c, 0..33): the
+            // nodes with candidate corner b, with a terminal candidate, still open
 #pragma unroll
-                    for (int b = 0; b < 9; ++b)
-                        if ((m >> b) & 1u) hit |= sr[r - 1 + b / 3][c - 1 + b % 3] != 0;
-                }
-                __syncwarp();
-                if (hit) {
-                    sr[r][c] = 1;
-                    ++flips;
-                }
-                __syncwarp();
+            for (int b = 0; b < 9; ++b) {
+                const uint64_t row = (uint64_t)__ballot_sync(0xffffffffu, (m >> b) & 1u) << 1;
+                if (lane == r - 1) cand_b[b] = row;
+            }
+            const uint64_t trow = (uint64_t)__ballot_sync(0xffffffffu, (m >> 9) & 1u) << 1;
+            const uint64_t orow = (uint64_t)__ballot_sync(0xffffffffu, (m >> 31) & 1u) << 1;
+            if (lane == r - 1) {
+                term_b = trow;
+                open_b = orow;
             }
         }
+    }
+    // Reached nodes as one 34-bit row per lane (lane = row 1..32, the halo rows
+    // 0 and 33 kept apart): a node is reached when a terminal or a reached node
+    // is among its candidate corners.  Jacobi rounds over the bit sets reach the
+    // tile's least fixed point for the launch's halo, the one the step-by-step
+    // Gauss-Seidel passes approach; a round costs a few dozen instructions for
+    // all 1024 nodes of the tile.
+    auto row_bits = [&](int r) -> uint64_t {
+        const uint64_t lo = __ballot_sync(0xffffffffu, sr[r][lane] != 0);
+        return lo | ((uint64_t)(sr[r][32] != 0) << 32) | ((uint64_t)(sr[r][33] != 0) << 33);
+    };
+    uint64_t R = 0;
+    for (int r = 1; r <= kTile; ++r) {
+        const uint64_t v = row_bits(r);
+        if (lane == r - 1) R = v;
+    }
+    const uint64_t H0 = row_bits(0), H1 = row_bits(kTile + 1);
+    const uint64_t R0 = R;
+    for (int it = 0; it <= kTile * kTile; ++it) {
+        const uint64_t up = __shfl_up_sync(0xffffffffu, R, 1), dn = __shfl_down_sync(0xffffffffu, R, 1);
+        const uint64_t rows[3] = {lane == 0 ? H0 : up, R, lane == kTile - 1 ? H1 : dn};
+        uint64_t hit = term_b;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const uint64_t src = rows[b / 3];
+            const int dx = b % 3;
+            hit |= cand_b[b] & (dx == 0 ? src << 1 : (dx == 2 ? src >> 1 : src));
+        }
+        const uint64_t nr = R | (hit & open_b);
+        const bool moved = nr != R;
+        R = nr;
+        if (!__any_sync(0xffffffffu, moved)) break;
+    }
+    const int flips = __popcll(R) - __popcll(R0);
+    // back to bytes, row by row (coalesced stores)
     const int x = x0 + lane;
     for (int r = 1; r <= kTile; ++r) {
+        const uint64_t row = __shfl_sync(0xffffffffu, R, r - 1);
         const int y = y0 - 1 + r;
         if (y > g.n1 - 2) break;
         if (x > g.n0 - 2) continue;
-        rch[(int64_t)y * g.n0 + x] = sr[r][1 + lane];
+        rch[(int64_t)y * g.n0 + x] = (uint8_t)((row >> (lane + 1)) & 1ull);
     }
     const int nf = warp_sum(flips);
     if (lane == 0) {
