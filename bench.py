@@ -101,15 +101,17 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic():
+def profile_traffic(key: str = "traffic_bytes_per_launch"):
     """DRAM bytes per launch of the sweep kernel from the committed ncu
-    summary (line 'traffic_bytes_per_launch: <int>'), or None."""
+    summary (line '<key>: <number>'), or None.  traffic_bytes_per_launch: the
+    launches as the solve runs them (L2 as the previous launch left it);
+    traffic_cold_bytes_per_launch: the same launches after a cache flush."""
     path = os.path.join(ROOT, "profiles", "k_value2d_f32_traffic.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m = re.search(key + r":\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
 
 
@@ -466,8 +468,9 @@ def run_ours(args, rank, world, dist):
     alu_peak = sms * FP32_LANES_PER_SM * sm_max * 1e6            # lane-ops/s
     roofline = roofline_value(s0, p, alu_peak, sms, sm_max)
     # the committed capture is of the 2D sweep on the default workload only
-    roofline["traffic"] = profile_traffic() if (FAMILY == "sincos2d" and N_FINE == 2049 and args.bc == "state"
-                                                and not args.reduce_r) else None
+    default_2d = FAMILY == "sincos2d" and N_FINE == 2049 and args.bc == "state" and not args.reduce_r
+    roofline["traffic"] = profile_traffic() if default_2d else None
+    roofline["traffic_cold"] = profile_traffic("traffic_cold_bytes_per_launch") if default_2d else None
     roofline_phi = roofline_colour(s0, alu_peak, sms, sm_max) if p.dim == 2 and p.n_coarse else None
 
     if rank == 0:

@@ -324,6 +324,27 @@ template <typename T> __device__ __forceinline__ void load_w3(const W3<T> &w, T 
     }
 }
 
+// Packed FP32 pairs (PTX .f32x2, sm_100 and later): one instruction forms the
+// same rounded operation on both halves of a 64-bit register pair.
+__device__ __forceinline__ unsigned long long p2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void p2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long p2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long p2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // The update of node (lx, ly, lz); mask has bit 9 dz + 3 dy + dx set when the
 // neighbour (dx-1, dy-1, dz-1) belongs to the node's patch or target part
 // (formed once per launch), everything else reads +inf.  tab: the weights in
@@ -385,6 +406,66 @@ __device__ __forceinline__ T sl_update3(const Tile3<T, kDir> &sm, int lx, int ly
             T v0 = w0[7] * hh;
 #pragma unroll
             for (int b = 0; b < 7; ++b) v0 = fma(w0[b], c[b], v0);
+            b0 = v0 < b0 ? v0 : b0;
+        }
+    }
+    return b0 < b1 ? b0 : b1;
+}
+
+// The same minimum with the controls of an octant two at a time through the
+// packed pairs (FP32, no cones), every operation rounded as in sl_update3.
+// tab holds, per octant, each pair (m, m + 1) of controls in the slots m and
+// m + 1 with their weights interleaved, slot m = (w_m[0], w_m+1[0], w_m[1],
+// w_m+1[1]) (w_m[2], ..), slot m + 1 the same for w[4..7] (w[7] = kap), and
+// an octant's last control, when its count is odd, plainly as in sl_update3.
+template <bool kDir>
+__device__ __forceinline__ float sl_update3p(const Tile3<float, kDir> &sm, int lx, int ly, int lz, uint32_t mask,
+                                             float hh, const CtlTable3<float> &ct, const W3<float> *tab) {
+    float nb[3][3][3];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                float other;
+                if constexpr (kDir) other = sm.d[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx];   // Eq. (dbc)
+                else other = Num<float>::big();
+                nb[dz][dy][dx] = ((mask >> (9 * dz + 3 * dy + dx)) & 1u) ? sm.u[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx]
+                                                                        : other;
+            }
+    const unsigned long long h2 = p2_pack(hh, hh);
+    float b0 = Num<float>::big(), b1 = Num<float>::big();
+    const float4 *t4 = reinterpret_cast<const float4 *>(tab);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int sx = (o & 1) ? 2 : 0, sy = (o & 2) ? 2 : 0, sz = (o & 4) ? 2 : 0;
+        float c[7];
+#pragma unroll
+        for (int b = 1; b < 8; ++b) c[b - 1] = nb[(b & 4) ? sz : 1][(b & 2) ? sy : 1][(b & 1) ? sx : 1];
+        int m = ct.obeg[o];
+        const int me = ct.obeg[o + 1];
+        for (; m + 1 < me; m += 2) {
+            const float4 q0 = t4[2 * m], q1 = t4[2 * m + 1], q2 = t4[2 * m + 2], q3 = t4[2 * m + 3];
+            unsigned long long v = p2_mul(p2_pack(q3.z, q3.w), h2);
+            v = p2_fma(p2_pack(q0.x, q0.y), p2_pack(c[0], c[0]), v);
+            v = p2_fma(p2_pack(q0.z, q0.w), p2_pack(c[1], c[1]), v);
+            v = p2_fma(p2_pack(q1.x, q1.y), p2_pack(c[2], c[2]), v);
+            v = p2_fma(p2_pack(q1.z, q1.w), p2_pack(c[3], c[3]), v);
+            v = p2_fma(p2_pack(q2.x, q2.y), p2_pack(c[4], c[4]), v);
+            v = p2_fma(p2_pack(q2.z, q2.w), p2_pack(c[5], c[5]), v);
+            v = p2_fma(p2_pack(q3.x, q3.y), p2_pack(c[6], c[6]), v);
+            float v0, v1;
+            p2_unpack(v, v0, v1);
+            b0 = v0 < b0 ? v0 : b0;
+            b1 = v1 < b1 ? v1 : b1;
+        }
+        if (m < me) {
+            float w0[8];
+            load_w3(tab[m], w0);
+            float v0 = w0[7] * hh;
+#pragma unroll
+            for (int b = 0; b < 7; ++b) v0 = fmaf(w0[b], c[b], v0);
             b0 = v0 < b0 ? v0 : b0;
         }
     }
@@ -538,7 +619,9 @@ __device__ __forceinline__ T sl_update3g(const Tile3<T, kDir> &sm, int lx, int l
 // data dval (Eq. dbc); a node's own pruned nodes (code -2 - patch) read +inf.
 // kGen: per-node feet from the column tables of gen (h is then unused).
 // kCone: add-on AO3, the minimum over the node's cone (cone, astar).
-template <typename T, bool kDir = false, bool kGen = false, bool kCone = false>
+// kPk (FP32, no kGen or kCone): the packed-pair update of sl_update3p, the
+// same results as the scalar one.
+template <typename T, bool kDir = false, bool kGen = false, bool kCone = false, bool kPk = false>
 __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restrict__ code,
                                                   const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                   TileSched s, int par, int rounds, unsigned long long *updates,
@@ -546,6 +629,7 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                                                   const T *__restrict__ dval = nullptr, const Gen3 gen = Gen3{},
                                                   const Cone3 *__restrict__ cone = nullptr,
                                                   const uint8_t *__restrict__ astar = nullptr) {
+    static_assert(!kPk || (sizeof(T) == 4 && !kGen && !kCone), "packed pairs: FP32 control tables only");
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -556,7 +640,27 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     __shared__ T hs[kT3][kT3][kT3];
     __shared__ uint8_t as[kCone ? kT3 : 1][kCone ? kT3 : 1][kCone ? kT3 : 1];   // a* per node (AO3)
     __shared__ W3<T> tab[kGen ? 1 : kMaxControls];
-    if constexpr (!kGen)
+    if constexpr (kPk) {
+        // slot m: the first (or second) half of the pair (m, m + 1) (or (m - 1, m)),
+        // or the octant's odd last control alone
+        for (int m = threadIdx.x; m < ct.nc; m += blockDim.x) {
+            int o = 0;
+            while (ct.obeg[o + 1] <= m) ++o;
+            const int r = m - ct.obeg[o];
+            float *k = reinterpret_cast<float *>(tab[m].k);
+            if ((r & 1) == 0 && m + 1 == ct.obeg[o + 1]) {
+                for (int b = 0; b < 7; ++b) k[b] = ct.kw[b][m];
+                k[7] = ct.kap[m];
+            } else {
+                const int m0 = m - (r & 1), half = r & 1;
+                for (int q = 0; q < 4; ++q) {
+                    const int b = 4 * half + q;
+                    k[2 * q] = b < 7 ? ct.kw[b][m0] : ct.kap[m0];
+                    k[2 * q + 1] = b < 7 ? ct.kw[b][m0 + 1] : ct.kap[m0 + 1];
+                }
+            }
+        }
+    } else if constexpr (!kGen)
         for (int m = threadIdx.x; m < ct.nc; m += blockDim.x) {
             for (int b = 0; b < 7; ++b) tab[m].k[b] = ct.kw[b][m];
             tab[m].k[7] = ct.kap[m];
@@ -612,6 +716,8 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
                     else if constexpr (kCone)
                         best = sl_update3<T, kDir, true>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab,
                                                          cone->mask[as[lz - 1][ly - 1][lx - 1]]);
+                    else if constexpr (kPk)
+                        best = sl_update3p<kDir>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
                     else
                         best = sl_update3<T, kDir>(sm, lx, ly, lz, m, hs[lz - 1][ly - 1][lx - 1], ct, tab);
                     if (best < Num<T>::thresh()) nw = clamp ? (best < nw ? best : nw) : best;
@@ -706,16 +812,18 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
         sdf[lz][ly][lx] = df;
     }
     __syncthreads();
-    // once per launch (codes do not change): per interior node the corners
-    // that reach it (cand, 27-bit over the 3x3x3 neighbourhood), whether one
-    // of them is terminal, and which of them are in the patch
-    __shared__ uint32_t cand[kT3 * kT3 * kT3];
-    __shared__ uint8_t hit0[kT3 * kT3 * kT3];
-    for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
-        const int lx = 1 + e % kT3, ly = 1 + (e / kT3) % kT3, lz = 1 + e / (kT3 * kT3);
+    // Thread (ly, lz) owns the x-row of the tile at (ly, lz) as a 10-bit set
+    // (bit lx, the halo at 0 and 9).  Once per launch (codes do not change):
+    // per node the corners that reach it (27 offsets over the 3x3x3
+    // neighbourhood), whether one of them is terminal, whether the node is
+    // free and unreached, gathered into one row set per offset.
+    const int ly = 1 + tid % kT3, lz = 1 + tid / kT3;
+    uint32_t cand_b[27];
+#pragma unroll
+    for (int b = 0; b < 27; ++b) cand_b[b] = 0u;
+    uint32_t term_b = 0u, open_b = 0u;
+    for (int lx = 1; lx <= kT3; ++lx) {
         const int8_t cd = sc[lz][ly][lx];
-        uint32_t cs = 0;
-        uint8_t h0 = 0;
         if (cd >= 0 && cd < kTargetBase && !sr[lz][ly][lx]) {
             const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
             uint32_t same = 0, term = 0;
@@ -737,40 +845,52 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
                 cu = &cone->uni[a < cone->nc ? a : cone->nc][0][0];
             }
             const uint32_t c = usable_union3<kGen>(same | term, lx, ly, lz, x0, y0, g, rt, gen, cu);
-            h0 = (c & term) != 0;
-            cs = c & same;
-            if (!h0 && !cs) cs = 0;
-            cs |= 0x80000000u;   // the node is free and unreached
+            if (c & term) term_b |= 1u << lx;
+            const uint32_t cs = c & same;
+#pragma unroll
+            for (int b = 0; b < 27; ++b) cand_b[b] |= ((cs >> b) & 1u) << lx;
+            open_b |= 1u << lx;
         }
-        cand[e] = cs;
-        hit0[e] = h0;
+    }
+    // rows as bit sets, double-buffered: the halo rows (ly or lz 0 or 9) in both
+    __shared__ uint32_t rows[2][E][E];
+    for (int e = tid; e < E * E; e += blockDim.x) {
+        const int y = e % E, z = e / E;
+        uint32_t v = 0;
+#pragma unroll
+        for (int x = 0; x < E; ++x) v |= (uint32_t)(sr[z][y][x] != 0) << x;
+        rows[0][z][y] = v;
+        rows[1][z][y] = v;
     }
     __syncthreads();
-    int flips = 0;
-    for (int dir = 0; dir < 6; ++dir)
-        for (int st = 0; st < kT3; ++st) {
-            int lx, ly, lz;
-            plane_node(dir, st, tid, lx, ly, lz);
-            const int e = ((lz - 1) * kT3 + (ly - 1)) * kT3 + (lx - 1);
-            const uint32_t cs = cand[e];
-            bool hit = false;
-            if ((cs & 0x80000000u) && !sr[lz][ly][lx]) {
-                hit = hit0[e] != 0;
-                uint32_t rest = cs & 0x7ffffffu;
-                while (!hit && rest) {
-                    const int bit = __ffs(rest) - 1;
-                    rest &= rest - 1u;
-                    const int dz = bit / 9, dy = (bit / 3) % 3, dx = bit % 3;
-                    hit = sr[lz - 1 + dz][ly - 1 + dy][lx - 1 + dx] != 0;
-                }
+    uint32_t R = rows[0][lz][ly];
+    const uint32_t R0 = R;
+    // Jacobi rounds to the tile's least fixed point for the launch's halo (the
+    // one the plane-by-plane Gauss-Seidel passes approach), one barrier each
+    int cur = 0;
+    for (int it = 0; it <= kT3 * kT3 * kT3; ++it) {
+        uint32_t hit = term_b;
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+                const uint32_t src = (dz == 1 && dy == 1) ? R : rows[cur][lz - 1 + dz][ly - 1 + dy];
+                const int b = 9 * dz + 3 * dy;
+                hit |= cand_b[b] & (src << 1);
+                hit |= cand_b[b + 1] & src;
+                hit |= cand_b[b + 2] & (src >> 1);
             }
-            __syncthreads();
-            if (hit) {
-                sr[lz][ly][lx] = 1;
-                ++flips;
-            }
-            __syncthreads();
-        }
+        const uint32_t nr = R | (hit & open_b);
+        const int moved = nr != R;
+        R = nr;
+        rows[cur ^ 1][lz][ly] = R;
+        if (!__syncthreads_or(moved)) break;
+        cur ^= 1;
+    }
+    const int flips = __popc(R) - __popc(R0);
+#pragma unroll
+    for (int lx = 1; lx <= kT3; ++lx) sr[lz][ly][lx] = (uint8_t)((R >> lx) & 1u);
+    __syncthreads();
     for (int e = tid; e < kT3 * kT3 * kT3; e += blockDim.x) {
         const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
@@ -1984,6 +2104,8 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
     ++p.stats.kernel_launches;
     const CtlTable3<T> ct = make_table3<T>(p);
     const bool timed = (p.desc.flags & HJBP_FLAG_TIME_SWEEPS) != 0;
+    // FP32: controls two at a time as packed pairs (same results); tune[6] = 2: one at a time
+    const bool packed = std::is_same<T, float>::value && p.desc.tune[6] != 2;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
     Run3 rr = run_tiles3(p, g, s, tol, cap, [&](int par) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -2006,9 +2128,15 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
         else if (gen)
             k_value3d<T, false, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
                                                                         ct, clamp, nullptr, *gen);
+        else if (dval && packed)
+            k_value3d<T, true, false, false, std::is_same<T, float>::value><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
         else if (dval)
             k_value3d<T, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
                                                                  clamp, dval);
+        else if (packed)
+            k_value3d<T, false, false, false, std::is_same<T, float>::value><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, nullptr);
         else
             k_value3d<T, false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
                                                                   clamp, nullptr);

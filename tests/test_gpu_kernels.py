@@ -86,3 +86,18 @@ def test_packed_pair_update_equals_scalar(pkg, case):
     assert s0 == 0 and s2 == 0
     assert np.array_equal(l0, l2)
     assert np.array_equal(u0, u2)
+
+
+@pytest.mark.parametrize("family", ["sin3d", "eikonal3d_dirichlet"])
+def test_packed_pair_update_3d_equals_scalar(pkg, family):
+    """3D: two controls of an octant per packed FP32x2 chain (the default)
+    against one at a time (tune[6] = 2), equal to the last bit."""
+    if family == "sin3d":
+        p, flags = W.sin3d(0, n=41, n_coarse=11, n_targets=4, radius=0.12), 0
+    else:
+        p, flags = W.eikonal3d(n=41, n_coarse=11, n_c=50), pkg.HJBP_FLAG_DIRICHLET
+    s0, u0, l0 = _solve(pkg, p, 1, None, flags)
+    s2, u2, l2 = _solve(pkg, p, 1, None, flags, tune6=2)
+    assert s0 == 0 and s2 == 0
+    assert np.array_equal(l0, l2)
+    assert np.array_equal(u0, u2)
