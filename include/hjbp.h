@@ -138,16 +138,23 @@ typedef struct {
     int max_sweeps;
     int flags;          /* HJBP_FLAG_* bits */
     int tune[8];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
-                           launch of the value sweep (2), [1] of the colour transport (2),
-                           [2] passes per launch of the 3D reachability sweep (1; the 2D one runs bit-set rounds to the tile's fixed point), [3] warps
+                           launch of the value sweep (2D: 4, 2 with tune[7] = 1; 3D: 1),
+                           [1] of the colour transport (2D: 4, 2 with tune[7] = 1; 3D: 2),
+                           [2] passes per launch of the 3D reachability sweep (1; the 2D
+                           one runs bit-set rounds to the tile's fixed point), [3] warps
                            per 32x32 tile of the 2D value sweep (1; 1, 2 or 4), [4] resident
                            warps per SM of the tile-queue sweep (occupancy limit), [5] the
                            fine-grid launches run the increasing or (alternately) the
                            decreasing pass of every axis: 3D default (0; 2 runs all six
-                           passes), 2D only with 1 (measured slower there), [6] 2D kernel
-                           variants: 0 default, 1 the per-control FP64 polish instead of the
-                           pair-form one, 2 the scalar FP32 update instead of the packed
-                           FP32x2 one (same results), [7] reserved (0) */
+                           passes), 2D only with 1 (measured slower there), [6] kernel
+                           variants: 0 default, 1 the per-control FP64 polish (2D) instead
+                           of the pair-form one, 2 the scalar FP32 update instead of the
+                           packed FP32x2 one (2D and 3D; same results), [7] the 2D FP32
+                           monotone value sweep publishes its tile boundary and re-reads
+                           its halo inside a launch: 0 after every pass (default), 2 after
+                           every round, 1 never (block-Jacobi launches, results the same
+                           to the last bit from run to run; with exchange the iterates
+                           depend on timing and the fixed point does not) */
     double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
                            minimum of Step 3.2 at node i to the controls a with
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse

@@ -95,7 +95,7 @@ extern "C" hjbp_status hjbp_autotune(const hjbp_problem_desc *desc, void *cuda_s
     }
     // candidates: value rounds x colour-transport rounds (one warp per tile,
     // one reach pass: the measured alternatives were slower everywhere)
-    std::vector<int> vr = desc->dim == 2 ? std::vector<int>{1, 2, 3} : std::vector<int>{1, 2};
+    std::vector<int> vr = desc->dim == 2 ? std::vector<int>{2, 3, 4} : std::vector<int>{1, 2};
     std::vector<int> pr = desc->n_coarse[0] == 0 ? std::vector<int>{0}
                                                  : (desc->dim == 2 ? std::vector<int>{2, 3, 4} : std::vector<int>{1, 2, 3});
     std::vector<int> best_t;

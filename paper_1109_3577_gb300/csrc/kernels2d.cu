@@ -499,13 +499,14 @@ __device__ __forceinline__ unsigned nbr_parities(const Grid2 &g, const TileSched
 // node's own patch includes its target part and its own pruned nodes (code
 // -2 - patch, value +inf).
 // kCone: the minimum runs over each node's AO3 cone (astar, cone).
-template <typename T, int NCLS, bool kDir, bool kCone = false>
+template <typename T, int NCLS, bool kDir, bool kCone = false, bool kX = false>
 __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restrict__ code,
                                                 const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                 TileSched s, int par, int rounds, unsigned long long *updates,
                                                 const CtlTable2<T> ct, int clamp, const T *__restrict__ dval,
                                                 const uint8_t *__restrict__ astar = nullptr,
-                                                const Cone2 *__restrict__ cone = nullptr, int packed = 0) {
+                                                const Cone2 *__restrict__ cone = nullptr, int packed = 0,
+                                                int xpass = 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -552,7 +553,14 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
                     const int py = (r == 0) ? 0 : (r == kH - 1 ? 2 : 1);
                     const bool inner = x >= 1 && x <= g.n0 - 2 && y >= 1 && y <= g.n1 - 2;
                     const bool odd = inner && ((pm >> (3 * py + px)) & 1u);
-                    v = odd ? b1[i] : b0[i];
+                    if constexpr (kX) {
+                        // the newer of the two buffers (values only decrease): a
+                        // neighbour's boundary may already hold this launch's rounds
+                        const T v0 = __ldcg(b0 + i), v1 = __ldcg(b1 + i);
+                        v = v0 < v1 ? v0 : v1;
+                    } else {
+                        v = odd ? b1[i] : b0[i];
+                    }
                     if constexpr (kDir) dv = dval[i];
                 }
                 sm.u[r][c] = v;
@@ -603,9 +611,58 @@ __global__ void __launch_bounds__(32) k_value2d(Grid2 g, const int8_t *__restric
     const bool uniform = !kDir && !kCone && __popcll(all_ids) <= 1;
     // AO2: the tile's sweep directions; or alternating halves (TileSched.alt)
     const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0xAu : 0x5u) : 0xFu);
+    auto exchange = [&]() {
+        // Halo exchange inside the launch (monotone update only): publish this
+        // tile's boundary lines into the buffer the launch writes, then read
+        // the halo again as the newer of the two buffers.  A neighbour that
+        // has published its round shows it here, one that has not shows its
+        // older value; both are values that node held, so the iteration keeps
+        // decreasing to the same fixed point (R8), and a change can cross a tile
+        // boundary at every exchange instead of once per launch.
+        T *dsx = ((pm >> 4) & 1u) ? b0 : b1;
+        const int xl = x0 + lane, yl = y0 + lane;
+        if (xl <= g.n0 - 2) {
+            if (y0 <= g.n1 - 2) dsx[(int64_t)y0 * g.n0 + xl] = sm.u[1][1 + lane];
+            const int yb = min(y0 + kTile - 1, g.n1 - 2);
+            if (yb >= y0) dsx[(int64_t)yb * g.n0 + xl] = sm.u[1 + yb - y0][1 + lane];
+        }
+        if (yl <= g.n1 - 2) {
+            if (x0 <= g.n0 - 2) dsx[(int64_t)yl * g.n0 + x0] = sm.u[1 + lane][1];
+            const int xb = min(x0 + kTile - 1, g.n0 - 2);
+            if (xb >= x0) dsx[(int64_t)yl * g.n0 + xb] = sm.u[1 + lane][1 + xb - x0];
+        }
+        // the 132 halo cells: rows 0 and 33 (34 each), columns 0 and 33 (32 each)
+        constexpr int kH = kTile + 2;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int q = lane + 32 * k;
+            if (q < 4 * kH - 4) {
+                int r, c;
+                if (q < kH) { r = 0; c = q; }
+                else if (q < 2 * kH) { r = kH - 1; c = q - kH; }
+                else if (q < 3 * kH - 2) { r = q - 2 * kH + 1; c = 0; }
+                else { r = q - (3 * kH - 2) + 1; c = kH - 1; }
+                const int x = x0 - 1 + c, y = y0 - 1 + r;
+                if (x >= 1 && x <= g.n0 - 2 && y >= 1 && y <= g.n1 - 2) {
+                    const int64_t i = (int64_t)y * g.n0 + x;
+                    const T v0 = __ldcg(b0 + i), v1 = __ldcg(b1 + i);
+                    const T v = v0 < v1 ? v0 : v1;
+                    if (v < sm.u[r][c]) sm.u[r][c] = v;
+                }
+            }
+        }
+        __syncwarp();
+    };
+    const int npass = __popc(tdirs);
+    int pass = 0;
     for (int rd = 0; rd < rounds; ++rd) {
         for (int dir = 0; dir < 4; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
+            if constexpr (kX) {
+                // between rounds (xpass = 0) or between passes (xpass = 1)
+                if (pass > 0 && (xpass || pass % npass == 0)) exchange();
+            }
+            ++pass;
             for (int st = 0; st < kTile; ++st) {
                 const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
                 const int c = (dir < 2) ? s1 : 1 + lane;
@@ -1707,8 +1764,14 @@ template <int RG, bool kSource> struct PhiSmem {
 //   correction (kSource = true):  d_i   <- kap (w10 d10 + w01 d01 + w11 d11 + r_i)
 // The bulk rises monotonically from 0; the tile's change is the max over
 // its colours.
-template <int RG, bool kSource>
-__global__ void __launch_bounds__(32 * (RG < 4 ? RG : 4)) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
+//
+// kX (bulk only: its values only rise): after every pass a colour's warp
+// publishes the tile's boundary lines of its colour into the buffer the launch
+// writes and re-reads its halo as the larger of the two buffers, so a
+// neighbour's progress inside the launch reaches the tile (same fixed point,
+// R8).
+template <int RG, bool kSource, bool kX = false>
+__global__ void __launch_bounds__(32 * (RG < 4 ? RG : 4), kX ? 7 : 8) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
                                               const uint8_t *__restrict__ astar, float *__restrict__ b0,
                                               float *__restrict__ b1, const float *__restrict__ src, TileSched s,
                                               int par, int rounds, const PhiCtl *__restrict__ pc,
@@ -1764,7 +1827,9 @@ __global__ void __launch_bounds__(32 * (RG < 4 ? RG : 4)) k_phi2d(Grid2 g, const
                     const float *bs = odd ? b1 : b0;
 #pragma unroll
                     for (int q = 0; q < RG; ++q) {
-                        const float v = bs[(int64_t)q * N + i];
+                        float v;
+                        if constexpr (kX) v = fmaxf(__ldcg(b0 + (int64_t)q * N + i), __ldcg(b1 + (int64_t)q * N + i));
+                        else v = bs[(int64_t)q * N + i];
                         sm.u[q][r][c] = v;
                         alive |= (unsigned)(v != 0.0f) << q;
                     }
@@ -1811,36 +1876,103 @@ __global__ void __launch_bounds__(32 * (RG < 4 ? RG : 4)) k_phi2d(Grid2 g, const
             atomicAdd(updates, (unsigned long long)na * (unsigned long long)__popc(alive) *
                                    (unsigned long long)__popc(tdirs) * (unsigned long long)rounds);
     }
-    // the passes of this warp's colours, one colour after the other
+    // the passes of this warp's colours, one colour after the other.  What a
+    // step needs besides the colour values (the node's code, a*, its weights
+    // and the source) does not change inside the launch, so it is read one
+    // step ahead and only the corner values stay on the step's dependent path.
+    struct Rec {
+        float k10, k01, k11, kp, sv;
+        int sx, sy;
+        bool active;
+    };
     for (int q = w; q < RG; q += W) {
         if (!((alive >> q) & 1u)) continue;
         float(*u)[kTile + 3] = sm.u[q];
+        auto node_at = [&](int dir, int st, int &r, int &c) {
+            const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
+            c = (dir < 2) ? s1 : 1 + lane;
+            r = (dir < 2) ? 1 + lane : s1;
+        };
+        auto record = [&](int r, int c) {
+            Rec e;
+            const int8_t cd = sm.c[r][c];
+            const uint8_t a = sm.a[r - 1][c - 1];
+            e.active = cd >= 0 && cd < kTargetBase && a != kNoControl;
+            const int ai = e.active ? a : 0;
+            e.sx = sm.sx[ai];
+            e.sy = sm.sy[ai];
+            e.k10 = sm.kw10[ai];
+            e.k01 = sm.kw01[ai];
+            e.k11 = sm.kw11[ai];
+            e.kp = kSource ? sm.kap[ai] : 0.0f;
+            e.sv = kSource ? sm.src[kSource ? q : 0][r - 1][c - 1] : 0.0f;
+            return e;
+        };
+        int pass = 0;
         for (int rd = 0; rd < rounds; ++rd) {
             for (int dir = 0; dir < 4; ++dir) {
                 if (!((tdirs >> dir) & 1u)) continue;
+                if constexpr (kX && !kSource) {
+                    if (pass > 0) {
+                        float *dq = (((pm >> 4) & 1u) ? b0 : b1) + (int64_t)q * N;
+                        const int xl = x0 + lane, yl = y0 + lane;
+                        if (xl <= g.n0 - 2) {
+                            if (y0 <= g.n1 - 2) dq[(int64_t)y0 * g.n0 + xl] = u[1][1 + lane];
+                            const int yb = min(y0 + kTile - 1, g.n1 - 2);
+                            if (yb >= y0) dq[(int64_t)yb * g.n0 + xl] = u[1 + yb - y0][1 + lane];
+                        }
+                        if (yl <= g.n1 - 2) {
+                            if (x0 <= g.n0 - 2) dq[(int64_t)yl * g.n0 + x0] = u[1 + lane][1];
+                            const int xb = min(x0 + kTile - 1, g.n0 - 2);
+                            if (xb >= x0) dq[(int64_t)yl * g.n0 + xb] = u[1 + lane][1 + xb - x0];
+                        }
+                        constexpr int kH = kTile + 2;
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            const int qq = lane + 32 * k;
+                            if (qq < 4 * kH - 4) {
+                                int hr, hc;
+                                if (qq < kH) { hr = 0; hc = qq; }
+                                else if (qq < 2 * kH) { hr = kH - 1; hc = qq - kH; }
+                                else if (qq < 3 * kH - 2) { hr = qq - 2 * kH + 1; hc = 0; }
+                                else { hr = qq - (3 * kH - 2) + 1; hc = kH - 1; }
+                                const int x = x0 - 1 + hc, y = y0 - 1 + hr;
+                                if (x >= 1 && x <= g.n0 - 2 && y >= 1 && y <= g.n1 - 2) {
+                                    const int64_t i = (int64_t)q * N + (int64_t)y * g.n0 + x;
+                                    const float v = fmaxf(__ldcg(b0 + i), __ldcg(b1 + i));
+                                    if (v > u[hr][hc]) u[hr][hc] = v;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                ++pass;
+                int r, c;
+                node_at(dir, 0, r, c);
+                Rec e = record(r, c);
                 for (int st = 0; st < kTile; ++st) {
-                    const int s1 = 1 + ((dir & 1) ? (kTile - 1 - st) : st);
-                    const int c = (dir < 2) ? s1 : 1 + lane;
-                    const int r = (dir < 2) ? 1 + lane : s1;
-                    const int8_t cd = sm.c[r][c];
-                    const uint8_t a = sm.a[r - 1][c - 1];
-                    const bool active = cd >= 0 && cd < kTargetBase && a != kNoControl;
+                    int rn, cn;
+                    node_at(dir, st + 1 < kTile ? st + 1 : st, rn, cn);
+                    const Rec en = record(rn, cn);
                     float nw = 0.0f;
-                    if (active) {
-                        const int sx = sm.sx[a], sy = sm.sy[a];
-                        float v = sm.kw10[a] * u[r][c + sx];
-                        v = fmaf(sm.kw01[a], u[r + sy][c], v);
-                        v = fmaf(sm.kw11[a], u[r + sy][c + sx], v);
+                    if (e.active) {
+                        float v = e.k10 * u[r][c + e.sx];
+                        v = fmaf(e.k01, u[r + e.sy][c], v);
+                        v = fmaf(e.k11, u[r + e.sy][c + e.sx], v);
                         if (kSource) {
-                            nw = fmaf(sm.kap[a], sm.src[q][r - 1][c - 1], v);
+                            nw = fmaf(e.kp, e.sv, v);
                         } else {
                             const float o = u[r][c];
                             nw = v > o ? v : o;
                         }
                     }
                     __syncwarp();
-                    if (active) u[r][c] = nw;
+                    if (e.active) u[r][c] = nw;
                     __syncwarp();
+                    e = en;
+                    r = rn;
+                    c = cn;
                 }
             }
         }
@@ -2827,6 +2959,12 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
     // the packed FP32-pair update (sl_update_x2, same result to the last bit);
     // tune[6] = 2: the scalar form
     const int packed = p.desc.tune[6] == 2 ? 0 : 1;
+    // FP32 monotone sweeps without cones exchange their halos inside the
+    // launch, after every pass (tune[7] = 0) or every round (2); tune[7] = 1
+    // keeps the deterministic block-Jacobi launches
+    const int xmode = p.desc.tune[7];
+    const bool xchg = std::is_same<T, float>::value && clamp && !cone && xmode != 1 && !(warps == 2 || warps == 4);
+    const int xpass = xmode == 2 ? 0 : 1;
     LaunchTimer timer(p, timed);
     RunResult rr = run_tiles(p, g, s, tol, cap, [&](int par, int) {
         timer.begin();
@@ -2851,6 +2989,18 @@ RunResult value2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const T *h, 
             launch_mw<T, 8, 4>(s.ntiles, p.stream, g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
         else if (mw)
             launch_mw<T, 0, 4>(s.ntiles, p.stream, g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
+        else if (xchg && dval && ct.d4 && ct.ncls == 8)
+            k_value2d<T, 8, true, false, true><<<s.ntiles, 32, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval, nullptr, nullptr, 0, xpass);
+        else if (xchg && dval)
+            k_value2d<T, 0, true, false, true><<<s.ntiles, 32, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval, nullptr, nullptr, 0, xpass);
+        else if (xchg && ct.d4 && ct.ncls == 8)
+            k_value2d<T, 8, false, false, true><<<s.ntiles, 32, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, nullptr, nullptr, nullptr, packed, xpass);
+        else if (xchg)
+            k_value2d<T, 0, false, false, true><<<s.ntiles, 32, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, nullptr, nullptr, nullptr, 0, xpass);
         else if (dval && ct.d4 && ct.ncls == 8)
             k_value2d<T, 8, true><<<s.ntiles, 32, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates, ct,
                                                                  clamp, dval);
@@ -3020,8 +3170,10 @@ hjbp_status solve2d(hjbp_plan &p) {
     const int hist = std::max(std::min(cap, 1 << 20), kReachCap);
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
     const int R = p.R;
-    const int vrounds = d.tune[0] > 0 ? d.tune[0] : 2;
-    const int prounds = d.tune[1] > 0 ? d.tune[1] : 2;
+    // rounds per launch: 4 while the halos are exchanged after every pass (a
+    // launch then carries a change across several tiles), 2 for block-Jacobi
+    const int vrounds = d.tune[0] > 0 ? d.tune[0] : (d.tune[7] == 1 ? 2 : 4);
+    const int prounds = d.tune[1] > 0 ? d.tune[1] : (d.tune[7] == 1 ? 2 : 4);
     hjbp_stats &S = p.stats;
     std::memset(&S, 0, sizeof(S));
     hjbp_status status = HJBP_OK;
@@ -3110,6 +3262,8 @@ hjbp_status solve2d(hjbp_plan &p) {
             check_cuda(cudaMemcpyAsync(dpc, &hpc, sizeof(PhiCtl), cudaMemcpyHostToDevice, st), "phi ctl");
             // colours per transport pass: up to 8 (one front propagation per group)
             const int RG = R > 4 ? 8 : (R >= 3 ? 4 : (R == 2 ? 2 : 1));
+            // the bulk exchanges halos inside a launch unless tune[7] = 1
+            const bool phi_x = d.tune[7] != 1;
             float *f0 = alloc_n<float>(p, N * RG), *f1 = alloc_n<float>(p, N * RG), *r32 = alloc_n<float>(p, N * RG);
             double *phig = alloc_n<double>(p, N * RG);
             float *rmax = alloc_n<float>(p, 1);
@@ -3126,6 +3280,9 @@ hjbp_status solve2d(hjbp_plan &p) {
                     constexpr int G = decltype(tag)::value;
                     check_cuda(cudaFuncSetAttribute(k_phi2d<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)sizeof(PhiSmem<G, false>)), "phi smem");
+                    check_cuda(cudaFuncSetAttribute(k_phi2d<G, false, true>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)sizeof(PhiSmem<G, false>)), "phi smem");
                     check_cuda(cudaFuncSetAttribute(k_phi2d<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)sizeof(PhiSmem<G, true>)), "phi smem");
                     // FP32 bulk solve
@@ -3133,8 +3290,13 @@ hjbp_status solve2d(hjbp_plan &p) {
                     ++p.stats.kernel_launches;
                     RunResult rp = run_tiles(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par, int) {
                         ptimer.begin();
-                        k_phi2d<G, false><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, false>), st>>>(
-                            g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc, pupd);
+                        if (phi_x)
+                            k_phi2d<G, false, true><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, false>),
+                                                      st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds,
+                                                            dpc, pupd);
+                        else
+                            k_phi2d<G, false><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, false>), st>>>(
+                                g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc, pupd);
                         ptimer.end();
                         ++p.stats.kernel_launches;
                     });
@@ -3188,17 +3350,28 @@ hjbp_status solve2d(hjbp_plan &p) {
             ++p.stats.kernel_launches;
             int8_t *lab2 = reinterpret_cast<int8_t *>(rch);  // scratch (reach flags are reset before use)
             unsigned long long *chg = alloc_n<unsigned long long>(p, 1);
-            for (int it = 0; it < 100000; ++it) {
+            // Jacobi rounds of Remark 3.1's fill, ping-ponged between the two label
+            // buffers, in batches between host checks (4, 8, .. 64 rounds): a round
+            // after the last change changes nothing, so the batches give the rounds'
+            // result exactly
+            int8_t *la = p.label_out, *lb = lab2;
+            int batch = 4;
+            for (int it = 0; it < 100000;) {
                 check_cuda(cudaMemsetAsync(chg, 0, sizeof(unsigned long long), st), "memset");
-                k_fill2d<<<grid_for(N), 256, 0, st>>>(g, p.label_out, lab2, chg);
-                ++p.stats.kernel_launches;
-                check_cuda(cudaMemcpyAsync(p.label_out, lab2, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
+                for (int k = 0; k < batch; ++k, ++it) {
+                    k_fill2d<<<grid_for(N), 256, 0, st>>>(g, la, lb, chg);
+                    ++p.stats.kernel_launches;
+                    std::swap(la, lb);
+                }
                 unsigned long long hc = 0;
                 check_cuda(cudaMemcpyAsync(&hc, chg, sizeof(hc), cudaMemcpyDeviceToHost, st), "fill count");
                 check_cuda(cudaStreamSynchronize(st), "fill sync");
                 S.uncovered_filled += (int64_t)hc;
                 if (!hc) break;
+                batch = std::min(2 * batch, 64);
             }
+            if (la != p.label_out)
+                check_cuda(cudaMemcpyAsync(p.label_out, la, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
             k_patch_codes<<<grid_for(N), 256, 0, st>>>(N, code0, p.label_out, code);
             ++p.stats.kernel_launches;
         }

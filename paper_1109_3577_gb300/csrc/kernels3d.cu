@@ -2447,17 +2447,28 @@ hjbp_status solve3d(hjbp_plan &p) {
             ++S.kernel_launches;
             int8_t *lab2 = reinterpret_cast<int8_t *>(rch);
             unsigned long long *chg = alloc3<unsigned long long>(p, 1);
-            for (int it = 0; it < 100000; ++it) {
+            // Jacobi rounds of Remark 3.1's fill, ping-ponged between the two label
+            // buffers, in batches between host checks (4, 8, .. 64 rounds): a round
+            // after the last change changes nothing, so the batches give the rounds'
+            // result exactly
+            int8_t *la = p.label_out, *lb = lab2;
+            int batch = 4;
+            for (int it = 0; it < 100000;) {
                 check_cuda(cudaMemsetAsync(chg, 0, sizeof(unsigned long long), st), "memset");
-                k_fill3d<<<grid_for3(N), 256, 0, st>>>(g, p.label_out, lab2, chg);
-                ++S.kernel_launches;
-                check_cuda(cudaMemcpyAsync(p.label_out, lab2, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
+                for (int k = 0; k < batch; ++k, ++it) {
+                    k_fill3d<<<grid_for3(N), 256, 0, st>>>(g, la, lb, chg);
+                    ++S.kernel_launches;
+                    std::swap(la, lb);
+                }
                 unsigned long long hc = 0;
                 check_cuda(cudaMemcpyAsync(&hc, chg, sizeof(hc), cudaMemcpyDeviceToHost, st), "fill count");
                 check_cuda(cudaStreamSynchronize(st), "fill sync");
                 S.uncovered_filled += (int64_t)hc;
                 if (!hc) break;
+                batch = std::min(2 * batch, 64);
             }
+            if (la != p.label_out)
+                check_cuda(cudaMemcpyAsync(p.label_out, la, (size_t)N, cudaMemcpyDeviceToDevice, st), "fill copy");
             k_patch_codes<<<grid_for3(N), 256, 0, st>>>(N, code0, p.label_out, code);
             ++S.kernel_launches;
         }

@@ -5,7 +5,9 @@ the one-warp sweep, in every mode the multi-warp kernel serves (FP32 and
 FP64, the symmetric pair form and the generic control table, state
 constraints and Dirichlet data, the monotone and the plain update), and the
 pair-form FP64 polish against the per-control polish within the tolerance
-of the polish itself."""
+of the polish itself.  These comparisons run the deterministic block-Jacobi
+launches (tune[7] = 1); the FP32 sweeps that exchange halos inside a launch
+(the default) are checked against them for the same fixed point."""
 import numpy as np
 import pytest
 
@@ -28,9 +30,9 @@ def pkg():
     return P
 
 
-def _solve(pkg, p, warps, precision=None, flags=0, tune6=0):
+def _solve(pkg, p, warps, precision=None, flags=0, tune6=0, tune7=1):
     prec = pkg.HJBP_FP32_POLISH64 if precision is None else precision
-    with pkg.Plan(p, precision=prec, flags=flags, tune=[0, 0, 0, warps, 0, 0, tune6, 0]) as plan:
+    with pkg.Plan(p, precision=prec, flags=flags, tune=[0, 0, 0, warps, 0, 0, tune6, tune7]) as plan:
         st = plan.solve()
         return st, plan.values(), plan.labels()
 
@@ -101,3 +103,26 @@ def test_packed_pair_update_3d_equals_scalar(pkg, family):
     assert s0 == 0 and s2 == 0
     assert np.array_equal(l0, l2)
     assert np.array_equal(u0, u2)
+
+
+@pytest.mark.parametrize("case", ["patchy_fp32_pairs", "dirichlet", "obstacles"])
+@pytest.mark.parametrize("tune7", [0, 2])
+def test_halo_exchange_reaches_the_same_fixed_point(pkg, case, tune7):
+    """The FP32 sweep that publishes its boundary and re-reads its halo
+    inside a launch (after every pass: tune[7] = 0, the default; after every
+    round: 2) reads a neighbour's older or newer value, both upper bounds of
+    the fixed point, so the monotone iteration ends at the same fixed point
+    (R8) as the block-Jacobi launches: within the stopping tolerance, and
+    within the parity bound of the FP64 oracle."""
+    make, prec, mode = CASES[case]
+    p = make()
+    flags = {"dirichlet": pkg.HJBP_FLAG_DIRICHLET, "warm": pkg.HJBP_FLAG_WARM_START}.get(mode, 0)
+    s1, u1, l1 = _solve(pkg, p, 1, None, flags, tune7=1)
+    sx, ux, lx = _solve(pkg, p, 1, None, flags, tune7=tune7)
+    assert s1 == 0 and sx == 0
+    assert np.array_equal(l1, lx)
+    fin = np.isfinite(u1)
+    assert np.array_equal(fin, np.isfinite(ux))
+    assert np.abs(ux[fin] - u1[fin]).max() <= 2e-5 * u1[fin].max()
+    ref = oracle.patchy_solve(p, tol=1e-12, dirichlet=mode == "dirichlet")
+    assert np.abs(ux[fin] - ref.u[fin]).max() <= 1e-4 * ref.u[fin].max()

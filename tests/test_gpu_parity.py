@@ -154,15 +154,27 @@ def test_patchy_fp64_mode(pkg):
 
 
 def test_repeat_solve_same_plan(pkg):
-    """A plan solved twice gives identical results (deterministic block-Jacobi
-    across tiles)."""
+    """A plan solved twice gives identical results with the deterministic
+    block-Jacobi launches (tune[7] = 1); with the default halo exchange inside
+    a launch the FP32 iterates depend on timing, and two solves agree within
+    the stopping tolerance (the labels, decided before the sweeps, exactly)."""
     p = _patchy_case(1, 129, 33, R=4, radius=0.2)
-    with pkg.Plan(p) as plan:
+    with pkg.Plan(p, tune=[0, 0, 0, 0, 0, 0, 0, 1]) as plan:
         plan.solve()
         u1, l1 = plan.values(), plan.labels()
         plan.solve()
         u2, l2 = plan.values(), plan.labels()
     assert np.array_equal(u1, u2) and np.array_equal(l1, l2)
+    with pkg.Plan(p) as plan:
+        plan.solve()
+        u3, l3 = plan.values(), plan.labels()
+        plan.solve()
+        u4, l4 = plan.values(), plan.labels()
+    assert np.array_equal(l3, l4) and np.array_equal(l1, l3)
+    fin = np.isfinite(u1)
+    assert np.array_equal(fin, np.isfinite(u3)) and np.array_equal(fin, np.isfinite(u4))
+    assert np.abs(u3[fin] - u4[fin]).max() <= 2e-5 * u1[fin].max()
+    assert np.abs(u3[fin] - u1[fin]).max() <= 2e-5 * u1[fin].max()
 
 
 def test_torch_allocator_and_stream(pkg):

@@ -1,6 +1,7 @@
 """Batched and served solves on the GPU: every result equals the same
-problem solved alone (the kernels are deterministic, so the mix cannot change
-a result), within the parity tolerance of the other tests."""
+problem solved alone, within the parity tolerance of the other tests (the
+labels exactly; the FP32 sweeps exchange halos inside a launch, so their
+iterates, not their fixed point, depend on timing)."""
 import time
 
 import numpy as np
