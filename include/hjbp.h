@@ -149,12 +149,14 @@ typedef struct {
                            passes), 2D only with 1 (measured slower there), [6] kernel
                            variants: 0 default, 1 the per-control FP64 polish (2D) instead
                            of the pair-form one, 2 the scalar FP32 update instead of the
-                           packed FP32x2 one (2D and 3D; same results), [7] the 2D FP32
-                           monotone value sweep publishes its tile boundary and re-reads
-                           its halo inside a launch: 0 after every pass (default), 2 after
-                           every round, 1 never (block-Jacobi launches, results the same
-                           to the last bit from run to run; with exchange the iterates
-                           depend on timing and the fixed point does not) */
+                           packed FP32x2 one (2D and 3D; same results), [7] the FP32
+                           monotone sweeps (value sweeps in 2D and 3D, the 2D colour-
+                           transport bulk) publish their tile boundary and re-read their
+                           halo inside a launch: 0 after every pass (default), 2 after
+                           every round (2D value sweep), 1 never (block-Jacobi launches,
+                           results the same to the last bit from run to run; with the
+                           exchange the iterates depend on timing, the fixed point does
+                           not) */
     double reduce_r;    /* add-on AO3 (Sec. 6), patchy solves only: r > 1 restricts the
                            minimum of Step 3.2 at node i to the controls a with
                            a . a*_{k~}(x_i) >= cos(pi / r) - 1e-12 (a*_{k~}: the coarse

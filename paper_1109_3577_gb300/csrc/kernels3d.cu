@@ -290,6 +290,38 @@ __device__ __forceinline__ double store_tile3(const Grid3 &g, const TileSched &s
     return (double)block_max64(mc, sm.redt);
 }
 
+// Halo exchange inside a launch of the monotone value sweep: the tile's
+// boundary nodes go to the buffer the launch writes, then the 488 halo cells
+// are read again as the newer (smaller) of the two buffers.  A neighbour that
+// has published shows its progress inside this launch, one that has not its
+// older value; either is a value that node held, an upper bound of the fixed
+// point, so the decreasing iteration keeps its fixed point (R8).  Ends with a
+// block barrier.
+template <typename T, bool kDir>
+__device__ __forceinline__ void exchange3(const Grid3 &g, const TileSched &s, int t, T *b0, T *b1, int x0, int y0,
+                                          int z0, Tile3<T, kDir> &sm) {
+    T *dst = s.latest[t] ? b0 : b1;
+    for (int e = threadIdx.x; e < kT3 * kT3 * kT3; e += blockDim.x) {
+        const int lx = e % kT3, ly = (e / kT3) % kT3, lz = e / (kT3 * kT3);
+        const bool edge = lx == 0 || lx == kT3 - 1 || ly == 0 || ly == kT3 - 1 || lz == 0 || lz == kT3 - 1;
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (!edge || x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        dst[((int64_t)z * g.n1 + y) * g.n0 + x] = sm.u[lz + 1][ly + 1][lx + 1];
+    }
+    constexpr int E = kT3 + 2;
+    for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
+        const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
+        const bool halo = lx == 0 || lx == E - 1 || ly == 0 || ly == E - 1 || lz == 0 || lz == E - 1;
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        if (!halo || x < 1 || y < 1 || z < 1 || x > g.n0 - 2 || y > g.n1 - 2 || z > g.n2 - 2) continue;
+        const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
+        const T v0 = __ldcg(b0 + i), v1 = __ldcg(b1 + i);
+        const T v = v0 < v1 ? v0 : v1;
+        if (v < sm.u[lz][ly][lx]) sm.u[lz][ly][lx] = v;
+    }
+    __syncthreads();
+}
+
 // Local coordinates (1..8) of the node thread `tid` updates at step `st` of
 // pass `dir` (0/1: +-x, 2/3: +-y, 4/5: +-z).
 __device__ __forceinline__ void plane_node(int dir, int st, int tid, int &lx, int &ly, int &lz) {
@@ -621,7 +653,8 @@ __device__ __forceinline__ T sl_update3g(const Tile3<T, kDir> &sm, int lx, int l
 // kCone: add-on AO3, the minimum over the node's cone (cone, astar).
 // kPk (FP32, no kGen or kCone): the packed-pair update of sl_update3p, the
 // same results as the scalar one.
-template <typename T, bool kDir = false, bool kGen = false, bool kCone = false, bool kPk = false>
+// kX: exchange the halo after every pass (exchange3; monotone update only).
+template <typename T, bool kDir = false, bool kGen = false, bool kCone = false, bool kPk = false, bool kX = false>
 __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restrict__ code,
                                                   const T *__restrict__ h, T *__restrict__ b0, T *__restrict__ b1,
                                                   TileSched s, int par, int rounds, unsigned long long *updates,
@@ -699,9 +732,14 @@ __global__ void __launch_bounds__(kT3n) k_value3d(Grid3 g, const int8_t *__restr
     __syncthreads();
     // AO2: the tile's sweep directions; or alternating halves
     const unsigned tdirs = s.dirs ? s.dirs[t] : (s.alt ? (par ? 0x2Au : 0x15u) : 0x3Fu);
+    int pass = 0;
     for (int rd = 0; rd < rounds; ++rd)
         for (int dir = 0; dir < 6; ++dir) {
             if (!((tdirs >> dir) & 1u)) continue;
+            if constexpr (kX) {
+                if (pass > 0) exchange3(g, s, t, b0, b1, x0, y0, z0, sm);
+            }
+            ++pass;
             for (int st = 0; st < kT3; ++st) {
                 int lx, ly, lz;
                 plane_node(dir, st, tid, lx, ly, lz);
@@ -2106,6 +2144,9 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
     const bool timed = (p.desc.flags & HJBP_FLAG_TIME_SWEEPS) != 0;
     // FP32: controls two at a time as packed pairs (same results); tune[6] = 2: one at a time
     const bool packed = std::is_same<T, float>::value && p.desc.tune[6] != 2;
+    // FP32 monotone sweeps exchange their halos after every pass (tune[7] = 1: block-Jacobi)
+    const bool xchg = std::is_same<T, float>::value && clamp && p.desc.tune[7] != 1;
+    constexpr bool kF = std::is_same<T, float>::value;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
     Run3 rr = run_tiles3(p, g, s, tol, cap, [&](int par) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -2128,6 +2169,18 @@ Run3 value3(hjbp_plan &p, const Grid3 &g, const int8_t *code, const T *h, T *b0,
         else if (gen)
             k_value3d<T, false, true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, h, b0, b1, s.d, par, rounds, updates,
                                                                         ct, clamp, nullptr, *gen);
+        else if (dval && packed && xchg)
+            k_value3d<T, true, false, false, kF, kF><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
+        else if (packed && xchg)
+            k_value3d<T, false, false, false, kF, kF><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, nullptr);
+        else if (dval && xchg)
+            k_value3d<T, true, false, false, false, kF><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
+        else if (xchg)
+            k_value3d<T, false, false, false, false, kF><<<s.ntiles, kT3n, 0, p.stream>>>(
+                g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, nullptr);
         else if (dval && packed)
             k_value3d<T, true, false, false, std::is_same<T, float>::value><<<s.ntiles, kT3n, 0, p.stream>>>(
                 g, code, h, b0, b1, s.d, par, rounds, updates, ct, clamp, dval);
