@@ -565,7 +565,8 @@ def batched_measure(P, count: int = 512, workers: int = 8, tune: bool = True):
            "speedup": seq / bat, "batched_s": bat, "one_at_a_time_s": seq, "workers": workers,
            "total_nodes": nodes, "node_control_updates_per_s_batched": ncu_bat / bat,
            "node_control_updates_per_s_one_at_a_time": ncu_seq / seq, "data": "synthetic", "dtype": "f32",
-           "accuracy": "same plans, same kernels: each result equals its solve alone (tests/test_gpu_serving.py)",
+           "accuracy": "same plans, same kernels: each result equals its solve alone within the parity tolerance, "
+                       "the labels exactly (tests/test_gpu_serving.py)",
            "autotuned": {"classes": classes, "seconds": t_tune} if tune else None}
     for pl in plans:
         pl.close()

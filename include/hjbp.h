@@ -138,7 +138,8 @@ typedef struct {
     int max_sweeps;
     int flags;          /* HJBP_FLAG_* bits */
     int tune[8];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
-                           launch of the value sweep (2D: 4, 2 with tune[7] = 1; 3D: 1),
+                           launch of the value sweep (2D: 4 where the halos are exchanged
+                           (see [7]), else 2; 3D: 1),
                            [1] of the colour transport (2D: 4, 2 with tune[7] = 1; 3D: 2),
                            [2] passes per launch of the 3D reachability sweep (1; the 2D
                            one runs bit-set rounds to the tile's fixed point), [3] warps

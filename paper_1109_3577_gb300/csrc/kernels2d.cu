@@ -3170,9 +3170,12 @@ hjbp_status solve2d(hjbp_plan &p) {
     const int hist = std::max(std::min(cap, 1 << 20), kReachCap);
     const bool fp32 = d.precision == HJBP_FP32_POLISH64;
     const int R = p.R;
-    // rounds per launch: 4 while the halos are exchanged after every pass (a
-    // launch then carries a change across several tiles), 2 for block-Jacobi
-    const int vrounds = d.tune[0] > 0 ? d.tune[0] : (d.tune[7] == 1 ? 2 : 4);
+    // rounds per launch: 4 where the halos are exchanged after every pass (a
+    // launch then carries a change across several tiles: the FP32 monotone
+    // value sweep and the colour bulk), 2 for block-Jacobi launches
+    const bool vx = fp32 && d.tune[7] != 1 && !(d.flags & (HJBP_FLAG_WARM_START | HJBP_FLAG_TILE_QUEUE)) &&
+                    d.reduce_r == 0.0 && d.tune[3] != 2 && d.tune[3] != 4;
+    const int vrounds = d.tune[0] > 0 ? d.tune[0] : (vx ? 4 : 2);
     const int prounds = d.tune[1] > 0 ? d.tune[1] : (d.tune[7] == 1 ? 2 : 4);
     hjbp_stats &S = p.stats;
     std::memset(&S, 0, sizeof(S));
