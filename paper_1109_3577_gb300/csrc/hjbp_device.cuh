@@ -241,6 +241,81 @@ __device__ inline double speed_at(const SpeedParams &sp, double x0, double x1, d
     }
 }
 
+// Separable speeds (HJBP_C_SINCOS2D, HJBP_C_SIN3D, HJBP_C_FOURIER2D) are
+// products of one factor per axis, so the set-up evaluates the trigonometric
+// factors once per grid line (speed_factor, nt per line) and a node only
+// multiplies them (speed_lines): the same FP64 operations on the same
+// arguments as speed_at, without an FP64 sin or cos per node.
+struct SpeedLines {
+    const double *f[3];   // per axis: nt factors per grid line, line-major; NULL: evaluate per node
+    int nt;
+};
+
+__host__ __device__ inline int speed_terms(int kind) {
+    return kind == HJBP_C_SINCOS2D || kind == HJBP_C_SIN3D ? 1 : (kind == HJBP_C_FOURIER2D ? 16 : 0);
+}
+
+// Factor m of axis `axis` at the coordinate x (speed_terms(kind) > 0).
+__device__ inline double speed_factor(const SpeedParams &sp, int axis, int m, double x) {
+    const double pi = 3.14159265358979323846;
+    switch (sp.kind) {
+    case HJBP_C_SINCOS2D:
+        return axis == 0 ? sin(2.0 * pi * x) : cos(2.0 * pi * x);
+    case HJBP_C_SIN3D:
+        return sin(pi * x);
+    default: {   // HJBP_C_FOURIER2D: cos(pi a x0 / 2 + theta_ab) cos(pi b x1 / 2 + psi_ab), m = 4 a + b
+        const int a = m / 4, b = m % 4;
+        return axis == 0 ? cos(pi * a * x / 2.0 + sp.p[16 + m]) : cos(pi * b * x / 2.0 + sp.p[32 + m]);
+    }
+    }
+}
+
+// c at the node (i0, i1, i2) from its lines' factors.
+__device__ inline double speed_lines(const SpeedParams &sp, const SpeedLines &L, int i0, int i1, int i2) {
+    switch (sp.kind) {
+    case HJBP_C_SINCOS2D:
+        return 1.0 + sp.p[0] * L.f[0][i0] * L.f[1][i1];
+    case HJBP_C_SIN3D:
+        return 1.0 + sp.p[0] * L.f[0][i0] * L.f[1][i1] * L.f[2][i2];
+    default: {   // HJBP_C_FOURIER2D
+        double g = 0.0, norm = 0.0;
+        for (int m = 0; m < 16; ++m) {
+            g += sp.p[m] * L.f[0][16 * i0 + m] * L.f[1][16 * i1 + m];
+            norm += fabs(sp.p[m]);
+        }
+        return 1.0 + 0.5 * g / norm;
+    }
+    }
+}
+
+// Factors of every grid line: thread e takes line e / nt of the axis whose
+// range holds it, term e % nt; x = lo + i k rounded as the set-up rounds it.
+static __global__ void k_speed_lines(SpeedParams sp, int nt, int n0, int n1, int n2, double lo0, double lo1,
+                                     double lo2, double k, double *f0, double *f1, double *f2) {
+    const int total = nt * (n0 + n1 + n2);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int line = e / nt;
+        const int m = e % nt;
+        int axis = 0;
+        double lo = lo0;
+        double *out = f0;
+        if (line >= n0) {
+            line -= n0;
+            axis = 1;
+            lo = lo1;
+            out = f1;
+            if (line >= n1) {
+                line -= n1;
+                axis = 2;
+                lo = lo2;
+                out = f2;
+            }
+        }
+        const double x = __dadd_rn(lo, __dmul_rn((double)line, k));
+        out[(int64_t)line * nt + m] = speed_factor(sp, axis, m, x);
+    }
+}
+
 // Dynamics of the set-up (hjbp_dyn_kind): for HJBP_DYN_DRIFT, f = s a + w.
 struct DynParams {
     int kind;

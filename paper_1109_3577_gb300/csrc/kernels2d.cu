@@ -40,7 +40,7 @@ namespace hjbp {
 // membership is decided exactly as x = lo + i k, r^2 = sum (x - c)^2 dictate.
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
                           int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
-                          double *__restrict__ fixed, DynParams dp, ObstacleSet os) {
+                          double *__restrict__ fixed, DynParams dp, ObstacleSet os, SpeedLines sl) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
@@ -49,7 +49,7 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
         double gap = 0.0, e[2];
         const int part = target_part2(ts, g, x0, x1, extra, &gap, e);
         const bool ring = ix == 0 || iy == 0 || ix == g.n0 - 1 || iy == g.n1 - 1;
-        const double c = speed_at(sp, x0, x1, 0.0);
+        const double c = sl.f[0] ? speed_lines(sp, sl, ix, iy, 0) : speed_at(sp, x0, x1, 0.0);
         const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
         const bool blocked = part < 0 && in_obstacle(os, x0, x1, 0.0);
         const double hh = stopped ? (double)INFINITY : __ddiv_rn(g.k, c);
@@ -3158,6 +3158,21 @@ RunResult value_wide2d(hjbp_plan &p, const Grid2 &g, const int8_t *code, const d
 
 }  // namespace
 
+// The per-line factors of a separable speed on grid g (SpeedLines), in the
+// plan's arena; no factors (per-node evaluation) for the other speeds.
+SpeedLines speed_lines2(hjbp_plan &p, const Grid2 &g, const SpeedParams &sp) {
+    SpeedLines sl{{nullptr, nullptr, nullptr}, speed_terms(sp.kind)};
+    if (sl.nt == 0) return sl;
+    double *f0 = alloc_n<double>(p, (int64_t)g.n0 * sl.nt), *f1 = alloc_n<double>(p, (int64_t)g.n1 * sl.nt);
+    const int total = sl.nt * (g.n0 + g.n1);
+    k_speed_lines<<<(total + 255) / 256, 256, 0, p.stream>>>(sp, sl.nt, g.n0, g.n1, 0, g.lo0, g.lo1, 0.0, g.k, f0, f1,
+                                                           nullptr);
+    ++p.stats.kernel_launches;
+    sl.f[0] = f0;
+    sl.f[1] = f1;
+    return sl;
+}
+
 hjbp_status solve2d(hjbp_plan &p) {
     const hjbp_problem_desc &d = p.desc;
     cudaStream_t st = p.stream;
@@ -3189,7 +3204,8 @@ hjbp_status solve2d(hjbp_plan &p) {
     float *h32 = fp32 ? alloc_n<float>(p, N) : nullptr;
     unsigned long long *updates = alloc_n<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
-    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr, make_dyn(p), os);
+    k_setup2d<<<grid_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr, make_dyn(p), os,
+                                           speed_lines2(p, g, sp));
     ++p.stats.kernel_launches;
     check_cuda(cudaGetLastError(), "setup");
     Sched sched = make_sched(p, g, hist);
@@ -3207,7 +3223,7 @@ hjbp_status solve2d(hjbp_plan &p) {
         double *cfix = alloc_n<double>(p, Nc);
         double *cb0 = alloc_n<double>(p, Nc), *cb1 = alloc_n<double>(p, Nc);
         k_setup2d<<<grid_for(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(2.0) / 2.0, 1, ccode, nullptr, ch64,
-                                                cfix, make_dyn(p), os);
+                                                cfix, make_dyn(p), os, speed_lines2(p, gc, sp));
         ++p.stats.kernel_launches;
         k_merge_targets<<<grid_for(Nc), 256, 0, st>>>(Nc, ccode);
         ++p.stats.kernel_launches;

@@ -132,7 +132,8 @@ template <typename V> __device__ __forceinline__ V block_max64(V v, V *scratch) 
 // |f(x, a)| over the controls instead of c(x).
 __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values,
                           int8_t *__restrict__ code, float *__restrict__ h32, double *__restrict__ h64,
-                          double *__restrict__ fixed, ObstacleSet os, const GenCtl *__restrict__ gctl = nullptr) {
+                          double *__restrict__ fixed, ObstacleSet os, SpeedLines sl,
+                          const GenCtl *__restrict__ gctl = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % g.n0);
@@ -144,7 +145,7 @@ __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, i
         double dist = 0.0;
         const int part = target_part3(ts, g.lo1, g.n1, g.k, x0, x1, x2, extra, &dist);
         const bool ring = ix == 0 || iy == 0 || iz == 0 || ix == g.n0 - 1 || iy == g.n1 - 1 || iz == g.n2 - 1;
-        const double c = speed_at(sp, x0, x1, x2);
+        const double c = sl.f[0] ? speed_lines(sp, sl, ix, iy, iz) : speed_at(sp, x0, x1, x2);
         const bool stopped = !(c > kStoppedSpeed);   // cannot move: like the ghost ring
         const bool blocked = part < 0 && in_obstacle(os, x0, x1, x2);   // obstacle (Sec. 4)
         const double hh = stopped ? (double)INFINITY : __ddiv_rn(g.k, c);
@@ -1402,7 +1403,10 @@ __global__ void __launch_bounds__(kT3n * phi3_groups<RG>()) k_phi3d(Grid3 g, con
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
     const int x0 = 1 + (t % g.ntx) * kT3, y0 = 1 + ((t / g.ntx) % g.nty) * kT3, z0 = 1 + (t / (g.ntx * g.nty)) * kT3;
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
-    __shared__ Phi3Smem<RG, kSource> sm;
+    // dynamic shared memory: eight colours with their source exceed the 48 KB
+    // of static shared memory
+    extern __shared__ __align__(16) unsigned char phi3_smem_raw[];
+    Phi3Smem<RG, kSource> &sm = *reinterpret_cast<Phi3Smem<RG, kSource> *>(phi3_smem_raw);
     __shared__ unsigned salive;   // colours nonzero somewhere in the tile image or its source
     constexpr int E = kT3 + 2;
     const int tid = threadIdx.x;
@@ -2319,6 +2323,23 @@ Run3 coarse3(hjbp_plan &p, const Grid3 &gc, const int8_t *code, const float *h32
 
 }  // namespace
 
+// The per-line factors of a separable speed on grid g (SpeedLines), in the
+// plan's arena; no factors (per-node evaluation) for the other speeds.
+SpeedLines speed_lines3(hjbp_plan &p, const Grid3 &g, const SpeedParams &sp) {
+    SpeedLines sl{{nullptr, nullptr, nullptr}, speed_terms(sp.kind)};
+    if (sl.nt == 0) return sl;
+    double *f0 = alloc3<double>(p, (int64_t)g.n0 * sl.nt), *f1 = alloc3<double>(p, (int64_t)g.n1 * sl.nt);
+    double *f2 = alloc3<double>(p, (int64_t)g.n2 * sl.nt);
+    const int total = sl.nt * (g.n0 + g.n1 + g.n2);
+    k_speed_lines<<<(total + 255) / 256, 256, 0, p.stream>>>(sp, sl.nt, g.n0, g.n1, g.n2, g.lo0, g.lo1, g.lo2, g.k, f0,
+                                                           f1, f2);
+    ++p.stats.kernel_launches;
+    sl.f[0] = f0;
+    sl.f[1] = f1;
+    sl.f[2] = f2;
+    return sl;
+}
+
 hjbp_status solve3d(hjbp_plan &p) {
     const hjbp_problem_desc &d = p.desc;
     cudaStream_t st = p.stream;
@@ -2372,7 +2393,7 @@ hjbp_status solve3d(hjbp_plan &p) {
     unsigned long long *updates = alloc3<unsigned long long>(p, 1);
     check_cuda(cudaMemsetAsync(updates, 0, sizeof(unsigned long long), st), "memset");
     k_setup3d<<<grid_for3(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, h32, h64, nullptr,
-                                            make_obstacles(3, d.n_obstacles, d.obstacles));
+                                            make_obstacles(3, d.n_obstacles, d.obstacles), speed_lines3(p, g, sp));
     ++S.kernel_launches;
     check_cuda(cudaGetLastError(), "setup3");
     Sched3 sched = make_sched3(p, g, hist);
@@ -2391,7 +2412,8 @@ hjbp_status solve3d(hjbp_plan &p) {
         double *cfix = alloc3<double>(p, Nc);
         float *ch32 = alloc3<float>(p, Nc);
         k_setup3d<<<grid_for3(Nc), 256, 0, st>>>(gc, sp, ts, p.kc * std::sqrt(3.0) / 2.0, 1, ccode, ch32, ch64,
-                                                 cfix, make_obstacles(3, d.n_obstacles, d.obstacles), dgc);
+                                                 cfix, make_obstacles(3, d.n_obstacles, d.obstacles),
+                                                 speed_lines3(p, gc, sp), dgc);
         k_merge_targets<<<grid_for3(Nc), 256, 0, st>>>(Nc, ccode);
         S.kernel_launches += 2;
         Gen3 gcoarse{};
@@ -2434,25 +2456,39 @@ hjbp_status solve3d(hjbp_plan &p) {
         }
         Ev3 e3(st);
         {
-            const int RG = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+            // colours per transport pass: up to 8 on grids of at most 4096 tiles (one
+            // front propagation for all colours; measured faster at 101^3), 4 on larger
+            // grids, where the launches fill the GPU and a CTA of 8 colours (46 KB of
+            // shared memory) halves the resident CTAs (257^3: labels 90 -> 100 ms)
+            const int RG = (R > 4 && sched.ntiles <= 4096) ? 8 : (R >= 3 ? 4 : (R == 2 ? 2 : 1));
             float *f0 = alloc3<float>(p, N * RG), *f1 = alloc3<float>(p, N * RG), *r32 = alloc3<float>(p, N * RG);
             double *phig = alloc3<double>(p, N * RG);
             float *rmax = alloc3<float>(p, 1);
             const double tolp = d.tol_phi > 0 ? d.tol_phi : 1e-10;
             for (int j0 = 0; j0 < R; j0 += RG) {
                 const int rg = std::min(RG, R - j0);
-                const int rgl = rg >= 4 ? 4 : (rg == 3 ? 4 : rg);
+                // colours past R in the last group see no target and stay 0
+                const int rgl = rg > 4 ? 8 : (rg >= 3 ? 4 : rg);
                 auto launch_group = [&](auto tag) {
                     constexpr int G = decltype(tag)::value;
+                    constexpr size_t kSb = sizeof(Phi3Smem<G, false>), kSs = sizeof(Phi3Smem<G, true>);
+                    check_cuda(cudaFuncSetAttribute(k_phi3d<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)kSb), "phi smem");
+                    check_cuda(cudaFuncSetAttribute(k_phi3d<G, false, true>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSb), "phi smem");
+                    check_cuda(cudaFuncSetAttribute(k_phi3d<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)kSs), "phi smem");
+                    check_cuda(cudaFuncSetAttribute(k_phi3d<G, true, true>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSs), "phi smem");
                     k_phi_init3d<G><<<grid_for3(N), 256, 0, st>>>(N, code0, j0, 0, f0, f1);
                     ++S.kernel_launches;
                     Run3 rp = run_tiles3(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par) {
                         if (per_node)
-                            k_phi3d<G, false, true><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(
+                            k_phi3d<G, false, true><<<sched.ntiles, kT3n * phi3_groups<G>(), kSb, st>>>(
                                 g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dct, gfine);
                         else
-                            k_phi3d<G, false><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(g, code0, p.astar, f0, f1, nullptr,
-                                                                             sched.d, par, prounds, dct);
+                            k_phi3d<G, false><<<sched.ntiles, kT3n * phi3_groups<G>(), kSb, st>>>(
+                                g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dct);
                         ++S.kernel_launches;
                     });
                     S.sweeps_phi += rp.launches;
@@ -2478,11 +2514,11 @@ hjbp_status solve3d(hjbp_plan &p) {
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         Run3 rc2 = run_tiles3(p, g, sched, told, cap, [&](int par) {
                             if (per_node)
-                                k_phi3d<G, true, true><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(
+                                k_phi3d<G, true, true><<<sched.ntiles, kT3n * phi3_groups<G>(), kSs, st>>>(
                                     g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dct, gfine);
                             else
-                                k_phi3d<G, true><<<sched.ntiles, kT3n * phi3_groups<G>(), 0, st>>>(g, code0, p.astar, f0, f1, r32,
-                                                                                sched.d, par, prounds, dct);
+                                k_phi3d<G, true><<<sched.ntiles, kT3n * phi3_groups<G>(), kSs, st>>>(
+                                    g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dct);
                             ++S.kernel_launches;
                         });
                         S.sweeps_phi += rc2.launches;
@@ -2492,7 +2528,8 @@ hjbp_status solve3d(hjbp_plan &p) {
                     check_cuda(cudaMemcpyAsync(p.phi + (int64_t)j0 * N, phig, sizeof(double) * N * rg,
                                                cudaMemcpyDeviceToDevice, st), "phi copy");
                 };
-                if (rgl == 4) launch_group(std::integral_constant<int, 4>());
+                if (rgl == 8) launch_group(std::integral_constant<int, 8>());
+                else if (rgl == 4) launch_group(std::integral_constant<int, 4>());
                 else if (rgl == 2) launch_group(std::integral_constant<int, 2>());
                 else launch_group(std::integral_constant<int, 1>());
             }

@@ -36,7 +36,7 @@ namespace hjbp {
 
 // Kernels defined in kernels2d.cu (the same ones hjbp_solve launches).
 __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, int boundary_values, int8_t *code,
-                          float *h32, double *h64, double *fixed, DynParams dp, ObstacleSet os);
+                          float *h32, double *h64, double *fixed, DynParams dp, ObstacleSet os, SpeedLines sl);
 __global__ void k_schedule2d(Grid2 g, TileSched s, int par, double tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
                                                 ReachTable2 rt, int passes, const double *dterm,
@@ -315,7 +315,8 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
     DynParams dp;
     std::memset(&dp, 0, sizeof(dp));   // f = c(x) a
     k_setup2d<<<blocks_for(N), 256, 0, st>>>(g, sp, ts, 0.0, 0, code0, nullptr, h64, nullptr, dp,
-                                             make_obstacles(2, desc->n_obstacles, desc->obstacles));
+                                             make_obstacles(2, desc->n_obstacles, desc->obstacles),
+                                             SpeedLines{{nullptr, nullptr, nullptr}, 0});   // c per node
     NA_CHECK(cudaGetLastError());
     NA_CHECK(cudaMemcpyAsync(code, code0, (size_t)N, cudaMemcpyDeviceToDevice, st));
     k_merge_targets<<<blocks_for(N), 256, 0, st>>>(N, code);

@@ -104,7 +104,7 @@ def test_autotune_picks_a_shape_and_caches_it(P, tmp_path):
     d, keep = P.desc_from_problem(p, flags=P.HJBP_FLAG_DIRICHLET)
     path = str(tmp_path / "tune.txt")
     t, cached = P.hjbp_autotune(d, 0, path)
-    assert not cached and t[0] in (1, 2, 3) and t[1] in (2, 3, 4)
+    assert not cached and t[0] in (2, 3, 4) and t[1] in (2, 3, 4)
     t2, cached2 = P.hjbp_autotune(d, 0, path)
     assert cached2 and t2 == t
     fields = open(path).read().split()
