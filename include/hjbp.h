@@ -140,7 +140,8 @@ typedef struct {
     int tune[8];        /* launch shape, 0 = default: [0] Gauss-Seidel rounds per tile
                            launch of the value sweep (2D: 4 where the halos are exchanged
                            (see [7]), else 2; 3D: 1),
-                           [1] of the colour transport (2D: 4, 2 with tune[7] = 1; 3D: 2),
+                           [1] of the colour transport (2D: 4 where the halos are
+                           exchanged, else 2; 3D: 2),
                            [2] passes per launch of the 3D reachability sweep (1; the 2D
                            one runs bit-set rounds to the tile's fixed point), [3] warps
                            per 32x32 tile of the 2D value sweep (1; 1, 2 or 4), [4] resident
@@ -152,7 +153,8 @@ typedef struct {
                            of the pair-form one, 2 the scalar FP32 update instead of the
                            packed FP32x2 one (2D and 3D; same results), [7] the FP32
                            monotone sweeps (value sweeps in 2D and 3D, the 2D colour-
-                           transport bulk) publish their tile boundary and re-read their
+                           transport bulk of up to four colours) publish their tile boundary
+                           and re-read their
                            halo inside a launch: 0 after every pass (default), 2 after
                            every round (2D value sweep), 1 never (block-Jacobi launches,
                            results the same to the last bit from run to run; with the

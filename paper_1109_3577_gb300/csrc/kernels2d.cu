@@ -1245,10 +1245,14 @@ __global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T
 // Dirichlet data (dterm != NULL, Eq. dbc) every node outside the patch whose
 // data is finite.  With AO3 cones (cone != NULL) a node uses only the controls
 // of its cone.  In place; monotone, so the order does not matter.
+// cache, cvalid (optional): the tile's row sets below depend on the codes
+// only, which do not change during one reach run, so the first launch that
+// visits a tile stores them (11 x 32 words per tile) and later ones load them.
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restrict__ code,
                                                 uint8_t *__restrict__ rch, TileSched s, int par,
                                                 ReachTable2 rt, int passes, const double *__restrict__ dterm,
-                                                const uint8_t *__restrict__ astar, const Cone2 *__restrict__ cone) {
+                                                const uint8_t *__restrict__ astar, const Cone2 *__restrict__ cone,
+                                                uint64_t *__restrict__ cache, uint8_t *__restrict__ cvalid) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -1257,6 +1261,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     __shared__ int8_t sc[kTile + 2][kTile + 4];
     __shared__ uint8_t sd[kTile + 2][kTile + 4];
     const int lane = threadIdx.x;
+    const bool cached = cache && cvalid[t];
     for (int r = 0; r < kTile + 2; ++r) {
         const int y = y0 - 1 + r;
         for (int c = lane; c < kTile + 2; c += 32) {
@@ -1265,9 +1270,11 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
             int8_t cd = kHard;
             if (x < g.n0 && y < g.n1) {
                 const int64_t i = (int64_t)y * g.n0 + x;
-                cd = code[i];
                 v = rch[i];
-                if (dterm) df = dterm[i] < kU0Bound;
+                if (!cached) {
+                    cd = code[i];
+                    if (dterm) df = dterm[i] < kU0Bound;
+                }
             }
             sr[r][c] = v;
             sc[r][c] = cd;
@@ -1276,10 +1283,16 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
     }
     __syncwarp();
     // per interior node: bits 0..8 candidate corners in the patch (3 dy + dx),
-    // bit 9 a candidate is terminal, bit 31 node free and unreached; pres: the
-    // corner patterns of the node's controls per quadrant
+    // bit 9 a candidate is terminal, bit 31 node free; pres: the corner
+    // patterns of the node's controls per quadrant
     uint64_t cand_b[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, term_b = 0, open_b = 0;
-    {
+    uint64_t *cl = cache ? cache + (int64_t)t * 11 * 32 : nullptr;
+    if (cached) {
+#pragma unroll
+        for (int b = 0; b < 9; ++b) cand_b[b] = cl[b * 32 + lane];
+        term_b = cl[9 * 32 + lane];
+        open_b = cl[10 * 32 + lane];
+    } else {
         const int c = 1 + lane;
         const uint32_t all = (uint32_t)rt.present[0] | ((uint32_t)rt.present[1] << 8) |
                              ((uint32_t)rt.present[2] << 16) | ((uint32_t)rt.present[3] << 24);
@@ -1293,7 +1306,7 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                 pw = cone->reach[a < cone->nc ? a : cone->nc];
             }
             uint32_t m = 0;
-            if (cd >= 0 && cd < kTargetBase && !sr[r][c]) {
+            if (cd >= 0 && cd < kTargetBase) {
                 const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
                 uint32_t same = 0, term = 0;
 #pragma unroll
@@ -1340,6 +1353,13 @@ __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *__restric
                 term_b = trow;
                 open_b = orow;
             }
+        }
+        if (cl) {
+#pragma unroll
+            for (int b = 0; b < 9; ++b) cl[b * 32 + lane] = cand_b[b];
+            cl[9 * 32 + lane] = term_b;
+            cl[10 * 32 + lane] = open_b;
+            if (lane == 0) cvalid[t] = 1;   // read by later launches only
         }
     }
     // Reached nodes as one 34-bit row per lane (lane = row 1..32, the halo rows
@@ -1770,16 +1790,19 @@ template <int RG, bool kSource> struct PhiSmem {
 // writes and re-reads its halo as the larger of the two buffers, so a
 // neighbour's progress inside the launch reaches the tile (same fixed point,
 // R8).
+// Warps per tile of the colour transport: one per colour.
+template <int RG> constexpr int phi_warps() { return RG; }
+
 template <int RG, bool kSource, bool kX = false>
-__global__ void __launch_bounds__(32 * (RG < 4 ? RG : 4), kX ? 7 : 8) k_phi2d(Grid2 g, const int8_t *__restrict__ code,
+__global__ void __launch_bounds__(32 * phi_warps<RG>(), RG == 8 ? 4 : (kX ? 7 : 8))
+    k_phi2d(Grid2 g, const int8_t *__restrict__ code,
                                               const uint8_t *__restrict__ astar, float *__restrict__ b0,
                                               float *__restrict__ b1, const float *__restrict__ src, TileSched s,
                                               int par, int rounds, const PhiCtl *__restrict__ pc,
                                               unsigned long long *updates = nullptr) {
-    // one warp per colour (up to four; with eight colours each warp takes two):
-    // the colours are independent linear systems, so the warps never wait on
-    // one another inside a pass
-    constexpr int W = RG < 4 ? RG : 4;
+    // one warp per colour: the colours are independent linear systems, so the
+    // warps never wait on one another inside a pass
+    constexpr int W = phi_warps<RG>();
     constexpr int NT = 32 * W;
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
@@ -2900,6 +2923,9 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
     const int passes = p.desc.tune[2] > 0 ? p.desc.tune[2] : 1;
     const ReachTable2 rt = make_reach(p);
     unsigned long long *removed = alloc_n<unsigned long long>(p, 1);
+    // per tile the candidate, terminal and free row sets of k_reach2d (11 x 32 words)
+    uint64_t *rcache = alloc_n<uint64_t>(p, (int64_t)std::max(1, s.ntiles) * 11 * 32);
+    uint8_t *rvalid = alloc_n<uint8_t>(p, std::max(1, s.ntiles));
     int total = 0;
     // each round prunes at least one node or ends the loop, so it ends after at
     // most N rounds
@@ -2913,8 +2939,11 @@ int reach2d(hjbp_plan &p, const Grid2 &g, int8_t *code, uint8_t *rch, Sched &s, 
         total += pe.launches;
         if (!pe.converged) throw HjbpError{HJBP_ECUDA, "peeling did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
+        // the codes changed (peel, prune): the tiles' cached row sets are stale
+        check_cuda(cudaMemsetAsync(rvalid, 0, (size_t)std::max(1, s.ntiles), p.stream), "reach cache reset");
         RunResult rr = run_tiles(p, g, s, 0.5f, cap, [&](int par, int) {
-            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt, passes, dterm, p.astar, cone);
+            k_reach2d<<<s.ntiles, 32, 0, p.stream>>>(g, code, rch, s.d, par, rt, passes, dterm, p.astar, cone,
+                                                     rcache, rvalid);
             ++p.stats.kernel_launches;
         });
         total += rr.launches;
@@ -3191,7 +3220,6 @@ hjbp_status solve2d(hjbp_plan &p) {
     const bool vx = fp32 && d.tune[7] != 1 && !(d.flags & (HJBP_FLAG_WARM_START | HJBP_FLAG_TILE_QUEUE)) &&
                     d.reduce_r == 0.0 && d.tune[3] != 2 && d.tune[3] != 4;
     const int vrounds = d.tune[0] > 0 ? d.tune[0] : (vx ? 4 : 2);
-    const int prounds = d.tune[1] > 0 ? d.tune[1] : (d.tune[7] == 1 ? 2 : 4);
     hjbp_stats &S = p.stats;
     std::memset(&S, 0, sizeof(S));
     hjbp_status status = HJBP_OK;
@@ -3281,8 +3309,13 @@ hjbp_status solve2d(hjbp_plan &p) {
             check_cuda(cudaMemcpyAsync(dpc, &hpc, sizeof(PhiCtl), cudaMemcpyHostToDevice, st), "phi ctl");
             // colours per transport pass: up to 8 (one front propagation per group)
             const int RG = R > 4 ? 8 : (R >= 3 ? 4 : (R == 2 ? 2 : 1));
-            // the bulk exchanges halos inside a launch unless tune[7] = 1
-            const bool phi_x = d.tune[7] != 1;
+            // the bulk of up to four colours exchanges halos inside a launch unless
+            // tune[7] = 1 (4 rounds per launch, else 2).  With eight colours the
+            // exchange's registers halve the resident CTAs (256 threads each) and the
+            // block-Jacobi launches measured faster (labels of 8 patches at 2049^2:
+            // 12.6 against 15.2 ms)
+            const bool phi_x = d.tune[7] != 1 && RG <= 4;
+            const int prounds = d.tune[1] > 0 ? d.tune[1] : (phi_x ? 4 : 2);
             float *f0 = alloc_n<float>(p, N * RG), *f1 = alloc_n<float>(p, N * RG), *r32 = alloc_n<float>(p, N * RG);
             double *phig = alloc_n<double>(p, N * RG);
             float *rmax = alloc_n<float>(p, 1);
@@ -3299,7 +3332,7 @@ hjbp_status solve2d(hjbp_plan &p) {
                     constexpr int G = decltype(tag)::value;
                     check_cuda(cudaFuncSetAttribute(k_phi2d<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)sizeof(PhiSmem<G, false>)), "phi smem");
-                    check_cuda(cudaFuncSetAttribute(k_phi2d<G, false, true>,
+                    check_cuda(cudaFuncSetAttribute(k_phi2d<G, false, (G <= 4)>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)sizeof(PhiSmem<G, false>)), "phi smem");
                     check_cuda(cudaFuncSetAttribute(k_phi2d<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -3309,12 +3342,12 @@ hjbp_status solve2d(hjbp_plan &p) {
                     ++p.stats.kernel_launches;
                     RunResult rp = run_tiles(p, g, sched, std::max(tolp, 2e-7), cap, [&](int par, int) {
                         ptimer.begin();
-                        if (phi_x)
-                            k_phi2d<G, false, true><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, false>),
+                        if (G <= 4 && phi_x)
+                            k_phi2d<G, false, (G <= 4)><<<sched.ntiles, 32 * phi_warps<G>(), sizeof(PhiSmem<G, false>),
                                                       st>>>(g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds,
                                                             dpc, pupd);
                         else
-                            k_phi2d<G, false><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, false>), st>>>(
+                            k_phi2d<G, false><<<sched.ntiles, 32 * phi_warps<G>(), sizeof(PhiSmem<G, false>), st>>>(
                                 g, code0, p.astar, f0, f1, nullptr, sched.d, par, prounds, dpc, pupd);
                         ptimer.end();
                         ++p.stats.kernel_launches;
@@ -3339,7 +3372,7 @@ hjbp_status solve2d(hjbp_plan &p) {
                         const float told = std::max((float)(tolp * 0.1), 1e-3f * hr);
                         RunResult rc = run_tiles(p, g, sched, told, cap, [&](int par, int) {
                             ptimer.begin();
-                            k_phi2d<G, true><<<sched.ntiles, 32 * (G < 4 ? G : 4), sizeof(PhiSmem<G, true>), st>>>(
+                            k_phi2d<G, true><<<sched.ntiles, 32 * phi_warps<G>(), sizeof(PhiSmem<G, true>), st>>>(
                                 g, code0, p.astar, f0, f1, r32, sched.d, par, prounds, dpc, pupd);
                             ptimer.end();
                             ++p.stats.kernel_launches;

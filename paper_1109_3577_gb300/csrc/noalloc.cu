@@ -40,7 +40,8 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
 __global__ void k_schedule2d(Grid2 g, TileSched s, int par, double tol, int launch);
 __global__ void __launch_bounds__(32) k_reach2d(Grid2 g, const int8_t *code, uint8_t *rch, TileSched s, int par,
                                                 ReachTable2 rt, int passes, const double *dterm,
-                                                const uint8_t *astar, const Cone2 *cone);
+                                                const uint8_t *astar, const Cone2 *cone, uint64_t *cache,
+                                                uint8_t *cvalid);
 __global__ void __launch_bounds__(32) k_peel2d(Grid2 g, int8_t *code, TileSched s, int par, ReachTable2 rt,
                                                const double *dterm, const uint8_t *astar, const Cone2 *cone);
 __global__ void k_reach_prune(int64_t N, int8_t *code, const uint8_t *rch, unsigned long long *removed);
@@ -337,7 +338,8 @@ extern "C" hjbp_status hjbp_solve_global2d_noalloc(const hjbp_problem_desc *desc
         if (!conv) return fail_static(HJBP_ECUDA, "peeling did not settle");
         NA_CHECK(cudaMemsetAsync(rch, 0, (size_t)N, st));
         hjbp_status rs = run(st, g, s, ntiles, iota, 0.5, 1 << 18, &conv, [&](int par) {
-            k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt, 2, nullptr, nullptr, nullptr);
+            k_reach2d<<<ntiles, 32, 0, st>>>(g, code, rch, s, par, rt, 2, nullptr, nullptr, nullptr, nullptr,
+                                             nullptr);   // no row-set cache: nothing to allocate
         });
         if (rs != HJBP_OK) return rs;
         if (!conv) return fail_static(HJBP_ECUDA, "reachability sweep did not settle");
