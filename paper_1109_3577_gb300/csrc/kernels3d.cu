@@ -820,10 +820,14 @@ __device__ __forceinline__ uint32_t usable_union3(uint32_t usable, int lx, int l
 
 // kGen: the corner sets of the per-node feet from the column tables.
 template <bool kGen>
+// cache, cvalid (optional): the row sets below depend on the codes only, which
+// do not change during one reach run, so the first launch that visits a tile
+// stores them (29 words per thread) and later ones load them.
 __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restrict__ code,
                                                   uint8_t *__restrict__ rch, TileSched s, int par, ReachTable3 rt,
                                                   const double *__restrict__ dterm, const Gen3 gen,
-                                                  const Cone3 *__restrict__ cone, const uint8_t *__restrict__ astar) {
+                                                  const Cone3 *__restrict__ cone, const uint8_t *__restrict__ astar,
+                                                  uint32_t *__restrict__ cache, uint8_t *__restrict__ cvalid) {
     if (blockIdx.x == 0 && threadIdx.x == 0) s.count[par ^ 1] = 0;
     if ((int)blockIdx.x >= s.count[par]) return;
     const int t = (par ? s.list[1] : s.list[0])[blockIdx.x];
@@ -835,6 +839,7 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
     __shared__ int flips_s;
     const int tid = threadIdx.x;
     if (tid == 0) flips_s = 0;
+    const bool cached = cache && cvalid[t];
     for (int e = tid; e < E * E * E; e += blockDim.x) {
         const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
         const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
@@ -842,9 +847,11 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
         int8_t cd = kHard;
         if (x < g.n0 && y < g.n1 && z < g.n2) {
             const int64_t i = ((int64_t)z * g.n1 + y) * g.n0 + x;
-            cd = code[i];
             v = rch[i];
-            if (dterm) df = dterm[i] < kU0Bound;
+            if (!cached) {
+                cd = code[i];
+                if (dterm) df = dterm[i] < kU0Bound;
+            }
         }
         sr[lz][ly][lx] = v;
         sc[lz][ly][lx] = cd;
@@ -861,9 +868,16 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
 #pragma unroll
     for (int b = 0; b < 27; ++b) cand_b[b] = 0u;
     uint32_t term_b = 0u, open_b = 0u;
+    uint32_t *cl = cache ? cache + (int64_t)t * 29 * kT3n : nullptr;
+    if (cached) {
+#pragma unroll
+        for (int b = 0; b < 27; ++b) cand_b[b] = cl[b * kT3n + tid];
+        term_b = cl[27 * kT3n + tid];
+        open_b = cl[28 * kT3n + tid];
+    } else {
     for (int lx = 1; lx <= kT3; ++lx) {
         const int8_t cd = sc[lz][ly][lx];
-        if (cd >= 0 && cd < kTargetBase && !sr[lz][ly][lx]) {
+        if (cd >= 0 && cd < kTargetBase) {
             const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
             uint32_t same = 0, term = 0;
 #pragma unroll
@@ -890,6 +904,14 @@ __global__ void __launch_bounds__(kT3n) k_reach3d(Grid3 g, const int8_t *__restr
             for (int b = 0; b < 27; ++b) cand_b[b] |= ((cs >> b) & 1u) << lx;
             open_b |= 1u << lx;
         }
+    }
+    if (cl) {
+#pragma unroll
+        for (int b = 0; b < 27; ++b) cl[b * kT3n + tid] = cand_b[b];
+        cl[27 * kT3n + tid] = term_b;
+        cl[28 * kT3n + tid] = open_b;
+        if (tid == 0) cvalid[t] = 1;   // read by later launches only
+    }
     }
     // rows as bit sets, double-buffered: the halo rows (ly or lz 0 or 9) in both
     __shared__ uint32_t rows[2][E][E];
@@ -2098,6 +2120,9 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
            const double *dterm = nullptr, const Gen3 *gen = nullptr, const Cone3 *cone = nullptr) {
     const ReachTable3 rt = make_reach3(p);
     unsigned long long *removed = alloc3<unsigned long long>(p, 1);
+    // per tile the candidate, terminal and free row sets of k_reach3d (29 words per thread)
+    uint32_t *rcache = alloc3<uint32_t>(p, (int64_t)std::max(1, s.ntiles) * 29 * kT3n);
+    uint8_t *rvalid = alloc3<uint8_t>(p, std::max(1, s.ntiles));
     int total = 0;
     // each round prunes at least one node or ends the loop, so it ends after at
     // most N rounds
@@ -2112,12 +2137,15 @@ int reach3(hjbp_plan &p, const Grid3 &g, int8_t *code, uint8_t *rch, Sched3 &s, 
         total += pe.launches;
         if (!pe.converged) throw HjbpError{HJBP_ECUDA, "peeling did not settle"};
         check_cuda(cudaMemsetAsync(rch, 0, (size_t)N, p.stream), "reach reset");
+        // the codes changed (peel, prune): the tiles' cached row sets are stale
+        check_cuda(cudaMemsetAsync(rvalid, 0, (size_t)std::max(1, s.ntiles), p.stream), "reach cache reset");
         Run3 rr = run_tiles3(p, g, s, 0.5f, kReachCap3, [&](int par) {
             if (gen)
-                k_reach3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, *gen, cone, p.astar);
+                k_reach3d<true><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, *gen, cone, p.astar,
+                                                                 rcache, rvalid);
             else
                 k_reach3d<false><<<s.ntiles, kT3n, 0, p.stream>>>(g, code, rch, s.d, par, rt, dterm, Gen3{}, cone,
-                                                                  p.astar);
+                                                                  p.astar, rcache, rvalid);
             ++p.stats.kernel_launches;
         });
         total += rr.launches;

@@ -192,9 +192,10 @@ size_t footprint(const hjbp_problem_desc *d) {
         for (int a = 0; a < d->dim; ++a) Nc *= d->n_coarse[a];
     }
     const int R = d->target_kind == HJBP_TARGET_BALLS ? d->n_targets : d->n_parts;
-    const int rg = R >= 4 ? 4 : R;
+    const int rg = R > 4 ? 8 : (R >= 4 ? 4 : R);
     // outputs + codes/h + value buffers + colour planes (FP32 x3, FP64 x2 per group) + phi (R planes)
-    size_t b = (size_t)N * (8 + 1 + 4 + 8 + 8 + 1 + 1 + 1 + 4 * 3 + 16);
+    // + the reach's cached row sets (2D: 2.75 B per node, 3D: 14.5 B)
+    size_t b = (size_t)N * (8 + 1 + 4 + 8 + 8 + 1 + 1 + 1 + 4 * 3 + 16 + (d->dim == 3 ? 15 : 3));
     // patchy: + U0, a*, colour planes, phi, the patch lists (node ids, tile entries)
     if (Nc) b += (size_t)N * (8 + 1 + (size_t)rg * (4 * 3 + 8) + 8 * (size_t)R + 4 + 8) + (size_t)Nc * 40;
     return b + (size_t(8) << 20);
