@@ -460,6 +460,37 @@ __device__ inline int target_part2(const TargetSet &ts, const Grid2 &g, double x
 }
 
 // Device-side state of one tile-sweep phase (active list, parities, ...).
+// Grid coordinates of node i of a row-major grid (n0 nodes per row, n1 rows
+// per plane).  Node counts below 2^31 (every grid in practice) use 32-bit
+// integer division, which runs on the integer and FP32 units; a 64-bit
+// division is a long instruction sequence on the narrow FP64 pipe of GB300.
+__device__ __forceinline__ void node_xy(int64_t i, int n0, int &x, int &y) {
+    if (i <= 0x7fffffffll) {
+        const unsigned j = (unsigned)i, q = j / (unsigned)n0;
+        y = (int)q;
+        x = (int)(j - q * (unsigned)n0);
+    } else {
+        const int64_t q = i / n0;
+        y = (int)q;
+        x = (int)(i - q * n0);
+    }
+}
+__device__ __forceinline__ void node_xyz(int64_t i, int n0, int n1, int &x, int &y, int &z) {
+    int r;
+    if (i <= 0x7fffffffll) {
+        const unsigned j = (unsigned)i, q = j / (unsigned)n0;
+        x = (int)(j - q * (unsigned)n0);
+        r = (int)q;
+    } else {
+        const int64_t q = i / n0;
+        x = (int)(i - q * n0);
+        r = (int)q;   // rows fit in 32 bits: n1 n2 < 2^31
+    }
+    const unsigned q2 = (unsigned)r / (unsigned)n1;
+    z = (int)q2;
+    y = (int)((unsigned)r - q2 * (unsigned)n1);
+}
+
 struct TileSched {
     int *list[2];         // active tile lists (double-buffered by launch parity)
     int *count;           // count[2]

@@ -43,7 +43,8 @@ __global__ void k_setup2d(Grid2 g, SpeedParams sp, TargetSet ts, double extra, i
                           double *__restrict__ fixed, DynParams dp, ObstacleSet os, SpeedLines sl) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+        int ix, iy;
+        node_xy(i, g.n0, ix, iy);
         const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
         const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
         double gap = 0.0, e[2];
@@ -1199,7 +1200,8 @@ __global__ void k_value_wide2d(Grid2 g, const int8_t *__restrict__ code, const T
         const T old = uin[i];
         T nw = old;
         if (cd >= 0 && cd < kTargetBase) {
-            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            int ix, iy;
+            node_xy(i, g.n0, ix, iy);
             const int8_t tg = (int8_t)(cd + kTargetBase);
             T nb[3][3];
 #pragma unroll
@@ -1537,7 +1539,8 @@ __global__ void k_gather2d(Grid2 g, const uint8_t *__restrict__ latest, const T 
                            const T *__restrict__ b1, T *__restrict__ out_t, double *__restrict__ out64) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.n0), y = (int)(i / g.n0);
+        int x, y;
+        node_xy(i, g.n0, x, y);
         const int tt = tile_of(g, x, y);
         const T v = (tt >= 0 && latest[tt]) ? b1[i] : b0[i];
         if (out_t) out_t[i] = v;
@@ -1567,7 +1570,8 @@ __global__ void k_u0_2d(Grid2 g, Grid2 gc, const int8_t *__restrict__ code, cons
             if (dlit) dlit[i] = Num<double>::big();
             continue;
         }
-        const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+        int ix, iy;
+        node_xy(i, g.n0, ix, iy);
         const double xi0 = (double)ix * (double)(gc.n0 - 1) / (double)(g.n0 - 1);
         const double xi1 = (double)iy * (double)(gc.n1 - 1) / (double)(g.n1 - 1);
         int b0 = (int)floor(xi0), b1 = (int)floor(xi1);
@@ -1601,7 +1605,8 @@ __global__ void k_feedback2d(Grid2 g, const int8_t *__restrict__ code, const dou
             astar[i] = kNoControl;
             continue;
         }
-        const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+        int ix, iy;
+        node_xy(i, g.n0, ix, iy);
         double nb[3][3];
         for (int dy = 0; dy < 3; ++dy)
             for (int dx = 0; dx < 3; ++dx) {
@@ -2042,7 +2047,8 @@ __global__ void k_phi_collect2d(Grid2 g, const uint8_t *__restrict__ latest, con
                                 const float *__restrict__ b1, double *__restrict__ out, int add) {
     const int64_t N = (int64_t)g.n0 * g.n1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.n0), y = (int)(i / g.n0);
+        int x, y;
+        node_xy(i, g.n0, x, y);
         const int tt = tile_of(g, x, y);
         const float *src = (tt >= 0 && latest[tt]) ? b1 : b0;
 #pragma unroll
@@ -2117,7 +2123,8 @@ __global__ void k_fill2d(Grid2 g, const int8_t *__restrict__ lin, int8_t *__rest
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         int8_t v = lin[i];
         if (v == -2) {
-            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            int ix, iy;
+            node_xy(i, g.n0, ix, iy);
             int8_t nv = -2;
             if (iy > 0 && lin[i - g.n0] >= 0) nv = lin[i - g.n0];
             else if (ix > 0 && lin[i - 1] >= 0) nv = lin[i - 1];
@@ -2214,7 +2221,8 @@ __global__ void k_polish2d(Grid2 g, const int8_t *__restrict__ code, const doubl
         const int8_t cd = code[i];
         double v = uin[i];
         if (cd >= 0 && cd < kTargetBase) {
-            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            int ix, iy;
+            node_xy(i, g.n0, ix, iy);
             const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
             double nb[3][3];
             float nf[3][3];
@@ -2306,7 +2314,8 @@ __global__ void k_polish2d_pf(Grid2 g, const int8_t *__restrict__ code, const do
         const int8_t cd = code[i];
         double v = uin[i];
         if (cd >= 0 && cd < kTargetBase && v < Num<double>::thresh()) {
-            const int ix = (int)(i % g.n0), iy = (int)(i / g.n0);
+            int ix, iy;
+            node_xy(i, g.n0, ix, iy);
             const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
             float nf[3][3];
             unsigned same = 0;

@@ -136,9 +136,8 @@ __global__ void k_setup3d(Grid3 g, SpeedParams sp, TargetSet ts, double extra, i
                           const GenCtl *__restrict__ gctl = nullptr) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % g.n0);
-        const int64_t r = i / g.n0;
-        const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+        int ix, iy, iz;
+        node_xyz(i, g.n0, g.n1, ix, iy, iz);
         const double x0 = __dadd_rn(g.lo0, __dmul_rn((double)ix, g.k));
         const double x1 = __dadd_rn(g.lo1, __dmul_rn((double)iy, g.k));
         const double x2 = __dadd_rn(g.lo2, __dmul_rn((double)iz, g.k));
@@ -1055,9 +1054,8 @@ __global__ void k_gather3d(Grid3 g, const uint8_t *__restrict__ latest, const T 
                            const T *__restrict__ b1, T *__restrict__ out_t, double *__restrict__ out64) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.n0);
-        const int64_t r = i / g.n0;
-        const int y = (int)(r % g.n1), z = (int)(r / g.n1);
+        int x, y, z;
+        node_xyz(i, g.n0, g.n1, x, y, z);
         const int tt = tile_of3(g, x, y, z);
         const T v = (tt >= 0 && latest[tt]) ? b1[i] : b0[i];
         if (out_t) out_t[i] = v;
@@ -1149,9 +1147,8 @@ __global__ void k_u0_3d(Grid3 g, Grid3 gc, const int8_t *__restrict__ code, cons
             if (u0f) u0f[i] = Num<float>::big();
             continue;
         }
-        const int ix = (int)(i % g.n0);
-        const int64_t r = i / g.n0;
-        const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+        int ix, iy, iz;
+        node_xyz(i, g.n0, g.n1, ix, iy, iz);
         const double xi[3] = {(double)ix * (double)(gc.n0 - 1) / (double)(g.n0 - 1),
                               (double)iy * (double)(gc.n1 - 1) / (double)(g.n1 - 1),
                               (double)iz * (double)(gc.n2 - 1) / (double)(g.n2 - 1)};
@@ -1583,9 +1580,8 @@ __global__ void k_phi_collect3d(Grid3 g, const uint8_t *__restrict__ latest, con
                                 const float *__restrict__ b1, double *__restrict__ out, int add) {
     const int64_t N = (int64_t)g.n0 * g.n1 * g.n2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.n0);
-        const int64_t r = i / g.n0;
-        const int y = (int)(r % g.n1), z = (int)(r / g.n1);
+        int x, y, z;
+        node_xyz(i, g.n0, g.n1, x, y, z);
         const int tt = tile_of3(g, x, y, z);
         const float *src = (tt >= 0 && latest[tt]) ? b1 : b0;
 #pragma unroll
@@ -1649,9 +1645,8 @@ __global__ void k_fill3d(Grid3 g, const int8_t *__restrict__ lin, int8_t *__rest
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         int8_t v = lin[i];
         if (v == -2) {
-            const int ix = (int)(i % g.n0);
-            const int64_t r = i / g.n0;
-            const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+            int ix, iy, iz;
+            node_xyz(i, g.n0, g.n1, ix, iy, iz);
             int8_t nv = -2;
             if (iz > 0 && lin[i - sz] >= 0) nv = lin[i - sz];
             else if (iy > 0 && lin[i - sy] >= 0) nv = lin[i - sy];
@@ -1725,9 +1720,8 @@ __global__ void k_polish3d(Grid3 g, const int8_t *__restrict__ code, const doubl
         const int8_t cd = code[i];
         double v = uin[i];
         if (cd >= 0 && cd < kTargetBase) {
-            const int ix = (int)(i % g.n0);
-            const int64_t r = i / g.n0;
-            const int iy = (int)(r % g.n1), iz = (int)(r / g.n1);
+            int ix, iy, iz;
+            node_xyz(i, g.n0, g.n1, ix, iy, iz);
             const int8_t tg = (int8_t)(cd + kTargetBase), pr = (int8_t)(-2 - cd);
             // only FP32 copies and masks stay live (FP64 compares and conversions
             // run at 1/64 rate); FP64 candidates re-read their corners.  Outside
